@@ -1,0 +1,260 @@
+"""Pins of the oracle's right-hand side and integrator against what the paper and the
+mathematics fix: continuum limits of each discrete term (Eqs. continuity:sph,
+mom:sph:press, mom:sph:visc, XSPH), conservation and dissipation invariants, the
+equation of state, closed forms of the first dam-break step and of free fall under
+the predictor-corrector of Sec. 2.1, and the Taylor-Green decay of Sec. 4.1."""
+import math
+
+import numpy as np
+import pytest
+import scipy.integrate as integrate
+
+import oracle as O
+import workloads as W
+
+
+def block(kind=W.QUINTIC, hdx=1.0, n=40):
+    """Fluid-only square lattice in a non-periodic box, at rest, rho = rho0."""
+    wl = W.taylor_green_2d(n=n, jitter=0.0, hdx=hdx)
+    wl.kernel = kind
+    wl.periodic = [0, 0, 0]
+    wl.lo, wl.hi = [-1.0, -1.0, 0.0], [2.0, 2.0, 0.0]
+    wl.nu = 0.0
+    s = O.state_of(wl)
+    for k in "uvw":
+        s[k][:] = 0.0
+    kh = (3.0 if kind == W.QUINTIC else 2.0) * wl.h
+    inner = (s["x"] > kh) & (s["x"] < 1 - kh) & (s["y"] > kh) & (s["y"] < 1 - kh)
+    return wl, s, inner
+
+
+def with_(s, **kw):
+    out = dict(s)
+    out.update(kw)
+    return out
+
+
+@pytest.mark.parametrize("kind,hdx,tol", [(W.QUINTIC, 1.0, 2e-3), (W.WENDLAND_C2, 1.3, 3e-2)])
+def test_continuity_limit(kind, hdx, tol):
+    """Eq. (continuity:sph) approximates -rho div u: u = beta x gives -rho0 beta."""
+    wl, s, inner = block(kind, hdx)
+    beta = 0.3
+    r = O.rhs(wl, with_(s, u=beta * s["x"]))
+    assert np.max(np.abs(r["arho"][inner] / (-wl.rho0 * beta) - 1.0)) < tol
+
+
+@pytest.mark.parametrize("kind,hdx,tol", [(W.QUINTIC, 1.0, 2e-3), (W.WENDLAND_C2, 1.3, 3e-2)])
+def test_pressure_gradient_limit(kind, hdx, tol):
+    """Eq. (mom:sph:press) approximates -grad p / rho for a linear density field, with
+    p from Eq. (eos): dp/dx = c0^2 (rho/rho0)^(gamma-1) drho/dx."""
+    wl, s, inner = block(kind, hdx)
+    eps = 1e-4
+    rho = wl.rho0 * (1.0 + eps * s["x"])
+    r = O.rhs(wl, with_(s, rho=rho))
+    dpdx = wl.c0 ** 2 * (rho / wl.rho0) ** 6 * wl.rho0 * eps
+    assert np.max(np.abs(r["ax"][inner] / (-dpdx / rho)[inner] - 1.0)) < tol
+    assert np.max(np.abs(r["ay"][inner])) < 1e-12 * np.max(np.abs(r["ax"]))
+
+
+@pytest.mark.parametrize("eta,tol", [(0.0, 2e-3), (0.01, 1e-2)])
+def test_laminar_viscosity_limit(eta, tol):
+    """Eq. (mom:sph:visc) approximates nu lap u: u = (y^2, 0) gives (2 nu, 0)."""
+    wl, s, inner = block()
+    nu = 0.01
+    r = O.rhs(wl, with_(s, u=s["y"] ** 2), nu=nu, eta=eta)
+    assert np.max(np.abs(r["ax"][inner] / (2 * nu) - 1.0)) < tol
+    assert np.max(np.abs(r["ay"][inner])) < 1e-12
+
+
+def test_xsph_limit():
+    """XSPH = eps sum_j m_j / rho_bar (u_j - u_i) W_ij; for u = (x^2, 0) at rho0 the
+    lattice sum tends to eps times the second moment of W, M2 = (1/d) int r^2 W dV."""
+    wl, s, inner = block()
+    eps = 0.5
+    r = O.rhs(wl, with_(s, u=s["x"] ** 2), xsph_eps=eps)
+    kh = 3.0 * wl.h
+    M2 = integrate.quad(lambda q: O.kernel(W.QUINTIC, 2, wl.h, q)[0] * q ** 3 * 2 * math.pi,
+                        0.0, kh, limit=200)[0] / 2.0
+    assert np.max(np.abs(r["xsx"][inner] / (eps * M2) - 1.0)) < 1e-3
+    # uniform velocity: no correction at all
+    r = O.rhs(wl, with_(s, u=np.full_like(s["x"], 0.7)), xsph_eps=eps)
+    assert np.max(np.abs(r["xsx"])) == 0.0
+
+
+def test_eos_sound_speed():
+    """Eq. (eos): p(rho0) = 0 and dp/drho at rho0 equals c0^2."""
+    wl, s, _ = block()
+    d = 1e-6
+    rho = np.full_like(s["x"], wl.rho0)
+    rho[0], rho[1] = wl.rho0 * (1 + d), wl.rho0 * (1 - d)
+    r = O.rhs(wl, with_(s, rho=rho))
+    assert np.all(r["p"][2:] == 0.0)
+    slope = (r["p"][0] - r["p"][1]) / (2 * d * wl.rho0)
+    assert abs(slope / wl.c0 ** 2 - 1.0) < 1e-8
+
+
+def _random_tg(n=24, seed=3):
+    wl = W.taylor_green_2d(n=n)
+    s = O.state_of(wl)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    s["u"] = rng.normal(0, 1, s["x"].shape)
+    s["v"] = rng.normal(0, 1, s["x"].shape)
+    s["rho"] = wl.rho0 * (1 + 0.01 * rng.normal(0, 1, s["x"].shape))
+    return wl, s
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_momentum_conserved(dim):
+    """Pressure, laminar and artificial viscosity terms are pairwise antisymmetric, so on
+    a periodic domain with g = 0 the total force vanishes."""
+    if dim == 2:
+        wl, s = _random_tg()
+    else:
+        wl = W.taylor_green_3d(n=10)
+        s = O.state_of(wl)
+        rng = np.random.Generator(np.random.PCG64(4))
+        for k in "uvw":
+            s[k] = rng.normal(0, 1, s["x"].shape)
+        s["rho"] = wl.rho0 * (1 + 0.01 * rng.normal(0, 1, s["x"].shape))
+    r = O.rhs(wl, s, alpha=0.1)
+    comps = [r["ax"], r["ay"], r["az"]][:dim]
+    for a in comps:
+        total = np.sum(s["m"] * a)
+        assert abs(total) <= 1e-12 * np.sum(np.abs(s["m"] * a))
+
+
+@pytest.mark.parametrize("which", ["laminar", "artificial"])
+def test_viscous_terms_dissipate(which):
+    """At uniform density (p = 0) the viscous power sum_i m_i u_i . a_i is negative."""
+    wl, s = _random_tg()
+    s["rho"][:] = wl.rho0
+    over = dict(nu=0.05, alpha=0.0) if which == "laminar" else dict(nu=0.0, alpha=0.1)
+    r = O.rhs(wl, s, **over)
+    power = np.sum(s["m"] * (s["u"] * r["ax"] + s["v"] * r["ay"]))
+    assert power < 0.0
+    # each pair contributes with one sign: removing half of the particles' motion
+    # still gives a negative power
+    s2 = dict(s)
+    s2["u"] = np.where(np.arange(s["x"].shape[0]) % 2 == 0, s["u"], 0.0)
+    r2 = O.rhs(wl, s2, **over)
+    assert np.sum(s2["m"] * (s2["u"] * r2["ax"] + s2["v"] * r2["ay"])) < 0.0
+
+
+def test_artificial_viscosity_only_acts_on_approaching_pairs():
+    """Monaghan AV is switched on by v_ij . r_ij < 0: a purely expanding flow gets no AV
+    force (p = 0 at rho0), a compressing one does."""
+    wl, s, inner = block()
+    r = O.rhs(wl, with_(s, u=0.2 * s["x"] ** 3, v=0.1 * s["y"] ** 3), alpha=0.1)
+    assert np.max(np.abs(r["ax"])) == 0.0 and np.max(np.abs(r["ay"])) == 0.0
+    r = O.rhs(wl, with_(s, u=-0.2 * s["x"] ** 3, v=-0.1 * s["y"] ** 3), alpha=0.1)
+    assert np.max(np.abs(r["ax"][inner])) > 0.0
+
+
+def test_dam_break_first_step_closed_form():
+    """At t = 0 (rho = rho0 so p = 0, u = 0) every fluid particle has a = g, arho = 0.
+    After the first kick-drift-kick step, particles with no wall neighbour have
+    u = g dt, x = x0 + dt (dt/2 g) and unchanged density."""
+    wl = W.dam_break_2d(dx=0.04)
+    s = O.state_of(wl)
+    fluid = s["role"] == W.FLUID
+    r0 = O.rhs(wl, s)
+    assert np.all(r0["ax"][fluid] == 0.0) and np.all(r0["ay"][fluid] == wl.g[1])
+    assert np.all(r0["arho"] == 0.0)
+    st, hist = O.run(wl, s, wl.dt, 1)
+    # particles farther than the support from every wall particle
+    kh = 2.0 * wl.h
+    wx, wy = s["x"][~fluid], s["y"][~fluid]
+    far = np.array([np.min((wx - a) ** 2 + (wy - b) ** 2) > (kh + 0.5 * abs(wl.g[1]) * wl.dt ** 2) ** 2
+                    for a, b in zip(s["x"], s["y"])]) & fluid
+    assert far.sum() > 100
+    half = 0.5 * wl.dt * wl.g[1]
+    assert np.all(st["v"][far] == half + half)
+    assert np.all(st["u"][far] == 0.0)
+    assert np.all(st["y"][far] == s["y"][far] + wl.dt * half)
+    assert np.all(st["rho"][far] == wl.rho0)
+    # walls do not move
+    assert np.all(st["x"][~fluid] == s["x"][~fluid]) and np.all(st["y"][~fluid] == s["y"][~fluid])
+
+
+def test_free_fall_is_exact_under_kick_drift_kick():
+    """A lone particle under constant g: x(t) = x0 + u0 t + g t^2 / 2, u = u0 + g t."""
+    wl = W.dam_break_2d(dx=0.04)
+    s = {k: np.array([v[0]]) for k, v in O.state_of(wl).items()}
+    s["x"][0], s["y"][0], s["u"][0], s["v"][0] = 1.7, 3.1, 0.4, 2.0
+    steps = 400
+    st, hist = O.run(wl, s, wl.dt, steps)
+    t = steps * wl.dt
+    g = wl.g[1]
+    assert abs(st["x"][0] - (1.7 + 0.4 * t)) < 1e-12
+    assert abs(st["y"][0] - (3.1 + 2.0 * t + 0.5 * g * t * t)) < 1e-12
+    assert abs(st["v"][0] - (2.0 + g * t)) < 1e-12
+    assert abs(hist[-1, 0] - t) < 1e-15
+
+
+def test_periodic_wrap_keeps_particles_in_the_box():
+    wl = W.taylor_green_2d(n=20)
+    s = O.state_of(wl)
+    s["u"][:] = 3.0
+    s["v"][:] = -2.0
+    st, _ = O.run(wl, s, 0.004, 30)
+    for c in ("x", "y"):
+        assert np.all(st[c] >= 0.0) and np.all(st[c] < 1.0)
+    # uniform translation: relative positions are kept (modulo the period)
+    d = (st["x"] - s["x"] - 30 * 0.004 * 3.0 + 0.5) % 1.0 - 0.5
+    assert np.max(np.abs(d)) < 1e-12
+
+
+def _tg_amplitude(st):
+    ut = -np.cos(2 * np.pi * st["x"]) * np.sin(2 * np.pi * st["y"])
+    vt = np.sin(2 * np.pi * st["x"]) * np.cos(2 * np.pi * st["y"])
+    return np.sum(st["u"] * ut + st["v"] * vt) / np.sum(ut * ut + vt * vt)
+
+
+def test_taylor_green_decay():
+    """Sec. 4.1 exact solution: the vortex amplitude decays as exp(-8 pi^2 t / Re).
+    Initial density from the exact pressure through Eq. (eos); lattice without jitter."""
+    wl = W.taylor_green_2d(n=50, jitter=0.0)
+    s = O.state_of(wl)
+    p = -(np.cos(4 * np.pi * s["x"]) + np.cos(4 * np.pi * s["y"])) / 4.0
+    s["rho"] = wl.rho0 * (1.0 + wl.gamma * p / (wl.rho0 * wl.c0 ** 2)) ** (1.0 / wl.gamma)
+    b = -8 * np.pi ** 2 / 100.0
+    a0 = _tg_amplitude(s)
+    st = s
+    amps = []
+    for k in range(2):
+        st, _ = O.run(wl, st, wl.dt, 50)
+        amps.append(_tg_amplitude(st) / a0)
+    for k, a in enumerate(amps):
+        assert abs(a / math.exp(b * 0.025 * (k + 1)) - 1.0) < 5e-3
+    fitted = math.log(amps[-1]) / 0.05
+    assert abs(fitted / b - 1.0) < 0.05
+
+
+def test_summation_density_run_matches_summation_of_final_positions():
+    wl = W.taylor_green_2d(n=24)
+    wl.density = 1
+    s = O.state_of(wl)
+    st, _ = O.run(wl, s, wl.dt, 5)
+    r = O.rhs(wl, st)
+    assert np.max(np.abs(r["rho"] - st["rho"])) == 0.0
+
+
+def test_worked_example_constants():
+    """The constants printed for the Sec. 3.2 dam-break example: the oracle's EOS has
+    B = rho0 c0^2 / gamma, and at rest every fluid particle feels a = (0, -9.81)."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "dam_break_listing.json")))
+    assert abs(g["mass"] - g["dx"] ** 2 * g["rho"]) < 1e-12
+    wl = W.dam_break_2d(dx=0.04, rho0=g["rho0"], hdx=g["hdx"])
+    wl.c0, wl.gamma, wl.g = g["c0"], float(g["gamma"]), [0.0, g["gravity_y"], 0.0]
+    s = O.state_of(wl)
+    d = 1e-3
+    s["rho"][0] = g["rho0"] * (1 + d)
+    r = O.rhs(wl, s)
+    assert abs(r["p"][0] - g["B"] * ((1 + d) ** g["gamma"] - 1.0)) < 1e-9 * g["B"]
+    fluid = s["role"] == W.FLUID
+    far = fluid.copy()
+    far[0] = False
+    far &= (s["x"] - s["x"][0]) ** 2 + (s["y"] - s["y"][0]) ** 2 > (2 * wl.h) ** 2
+    assert np.all(r["ay"][far] == g["gravity_y"]) and np.all(r["ax"][far] == 0.0)
