@@ -1,0 +1,397 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 WCSPH particle loop.
+
+A step is one pass of the whole per-timestep hot path over the workload: drift + cell
+keys, radix sort, reorder + EOS, cell table, fused pair loop with the corrector kick and
+the FP64 reductions (one captured CUDA graph). Default workload: the 2D dam break of the
+precision configuration (20,000 fluid + 3,618 wall particles, Wendland C2, FP32 pair loops
+with an FP64 integrator). Inputs are resident in HBM; L2 is flushed (a 512 MB write)
+between timed steps because the working set (a few MB) would otherwise stay in L2.
+
+Prints one JSON line. ``--impl reference`` times the CPU oracle on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "neighbour-pair interactions/s and particle-steps/s, FP32 vs FP64 at stated error"
+UNIT = "neighbour-pair interactions/s"
+FP32_LANES_PER_SM = 128   # FP32 CUDA-core lanes per Blackwell SM (4 sub-partitions x 32)
+SMS = 152
+SM_MAX_MHZ = 2070.0
+
+
+def workload(name: str):
+    import workloads as W
+    table = {
+        "dam_break_2d": lambda: W.dam_break_2d(),
+        "taylor_green_2d": lambda: W.taylor_green_2d(),
+        "taylor_green_3d": lambda: W.taylor_green_3d(),
+        "dam_break_3d": lambda: W.dam_break_3d(),
+    }
+    return table[name]()
+
+
+def describe(wl) -> dict:
+    kern = "quintic spline" if wl.kernel == 0 else "Wendland C2"
+    prec = "FP32 pair loops / FP64 integrator" if wl.precision == 1 else "FP64"
+    return {
+        "workload": f"{wl.name}: {wl.n_fluid:,} fluid + {wl.n_total - wl.n_fluid:,} wall particles, "
+                    f"{wl.dim}D, {kern} h={wl.h:g}, {prec}, alpha={wl.alpha:g}, xsph={wl.xsph_eps:g}, "
+                    f"nu={wl.nu:g}, dt={wl.dt:.6g}, neighbour rebuild every step",
+        "particles": wl.n_total,
+        "fluid_particles": wl.n_fluid,
+        "l2": "flushed between timed steps (512 MB write)",
+        "parallelism": "replicas (one independent problem per GPU)",
+    }
+
+
+# --------------------------------------------------------------------- flops
+def pair_flops(wl) -> dict:
+    """Algorithmic FP32 operations per candidate and per interacting pair of the fused loop
+    (add, sub, mul, div, sqrt = 1; a Neumaier compensated add = 4), by destination role."""
+    d = wl.dim
+    cand = (d) + d + (d - 1)                      # differences, squares, sum
+    base = 2 + (5 if wl.kernel == 1 else 8) + 1   # sqrt, q; kernel f(q); gfac
+    base += d + (2 * d - 1)                       # v_ij, v_ij . r_ij
+    cont = 2 + 4                                  # m_j Gk (v.r), compensated add
+    wall_dest = base + cont
+    fluid = base + cont + 1 + 2 + 2               # Pr_i + Pr_j, rhobar, cg
+    if wl.alpha:
+        fluid += 0.5 * 6                          # Monaghan AV on approaching pairs (~half)
+    lam = 7 if wl.nu else 0
+    fluid += lam + d * ((3 if wl.nu else 1) + 4)  # momentum per axis + compensated add
+    if wl.xsph_eps:
+        fluid += (5 if wl.kernel == 1 else 10) + 1 + 3 + d * (1 + 4)
+    return {"candidate": cand, "fluid_dest_pair": fluid, "wall_dest_pair": wall_dest}
+
+
+# --------------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, gpu_index: str):
+        self.path = os.path.join(tempfile.gettempdir(), f"clocks_{os.getpid()}.csv")
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", gpu_index, f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:  # noqa: BLE001
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:  # noqa: BLE001
+            self.p.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ GPU arm
+def gpu_arm(args, rank, world, dist):
+    import numpy as np
+    import torch
+
+    import paper_1909_04504_gb300 as G
+
+    dev = torch.cuda.current_device()
+    wl = workload(args.workload)
+    sch = G.scheme_of(wl)
+    sim = G.Simulation.from_workload(wl)
+    stream = sim.stream
+    sim.set_timing(True)
+    sim.step(sch, wl.dt, args.warmup)
+    flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.int32, device=dev)
+    e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    pair_ms, phases = [], {k: 0.0 for k in G.Simulation.PHASES}
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:  # noqa: BLE001
+        uuid = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
+    sampler = ClockSampler(uuid)
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0[k].record(stream)
+        sim.step_async(sch, wl.dt, 1)
+        e1[k].record(stream)
+        ph = sim.phase_times()  # waits for the step
+        pair_ms.append(ph["pairs"])
+        for key in phases:
+            phases[key] += ph[key]
+    sim.synchronize()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t_wall = time.perf_counter() - t_wall0
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in zip(e0, e1)]
+    total_ms = sum(step_ms)
+    hist = sim.history()
+    pairs = float(hist[-args.steps:, 8].sum())
+    cand = float(hist[-args.steps:, 9].sum())
+    n = sim.n
+    if dist:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * pairs / (total_ms / 1e3)
+    psteps = world * n * args.steps / (total_ms / 1e3)
+
+    # ---- roofline of the dominant kernel (pair loop), algorithmic flops / live duration
+    fl = pair_flops(wl)
+    off, idx = sim.neighbors()
+    role = np.concatenate([np.full(a.n, a.role) for a in wl.arrays])
+    rows = np.repeat(np.arange(n), np.diff(off))
+    fluid_dest = int(np.sum(role[rows] == 0))
+    wall_dest = int(np.sum((role[rows] == 1) & (role[idx] == 0)))
+    frac_fluid = fluid_dest / max(fluid_dest + wall_dest, 1)
+    flops = (fl["candidate"] * cand + pairs * (frac_fluid * fl["fluid_dest_pair"]
+                                                + (1 - frac_fluid) * fl["wall_dest_pair"]))
+    flops_per_launch = flops / args.steps
+    pair_avg_ms = sum(pair_ms) / len(pair_ms)
+    achieved = flops_per_launch / (pair_avg_ms / 1e3) / 1e12
+    peak = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    if wl.precision == 0:
+        peak = peak / 64.0  # FP64 CUDA-core rate of this part: 1/64 of FP32
+    roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 3),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 5), "traffic": None,
+                "kernel": "k_pairs (fused continuity + momentum + AV + XSPH + kick + reductions)",
+                "flops_per_launch": flops_per_launch, "avg_launch_ms": round(pair_avg_ms, 5),
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
+    phase_avg = {k: round(v / args.steps, 5) for k, v in phases.items()}
+
+    # ---- end to end through the C ABI with host buffers
+    blob = sim.save_state()
+    pinned = torch.empty(len(blob), dtype=torch.uint8, pin_memory=True).numpy()
+    pinned[:] = np.frombuffer(blob, dtype=np.uint8)
+    e2e_steps = min(args.steps, 200)
+    sim.set_timing(False)
+    sim.load_state(pinned)
+    sim.step(sch, wl.dt, 1)  # re-capture without timing events
+    tt = time.perf_counter()
+    e2e_pairs = 0.0
+    for _ in range(e2e_steps):
+        sim.load_state(pinned)
+        sim.step(sch, wl.dt, 1)
+        e2e_pairs += sim.diagnostics()[8]
+    e2e_s = time.perf_counter() - tt
+    e2e = {"value": world * e2e_pairs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": len(blob),
+           "d2h_bytes_per_step": 8 * G.DIAG_COUNT,
+           "path": "sph_load_state(pinned host state) + sph_step + sph_diagnostics per step"}
+
+    # ---- FP64 mode of the same workload (the metric compares FP32 with FP64)
+    fp64 = None
+    if wl.precision == 1 and args.fp64_steps > 0:
+        sim64 = G.Simulation.from_workload(wl.with_precision(0))
+        sim64.step(sch, wl.dt, args.warmup)
+        f0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.fp64_steps)]
+        f1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.fp64_steps)]
+        for k in range(args.fp64_steps):
+            with torch.cuda.stream(sim64.stream):
+                flush.zero_()
+            f0[k].record(sim64.stream)
+            sim64.step_async(sch, wl.dt, 1)
+            f1[k].record(sim64.stream)
+        sim64.synchronize()
+        torch.cuda.synchronize()
+        ms64 = sum(a.elapsed_time(b) for a, b in zip(f0, f1))
+        h64 = sim64.history()
+        p64 = float(h64[-args.fp64_steps:, 8].sum())
+        v64 = p64 / (ms64 / 1e3)
+        fp64 = {"value": world * v64, "unit": UNIT, "steps": args.fp64_steps,
+                "ms_per_step": ms64 / args.fp64_steps,
+                "fp32_speedup": round(value / (world * v64), 3)}
+        sim64.close()
+
+    state0 = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        state0 = one_step_states(wl, sch)
+    sim.close()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if wl.precision == 1 else "f64", "data": "synthetic",
+        "config": describe(wl),
+        "particle_steps_per_s": psteps, "candidates_per_s": world * cand / (total_ms / 1e3),
+        "pairs_per_step": pairs / args.steps, "phase_ms": phase_avg,
+        "roofline": roofline, "e2e": e2e, "fp64_mode": fp64,
+        "gpu_launches": None, "clocks": clocks, "wall_s": round(t_wall, 3),
+    }
+    import paper_1909_04504_gb300 as G2  # noqa: F401
+    with G.Simulation.from_workload(wl) as s2:
+        line["gpu_launches"] = s2.kernels_per_step(sch) * args.steps
+    return line, state0, wl
+
+
+def one_step_states(wl, sch):
+    """GPU state after one step in FP32 and FP64 mode (for the error beside the metric)."""
+    import paper_1909_04504_gb300 as G
+    out = {}
+    for prec in (1, 0):
+        with G.Simulation.from_workload(wl.with_precision(prec)) as s:
+            s.step(sch, wl.dt, 1)
+            out[prec] = s.state()
+    return out
+
+
+# ---------------------------------------------------------------- oracle legs
+def cpu_baseline(wl, target_s: float, states=None) -> dict:
+    """The oracle as it stands, timed on the host cores on a bounded sample of the workload."""
+    import numpy as np
+
+    import oracle as O
+    O.build()
+    s = O.state_of(wl)
+    t0 = time.perf_counter()
+    _, h = O.run(wl, s, wl.dt, 1)
+    t1 = time.perf_counter() - t0  # one step + the initial evaluation
+    steps = max(1, min(2000, int(target_s / max(t1 / 2.0, 1e-6)) - 1))
+    t0 = time.perf_counter()
+    st, h = O.run(wl, s, wl.dt, steps)
+    dt = time.perf_counter() - t0
+    pairs = float(h[:, 8].sum())  # the initial evaluation is timed and counted too
+    out = {"value": pairs / dt, "unit": UNIT, "cores": O.threads(), "kind": "oracle",
+           "sample": f"{steps} steps of {wl.name} from its initial state "
+                     f"({steps + 1} right-hand-side evaluations), {dt:.1f} s"}
+    if states is not None:
+        ref, _ = O.run(wl, s, wl.dt, 1)
+        err = {}
+        for prec, g in states.items():
+            key = "fp32_rel_l2" if prec == 1 else "fp64_normwise"
+            vals = []
+            for k in ("x", "y", "z", "u", "v", "w", "rho")[: (7 if wl.dim == 3 else 5)]:
+                if wl.dim == 2 and k in ("z", "w"):
+                    continue
+                a, b = g[k], ref[k]
+                if prec == 1:
+                    vals.append(float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)))
+                else:
+                    vals.append(float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)))
+            err[key] = max(vals)
+        out["one_step_error_vs_oracle"] = err
+    return out
+
+
+def reference_arm(args):
+    """Times the oracle on the host cores in the base contract's reference slot."""
+    import oracle as O
+    wl = workload(args.workload)
+    O.build()
+    s = O.state_of(wl)
+    t0 = time.perf_counter()
+    st, _ = O.run(wl, s, wl.dt, max(1, args.warmup))
+    warm_s = time.perf_counter() - t0
+    per_step = warm_s / (max(1, args.warmup) + 1)
+    steps = args.steps
+    cap = max(1, int(150.0 / max(per_step, 1e-6)))
+    sample_steps = min(steps, cap)
+    t0 = time.perf_counter()
+    st, h = O.run(wl, st, wl.dt, sample_steps)
+    el = time.perf_counter() - t0
+    pairs = float(h[:, 8].sum())
+    value = pairs / el
+    sample = (f"{sample_steps} oracle steps of {wl.name} (+1 initial evaluation) after "
+              f"{args.warmup} warm-up steps, {el:.1f} s")
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * el / sample_steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": describe(wl),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="dam_break_2d",
+                    choices=["dam_break_2d", "taylor_green_2d", "taylor_green_3d", "dam_break_3d"])
+    ap.add_argument("--flush-mb", type=int, default=512)
+    ap.add_argument("--fp64-steps", type=int, default=200)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        print(json.dumps(reference_arm(args)), flush=True)
+        return
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(local)
+        tdist.init_process_group("nccl")
+        dist = tdist
+    else:
+        torch.cuda.set_device(0)
+    line, states, wl = gpu_arm(args, rank, world, dist)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds, states)
+        else:
+            line["cpu_baseline"] = None
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

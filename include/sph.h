@@ -1,0 +1,236 @@
+/*
+ * sph.h - C ABI of a GB300-native implementation of the data-parallel hot path of
+ * weakly-compressible SPH (WCSPH) as described in the PySPH paper: uniform-grid
+ * neighbour search (cell keys, radix sort, reorder, cell table; Sec. 2.2), the fused
+ * pair loops (summation density Eq. 2 or continuity Eq. continuity:sph, Tait EOS
+ * Eq. eos, momentum Eqs. mom:sph, mom:sph:press, mom:sph:visc with Monaghan
+ * artificial viscosity and XSPH; quintic spline and Wendland C2 kernels) and the
+ * predictor-corrector integrator of Sec. 2.1 with periodic wrap and static wall
+ * particles.
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns an sph_status; nothing aborts, traps or exits. On failure the
+ *    message is available from sph_last_error().
+ *  - Host pointers ("host") are read or written only during the call. Device memory
+ *    belongs to the context (allocated through the caller's allocator, or cudaMalloc
+ *    when none is given) and is released by sph_destroy().
+ *  - Particle ids are global: the arrays given to sph_create are concatenated in order,
+ *    so array a, local index i has global id offset(a) + i. Every per-particle output
+ *    is in that original order, whatever order the device keeps internally.
+ *  - All device work is issued on the stream given at creation. Calls that return data
+ *    to the host synchronise that stream. A context is used from one thread at a time.
+ */
+#ifndef SPH_H
+#define SPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sph_ctx sph_ctx;
+
+typedef enum {
+    SPH_OK = 0,
+    SPH_ERR_INVALID = 1,    /* an argument is out of range or inconsistent */
+    SPH_ERR_CUDA = 2,       /* a CUDA runtime call or a kernel launch failed */
+    SPH_ERR_OOM = 3,        /* the allocator returned NULL */
+    SPH_ERR_NONFINITE = 4,  /* a step produced NaN/Inf; later steps of the call were skipped */
+    SPH_ERR_DOMAIN = 5,     /* reserved: particle outside the cell box (such particles are
+                               clamped into the edge cells and counted, not rejected) */
+    SPH_ERR_CAPACITY = 6,   /* a caller buffer or a fixed capacity is too small */
+    SPH_ERR_TIMEOUT = 7,    /* a bounded device-side wait gave up */
+    SPH_ERR_STATE = 8       /* the call is not valid in the context's current state */
+} sph_status;
+
+typedef enum { SPH_KERNEL_QUINTIC = 0, SPH_KERNEL_WENDLAND_C2 = 1 } sph_kernel;
+typedef enum { SPH_PREC_FP64 = 0, SPH_PREC_FP32 = 1 } sph_precision;
+typedef enum { SPH_ROLE_FLUID = 0, SPH_ROLE_WALL = 1 } sph_role;
+typedef enum { SPH_DENSITY_CONTINUITY = 0, SPH_DENSITY_SUMMATION = 1 } sph_density;
+
+/* Geometry of a problem (Sec. 2.2, Sec. 3 create_domain).
+ *  dim        2 or 3.
+ *  kernel     sph_kernel: quintic spline (support 3h) or Wendland C2 (support 2h).
+ *  precision  sph_precision of the pair loops. FP32: positions are rounded once to
+ *             float and the neighbour test and pair sums run in float with compensated
+ *             (Neumaier) per-particle sums; the integrator, the state and the
+ *             reductions stay FP64. FP64: everything in double.
+ *  periodic   per axis; a periodic axis wraps positions into [lo, hi) and uses the
+ *             minimum image in the neighbour test. It needs at least 3 cells.
+ *  h          smoothing length (constant for all particles).
+ *  lo, hi     cell box. On a periodic axis it is the period. Cells per axis:
+ *             n = floor((hi - lo) / (k h * 1.00001)), size (hi - lo) / n, with k the
+ *             support factor; a particle outside the box on a non-periodic axis is
+ *             clamped into the edge cell (the result stays exact, only slower). */
+typedef struct {
+    int32_t dim;
+    int32_t kernel;
+    int32_t precision;
+    int32_t periodic[3];
+    double h;
+    double lo[3];
+    double hi[3];
+} sph_domain;
+
+/* One named particle array (the ParticleArray of Sec. 3.2.1). Host pointers, copied at
+ * creation, n entries each. z and w may be NULL in 2D; u, v, w may be NULL (zero).
+ * x, y, rho, m are required. Wall particles never move: their x and u stay as given. */
+typedef struct {
+    const char* name;
+    int32_t role;
+    int64_t n;
+    const double* x;
+    const double* y;
+    const double* z;
+    const double* u;
+    const double* v;
+    const double* w;
+    const double* rho;
+    const double* m;
+} sph_array_desc;
+
+/* Equations of one right-hand-side evaluation (Sec. 3.2 groups: [summation density],
+ * EOS, then continuity + momentum; walls take continuity from fluid sources only).
+ *  density    sph_density.
+ *  rho0, c0, gamma   Tait EOS, Eq. eos: p = c0^2 rho0 / gamma ((rho/rho0)^gamma - 1).
+ *  nu, eta    laminar viscosity, Eq. mom:sph:visc (term off when nu == 0).
+ *  alpha      Monaghan artificial viscosity: Pi_ij = -alpha c0 mu_ij / rhobar_ij when
+ *             v_ij . r_ij < 0, mu_ij = h v_ij . r_ij / (r^2 + 0.01 h^2) (off when 0).
+ *  xsph_eps   XSPH: dx_i = eps sum_fluid j m_j / rhobar_ij (u_j - u_i) W_ij, added to the
+ *             drift velocity (off when 0).
+ *  g          body acceleration of fluid particles, Eq. mom:sph. */
+typedef struct {
+    int32_t density;
+    int32_t reserved;
+    double rho0;
+    double c0;
+    double gamma;
+    double nu;
+    double eta;
+    double alpha;
+    double xsph_eps;
+    double g[3];
+} sph_scheme;
+
+/* Device allocator callbacks: return a device pointer of at least `bytes` bytes aligned
+ * to 256 bytes (NULL on failure) / release it. Both may be NULL to use cudaMalloc. */
+typedef void* (*sph_alloc_fn)(size_t bytes, void* user);
+typedef void (*sph_free_fn)(void* ptr, void* user);
+
+/* Diagnostics record layout (sph_diagnostics, sph_history). FP64 reductions over
+ * fluid particles after the last right-hand-side evaluation (Sec. 2.1 criteria). */
+enum {
+    SPH_DIAG_T = 0,          /* simulated time */
+    SPH_DIAG_DT = 1,         /* step used to reach it (0 for the initial evaluation) */
+    SPH_DIAG_KE = 2,         /* 1/2 sum m |u|^2 */
+    SPH_DIAG_UMAX = 3,       /* max |u| */
+    SPH_DIAG_PX = 4,         /* sum m u (x, y, z) */
+    SPH_DIAG_PY = 5,
+    SPH_DIAG_PZ = 6,
+    SPH_DIAG_AMAX = 7,       /* max |a| */
+    SPH_DIAG_PAIRS = 8,      /* ordered interacting pairs i != j of the evaluation */
+    SPH_DIAG_CANDIDATES = 9, /* ordered pairs examined in the 3^d cell stencil, j != i */
+    SPH_DIAG_STEP = 10,      /* steps taken since creation */
+    SPH_DIAG_OUTSIDE = 11,   /* particles clamped into an edge cell at the last build */
+    SPH_DIAG_COUNT = 12
+};
+
+/* Create a context: copy the arrays to the device (global ids in array order), wrap
+ * periodic coordinates into the box. `stream` is a cudaStream_t (NULL: the context creates
+ * and owns a non-blocking stream, needed because steps run as captured CUDA graphs). Returns SPH_ERR_INVALID for a bad domain (dim, kernel, h <= 0, empty box,
+ * a periodic axis with fewer than 3 cells, more than 2^31 - 1 particles). */
+sph_status sph_create(const sph_domain* domain, const sph_array_desc* arrays, int32_t n_arrays,
+                      void* stream, sph_alloc_fn alloc, sph_free_fn free_fn, void* alloc_user,
+                      sph_ctx** out);
+
+/* Release every device buffer and the context. NULL is ignored. */
+void sph_destroy(sph_ctx* ctx);
+
+/* Message of the last failed call on ctx (ctx NULL: of the last failed sph_create on this
+ * thread). Valid until the next call on the same context. */
+const char* sph_last_error(const sph_ctx* ctx);
+
+/* Particle count of array `array` (-1: all particles). */
+sph_status sph_count(const sph_ctx* ctx, int32_t array, int64_t* n);
+
+/* Cell grid: cells per axis, cell sizes, total cells (Sec. 2.2). */
+sph_status sph_grid(const sph_ctx* ctx, int32_t n_cells[3], double cell_size[3], int64_t* ncells);
+
+/* Neighbour build at the current positions (Sec. 2.2, Z-order/cell sort): cell key per
+ * particle, stable radix sort, reorder of the state into cell order and the cell table. */
+sph_status sph_build_neighbors(sph_ctx* ctx);
+
+/* Cell table of the last build, host buffers. cell_of (n_total, original order): linear
+ * cell id cx + nx (cy + ny cz). offsets (ncells + 1): offsets[c] = particles in cells < c,
+ * so cell c holds sorted positions [offsets[c], offsets[c+1]). order (n_total, may be
+ * NULL): global id at each sorted position. Builds first if positions changed. */
+sph_status sph_get_cells(sph_ctx* ctx, uint32_t* cell_of, uint32_t* offsets, int64_t* order);
+
+/* Neighbour lists at the current positions in CSR form, original ids, ascending in each
+ * row, i != j, r^2 < (k h)^2 in the mode's precision (the same test the pair loops use).
+ * offsets: n_total + 1 host int64. idx: host int32 of capacity *nnz (in), or NULL to ask
+ * only for the size. *nnz receives the count. Debug / parity path, not a fast path. */
+sph_status sph_get_neighbors(sph_ctx* ctx, int64_t* offsets, int32_t* idx, int64_t* nnz);
+
+/* One right-hand-side evaluation at the current state without updating it (the
+ * SPHEvaluator use of Sec. 3.4). Rates are then readable with sph_get ("arho", "ax",
+ * "ay", "az", "xsx", "xsy", "xsz"); with summation density "rho" receives the sum. */
+sph_status sph_eval_rhs(sph_ctx* ctx, const sph_scheme* scheme);
+
+/* Advance nsteps predictor-corrector steps (Sec. 2.1, kick-drift-kick, one RHS per step
+ * at (x^{n+1}, u^{n+1/2}, rho^{n+1/2}); neighbours rebuilt every step). dt > 0 fixes the
+ * step; dt <= 0 takes min(0.25 h / (c0 + max|u|), 0.25 sqrt(h / max|a|), 0.125 h^2 / nu)
+ * from the previous evaluation. Rates carried between calls are recomputed first when the
+ * state was set or the scheme differs. The steps run as replays of a captured CUDA graph.
+ * SPH_ERR_NONFINITE: the state is that of the step where NaN/Inf appeared. */
+sph_status sph_step(sph_ctx* ctx, const sph_scheme* scheme, double dt, int32_t nsteps);
+
+/* As sph_step, but returns once the steps are enqueued on the context stream without
+ * waiting for them (an initial evaluation, when needed, is enqueued too). Device-side
+ * failures (SPH_ERR_NONFINITE) are reported by the next sph_synchronize. */
+sph_status sph_step_async(sph_ctx* ctx, const sph_scheme* scheme, double dt, int32_t nsteps);
+
+/* Wait for all work enqueued on the context stream; returns the device status. */
+sph_status sph_synchronize(sph_ctx* ctx);
+
+/* Phase timing. enable != 0: steps captured from now on record CUDA events between their
+ * phases (a few microseconds of overhead per step). sph_phase_times then gives the device
+ * time in ms of the last completed step's phases: out[0] drift + cell keys, out[1] radix
+ * sort, out[2] reorder + EOS, out[3] cell table, out[4] pair loop (summation density
+ * included) with the corrector kick and reductions. SPH_ERR_STATE if no timed step ran. */
+sph_status sph_set_timing(sph_ctx* ctx, int32_t enable);
+sph_status sph_phase_times(sph_ctx* ctx, float out[5]);
+
+/* Kernel launches one step issues (for launch accounting). */
+sph_status sph_kernels_per_step(const sph_ctx* ctx, const sph_scheme* scheme, int32_t* count);
+
+/* Property of one array (or -1 for all particles) into a host buffer, original order.
+ * prop: "x" "y" "z" "u" "v" "w" "rho" "m", or rates of the last evaluation "arho" "ax"
+ * "ay" "az" "xsx" "xsy" "xsz". */
+sph_status sph_get(sph_ctx* ctx, int32_t array, const char* prop, double* out);
+
+/* Overwrite one property ("x" "y" "z" "u" "v" "w" "rho" "m") of one array (or -1 for all
+ * particles) from a host buffer in original order. Invalidates rates and neighbours. */
+sph_status sph_set(sph_ctx* ctx, int32_t array, const char* prop, const double* in);
+
+/* Diagnostics record of the last evaluation (SPH_DIAG_COUNT doubles, host). */
+sph_status sph_diagnostics(sph_ctx* ctx, double* out);
+
+/* Records of the steps of the last sph_step call, oldest first, into out
+ * (capacity max_records * SPH_DIAG_COUNT doubles); *count receives how many were written.
+ * The context keeps the most recent 65536 records. */
+sph_status sph_history(sph_ctx* ctx, double* out, int32_t max_records, int32_t* count);
+
+/* Full device state (positions, velocities, density, mass, rates, internal order, time)
+ * to/from a host buffer. buf NULL: *bytes receives the size. Loading restores the exact
+ * state so that a resumed run is bitwise identical to an uninterrupted one. */
+sph_status sph_save_state(sph_ctx* ctx, void* buf, size_t* bytes);
+sph_status sph_load_state(sph_ctx* ctx, const void* buf, size_t bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPH_H */

@@ -1,0 +1,359 @@
+"""Thin ctypes binding of the C ABI in ``include/sph.h`` (argument marshalling only).
+
+Every step of the particle loop runs in the CUDA library ``_build/libsph_gb300.so``.
+There is no CPU fallback: loading fails loudly when the library is missing or no GPU
+is present. PyTorch supplies the stream and, optionally, device memory through its
+caching allocator.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+QUINTIC, WENDLAND_C2 = 0, 1
+PREC_FP64, PREC_FP32 = 0, 1
+FLUID, WALL = 0, 1
+CONTINUITY, SUMMATION = 0, 1
+DIAG_COUNT = 12
+DIAG_NAMES = ("t", "dt", "ke", "umax", "px", "py", "pz", "amax", "pairs", "candidates",
+              "step", "outside")
+STATUS = {0: "SPH_OK", 1: "SPH_ERR_INVALID", 2: "SPH_ERR_CUDA", 3: "SPH_ERR_OOM",
+          4: "SPH_ERR_NONFINITE", 5: "SPH_ERR_DOMAIN", 6: "SPH_ERR_CAPACITY",
+          7: "SPH_ERR_TIMEOUT", 8: "SPH_ERR_STATE"}
+
+
+class SphError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Domain(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("kernel", C.c_int32), ("precision", C.c_int32),
+                ("periodic", C.c_int32 * 3), ("h", C.c_double), ("lo", C.c_double * 3),
+                ("hi", C.c_double * 3)]
+
+
+class ArrayDesc(C.Structure):
+    _fields_ = [("name", C.c_char_p), ("role", C.c_int32), ("n", C.c_int64)] + \
+               [(k, C.POINTER(C.c_double)) for k in ("x", "y", "z", "u", "v", "w", "rho", "m")]
+
+
+class Scheme(C.Structure):
+    _fields_ = [("density", C.c_int32), ("reserved", C.c_int32), ("rho0", C.c_double),
+                ("c0", C.c_double), ("gamma", C.c_double), ("nu", C.c_double),
+                ("eta", C.c_double), ("alpha", C.c_double), ("xsph_eps", C.c_double),
+                ("g", C.c_double * 3)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+_lib = None
+EXPORTS = ("sph_create", "sph_destroy", "sph_last_error", "sph_count", "sph_grid",
+           "sph_build_neighbors", "sph_get_cells", "sph_get_neighbors", "sph_eval_rhs",
+           "sph_step", "sph_step_async", "sph_synchronize", "sph_set_timing", "sph_phase_times",
+           "sph_kernels_per_step", "sph_get", "sph_set", "sph_diagnostics", "sph_history",
+           "sph_save_state", "sph_load_state")
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load the CUDA library (building it first when asked). Raises if unavailable."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path}")
+    L = C.CDLL(path)
+    P, d, i32, i64 = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int32), C.POINTER(C.c_int64)
+    u32 = C.POINTER(C.c_uint32)
+    ctxp = C.c_void_p
+    L.sph_create.argtypes = [C.POINTER(Domain), C.POINTER(ArrayDesc), C.c_int32, P, ALLOC_FN,
+                             FREE_FN, P, C.POINTER(ctxp)]
+    L.sph_destroy.argtypes = [ctxp]
+    L.sph_destroy.restype = None
+    L.sph_last_error.argtypes = [ctxp]
+    L.sph_last_error.restype = C.c_char_p
+    L.sph_count.argtypes = [ctxp, C.c_int32, i64]
+    L.sph_grid.argtypes = [ctxp, i32, d, i64]
+    L.sph_build_neighbors.argtypes = [ctxp]
+    L.sph_get_cells.argtypes = [ctxp, u32, u32, i64]
+    L.sph_get_neighbors.argtypes = [ctxp, i64, i32, i64]
+    L.sph_eval_rhs.argtypes = [ctxp, C.POINTER(Scheme)]
+    L.sph_step.argtypes = [ctxp, C.POINTER(Scheme), C.c_double, C.c_int32]
+    L.sph_step_async.argtypes = [ctxp, C.POINTER(Scheme), C.c_double, C.c_int32]
+    L.sph_synchronize.argtypes = [ctxp]
+    L.sph_set_timing.argtypes = [ctxp, C.c_int32]
+    L.sph_phase_times.argtypes = [ctxp, C.POINTER(C.c_float)]
+    L.sph_kernels_per_step.argtypes = [ctxp, C.POINTER(Scheme), i32]
+    L.sph_get.argtypes = [ctxp, C.c_int32, C.c_char_p, d]
+    L.sph_set.argtypes = [ctxp, C.c_int32, C.c_char_p, d]
+    L.sph_diagnostics.argtypes = [ctxp, d]
+    L.sph_history.argtypes = [ctxp, d, C.c_int32, i32]
+    L.sph_save_state.argtypes = [ctxp, P, C.POINTER(C.c_size_t)]
+    L.sph_load_state.argtypes = [ctxp, P, C.c_size_t]
+    for name in EXPORTS:
+        if name not in ("sph_destroy", "sph_last_error"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _dptr(a: Optional[np.ndarray]):
+    if a is None:
+        return None
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def make_scheme(density=CONTINUITY, rho0=1.0, c0=10.0, gamma=7.0, nu=0.0, eta=0.01, alpha=0.0,
+                xsph_eps=0.0, g=(0.0, 0.0, 0.0)) -> Scheme:
+    s = Scheme()
+    s.density, s.rho0, s.c0, s.gamma = int(density), rho0, c0, gamma
+    s.nu, s.eta, s.alpha, s.xsph_eps = nu, eta, alpha, xsph_eps
+    for k in range(3):
+        s.g[k] = float(g[k])
+    return s
+
+
+def scheme_of(wl, **over) -> Scheme:
+    """Scheme from an object with the workload attributes (rho0, c0, gamma, nu, ...)."""
+    kw = dict(density=wl.density, rho0=wl.rho0, c0=wl.c0, gamma=wl.gamma, nu=wl.nu, eta=wl.eta,
+              alpha=wl.alpha, xsph_eps=wl.xsph_eps, g=wl.g)
+    kw.update(over)
+    return make_scheme(**kw)
+
+
+class _TorchAllocator:
+    """Routes the library's device allocations through PyTorch's caching allocator."""
+
+    def __init__(self, device: int, stream):
+        import torch
+        self._torch = torch
+        self._device = device
+        self._stream = stream
+        self.alloc = ALLOC_FN(self._alloc)
+        self.free = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, user):
+        try:
+            return int(self._torch.cuda.caching_allocator_alloc(int(nbytes), self._device,
+                                                                 self._stream))
+        except Exception:  # noqa: BLE001 - reported to the library as NULL
+            return None
+
+    def _free(self, ptr, user):
+        if ptr:
+            self._torch.cuda.caching_allocator_delete(ptr)
+
+
+class Simulation:
+    """One WCSPH problem resident on the GPU (a ``sph_ctx``)."""
+
+    def __init__(self, dim: int, kernel: int, precision: int, h: float, lo: Sequence[float],
+                 hi: Sequence[float], periodic: Sequence[int], arrays: Sequence[dict],
+                 stream=None, torch_alloc: bool = True):
+        self._L = load()
+        dom = Domain()
+        dom.dim, dom.kernel, dom.precision, dom.h = dim, kernel, precision, h
+        for k in range(3):
+            dom.periodic[k] = int(periodic[k])
+            dom.lo[k] = float(lo[k])
+            dom.hi[k] = float(hi[k])
+        self.dim = dim
+        self._keep = []
+        descs = (ArrayDesc * len(arrays))()
+        for a, arr in enumerate(arrays):
+            dsc = descs[a]
+            name = str(arr.get("name", f"array{a}")).encode()
+            self._keep.append(name)
+            dsc.name = name
+            dsc.role = int(arr.get("role", FLUID))
+            x = _f64(arr["x"])
+            dsc.n = x.shape[0]
+            for k in ("x", "y", "z", "u", "v", "w", "rho", "m"):
+                v = arr.get(k)
+                if v is None:
+                    setattr(dsc, k, None)
+                    continue
+                v = _f64(v)
+                if v.shape[0] != dsc.n:
+                    raise ValueError(f"array {a}: {k} has {v.shape[0]} entries, expected {dsc.n}")
+                self._keep.append(v)
+                setattr(dsc, k, _dptr(v))
+        self._stream_obj = None
+        stream_handle = None
+        self._alloc = None
+        alloc_fn, free_fn = ALLOC_FN(), FREE_FN()
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the WCSPH library runs on the GPU only")
+        if stream is None:
+            self._stream_obj = torch.cuda.Stream()
+            stream_handle = self._stream_obj.cuda_stream
+        else:
+            stream_handle = int(getattr(stream, "cuda_stream", stream))
+        if torch_alloc:
+            dev = torch.cuda.current_device()
+            self._alloc = _TorchAllocator(dev, stream_handle)
+            alloc_fn, free_fn = self._alloc.alloc, self._alloc.free
+        ctx = C.c_void_p()
+        st = self._L.sph_create(C.byref(dom), descs, len(arrays), C.c_void_p(stream_handle),
+                                alloc_fn, free_fn, None, C.byref(ctx))
+        self._keep = []
+        if st != 0:
+            raise SphError(st, self._L.sph_last_error(None).decode())
+        self._ctx = ctx
+        self.n = self.count(-1)
+
+    @classmethod
+    def from_workload(cls, wl, precision: Optional[int] = None, **kw) -> "Simulation":
+        arrays = [dict(name=a.name, role=a.role, x=a.x, y=a.y, z=a.z, u=a.u, v=a.v, w=a.w,
+                       rho=a.rho, m=a.m) for a in wl.arrays]
+        return cls(wl.dim, wl.kernel, wl.precision if precision is None else precision, wl.h,
+                   wl.lo, wl.hi, wl.periodic, arrays, **kw)
+
+    # ---------------------------------------------------------------- plumbing
+    def _check(self, st: int):
+        if st != 0:
+            raise SphError(st, self._L.sph_last_error(self._ctx).decode())
+
+    @property
+    def stream(self):
+        return self._stream_obj
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._L.sph_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # --------------------------------------------------------------- the C ABI
+    def count(self, array: int = -1) -> int:
+        n = C.c_int64()
+        self._check(self._L.sph_count(self._ctx, array, C.byref(n)))
+        return n.value
+
+    def grid(self):
+        nc = (C.c_int32 * 3)()
+        cs = (C.c_double * 3)()
+        total = C.c_int64()
+        self._check(self._L.sph_grid(self._ctx, nc, cs, C.byref(total)))
+        return list(nc), list(cs), total.value
+
+    def build_neighbors(self):
+        self._check(self._L.sph_build_neighbors(self._ctx))
+
+    def cells(self):
+        _, _, ncells = self.grid()
+        cell_of = np.zeros(self.n, np.uint32)
+        off = np.zeros(ncells + 1, np.uint32)
+        order = np.zeros(self.n, np.int64)
+        self._check(self._L.sph_get_cells(self._ctx, cell_of.ctypes.data_as(C.POINTER(C.c_uint32)),
+                                          off.ctypes.data_as(C.POINTER(C.c_uint32)),
+                                          order.ctypes.data_as(C.POINTER(C.c_int64))))
+        return cell_of, off, order
+
+    def neighbors(self):
+        off = np.zeros(self.n + 1, np.int64)
+        nnz = C.c_int64(0)
+        i64 = C.POINTER(C.c_int64)
+        self._check(self._L.sph_get_neighbors(self._ctx, off.ctypes.data_as(i64), None,
+                                              C.byref(nnz)))
+        idx = np.zeros(max(nnz.value, 1), np.int32)
+        self._check(self._L.sph_get_neighbors(self._ctx, off.ctypes.data_as(i64),
+                                              idx.ctypes.data_as(C.POINTER(C.c_int32)),
+                                              C.byref(nnz)))
+        return off, idx[:nnz.value]
+
+    def eval_rhs(self, scheme: Scheme):
+        self._check(self._L.sph_eval_rhs(self._ctx, C.byref(scheme)))
+
+    def step(self, scheme: Scheme, dt: float, nsteps: int = 1):
+        self._check(self._L.sph_step(self._ctx, C.byref(scheme), float(dt), int(nsteps)))
+
+    def step_async(self, scheme: Scheme, dt: float, nsteps: int = 1):
+        self._check(self._L.sph_step_async(self._ctx, C.byref(scheme), float(dt), int(nsteps)))
+
+    def synchronize(self):
+        self._check(self._L.sph_synchronize(self._ctx))
+
+    def set_timing(self, enable: bool = True):
+        self._check(self._L.sph_set_timing(self._ctx, int(bool(enable))))
+
+    PHASES = ("keys", "sort", "reorder", "cells", "pairs")
+
+    def phase_times(self) -> dict:
+        out = (C.c_float * 5)()
+        self._check(self._L.sph_phase_times(self._ctx, out))
+        return dict(zip(self.PHASES, [float(v) for v in out]))
+
+    def kernels_per_step(self, scheme: Scheme) -> int:
+        n = C.c_int32()
+        self._check(self._L.sph_kernels_per_step(self._ctx, C.byref(scheme), C.byref(n)))
+        return n.value
+
+    def get(self, prop: str, array: int = -1) -> np.ndarray:
+        out = np.zeros(self.count(array))
+        self._check(self._L.sph_get(self._ctx, array, prop.encode(), _dptr(out)))
+        return out
+
+    def set(self, prop: str, values, array: int = -1):
+        v = _f64(values)
+        if v.shape[0] != self.count(array):
+            raise ValueError("wrong length")
+        self._check(self._L.sph_set(self._ctx, array, prop.encode(), _dptr(v)))
+
+    def state(self) -> dict:
+        return {k: self.get(k) for k in ("x", "y", "z", "u", "v", "w", "rho", "m")}
+
+    def rates(self) -> dict:
+        return {k: self.get(k) for k in ("arho", "ax", "ay", "az", "xsx", "xsy", "xsz")}
+
+    def diagnostics(self) -> np.ndarray:
+        out = np.zeros(DIAG_COUNT)
+        self._check(self._L.sph_diagnostics(self._ctx, _dptr(out)))
+        return out
+
+    def history(self, max_records: int = 65536) -> np.ndarray:
+        out = np.zeros((max_records, DIAG_COUNT))
+        n = C.c_int32()
+        self._check(self._L.sph_history(self._ctx, _dptr(out), max_records, C.byref(n)))
+        return out[:n.value]
+
+    def save_state(self) -> bytes:
+        size = C.c_size_t(0)
+        self._check(self._L.sph_save_state(self._ctx, None, C.byref(size)))
+        buf = C.create_string_buffer(size.value)
+        self._check(self._L.sph_save_state(self._ctx, buf, C.byref(size)))
+        return buf.raw
+
+    def load_state(self, blob: bytes):
+        buf = C.create_string_buffer(blob, len(blob))
+        self._check(self._L.sph_load_state(self._ctx, buf, len(blob)))

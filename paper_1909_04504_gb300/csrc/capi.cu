@@ -1,0 +1,901 @@
+// Host runtime and C ABI (include/sph.h): context, device arena, the per-step launch
+// sequence (Sec. 2.1 one_timestep: compute accelerations after a neighbour update, stage,
+// update_domain), CUDA-graph capture of a step, state I/O and the debug exports.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sph.h"
+#include "sph_device.cuh"
+#include "sph_launch.h"
+
+using namespace sph;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+constexpr double PI = 3.14159265358979323846;
+constexpr uint32_t STATE_MAGIC = 0x53504853u;  // "SPHS"
+constexpr uint32_t STATE_VERSION = 1;
+
+struct StateHeader {
+    uint32_t magic, version;
+    int64_t n;
+    int32_t dim, precision, have_rates, cur;
+    double t, dt;
+    unsigned long long step;
+    sph_scheme scheme;
+};
+
+}  // namespace
+
+struct sph_ctx {
+    int device = 0;
+    int sms = 1;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    sph_alloc_fn alloc = nullptr;
+    sph_free_fn free_fn = nullptr;
+    void* user = nullptr;
+    std::string err;
+
+    sph_domain dom{};
+    Grid G{};
+    int N = 0;
+    std::vector<int64_t> arr_off;  // n_arrays + 1
+    int passes = 1;
+
+    // device arena
+    void* arena = nullptr;
+    size_t arena_bytes = 0;
+    ParticleSet set[2]{};
+    int cur = 0;
+    void* P = nullptr;
+    void* Q = nullptr;
+    void* R = nullptr;
+    uint32_t* keys[2]{};
+    uint32_t* vals[2]{};
+    uint32_t* skeys = nullptr;
+    uint32_t* off = nullptr;
+    uint32_t* hist = nullptr;
+    double* partials = nullptr;
+    Control* ctl = nullptr;
+    double* history = nullptr;
+    void* io = nullptr;  // scratch for get/set/exports: 4 N + 2 (8 N + 8) bytes, 256-aligned parts
+    int pair_grid = 1;
+
+    bool have_rates = false;
+    bool nbr_valid = false;
+    sph_scheme rates_scheme{};
+    unsigned hist_at_call = 0;
+
+    unsigned steps_total = 0;  // steps enqueued since creation / the last load (history index)
+
+    // phase timing events (recorded inside captured steps when enabled)
+    bool timing = false;
+    bool timed_step_ran = false;
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+
+    // captured step graphs, one per parity of `cur`
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    sph_scheme graph_scheme{};
+    double graph_dt = 0.0;
+    bool graph_timed = false;
+};
+
+namespace {
+
+sph_status fail(sph_ctx* c, sph_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    else g_create_error = msg;
+    return s;
+}
+
+sph_status cuda_fail(sph_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, SPH_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
+    } while (0)
+
+double support_factor(int kernel) { return kernel == SPH_KERNEL_QUINTIC ? 3.0 : 2.0; }
+
+double sigma(int kernel, int dim) {
+    if (kernel == SPH_KERNEL_QUINTIC) return dim == 2 ? 7.0 / (478.0 * PI) : 1.0 / (120.0 * PI);
+    return dim == 2 ? 7.0 / (4.0 * PI) : 21.0 / (16.0 * PI);
+}
+
+// Cells no smaller than the support radius (with a 1e-5 relative margin so that the
+// mode-precision neighbour test never accepts a pair two cells apart).
+sph_status make_grid(sph_ctx* c, const sph_domain& D, Grid* G) {
+    if (D.dim != 2 && D.dim != 3) return fail(c, SPH_ERR_INVALID, "dim must be 2 or 3");
+    if (D.kernel != SPH_KERNEL_QUINTIC && D.kernel != SPH_KERNEL_WENDLAND_C2)
+        return fail(c, SPH_ERR_INVALID, "unknown kernel");
+    if (D.precision != SPH_PREC_FP64 && D.precision != SPH_PREC_FP32)
+        return fail(c, SPH_ERR_INVALID, "unknown precision");
+    const double kh = support_factor(D.kernel) * D.h;
+    if (!(D.h > 0.0) || !std::isfinite(kh)) return fail(c, SPH_ERR_INVALID, "h must be > 0");
+    G->dim = D.dim;
+    double ncells = 1.0;
+    for (int d = 0; d < 3; ++d) {
+        if (d < D.dim) {
+            const double ext = D.hi[d] - D.lo[d];
+            if (!(ext > 0.0)) return fail(c, SPH_ERR_INVALID, "empty cell box");
+            double nd = std::floor(ext / (kh * 1.00001));
+            if (nd < 1.0) nd = 1.0;
+            if (nd > 1e7) return fail(c, SPH_ERR_INVALID, "too many cells");
+            G->nc[d] = (int)nd;
+            G->periodic[d] = D.periodic[d] ? 1 : 0;
+            if (G->periodic[d] && G->nc[d] < 3)
+                return fail(c, SPH_ERR_INVALID, "a periodic axis needs at least 3 cells");
+            G->cs[d] = ext / (double)G->nc[d];
+            G->lo[d] = D.lo[d];
+            G->hi[d] = D.hi[d];
+            G->L[d] = ext;
+        } else {
+            G->nc[d] = 1;
+            G->periodic[d] = 0;
+            G->cs[d] = 1.0;
+            G->lo[d] = 0.0;
+            G->hi[d] = 1.0;
+            G->L[d] = 1.0;
+        }
+        ncells *= G->nc[d];
+    }
+    if (ncells > 2147483000.0) return fail(c, SPH_ERR_INVALID, "too many cells");
+    G->ncells = (int)ncells;
+    return SPH_OK;
+}
+
+template <class Real>
+PairConst<Real> pair_const(const sph_ctx* c, const sph_scheme* s) {
+    const sph_domain& D = c->dom;
+    PairConst<Real> K{};
+    for (int d = 0; d < 3; ++d) {
+        K.L[d] = (Real)(c->G.L[d]);
+        K.halfL[d] = K.L[d] * (Real)0.5;
+    }
+    const Real kh = (Real)support_factor(D.kernel) * (Real)D.h;
+    K.kh2 = kh * kh;
+    K.h = (Real)D.h;
+    K.inv_h = (Real)(1.0 / D.h);
+    const double sg = sigma(D.kernel, D.dim);
+    const double hd = std::pow(D.h, D.dim);
+    K.wfac = (Real)(sg / hd);
+    K.gfac = (Real)(sg / (hd * D.h * D.h));
+    if (s) {
+        K.eta_h2 = (Real)(s->eta * D.h * D.h);
+        K.av_h2 = (Real)(0.01 * D.h * D.h);
+        K.nu4 = (Real)(4.0 * s->nu);
+        K.alpha_c0 = (Real)(s->alpha * s->c0);
+        K.xsph = (Real)s->xsph_eps;
+        int f = 0;
+        if (s->density == SPH_DENSITY_CONTINUITY) f |= F_CONTINUITY;
+        if (s->nu != 0.0) f |= F_LAMINAR;
+        if (s->alpha != 0.0) f |= F_AV;
+        if (s->xsph_eps != 0.0) f |= F_XSPH;
+        K.flags = f;
+    }
+    return K;
+}
+
+StepConst step_const(const sph_ctx* c, const sph_scheme* s, double dt_fixed) {
+    StepConst C{};
+    C.rho0 = s->rho0;
+    C.inv_rho0 = 1.0 / s->rho0;
+    C.gamma = s->gamma;
+    C.B = s->c0 * s->c0 * s->rho0 / s->gamma;
+    for (int d = 0; d < 3; ++d) C.g[d] = s->g[d];
+    C.h = c->dom.h;
+    C.c0 = s->c0;
+    C.nu = s->nu;
+    C.dt_fixed = dt_fixed;
+    C.continuity = s->density == SPH_DENSITY_CONTINUITY;
+    C.gamma7 = s->gamma == 7.0;
+    C.precision = c->dom.precision;
+    return C;
+}
+
+sph_status check_scheme(sph_ctx* c, const sph_scheme* s) {
+    if (!s) return fail(c, SPH_ERR_INVALID, "scheme is NULL");
+    if (s->density != SPH_DENSITY_CONTINUITY && s->density != SPH_DENSITY_SUMMATION)
+        return fail(c, SPH_ERR_INVALID, "unknown density formulation");
+    if (!(s->rho0 > 0.0) || !(s->c0 > 0.0) || !(s->gamma > 0.0))
+        return fail(c, SPH_ERR_INVALID, "rho0, c0 and gamma must be > 0");
+    if (!(s->nu >= 0.0) || !(s->eta >= 0.0) || !(s->alpha >= 0.0) || !std::isfinite(s->xsph_eps))
+        return fail(c, SPH_ERR_INVALID, "nu, eta, alpha must be >= 0");
+    return SPH_OK;
+}
+
+bool same_scheme(const sph_scheme& a, const sph_scheme& b) { return std::memcmp(&a, &b, sizeof a) == 0; }
+
+// Neighbour build: [drift] + keys, radix sort, gather into the other set (+EOS shadow),
+// cell table. Enqueued on the context stream (capturable).
+void mark(sph_ctx* c, int k, bool timed) {
+    if (timed) cudaEventRecordWithFlags(c->ev[k], c->stream, cudaEventRecordExternal);
+}
+
+void enqueue_build(sph_ctx* c, const StepConst& C, int drift, int kick, int carry_rates,
+                   bool timed = false) {
+    cudaStream_t st = c->stream;
+    cudaMemsetAsync(&c->ctl->outside, 0, sizeof(unsigned), st);
+    mark(c, 0, timed);
+    launch_drift_keys(c->set[c->cur], c->N, c->G, C, c->ctl, drift, c->keys[0], st, c->sms);
+    mark(c, 1, timed);
+    int b = launch_radix_sort(c->keys, c->vals, c->N, c->passes, c->hist, c->ctl, st);
+    c->skeys = c->keys[b];
+    mark(c, 2, timed);
+    const int nxt = c->cur ^ 1;
+    launch_reorder(c->dom.precision, c->set[c->cur], c->set[nxt], c->vals[b], c->N, c->dom.dim, C,
+                   c->ctl, kick, carry_rates, c->P, c->Q, c->R, st, c->sms);
+    mark(c, 3, timed);
+    launch_cell_offsets(c->skeys, c->N, c->G.ncells, c->off, c->ctl, st, c->sms);
+    mark(c, 4, timed);
+    c->cur = nxt;
+}
+
+void enqueue_eval(sph_ctx* c, const sph_scheme* s, const StepConst& C, int kick) {
+    PairLaunch L{};
+    L.precision = c->dom.precision;
+    L.dim = c->dom.dim;
+    L.kernel = c->dom.kernel;
+    L.summation = s->density == SPH_DENSITY_SUMMATION;
+    L.kick = kick;
+    L.n = c->N;
+    L.grid = c->pair_grid;
+    L.P = c->P;
+    L.Q = c->Q;
+    L.R = c->R;
+    L.skeys = c->skeys;
+    L.off = c->off;
+    L.G = c->G;
+    L.C = C;
+    L.S = c->set[c->cur];
+    L.ctl = c->ctl;
+    L.partials = c->partials;
+    L.history = c->history;
+    launch_pairs(L, pair_const<float>(c, s), pair_const<double>(c, s), c->stream);
+}
+
+sph_status sync_status(sph_ctx* c) {
+    unsigned status = 0;
+    CK(cudaMemcpyAsync(&status, &c->ctl->status, sizeof status, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaGetLastError());
+    if (status & ST_NONFINITE) return fail(c, SPH_ERR_NONFINITE, "non-finite state detected");
+    if (status & ST_TIMEOUT) return fail(c, SPH_ERR_TIMEOUT, "device wait timed out");
+    return SPH_OK;
+}
+
+// Initial right-hand side at the current state (no drift, no kick).
+sph_status initial_eval(sph_ctx* c, const sph_scheme* s, double dt_fixed) {
+    StepConst C = step_const(c, s, dt_fixed);
+    enqueue_build(c, C, 0, 0, 0);
+    enqueue_eval(c, s, C, 0);
+    CK(cudaGetLastError());
+    c->have_rates = true;
+    c->nbr_valid = true;
+    c->rates_scheme = *s;
+    return SPH_OK;
+}
+
+void drop_graphs(sph_ctx* c) {
+    for (int k = 0; k < 2; ++k)
+        if (c->graph[k]) {
+            cudaGraphExecDestroy(c->graph[k]);
+            c->graph[k] = nullptr;
+        }
+}
+
+sph_status capture_step_graphs(sph_ctx* c, const sph_scheme* s, double dt) {
+    drop_graphs(c);
+    StepConst C = step_const(c, s, dt);
+    const int cur0 = c->cur;
+    for (int k = 0; k < 2; ++k) {
+        c->cur = cur0 ^ k;
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        enqueue_build(c, C, 1, 1, 0, c->timing);
+        enqueue_eval(c, s, C, 1);
+        mark(c, 5, c->timing);
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (e != cudaSuccess) {
+            c->cur = cur0;
+            return cuda_fail(c, e, "cudaStreamEndCapture");
+        }
+        const int slot = c->cur ^ 1;  // graph launched when cur == slot (before the step)
+        (void)slot;
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            c->cur = cur0;
+            return cuda_fail(c, e, "cudaGraphInstantiate");
+        }
+        c->graph[cur0 ^ k] = ex;
+    }
+    c->cur = cur0;
+    c->graph_scheme = *s;
+    c->graph_dt = dt;
+    c->graph_timed = c->timing;
+    return SPH_OK;
+}
+
+void* arena_take(char*& p, size_t bytes) {
+    void* r = p;
+    p += (bytes + 255) & ~size_t(255);
+    return r;
+}
+
+sph_status prop_field(sph_ctx* c, const char* prop, bool writable, double** field) {
+    if (!prop) return fail(c, SPH_ERR_INVALID, "prop is NULL");
+    ParticleSet& S = c->set[c->cur];
+    struct { const char* name; double* f; bool w; } table[] = {
+        {"x", S.x[0], true}, {"y", S.x[1], true}, {"z", S.x[2], true},
+        {"u", S.u[0], true}, {"v", S.u[1], true}, {"w", S.u[2], true},
+        {"rho", S.rho, true}, {"m", S.m, true},
+        {"arho", S.arho, false}, {"ax", S.a[0], false}, {"ay", S.a[1], false}, {"az", S.a[2], false},
+        {"xsx", S.xs[0], false}, {"xsy", S.xs[1], false}, {"xsz", S.xs[2], false}};
+    for (auto& t : table)
+        if (std::strcmp(t.name, prop) == 0) {
+            if (writable && !t.w) return fail(c, SPH_ERR_INVALID, std::string("read-only property ") + prop);
+            *field = t.f;
+            return SPH_OK;
+        }
+    return fail(c, SPH_ERR_INVALID, std::string("unknown property ") + prop);
+}
+
+sph_status array_range(sph_ctx* c, int32_t array, uint32_t* first, uint32_t* count) {
+    const int na = (int)c->arr_off.size() - 1;
+    if (array == -1) {
+        *first = 0;
+        *count = (uint32_t)c->N;
+        return SPH_OK;
+    }
+    if (array < 0 || array >= na) return fail(c, SPH_ERR_INVALID, "array index out of range");
+    *first = (uint32_t)c->arr_off[array];
+    *count = (uint32_t)(c->arr_off[array + 1] - c->arr_off[array]);
+    return SPH_OK;
+}
+
+sph_status ensure_neighbors(sph_ctx* c) {
+    if (c->nbr_valid) return SPH_OK;
+    sph_scheme dummy{};
+    dummy.rho0 = 1.0;
+    dummy.c0 = 1.0;
+    dummy.gamma = 7.0;
+    StepConst C = step_const(c, c->have_rates ? &c->rates_scheme : &dummy, 0.0);
+    enqueue_build(c, C, 0, 0, c->have_rates ? 1 : 0);
+    CK(cudaGetLastError());
+    c->nbr_valid = true;
+    return SPH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sph_status sph_create(const sph_domain* domain, const sph_array_desc* arrays, int32_t n_arrays,
+                      void* stream, sph_alloc_fn alloc, sph_free_fn free_fn, void* alloc_user,
+                      sph_ctx** out) {
+    if (!out) return fail(nullptr, SPH_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!domain || !arrays || n_arrays < 1) return fail(nullptr, SPH_ERR_INVALID, "no arrays");
+    if ((alloc == nullptr) != (free_fn == nullptr))
+        return fail(nullptr, SPH_ERR_INVALID, "give both allocator callbacks or neither");
+    sph_ctx* c = new (std::nothrow) sph_ctx();
+    if (!c) return fail(nullptr, SPH_ERR_OOM, "host allocation failed");
+    c->dom = *domain;
+    Grid G{};
+    sph_status s = make_grid(c, *domain, &G);
+    if (s != SPH_OK) {
+        g_create_error = c->err;
+        delete c;
+        return s;
+    }
+    c->G = G;
+    c->arr_off.assign(1, 0);
+    for (int a = 0; a < n_arrays; ++a) {
+        const sph_array_desc& A = arrays[a];
+        if (A.n < 0 || (A.n > 0 && (!A.x || !A.y || !A.rho || !A.m)) ||
+            (domain->dim == 3 && A.n > 0 && !A.z) ||
+            (A.role != SPH_ROLE_FLUID && A.role != SPH_ROLE_WALL)) {
+            g_create_error = "array " + std::to_string(a) + ": missing x, y, (z), rho or m, or bad role";
+            delete c;
+            return SPH_ERR_INVALID;
+        }
+        c->arr_off.push_back(c->arr_off.back() + A.n);
+    }
+    if (c->arr_off.back() > 0x7ffffff0LL || c->arr_off.back() < 1) {
+        g_create_error = "particle count must be in [1, 2^31)";
+        delete c;
+        return SPH_ERR_INVALID;
+    }
+    c->N = (int)c->arr_off.back();
+    c->alloc = alloc;
+    c->free_fn = free_fn;
+    c->user = alloc_user;
+
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e != cudaSuccess) {
+        g_create_error = std::string("no CUDA device: ") + cudaGetErrorString(e);
+        delete c;
+        return SPH_ERR_CUDA;
+    }
+    if (stream) {
+        c->stream = (cudaStream_t)stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            g_create_error = std::string("cudaStreamCreate: ") + cudaGetErrorString(e);
+            delete c;
+            return SPH_ERR_CUDA;
+        }
+        c->own_stream = true;
+    }
+    c->passes = radix_passes(G.ncells);
+    if (c->passes < 1) c->passes = 1;
+    int bps = pairs_max_blocks_per_sm(domain->precision, domain->dim, domain->kernel);
+    long long want = ((long long)c->N + pair_threads() - 1) / pair_threads();
+    long long cap = (long long)c->sms * bps;
+    c->pair_grid = (int)(want < cap ? want : cap);
+    if (c->pair_grid < 1) c->pair_grid = 1;
+
+    // ---- arena
+    const size_t N = (size_t)c->N;
+    const size_t real = domain->precision == SPH_PREC_FP32 ? 4 : 8;
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    size_t bytes = 0;
+    bytes += 2 * (15 * al(N * 8) + al(N * 4));                 // two particle sets
+    bytes += 2 * al(N * 4 * real) + al(N * real);              // shadow P, Q, R
+    bytes += 4 * al(N * 4);                                    // keys, vals
+    bytes += al(((size_t)G.ncells + 1) * 4);                   // cell offsets
+    bytes += al(radix_hist_words(c->N) * 4);                   // radix histograms
+    bytes += al((size_t)c->pair_grid * partial_stride() * 8);  // block partials
+    bytes += al(sizeof(Control));
+    bytes += al((size_t)HIST_CAP * DIAG_N * 8);                // history ring
+    const size_t io_bytes = al(N * 4) + 2 * al(N * 8 + 8);     // io scratch
+    bytes += io_bytes;
+    c->arena_bytes = bytes;
+    if (alloc) c->arena = alloc(bytes, alloc_user);
+    else if (cudaMalloc(&c->arena, bytes) != cudaSuccess) c->arena = nullptr;
+    if (!c->arena) {
+        cudaGetLastError();
+        g_create_error = "device allocation of " + std::to_string(bytes) + " bytes failed";
+        if (c->own_stream) cudaStreamDestroy(c->stream);
+        delete c;
+        return SPH_ERR_OOM;
+    }
+    char* p = (char*)c->arena;
+    for (int k = 0; k < 2; ++k) {
+        ParticleSet& S = c->set[k];
+        for (int d = 0; d < 3; ++d) S.x[d] = (double*)arena_take(p, N * 8);
+        for (int d = 0; d < 3; ++d) S.u[d] = (double*)arena_take(p, N * 8);
+        S.rho = (double*)arena_take(p, N * 8);
+        S.m = (double*)arena_take(p, N * 8);
+        S.arho = (double*)arena_take(p, N * 8);
+        for (int d = 0; d < 3; ++d) S.a[d] = (double*)arena_take(p, N * 8);
+        for (int d = 0; d < 3; ++d) S.xs[d] = (double*)arena_take(p, N * 8);
+        S.tag = (uint32_t*)arena_take(p, N * 4);
+    }
+    c->P = arena_take(p, N * 4 * real);
+    c->Q = arena_take(p, N * 4 * real);
+    c->R = arena_take(p, N * real);
+    for (int k = 0; k < 2; ++k) c->keys[k] = (uint32_t*)arena_take(p, N * 4);
+    for (int k = 0; k < 2; ++k) c->vals[k] = (uint32_t*)arena_take(p, N * 4);
+    c->off = (uint32_t*)arena_take(p, ((size_t)G.ncells + 1) * 4);
+    c->hist = (uint32_t*)arena_take(p, radix_hist_words(c->N) * 4);
+    c->partials = (double*)arena_take(p, (size_t)c->pair_grid * partial_stride() * 8);
+    c->ctl = (Control*)arena_take(p, sizeof(Control));
+    c->history = (double*)arena_take(p, (size_t)HIST_CAP * DIAG_N * 8);
+    c->io = arena_take(p, io_bytes);
+    c->skeys = c->keys[0];
+
+    // ---- upload
+    sph_status rc = SPH_OK;
+    {
+        std::vector<double> h(N);
+        std::vector<uint32_t> tag(N);
+        ParticleSet& S = c->set[0];
+        auto upload = [&](double* dst, int which) -> cudaError_t {
+            for (int a = 0; a < n_arrays; ++a) {
+                const sph_array_desc& A = arrays[a];
+                const double* src = nullptr;
+                switch (which) {
+                    case 0: src = A.x; break;
+                    case 1: src = A.y; break;
+                    case 2: src = A.z; break;
+                    case 3: src = A.u; break;
+                    case 4: src = A.v; break;
+                    case 5: src = A.w; break;
+                    case 6: src = A.rho; break;
+                    default: src = A.m; break;
+                }
+                if ((which == 2 || which == 5) && domain->dim == 2) src = nullptr;
+                for (int64_t i = 0; i < A.n; ++i) h[c->arr_off[a] + i] = src ? src[i] : 0.0;
+            }
+            return cudaMemcpyAsync(dst, h.data(), N * 8, cudaMemcpyHostToDevice, c->stream);
+        };
+        cudaError_t ue = cudaSuccess;
+        double* dsts[8] = {S.x[0], S.x[1], S.x[2], S.u[0], S.u[1], S.u[2], S.rho, S.m};
+        for (int k = 0; k < 8 && ue == cudaSuccess; ++k) {
+            ue = upload(dsts[k], k);
+            if (ue == cudaSuccess) ue = cudaStreamSynchronize(c->stream);
+        }
+        for (int a = 0; a < n_arrays; ++a)
+            for (int64_t i = 0; i < arrays[a].n; ++i)
+                tag[c->arr_off[a] + i] = (uint32_t)(c->arr_off[a] + i) |
+                                         (arrays[a].role == SPH_ROLE_WALL ? WALL_BIT : 0u);
+        if (ue == cudaSuccess)
+            ue = cudaMemcpyAsync(S.tag, tag.data(), N * 4, cudaMemcpyHostToDevice, c->stream);
+        // zero rates and the unused axes of both sets, the control block and the history
+        for (int k = 0; k < 2 && ue == cudaSuccess; ++k) {
+            ParticleSet& T = c->set[k];
+            double* zs[7] = {T.arho, T.a[0], T.a[1], T.a[2], T.xs[0], T.xs[1], T.xs[2]};
+            for (double* z : zs)
+                if (ue == cudaSuccess) ue = cudaMemsetAsync(z, 0, N * 8, c->stream);
+            if (k == 1) {
+                double* zz[8] = {T.x[0], T.x[1], T.x[2], T.u[0], T.u[1], T.u[2], T.rho, T.m};
+                for (double* z : zz)
+                    if (ue == cudaSuccess) ue = cudaMemsetAsync(z, 0, N * 8, c->stream);
+            }
+        }
+        if (ue == cudaSuccess) ue = cudaMemsetAsync(c->ctl, 0, sizeof(Control), c->stream);
+        if (ue == cudaSuccess) ue = cudaMemsetAsync(c->history, 0, (size_t)HIST_CAP * DIAG_N * 8, c->stream);
+        if (ue == cudaSuccess) {
+            launch_wrap_all(c->set[0], c->N, c->G, c->stream, c->sms);
+            ue = cudaGetLastError();
+        }
+        if (ue == cudaSuccess) ue = cudaStreamSynchronize(c->stream);
+        if (ue != cudaSuccess) {
+            g_create_error = std::string("upload: ") + cudaGetErrorString(ue);
+            rc = SPH_ERR_CUDA;
+        }
+    }
+    if (rc != SPH_OK) {
+        sph_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return SPH_OK;
+}
+
+void sph_destroy(sph_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    drop_graphs(c);
+    for (int k = 0; k < 6; ++k)
+        if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+    if (c->arena) {
+        if (c->free_fn) c->free_fn(c->arena, c->user);
+        else cudaFree(c->arena);
+    }
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+const char* sph_last_error(const sph_ctx* c) {
+    return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+sph_status sph_count(const sph_ctx* ctx, int32_t array, int64_t* n) {
+    sph_ctx* c = const_cast<sph_ctx*>(ctx);
+    if (!c || !n) return fail(c, SPH_ERR_INVALID, "NULL argument");
+    uint32_t first, count;
+    sph_status s = array_range(c, array, &first, &count);
+    if (s != SPH_OK) return s;
+    *n = count;
+    return SPH_OK;
+}
+
+sph_status sph_grid(const sph_ctx* ctx, int32_t n_cells[3], double cell_size[3], int64_t* ncells) {
+    sph_ctx* c = const_cast<sph_ctx*>(ctx);
+    if (!c || !n_cells || !cell_size || !ncells) return fail(c, SPH_ERR_INVALID, "NULL argument");
+    for (int d = 0; d < 3; ++d) {
+        n_cells[d] = c->G.nc[d];
+        cell_size[d] = c->G.cs[d];
+    }
+    *ncells = c->G.ncells;
+    return SPH_OK;
+}
+
+sph_status sph_build_neighbors(sph_ctx* c) {
+    if (!c) return fail(c, SPH_ERR_INVALID, "ctx is NULL");
+    c->nbr_valid = false;
+    sph_status s = ensure_neighbors(c);
+    if (s != SPH_OK) return s;
+    return sync_status(c);
+}
+
+sph_status sph_get_cells(sph_ctx* c, uint32_t* cell_of, uint32_t* offsets, int64_t* order) {
+    if (!c || !cell_of || !offsets) return fail(c, SPH_ERR_INVALID, "NULL argument");
+    sph_status s = ensure_neighbors(c);
+    if (s != SPH_OK) return s;
+    uint32_t* d_cell = (uint32_t*)c->io;
+    int64_t* d_order = (int64_t*)((char*)c->io + (((size_t)c->N * 4 + 255) & ~size_t(255)));
+    launch_cell_of_by_id(c->skeys, c->set[c->cur].tag, c->N, d_cell, d_order, c->stream, c->sms);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(cell_of, d_cell, (size_t)c->N * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(offsets, c->off, ((size_t)c->G.ncells + 1) * 4, cudaMemcpyDeviceToHost, c->stream));
+    if (order)
+        CK(cudaMemcpyAsync(order, d_order, (size_t)c->N * 8, cudaMemcpyDeviceToHost, c->stream));
+    return sync_status(c);
+}
+
+sph_status sph_get_neighbors(sph_ctx* c, int64_t* offsets, int32_t* idx, int64_t* nnz) {
+    if (!c || !offsets || !nnz) return fail(c, SPH_ERR_INVALID, "NULL argument");
+    sph_status s = ensure_neighbors(c);
+    if (s != SPH_OK) return s;
+    const PairConst<float> Kf = pair_const<float>(c, nullptr);
+    const PairConst<double> Kd = pair_const<double>(c, nullptr);
+    uint32_t* d_counts = (uint32_t*)c->io;
+    launch_export_neighbors(c->dom.precision, c->dom.dim, c->P, c->skeys, c->off,
+                            c->set[c->cur].tag, c->N, c->G, Kf, Kd, 0, d_counts, nullptr, nullptr,
+                            c->stream, c->sms);
+    CK(cudaGetLastError());
+    std::vector<uint32_t> counts(c->N);
+    CK(cudaMemcpyAsync(counts.data(), d_counts, (size_t)c->N * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    offsets[0] = 0;
+    for (int i = 0; i < c->N; ++i) offsets[i + 1] = offsets[i] + counts[i];
+    const int64_t total = offsets[c->N];
+    if (!idx) {
+        *nnz = total;
+        return SPH_OK;
+    }
+    if (*nnz < total) {
+        *nnz = total;
+        return fail(c, SPH_ERR_CAPACITY, "idx buffer too small");
+    }
+    *nnz = total;
+    if (total == 0) return SPH_OK;
+    int64_t* d_rows = (int64_t*)c->io;
+    CK(cudaMemcpyAsync(d_rows, offsets, ((size_t)c->N + 1) * 8, cudaMemcpyHostToDevice, c->stream));
+    void* d_idx = nullptr;
+    if (c->alloc) d_idx = c->alloc((size_t)total * 4, c->user);
+    else if (cudaMalloc(&d_idx, (size_t)total * 4) != cudaSuccess) d_idx = nullptr;
+    if (!d_idx) {
+        cudaGetLastError();
+        return fail(c, SPH_ERR_OOM, "neighbour export buffer");
+    }
+    launch_export_neighbors(c->dom.precision, c->dom.dim, c->P, c->skeys, c->off,
+                            c->set[c->cur].tag, c->N, c->G, Kf, Kd, 1, nullptr, d_rows,
+                            (int32_t*)d_idx, c->stream, c->sms);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(idx, d_idx, (size_t)total * 4, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (c->free_fn) c->free_fn(d_idx, c->user);
+    else cudaFree(d_idx);
+    if (e != cudaSuccess) return cuda_fail(c, e, "neighbour export");
+    return SPH_OK;
+}
+
+sph_status sph_eval_rhs(sph_ctx* c, const sph_scheme* scheme) {
+    if (!c) return fail(c, SPH_ERR_INVALID, "ctx is NULL");
+    sph_status s = check_scheme(c, scheme);
+    if (s != SPH_OK) return s;
+    s = initial_eval(c, scheme, 0.0);
+    if (s != SPH_OK) return s;
+    return sync_status(c);
+}
+
+sph_status sph_step_async(sph_ctx* c, const sph_scheme* scheme, double dt, int32_t nsteps) {
+    if (!c) return fail(c, SPH_ERR_INVALID, "ctx is NULL");
+    sph_status s = check_scheme(c, scheme);
+    if (s != SPH_OK) return s;
+    if (nsteps < 0) return fail(c, SPH_ERR_INVALID, "nsteps < 0");
+    if (!std::isfinite(dt)) return fail(c, SPH_ERR_INVALID, "dt is not finite");
+    if (dt <= 0.0) dt = 0.0;
+    c->hist_at_call = c->steps_total;
+    if (!c->have_rates || !same_scheme(*scheme, c->rates_scheme)) {
+        s = initial_eval(c, scheme, dt);
+        if (s != SPH_OK) return s;
+    }
+    if (dt > 0.0) CK(cudaMemcpyAsync(&c->ctl->dt, &dt, sizeof dt, cudaMemcpyHostToDevice, c->stream));
+    if (nsteps == 0) return SPH_OK;
+    if (!c->graph[0] || !same_scheme(*scheme, c->graph_scheme) || c->graph_dt != dt ||
+        c->graph_timed != c->timing) {
+        s = capture_step_graphs(c, scheme, dt);
+        if (s != SPH_OK) return s;
+    }
+    for (int k = 0; k < nsteps; ++k) {
+        CK(cudaGraphLaunch(c->graph[c->cur], c->stream));
+        c->cur ^= 1;
+    }
+    c->steps_total += (unsigned)nsteps;
+    // the build inside the graph leaves the sorted keys in the parity-fixed buffer
+    c->skeys = c->keys[c->passes & 1];
+    c->nbr_valid = true;
+    c->have_rates = true;
+    if (c->timing) c->timed_step_ran = true;
+    return SPH_OK;
+}
+
+sph_status sph_synchronize(sph_ctx* c) {
+    if (!c) return fail(c, SPH_ERR_INVALID, "ctx is NULL");
+    return sync_status(c);
+}
+
+sph_status sph_step(sph_ctx* c, const sph_scheme* scheme, double dt, int32_t nsteps) {
+    sph_status s = sph_step_async(c, scheme, dt, nsteps);
+    if (s != SPH_OK) return s;
+    return sync_status(c);
+}
+
+sph_status sph_set_timing(sph_ctx* c, int32_t enable) {
+    if (!c) return fail(c, SPH_ERR_INVALID, "ctx is NULL");
+    if (enable && !c->ev[0])
+        for (int k = 0; k < 6; ++k) CK(cudaEventCreate(&c->ev[k]));
+    c->timing = enable != 0;
+    return SPH_OK;
+}
+
+sph_status sph_phase_times(sph_ctx* c, float out[5]) {
+    if (!c || !out) return fail(c, SPH_ERR_INVALID, "NULL argument");
+    if (!c->timed_step_ran || !c->ev[0]) return fail(c, SPH_ERR_STATE, "no timed step has run");
+    CK(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < 5; ++k) CK(cudaEventElapsedTime(&out[k], c->ev[k], c->ev[k + 1]));
+    return SPH_OK;
+}
+
+sph_status sph_kernels_per_step(const sph_ctx* ctx, const sph_scheme* scheme, int32_t* count) {
+    sph_ctx* c = const_cast<sph_ctx*>(ctx);
+    if (!c || !scheme || !count) return fail(c, SPH_ERR_INVALID, "NULL argument");
+    // drift+keys, 3 per radix pass, reorder, cell table, [summation density], pair loop
+    *count = 1 + 3 * c->passes + 1 + 1 + (scheme->density == SPH_DENSITY_SUMMATION ? 1 : 0) + 1;
+    return SPH_OK;
+}
+
+sph_status sph_get(sph_ctx* c, int32_t array, const char* prop, double* out) {
+    if (!c || !out) return fail(c, SPH_ERR_INVALID, "NULL argument");
+    double* field = nullptr;
+    sph_status s = prop_field(c, prop, false, &field);
+    if (s != SPH_OK) return s;
+    uint32_t first, count;
+    s = array_range(c, array, &first, &count);
+    if (s != SPH_OK) return s;
+    if (count == 0) return SPH_OK;
+    double* d_out = (double*)c->io;
+    launch_gather_by_id(field, c->set[c->cur].tag, c->N, first, count, d_out, c->stream, c->sms);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(out, d_out, (size_t)count * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return SPH_OK;
+}
+
+sph_status sph_set(sph_ctx* c, int32_t array, const char* prop, const double* in) {
+    if (!c || !in) return fail(c, SPH_ERR_INVALID, "NULL argument");
+    double* field = nullptr;
+    sph_status s = prop_field(c, prop, true, &field);
+    if (s != SPH_OK) return s;
+    uint32_t first, count;
+    s = array_range(c, array, &first, &count);
+    if (s != SPH_OK) return s;
+    if (count == 0) return SPH_OK;
+    double* d_in = (double*)c->io;
+    CK(cudaMemcpyAsync(d_in, in, (size_t)count * 8, cudaMemcpyHostToDevice, c->stream));
+    launch_scatter_by_id(field, c->set[c->cur].tag, c->N, first, count, d_in, c->stream, c->sms);
+    if (prop[0] == 'x' || prop[0] == 'y' || prop[0] == 'z')
+        launch_wrap_all(c->set[c->cur], c->N, c->G, c->stream, c->sms);
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync(&c->ctl->status, 0, sizeof(unsigned), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->have_rates = false;
+    c->nbr_valid = false;
+    return SPH_OK;
+}
+
+sph_status sph_diagnostics(sph_ctx* c, double* out) {
+    if (!c || !out) return fail(c, SPH_ERR_INVALID, "NULL argument");
+    CK(cudaMemcpyAsync(out, c->ctl->rec, DIAG_N * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return SPH_OK;
+}
+
+sph_status sph_history(sph_ctx* c, double* out, int32_t max_records, int32_t* count) {
+    if (!c || !out || !count || max_records < 0) return fail(c, SPH_ERR_INVALID, "bad argument");
+    unsigned end = 0;
+    CK(cudaMemcpyAsync(&end, &c->ctl->hist_count, sizeof end, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    unsigned begin = c->hist_at_call;
+    unsigned avail = end >= begin ? end - begin : 0u;
+    if (avail > (unsigned)HIST_CAP) {
+        begin = end - HIST_CAP;
+        avail = HIST_CAP;
+    }
+    unsigned n = avail < (unsigned)max_records ? avail : (unsigned)max_records;
+    unsigned done = 0;
+    while (done < n) {  // at most two contiguous pieces of the ring
+        unsigned slot = (begin + done) % HIST_CAP;
+        unsigned piece = n - done;
+        if (piece > HIST_CAP - slot) piece = HIST_CAP - slot;
+        CK(cudaMemcpyAsync(out + (size_t)done * DIAG_N, c->history + (size_t)slot * DIAG_N,
+                           (size_t)piece * DIAG_N * 8, cudaMemcpyDeviceToHost, c->stream));
+        done += piece;
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    *count = (int32_t)n;
+    return SPH_OK;
+}
+
+sph_status sph_save_state(sph_ctx* c, void* buf, size_t* bytes) {
+    if (!c || !bytes) return fail(c, SPH_ERR_INVALID, "NULL argument");
+    const size_t N = (size_t)c->N;
+    const size_t need = sizeof(StateHeader) + 15 * N * 8 + N * 4;
+    if (!buf) {
+        *bytes = need;
+        return SPH_OK;
+    }
+    if (*bytes < need) {
+        *bytes = need;
+        return fail(c, SPH_ERR_CAPACITY, "state buffer too small");
+    }
+    StateHeader H{};
+    H.magic = STATE_MAGIC;
+    H.version = STATE_VERSION;
+    H.n = c->N;
+    H.dim = c->dom.dim;
+    H.precision = c->dom.precision;
+    H.have_rates = c->have_rates;
+    H.scheme = c->rates_scheme;
+    Control ctl{};
+    CK(cudaMemcpyAsync(&ctl, c->ctl, sizeof ctl, cudaMemcpyDeviceToHost, c->stream));
+    const ParticleSet& S = c->set[c->cur];
+    const double* fields[15] = {S.x[0], S.x[1], S.x[2], S.u[0], S.u[1], S.u[2], S.rho, S.m,
+                                S.arho, S.a[0], S.a[1], S.a[2], S.xs[0], S.xs[1], S.xs[2]};
+    char* p = (char*)buf + sizeof(StateHeader);
+    for (int k = 0; k < 15; ++k)
+        CK(cudaMemcpyAsync(p + (size_t)k * N * 8, fields[k], N * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(p + 15 * N * 8, S.tag, N * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    H.t = ctl.t;
+    H.dt = ctl.dt;
+    H.step = ctl.step;
+    std::memcpy(buf, &H, sizeof H);
+    *bytes = need;
+    return SPH_OK;
+}
+
+sph_status sph_load_state(sph_ctx* c, const void* buf, size_t bytes) {
+    if (!c || !buf) return fail(c, SPH_ERR_INVALID, "NULL argument");
+    const size_t N = (size_t)c->N;
+    const size_t need = sizeof(StateHeader) + 15 * N * 8 + N * 4;
+    StateHeader H;
+    if (bytes < sizeof H) return fail(c, SPH_ERR_INVALID, "state buffer too small");
+    std::memcpy(&H, buf, sizeof H);
+    if (H.magic != STATE_MAGIC || H.version != STATE_VERSION || H.n != c->N || H.dim != c->dom.dim ||
+        bytes < need)
+        return fail(c, SPH_ERR_INVALID, "state buffer does not match this context");
+    const ParticleSet& S = c->set[c->cur];
+    double* fields[15] = {S.x[0], S.x[1], S.x[2], S.u[0], S.u[1], S.u[2], S.rho, S.m,
+                          S.arho, S.a[0], S.a[1], S.a[2], S.xs[0], S.xs[1], S.xs[2]};
+    const char* p = (const char*)buf + sizeof(StateHeader);
+    for (int k = 0; k < 15; ++k)
+        CK(cudaMemcpyAsync(fields[k], p + (size_t)k * N * 8, N * 8, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(S.tag, p + 15 * N * 8, N * 4, cudaMemcpyHostToDevice, c->stream));
+    Control ctl{};
+    ctl.t = H.t;
+    ctl.dt = H.dt;
+    ctl.step = H.step;
+    CK(cudaMemcpyAsync(c->ctl, &ctl, sizeof ctl, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->have_rates = H.have_rates != 0;
+    c->rates_scheme = H.scheme;
+    c->nbr_valid = false;
+    c->hist_at_call = 0;
+    c->steps_total = 0;
+    return SPH_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,472 @@
+// Neighbour-search build of the uniform cell grid (Sec. 2.2, the Z-order / cell-sort
+// approach the paper provides on GPUs): cell key per particle (fused with the
+// predictor half-kick and drift of Sec. 2.1 and the periodic wrap), a stable LSD radix
+// sort of (key, index), the gather of the FP64 state into cell order with the Tait EOS
+// (Eq. eos) fused into the write of the pair-loop shadow arrays, and the cell table.
+#include "sph_device.cuh"
+#include "sph_launch.h"
+
+namespace sph {
+
+// ----------------------------------------------------------- drift + cell key
+// Per particle in the current order: for fluid, u_half = u + dt/2 a and
+// x <- wrap(x + dt (u_half + xsph)) (written back in place); then the linear cell id
+// of the position rounded to the pair-loop precision.
+__global__ void k_drift_keys(ParticleSet S, int n, Grid G, StepConst C, Control* ctl,
+                             int drift, uint32_t* keys) {
+    if (ctl->status) return;
+    const double dt = ctl->dt;
+    unsigned outside = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const bool fluid = !(S.tag[i] & WALL_BIT);
+        int c[3] = {0, 0, 0};
+        int clamped = 0;
+        for (int d = 0; d < G.dim; ++d) {
+            double x = S.x[d][i];
+            if (drift && fluid) {
+                double uh = S.u[d][i] + 0.5 * dt * S.a[d][i];
+                x = x + dt * (uh + S.xs[d][i]);
+                if (G.periodic[d] && !(x >= G.lo[d] && x < G.hi[d])) {
+                    double k = floor(__ddiv_rn(__dsub_rn(x, G.lo[d]), G.L[d]));
+                    x = __dsub_rn(x, __dmul_rn(k, G.L[d]));
+                    if (x >= G.hi[d]) x = __dsub_rn(x, G.L[d]);
+                    if (x < G.lo[d]) x = G.lo[d];
+                }
+                S.x[d][i] = x;
+            }
+            double xm = C.precision ? (double)__double2float_rn(x) : x;
+            c[d] = cell_coord(xm, G.lo[d], G.cs[d], G.nc[d], &clamped);
+        }
+        outside += clamped;
+        keys[i] = (uint32_t)(c[0] + G.nc[0] * (c[1] + G.nc[1] * c[2]));
+    }
+    // count clamped particles (warp-aggregated)
+    for (int o = 16; o > 0; o >>= 1) outside += __shfl_down_sync(0xffffffffu, outside, o);
+    if ((threadIdx.x & 31) == 0 && outside) atomicAdd(&ctl->outside, outside);
+}
+
+// -------------------------------------------------------------- radix sort
+// Stable least-significant-digit radix sort, 8-bit digits. A tile of SORT_TILE keys
+// belongs to one block; inside the tile warp w owns the contiguous range
+// [w * 512, (w + 1) * 512) and walks it in order, so block order, warp order,
+// iteration order and lane order reproduce the input order (stability).
+constexpr int RADIX = 256;
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_WARPS = SORT_THREADS / 32;
+constexpr int SORT_ITEMS = 16;
+constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
+
+__global__ void __launch_bounds__(SORT_THREADS)
+k_radix_hist(const uint32_t* __restrict__ keys, int n, int shift, uint32_t* hist, int nblocks,
+             const Control* ctl) {
+    __shared__ uint32_t h[RADIX];
+    if (ctl->status) return;
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int base = blockIdx.x * SORT_TILE;
+#pragma unroll 4
+    for (int k = 0; k < SORT_ITEMS; ++k) {
+        int idx = base + k * SORT_THREADS + threadIdx.x;
+        if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & (RADIX - 1)], 1u);
+    }
+    __syncthreads();
+    hist[threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+// Exclusive scan of each digit's row of per-block counts; totals[d] = row sum.
+__global__ void __launch_bounds__(1024)
+k_radix_scan(uint32_t* hist, int nblocks, uint32_t* totals, const Control* ctl) {
+    __shared__ uint32_t wsum[32];
+    if (ctl->status) return;
+    uint32_t* row = hist + (size_t)blockIdx.x * nblocks;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t carry = 0;
+    for (int base = 0; base < nblocks; base += 1024) {
+        int i = base + threadIdx.x;
+        uint32_t v = i < nblocks ? row[i] : 0u;
+        uint32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t s = wsum[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += y;
+            }
+            wsum[lane] = s;
+        }
+        __syncthreads();
+        uint32_t excl = carry + x - v + (warp ? wsum[warp - 1] : 0u);
+        if (i < nblocks) row[i] = excl;
+        carry += wsum[31];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) totals[blockIdx.x] = carry;
+}
+
+__global__ void __launch_bounds__(SORT_THREADS)
+k_radix_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+                uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int n, int shift,
+                const uint32_t* __restrict__ hist, const uint32_t* __restrict__ totals, int nblocks,
+                const Control* ctl) {
+    __shared__ uint32_t base_d[RADIX];
+    __shared__ uint32_t wcnt[SORT_WARPS][RADIX];
+    __shared__ uint32_t wsum[SORT_WARPS];
+    if (ctl->status) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // digit bases: exclusive scan of the 256 digit totals, plus this block's offset
+    {
+        uint32_t v = totals[tid];
+        uint32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        for (int w = 0; w < SORT_WARPS; ++w) wcnt[w][tid] = 0;
+        __syncthreads();
+        uint32_t pre = 0;
+        for (int w = 0; w < warp; ++w) pre += wsum[w];
+        base_d[tid] = pre + x - v + hist[tid * nblocks + blockIdx.x];
+    }
+    __syncthreads();
+    const int wbase = blockIdx.x * SORT_TILE + warp * (SORT_TILE / SORT_WARPS);
+    uint32_t kr[SORT_ITEMS], vr[SORT_ITEMS], rank[SORT_ITEMS];
+    const unsigned ltmask = lanemask_lt();
+#pragma unroll
+    for (int it = 0; it < SORT_ITEMS; ++it) {
+        int idx = wbase + it * 32 + lane;
+        bool valid = idx < n;
+        uint32_t key = valid ? keys_in[idx] : 0u;
+        uint32_t d = valid ? ((key >> shift) & (RADIX - 1)) : (uint32_t)RADIX;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        uint32_t before = valid ? wcnt[warp][d] : 0u;
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] = before + __popc(peers);
+        __syncwarp();
+        kr[it] = key;
+        vr[it] = valid ? (vals_in ? vals_in[idx] : (uint32_t)idx) : 0u;
+        rank[it] = before + __popc(peers & ltmask);
+    }
+    __syncthreads();
+    {   // exclusive prefix over warps, per digit
+        uint32_t run = 0;
+        for (int w = 0; w < SORT_WARPS; ++w) {
+            uint32_t c = wcnt[w][tid];
+            wcnt[w][tid] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < SORT_ITEMS; ++it) {
+        int idx = wbase + it * 32 + lane;
+        if (idx < n) {
+            uint32_t d = (kr[it] >> shift) & (RADIX - 1);
+            uint32_t pos = base_d[d] + wcnt[warp][d] + rank[it];
+            keys_out[pos] = kr[it];
+            vals_out[pos] = vr[it];
+        }
+    }
+}
+
+// offsets[c] = number of sorted keys < c, for c in [0, ncells].
+__global__ void k_cell_offsets(const uint32_t* __restrict__ skeys, int n, int ncells,
+                               uint32_t* __restrict__ off, const Control* ctl) {
+    if (ctl->status) return;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= ncells; c += gridDim.x * blockDim.x) {
+        int lo = 0, hi = n;
+        while (lo < hi) {
+            int mid = (lo + hi) >> 1;
+            if (skeys[mid] < (uint32_t)c) lo = mid + 1;
+            else hi = mid;
+        }
+        off[c] = (uint32_t)lo;
+    }
+}
+
+// ------------------------------------------------------------------ reorder
+// Gather the state into cell order. kick: predictor half-kick of velocity (fluid) and
+// density (continuity). Rates are carried along only outside a step (carry_rates).
+// Writes the pair-loop shadow: P = (x, y, z, +-m) with the sign marking walls,
+// Q = (u, v, w, rho), R = p / rho^2 with p from the Tait EOS (Eq. eos) in FP64.
+template <class Real>
+__global__ void k_reorder(ParticleSet in, ParticleSet out, const uint32_t* __restrict__ perm,
+                          int n, int dim, StepConst C, Control* ctl, int kick, int carry_rates,
+                          typename V4<Real>::T* __restrict__ P, typename V4<Real>::T* __restrict__ Q,
+                          Real* __restrict__ R) {
+    if (ctl->status) return;
+    const double dt = ctl->dt;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int o = (int)perm[k];
+        const uint32_t tag = in.tag[o];
+        const bool fluid = !(tag & WALL_BIT);
+        double x[3] = {0, 0, 0}, u[3] = {0, 0, 0};
+        for (int d = 0; d < dim; ++d) {
+            x[d] = in.x[d][o];
+            u[d] = in.u[d][o];
+            if (kick && fluid) u[d] += 0.5 * dt * in.a[d][o];
+            out.x[d][k] = x[d];
+            out.u[d][k] = u[d];
+        }
+        double rho = in.rho[o];
+        if (kick && C.continuity) rho += 0.5 * dt * in.arho[o];
+        const double m = in.m[o];
+        out.rho[k] = rho;
+        out.m[k] = m;
+        out.tag[k] = tag;
+        if (carry_rates) {
+            out.arho[k] = in.arho[o];
+            for (int d = 0; d < dim; ++d) {
+                out.a[d][k] = in.a[d][o];
+                out.xs[d][k] = in.xs[d][o];
+            }
+        }
+        double r = rho * C.inv_rho0;
+        double rg;
+        if (C.gamma7) {
+            double r2 = r * r;
+            rg = r2 * r2 * r2 * r;
+        } else {
+            rg = pow(r, C.gamma);
+        }
+        const double p = C.B * (rg - 1.0);
+        typename V4<Real>::T pv, qv;
+        pv.x = (Real)x[0]; pv.y = (Real)x[1]; pv.z = (Real)x[2];
+        pv.w = (Real)(fluid ? m : -m);
+        qv.x = (Real)u[0]; qv.y = (Real)u[1]; qv.z = (Real)u[2]; qv.w = (Real)rho;
+        P[k] = pv;
+        Q[k] = qv;
+        R[k] = (Real)(p / (rho * rho));
+    }
+}
+
+// --------------------------------------------------------- get / set helpers
+// out[id - first] = field[k] for particles whose global id lies in [first, first + count).
+__global__ void k_gather_by_id(const double* __restrict__ field, const uint32_t* __restrict__ tag,
+                               int n, uint32_t first, uint32_t count, double* __restrict__ out) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        uint32_t id = tag[k] & ID_MASK;
+        if (id - first < count) out[id - first] = field[k];
+    }
+}
+
+__global__ void k_scatter_by_id(double* __restrict__ field, const uint32_t* __restrict__ tag, int n,
+                                uint32_t first, uint32_t count, const double* __restrict__ in) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        uint32_t id = tag[k] & ID_MASK;
+        if (id - first < count) field[k] = in[id - first];
+    }
+}
+
+__global__ void k_cell_of_by_id(const uint32_t* __restrict__ skeys, const uint32_t* __restrict__ tag,
+                                int n, uint32_t* __restrict__ cell_of, int64_t* __restrict__ order) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        uint32_t id = tag[k] & ID_MASK;
+        cell_of[id] = skeys[k];
+        order[k] = (int64_t)id;
+    }
+}
+
+// Wrap periodic coordinates into the box (at creation and after sph_set).
+__global__ void k_wrap_all(ParticleSet S, int n, Grid G) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        for (int d = 0; d < G.dim; ++d) {
+            if (!G.periodic[d]) continue;
+            double x = S.x[d][i];
+            if (x >= G.lo[d] && x < G.hi[d]) continue;
+            double k = floor(__ddiv_rn(__dsub_rn(x, G.lo[d]), G.L[d]));
+            x = __dsub_rn(x, __dmul_rn(k, G.L[d]));
+            if (x >= G.hi[d]) x = __dsub_rn(x, G.L[d]);
+            if (x < G.lo[d]) x = G.lo[d];
+            S.x[d][i] = x;
+        }
+    }
+}
+
+// ------------------------------------------------------ neighbour export
+// The same stencil walk and predicate as the pair loops; pass 0 counts, pass 1 writes
+// the original ids of the neighbours of sorted particle k at offsets[id(k)] and sorts
+// the row ascending.
+template <class Real, int DIM>
+__global__ void k_export_neighbors(const typename V4<Real>::T* __restrict__ P,
+                                   const uint32_t* __restrict__ skeys,
+                                   const uint32_t* __restrict__ off,
+                                   const uint32_t* __restrict__ tag, int n, Grid G,
+                                   PairConst<Real> K, int pass, uint32_t* __restrict__ counts,
+                                   const int64_t* __restrict__ row_off, int32_t* __restrict__ idx) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const typename V4<Real>::T pi = P[i];
+        const uint32_t key = skeys[i];
+        const int cx = key % G.nc[0];
+        const int cy = (key / G.nc[0]) % G.nc[1];
+        const int cz = key / (G.nc[0] * G.nc[1]);
+        const uint32_t id = tag[i] & ID_MASK;
+        int64_t w = pass ? row_off[id] : 0;
+        const int64_t w0 = w;
+        uint32_t cnt = 0;
+        for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz) {
+            int z = cz + dz;
+            if (DIM == 3) {
+                if (z < 0 || z >= G.nc[2]) {
+                    if (!G.periodic[2]) continue;
+                    z = (z + G.nc[2]) % G.nc[2];
+                }
+            }
+            for (int dy = -1; dy <= 1; ++dy) {
+                int y = cy + dy;
+                if (y < 0 || y >= G.nc[1]) {
+                    if (!G.periodic[1]) continue;
+                    y = (y + G.nc[1]) % G.nc[1];
+                }
+                const int row = G.nc[0] * (y + G.nc[1] * z);
+                int xr[2][2];
+                int nruns = 0;
+                int x0 = cx - 1, x1 = cx + 1;
+                if (G.periodic[0]) {
+                    if (x0 < 0) { xr[nruns][0] = G.nc[0] - 1; xr[nruns][1] = G.nc[0] - 1; ++nruns; x0 = 0; }
+                    if (x1 >= G.nc[0]) { xr[nruns][0] = 0; xr[nruns][1] = 0; ++nruns; x1 = G.nc[0] - 1; }
+                } else {
+                    if (x0 < 0) x0 = 0;
+                    if (x1 >= G.nc[0]) x1 = G.nc[0] - 1;
+                }
+                xr[nruns][0] = x0; xr[nruns][1] = x1; ++nruns;
+                for (int r = 0; r < nruns; ++r) {
+                    const uint32_t jb = off[row + xr[r][0]], je = off[row + xr[r][1] + 1];
+                    for (uint32_t j = jb; j < je; ++j) {
+                        if ((int)j == i) continue;
+                        const typename V4<Real>::T pj = P[j];
+                        Real dx = min_image(rn_sub(pi.x, pj.x), G.periodic[0], K.L[0], K.halfL[0]);
+                        Real dy = min_image(rn_sub(pi.y, pj.y), G.periodic[1], K.L[1], K.halfL[1]);
+                        Real dzv = DIM == 3 ? min_image(rn_sub(pi.z, pj.z), G.periodic[2], K.L[2], K.halfL[2]) : Real(0);
+                        Real r2 = dist2<Real, DIM>(dx, dy, dzv);
+                        if (!(r2 < K.kh2)) continue;
+                        if (pass) idx[w++] = (int32_t)(tag[j] & ID_MASK);
+                        ++cnt;
+                    }
+                }
+            }
+        }
+        if (!pass) {
+            counts[id] = cnt;
+        } else {
+            for (int64_t a = w0 + 1; a < w; ++a) {  // insertion sort of the row
+                int32_t v = idx[a];
+                int64_t b = a - 1;
+                while (b >= w0 && idx[b] > v) { idx[b + 1] = idx[b]; --b; }
+                idx[b + 1] = v;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+static inline int grid_for(long long n, int threads, int cap) {
+    long long b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (int)b;
+}
+
+void launch_drift_keys(const ParticleSet& S, int n, const Grid& G, const StepConst& C,
+                       Control* ctl, int drift, uint32_t* keys, cudaStream_t st, int sms) {
+    k_drift_keys<<<grid_for(n, 256, sms * 8), 256, 0, st>>>(S, n, G, C, ctl, drift, keys);
+}
+
+int radix_passes(int ncells) {
+    int bits = 0;
+    while (bits < 32 && (1ull << bits) < (unsigned long long)ncells) ++bits;
+    return (bits + 7) / 8;
+}
+
+size_t radix_hist_words(int n) {
+    int nblocks = (n + SORT_TILE - 1) / SORT_TILE;
+    if (nblocks < 1) nblocks = 1;
+    return (size_t)RADIX * nblocks + RADIX;
+}
+
+// Sorts (keys[0], iota) by the low `passes * 8` bits; returns the buffer index (0 or 1)
+// holding the sorted keys and the permutation (sorted position -> previous position).
+int launch_radix_sort(uint32_t* keys[2], uint32_t* vals[2], int n, int passes, uint32_t* hist,
+                      Control* ctl, cudaStream_t st) {
+    int nblocks = (n + SORT_TILE - 1) / SORT_TILE;
+    if (nblocks < 1) nblocks = 1;
+    uint32_t* totals = hist + (size_t)RADIX * nblocks;
+    int cur = 0;
+    for (int p = 0; p < passes; ++p) {
+        int shift = 8 * p;
+        k_radix_hist<<<nblocks, SORT_THREADS, 0, st>>>(keys[cur], n, shift, hist, nblocks, ctl);
+        k_radix_scan<<<RADIX, 1024, 0, st>>>(hist, nblocks, totals, ctl);
+        k_radix_scatter<<<nblocks, SORT_THREADS, 0, st>>>(keys[cur], p == 0 ? nullptr : vals[cur],
+                                                          keys[cur ^ 1], vals[cur ^ 1], n, shift,
+                                                          hist, totals, nblocks, ctl);
+        cur ^= 1;
+    }
+    return cur;
+}
+
+void launch_cell_offsets(const uint32_t* skeys, int n, int ncells, uint32_t* off, Control* ctl,
+                         cudaStream_t st, int sms) {
+    k_cell_offsets<<<grid_for((long long)ncells + 1, 256, sms * 8), 256, 0, st>>>(skeys, n, ncells,
+                                                                                  off, ctl);
+}
+
+void launch_reorder(int precision, const ParticleSet& in, const ParticleSet& out,
+                    const uint32_t* perm, int n, int dim, const StepConst& C, Control* ctl,
+                    int kick, int carry_rates, void* P, void* Q, void* R, cudaStream_t st, int sms) {
+    int g = grid_for(n, 256, sms * 8);
+    if (precision)
+        k_reorder<float><<<g, 256, 0, st>>>(in, out, perm, n, dim, C, ctl, kick, carry_rates,
+                                            (F4*)P, (F4*)Q, (float*)R);
+    else
+        k_reorder<double><<<g, 256, 0, st>>>(in, out, perm, n, dim, C, ctl, kick, carry_rates,
+                                             (D4*)P, (D4*)Q, (double*)R);
+}
+
+void launch_gather_by_id(const double* field, const uint32_t* tag, int n, uint32_t first,
+                         uint32_t count, double* out, cudaStream_t st, int sms) {
+    k_gather_by_id<<<grid_for(n, 256, sms * 8), 256, 0, st>>>(field, tag, n, first, count, out);
+}
+
+void launch_scatter_by_id(double* field, const uint32_t* tag, int n, uint32_t first,
+                          uint32_t count, const double* in, cudaStream_t st, int sms) {
+    k_scatter_by_id<<<grid_for(n, 256, sms * 8), 256, 0, st>>>(field, tag, n, first, count, in);
+}
+
+void launch_cell_of_by_id(const uint32_t* skeys, const uint32_t* tag, int n, uint32_t* cell_of,
+                          int64_t* order, cudaStream_t st, int sms) {
+    k_cell_of_by_id<<<grid_for(n, 256, sms * 8), 256, 0, st>>>(skeys, tag, n, cell_of, order);
+}
+
+void launch_wrap_all(const ParticleSet& S, int n, const Grid& G, cudaStream_t st, int sms) {
+    k_wrap_all<<<grid_for(n, 256, sms * 8), 256, 0, st>>>(S, n, G);
+}
+
+void launch_export_neighbors(int precision, int dim, const void* P, const uint32_t* skeys,
+                             const uint32_t* off, const uint32_t* tag, int n, const Grid& G,
+                             const PairConst<float>& Kf, const PairConst<double>& Kd, int pass,
+                             uint32_t* counts, const int64_t* row_off, int32_t* idx,
+                             cudaStream_t st, int sms) {
+    int g = grid_for(n, 128, sms * 16);
+    if (precision) {
+        if (dim == 2)
+            k_export_neighbors<float, 2><<<g, 128, 0, st>>>((const F4*)P, skeys, off, tag, n, G, Kf,
+                                                            pass, counts, row_off, idx);
+        else
+            k_export_neighbors<float, 3><<<g, 128, 0, st>>>((const F4*)P, skeys, off, tag, n, G, Kf,
+                                                            pass, counts, row_off, idx);
+    } else {
+        if (dim == 2)
+            k_export_neighbors<double, 2><<<g, 128, 0, st>>>((const D4*)P, skeys, off, tag, n, G, Kd,
+                                                             pass, counts, row_off, idx);
+        else
+            k_export_neighbors<double, 3><<<g, 128, 0, st>>>((const D4*)P, skeys, off, tag, n, G, Kd,
+                                                             pass, counts, row_off, idx);
+    }
+}
+
+}  // namespace sph

@@ -1,0 +1,213 @@
+// Device-side definitions shared by the CUDA translation units of the WCSPH library:
+// the particle-set layout in HBM, the launch argument blocks, the neighbour predicate,
+// the smoothing kernels and the compensated accumulator.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sph {
+
+constexpr int QUINTIC = 0;
+constexpr int WENDLAND_C2 = 1;
+constexpr uint32_t WALL_BIT = 0x80000000u;  // tag = global id | WALL_BIT for wall particles
+constexpr uint32_t ID_MASK = 0x7fffffffu;
+
+// Status bits raised on the device (host maps them to sph_status).
+constexpr unsigned ST_NONFINITE = 1u;
+constexpr unsigned ST_TIMEOUT = 2u;
+
+// Equation switches of one right-hand-side evaluation.
+constexpr int F_CONTINUITY = 1;   // Eq. continuity:sph (else summation density, Eq. 2)
+constexpr int F_LAMINAR = 2;      // Eq. mom:sph:visc
+constexpr int F_AV = 4;           // Monaghan artificial viscosity
+constexpr int F_XSPH = 8;         // XSPH correction
+
+constexpr int DIAG_N = 12;
+constexpr int HIST_CAP = 65536;
+
+// 16- and 32-byte vectors: one vector load per particle record.
+struct __align__(16) F4 { float x, y, z, w; };
+struct __align__(32) D4 { double x, y, z, w; };
+template <class Real> struct V4;
+template <> struct V4<float> { using T = F4; };
+template <> struct V4<double> { using T = D4; };
+
+// One copy of the FP64 particle state, struct of arrays, in the device's internal
+// (cell-sorted) order. Two copies exist; a rebuild gathers one into the other.
+struct ParticleSet {
+    double* x[3];
+    double* u[3];
+    double* rho;
+    double* m;
+    double* arho;   // rates of the last evaluation
+    double* a[3];
+    double* xs[3];  // XSPH velocity correction
+    uint32_t* tag;  // global id | WALL_BIT
+};
+
+// Device control block: time, step size, diagnostics, status.
+struct Control {
+    double dt;            // step used by the next drift / kick
+    double t;
+    double rec[DIAG_N];   // diagnostics record of the last evaluation
+    unsigned long long step;
+    unsigned int status;
+    unsigned int ticket;  // last-block counter of the reduction
+    unsigned int outside; // particles clamped into an edge cell at the last key build
+    unsigned int hist_count;
+};
+
+// Grid of cells (Sec. 2.2): cells no smaller than the support radius.
+struct Grid {
+    int dim;
+    int nc[3];
+    int periodic[3];
+    int ncells;
+    double lo[3], cs[3], L[3], hi[3];
+};
+
+// Constants of the pair loops in the precision of the mode.
+template <class Real>
+struct PairConst {
+    Real L[3], halfL[3];
+    Real kh2;       // (k h)^2, computed as (k * h) * (k * h) in Real
+    Real inv_h;
+    Real h;
+    Real wfac;      // sigma / h^d
+    Real gfac;      // sigma / h^(d+2)
+    Real eta_h2;    // eta h^2
+    Real av_h2;     // 0.01 h^2
+    Real nu4;       // 4 nu
+    Real alpha_c0;  // alpha c0
+    Real xsph;
+    int flags;
+};
+
+// Constants of the FP64 per-particle stages.
+struct StepConst {
+    double rho0, inv_rho0, B, gamma;  // Tait: p = B ((rho/rho0)^gamma - 1)
+    double g[3];
+    double h, c0, nu;
+    double dt_fixed;                  // > 0 fixed step, else CFL-type step
+    int continuity;
+    int gamma7;                       // gamma == 7: power by multiplications
+    int precision;                    // 1: positions rounded to float for binning
+};
+
+// --------------------------------------------------------------- rounding helpers
+__device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float rn_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rn_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double rn_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+
+// Separation of the neighbour test: difference with the minimum image on periodic
+// axes. Every operation is rounded on its own (no fused multiply-add), so the result
+// is the same IEEE value on any machine.
+template <class Real>
+__device__ __forceinline__ Real min_image(Real d, int periodic, Real L, Real halfL) {
+    if (periodic) {
+        if (d > halfL) d = rn_sub(d, L);
+        else if (d < -halfL) d = rn_add(d, L);
+    }
+    return d;
+}
+
+// r^2 = ((dx dx) + dy dy) + dz dz, each operation rounded separately.
+template <class Real, int DIM>
+__device__ __forceinline__ Real dist2(Real dx, Real dy, Real dz) {
+    Real r2 = rn_add(rn_mul(dx, dx), rn_mul(dy, dy));
+    if (DIM == 3) r2 = rn_add(r2, rn_mul(dz, dz));
+    return r2;
+}
+
+// Cell coordinate of a position on one axis: floor((x_mode - lo) / cs), clamped.
+__device__ __forceinline__ int cell_coord(double xm, double lo, double cs, int n, int* clamped) {
+    double v = __ddiv_rn(__dsub_rn(xm, lo), cs);
+    double c = floor(v);
+    if (!(c >= 0.0)) { *clamped = 1; return 0; }
+    if (c > (double)(n - 1)) { *clamped = 1; return n - 1; }
+    return (int)c;
+}
+
+// ------------------------------------------------------------------- kernels
+// Unnormalised smoothing function w(q) and f(q) = w'(q) / q, so that
+// W = wfac w(q) and grad_i W = gfac f(q) (x_i - x_j) with no division by r.
+//  quintic (support 3): w = (3-q)^5 - 6 (2-q)^5 + 15 (1-q)^5 with terms where positive;
+//    f = -50 q^3 + 120 q^2 - 120 on [0,1), (-5 (3-q)^4 + 30 (2-q)^4) / q on [1,2),
+//    -5 (3-q)^4 / q on [2,3).
+//  Wendland C2 (support 2): w = (1 - q/2)^4 (2q + 1), f = -5 (1 - q/2)^3.
+template <class Real, int KERNEL>
+__device__ __forceinline__ Real kernel_f(Real q) {
+    if (KERNEL == QUINTIC) {
+        if (q < Real(1)) {
+            return (Real(-50) * q + Real(120)) * q * q - Real(120);
+        }
+        Real t3 = Real(3) - q;
+        Real t3s = t3 * t3;
+        Real p = Real(-5) * t3s * t3s;
+        if (q < Real(2)) {
+            Real t2 = Real(2) - q;
+            Real t2s = t2 * t2;
+            p += Real(30) * t2s * t2s;
+        }
+        return p / q;
+    } else {
+        Real t = Real(1) - Real(0.5) * q;
+        return Real(-5) * t * t * t;
+    }
+}
+
+template <class Real, int KERNEL>
+__device__ __forceinline__ Real kernel_w(Real q) {
+    if (KERNEL == QUINTIC) {
+        Real t3 = Real(3) - q;
+        Real t3s = t3 * t3;
+        Real w = t3s * t3s * t3;
+        if (q < Real(2)) {
+            Real t2 = Real(2) - q;
+            Real t2s = t2 * t2;
+            w -= Real(6) * t2s * t2s * t2;
+            if (q < Real(1)) {
+                Real t1 = Real(1) - q;
+                Real t1s = t1 * t1;
+                w += Real(15) * t1s * t1s * t1;
+            }
+        }
+        return w;
+    } else {
+        Real t = Real(1) - Real(0.5) * q;
+        Real t2 = t * t;
+        return t2 * t2 * (Real(2) * q + Real(1));
+    }
+}
+
+// --------------------------------------------------------- compensated sums
+// Neumaier's improved Kahan-Babuska summation for FP32 per-particle sums; a plain sum
+// in FP64 mode. The value is read out in FP64 as s + c.
+template <class Real>
+struct Acc {
+    Real s, c;
+    __device__ __forceinline__ void zero() { s = Real(0); c = Real(0); }
+    __device__ __forceinline__ void add(Real v) {
+        if (sizeof(Real) == 4) {
+            Real t = s + v;
+            Real e = (fabs(s) >= fabs(v)) ? ((s - t) + v) : ((v - t) + s);
+            c += e;
+            s = t;
+        } else {
+            s += v;
+        }
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+}  // namespace sph

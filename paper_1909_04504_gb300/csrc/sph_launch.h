@@ -1,0 +1,58 @@
+// Host-side launchers of the device kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "sph_device.cuh"
+
+namespace sph {
+
+// nnps.cu
+void launch_drift_keys(const ParticleSet& S, int n, const Grid& G, const StepConst& C,
+                       Control* ctl, int drift, uint32_t* keys, cudaStream_t st, int sms);
+int radix_passes(int ncells);
+size_t radix_hist_words(int n);
+int launch_radix_sort(uint32_t* keys[2], uint32_t* vals[2], int n, int passes, uint32_t* hist,
+                      Control* ctl, cudaStream_t st);
+void launch_cell_offsets(const uint32_t* skeys, int n, int ncells, uint32_t* off, Control* ctl,
+                         cudaStream_t st, int sms);
+void launch_reorder(int precision, const ParticleSet& in, const ParticleSet& out,
+                    const uint32_t* perm, int n, int dim, const StepConst& C, Control* ctl,
+                    int kick, int carry_rates, void* P, void* Q, void* R, cudaStream_t st, int sms);
+void launch_gather_by_id(const double* field, const uint32_t* tag, int n, uint32_t first,
+                         uint32_t count, double* out, cudaStream_t st, int sms);
+void launch_scatter_by_id(double* field, const uint32_t* tag, int n, uint32_t first,
+                          uint32_t count, const double* in, cudaStream_t st, int sms);
+void launch_cell_of_by_id(const uint32_t* skeys, const uint32_t* tag, int n, uint32_t* cell_of,
+                          int64_t* order, cudaStream_t st, int sms);
+void launch_wrap_all(const ParticleSet& S, int n, const Grid& G, cudaStream_t st, int sms);
+void launch_export_neighbors(int precision, int dim, const void* P, const uint32_t* skeys,
+                             const uint32_t* off, const uint32_t* tag, int n, const Grid& G,
+                             const PairConst<float>& Kf, const PairConst<double>& Kd, int pass,
+                             uint32_t* counts, const int64_t* row_off, int32_t* idx,
+                             cudaStream_t st, int sms);
+
+// pairs.cu
+struct PairLaunch {
+    int precision, dim, kernel, summation, kick, n, grid;
+    const void* P;
+    void* Q;
+    void* R;
+    const uint32_t* skeys;
+    const uint32_t* off;
+    Grid G;
+    StepConst C;
+    ParticleSet S;
+    Control* ctl;
+    double* partials;
+    double* history;
+};
+int pair_threads();
+int partial_stride();
+void launch_pairs(const PairLaunch& L, const PairConst<float>& Kf, const PairConst<double>& Kd,
+                  cudaStream_t st);
+int pairs_max_blocks_per_sm(int precision, int dim, int kernel);
+
+}  // namespace sph

@@ -1,0 +1,243 @@
+"""GPU-vs-oracle parity through the C ABI (sm_103a kernels).
+
+Bars (stated per test): neighbour sets, cell tables and pair counts bit-exact given the
+same coordinates; FP64 mode <= 1e-10 normwise relative per field; FP32 pair loops
+<= 1e-4 relative L2 per field; Taylor-Green max-velocity curve within 1 % of the
+oracle's (FP64 mode: far tighter)."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from gpu_util import csr_equal, normwise, oracle_wl, rel_l2, sim_of
+
+import paper_1909_04504_gb300 as G
+
+pytestmark = pytest.mark.gpu
+
+FIELDS_2D = ("x", "y", "u", "v", "rho")
+FIELDS_3D = ("x", "y", "z", "u", "v", "w", "rho")
+RATES_2D = ("arho", "ax", "ay", "xsx", "xsy")
+RATES_3D = ("arho", "ax", "ay", "az", "xsx", "xsy", "xsz")
+
+
+def small_configs():
+    """Structures of the five workloads at oracle-friendly sizes (several tiles, ragged)."""
+    tg2 = W.taylor_green_2d(n=50)
+    db2 = W.dam_break_2d(dx=0.02)
+    tg3 = W.taylor_green_3d(n=16)
+    db3 = W.dam_break_3d(dx=0.04)
+    return {"tg2d": tg2, "db2d": db2, "tg3d": tg3, "db3d": db3}
+
+
+CONFIGS = small_configs()
+
+
+@pytest.mark.parametrize("name", sorted(CONFIGS))
+@pytest.mark.parametrize("prec", [G.PREC_FP64, G.PREC_FP32])
+def test_cells_and_neighbours_bit_exact(name, prec):
+    wl = oracle_wl(CONFIGS[name], prec)
+    s = O.state_of(wl)
+    with sim_of(wl) as sim:
+        nc, cs, ncells = sim.grid()
+        onc, ocs, oncells = O.grid(wl)
+        assert nc == onc and cs == ocs and ncells == oncells
+        cell_of, off, order = sim.cells()
+        ocell, ooff, oorder = O.cells(wl, s["x"], s["y"], s["z"])
+        assert np.array_equal(cell_of, ocell)
+        assert np.array_equal(off, ooff)
+        # the device order is a stable-by-cell permutation: cells ascending
+        assert np.all(np.diff(cell_of[order].astype(np.int64)) >= 0)
+        noff, nidx = sim.neighbors()
+        ooff2, oidx, _ = O.neighbors(wl, s["x"], s["y"], s["z"])
+        assert csr_equal(noff, nidx, ooff2, oidx)
+
+
+@pytest.mark.parametrize("name", sorted(CONFIGS))
+@pytest.mark.parametrize("prec", [G.PREC_FP64, G.PREC_FP32])
+def test_rhs_matches_oracle(name, prec):
+    wl = oracle_wl(CONFIGS[name], prec)
+    s = O.state_of(wl)
+    rng = np.random.Generator(np.random.PCG64(11))
+    fluid = s["role"] == W.FLUID
+    # a non-trivial state: perturbed density (pressure) and velocity on fluid particles
+    s["rho"] = s["rho"] * (1.0 + 0.003 * rng.normal(size=s["rho"].shape))
+    for k in ("u", "v", "w")[:wl.dim]:
+        s[k] = np.where(fluid, s[k] + 0.05 * rng.normal(size=s[k].shape), 0.0)
+    ref = O.rhs(wl, s)
+    with sim_of(wl) as sim:
+        for k in ["rho"] + ["u", "v", "w"][:wl.dim]:
+            sim.set(k, s[k])
+        sim.eval_rhs(G.scheme_of(wl))
+        r = sim.rates()
+        d = sim.diagnostics()
+        assert d[8] == ref["pairs"] and d[9] == ref["candidates"]
+        rates = RATES_3D if wl.dim == 3 else RATES_2D
+        for k in rates:
+            if np.max(np.abs(ref[k])) == 0.0:
+                assert np.max(np.abs(r[k])) < 1e-12
+                continue
+            if prec == G.PREC_FP64:
+                assert normwise(r[k], ref[k]) <= 1e-10, k
+            else:
+                assert rel_l2(r[k], ref[k]) <= 1e-4, k
+
+
+@pytest.mark.parametrize("name", sorted(CONFIGS))
+@pytest.mark.parametrize("prec", [G.PREC_FP64, G.PREC_FP32])
+def test_one_step_fields(name, prec):
+    wl = oracle_wl(CONFIGS[name], prec)
+    s = O.state_of(wl)
+    st, hist = O.run(wl, s, wl.dt, 1)
+    with sim_of(wl) as sim:
+        sim.step(G.scheme_of(wl), wl.dt, 1)
+        g = sim.state()
+        h = sim.history()
+    fields = FIELDS_3D if wl.dim == 3 else FIELDS_2D
+    for k in fields:
+        if prec == G.PREC_FP64:
+            assert normwise(g[k], st[k]) <= 1e-10, k
+        else:
+            assert rel_l2(g[k], st[k]) <= 1e-4, k
+    assert h.shape[0] == 1
+    assert abs(h[0, 0] - hist[1, 0]) < 1e-15 and h[0, 8] == hist[1, 8] and h[0, 9] == hist[1, 9]
+
+
+def test_taylor_green_decay_curve_fp64():
+    """Config 1 (2D TG, FP64, 2,500 particles, 200 steps): max |u| curve vs the oracle."""
+    wl = W.taylor_green_2d(n=50, steps=200)
+    s = O.state_of(wl)
+    st, hist = O.run(wl, s, wl.dt, wl.steps)
+    with sim_of(wl) as sim:
+        sim.step(G.scheme_of(wl), wl.dt, wl.steps)
+        h = sim.history()
+        g = sim.state()
+    assert h.shape[0] == wl.steps
+    umax_g, umax_o = h[:, 3], hist[1:, 3]
+    assert np.max(np.abs(umax_g - umax_o) / umax_o) <= 0.01
+    assert np.max(np.abs(umax_g - umax_o) / umax_o) <= 1e-9  # FP64: far inside the 1 % bar
+    for k in FIELDS_2D:
+        assert normwise(g[k], st[k]) <= 1e-8, k
+
+
+def test_taylor_green_decay_curve_fp32():
+    wl = W.taylor_green_2d(n=50, steps=200, precision=W.PREC_FP32)
+    s = O.state_of(wl)
+    _, hist = O.run(wl, s, wl.dt, wl.steps)
+    with sim_of(wl) as sim:
+        sim.step(G.scheme_of(wl), wl.dt, wl.steps)
+        h = sim.history()
+    assert np.max(np.abs(h[:, 3] - hist[1:, 3]) / hist[1:, 3]) <= 0.01
+
+
+@pytest.mark.parametrize("prec", [G.PREC_FP64, G.PREC_FP32])
+def test_neighbours_mid_run_given_same_coordinates(prec):
+    """After steps, the GPU's positions fed to the oracle give the GPU's neighbour sets."""
+    wl = W.dam_break_2d(dx=0.02, precision=prec)
+    with sim_of(wl) as sim:
+        sim.step(G.scheme_of(wl), wl.dt, 50)
+        g = sim.state()
+        noff, nidx = sim.neighbors()
+        cell_of, off, _ = sim.cells()
+    ooff, oidx, _ = O.neighbors(wl, g["x"], g["y"])
+    assert csr_equal(noff, nidx, ooff, oidx)
+    ocell, ooffs, _ = O.cells(wl, g["x"], g["y"])
+    assert np.array_equal(cell_of, ocell) and np.array_equal(off, ooffs)
+
+
+def test_summation_density_matches_oracle():
+    wl = W.taylor_green_2d(n=40)
+    wl.density = G.SUMMATION
+    s = O.state_of(wl)
+    ref = O.rhs(wl, s)
+    st, _ = O.run(wl, s, wl.dt, 3)
+    with sim_of(wl) as sim:
+        sim.eval_rhs(G.scheme_of(wl))
+        assert normwise(sim.get("rho"), ref["rho"]) <= 1e-12
+        assert normwise(sim.get("ax"), ref["ax"]) <= 1e-10
+        sim.step(G.scheme_of(wl), wl.dt, 3)
+        for k in FIELDS_2D:
+            assert normwise(sim.get(k), st[k]) <= 1e-10, k
+
+
+def test_full_size_dam_break_2d_rhs_and_step():
+    """Config 2 at full size (20,000 fluid + 3,618 wall, FP32 pairs): one step vs oracle."""
+    wl = W.dam_break_2d()
+    s = O.state_of(wl)
+    st, hist = O.run(wl, s, wl.dt, 1)
+    with sim_of(wl) as sim:
+        sim.step(G.scheme_of(wl), wl.dt, 1)
+        g = sim.state()
+        h = sim.history()
+        noff, nidx = sim.neighbors()
+    for k in FIELDS_2D:
+        assert rel_l2(g[k], st[k]) <= 1e-4, k
+    assert h[0, 8] == hist[1, 8] and h[0, 9] == hist[1, 9]
+    ooff, oidx, _ = O.neighbors(wl, g["x"], g["y"])
+    assert csr_equal(noff, nidx, ooff, oidx)
+
+
+def test_deterministic_and_resumable():
+    wl = W.dam_break_2d(dx=0.02, precision=W.PREC_FP32)
+    sch = G.scheme_of(wl)
+    with sim_of(wl) as a, sim_of(wl) as b:
+        a.step(sch, wl.dt, 20)
+        blob = a.save_state()
+        a.step(sch, wl.dt, 15)
+        b.step(sch, wl.dt, 5)
+        b.load_state(blob)
+        b.step(sch, wl.dt, 15)
+        for k in FIELDS_2D:
+            assert np.array_equal(a.get(k), b.get(k)), k
+        assert np.array_equal(a.diagnostics(), b.diagnostics())
+
+
+def test_set_get_roundtrip_and_errors():
+    wl = W.dam_break_2d(dx=0.05)
+    with sim_of(wl) as sim:
+        v = np.arange(sim.count(0), dtype=np.float64)
+        sim.set("u", v, array=0)
+        assert np.array_equal(sim.get("u", array=0), v)
+        assert np.array_equal(sim.get("u", array=1), np.zeros(sim.count(1)))
+        with pytest.raises(G.SphError):
+            sim.get("nope")
+        with pytest.raises(G.SphError):
+            sim.set("ax", np.zeros(sim.count()))
+        with pytest.raises(G.SphError):
+            sim.get("x", array=7)
+        bad = G.scheme_of(wl)
+        bad.c0 = -1.0
+        with pytest.raises(G.SphError):
+            sim.step(bad, wl.dt, 1)
+
+
+def test_nonfinite_is_reported_and_stops():
+    wl = W.taylor_green_2d(n=20)
+    with sim_of(wl) as sim:
+        u = sim.get("u")
+        u[3] = np.nan
+        sim.set("u", u)
+        with pytest.raises(G.SphError) as e:
+            sim.step(G.scheme_of(wl), wl.dt, 5)
+        assert e.value.status == 4
+        # the state is kept at the failing evaluation: later steps were skipped
+        assert sim.diagnostics()[10] <= 1
+
+
+def test_invalid_domain_rejected():
+    wl = W.taylor_green_2d(n=5)  # a periodic axis with fewer than three cells
+    with pytest.raises(G.SphError):
+        sim_of(wl)
+
+
+def test_adaptive_dt_matches_oracle():
+    wl = W.dam_break_2d(dx=0.04, precision=W.PREC_FP64)
+    s = O.state_of(wl)
+    st, hist = O.run(wl, s, 0.0, 10)
+    with sim_of(wl) as sim:
+        sim.step(G.scheme_of(wl), 0.0, 10)
+        h = sim.history()
+        g = sim.state()
+    assert np.max(np.abs(h[:, 1] - hist[1:, 1]) / hist[1:, 1]) < 1e-12
+    for k in FIELDS_2D:
+        assert normwise(g[k], st[k]) <= 1e-10, k
