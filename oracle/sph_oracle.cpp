@@ -28,8 +28,9 @@
  *    c_d = floor(((double)x_mode - lo_d) / cs_d) clamped to [0, n_d - 1];
  *  - eta = 0.01 in the laminar viscosity, Monaghan AV with beta = 0 and 0.01 h^2;
  *  - XSPH over fluid sources, entering the drift only;
- *  - predictor-corrector as kick-drift-kick, density kicked like velocity, one RHS
- *    per step at (x^{n+1}, u^{n+1/2}, rho^{n+1/2});
+ *  - predictor-corrector as kick-drift-kick for u and x; the density advanced like the
+ *    positions with the continuity rate at (x^{n+1}, u^{n+1/2}) before the momentum
+ *    evaluation at (x^{n+1}, u^{n+1/2}, rho^{n+1});
  *  - walls static (x and u fixed), wall density from continuity with fluid sources.
  */
 #include <algorithm>
@@ -340,13 +341,15 @@ struct Counts {
 
 /* ------------------------------------------------------------- the RHS
  * One evaluation of the right-hand sides at state S, in the group order of
- * Sec. 3.2: [summation density], EOS on all particles, then continuity and
- * momentum (with XSPH) on every destination. Sources are visited in ascending
- * particle id.
+ * Sec. 3.2: the density group (summation density, Eq. 2, or the continuity rate,
+ * Eq. continuity:sph, with the density advanced by dt_rho times that rate), the EOS
+ * on all particles, then momentum (with XSPH) on every fluid destination. Sources
+ * are visited in ascending particle id. dt_rho = 0 leaves the density unchanged
+ * (an evaluation without a step).
  */
 template <class T>
 void rhs(const ora_params* P, T nu, T alpha, int64_t n, State<T>& S, const double* m,
-         const uint8_t* role, Rates<T>& R, Counts* counts) {
+         const uint8_t* role, Rates<T>& R, Counts* counts, double dt_rho) {
     const int dim = P->dim;
     std::vector<double> px[3];
     const double* xp[3] = {nullptr, nullptr, nullptr};
@@ -406,10 +409,32 @@ void rhs(const ora_params* P, T nu, T alpha, int64_t n, State<T>& S, const doubl
         S.rho = rho_new;
     }
 
+    /* Eq. (continuity:sph); wall destinations take fluid sources only. The density
+     * is then advanced with the rate, like the positions (Sec. 2.1 reading). */
+    R.arho.assign(n, T(0.0));
+    if (P->density != DENSITY_SUMMATION) {
+#pragma omp parallel for schedule(dynamic, 256)
+        for (int64_t i = 0; i < n; ++i) {
+            const bool fluid_i = role[i] == ROLE_FLUID;
+            T arho = T(0.0);
+            for (int64_t j : nbr[i]) {
+                if (!fluid_i && role[j] != ROLE_FLUID) continue;
+                T r[3], W, gW[3];
+                diff(i, j, r);
+                kern(r, &W, gW);
+                T vdotg = T(0.0);
+                for (int d = 0; d < dim; ++d) vdotg = vdotg + (S.u[d][i] - S.u[d][j]) * gW[d];
+                arho = arho + m[j] * vdotg;
+            }
+            R.arho[i] = arho;
+        }
+        if (dt_rho != 0.0)
+            for (int64_t i = 0; i < n; ++i) S.rho[i] = S.rho[i] + dt_rho * R.arho[i];
+    }
+
     R.p.assign(n, T(0.0));
     for (int64_t i = 0; i < n; ++i) R.p[i] = tait(P, S.rho[i]);
 
-    R.arho.assign(n, T(0.0));
     for (int d = 0; d < 3; ++d) {
         R.a[d].assign(n, T(0.0));
         R.xs[d].assign(n, T(0.0));
@@ -419,7 +444,7 @@ void rhs(const ora_params* P, T nu, T alpha, int64_t n, State<T>& S, const doubl
 #pragma omp parallel for schedule(dynamic, 256)
     for (int64_t i = 0; i < n; ++i) {
         const bool fluid_i = role[i] == ROLE_FLUID;
-        T arho = T(0.0), a[3] = {T(0.0), T(0.0), T(0.0)}, xs[3] = {T(0.0), T(0.0), T(0.0)};
+        T a[3] = {T(0.0), T(0.0), T(0.0)}, xs[3] = {T(0.0), T(0.0), T(0.0)};
         const T Pr_i = R.p[i] / (S.rho[i] * S.rho[i]);
         for (int64_t j : nbr[i]) {
             const bool fluid_j = role[j] == ROLE_FLUID;
@@ -428,16 +453,13 @@ void rhs(const ora_params* P, T nu, T alpha, int64_t n, State<T>& S, const doubl
             T r[3], W, gW[3];
             diff(i, j, r);
             T r2 = kern(r, &W, gW);
-            T vij[3], vdotg = T(0.0), vdotr = T(0.0), rdotg = T(0.0);
+            if (!fluid_i) continue;
+            T vij[3], vdotr = T(0.0), rdotg = T(0.0);
             for (int d = 0; d < 3; ++d) vij[d] = S.u[d][i] - S.u[d][j];
             for (int d = 0; d < dim; ++d) {
-                vdotg = vdotg + vij[d] * gW[d];
                 vdotr = vdotr + vij[d] * r[d];
                 rdotg = rdotg + r[d] * gW[d];
             }
-            /* Eq. (continuity:sph); wall destinations take fluid sources only. */
-            if (P->density != DENSITY_SUMMATION) arho = arho + m[j] * vdotg;
-            if (!fluid_i) continue;
             /* Eq. (mom:sph:press). */
             T Pr_j = R.p[j] / (S.rho[j] * S.rho[j]);
             T pf = Pr_i + Pr_j;
@@ -462,7 +484,6 @@ void rhs(const ora_params* P, T nu, T alpha, int64_t n, State<T>& S, const doubl
         }
         if (fluid_i)
             for (int d = 0; d < dim; ++d) a[d] = a[d] + P->g[d];  // body force, Eq. (mom:sph)
-        R.arho[i] = arho;
         for (int d = 0; d < 3; ++d) { R.a[d][i] = a[d]; R.xs[d][i] = xs[d]; }
     }
     if (counts) {
@@ -511,13 +532,16 @@ double cfl_dt(const ora_params* P, double umax, double amax) {
 }
 
 /* ------------------------------------------------------- the integrator
- * Sec. 2.1 predictor-corrector, read as kick-drift-kick:
- *   u^{n+1/2} = u^n + dt/2 a^n,  rho^{n+1/2} = rho^n + dt/2 arho^n,
+ * Sec. 2.1 predictor-corrector, read as kick-drift-kick for u and x, with the
+ * density advanced like the positions (it is a function of the configuration):
+ *   u^{n+1/2} = u^n + dt/2 a^n,
  *   x^{n+1} = wrap(x^n + dt (u^{n+1/2} + xsph^n)),
- *   (a, arho, xsph)^{n+1} = RHS(x^{n+1}, u^{n+1/2}, rho^{n+1/2}),
- *   u^{n+1} = u^{n+1/2} + dt/2 a^{n+1},  rho^{n+1} = rho^{n+1/2} + dt/2 arho^{n+1}.
- * Walls keep x and u; their density is kicked. With summation density the RHS
- * replaces rho and no density kick is applied.
+ *   arho^{n+1} = D(x^{n+1}, u^{n+1/2}),  rho^{n+1} = rho^n + dt arho^{n+1},
+ *   (a, xsph)^{n+1} = momentum(x^{n+1}, u^{n+1/2}, rho^{n+1}),
+ *   u^{n+1} = u^{n+1/2} + dt/2 a^{n+1}.
+ * (Kicking the density like the velocity instead makes the half-step sequence a
+ * forward-Euler map of the acoustic pair (u, rho) and diverges.) Walls keep x and
+ * u; their density is advanced. With summation density the RHS replaces rho.
  */
 template <class T>
 double run(const ora_params* P, T nu, T alpha, int64_t n, State<T>& S, const double* m,
@@ -528,12 +552,11 @@ double run(const ora_params* P, T nu, T alpha, int64_t n, State<T>& S, const dou
             for (int64_t i = 0; i < n; ++i) S.x[d][i] = wrap_t(S.x[d][i], P->lo[d], P->hi[d]);
     Rates<T> R;
     Counts c;
-    rhs(P, nu, alpha, n, S, m, role, R, &c);
+    rhs(P, nu, alpha, n, S, m, role, R, &c, 0.0);
     double t = 0.0;
     std::vector<double> rec(HIST);
     diagnostics(P, n, S, R, m, role, t, 0.0, c, rec.data());
     if (hist) std::memcpy(hist, rec.data(), sizeof(double) * HIST);
-    const bool cont = P->density != DENSITY_SUMMATION;
     for (int step = 0; step < nsteps; ++step) {
         double dt = dt_fixed > 0.0 ? dt_fixed : cfl_dt(P, rec[3], rec[7]);
         for (int64_t i = 0; i < n; ++i) {
@@ -544,14 +567,11 @@ double run(const ora_params* P, T nu, T alpha, int64_t n, State<T>& S, const dou
                     S.x[d][i] = P->periodic[d] ? wrap_t(xn, P->lo[d], P->hi[d]) : xn;
                 }
             }
-            if (cont) S.rho[i] = S.rho[i] + 0.5 * dt * R.arho[i];
         }
-        rhs(P, nu, alpha, n, S, m, role, R, &c);
-        for (int64_t i = 0; i < n; ++i) {
+        rhs(P, nu, alpha, n, S, m, role, R, &c, dt);
+        for (int64_t i = 0; i < n; ++i)
             if (role[i] == ROLE_FLUID)
                 for (int d = 0; d < dim; ++d) S.u[d][i] = S.u[d][i] + 0.5 * dt * R.a[d][i];
-            if (cont) S.rho[i] = S.rho[i] + 0.5 * dt * R.arho[i];
-        }
         t += dt;
         diagnostics(P, n, S, R, m, role, t, dt, c, rec.data());
         if (hist) std::memcpy(hist + (size_t)(step + 1) * HIST, rec.data(), sizeof(double) * HIST);
@@ -657,7 +677,7 @@ int ora_rhs(const ora_params* P, int64_t n, const double* x, const double* y, co
     load_state(P, n, xs, us, rho, S);
     Rates<double> R;
     Counts c;
-    rhs<double>(P, P->nu, P->alpha, n, S, m, role, R, &c);
+    rhs<double>(P, P->nu, P->alpha, n, S, m, role, R, &c, 0.0);
     double* outs_a[3] = {ax, ay, az};
     double* outs_x[3] = {xsx, xsy, xsz};
     for (int64_t i = 0; i < n; ++i) {

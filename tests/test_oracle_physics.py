@@ -153,7 +153,9 @@ def test_artificial_viscosity_only_acts_on_approaching_pairs():
 def test_dam_break_first_step_closed_form():
     """At t = 0 (rho = rho0 so p = 0, u = 0) every fluid particle has a = g, arho = 0.
     After the first kick-drift-kick step, particles with no wall neighbour have
-    u = g dt, x = x0 + dt (dt/2 g) and unchanged density."""
+    u = g dt, x = x0 + dt (dt/2 g) and unchanged density. (Wall contact changes the
+    density of fluid within one support of a wall at the first step, whose pressure then
+    reaches one support further: the closed form holds beyond two supports.)"""
     wl = W.dam_break_2d(dx=0.04)
     s = O.state_of(wl)
     fluid = s["role"] == W.FLUID
@@ -161,8 +163,8 @@ def test_dam_break_first_step_closed_form():
     assert np.all(r0["ax"][fluid] == 0.0) and np.all(r0["ay"][fluid] == wl.g[1])
     assert np.all(r0["arho"] == 0.0)
     st, hist = O.run(wl, s, wl.dt, 1)
-    # particles farther than the support from every wall particle
-    kh = 2.0 * wl.h
+    # particles farther than two supports from every wall particle
+    kh = 2.0 * (2.0 * wl.h)
     wx, wy = s["x"][~fluid], s["y"][~fluid]
     far = np.array([np.min((wx - a) ** 2 + (wy - b) ** 2) > (kh + 0.5 * abs(wl.g[1]) * wl.dt ** 2) ** 2
                     for a, b in zip(s["x"], s["y"])]) & fluid
