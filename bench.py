@@ -141,6 +141,7 @@ def gpu_arm(args, rank, world, dist):
     e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     pair_ms, phases = [], {k: 0.0 for k in G.Simulation.PHASES}
+    counts = [0.0, 0.0, 0.0]  # interacting pairs, candidates, wall-destination pairs
     uuid = None
     try:
         uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
@@ -162,6 +163,10 @@ def gpu_arm(args, rank, world, dist):
         pair_ms.append(ph["pairs"])
         for key in phases:
             phases[key] += ph[key]
+        dg = sim.diagnostics()
+        counts[0] += dg[8]
+        counts[1] += dg[9]
+        counts[2] += dg[12]
     sim.synchronize()
     torch.cuda.synchronize()
     if dist:
@@ -170,9 +175,7 @@ def gpu_arm(args, rank, world, dist):
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in zip(e0, e1)]
     total_ms = sum(step_ms)
-    hist = sim.history()
-    pairs = float(hist[-args.steps:, 8].sum())
-    cand = float(hist[-args.steps:, 9].sum())
+    pairs, cand, wall_pairs = counts
     n = sim.n
     if dist:
         t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
@@ -183,14 +186,8 @@ def gpu_arm(args, rank, world, dist):
 
     # ---- roofline of the dominant kernel (pair loop), algorithmic flops / live duration
     fl = pair_flops(wl)
-    off, idx = sim.neighbors()
-    role = np.concatenate([np.full(a.n, a.role) for a in wl.arrays])
-    rows = np.repeat(np.arange(n), np.diff(off))
-    fluid_dest = int(np.sum(role[rows] == 0))
-    wall_dest = int(np.sum((role[rows] == 1) & (role[idx] == 0)))
-    frac_fluid = fluid_dest / max(fluid_dest + wall_dest, 1)
-    flops = (fl["candidate"] * cand + pairs * (frac_fluid * fl["fluid_dest_pair"]
-                                                + (1 - frac_fluid) * fl["wall_dest_pair"]))
+    flops = (fl["candidate"] * cand + (pairs - wall_pairs) * fl["fluid_dest_pair"]
+             + wall_pairs * fl["wall_dest_pair"])
     flops_per_launch = flops / args.steps
     pair_avg_ms = sum(pair_ms) / len(pair_ms)
     achieved = flops_per_launch / (pair_avg_ms / 1e3) / 1e12
@@ -230,17 +227,17 @@ def gpu_arm(args, rank, world, dist):
         sim64.step(sch, wl.dt, args.warmup)
         f0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.fp64_steps)]
         f1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.fp64_steps)]
+        p64 = 0.0
         for k in range(args.fp64_steps):
             with torch.cuda.stream(sim64.stream):
                 flush.zero_()
             f0[k].record(sim64.stream)
             sim64.step_async(sch, wl.dt, 1)
             f1[k].record(sim64.stream)
-        sim64.synchronize()
+            sim64.synchronize()
+            p64 += sim64.diagnostics()[8]
         torch.cuda.synchronize()
         ms64 = sum(a.elapsed_time(b) for a, b in zip(f0, f1))
-        h64 = sim64.history()
-        p64 = float(h64[-args.fp64_steps:, 8].sum())
         v64 = p64 / (ms64 / 1e3)
         fp64 = {"value": world * v64, "unit": UNIT, "steps": args.fp64_steps,
                 "ms_per_step": ms64 / args.fp64_steps,

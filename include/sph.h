@@ -134,7 +134,8 @@ enum {
     SPH_DIAG_CANDIDATES = 9, /* ordered pairs examined in the 3^d cell stencil, j != i */
     SPH_DIAG_STEP = 10,      /* steps taken since creation */
     SPH_DIAG_OUTSIDE = 11,   /* particles clamped into an edge cell at the last build */
-    SPH_DIAG_COUNT = 12
+    SPH_DIAG_WALL_PAIRS = 12,/* of SPH_DIAG_PAIRS, those with a wall destination */
+    SPH_DIAG_COUNT = 13
 };
 
 /* Create a context: copy the arrays to the device (global ids in array order), wrap
@@ -179,8 +180,10 @@ sph_status sph_get_neighbors(sph_ctx* ctx, int64_t* offsets, int32_t* idx, int64
  * "ay", "az", "xsx", "xsy", "xsz"); with summation density "rho" receives the sum. */
 sph_status sph_eval_rhs(sph_ctx* ctx, const sph_scheme* scheme);
 
-/* Advance nsteps predictor-corrector steps (Sec. 2.1, kick-drift-kick, one RHS per step
- * at (x^{n+1}, u^{n+1/2}, rho^{n+1/2}); neighbours rebuilt every step). dt > 0 fixes the
+/* Advance nsteps predictor-corrector steps (Sec. 2.1, kick-drift-kick for u and x; the
+ * density advanced like the positions, rho^{n+1} = rho^n + dt D(x^{n+1}, u^{n+1/2}), then
+ * the momentum evaluated at (x^{n+1}, u^{n+1/2}, rho^{n+1}); neighbours rebuilt every
+ * step). dt > 0 fixes the
  * step; dt <= 0 takes min(0.25 h / (c0 + max|u|), 0.25 sqrt(h / max|a|), 0.125 h^2 / nu)
  * from the previous evaluation. Rates carried between calls are recomputed first when the
  * state was set or the scheme differs. The steps run as replays of a captured CUDA graph.

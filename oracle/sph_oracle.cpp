@@ -327,11 +327,23 @@ double wrap_t<double>(double x, double lo, double hi) { return wrap1(x, lo, hi);
 template <>
 Dual wrap_t<Dual>(Dual x, double lo, double hi) { return Dual(wrap1(x.v, lo, hi), x.d); }
 
-/* EOS, Eq. (eos): p = c0^2 rho0 / gamma * ((rho / rho0)^gamma - 1). */
+/* EOS, Eq. (eos): p = c0^2 rho0 / gamma * ((rho / rho0)^gamma - 1), evaluated as
+ * B expm1(gamma log1p(delta)) with delta = (rho - rho0) / rho0: the same quantity
+ * without the cancellation of (rho/rho0)^gamma - 1 near rho0 (condition ~ 1/delta). */
+inline double tait_ratio(double delta, double gamma) {
+    return std::expm1(gamma * std::log1p(delta));
+}
+inline Dual tait_ratio(Dual delta, double gamma) {
+    double l = std::log1p(delta.v);
+    double e = std::expm1(gamma * l);
+    // d/ddelta expm1(gamma log1p(delta)) = gamma (1 + delta)^(gamma - 1)
+    return Dual(e, gamma * std::exp((gamma - 1.0) * l) * delta.d);
+}
 template <class T>
 T tait(const ora_params* P, T rho) {
     double B = P->c0 * P->c0 * P->rho0 / P->gamma;
-    return B * (pow_(rho / P->rho0, P->gamma) - 1.0);
+    T delta = (rho - P->rho0) / P->rho0;
+    return B * tait_ratio(delta, P->gamma);
 }
 
 struct Counts {

@@ -19,9 +19,9 @@ QUINTIC, WENDLAND_C2 = 0, 1
 PREC_FP64, PREC_FP32 = 0, 1
 FLUID, WALL = 0, 1
 CONTINUITY, SUMMATION = 0, 1
-DIAG_COUNT = 12
+DIAG_COUNT = 13
 DIAG_NAMES = ("t", "dt", "ke", "umax", "px", "py", "pz", "amax", "pairs", "candidates",
-              "step", "outside")
+              "step", "outside", "wall_pairs")
 STATUS = {0: "SPH_OK", 1: "SPH_ERR_INVALID", 2: "SPH_ERR_CUDA", 3: "SPH_ERR_OOM",
           4: "SPH_ERR_NONFINITE", 5: "SPH_ERR_DOMAIN", 6: "SPH_ERR_CAPACITY",
           7: "SPH_ERR_TIMEOUT", 8: "SPH_ERR_STATE"}
@@ -354,6 +354,13 @@ class Simulation:
         self._check(self._L.sph_save_state(self._ctx, buf, C.byref(size)))
         return buf.raw
 
-    def load_state(self, blob: bytes):
+    def load_state(self, blob):
+        """Restore a state from bytes or from a contiguous uint8 numpy array (read in place,
+        so a pinned host array is copied to the device without staging)."""
+        if isinstance(blob, np.ndarray):
+            assert blob.dtype == np.uint8 and blob.flags.c_contiguous
+            self._check(self._L.sph_load_state(self._ctx, C.c_void_p(blob.ctypes.data),
+                                               blob.nbytes))
+            return
         buf = C.create_string_buffer(blob, len(blob))
         self._check(self._L.sph_load_state(self._ctx, buf, len(blob)))

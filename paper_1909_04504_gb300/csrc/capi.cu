@@ -752,8 +752,8 @@ sph_status sph_phase_times(sph_ctx* c, float out[5]) {
 sph_status sph_kernels_per_step(const sph_ctx* ctx, const sph_scheme* scheme, int32_t* count) {
     sph_ctx* c = const_cast<sph_ctx*>(ctx);
     if (!c || !scheme || !count) return fail(c, SPH_ERR_INVALID, "NULL argument");
-    // drift+keys, 3 per radix pass, reorder, cell table, [summation density], pair loop
-    *count = 1 + 3 * c->passes + 1 + 1 + (scheme->density == SPH_DENSITY_SUMMATION ? 1 : 0) + 1;
+    // drift+keys, 3 per radix pass, reorder, cell table, density pass, momentum pass
+    *count = 1 + 3 * c->passes + 1 + 1 + 1 + 1;
     return SPH_OK;
 }
 

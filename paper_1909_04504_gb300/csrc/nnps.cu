@@ -190,8 +190,9 @@ __global__ void k_cell_offsets(const uint32_t* __restrict__ skeys, int n, int nc
 }
 
 // ------------------------------------------------------------------ reorder
-// Gather the state into cell order. kick: predictor half-kick of velocity (fluid) and
-// density (continuity). Rates are carried along only outside a step (carry_rates).
+// Gather the state into cell order. kick: predictor half-kick of the fluid velocity
+// (the density is advanced later, like the positions, by the density pass). Rates are
+// carried along only outside a step (carry_rates).
 // Writes the pair-loop shadow: P = (x, y, z, +-m) with the sign marking walls,
 // Q = (u, v, w, rho), R = p / rho^2 with p from the Tait EOS (Eq. eos) in FP64.
 template <class Real>
@@ -213,8 +214,7 @@ __global__ void k_reorder(ParticleSet in, ParticleSet out, const uint32_t* __res
             out.x[d][k] = x[d];
             out.u[d][k] = u[d];
         }
-        double rho = in.rho[o];
-        if (kick && C.continuity) rho += 0.5 * dt * in.arho[o];
+        const double rho = in.rho[o];
         const double m = in.m[o];
         out.rho[k] = rho;
         out.m[k] = m;
@@ -226,15 +226,7 @@ __global__ void k_reorder(ParticleSet in, ParticleSet out, const uint32_t* __res
                 out.xs[d][k] = in.xs[d][o];
             }
         }
-        double r = rho * C.inv_rho0;
-        double rg;
-        if (C.gamma7) {
-            double r2 = r * r;
-            rg = r2 * r2 * r2 * r;
-        } else {
-            rg = pow(r, C.gamma);
-        }
-        const double p = C.B * (rg - 1.0);
+        const double p = tait_pressure(rho, C);
         typename V4<Real>::T pv, qv;
         pv.x = (Real)x[0]; pv.y = (Real)x[1]; pv.z = (Real)x[2];
         pv.w = (Real)(fluid ? m : -m);

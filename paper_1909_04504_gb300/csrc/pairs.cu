@@ -54,73 +54,53 @@ __device__ __forceinline__ void cell_of_key(const Grid& G, uint32_t key, int& cx
     cz = (int)(r / (uint32_t)G.nc[1]);
 }
 
-// ------------------------------------------------------ summation density
+// Block sum of up to 3 counters into partials[blockIdx.x * PARTIAL_STRIDE + first + k]
+// (fixed tree order).
+__device__ __forceinline__ void block_counts(double c0, double c1, double c2, double* partials,
+                                             int first) {
+    __shared__ double red[PAIR_THREADS / 32][3];
+    double v[3] = {c0, c1, c2};
+    for (int o = 16; o > 0; o >>= 1)
+        for (int k = 0; k < 3; ++k) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+        for (int k = 0; k < 3; ++k) red[warp][k] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int k = 0; k < 3; ++k) {
+            double t = red[0][k];
+            for (int w = 1; w < PAIR_THREADS / 32; ++w) t += red[w][k];
+            partials[(size_t)blockIdx.x * PARTIAL_STRIDE + first + k] = t;
+        }
+}
+
+// ---------------------------------------------------------------- density pass
+// First group of an evaluation (Sec. 3.2): the density of every particle, then the EOS.
+//  summation (Eq. 2): rho_i = sum_j m_j W_ij, self term included;
+//  continuity (Eq. continuity:sph): arho_i = sum_j m_j v_ij . grad_i W_ij (walls take
+//    fluid sources only) and, inside a step, rho_i += dt arho_i, advancing the density
+//    like the positions with the half-step velocities (Sec. 2.1 reading).
+// Then p = B ((rho/rho0)^gamma - 1) in FP64 and the shadow rho, p / rho^2. Counts the
+// interacting pairs (i != j inside the support, not both walls) and the candidates.
 template <class Real, int DIM, int KERNEL>
 __global__ void __launch_bounds__(PAIR_THREADS)
 k_density(const typename V4<Real>::T* __restrict__ P, typename V4<Real>::T* __restrict__ Q,
           Real* __restrict__ R, const uint32_t* __restrict__ skeys, const uint32_t* __restrict__ off,
-          int n, Grid G, PairConst<Real> K, StepConst C, ParticleSet S, const Control* ctl) {
+          int n, Grid G, PairConst<Real> K, StepConst C, ParticleSet S, const Control* ctl,
+          int kick, double* __restrict__ partials) {
     if (ctl->status) return;
+    const double dt = ctl->dt;
+    const bool summation = !(K.flags & F_CONTINUITY);
+    double c_pairs = 0, c_cand = 0, c_wall = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const typename V4<Real>::T pi = P[i];
+        const typename V4<Real>::T qi = Q[i];
+        const bool fluid_i = pi.w > Real(0);
         int cx, cy, cz;
         cell_of_key(G, skeys[i], cx, cy, cz);
         Acc<Real> sum;
         sum.zero();
-        sum.add(fabs(pi.w) * K.wfac * kernel_w<Real, KERNEL>(Real(0)));
-        for_each_run<DIM>(G, off, cx, cy, cz, [&](uint32_t jb, uint32_t je) {
-            for (uint32_t j = jb; j < je; ++j) {
-                if ((int)j == i) continue;
-                const typename V4<Real>::T pj = P[j];
-                Real dx = min_image(rn_sub(pi.x, pj.x), G.periodic[0], K.L[0], K.halfL[0]);
-                Real dy = min_image(rn_sub(pi.y, pj.y), G.periodic[1], K.L[1], K.halfL[1]);
-                Real dz = DIM == 3 ? min_image(rn_sub(pi.z, pj.z), G.periodic[2], K.L[2], K.halfL[2]) : Real(0);
-                Real r2 = dist2<Real, DIM>(dx, dy, dz);
-                if (!(r2 < K.kh2)) continue;
-                Real q = sqrt(r2) * K.inv_h;
-                sum.add(fabs(pj.w) * K.wfac * kernel_w<Real, KERNEL>(q));
-            }
-        });
-        const double rho = sum.value();
-        S.rho[i] = rho;
-        double r = rho * C.inv_rho0;
-        double rg;
-        if (C.gamma7) {
-            double r2 = r * r;
-            rg = r2 * r2 * r2 * r;
-        } else {
-            rg = pow(r, C.gamma);
-        }
-        const double p = C.B * (rg - 1.0);
-        typename V4<Real>::T qi = Q[i];
-        qi.w = (Real)rho;
-        Q[i] = qi;
-        R[i] = (Real)(p / (rho * rho));
-    }
-}
-
-// ------------------------------------------------------------ fused pair loop
-template <class Real, int DIM, int KERNEL>
-__global__ void __launch_bounds__(PAIR_THREADS)
-k_pairs(const typename V4<Real>::T* __restrict__ P, const typename V4<Real>::T* __restrict__ Q,
-        const Real* __restrict__ R, const uint32_t* __restrict__ skeys,
-        const uint32_t* __restrict__ off, int n, Grid G, PairConst<Real> K, StepConst C,
-        ParticleSet S, Control* ctl, int kick, double* __restrict__ partials,
-        double* __restrict__ history) {
-    if (ctl->status) return;
-    const double dt = ctl->dt;
-    const int flags = K.flags;
-    double d_px = 0, d_py = 0, d_pz = 0, d_ke = 0, d_u2 = 0, d_a2 = 0, d_pairs = 0, d_cand = 0;
-    int bad = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const typename V4<Real>::T pi = P[i];
-        const typename V4<Real>::T qi = Q[i];
-        const Real pri = R[i];
-        const bool fluid_i = pi.w > Real(0);
-        int cx, cy, cz;
-        cell_of_key(G, skeys[i], cx, cy, cz);
-        Acc<Real> arho, ax, ay, az, sx, sy, sz;
-        arho.zero(); ax.zero(); ay.zero(); az.zero(); sx.zero(); sy.zero(); sz.zero();
+        if (summation) sum.add(fabs(pi.w) * K.wfac * kernel_w<Real, KERNEL>(Real(0)));
         uint32_t npairs = 0, ncand = 0;
         for_each_run<DIM>(G, off, cx, cy, cz, [&](uint32_t jb, uint32_t je) {
             for (uint32_t j = jb; j < je; ++j) {
@@ -132,22 +112,100 @@ k_pairs(const typename V4<Real>::T* __restrict__ P, const typename V4<Real>::T* 
                 Real dz = DIM == 3 ? min_image(rn_sub(pi.z, pj.z), G.periodic[2], K.L[2], K.halfL[2]) : Real(0);
                 Real r2 = dist2<Real, DIM>(dx, dy, dz);
                 if (!(r2 < K.kh2)) continue;
+                const bool interacting = fluid_i || pj.w > Real(0);
+                npairs += interacting;
+                const Real q = sqrt(r2) * K.inv_h;
+                if (summation) {
+                    sum.add(fabs(pj.w) * K.wfac * kernel_w<Real, KERNEL>(q));
+                } else if (interacting) {
+                    const typename V4<Real>::T qj = Q[j];
+                    const Real Gk = K.gfac * kernel_f<Real, KERNEL>(q);
+                    const Real vdotr = (qi.x - qj.x) * dx + (qi.y - qj.y) * dy +
+                                       (DIM == 3 ? (qi.z - qj.z) * dz : Real(0));
+                    sum.add(fabs(pj.w) * Gk * vdotr);
+                }
+            }
+        });
+        double rho;
+        if (summation) {
+            rho = sum.value();
+            S.arho[i] = 0.0;
+        } else {
+            const double ar = sum.value();
+            S.arho[i] = ar;
+            rho = S.rho[i];
+            if (kick) rho += dt * ar;
+        }
+        S.rho[i] = rho;
+        const double p = tait_pressure(rho, C);
+        reinterpret_cast<Real*>(&Q[i])[3] = (Real)rho;
+        R[i] = (Real)(p / (rho * rho));
+        c_pairs += (double)npairs;
+        c_cand += (double)ncand;
+        if (!fluid_i) c_wall += (double)npairs;
+    }
+    block_counts(c_pairs, c_cand, c_wall, partials, 10);
+}
+
+// ------------------------------------------------------------ momentum pass
+// Second group of an evaluation: for every fluid destination, pressure Eq.
+// (mom:sph:press), laminar viscosity Eq. (mom:sph:visc), Monaghan artificial viscosity,
+// XSPH over fluid sources, the body force of Eq. (mom:sph); then, inside a step, the
+// corrector half-kick u^{n+1} = u^{n+1/2} + dt/2 a^{n+1} (Sec. 2.1) and the FP64
+// diagnostics. The last block to finish reduces the block partials in a fixed order
+// (deterministic), writes the record, the next dt and the non-finite status.
+template <class Real, int DIM, int KERNEL>
+__global__ void __launch_bounds__(PAIR_THREADS)
+k_pairs(const typename V4<Real>::T* __restrict__ P, const typename V4<Real>::T* __restrict__ Q,
+        const Real* __restrict__ R, const uint32_t* __restrict__ skeys,
+        const uint32_t* __restrict__ off, int n, Grid G, PairConst<Real> K, StepConst C,
+        ParticleSet S, Control* ctl, int kick, double* __restrict__ partials,
+        double* __restrict__ history) {
+    if (ctl->status) return;
+    const double dt = ctl->dt;
+    const int flags = K.flags;
+    double d_px = 0, d_py = 0, d_pz = 0, d_ke = 0, d_u2 = 0, d_a2 = 0;
+    int bad = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const typename V4<Real>::T pi = P[i];
+        const bool fluid_i = pi.w > Real(0);
+        if (!fluid_i) {  // walls: no momentum equation, static
+            for (int d = 0; d < DIM; ++d) {
+                S.a[d][i] = 0.0;
+                S.xs[d][i] = 0.0;
+            }
+            if (!isfinite(S.rho[i])) bad = 1;
+            continue;
+        }
+        const typename V4<Real>::T qi = Q[i];
+        const Real pri = R[i];
+        int cx, cy, cz;
+        cell_of_key(G, skeys[i], cx, cy, cz);
+        Acc<Real> ax, ay, az, sx, sy, sz;
+        ax.zero(); ay.zero(); az.zero(); sx.zero(); sy.zero(); sz.zero();
+        for_each_run<DIM>(G, off, cx, cy, cz, [&](uint32_t jb, uint32_t je) {
+            for (uint32_t j = jb; j < je; ++j) {
+                if ((int)j == i) continue;
+                const typename V4<Real>::T pj = P[j];
+                Real dx = min_image(rn_sub(pi.x, pj.x), G.periodic[0], K.L[0], K.halfL[0]);
+                Real dy = min_image(rn_sub(pi.y, pj.y), G.periodic[1], K.L[1], K.halfL[1]);
+                Real dz = DIM == 3 ? min_image(rn_sub(pi.z, pj.z), G.periodic[2], K.L[2], K.halfL[2]) : Real(0);
+                Real r2 = dist2<Real, DIM>(dx, dy, dz);
+                if (!(r2 < K.kh2)) continue;
                 const bool fluid_j = pj.w > Real(0);
-                if (!fluid_i && !fluid_j) continue;  // wall-wall pairs carry no equation
-                ++npairs;
                 const typename V4<Real>::T qj = Q[j];
                 const Real mj = fabs(pj.w);
                 const Real q = sqrt(r2) * K.inv_h;
                 const Real Gk = K.gfac * kernel_f<Real, KERNEL>(q);  // grad_i W = Gk (x_i - x_j)
                 const Real vx = qi.x - qj.x, vy = qi.y - qj.y, vz = DIM == 3 ? qi.z - qj.z : Real(0);
-                const Real vdotr = vx * dx + vy * dy + (DIM == 3 ? vz * dz : Real(0));
-                if (flags & F_CONTINUITY) arho.add(mj * Gk * vdotr);
-                if (!fluid_i) continue;
                 Real coef = pri + R[j];
                 const Real rhobar = Real(0.5) * (qi.w + qj.w);
-                if ((flags & F_AV) && vdotr < Real(0)) {
-                    const Real mu = K.h * vdotr / (r2 + K.av_h2);
-                    coef -= K.alpha_c0 * mu / rhobar;
+                if (flags & F_AV) {
+                    const Real vdotr = vx * dx + vy * dy + (DIM == 3 ? vz * dz : Real(0));
+                    if (vdotr < Real(0)) {
+                        const Real mu = K.h * vdotr / (r2 + K.av_h2);
+                        coef -= K.alpha_c0 * mu / rhobar;
+                    }
                 }
                 const Real cg = -mj * coef * Gk;
                 Real cv = Real(0);
@@ -166,69 +224,58 @@ k_pairs(const typename V4<Real>::T* __restrict__ P, const typename V4<Real>::T* 
         // epilogue: FP64 rates, corrector half-kick, diagnostics
         double a[3] = {ax.value(), ay.value(), az.value()};
         double xs[3] = {sx.value(), sy.value(), sz.value()};
-        const double ar = arho.value();
-        if (fluid_i)
-            for (int d = 0; d < DIM; ++d) a[d] += C.g[d];
-        S.arho[i] = ar;
+        for (int d = 0; d < DIM; ++d) a[d] += C.g[d];
+        double u[3] = {0, 0, 0};
+        double u2 = 0, a2 = 0;
         for (int d = 0; d < DIM; ++d) {
             S.a[d][i] = a[d];
             S.xs[d][i] = xs[d];
-        }
-        double u[3] = {0, 0, 0};
-        for (int d = 0; d < DIM; ++d) {
             u[d] = S.u[d][i];
-            if (kick && fluid_i) {
+            if (kick) {
                 u[d] += 0.5 * dt * a[d];
                 S.u[d][i] = u[d];
             }
+            u2 += u[d] * u[d];
+            a2 += a[d] * a[d];
+            if (!isfinite(u[d]) || !isfinite(S.x[d][i])) bad = 1;
         }
-        double rho = S.rho[i];
-        if (kick && C.continuity) {
-            rho += 0.5 * dt * ar;
-            S.rho[i] = rho;
-        }
-        if (!isfinite(rho) || !isfinite(ar)) bad = 1;
-        if (fluid_i) {
-            const double m = S.m[i];
-            double u2 = 0, a2 = 0;
-            for (int d = 0; d < DIM; ++d) {
-                u2 += u[d] * u[d];
-                a2 += a[d] * a[d];
-                if (!isfinite(u[d]) || !isfinite(S.x[d][i])) bad = 1;
-            }
-            d_px += m * u[0];
-            d_py += m * u[1];
-            d_pz += m * u[2];
-            d_ke += 0.5 * m * u2;
-            d_u2 = fmax(d_u2, u2);
-            d_a2 = fmax(d_a2, a2);
-            if (!isfinite(a2)) bad = 1;
-        }
-        d_pairs += (double)npairs;
-        d_cand += (double)ncand;
+        if (!isfinite(S.rho[i]) || !isfinite(a2)) bad = 1;
+        const double m = S.m[i];
+        d_px += m * u[0];
+        d_py += m * u[1];
+        d_pz += m * u[2];
+        d_ke += 0.5 * m * u2;
+        d_u2 = fmax(d_u2, u2);
+        d_a2 = fmax(d_a2, a2);
     }
 
     // ---- block reduction (fixed tree order: deterministic)
-    __shared__ double red[PAIR_THREADS / 32][10];
+    constexpr int NV = 7;  // px py pz ke u2max a2max bad
+    __shared__ double red[PAIR_THREADS / 32][NV];
     __shared__ bool is_last;
-    double v[10] = {d_px, d_py, d_pz, d_ke, d_u2, d_a2, d_pairs, d_cand, (double)bad, 0.0};
+    double v[NV] = {d_px, d_py, d_pz, d_ke, d_u2, d_a2, (double)bad};
+    auto is_max = [](int k) { return k >= 4; };
+#pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        for (int k = 0; k < 9; ++k) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
             double y = __shfl_down_sync(0xffffffffu, v[k], o);
-            v[k] = (k == 4 || k == 5 || k == 8) ? fmax(v[k], y) : v[k] + y;
+            v[k] = is_max(k) ? fmax(v[k], y) : v[k] + y;
         }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0)
-        for (int k = 0; k < 9; ++k) red[warp][k] = v[k];
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) red[warp][k] = v[k];
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double out[9];
-        for (int k = 0; k < 9; ++k) out[k] = red[0][k];
-        for (int w = 1; w < PAIR_THREADS / 32; ++w)
-            for (int k = 0; k < 9; ++k)
-                out[k] = (k == 4 || k == 5 || k == 8) ? fmax(out[k], red[w][k]) : out[k] + red[w][k];
-        for (int k = 0; k < 9; ++k) partials[(size_t)blockIdx.x * PARTIAL_STRIDE + k] = out[k];
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double t = red[0][k];
+            for (int w = 1; w < PAIR_THREADS / 32; ++w) t = is_max(k) ? fmax(t, red[w][k]) : t + red[w][k];
+            partials[(size_t)blockIdx.x * PARTIAL_STRIDE + k] = t;
+        }
         __threadfence();
         unsigned t = atomicAdd(&ctl->ticket, 1u);
         is_last = (t == gridDim.x - 1);
@@ -236,31 +283,41 @@ k_pairs(const typename V4<Real>::T* __restrict__ P, const typename V4<Real>::T* 
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    // ---- last block: reduce the partials in a fixed order and finalise
-    for (int k = 0; k < 9; ++k) v[k] = 0.0;
+    // ---- last block: reduce the partials (this pass: 0..6, density pass: 10..12)
+    constexpr int NT = 10;
+    double w[NT];
+#pragma unroll
+    for (int k = 0; k < NT; ++k) w[k] = 0.0;
     for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
         const volatile double* p = partials + (size_t)b * PARTIAL_STRIDE;
-        for (int k = 0; k < 9; ++k) {
-            double y = p[k];
-            v[k] = (k == 4 || k == 5 || k == 8) ? fmax(v[k], y) : v[k] + y;
-        }
+#pragma unroll
+        for (int k = 0; k < NV; ++k) w[k] = is_max(k) ? fmax(w[k], p[k]) : w[k] + p[k];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) w[NV + k] += p[10 + k];
     }
+#pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        for (int k = 0; k < 9; ++k) {
-            double y = __shfl_down_sync(0xffffffffu, v[k], o);
-            v[k] = (k == 4 || k == 5 || k == 8) ? fmax(v[k], y) : v[k] + y;
+#pragma unroll
+        for (int k = 0; k < NT; ++k) {
+            double y = __shfl_down_sync(0xffffffffu, w[k], o);
+            w[k] = (k >= 4 && k < NV) ? fmax(w[k], y) : w[k] + y;
         }
     }
-    __syncthreads();
-    if (lane == 0)
-        for (int k = 0; k < 9; ++k) red[warp][k] = v[k];
+    __shared__ double red2[PAIR_THREADS / 32][NT];
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < NT; ++k) red2[warp][k] = w[k];
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double out[9];
-        for (int k = 0; k < 9; ++k) out[k] = red[0][k];
-        for (int w = 1; w < PAIR_THREADS / 32; ++w)
-            for (int k = 0; k < 9; ++k)
-                out[k] = (k == 4 || k == 5 || k == 8) ? fmax(out[k], red[w][k]) : out[k] + red[w][k];
+        double out[NT];
+#pragma unroll
+        for (int k = 0; k < NT; ++k) {
+            double t = red2[0][k];
+            for (int ww = 1; ww < PAIR_THREADS / 32; ++ww)
+                t = (k >= 4 && k < NV) ? fmax(t, red2[ww][k]) : t + red2[ww][k];
+            out[k] = t;
+        }
         ctl->ticket = 0;
         double* rec = ctl->rec;
         if (kick) {
@@ -275,11 +332,12 @@ k_pairs(const typename V4<Real>::T* __restrict__ P, const typename V4<Real>::T* 
         rec[5] = out[1];
         rec[6] = out[2];
         rec[7] = sqrt(out[5]);
-        rec[8] = out[6];
-        rec[9] = out[7];
+        rec[8] = out[7];
+        rec[9] = out[8];
         rec[10] = (double)ctl->step;
         rec[11] = (double)ctl->outside;
-        if (out[8] != 0.0) ctl->status |= ST_NONFINITE;
+        rec[12] = out[9];
+        if (out[6] != 0.0) ctl->status |= ST_NONFINITE;
         double dt_next = C.dt_fixed;
         if (!(dt_next > 0.0)) {
             dt_next = 0.25 * C.h / (C.c0 + rec[3]);
@@ -300,9 +358,9 @@ k_pairs(const typename V4<Real>::T* __restrict__ P, const typename V4<Real>::T* 
 template <class Real, int DIM, int KERNEL>
 static void pairs_t(const PairLaunch& L, const PairConst<Real>& K, cudaStream_t st) {
     using V = typename V4<Real>::T;
-    if (L.summation)
-        k_density<Real, DIM, KERNEL><<<L.grid, PAIR_THREADS, 0, st>>>(
-            (const V*)L.P, (V*)L.Q, (Real*)L.R, L.skeys, L.off, L.n, L.G, K, L.C, L.S, L.ctl);
+    k_density<Real, DIM, KERNEL><<<L.grid, PAIR_THREADS, 0, st>>>(
+        (const V*)L.P, (V*)L.Q, (Real*)L.R, L.skeys, L.off, L.n, L.G, K, L.C, L.S, L.ctl, L.kick,
+        L.partials);
     k_pairs<Real, DIM, KERNEL><<<L.grid, PAIR_THREADS, 0, st>>>(
         (const V*)L.P, (const V*)L.Q, (const Real*)L.R, L.skeys, L.off, L.n, L.G, K, L.C, L.S,
         L.ctl, L.kick, L.partials, L.history);

@@ -23,7 +23,7 @@ constexpr int F_LAMINAR = 2;      // Eq. mom:sph:visc
 constexpr int F_AV = 4;           // Monaghan artificial viscosity
 constexpr int F_XSPH = 8;         // XSPH correction
 
-constexpr int DIAG_N = 12;
+constexpr int DIAG_N = 13;
 constexpr int HIST_CAP = 65536;
 
 // 16- and 32-byte vectors: one vector load per particle record.
@@ -182,6 +182,21 @@ __device__ __forceinline__ Real kernel_w(Real q) {
         Real t2 = t * t;
         return t2 * t2 * (Real(2) * q + Real(1));
     }
+}
+
+// Tait EOS (Eq. eos) in FP64: p = B ((rho/rho0)^gamma - 1), evaluated through
+// delta = (rho - rho0) / rho0 without the cancellation of the difference near rho0:
+// for gamma = 7 the exact binomial polynomial delta (7 + 21 delta + 35 delta^2 + ...),
+// otherwise expm1(gamma log1p(delta)).
+__device__ __forceinline__ double tait_pressure(double rho, const StepConst& C) {
+    const double d = (rho - C.rho0) * C.inv_rho0;
+    double e;
+    if (C.gamma7) {
+        e = d * (7.0 + d * (21.0 + d * (35.0 + d * (35.0 + d * (21.0 + d * (7.0 + d))))));
+    } else {
+        e = expm1(C.gamma * log1p(d));
+    }
+    return C.B * e;
 }
 
 // --------------------------------------------------------- compensated sums
