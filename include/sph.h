@@ -232,6 +232,47 @@ sph_status sph_history(sph_ctx* ctx, double* out, int32_t max_records, int32_t* 
 sph_status sph_save_state(sph_ctx* ctx, void* buf, size_t* bytes);
 sph_status sph_load_state(sph_ctx* ctx, const void* buf, size_t bytes);
 
+/* ---------------------------------------------------------------------------------
+ * Allocation-free cell sort. The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory -- for example code that runs inside a
+ * host framework whose memory pool has already reserved the device (any cudaMalloc
+ * beyond that budget fails or is forbidden), or a latency-critical loop where
+ * cudaMalloc's implicit device-wide synchronisation is not acceptable. It performs the
+ * neighbour-build sort of sph_build_neighbors on caller-owned device buffers and calls
+ * no cudaMalloc, cudaFree or other allocating routine.
+ *
+ * Scratch: one fixed device array of about 12.8 MB inside the library (keys, values and
+ * histograms for up to SPH_NOALLOC_MAX_PARTICLES particles). Every GPU that loads the
+ * library holds it until the process exits. All calls share it and it keeps the last
+ * call's contents: calls whose work overlaps on the GPU (for example on two streams, or
+ * from two threads) race on it and must be serialised by the caller.
+ *
+ * Set-up: the first call on each device looks up that device's address of the array
+ * (cudaGetSymbolAddress, with the device current); make that first call before any
+ * stream capture on the device.
+ *
+ *  domain        grid and binning as in sph_create (dim, kernel, precision, periodic, h,
+ *                lo, hi); the cell count follows the same rule.
+ *  x, y, z       device pointers to n FP64 positions (z NULL in 2D). Positions on a
+ *                periodic axis must already lie in [lo, hi); positions outside the box
+ *                are clamped into the edge cells.
+ *  n             particle count, 0 <= n <= SPH_NOALLOC_MAX_PARTICLES; larger n returns
+ *                SPH_ERR_CAPACITY before any device work.
+ *  order         device, n entries (out): input index at each sorted position; a stable
+ *                sort by linear cell id, so ties keep the input order.
+ *  cell_offsets  device, offsets_capacity entries (out): offsets[c] = number of particles
+ *                in cells < c, ncells + 1 entries. NULL: only *ncells_out is set.
+ *  ncells_out    host (out): number of cells.
+ *  stream        cudaStream_t the work is enqueued on (NULL: legacy default stream); the
+ *                call returns without waiting for it.
+ * Errors: SPH_ERR_INVALID (bad domain or NULL buffer), SPH_ERR_CAPACITY (n too large or
+ * offsets_capacity < ncells + 1), SPH_ERR_CUDA; the message is in sph_last_error(NULL). */
+#define SPH_NOALLOC_MAX_PARTICLES 1048576
+sph_status sph_cell_sort_noalloc(const sph_domain* domain, const double* x, const double* y,
+                                 const double* z, int64_t n, uint32_t* order,
+                                 uint32_t* cell_offsets, int64_t offsets_capacity,
+                                 int64_t* ncells_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -382,6 +382,10 @@ sph_status ensure_neighbors(sph_ctx* c) {
 
 }  // namespace
 
+namespace sph {
+void set_global_error(const std::string& msg) { g_create_error = msg; }
+}  // namespace sph
+
 extern "C" {
 
 sph_status sph_create(const sph_domain* domain, const sph_array_desc* arrays, int32_t n_arrays,

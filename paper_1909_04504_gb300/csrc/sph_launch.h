@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "sph_device.cuh"
 
 namespace sph {
@@ -33,6 +35,9 @@ void launch_export_neighbors(int precision, int dim, const void* P, const uint32
                              const PairConst<float>& Kf, const PairConst<double>& Kd, int pass,
                              uint32_t* counts, const int64_t* row_off, int32_t* idx,
                              cudaStream_t st, int sms);
+
+// capi.cu: sets the message sph_last_error(NULL) returns on this thread
+void set_global_error(const std::string& msg);
 
 // pairs.cu
 struct PairLaunch {
