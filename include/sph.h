@@ -206,6 +206,20 @@ sph_status sph_synchronize(sph_ctx* ctx);
 sph_status sph_set_timing(sph_ctx* ctx, int32_t enable);
 sph_status sph_phase_times(sph_ctx* ctx, float out[5]);
 
+/* Tile shape of the momentum pass: lanes per destination particle (1, 2, 4 or 8) that
+ * share its neighbour list (the density pass always gives one thread per destination).
+ * More lanes hide latency on small problems. Changing it changes the summation order
+ * (results stay within rounding of each other) and forces a new graph capture. */
+sph_status sph_set_groups(sph_ctx* ctx, int32_t momentum_lanes);
+
+/* Autotuner: times the momentum pass for every tile shape on the current state (the
+ * evaluations act like sph_eval_rhs), keeps the fastest, caches the choice for this
+ * (precision, dim, kernel, log2 n) for contexts created later in the process, and returns
+ * it in *chosen (may be NULL). Contexts start from a cached choice, else 4 lanes below
+ * 200,000 particles and 1 above. Timing-dependent: call it explicitly, not inside a run
+ * whose bitwise reproducibility matters. */
+sph_status sph_autotune(sph_ctx* ctx, const sph_scheme* scheme, int32_t* chosen);
+
 /* Kernel launches one step issues (for launch accounting). */
 sph_status sph_kernels_per_step(const sph_ctx* ctx, const sph_scheme* scheme, int32_t* count);
 

@@ -58,7 +58,7 @@ _lib = None
 EXPORTS = ("sph_create", "sph_destroy", "sph_last_error", "sph_count", "sph_grid",
            "sph_build_neighbors", "sph_get_cells", "sph_get_neighbors", "sph_eval_rhs",
            "sph_step", "sph_step_async", "sph_synchronize", "sph_set_timing", "sph_phase_times",
-           "sph_kernels_per_step", "sph_get", "sph_set", "sph_diagnostics", "sph_history",
+           "sph_kernels_per_step", "sph_set_groups", "sph_autotune", "sph_get", "sph_set", "sph_diagnostics", "sph_history",
            "sph_save_state", "sph_load_state")
 
 
@@ -98,6 +98,8 @@ def load(build_if_missing: bool = True):
     L.sph_set_timing.argtypes = [ctxp, C.c_int32]
     L.sph_phase_times.argtypes = [ctxp, C.POINTER(C.c_float)]
     L.sph_kernels_per_step.argtypes = [ctxp, C.POINTER(Scheme), i32]
+    L.sph_set_groups.argtypes = [ctxp, C.c_int32]
+    L.sph_autotune.argtypes = [ctxp, C.POINTER(Scheme), i32]
     L.sph_get.argtypes = [ctxp, C.c_int32, C.c_char_p, d]
     L.sph_set.argtypes = [ctxp, C.c_int32, C.c_char_p, d]
     L.sph_diagnostics.argtypes = [ctxp, d]
@@ -318,6 +320,14 @@ class Simulation:
         n = C.c_int32()
         self._check(self._L.sph_kernels_per_step(self._ctx, C.byref(scheme), C.byref(n)))
         return n.value
+
+    def set_groups(self, momentum_lanes: int):
+        self._check(self._L.sph_set_groups(self._ctx, int(momentum_lanes)))
+
+    def autotune(self, scheme: Scheme) -> int:
+        out = C.c_int32()
+        self._check(self._L.sph_autotune(self._ctx, C.byref(scheme), C.byref(out)))
+        return int(out.value)
 
     def get(self, prop: str, array: int = -1) -> np.ndarray:
         out = np.zeros(self.count(array))

@@ -6,8 +6,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "sph.h"
@@ -64,11 +66,18 @@ struct sph_ctx {
     uint32_t* skeys = nullptr;
     uint32_t* off = nullptr;
     uint32_t* hist = nullptr;
-    double* partials = nullptr;
+    double* pm = nullptr;  // momentum-pass block partials (8 doubles per block)
+    double* pd = nullptr;  // density-pass block partials (4 doubles per block)
     Control* ctl = nullptr;
     double* history = nullptr;
     void* io = nullptr;  // scratch for get/set/exports: 4 N + 2 (8 N + 8) bytes, 256-aligned parts
-    int pair_grid = 1;
+    int grid_cap = 1;                 // largest pair-pass grid (sizes pm, pd)
+    int bps[2][4] = {{1, 1, 1, 1}, {1, 1, 1, 1}};  // blocks per SM: [pass][T = 1, 2, 4, 8]
+    int group_d = 1, group_m = 1;     // lanes per destination (density pass: always 1)
+    int grid_d = 1, grid_m = 1;
+    uint32_t* nl = nullptr;           // neighbour list nl[k * N + i], separately allocated
+    uint32_t* cnt = nullptr;          // list length per particle (arena)
+    int maxn = 0;                     // list capacity per particle
 
     bool have_rates = false;
     bool nbr_valid = false;
@@ -220,6 +229,55 @@ bool same_scheme(const sph_scheme& a, const sph_scheme& b) { return std::memcmp(
 
 // Neighbour build: [drift] + keys, radix sort, gather into the other set (+EOS shadow),
 // cell table. Enqueued on the context stream (capturable).
+int tindex(int T) { return T == 1 ? 0 : (T == 2 ? 1 : (T == 4 ? 2 : 3)); }
+
+// Grid of a pair pass: one group of T lanes per particle, capped at what fits on the GPU.
+int pass_grid(const sph_ctx* c, int pass, int T) {
+    long long want = ((long long)c->N * T + pair_threads() - 1) / pair_threads();
+    long long cap = (long long)c->sms * c->bps[pass][tindex(T)];
+    long long g = want < cap ? want : cap;
+    return g < 1 ? 1 : (int)g;
+}
+
+void set_groups(sph_ctx* c, int td, int tm) {
+    c->group_d = td;
+    c->group_m = tm;
+    c->grid_d = pass_grid(c, 0, td);
+    c->grid_m = pass_grid(c, 1, tm);
+}
+
+// Process-wide autotuner cache: (precision, dim, kernel, log2 N) -> group sizes.
+struct TuneKey {
+    int precision, dim, kernel, nbucket;
+    bool operator==(const TuneKey& o) const {
+        return precision == o.precision && dim == o.dim && kernel == o.kernel && nbucket == o.nbucket;
+    }
+};
+std::mutex g_tune_lock;
+std::vector<std::pair<TuneKey, std::pair<int, int>>> g_tune_cache;
+
+TuneKey tune_key(const sph_ctx* c) {
+    int b = 0;
+    while ((1ll << (b + 1)) <= (long long)c->N) ++b;
+    return TuneKey{c->dom.precision, c->dom.dim, c->dom.kernel, b};
+}
+
+// Momentum-pass lanes per destination before any tuning: a cached tuning result for
+// this shape, else 4 for small problems (more threads to hide latency) and 1 otherwise.
+void default_groups(const sph_ctx* c, int* td, int* tm) {
+    *td = 1;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_lock);
+        const TuneKey k = tune_key(c);
+        for (auto& e : g_tune_cache)
+            if (e.first == k) {
+                *tm = e.second.second;
+                return;
+            }
+    }
+    *tm = c->N < 200000 ? 4 : 1;
+}
+
 void mark(sph_ctx* c, int k, bool timed) {
     if (timed) cudaEventRecordWithFlags(c->ev[k], c->stream, cudaEventRecordExternal);
 }
@@ -248,10 +306,12 @@ void enqueue_eval(sph_ctx* c, const sph_scheme* s, const StepConst& C, int kick)
     L.precision = c->dom.precision;
     L.dim = c->dom.dim;
     L.kernel = c->dom.kernel;
-    L.summation = s->density == SPH_DENSITY_SUMMATION;
     L.kick = kick;
     L.n = c->N;
-    L.grid = c->pair_grid;
+    L.group_d = c->group_d;
+    L.group_m = c->group_m;
+    L.grid_d = c->grid_d;
+    L.grid_m = c->grid_m;
     L.P = c->P;
     L.Q = c->Q;
     L.R = c->R;
@@ -261,7 +321,11 @@ void enqueue_eval(sph_ctx* c, const sph_scheme* s, const StepConst& C, int kick)
     L.C = C;
     L.S = c->set[c->cur];
     L.ctl = c->ctl;
-    L.partials = c->partials;
+    L.nl = c->nl;
+    L.cnt = c->cnt;
+    L.maxn = c->maxn;
+    L.pm = c->pm;
+    L.pd = c->pd;
     L.history = c->history;
     launch_pairs(L, pair_const<float>(c, s), pair_const<double>(c, s), c->stream);
 }
@@ -273,18 +337,10 @@ sph_status sync_status(sph_ctx* c) {
     CK(cudaGetLastError());
     if (status & ST_NONFINITE) return fail(c, SPH_ERR_NONFINITE, "non-finite state detected");
     if (status & ST_TIMEOUT) return fail(c, SPH_ERR_TIMEOUT, "device wait timed out");
-    return SPH_OK;
-}
-
-// Initial right-hand side at the current state (no drift, no kick).
-sph_status initial_eval(sph_ctx* c, const sph_scheme* s, double dt_fixed) {
-    StepConst C = step_const(c, s, dt_fixed);
-    enqueue_build(c, C, 0, 0, 0);
-    enqueue_eval(c, s, C, 0);
-    CK(cudaGetLastError());
-    c->have_rates = true;
-    c->nbr_valid = true;
-    c->rates_scheme = *s;
+    if (status & ST_CAPACITY)
+        return fail(c, SPH_ERR_CAPACITY,
+                    "a particle has more neighbours than the list capacity (" +
+                        std::to_string(c->maxn) + "); set the state again to re-size it");
     return SPH_OK;
 }
 
@@ -294,6 +350,59 @@ void drop_graphs(sph_ctx* c) {
             cudaGraphExecDestroy(c->graph[k]);
             c->graph[k] = nullptr;
         }
+}
+
+void free_dev(sph_ctx* c, void* p) {
+    if (!p) return;
+    if (c->free_fn) c->free_fn(p, c->user);
+    else cudaFree(p);
+}
+
+// Neighbour-list capacity: count the neighbours of every particle at the current cell
+// table and make room for twice the largest count (+32), rounded up to a multiple of 32.
+sph_status ensure_list_capacity(sph_ctx* c) {
+    const PairConst<float> Kf = pair_const<float>(c, nullptr);
+    const PairConst<double> Kd = pair_const<double>(c, nullptr);
+    uint32_t* d_counts = (uint32_t*)c->io;
+    launch_export_neighbors(c->dom.precision, c->dom.dim, c->P, c->skeys, c->off,
+                            c->set[c->cur].tag, c->N, c->G, Kf, Kd, 0, d_counts, nullptr, nullptr,
+                            c->stream, c->sms);
+    CK(cudaGetLastError());
+    std::vector<uint32_t> counts(c->N);
+    CK(cudaMemcpyAsync(counts.data(), d_counts, (size_t)c->N * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    uint32_t mx = 0;
+    for (uint32_t v : counts) mx = v > mx ? v : mx;
+    if (c->nl && (uint32_t)c->maxn >= mx + mx / 4 + 8) return SPH_OK;
+    int want = (int)((2 * mx + 32 + 31) / 32 * 32);
+    void* p = nullptr;
+    const size_t bytes = (size_t)want * c->N * 4;
+    if (c->alloc) p = c->alloc(bytes, c->user);
+    else if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+    if (!p) {
+        cudaGetLastError();
+        return fail(c, SPH_ERR_OOM, "neighbour list of " + std::to_string(bytes) + " bytes");
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    free_dev(c, c->nl);
+    c->nl = (uint32_t*)p;
+    c->maxn = want;
+    drop_graphs(c);
+    return SPH_OK;
+}
+
+// Initial right-hand side at the current state (no drift, no kick).
+sph_status initial_eval(sph_ctx* c, const sph_scheme* s, double dt_fixed) {
+    StepConst C = step_const(c, s, dt_fixed);
+    enqueue_build(c, C, 0, 0, 0);
+    sph_status st = ensure_list_capacity(c);
+    if (st != SPH_OK) return st;
+    enqueue_eval(c, s, C, 0);
+    CK(cudaGetLastError());
+    c->have_rates = true;
+    c->nbr_valid = true;
+    c->rates_scheme = *s;
+    return SPH_OK;
 }
 
 sph_status capture_step_graphs(sph_ctx* c, const sph_scheme* s, double dt) {
@@ -449,11 +558,18 @@ sph_status sph_create(const sph_domain* domain, const sph_array_desc* arrays, in
     }
     c->passes = radix_passes(G.ncells);
     if (c->passes < 1) c->passes = 1;
-    int bps = pairs_max_blocks_per_sm(domain->precision, domain->dim, domain->kernel);
-    long long want = ((long long)c->N + pair_threads() - 1) / pair_threads();
-    long long cap = (long long)c->sms * bps;
-    c->pair_grid = (int)(want < cap ? want : cap);
-    if (c->pair_grid < 1) c->pair_grid = 1;
+    c->grid_cap = 1;
+    for (int pass = 0; pass < 2; ++pass)
+        for (int k = 0; k < 4; ++k) {
+            c->bps[pass][k] = pairs_max_blocks_per_sm(domain->precision, pass, domain->dim,
+                                                      domain->kernel, 1 << k);
+            if (c->sms * c->bps[pass][k] > c->grid_cap) c->grid_cap = c->sms * c->bps[pass][k];
+        }
+    {
+        int td = 1, tm = 1;
+        default_groups(c, &td, &tm);
+        set_groups(c, td, tm);
+    }
 
     // ---- arena
     const size_t N = (size_t)c->N;
@@ -465,7 +581,8 @@ sph_status sph_create(const sph_domain* domain, const sph_array_desc* arrays, in
     bytes += 4 * al(N * 4);                                    // keys, vals
     bytes += al(((size_t)G.ncells + 1) * 4);                   // cell offsets
     bytes += al(radix_hist_words(c->N) * 4);                   // radix histograms
-    bytes += al((size_t)c->pair_grid * partial_stride() * 8);  // block partials
+    bytes += al((size_t)c->grid_cap * 8 * 8) + al((size_t)c->grid_cap * 4 * 8);  // partials
+    bytes += al(N * 4);                                        // neighbour-list lengths
     bytes += al(sizeof(Control));
     bytes += al((size_t)HIST_CAP * DIAG_N * 8);                // history ring
     const size_t io_bytes = al(N * 4) + 2 * al(N * 8 + 8);     // io scratch
@@ -499,7 +616,9 @@ sph_status sph_create(const sph_domain* domain, const sph_array_desc* arrays, in
     for (int k = 0; k < 2; ++k) c->vals[k] = (uint32_t*)arena_take(p, N * 4);
     c->off = (uint32_t*)arena_take(p, ((size_t)G.ncells + 1) * 4);
     c->hist = (uint32_t*)arena_take(p, radix_hist_words(c->N) * 4);
-    c->partials = (double*)arena_take(p, (size_t)c->pair_grid * partial_stride() * 8);
+    c->pm = (double*)arena_take(p, (size_t)c->grid_cap * 8 * 8);
+    c->pd = (double*)arena_take(p, (size_t)c->grid_cap * 4 * 8);
+    c->cnt = (uint32_t*)arena_take(p, N * 4);
     c->ctl = (Control*)arena_take(p, sizeof(Control));
     c->history = (double*)arena_take(p, (size_t)HIST_CAP * DIAG_N * 8);
     c->io = arena_take(p, io_bytes);
@@ -580,10 +699,8 @@ void sph_destroy(sph_ctx* c) {
     drop_graphs(c);
     for (int k = 0; k < 6; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
-    if (c->arena) {
-        if (c->free_fn) c->free_fn(c->arena, c->user);
-        else cudaFree(c->arena);
-    }
+    free_dev(c, c->nl);
+    free_dev(c, c->arena);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -759,6 +876,93 @@ sph_status sph_kernels_per_step(const sph_ctx* ctx, const sph_scheme* scheme, in
     // drift+keys, 3 per radix pass, reorder, cell table, density pass, momentum pass
     *count = 1 + 3 * c->passes + 1 + 1 + 1 + 1;
     return SPH_OK;
+}
+
+sph_status sph_set_groups(sph_ctx* c, int32_t momentum_lanes) {
+    if (!c) return fail(c, SPH_ERR_INVALID, "ctx is NULL");
+    if (momentum_lanes != 1 && momentum_lanes != 2 && momentum_lanes != 4 && momentum_lanes != 8)
+        return fail(c, SPH_ERR_INVALID, "lanes per destination must be 1, 2, 4 or 8");
+    set_groups(c, 1, momentum_lanes);
+    drop_graphs(c);
+    return SPH_OK;
+}
+
+sph_status sph_autotune(sph_ctx* c, const sph_scheme* scheme, int32_t* chosen) {
+    if (!c) return fail(c, SPH_ERR_INVALID, "ctx is NULL");
+    sph_status s = check_scheme(c, scheme);
+    if (s != SPH_OK) return s;
+    s = initial_eval(c, scheme, 0.0);  // neighbours, list and a density pass at this state
+    if (s != SPH_OK) return s;
+    s = sync_status(c);
+    if (s != SPH_OK) return s;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const StepConst C = step_const(c, scheme, 0.0);
+    const PairConst<float> Kf = pair_const<float>(c, scheme);
+    const PairConst<double> Kd = pair_const<double>(c, scheme);
+    PairLaunch L{};
+    L.precision = c->dom.precision;
+    L.dim = c->dom.dim;
+    L.kernel = c->dom.kernel;
+    L.kick = 0;
+    L.n = c->N;
+    L.P = c->P;
+    L.Q = c->Q;
+    L.R = c->R;
+    L.skeys = c->skeys;
+    L.off = c->off;
+    L.G = c->G;
+    L.C = C;
+    L.S = c->set[c->cur];
+    L.ctl = c->ctl;
+    L.nl = c->nl;
+    L.cnt = c->cnt;
+    L.maxn = c->maxn;
+    L.pm = c->pm;
+    L.pd = c->pd;
+    L.history = c->history;
+    L.group_d = 1;
+    L.grid_d = c->grid_d;
+    int best = c->group_m;
+    float best_ms = 1e30f;
+    const int reps = 5;
+    for (int T = 1; T <= 8; T *= 2) {
+        L.group_m = T;
+        L.grid_m = pass_grid(c, 1, T);
+        for (int r = 0; r <= reps; ++r) {
+            if (r == 1) CK(cudaEventRecord(e0, c->stream));
+            launch_momentum_pass(L, Kf, Kd, c->stream);
+        }
+        CK(cudaEventRecord(e1, c->stream));
+        CK(cudaEventSynchronize(e1));
+        CK(cudaGetLastError());
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = T;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_lock);
+        const TuneKey k = tune_key(c);
+        bool found = false;
+        for (auto& e : g_tune_cache)
+            if (e.first == k) {
+                e.second = {1, best};
+                found = true;
+            }
+        if (!found) g_tune_cache.push_back({k, {1, best}});
+    }
+    set_groups(c, 1, best);
+    drop_graphs(c);
+    s = initial_eval(c, scheme, 0.0);  // leave rates and diagnostics of the chosen shape
+    if (s != SPH_OK) return s;
+    if (chosen) *chosen = best;
+    return sync_status(c);
 }
 
 sph_status sph_get(sph_ctx* c, int32_t array, const char* prop, double* out) {

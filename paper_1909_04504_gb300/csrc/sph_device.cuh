@@ -16,6 +16,7 @@ constexpr uint32_t ID_MASK = 0x7fffffffu;
 // Status bits raised on the device (host maps them to sph_status).
 constexpr unsigned ST_NONFINITE = 1u;
 constexpr unsigned ST_TIMEOUT = 2u;
+constexpr unsigned ST_CAPACITY = 4u;
 
 // Equation switches of one right-hand-side evaluation.
 constexpr int F_CONTINUITY = 1;   // Eq. continuity:sph (else summation density, Eq. 2)

@@ -39,9 +39,11 @@ void launch_export_neighbors(int precision, int dim, const void* P, const uint32
 // capi.cu: sets the message sph_last_error(NULL) returns on this thread
 void set_global_error(const std::string& msg);
 
-// pairs.cu
+// pairs.cu: one evaluation = density pass (group size group_d, grid_d blocks) then
+// momentum pass (group_m, grid_m). pm / pd: per-block partials of the two passes.
 struct PairLaunch {
-    int precision, dim, kernel, summation, kick, n, grid;
+    int precision, dim, kernel, kick, n;
+    int group_d, group_m, grid_d, grid_m;
     const void* P;
     void* Q;
     void* R;
@@ -51,13 +53,22 @@ struct PairLaunch {
     StepConst C;
     ParticleSet S;
     Control* ctl;
-    double* partials;
+    uint32_t* nl;   // neighbour list, nl[k * n + i], k < maxn
+    uint32_t* cnt;  // list length per particle
+    int maxn;
+    double* pm;  // 8 doubles per momentum block
+    double* pd;  // 4 doubles per density block
     double* history;
 };
 int pair_threads();
-int partial_stride();
 void launch_pairs(const PairLaunch& L, const PairConst<float>& Kf, const PairConst<double>& Kd,
                   cudaStream_t st);
-int pairs_max_blocks_per_sm(int precision, int dim, int kernel);
+void launch_density_pass(const PairLaunch& L, const PairConst<float>& Kf,
+                         const PairConst<double>& Kd, cudaStream_t st);
+void launch_momentum_pass(const PairLaunch& L, const PairConst<float>& Kf,
+                          const PairConst<double>& Kd, cudaStream_t st);
+// pass 0: density (thread per destination), 1: momentum (T = 1, 2, 4 or 8 lanes per
+// destination)
+int pairs_max_blocks_per_sm(int precision, int pass, int dim, int kernel, int T);
 
 }  // namespace sph
