@@ -223,6 +223,26 @@ sph_status sph_autotune(sph_ctx* ctx, const sph_scheme* scheme, int32_t* chosen)
 /* Kernel launches one step issues (for launch accounting). */
 sph_status sph_kernels_per_step(const sph_ctx* ctx, const sph_scheme* scheme, int32_t* count);
 
+/* Hand-written adjoint of K predictor-corrector steps with fixed dt (the neighbour set of
+ * every step held fixed): starting from the current state, runs K steps (the context ends
+ * in the final state, as after sph_step) and returns the gradient of the final kinetic
+ * energy KE = 1/2 sum_fluid m |u|^2 with respect to
+ *   dKE_du0   (host, dim arrays of n_total doubles, original order, walls 0): the fluid
+ *             velocities of the current state, which are treated as initial values, with
+ *             the initial evaluation recomputed from them (as sph_eval_rhs does);
+ *   dKE_dnu   the laminar viscosity nu of the scheme;
+ *   dKE_dalpha the artificial-viscosity coefficient alpha (0 when alpha is 0: the term
+ *             is then switched off).
+ * Any output may be NULL. Checkpoint and recompute: the state is saved every ckpt_every
+ * steps (<= 0: ceil(sqrt K)); each segment is recomputed once, taping the pair-loop
+ * inputs of its steps, and reversed. Pair terms in the pair-loop precision with
+ * compensated sums; adjoint state and the scalar gradients in FP64. Continuity
+ * formulation only (SPH_ERR_INVALID for summation density), dt > 0 required. Device
+ * workspace: about (K / ckpt_every + 1) * 124 + (ckpt_every + 1) * 44 + 300 bytes per
+ * particle in FP32 mode, allocated for the call. */
+sph_status sph_backward(sph_ctx* ctx, const sph_scheme* scheme, double dt, int32_t K,
+                        int32_t ckpt_every, double* dKE_du0, double* dKE_dnu, double* dKE_dalpha);
+
 /* Property of one array (or -1 for all particles) into a host buffer, original order.
  * prop: "x" "y" "z" "u" "v" "w" "rho" "m", or rates of the last evaluation "arho" "ax"
  * "ay" "az" "xsx" "xsy" "xsz". */

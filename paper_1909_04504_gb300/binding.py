@@ -58,7 +58,7 @@ _lib = None
 EXPORTS = ("sph_create", "sph_destroy", "sph_last_error", "sph_count", "sph_grid",
            "sph_build_neighbors", "sph_get_cells", "sph_get_neighbors", "sph_eval_rhs",
            "sph_step", "sph_step_async", "sph_synchronize", "sph_set_timing", "sph_phase_times",
-           "sph_kernels_per_step", "sph_set_groups", "sph_autotune", "sph_get", "sph_set", "sph_diagnostics", "sph_history",
+           "sph_kernels_per_step", "sph_set_groups", "sph_autotune", "sph_backward", "sph_get", "sph_set", "sph_diagnostics", "sph_history",
            "sph_save_state", "sph_load_state")
 
 
@@ -99,6 +99,7 @@ def load(build_if_missing: bool = True):
     L.sph_phase_times.argtypes = [ctxp, C.POINTER(C.c_float)]
     L.sph_kernels_per_step.argtypes = [ctxp, C.POINTER(Scheme), i32]
     L.sph_set_groups.argtypes = [ctxp, C.c_int32]
+    L.sph_backward.argtypes = [ctxp, C.POINTER(Scheme), C.c_double, C.c_int32, C.c_int32, d, d, d]
     L.sph_autotune.argtypes = [ctxp, C.POINTER(Scheme), i32]
     L.sph_get.argtypes = [ctxp, C.c_int32, C.c_char_p, d]
     L.sph_set.argtypes = [ctxp, C.c_int32, C.c_char_p, d]
@@ -328,6 +329,14 @@ class Simulation:
         out = C.c_int32()
         self._check(self._L.sph_autotune(self._ctx, C.byref(scheme), C.byref(out)))
         return int(out.value)
+
+    def backward(self, scheme: Scheme, dt: float, K: int, ckpt_every: int = 0):
+        """Run K steps and return (dKE/du0 [dim, n] in original order, dKE/dnu, dKE/dalpha)."""
+        out = np.zeros((self.dim, self.n))
+        gnu, gal = C.c_double(), C.c_double()
+        self._check(self._L.sph_backward(self._ctx, C.byref(scheme), float(dt), int(K),
+                                         int(ckpt_every), _dptr(out), C.byref(gnu), C.byref(gal)))
+        return out, gnu.value, gal.value
 
     def get(self, prop: str, array: int = -1) -> np.ndarray:
         out = np.zeros(self.count(array))

@@ -1,0 +1,516 @@
+// Hand-written adjoint of the neighbour-fixed WCSPH step (reverse of the Sec. 2.1
+// predictor-corrector with the density advanced like the positions):
+//   forward step n -> n+1 (cell order O_n -> O_{n+1}, perm: O_{n+1} -> O_n):
+//     drift  uh = u + dt/2 a, x' = x + dt (uh + xsph)          (fluid, order O_n)
+//     gather x, uh, rho into O_{n+1}
+//     density  rho' = rho + dt D(x, uh)                         (Eq. continuity:sph)
+//     momentum (a', xsph') = M(x, uh, rho') + g                 (Eqs. mom:sph*, AV, XSPH)
+//     kick   u' = uh + dt/2 a'
+//   reverse (cotangents of x, u', rho', a', xsph' in O_{n+1}):
+//     abar = lambda_a' + dt/2 lambda_u', lambda_uh = lambda_u'
+//     momentum VJP  -> lambda_x, lambda_uh, lambda_rho' (+ Pr chain), nu-bar, alpha-bar
+//     continuity VJP with cotangent dt (lambda_rho' + momentum part) -> lambda_x, lambda_uh
+//     scatter to O_n and the drift transpose.
+// The pair VJPs are gathers over each particle's neighbour list: a particle collects the
+// terms where it is the destination (its own cotangents) and where it is the source (the
+// neighbour's cotangents), so no atomics are needed. Pair arithmetic in the pair-loop
+// precision with compensated per-particle sums; adjoint state and scalar gradients in FP64.
+#include "pairs_impl.cuh"
+
+namespace sph {
+
+// ----------------------------------------------------------- list rebuild
+// Cell key of each taped particle from its pair-loop position (the forward's binning).
+template <class Real>
+__global__ void k_adj_keys(const typename V4<Real>::T* __restrict__ P, int n, Grid G,
+                           uint32_t* __restrict__ keys) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const typename V4<Real>::T p = P[i];
+        const double xs[3] = {(double)p.x, (double)p.y, (double)p.z};
+        int c[3] = {0, 0, 0};
+        int clamped = 0;
+        for (int d = 0; d < G.dim; ++d) c[d] = cell_coord(xs[d], G.lo[d], G.cs[d], G.nc[d], &clamped);
+        keys[i] = (uint32_t)(c[0] + G.nc[0] * (c[1] + G.nc[1] * c[2]));
+    }
+}
+
+// Neighbour list of the taped configuration with the continuity-mode rule (a fluid
+// destination lists every neighbour, a wall destination its fluid neighbours).
+template <class Real, int DIM>
+__global__ void __launch_bounds__(PAIR_THREADS)
+k_adj_list(const typename V4<Real>::T* __restrict__ P, const uint32_t* __restrict__ skeys,
+           const uint32_t* __restrict__ off, int n, Grid G, PairConst<Real> K,
+           uint32_t* __restrict__ nl, uint32_t* __restrict__ cnt, int maxn, Control* ctl) {
+    int overflow = 0;
+    for (int i = blockIdx.x * PAIR_THREADS + threadIdx.x; i < n; i += gridDim.x * PAIR_THREADS) {
+        const typename V4<Real>::T pi = P[i];
+        const bool fluid_i = pi.w > Real(0);
+        int cx, cy, cz;
+        cell_of_key(G, skeys[i], cx, cy, cz);
+        uint32_t k = 0;
+        for_each_run<DIM>(G, off, cx, cy, cz, [&](uint32_t jb, uint32_t je) {
+            for (uint32_t j = jb; j < je; ++j) {
+                if ((int)j == i) continue;
+                const typename V4<Real>::T pj = P[j];
+                Real dx, dy, dz;
+                const Real r2 = separation<Real, DIM>(pi, pj, G, K, dx, dy, dz);
+                if (r2 < K.kh2 && (fluid_i || pj.w > Real(0))) {
+                    if (k < (uint32_t)maxn) nl[(size_t)k * n + i] = j;
+                    ++k;
+                }
+            }
+        });
+        if (k > (uint32_t)maxn) {
+            overflow = 1;
+            k = maxn;
+        }
+        cnt[i] = k;
+    }
+    if (overflow) atomicOr(&ctl->status, ST_CAPACITY);
+}
+
+// ------------------------------------------------------------- kernel derivative
+// fp(q) = f'(q) / q with f = w'(q) / q the gradient factor of the pair loops, so that
+// d(Gk)/dr_vec = gfac fp(q) / h^2 * r_vec.
+template <class Real, int KERNEL>
+__device__ __forceinline__ Real kernel_fp(Real q) {
+    if (KERNEL == QUINTIC) {
+        if (q < Real(1)) return Real(-150) * q + Real(240);
+        const Real t3 = Real(3) - q;
+        Real w1 = Real(-5) * t3 * t3 * t3 * t3;
+        Real w1p = Real(20) * t3 * t3 * t3;
+        if (q < Real(2)) {
+            const Real t2 = Real(2) - q;
+            w1 += Real(30) * t2 * t2 * t2 * t2;
+            w1p -= Real(120) * t2 * t2 * t2;
+        }
+        return (w1p * q - w1) / (q * q * q);
+    } else {
+        if (q < Real(1e-6)) return Real(0);  // multiplies r_vec -> 0 (coincident particles)
+        const Real t = Real(1) - Real(0.5) * q;
+        return Real(7.5) * t * t / q;
+    }
+}
+
+// Cotangents of one destination's momentum equation: abar (acceleration), sbar (XSPH).
+template <class Real>
+struct MomCot {
+    Real ax, ay, az, sx, sy, sz;
+};
+
+// VJP of the momentum + XSPH terms of the ordered pair (i dest fluid, j source) with the
+// cotangents of i. Inputs: r = x_i - x_j, v = u_i - u_j, densities, Pr = p / rho^2, m_j,
+// whether j is fluid. Outputs (added): g_r, g_v (vectors), g_rho_i, g_rho_j, g_pr (the
+// same for Pr_i and Pr_j), g_nu, g_alpha.
+template <class Real, int DIM, int KERNEL>
+__device__ __forceinline__ void momentum_vjp(Real rx, Real ry, Real rz, Real r2, Real vx, Real vy,
+                                             Real vz, Real rho_i, Real rho_j, Real pr_i, Real pr_j,
+                                             Real mj, bool fluid_j, const MomCot<Real>& c,
+                                             const PairConst<Real>& K, int flags, Real* g_r,
+                                             Real* g_v, Real& g_rho_i, Real& g_rho_j, Real& g_pr,
+                                             Real& g_nu, Real& g_alpha) {
+    const Real q = sqrt(r2) * K.inv_h;
+    const Real Gk = K.gfac * kernel_f<Real, KERNEL>(q);
+    const Real Gp = K.gfac * kernel_fp<Real, KERNEL>(q) * (K.inv_h * K.inv_h);  // dGk/dr = Gp r
+    const Real vr = vx * rx + vy * ry + (DIM == 3 ? vz * rz : Real(0));
+    const Real ar = c.ax * rx + c.ay * ry + (DIM == 3 ? c.az * rz : Real(0));
+    const Real av = c.ax * vx + c.ay * vy + (DIM == 3 ? c.az * vz : Real(0));
+    const Real rhobar = Real(0.5) * (rho_i + rho_j);
+    // pressure + artificial viscosity: a_i += -m_j (Pr_i + Pr_j + Pi) Gk r
+    Real Pi = Real(0), dPi_dvr = Real(0), dPi_dr2 = Real(0), dPi_drhobar = Real(0);
+    const bool av_on = (flags & F_AV) && vr < Real(0);
+    if (av_on) {
+        const Real den = r2 + K.av_h2;
+        const Real mu = K.h * vr / den;
+        Pi = -K.alpha_c0 * mu / rhobar;
+        dPi_dvr = -K.alpha_c0 * K.h / (den * rhobar);
+        dPi_dr2 = K.alpha_c0 * mu / (den * rhobar);  // d(-a c mu/rb)/dr2 with dmu/dr2 = -mu/den
+        dPi_drhobar = -Pi / rhobar;
+        g_alpha += -mj * Gk * ar * (-K.c0 * mu / rhobar);  // dPi/dalpha = -c0 mu / rhobar
+    }
+    const Real coef = pr_i + pr_j + Pi;
+    // d(ar Gk coef)/dr: ar -> abar, Gk -> Gp r, coef -> dPi/dr (vr: v, r2: 2 r)
+    const Real s1 = -mj * (coef * Gp * ar + Gk * ar * dPi_dr2 * Real(2));
+    const Real s2 = -mj * coef * Gk;
+    const Real s3 = -mj * Gk * ar * dPi_dvr;
+    g_r[0] += s1 * rx + s2 * c.ax + s3 * vx;
+    g_r[1] += s1 * ry + s2 * c.ay + s3 * vy;
+    if (DIM == 3) g_r[2] += s1 * rz + s2 * c.az + s3 * vz;
+    g_v[0] += s3 * rx;
+    g_v[1] += s3 * ry;
+    if (DIM == 3) g_v[2] += s3 * rz;
+    g_pr += -mj * Gk * ar;
+    const Real gP_rhobar = -mj * Gk * ar * dPi_drhobar * Real(0.5);
+    g_rho_i += gP_rhobar;
+    g_rho_j += gP_rhobar;
+    // laminar viscosity: a_i += m_j 4 nu / (rho_i + rho_j) Gk g2 v, g2 = r2 / (r2 + eta h^2)
+    if (flags & F_LAMINAR) {
+        const Real den = r2 + K.eta_h2;
+        const Real g2 = r2 / den;
+        const Real dg2 = K.eta_h2 / (den * den);  // d g2 / d r2
+        const Real rs = rho_i + rho_j;
+        const Real cvn = mj * K.nu4 / rs;  // cv / (Gk g2)
+        const Real t1 = cvn * av * (Gp * g2 + Gk * dg2 * Real(2));
+        g_r[0] += t1 * rx;
+        g_r[1] += t1 * ry;
+        if (DIM == 3) g_r[2] += t1 * rz;
+        const Real cv = cvn * Gk * g2;
+        g_v[0] += cv * c.ax;
+        g_v[1] += cv * c.ay;
+        if (DIM == 3) g_v[2] += cv * c.az;
+        const Real grs = -cv * av / rs;
+        g_rho_i += grs;
+        g_rho_j += grs;
+        g_nu += Real(4) * mj / rs * Gk * g2 * av;  // d/dnu (nu4 = 4 nu)
+    }
+    // XSPH over fluid sources: xs_i += -eps m_j W v / rhobar
+    if ((flags & F_XSPH) && fluid_j) {
+        const Real W = K.wfac * kernel_w<Real, KERNEL>(q);
+        const Real sv = c.sx * vx + c.sy * vy + (DIM == 3 ? c.sz * vz : Real(0));
+        const Real e = K.xsph * mj / rhobar;
+        const Real t1 = -e * sv * Gk;  // dW/dr = Gk r
+        g_r[0] += t1 * rx;
+        g_r[1] += t1 * ry;
+        if (DIM == 3) g_r[2] += t1 * rz;
+        g_v[0] += -e * W * c.sx;
+        g_v[1] += -e * W * c.sy;
+        if (DIM == 3) g_v[2] += -e * W * c.sz;
+        const Real grb = e * W * sv / rhobar * Real(0.5);
+        g_rho_i += grb;
+        g_rho_j += grb;
+    }
+}
+
+// ------------------------------------------------------------ adjoint kernels
+// Cotangent shadow of one evaluation in the taped order: CA = (abar, c_rho) and
+// CS = (sbar, 0) for fluid particles (walls: zero), lambda_uh = lambda_u.
+// kick = 1 adds the corrector's dt/2 lambda_u' to abar (a step); 0 for the initial
+// evaluation (no kick follows it).
+template <class Real>
+__global__ void k_adj_cot(AdjSet L, const typename V4<Real>::T* __restrict__ P, int n, double dt,
+                          int kick, typename V4<Real>::T* __restrict__ CA,
+                          typename V4<Real>::T* __restrict__ CS, double* __restrict__ luh0,
+                          double* __restrict__ luh1, double* __restrict__ luh2, int dim) {
+    double* luh[3] = {luh0, luh1, luh2};
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const bool fluid = P[k].w > Real(0);
+        typename V4<Real>::T ca, cs;
+        double ab[3] = {0, 0, 0}, sb[3] = {0, 0, 0};
+        for (int d = 0; d < dim; ++d) {
+            if (fluid) {
+                ab[d] = L.a[d][k] + (kick ? 0.5 * dt * L.u[d][k] : 0.0);
+                sb[d] = L.xs[d][k];
+                luh[d][k] = L.u[d][k];
+            } else {
+                luh[d][k] = 0.0;
+            }
+        }
+        ca.x = (Real)ab[0]; ca.y = (Real)ab[1]; ca.z = (Real)ab[2]; ca.w = Real(0);
+        cs.x = (Real)sb[0]; cs.y = (Real)sb[1]; cs.z = (Real)sb[2]; cs.w = Real(0);
+        CA[k] = ca;
+        CS[k] = cs;
+    }
+}
+
+// Block sum of two scalars added to the running totals by the last block (fixed order).
+__device__ __forceinline__ void adj_scalars(double a, double b, double* part, AdjCtl* actl) {
+    __shared__ double red[PAIR_THREADS / 32][2];
+    __shared__ bool last;
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[warp][0] = a;
+        red[warp][1] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s0 = 0, s1 = 0;
+        for (int w = 0; w < PAIR_THREADS / 32; ++w) {
+            s0 += red[w][0];
+            s1 += red[w][1];
+        }
+        part[2 * blockIdx.x] = s0;
+        part[2 * blockIdx.x + 1] = s1;
+        __threadfence();
+        last = atomicAdd(&actl->ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        double s0 = 0, s1 = 0;
+        const volatile double* vp = part;
+        for (int bk = 0; bk < (int)gridDim.x; ++bk) {
+            s0 += vp[2 * bk];
+            s1 += vp[2 * bk + 1];
+        }
+        actl->g_nu += s0;
+        actl->g_alpha += s1;
+        actl->ticket = 0;
+        __threadfence();
+    }
+}
+
+// Momentum + XSPH VJP gather. For particle k over its list: as destination (fluid k, its
+// cotangents) and as source of each fluid neighbour j (j's cotangents). Adds to
+// lambda_x and lambda_uh (fluid k), writes rhom_k = d/drho' of the momentum terms (the
+// Pr = p / rho^2 part through the EOS derivative), and accumulates d/dnu, d/dalpha.
+template <class Real, int DIM, int KERNEL>
+__global__ void __launch_bounds__(PAIR_THREADS)
+k_adj_momentum(const typename V4<Real>::T* __restrict__ P, const typename V4<Real>::T* __restrict__ Q,
+               const Real* __restrict__ R, const uint32_t* __restrict__ nl,
+               const uint32_t* __restrict__ cnt, int n, Grid G, PairConst<Real> K, StepConst C,
+               const typename V4<Real>::T* __restrict__ CA, const typename V4<Real>::T* __restrict__ CS,
+               AdjSet L, double* __restrict__ luh0, double* __restrict__ luh1,
+               double* __restrict__ luh2, double* __restrict__ rhom, double* __restrict__ part,
+               AdjCtl* actl) {
+    double* luh[3] = {luh0, luh1, luh2};
+    const int flags = K.flags;
+    double s_nu = 0, s_alpha = 0;
+    for (int k = blockIdx.x * PAIR_THREADS + threadIdx.x; k < n; k += gridDim.x * PAIR_THREADS) {
+        const typename V4<Real>::T pk = P[k];
+        const typename V4<Real>::T qk = Q[k];
+        const Real prk = R[k];
+        const bool fluid_k = pk.w > Real(0);
+        const Real mk = fabs(pk.w);
+        const typename V4<Real>::T cak = CA[k], csk = CS[k];
+        const MomCot<Real> cot_k{cak.x, cak.y, cak.z, csk.x, csk.y, csk.z};
+        Acc<Real> gx[3], gu[3], grho, gpr, gnu, gal;
+        for (int d = 0; d < 3; ++d) {
+            gx[d].zero();
+            gu[d].zero();
+        }
+        grho.zero(); gpr.zero(); gnu.zero(); gal.zero();
+        const uint32_t nk = cnt[k];
+        for (uint32_t kk = 0; kk < nk; ++kk) {
+            const uint32_t j = nl[(size_t)kk * n + k];
+            const typename V4<Real>::T pj = P[j];
+            Real rx, ry, rz;
+            const Real r2 = separation<Real, DIM>(pk, pj, G, K, rx, ry, rz);
+            const typename V4<Real>::T qj = Q[j];
+            const Real prj = R[j];
+            const bool fluid_j = pj.w > Real(0);
+            const Real vx = qk.x - qj.x, vy = qk.y - qj.y, vz = DIM == 3 ? qk.z - qj.z : Real(0);
+            if (fluid_k) {  // k is the destination
+                Real g_r[3] = {0, 0, 0}, g_v[3] = {0, 0, 0}, g_ri = 0, g_rj = 0, g_p = 0, g_n = 0,
+                     g_a = 0;
+                momentum_vjp<Real, DIM, KERNEL>(rx, ry, rz, r2, vx, vy, vz, qk.w, qj.w, prk, prj,
+                                                fabs(pj.w), fluid_j, cot_k, K, flags, g_r, g_v, g_ri,
+                                                g_rj, g_p, g_n, g_a);
+                for (int d = 0; d < DIM; ++d) {
+                    gx[d].add(g_r[d]);
+                    gu[d].add(g_v[d]);
+                }
+                grho.add(g_ri);
+                gpr.add(g_p);
+                gnu.add(g_n);
+                gal.add(g_a);
+            }
+            if (fluid_j) {  // k is the source of destination j
+                const typename V4<Real>::T caj = CA[j], csj = CS[j];
+                const MomCot<Real> cot_j{caj.x, caj.y, caj.z, csj.x, csj.y, csj.z};
+                Real g_r[3] = {0, 0, 0}, g_v[3] = {0, 0, 0}, g_ri = 0, g_rj = 0, g_p = 0, g_n = 0,
+                     g_a = 0;
+                momentum_vjp<Real, DIM, KERNEL>(-rx, -ry, -rz, r2, -vx, -vy, -vz, qj.w, qk.w, prj,
+                                                prk, mk, fluid_k, cot_j, K, flags, g_r, g_v, g_ri,
+                                                g_rj, g_p, g_n, g_a);
+                for (int d = 0; d < DIM; ++d) {
+                    gx[d].add(-g_r[d]);
+                    gu[d].add(-g_v[d]);
+                }
+                grho.add(g_rj);
+                gpr.add(g_p);
+            }
+        }
+        if (fluid_k)
+            for (int d = 0; d < DIM; ++d) {
+                L.x[d][k] += gx[d].value();
+                luh[d][k] += gu[d].value();
+            }
+        // EOS chain: d(p / rho^2)/drho = c0^2 (rho/rho0)^(gamma-1) / rho^2 - 2 p / rho^3
+        const double rho = (double)qk.w;
+        const double p = tait_pressure(rho, C);
+        const double dp = C.c0 * C.c0 * pow(rho * C.inv_rho0, C.gamma - 1.0);
+        const double dpr = dp / (rho * rho) - 2.0 * p / (rho * rho * rho);
+        rhom[k] = grho.value() + dpr * gpr.value();
+        s_nu += gnu.value();
+        s_alpha += gal.value();
+    }
+    adj_scalars(s_nu, s_alpha, part, actl);
+}
+
+// Continuity cotangent c_k = dt lambda_rho'_total,k and the total density adjoint.
+template <class Real>
+__global__ void k_adj_rho(AdjSet L, const double* __restrict__ rhom, int n, double dt,
+                          typename V4<Real>::T* __restrict__ CA, double* __restrict__ lrho_tot) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const double t = L.rho[k] + rhom[k];
+        lrho_tot[k] = t;
+        reinterpret_cast<Real*>(&CA[k])[3] = (Real)(dt * t);
+    }
+}
+
+// Continuity VJP gather: arho_i = sum_j m_j Gk_ij (v_ij . r_ij) over interacting pairs.
+// Both roles of k combine into (c_k m_j + c_j m_k) (Gp vr r + Gk v) for lambda_x and
+// (c_k m_j + c_j m_k) Gk r for lambda_uh (fluid k).
+template <class Real, int DIM, int KERNEL>
+__global__ void __launch_bounds__(PAIR_THREADS)
+k_adj_continuity(const typename V4<Real>::T* __restrict__ P, const typename V4<Real>::T* __restrict__ Q,
+                 const uint32_t* __restrict__ nl, const uint32_t* __restrict__ cnt, int n, Grid G,
+                 PairConst<Real> K, const typename V4<Real>::T* __restrict__ CA, AdjSet L,
+                 double* __restrict__ luh0, double* __restrict__ luh1, double* __restrict__ luh2) {
+    double* luh[3] = {luh0, luh1, luh2};
+    for (int k = blockIdx.x * PAIR_THREADS + threadIdx.x; k < n; k += gridDim.x * PAIR_THREADS) {
+        const typename V4<Real>::T pk = P[k];
+        if (!(pk.w > Real(0))) continue;  // walls: x and u are constants
+        const typename V4<Real>::T qk = Q[k];
+        const Real mk = fabs(pk.w);
+        const Real ck = reinterpret_cast<const Real*>(&CA[k])[3];
+        Acc<Real> gx[3], gu[3];
+        for (int d = 0; d < 3; ++d) {
+            gx[d].zero();
+            gu[d].zero();
+        }
+        const uint32_t nk = cnt[k];
+        for (uint32_t kk = 0; kk < nk; ++kk) {
+            const uint32_t j = nl[(size_t)kk * n + k];
+            const typename V4<Real>::T pj = P[j];
+            Real rx, ry, rz;
+            const Real r2 = separation<Real, DIM>(pk, pj, G, K, rx, ry, rz);
+            const typename V4<Real>::T qj = Q[j];
+            const Real cj = reinterpret_cast<const Real*>(&CA[j])[3];
+            const Real q = sqrt(r2) * K.inv_h;
+            const Real Gk = K.gfac * kernel_f<Real, KERNEL>(q);
+            const Real Gp = K.gfac * kernel_fp<Real, KERNEL>(q) * (K.inv_h * K.inv_h);
+            const Real vx = qk.x - qj.x, vy = qk.y - qj.y, vz = DIM == 3 ? qk.z - qj.z : Real(0);
+            const Real vr = vx * rx + vy * ry + (DIM == 3 ? vz * rz : Real(0));
+            const Real w = ck * fabs(pj.w) + cj * mk;
+            const Real a = w * Gp * vr, b = w * Gk;
+            gx[0].add(a * rx + b * vx);
+            gx[1].add(a * ry + b * vy);
+            if (DIM == 3) gx[2].add(a * rz + b * vz);
+            gu[0].add(b * rx);
+            gu[1].add(b * ry);
+            if (DIM == 3) gu[2].add(b * rz);
+        }
+        for (int d = 0; d < DIM; ++d) {
+            L.x[d][k] += gx[d].value();
+            luh[d][k] += gu[d].value();
+        }
+    }
+}
+
+// Transpose of the gather (O_n <- O_{n+1}) and of the drift/kick of the previous state:
+// uh = u + dt/2 a feeds both the evaluation (lambda_uh) and x' = x + dt (uh + xsph).
+__global__ void k_adj_scatter(AdjSet in, AdjSet out, const double* __restrict__ luh0,
+                              const double* __restrict__ luh1, const double* __restrict__ luh2,
+                              const double* __restrict__ lrho_tot, const uint32_t* __restrict__ perm,
+                              const uint32_t* __restrict__ tag, int n, int dim, double dt) {
+    const double* luh[3] = {luh0, luh1, luh2};
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const int o = (int)perm[k];
+        const bool fluid = !(tag[k] & WALL_BIT);
+        for (int d = 0; d < dim; ++d) {
+            const double lx = fluid ? in.x[d][k] : 0.0;
+            const double lu = fluid ? luh[d][k] : 0.0;
+            out.x[d][o] = lx;
+            out.u[d][o] = lu + dt * lx;
+            out.a[d][o] = 0.5 * dt * lu + 0.5 * dt * dt * lx;
+            out.xs[d][o] = dt * lx;
+        }
+        out.rho[o] = lrho_tot[k];
+    }
+}
+
+// Final adjoint of the initial velocities, scattered to global ids: out[d * n + id].
+__global__ void k_adj_to_original(const double* __restrict__ luh0, const double* __restrict__ luh1,
+                                  const double* __restrict__ luh2, const uint32_t* __restrict__ tag,
+                                  int n, int dim, double* __restrict__ out) {
+    const double* luh[3] = {luh0, luh1, luh2};
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const uint32_t t = tag[k];
+        const uint32_t id = t & ID_MASK;
+        const bool fluid = !(t & WALL_BIT);
+        for (int d = 0; d < dim; ++d) out[(size_t)d * n + id] = fluid ? luh[d][k] : 0.0;
+    }
+}
+
+// Terminal cotangent of KE = 1/2 sum_fluid m |u|^2 in the final order: lambda_u = m u.
+__global__ void k_adj_terminal(AdjSet L, ParticleSet S, int n, int dim) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const bool fluid = !(S.tag[k] & WALL_BIT);
+        for (int d = 0; d < 3; ++d) {
+            L.x[d][k] = 0.0;
+            L.u[d][k] = (fluid && d < dim) ? S.m[k] * S.u[d][k] : 0.0;
+            L.a[d][k] = 0.0;
+            L.xs[d][k] = 0.0;
+        }
+        L.rho[k] = 0.0;
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+static inline int grid_of(long long n, int threads, int cap) {
+    long long b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    return (int)(b > cap ? cap : b);
+}
+
+template <class Real, int DIM, int KERNEL>
+static void adj_eval_t(const AdjLaunch& A, const PairConst<Real>& K, cudaStream_t st) {
+    using V = typename V4<Real>::T;
+    const int g256 = grid_of(A.n, 256, A.sms * 8);
+    const int gp = grid_of(A.n, PAIR_THREADS, A.sms * 16);
+    // list of the taped configuration
+    k_adj_keys<Real><<<g256, 256, 0, st>>>((const V*)A.P, A.n, A.G, A.keys);
+    launch_cell_offsets(A.keys, A.n, A.G.ncells, A.off, A.ctl, st, A.sms);
+    k_adj_list<Real, DIM><<<gp, PAIR_THREADS, 0, st>>>((const V*)A.P, A.keys, A.off, A.n, A.G, K,
+                                                       A.nl, A.cnt, A.maxn, A.ctl);
+    k_adj_cot<Real><<<g256, 256, 0, st>>>(A.L, (const V*)A.P, A.n, A.dt, A.kick, (V*)A.CA,
+                                          (V*)A.CS, A.luh[0], A.luh[1], A.luh[2], DIM);
+    k_adj_momentum<Real, DIM, KERNEL><<<gp, PAIR_THREADS, 0, st>>>(
+        (const V*)A.P, (const V*)A.Q, (const Real*)A.R, A.nl, A.cnt, A.n, A.G, K, A.C,
+        (const V*)A.CA, (const V*)A.CS, A.L, A.luh[0], A.luh[1], A.luh[2], A.rhom, A.part, A.actl);
+    k_adj_rho<Real><<<g256, 256, 0, st>>>(A.L, A.rhom, A.n, A.kick ? A.dt : 0.0, (V*)A.CA,
+                                          A.lrho_tot);
+    if (A.kick)
+        k_adj_continuity<Real, DIM, KERNEL><<<gp, PAIR_THREADS, 0, st>>>(
+            (const V*)A.P, (const V*)A.Q, A.nl, A.cnt, A.n, A.G, K, (const V*)A.CA, A.L, A.luh[0],
+            A.luh[1], A.luh[2]);
+}
+
+void launch_adjoint_eval(const AdjLaunch& A, const PairConst<float>& Kf, const PairConst<double>& Kd,
+                         cudaStream_t st) {
+    const int sel = (A.precision ? 4 : 0) + (A.dim == 3 ? 2 : 0) + (A.kernel == WENDLAND_C2 ? 1 : 0);
+    switch (sel) {
+        case 0: adj_eval_t<double, 2, QUINTIC>(A, Kd, st); break;
+        case 1: adj_eval_t<double, 2, WENDLAND_C2>(A, Kd, st); break;
+        case 2: adj_eval_t<double, 3, QUINTIC>(A, Kd, st); break;
+        case 3: adj_eval_t<double, 3, WENDLAND_C2>(A, Kd, st); break;
+        case 4: adj_eval_t<float, 2, QUINTIC>(A, Kf, st); break;
+        case 5: adj_eval_t<float, 2, WENDLAND_C2>(A, Kf, st); break;
+        case 6: adj_eval_t<float, 3, QUINTIC>(A, Kf, st); break;
+        default: adj_eval_t<float, 3, WENDLAND_C2>(A, Kf, st); break;
+    }
+}
+
+void launch_adjoint_scatter(const AdjLaunch& A, const AdjSet& out, cudaStream_t st) {
+    k_adj_scatter<<<grid_of(A.n, 256, A.sms * 8), 256, 0, st>>>(
+        A.L, out, A.luh[0], A.luh[1], A.luh[2], A.lrho_tot, A.perm, A.tag, A.n, A.dim, A.dt);
+}
+
+void launch_adjoint_terminal(const AdjSet& L, const ParticleSet& S, int n, int dim, int sms,
+                             cudaStream_t st) {
+    k_adj_terminal<<<grid_of(n, 256, sms * 8), 256, 0, st>>>(L, S, n, dim);
+}
+
+void launch_adjoint_to_original(const AdjLaunch& A, double* out, cudaStream_t st) {
+    k_adj_to_original<<<grid_of(A.n, 256, A.sms * 8), 256, 0, st>>>(A.luh[0], A.luh[1], A.luh[2],
+                                                                     A.tag, A.n, A.dim, out);
+}
+
+int adjoint_partial_blocks(int n, int sms) { return grid_of(n, PAIR_THREADS, sms * 16); }
+
+}  // namespace sph

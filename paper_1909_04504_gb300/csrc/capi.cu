@@ -186,6 +186,7 @@ PairConst<Real> pair_const(const sph_ctx* c, const sph_scheme* s) {
         K.av_h2 = (Real)(0.01 * D.h * D.h);
         K.nu4 = (Real)(4.0 * s->nu);
         K.alpha_c0 = (Real)(s->alpha * s->c0);
+        K.c0 = (Real)s->c0;
         K.xsph = (Real)s->xsph_eps;
         int f = 0;
         if (s->density == SPH_DENSITY_CONTINUITY) f |= F_CONTINUITY;
@@ -963,6 +964,255 @@ sph_status sph_autotune(sph_ctx* c, const sph_scheme* scheme, int32_t* chosen) {
     if (s != SPH_OK) return s;
     if (chosen) *chosen = best;
     return sync_status(c);
+}
+
+// ------------------------------------------------------------------- adjoint
+namespace {
+
+// Snapshot of the FP64 state of the current set (x, u, rho, m, arho, a, xsph, tag).
+struct Snapshot {
+    double* f[15];
+    uint32_t* tag;
+};
+
+void snap_take(sph_ctx* c, char*& p, Snapshot& sn) {
+    for (int k = 0; k < 15; ++k) sn.f[k] = (double*)arena_take(p, (size_t)c->N * 8);
+    sn.tag = (uint32_t*)arena_take(p, (size_t)c->N * 4);
+}
+
+void set_fields(const ParticleSet& S, double* const* f_in, double** f_out) {
+    double* fs[15] = {S.x[0], S.x[1], S.x[2], S.u[0], S.u[1], S.u[2], S.rho, S.m,
+                      S.arho, S.a[0], S.a[1], S.a[2], S.xs[0], S.xs[1], S.xs[2]};
+    (void)f_in;
+    for (int k = 0; k < 15; ++k) f_out[k] = fs[k];
+}
+
+cudaError_t snap_save(sph_ctx* c, const Snapshot& sn) {
+    double* fs[15];
+    set_fields(c->set[c->cur], nullptr, fs);
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 15 && e == cudaSuccess; ++k)
+        e = cudaMemcpyAsync(sn.f[k], fs[k], (size_t)c->N * 8, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sn.tag, c->set[c->cur].tag, (size_t)c->N * 4, cudaMemcpyDeviceToDevice,
+                            c->stream);
+    return e;
+}
+
+cudaError_t snap_load(sph_ctx* c, const Snapshot& sn) {
+    double* fs[15];
+    set_fields(c->set[c->cur], nullptr, fs);
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 15 && e == cudaSuccess; ++k)
+        e = cudaMemcpyAsync(fs[k], sn.f[k], (size_t)c->N * 8, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->set[c->cur].tag, sn.tag, (size_t)c->N * 4, cudaMemcpyDeviceToDevice,
+                            c->stream);
+    return e;
+}
+
+// Taped evaluation: the pair-loop shadow after its density pass, the permutation to the
+// previous order and the tags, all in the evaluation's cell order.
+struct TapeEntry {
+    void* P;
+    void* Q;
+    void* R;
+    uint32_t* perm;
+    uint32_t* tag;
+};
+
+void tape_take(sph_ctx* c, char*& p, TapeEntry& t) {
+    const size_t real = c->dom.precision ? 4 : 8;
+    t.P = arena_take(p, (size_t)c->N * 4 * real);
+    t.Q = arena_take(p, (size_t)c->N * 4 * real);
+    t.R = arena_take(p, (size_t)c->N * real);
+    t.perm = (uint32_t*)arena_take(p, (size_t)c->N * 4);
+    t.tag = (uint32_t*)arena_take(p, (size_t)c->N * 4);
+}
+
+cudaError_t tape_record(sph_ctx* c, const TapeEntry& t) {
+    const size_t real = c->dom.precision ? 4 : 8;
+    const size_t N = (size_t)c->N;
+    cudaError_t e = cudaMemcpyAsync(t.P, c->P, N * 4 * real, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t.Q, c->Q, N * 4 * real, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t.R, c->R, N * real, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(t.perm, c->vals[c->passes & 1], N * 4, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(t.tag, c->set[c->cur].tag, N * 4, cudaMemcpyDeviceToDevice, c->stream);
+    return e;
+}
+
+AdjSet adj_take(sph_ctx* c, char*& p) {
+    AdjSet L{};
+    for (int d = 0; d < 3; ++d) L.x[d] = (double*)arena_take(p, (size_t)c->N * 8);
+    for (int d = 0; d < 3; ++d) L.u[d] = (double*)arena_take(p, (size_t)c->N * 8);
+    L.rho = (double*)arena_take(p, (size_t)c->N * 8);
+    for (int d = 0; d < 3; ++d) L.a[d] = (double*)arena_take(p, (size_t)c->N * 8);
+    for (int d = 0; d < 3; ++d) L.xs[d] = (double*)arena_take(p, (size_t)c->N * 8);
+    return L;
+}
+
+}  // namespace
+
+sph_status sph_backward(sph_ctx* c, const sph_scheme* scheme, double dt, int32_t K,
+                        int32_t ckpt_every, double* dKE_du0, double* dKE_dnu, double* dKE_dalpha) {
+    if (!c) return fail(c, SPH_ERR_INVALID, "ctx is NULL");
+    sph_status s = check_scheme(c, scheme);
+    if (s != SPH_OK) return s;
+    if (scheme->density != SPH_DENSITY_CONTINUITY)
+        return fail(c, SPH_ERR_INVALID, "the adjoint covers the continuity formulation only");
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, SPH_ERR_INVALID, "the adjoint needs a fixed dt > 0");
+    if (K < 0) return fail(c, SPH_ERR_INVALID, "K < 0");
+    int C = ckpt_every;
+    if (C <= 0) C = (int)std::ceil(std::sqrt((double)(K > 0 ? K : 1)));
+    if (C > K && K > 0) C = K;
+    if (C < 1) C = 1;
+    const int nseg = K > 0 ? (K + C - 1) / C : 0;
+    const size_t N = (size_t)c->N;
+    const size_t real = c->dom.precision ? 4 : 8;
+    auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const int pblocks = adjoint_partial_blocks(c->N, c->sms);
+    size_t bytes = 0;
+    bytes += (size_t)(nseg + 1) * (15 * al(N * 8) + al(N * 4));                 // checkpoints + final
+    bytes += (size_t)(C + 1) * (2 * al(N * 4 * real) + al(N * real) + 2 * al(N * 4));  // tape
+    bytes += 2 * 13 * al(N * 8) + 5 * al(N * 8) + 2 * al(N * 4 * real);         // adjoint state
+    bytes += al(N * 8 * 3) + al((size_t)pblocks * 16) + al(sizeof(AdjCtl));
+    void* arena = nullptr;
+    if (c->alloc) arena = c->alloc(bytes, c->user);
+    else if (cudaMalloc(&arena, bytes) != cudaSuccess) arena = nullptr;
+    if (!arena) {
+        cudaGetLastError();
+        return fail(c, SPH_ERR_OOM, "adjoint workspace of " + std::to_string(bytes) + " bytes");
+    }
+    struct Guard {
+        sph_ctx* c;
+        void* p;
+        ~Guard() {
+            cudaStreamSynchronize(c->stream);
+            free_dev(c, p);
+        }
+    } guard{c, arena};
+    char* p = (char*)arena;
+    std::vector<Snapshot> ck(nseg + 1);
+    for (auto& sn : ck) snap_take(c, p, sn);  // ck[nseg] holds the final state
+    std::vector<TapeEntry> tape(C + 1);       // tape[C] holds the initial evaluation
+    for (auto& t : tape) tape_take(c, p, t);
+    AdjSet L[2] = {adj_take(c, p), adj_take(c, p)};
+    double* luh[3];
+    for (int d = 0; d < 3; ++d) luh[d] = (double*)arena_take(p, N * 8);
+    double* rhom = (double*)arena_take(p, N * 8);
+    double* lrho_tot = (double*)arena_take(p, N * 8);
+    void* CA = arena_take(p, N * 4 * real);
+    void* CS = arena_take(p, N * 4 * real);
+    double* d_out = (double*)arena_take(p, N * 8 * 3);
+    double* part = (double*)arena_take(p, (size_t)pblocks * 16);
+    AdjCtl* actl = (AdjCtl*)arena_take(p, sizeof(AdjCtl));
+    CK(cudaMemsetAsync(actl, 0, sizeof(AdjCtl), c->stream));
+    CK(cudaMemsetAsync(d_out, 0, N * 8 * 3, c->stream));
+
+    // ---- forward: initial evaluation (taped) and checkpoints every C steps
+    s = initial_eval(c, scheme, dt);
+    if (s != SPH_OK) return s;
+    CK(cudaMemcpyAsync(&c->ctl->dt, &dt, sizeof dt, cudaMemcpyHostToDevice, c->stream));
+    CK(tape_record(c, tape[C]));
+    if (!c->graph[0] || !same_scheme(*scheme, c->graph_scheme) || c->graph_dt != dt ||
+        c->graph_timed != c->timing) {
+        s = capture_step_graphs(c, scheme, dt);
+        if (s != SPH_OK) return s;
+    }
+    for (int step = 0; step < K; ++step) {
+        if (step % C == 0) CK(snap_save(c, ck[step / C]));
+        CK(cudaGraphLaunch(c->graph[c->cur], c->stream));
+        c->cur ^= 1;
+    }
+    CK(snap_save(c, ck[nseg]));
+    Control ctl_final{};
+    CK(cudaMemcpyAsync(&ctl_final, c->ctl, sizeof ctl_final, cudaMemcpyDeviceToHost, c->stream));
+    s = sync_status(c);
+    if (s != SPH_OK) return s;
+
+    // ---- reverse
+    const StepConst Cst = step_const(c, scheme, dt);
+    const PairConst<float> Kf = pair_const<float>(c, scheme);
+    const PairConst<double> Kd = pair_const<double>(c, scheme);
+    AdjLaunch A{};
+    A.precision = c->dom.precision;
+    A.dim = c->dom.dim;
+    A.kernel = c->dom.kernel;
+    A.n = c->N;
+    A.sms = c->sms;
+    A.maxn = c->maxn;
+    A.dt = dt;
+    A.G = c->G;
+    A.C = Cst;
+    for (int d = 0; d < 3; ++d) A.luh[d] = luh[d];
+    A.rhom = rhom;
+    A.lrho_tot = lrho_tot;
+    A.CA = CA;
+    A.CS = CS;
+    A.keys = c->keys[0];
+    A.off = c->off;
+    A.nl = c->nl;
+    A.cnt = c->cnt;
+    A.part = part;
+    A.actl = actl;
+    A.ctl = c->ctl;
+    int lc = 0;
+    launch_adjoint_terminal(L[lc], c->set[c->cur], c->N, c->dom.dim, c->sms, c->stream);
+    for (int seg = nseg - 1; seg >= 0; --seg) {
+        const int s0 = seg * C, s1 = std::min(K, s0 + C);
+        CK(snap_load(c, ck[seg]));
+        CK(cudaMemsetAsync(&c->ctl->status, 0, sizeof(unsigned), c->stream));
+        CK(cudaMemcpyAsync(&c->ctl->dt, &dt, sizeof dt, cudaMemcpyHostToDevice, c->stream));
+        for (int step = s0; step < s1; ++step) {
+            CK(cudaGraphLaunch(c->graph[c->cur], c->stream));
+            c->cur ^= 1;
+            CK(tape_record(c, tape[step - s0]));
+        }
+        for (int step = s1 - 1; step >= s0; --step) {
+            const TapeEntry& t = tape[step - s0];
+            A.P = t.P;
+            A.Q = t.Q;
+            A.R = t.R;
+            A.perm = t.perm;
+            A.tag = t.tag;
+            A.kick = 1;
+            A.L = L[lc];
+            launch_adjoint_eval(A, Kf, Kd, c->stream);
+            launch_adjoint_scatter(A, L[lc ^ 1], c->stream);
+            lc ^= 1;
+        }
+        CK(cudaGetLastError());
+    }
+    // initial evaluation: (a0, xsph0) = M(x0, u0, rho0), no density update, no kick
+    A.P = tape[C].P;
+    A.Q = tape[C].Q;
+    A.R = tape[C].R;
+    A.perm = tape[C].perm;
+    A.tag = tape[C].tag;
+    A.kick = 0;
+    A.L = L[lc];
+    launch_adjoint_eval(A, Kf, Kd, c->stream);
+    launch_adjoint_to_original(A, d_out, c->stream);
+    CK(cudaGetLastError());
+    AdjCtl actl_h{};
+    CK(cudaMemcpyAsync(&actl_h, actl, sizeof actl_h, cudaMemcpyDeviceToHost, c->stream));
+    if (dKE_du0)
+        CK(cudaMemcpyAsync(dKE_du0, d_out, N * 8 * c->dom.dim, cudaMemcpyDeviceToHost, c->stream));
+    // leave the context in the final state of the K steps
+    CK(snap_load(c, ck[nseg]));
+    CK(cudaMemcpyAsync(c->ctl, &ctl_final, sizeof ctl_final, cudaMemcpyHostToDevice, c->stream));
+    s = sync_status(c);
+    if (s != SPH_OK) return s;
+    c->nbr_valid = false;
+    c->have_rates = true;
+    c->rates_scheme = *scheme;
+    c->hist_at_call = c->steps_total;
+    c->steps_total += (unsigned)K;
+    if (dKE_dnu) *dKE_dnu = actl_h.g_nu;
+    if (dKE_dalpha) *dKE_dalpha = actl_h.g_alpha;
+    return SPH_OK;
 }
 
 sph_status sph_get(sph_ctx* c, int32_t array, const char* prop, double* out) {

@@ -81,6 +81,7 @@ struct PairConst {
     Real av_h2;     // 0.01 h^2
     Real nu4;       // 4 nu
     Real alpha_c0;  // alpha c0
+    Real c0;
     Real xsph;
     int flags;
 };

@@ -71,4 +71,49 @@ void launch_momentum_pass(const PairLaunch& L, const PairConst<float>& Kf,
 // destination)
 int pairs_max_blocks_per_sm(int precision, int pass, int dim, int kernel, int T);
 
+// adjoint.cu: adjoint state (FP64, cell order of the current evaluation)
+struct AdjSet {
+    double* x[3];
+    double* u[3];
+    double* rho;
+    double* a[3];
+    double* xs[3];
+};
+struct AdjCtl {
+    double g_nu, g_alpha;  // running d KE / d nu, d KE / d alpha
+    unsigned ticket;
+};
+// One reversed evaluation on a taped configuration (P, Q, R after its density pass).
+struct AdjLaunch {
+    int precision, dim, kernel, n, sms, kick, maxn;
+    double dt;
+    const void* P;
+    const void* Q;
+    const void* R;
+    const uint32_t* perm;  // taped order -> previous order
+    const uint32_t* tag;   // taped order
+    Grid G;
+    StepConst C;
+    AdjSet L;              // cotangents in the taped order (in: state, out: += x)
+    double* luh[3];        // lambda of the evaluation velocities
+    double* rhom;
+    double* lrho_tot;
+    void* CA;
+    void* CS;
+    uint32_t* keys;
+    uint32_t* off;
+    uint32_t* nl;
+    uint32_t* cnt;
+    double* part;
+    AdjCtl* actl;
+    Control* ctl;
+};
+void launch_adjoint_eval(const AdjLaunch& A, const PairConst<float>& Kf, const PairConst<double>& Kd,
+                         cudaStream_t st);
+void launch_adjoint_scatter(const AdjLaunch& A, const AdjSet& out, cudaStream_t st);
+void launch_adjoint_terminal(const AdjSet& L, const ParticleSet& S, int n, int dim, int sms,
+                             cudaStream_t st);
+void launch_adjoint_to_original(const AdjLaunch& A, double* out, cudaStream_t st);
+int adjoint_partial_blocks(int n, int sms);
+
 }  // namespace sph
