@@ -243,6 +243,32 @@ sph_status sph_kernels_per_step(const sph_ctx* ctx, const sph_scheme* scheme, in
 sph_status sph_backward(sph_ctx* ctx, const sph_scheme* scheme, double dt, int32_t K,
                         int32_t ckpt_every, double* dKE_du0, double* dKE_dnu, double* dKE_dalpha);
 
+/* ---------------------------------------------------------------------------------
+ * Batches: many independent problems of uneven size advanced together in the same
+ * launches (one CUDA graph per step for all of them). Instances share dim, kernel and
+ * precision; each has its own domain (grid), scheme and time step.
+ *
+ * sph_create_batch: domains[k] and arrays_per_instance[k] consecutive entries of `arrays`
+ * describe instance k. Global particle ids (and array indices for sph_get / sph_set)
+ * follow the concatenation of all arrays. Other arguments as in sph_create. */
+sph_status sph_create_batch(const sph_domain* domains, const sph_array_desc* arrays,
+                            const int32_t* arrays_per_instance, int32_t n_instances, void* stream,
+                            sph_alloc_fn alloc, sph_free_fn free_fn, void* alloc_user,
+                            sph_ctx** out);
+
+/* Advance every instance nsteps steps; schemes[k] and dt[k] (dt <= 0: CFL-type step of
+ * that instance) per instance; all instances share the density formulation. The first
+ * call (or a change of schemes or dts) evaluates every instance at its current state.
+ * Same integrator and equations as sph_step. Single-problem calls (sph_step,
+ * sph_eval_rhs, sph_backward, sph_get_cells, sph_get_neighbors, sph_build_neighbors)
+ * return SPH_ERR_STATE on a batch; sph_get, sph_set, sph_set_groups, sph_autotune (scheme
+ * ignored, after a first sph_step_batch), sph_set_timing and sph_phase_times work. */
+sph_status sph_step_batch(sph_ctx* ctx, const sph_scheme* schemes, const double* dt, int32_t nsteps);
+
+/* Diagnostics record (SPH_DIAG_COUNT doubles) of every instance after its last evaluation,
+ * instance-major, into out (n_instances * SPH_DIAG_COUNT doubles, host). */
+sph_status sph_batch_diagnostics(sph_ctx* ctx, double* out);
+
 /* Property of one array (or -1 for all particles) into a host buffer, original order.
  * prop: "x" "y" "z" "u" "v" "w" "rho" "m", or rates of the last evaluation "arho" "ax"
  * "ay" "az" "xsx" "xsy" "xsz". */

@@ -59,7 +59,8 @@ EXPORTS = ("sph_create", "sph_destroy", "sph_last_error", "sph_count", "sph_grid
            "sph_build_neighbors", "sph_get_cells", "sph_get_neighbors", "sph_eval_rhs",
            "sph_step", "sph_step_async", "sph_synchronize", "sph_set_timing", "sph_phase_times",
            "sph_kernels_per_step", "sph_set_groups", "sph_autotune", "sph_backward", "sph_get", "sph_set", "sph_diagnostics", "sph_history",
-           "sph_save_state", "sph_load_state")
+           "sph_save_state", "sph_load_state", "sph_create_batch", "sph_step_batch",
+           "sph_batch_diagnostics")
 
 
 def library_path() -> str:
@@ -101,6 +102,10 @@ def load(build_if_missing: bool = True):
     L.sph_set_groups.argtypes = [ctxp, C.c_int32]
     L.sph_backward.argtypes = [ctxp, C.POINTER(Scheme), C.c_double, C.c_int32, C.c_int32, d, d, d]
     L.sph_autotune.argtypes = [ctxp, C.POINTER(Scheme), i32]
+    L.sph_create_batch.argtypes = [C.POINTER(Domain), C.POINTER(ArrayDesc), i32, C.c_int32, P,
+                                   ALLOC_FN, FREE_FN, P, C.POINTER(ctxp)]
+    L.sph_step_batch.argtypes = [ctxp, C.POINTER(Scheme), d, C.c_int32]
+    L.sph_batch_diagnostics.argtypes = [ctxp, d]
     L.sph_get.argtypes = [ctxp, C.c_int32, C.c_char_p, d]
     L.sph_set.argtypes = [ctxp, C.c_int32, C.c_char_p, d]
     L.sph_diagnostics.argtypes = [ctxp, d]
@@ -325,9 +330,10 @@ class Simulation:
     def set_groups(self, momentum_lanes: int):
         self._check(self._L.sph_set_groups(self._ctx, int(momentum_lanes)))
 
-    def autotune(self, scheme: Scheme) -> int:
+    def autotune(self, scheme: Optional[Scheme]) -> int:
         out = C.c_int32()
-        self._check(self._L.sph_autotune(self._ctx, C.byref(scheme), C.byref(out)))
+        self._check(self._L.sph_autotune(self._ctx, None if scheme is None else C.byref(scheme),
+                                         C.byref(out)))
         return int(out.value)
 
     def backward(self, scheme: Scheme, dt: float, K: int, ckpt_every: int = 0):
@@ -383,3 +389,108 @@ class Simulation:
             return
         buf = C.create_string_buffer(blob, len(blob))
         self._check(self._L.sph_load_state(self._ctx, buf, len(blob)))
+
+
+def _domain_of(wl, precision=None) -> Domain:
+    dom = Domain()
+    dom.dim, dom.kernel, dom.h = wl.dim, wl.kernel, wl.h
+    dom.precision = wl.precision if precision is None else precision
+    for k in range(3):
+        dom.periodic[k] = int(wl.periodic[k])
+        dom.lo[k] = float(wl.lo[k])
+        dom.hi[k] = float(wl.hi[k])
+    return dom
+
+
+class BatchSimulation(Simulation):
+    """Many independent problems (a batch context) advanced in the same launches."""
+
+    def __init__(self, workloads: Sequence, precision: Optional[int] = None, stream=None,
+                 torch_alloc: bool = True):
+        import torch
+        self._L = load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the WCSPH library runs on the GPU only")
+        self.workloads = list(workloads)
+        self.ninst = len(self.workloads)
+        self.dim = self.workloads[0].dim
+        doms = (Domain * self.ninst)(*[_domain_of(w, precision) for w in self.workloads])
+        flat = [a for w in self.workloads for a in w.arrays]
+        per = (C.c_int32 * self.ninst)(*[len(w.arrays) for w in self.workloads])
+        descs = (ArrayDesc * len(flat))()
+        keep = []
+        for a, arr in enumerate(flat):
+            dsc = descs[a]
+            name = arr.name.encode()
+            keep.append(name)
+            dsc.name, dsc.role, dsc.n = name, int(arr.role), int(arr.n)
+            for k in ("x", "y", "z", "u", "v", "w", "rho", "m"):
+                v = _f64(getattr(arr, k))
+                keep.append(v)
+                setattr(dsc, k, _dptr(v))
+        self._stream_obj = torch.cuda.Stream() if stream is None else None
+        handle = self._stream_obj.cuda_stream if stream is None else int(getattr(stream, "cuda_stream", stream))
+        self._alloc = None
+        alloc_fn, free_fn = ALLOC_FN(), FREE_FN()
+        if torch_alloc:
+            self._alloc = _TorchAllocator(torch.cuda.current_device(), handle)
+            alloc_fn, free_fn = self._alloc.alloc, self._alloc.free
+        ctx = C.c_void_p()
+        st = self._L.sph_create_batch(doms, descs, per, self.ninst, C.c_void_p(handle), alloc_fn,
+                                      free_fn, None, C.byref(ctx))
+        if st != 0:
+            raise SphError(st, self._L.sph_last_error(None).decode())
+        self._ctx = ctx
+        self.n = self.count(-1)
+        sizes = [sum(a.n for a in w.arrays) for w in self.workloads]
+        self.bounds = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+
+    def step_batch(self, schemes: Sequence[Scheme], dts: Sequence[float], nsteps: int = 1):
+        arr = (Scheme * self.ninst)(*schemes)
+        d = np.ascontiguousarray(dts, dtype=np.float64)
+        self._check(self._L.sph_step_batch(self._ctx, arr, _dptr(d), int(nsteps)))
+
+    def batch_diagnostics(self) -> np.ndarray:
+        out = np.zeros((self.ninst, DIAG_COUNT))
+        self._check(self._L.sph_batch_diagnostics(self._ctx, _dptr(out)))
+        return out
+
+    def instance_state(self, k: int) -> dict:
+        st = self.state()
+        b, e = self.bounds[k], self.bounds[k + 1]
+        return {key: v[b:e] for key, v in st.items()}
+
+
+def final_kinetic_energy(sim: "Simulation", scheme: Scheme, dt: float, K: int, u0, nu, alpha=None,
+                         ckpt_every: int = 0):
+    """KE after K steps as a differentiable function of the initial fluid velocities ``u0``
+    (torch tensor [dim, n], original order) and the viscosities ``nu`` (and ``alpha``), via a
+    torch.autograd.Function whose backward is the hand-written adjoint (sph_backward).
+    Sets the simulation's velocities to u0 and leaves it K steps later."""
+    import torch
+
+    class _FinalKE(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, u0_t, nu_t, alpha_t):
+            sch = Scheme.from_buffer_copy(scheme)
+            sch.nu = float(nu_t)
+            sch.alpha = float(alpha_t)
+            u = u0_t.detach().to("cpu", torch.float64).numpy()
+            for k, name in enumerate(("u", "v", "w")[:sim.dim]):
+                sim.set(name, u[k])
+            gu, gnu, gal = sim.backward(sch, dt, K, ckpt_every)
+            ke = float(sim.diagnostics()[2])
+            ctx.save_for_backward(torch.as_tensor(gu, dtype=u0_t.dtype, device=u0_t.device),
+                                  torch.tensor(gnu, dtype=nu_t.dtype, device=nu_t.device),
+                                  torch.tensor(gal, dtype=alpha_t.dtype, device=alpha_t.device))
+            return torch.tensor(ke, dtype=torch.float64, device=u0_t.device)
+
+        @staticmethod
+        def backward(ctx, g):
+            gu, gnu, gal = ctx.saved_tensors
+            return g * gu, g * gnu, g * gal
+
+    if alpha is None:
+        import torch as _t
+        alpha = _t.tensor(float(scheme.alpha), dtype=_t.float64)
+    return _FinalKE.apply(u0, nu, alpha)

@@ -91,11 +91,25 @@ struct sph_ctx {
     bool timed_step_ran = false;
     cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 
+    // batch of independent instances (ninst > 0)
+    int ninst = 0;
+    std::vector<sph_domain> doms;     // per instance
+    std::vector<Grid> grids;          // per instance
+    std::vector<uint32_t> id_bounds_h, cell_bounds_h;
+    void* d_tab = nullptr;            // Inst<Real>[ninst]
+    uint32_t* d_id_bounds = nullptr;
+    uint32_t* d_cell_bounds = nullptr;
+    double* idt = nullptr;
+    double* it = nullptr;
+    double* irec = nullptr;
+    uint32_t* pcount = nullptr;
+    std::vector<sph_scheme> batch_schemes;
+    std::vector<double> batch_dt;
+
     // captured step graphs, one per parity of `cur`
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
-    sph_scheme graph_scheme{};
-    double graph_dt = 0.0;
     bool graph_timed = false;
+    std::vector<unsigned char> tab_host;  // copy of the device instance table
 };
 
 namespace {
@@ -166,11 +180,10 @@ sph_status make_grid(sph_ctx* c, const sph_domain& D, Grid* G) {
 }
 
 template <class Real>
-PairConst<Real> pair_const(const sph_ctx* c, const sph_scheme* s) {
-    const sph_domain& D = c->dom;
+PairConst<Real> pair_const_dg(const sph_domain& D, const Grid& Gr, const sph_scheme* s) {
     PairConst<Real> K{};
     for (int d = 0; d < 3; ++d) {
-        K.L[d] = (Real)(c->G.L[d]);
+        K.L[d] = (Real)(Gr.L[d]);
         K.halfL[d] = K.L[d] * (Real)0.5;
     }
     const Real kh = (Real)support_factor(D.kernel) * (Real)D.h;
@@ -198,21 +211,30 @@ PairConst<Real> pair_const(const sph_ctx* c, const sph_scheme* s) {
     return K;
 }
 
-StepConst step_const(const sph_ctx* c, const sph_scheme* s, double dt_fixed) {
+template <class Real>
+PairConst<Real> pair_const(const sph_ctx* c, const sph_scheme* s) {
+    return pair_const_dg<Real>(c->dom, c->G, s);
+}
+
+StepConst step_const_d(const sph_domain& D, const sph_scheme* s, double dt_fixed) {
     StepConst C{};
     C.rho0 = s->rho0;
     C.inv_rho0 = 1.0 / s->rho0;
     C.gamma = s->gamma;
     C.B = s->c0 * s->c0 * s->rho0 / s->gamma;
     for (int d = 0; d < 3; ++d) C.g[d] = s->g[d];
-    C.h = c->dom.h;
+    C.h = D.h;
     C.c0 = s->c0;
     C.nu = s->nu;
     C.dt_fixed = dt_fixed;
     C.continuity = s->density == SPH_DENSITY_CONTINUITY;
     C.gamma7 = s->gamma == 7.0;
-    C.precision = c->dom.precision;
+    C.precision = D.precision;
     return C;
+}
+
+StepConst step_const(const sph_ctx* c, const sph_scheme* s, double dt_fixed) {
+    return step_const_d(c->dom, s, dt_fixed);
 }
 
 sph_status check_scheme(sph_ctx* c, const sph_scheme* s) {
@@ -283,52 +305,104 @@ void mark(sph_ctx* c, int k, bool timed) {
     if (timed) cudaEventRecordWithFlags(c->ev[k], c->stream, cudaEventRecordExternal);
 }
 
-void enqueue_build(sph_ctx* c, const StepConst& C, int drift, int kick, int carry_rates,
-                   bool timed = false) {
+int ntab(const sph_ctx* c) { return c->ninst ? c->ninst : 1; }
+
+// Launch description of the context's current state (instance table, buffers).
+StepLaunch step_launch(sph_ctx* c, int kick) {
+    StepLaunch L{};
+    L.precision = c->dom.precision;
+    L.dim = c->dom.dim;
+    L.kernel = c->dom.kernel;
+    L.n = c->N;
+    L.sms = c->sms;
+    L.ninst = ntab(c);
+    L.kick = kick;
+    L.maxn = c->maxn;
+    L.group_m = c->group_m;
+    L.grid_d = c->grid_d;
+    L.grid_m = c->grid_m;
+    L.finalize = c->ninst == 0;
+    L.tab = c->d_tab;
+    L.id_bounds = c->d_id_bounds;
+    L.cell_bounds = c->d_cell_bounds;
+    L.idt = c->ninst ? c->idt : &c->ctl->dt;
+    L.it = c->it;
+    L.irec = c->irec;
+    L.Sin = c->set[c->cur];
+    L.S = c->set[c->cur];
+    L.P = c->P;
+    L.Q = c->Q;
+    L.R = c->R;
+    L.skeys = c->skeys;
+    L.off = c->off;
+    L.nl = c->nl;
+    L.cnt = c->cnt;
+    L.pcount = c->pcount;
+    L.pm = c->pm;
+    L.pd = c->pd;
+    L.history = c->history;
+    L.ctl = c->ctl;
+    return L;
+}
+
+// Neighbour build: [drift] + keys, radix sort, gather into the other set (+EOS shadow),
+// cell table. Enqueued on the context stream (capturable); constants from the table.
+void enqueue_build(sph_ctx* c, int drift, int kick, int carry_rates, bool timed = false) {
     cudaStream_t st = c->stream;
     cudaMemsetAsync(&c->ctl->outside, 0, sizeof(unsigned), st);
+    StepLaunch L = step_launch(c, kick);
     mark(c, 0, timed);
-    launch_drift_keys(c->set[c->cur], c->N, c->G, C, c->ctl, drift, c->keys[0], st, c->sms);
+    launch_drift_keys(L, drift, c->keys[0], st);
     mark(c, 1, timed);
-    int b = launch_radix_sort(c->keys, c->vals, c->N, c->passes, c->hist, c->ctl, st);
+    const int b = launch_radix_sort(c->keys, c->vals, c->N, c->passes, c->hist, c->ctl, st);
     c->skeys = c->keys[b];
     mark(c, 2, timed);
     const int nxt = c->cur ^ 1;
-    launch_reorder(c->dom.precision, c->set[c->cur], c->set[nxt], c->vals[b], c->N, c->dom.dim, C,
-                   c->ctl, kick, carry_rates, c->P, c->Q, c->R, st, c->sms);
+    L.S = c->set[nxt];
+    L.skeys = c->skeys;
+    launch_reorder(L, c->vals[b], carry_rates, st);
     mark(c, 3, timed);
     launch_cell_offsets(c->skeys, c->N, c->G.ncells, c->off, c->ctl, st, c->sms);
     mark(c, 4, timed);
     c->cur = nxt;
 }
 
-void enqueue_eval(sph_ctx* c, const sph_scheme* s, const StepConst& C, int kick) {
-    PairLaunch L{};
-    L.precision = c->dom.precision;
-    L.dim = c->dom.dim;
-    L.kernel = c->dom.kernel;
-    L.kick = kick;
-    L.n = c->N;
-    L.group_d = c->group_d;
-    L.group_m = c->group_m;
-    L.grid_d = c->grid_d;
-    L.grid_m = c->grid_m;
-    L.P = c->P;
-    L.Q = c->Q;
-    L.R = c->R;
-    L.skeys = c->skeys;
-    L.off = c->off;
-    L.G = c->G;
-    L.C = C;
-    L.S = c->set[c->cur];
-    L.ctl = c->ctl;
-    L.nl = c->nl;
-    L.cnt = c->cnt;
-    L.maxn = c->maxn;
-    L.pm = c->pm;
-    L.pd = c->pd;
-    L.history = c->history;
-    launch_pairs(L, pair_const<float>(c, s), pair_const<double>(c, s), c->stream);
+void enqueue_eval(sph_ctx* c, int kick) { launch_pairs(step_launch(c, kick), c->stream); }
+
+// Instance table on the device: one entry (a single problem: its domain, scheme, dt) or
+// one per batch instance. Uploaded outside graph capture when it changes.
+template <class Real>
+void table_bytes(const sph_ctx* c, const sph_scheme* schemes, const double* dts,
+                 std::vector<unsigned char>& bytes) {
+    const int nt = ntab(c);
+    bytes.assign((size_t)nt * sizeof(Inst<Real>), 0);
+    Inst<Real>* T = (Inst<Real>*)bytes.data();
+    for (int k = 0; k < nt; ++k) {
+        const sph_domain& D = c->ninst ? c->doms[k] : c->dom;
+        const Grid& Gk = c->ninst ? c->grids[k] : c->G;
+        Inst<Real> I{};
+        I.G = Gk;
+        I.K = pair_const_dg<Real>(D, Gk, &schemes[k]);
+        I.C = step_const_d(D, &schemes[k], dts[k] > 0.0 ? dts[k] : 0.0);
+        I.cell_base = c->ninst ? c->cell_bounds_h[k] : 0u;
+        I.cell_base_end = c->ninst ? c->cell_bounds_h[k + 1] : (uint32_t)c->G.ncells;
+        T[k] = I;
+    }
+}
+
+sph_status upload_table(sph_ctx* c, const sph_scheme* schemes, const double* dts) {
+    std::vector<unsigned char> bytes;
+    if (c->dom.precision) table_bytes<float>(c, schemes, dts, bytes);
+    else table_bytes<double>(c, schemes, dts, bytes);
+    if (bytes == c->tab_host) return SPH_OK;
+    CK(cudaMemcpyAsync(c->d_tab, bytes.data(), bytes.size(), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->tab_host.swap(bytes);
+    return SPH_OK;
+}
+
+sph_status upload_single(sph_ctx* c, const sph_scheme* s, double dt_fixed) {
+    return upload_table(c, s, &dt_fixed);
 }
 
 sph_status sync_status(sph_ctx* c) {
@@ -394,11 +468,12 @@ sph_status ensure_list_capacity(sph_ctx* c) {
 
 // Initial right-hand side at the current state (no drift, no kick).
 sph_status initial_eval(sph_ctx* c, const sph_scheme* s, double dt_fixed) {
-    StepConst C = step_const(c, s, dt_fixed);
-    enqueue_build(c, C, 0, 0, 0);
-    sph_status st = ensure_list_capacity(c);
+    sph_status st = upload_single(c, s, dt_fixed);
     if (st != SPH_OK) return st;
-    enqueue_eval(c, s, C, 0);
+    enqueue_build(c, 0, 0, 0);
+    st = ensure_list_capacity(c);
+    if (st != SPH_OK) return st;
+    enqueue_eval(c, 0);
     CK(cudaGetLastError());
     c->have_rates = true;
     c->nbr_valid = true;
@@ -406,24 +481,24 @@ sph_status initial_eval(sph_ctx* c, const sph_scheme* s, double dt_fixed) {
     return SPH_OK;
 }
 
-sph_status capture_step_graphs(sph_ctx* c, const sph_scheme* s, double dt) {
+// Captures one step for each parity of the set in use. The constants live in the device
+// table, so the graphs stay valid when a scheme or dt changes; they are recaptured when
+// the buffers, the tile shape or the timing mode change (drop_graphs).
+sph_status capture_step_graphs(sph_ctx* c) {
     drop_graphs(c);
-    StepConst C = step_const(c, s, dt);
     const int cur0 = c->cur;
     for (int k = 0; k < 2; ++k) {
         c->cur = cur0 ^ k;
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-        enqueue_build(c, C, 1, 1, 0, c->timing);
-        enqueue_eval(c, s, C, 1);
+        enqueue_build(c, 1, 1, 0, c->timing);
+        enqueue_eval(c, 1);
         mark(c, 5, c->timing);
         cudaError_t e = cudaStreamEndCapture(c->stream, &g);
         if (e != cudaSuccess) {
             c->cur = cur0;
             return cuda_fail(c, e, "cudaStreamEndCapture");
         }
-        const int slot = c->cur ^ 1;  // graph launched when cur == slot (before the step)
-        (void)slot;
         cudaGraphExec_t ex = nullptr;
         e = cudaGraphInstantiate(&ex, g, 0);
         cudaGraphDestroy(g);
@@ -434,8 +509,6 @@ sph_status capture_step_graphs(sph_ctx* c, const sph_scheme* s, double dt) {
         c->graph[cur0 ^ k] = ex;
     }
     c->cur = cur0;
-    c->graph_scheme = *s;
-    c->graph_dt = dt;
     c->graph_timed = c->timing;
     return SPH_OK;
 }
@@ -483,8 +556,9 @@ sph_status ensure_neighbors(sph_ctx* c) {
     dummy.rho0 = 1.0;
     dummy.c0 = 1.0;
     dummy.gamma = 7.0;
-    StepConst C = step_const(c, c->have_rates ? &c->rates_scheme : &dummy, 0.0);
-    enqueue_build(c, C, 0, 0, c->have_rates ? 1 : 0);
+    sph_status st = upload_single(c, c->have_rates ? &c->rates_scheme : &dummy, 0.0);
+    if (st != SPH_OK) return st;
+    enqueue_build(c, 0, 0, c->have_rates ? 1 : 0);
     CK(cudaGetLastError());
     c->nbr_valid = true;
     return SPH_OK;
@@ -496,18 +570,23 @@ namespace sph {
 void set_global_error(const std::string& msg) { g_create_error = msg; }
 }  // namespace sph
 
-extern "C" {
+extern "C" void sph_destroy(sph_ctx* c);
 
-sph_status sph_create(const sph_domain* domain, const sph_array_desc* arrays, int32_t n_arrays,
-                      void* stream, sph_alloc_fn alloc, sph_free_fn free_fn, void* alloc_user,
-                      sph_ctx** out) {
+namespace {
+
+// Context creation for one problem (ninst = 0) or a batch of ninst instances, whose
+// arrays follow each other (arrays_per_inst[k] arrays for instance k).
+sph_status create_impl(const sph_domain* domains, int ninst, const sph_array_desc* arrays,
+                       const int32_t* arrays_per_inst, int32_t n_arrays, void* stream,
+                       sph_alloc_fn alloc, sph_free_fn free_fn, void* alloc_user, sph_ctx** out) {
     if (!out) return fail(nullptr, SPH_ERR_INVALID, "out is NULL");
     *out = nullptr;
-    if (!domain || !arrays || n_arrays < 1) return fail(nullptr, SPH_ERR_INVALID, "no arrays");
+    if (!domains || !arrays || n_arrays < 1) return fail(nullptr, SPH_ERR_INVALID, "no arrays");
     if ((alloc == nullptr) != (free_fn == nullptr))
         return fail(nullptr, SPH_ERR_INVALID, "give both allocator callbacks or neither");
     sph_ctx* c = new (std::nothrow) sph_ctx();
     if (!c) return fail(nullptr, SPH_ERR_OOM, "host allocation failed");
+    const sph_domain* domain = &domains[0];
     c->dom = *domain;
     Grid G{};
     sph_status s = make_grid(c, *domain, &G);
@@ -517,6 +596,48 @@ sph_status sph_create(const sph_domain* domain, const sph_array_desc* arrays, in
         return s;
     }
     c->G = G;
+    if (ninst > 0) {
+        // per-instance grids; global cell ids are consecutive per instance
+        c->ninst = ninst;
+        c->doms.assign(domains, domains + ninst);
+        c->grids.resize(ninst);
+        c->cell_bounds_h.assign(1, 0);
+        double total = 0.0;
+        int na = 0;
+        for (int k = 0; k < ninst; ++k) {
+            const sph_domain& D = domains[k];
+            if (D.dim != domain->dim || D.kernel != domain->kernel || D.precision != domain->precision) {
+                g_create_error = "batch instances must share dim, kernel and precision";
+                delete c;
+                return SPH_ERR_INVALID;
+            }
+            s = make_grid(c, D, &c->grids[k]);
+            if (s != SPH_OK) {
+                g_create_error = "instance " + std::to_string(k) + ": " + c->err;
+                delete c;
+                return s;
+            }
+            total += c->grids[k].ncells;
+            if (total > 2147483000.0) {
+                g_create_error = "too many cells in the batch";
+                delete c;
+                return SPH_ERR_INVALID;
+            }
+            c->cell_bounds_h.push_back((uint32_t)total);
+            if (!arrays_per_inst || arrays_per_inst[k] < 1) {
+                g_create_error = "every instance needs at least one array";
+                delete c;
+                return SPH_ERR_INVALID;
+            }
+            na += arrays_per_inst[k];
+        }
+        if (na != n_arrays) {
+            g_create_error = "arrays_per_instance does not add up to the array count";
+            delete c;
+            return SPH_ERR_INVALID;
+        }
+        c->G.ncells = (int)total;
+    }
     c->arr_off.assign(1, 0);
     for (int a = 0; a < n_arrays; ++a) {
         const sph_array_desc& A = arrays[a];
@@ -535,6 +656,17 @@ sph_status sph_create(const sph_domain* domain, const sph_array_desc* arrays, in
         return SPH_ERR_INVALID;
     }
     c->N = (int)c->arr_off.back();
+    if (ninst > 0) {
+        c->id_bounds_h.assign(1, 0);
+        int a = 0;
+        for (int k = 0; k < ninst; ++k) {
+            a += arrays_per_inst[k];
+            c->id_bounds_h.push_back((uint32_t)c->arr_off[a]);
+        }
+    } else {  // a single problem is a table of one instance
+        c->id_bounds_h = {0u, (uint32_t)c->N};
+        c->cell_bounds_h = {0u, (uint32_t)c->G.ncells};
+    }
     c->alloc = alloc;
     c->free_fn = free_fn;
     c->user = alloc_user;
@@ -557,7 +689,7 @@ sph_status sph_create(const sph_domain* domain, const sph_array_desc* arrays, in
         }
         c->own_stream = true;
     }
-    c->passes = radix_passes(G.ncells);
+    c->passes = radix_passes(c->G.ncells);  // global cell ids of all instances
     if (c->passes < 1) c->passes = 1;
     c->grid_cap = 1;
     for (int pass = 0; pass < 2; ++pass)
@@ -580,7 +712,7 @@ sph_status sph_create(const sph_domain* domain, const sph_array_desc* arrays, in
     bytes += 2 * (15 * al(N * 8) + al(N * 4));                 // two particle sets
     bytes += 2 * al(N * 4 * real) + al(N * real);              // shadow P, Q, R
     bytes += 4 * al(N * 4);                                    // keys, vals
-    bytes += al(((size_t)G.ncells + 1) * 4);                   // cell offsets
+    bytes += al(((size_t)c->G.ncells + 1) * 4);                // cell offsets
     bytes += al(radix_hist_words(c->N) * 4);                   // radix histograms
     bytes += al((size_t)c->grid_cap * 8 * 8) + al((size_t)c->grid_cap * 4 * 8);  // partials
     bytes += al(N * 4);                                        // neighbour-list lengths
@@ -588,6 +720,10 @@ sph_status sph_create(const sph_domain* domain, const sph_array_desc* arrays, in
     bytes += al((size_t)HIST_CAP * DIAG_N * 8);                // history ring
     const size_t io_bytes = al(N * 4) + 2 * al(N * 8 + 8);     // io scratch
     bytes += io_bytes;
+    const size_t inst_bytes = domain->precision == SPH_PREC_FP32 ? sizeof(Inst<float>) : sizeof(Inst<double>);
+    const size_t nt = ninst > 0 ? (size_t)ninst : 1;
+    bytes += al(nt * inst_bytes) + 2 * al((nt + 1) * 4);        // instance table, bounds
+    if (ninst > 0) bytes += 2 * al(nt * 8) + al(nt * DIAG_N * 8) + al(N * 8);
     c->arena_bytes = bytes;
     if (alloc) c->arena = alloc(bytes, alloc_user);
     else if (cudaMalloc(&c->arena, bytes) != cudaSuccess) c->arena = nullptr;
@@ -615,7 +751,7 @@ sph_status sph_create(const sph_domain* domain, const sph_array_desc* arrays, in
     c->R = arena_take(p, N * real);
     for (int k = 0; k < 2; ++k) c->keys[k] = (uint32_t*)arena_take(p, N * 4);
     for (int k = 0; k < 2; ++k) c->vals[k] = (uint32_t*)arena_take(p, N * 4);
-    c->off = (uint32_t*)arena_take(p, ((size_t)G.ncells + 1) * 4);
+    c->off = (uint32_t*)arena_take(p, ((size_t)c->G.ncells + 1) * 4);
     c->hist = (uint32_t*)arena_take(p, radix_hist_words(c->N) * 4);
     c->pm = (double*)arena_take(p, (size_t)c->grid_cap * 8 * 8);
     c->pd = (double*)arena_take(p, (size_t)c->grid_cap * 4 * 8);
@@ -624,6 +760,15 @@ sph_status sph_create(const sph_domain* domain, const sph_array_desc* arrays, in
     c->history = (double*)arena_take(p, (size_t)HIST_CAP * DIAG_N * 8);
     c->io = arena_take(p, io_bytes);
     c->skeys = c->keys[0];
+    c->d_tab = arena_take(p, nt * inst_bytes);
+    c->d_id_bounds = (uint32_t*)arena_take(p, (nt + 1) * 4);
+    c->d_cell_bounds = (uint32_t*)arena_take(p, (nt + 1) * 4);
+    if (ninst > 0) {
+        c->idt = (double*)arena_take(p, (size_t)ninst * 8);
+        c->it = (double*)arena_take(p, (size_t)ninst * 8);
+        c->irec = (double*)arena_take(p, (size_t)ninst * DIAG_N * 8);
+        c->pcount = (uint32_t*)arena_take(p, N * 8);
+    }
 
     // ---- upload
     sph_status rc = SPH_OK;
@@ -676,9 +821,29 @@ sph_status sph_create(const sph_domain* domain, const sph_array_desc* arrays, in
         }
         if (ue == cudaSuccess) ue = cudaMemsetAsync(c->ctl, 0, sizeof(Control), c->stream);
         if (ue == cudaSuccess) ue = cudaMemsetAsync(c->history, 0, (size_t)HIST_CAP * DIAG_N * 8, c->stream);
-        if (ue == cudaSuccess) {
+        if (ue == cudaSuccess && ninst == 0) {
             launch_wrap_all(c->set[0], c->N, c->G, c->stream, c->sms);
             ue = cudaGetLastError();
+        }
+        for (int k = 0; k < ninst && ue == cudaSuccess; ++k) {  // each instance in its box
+            ParticleSet sub = c->set[0];
+            const uint32_t f = c->id_bounds_h[k];
+            for (int d = 0; d < 3; ++d) sub.x[d] += f;
+            launch_wrap_all(sub, (int)(c->id_bounds_h[k + 1] - f), c->grids[k], c->stream, c->sms);
+            ue = cudaGetLastError();
+        }
+        if (ue == cudaSuccess) {
+            ue = cudaMemcpyAsync(c->d_id_bounds, c->id_bounds_h.data(), (nt + 1) * 4,
+                                 cudaMemcpyHostToDevice, c->stream);
+            if (ue == cudaSuccess)
+                ue = cudaMemcpyAsync(c->d_cell_bounds, c->cell_bounds_h.data(), (nt + 1) * 4,
+                                     cudaMemcpyHostToDevice, c->stream);
+            if (ue == cudaSuccess) ue = cudaStreamSynchronize(c->stream);
+        }
+        if (ninst > 0 && ue == cudaSuccess) {
+            if (ue == cudaSuccess) ue = cudaMemsetAsync(c->irec, 0, (size_t)ninst * DIAG_N * 8, c->stream);
+            if (ue == cudaSuccess) ue = cudaMemsetAsync(c->it, 0, (size_t)ninst * 8, c->stream);
+            if (ue == cudaSuccess) ue = cudaStreamSynchronize(c->stream);
         }
         if (ue == cudaSuccess) ue = cudaStreamSynchronize(c->stream);
         if (ue != cudaSuccess) {
@@ -692,6 +857,135 @@ sph_status sph_create(const sph_domain* domain, const sph_array_desc* arrays, in
     }
     *out = c;
     return SPH_OK;
+}
+
+// ---------------------------------------------------------------- batches
+sph_status grow_list(sph_ctx* c, int want) {
+    void* p = nullptr;
+    const size_t bytes = (size_t)want * c->N * 4;
+    if (c->alloc) p = c->alloc(bytes, c->user);
+    else if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+    if (!p) {
+        cudaGetLastError();
+        return fail(c, SPH_ERR_OOM, "neighbour list of " + std::to_string(bytes) + " bytes");
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    free_dev(c, c->nl);
+    c->nl = (uint32_t*)p;
+    c->maxn = want;
+    drop_graphs(c);
+    return SPH_OK;
+}
+
+// Initial evaluation of every instance; the neighbour list grows until it holds the
+// largest neighbourhood twice over (+32).
+sph_status batch_initial_eval(sph_ctx* c) {
+    if (!c->nl) {
+        sph_status s = grow_list(c, c->dom.dim == 2 ? 64 : 256);
+        if (s != SPH_OK) return s;
+    }
+    enqueue_build(c, 0, 0, 0);
+    for (int attempt = 0; attempt < 8; ++attempt) {
+        enqueue_eval(c, 0);
+        unsigned status = 0;
+        CK(cudaMemcpyAsync(&status, &c->ctl->status, sizeof status, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        if (!(status & ST_CAPACITY)) break;
+        CK(cudaMemsetAsync(&c->ctl->status, 0, sizeof(unsigned), c->stream));
+        sph_status s = grow_list(c, c->maxn * 2);
+        if (s != SPH_OK) return s;
+    }
+    std::vector<uint32_t> counts(c->N);
+    CK(cudaMemcpyAsync(counts.data(), c->cnt, (size_t)c->N * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    uint32_t mx = 0;
+    for (uint32_t v : counts) mx = v > mx ? v : mx;
+    if ((uint32_t)c->maxn < 2 * mx + 32) {
+        sph_status s = grow_list(c, (int)((2 * mx + 32 + 31) / 32 * 32));
+        if (s != SPH_OK) return s;
+    }
+    c->have_rates = true;
+    c->nbr_valid = true;
+    return SPH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sph_status sph_step_batch(sph_ctx* c, const sph_scheme* schemes, const double* dt, int32_t nsteps) {
+    if (!c) return fail(c, SPH_ERR_INVALID, "ctx is NULL");
+    if (c->ninst == 0) return fail(c, SPH_ERR_STATE, "not a batch context");
+    if (!schemes || !dt || nsteps < 0) return fail(c, SPH_ERR_INVALID, "bad arguments");
+    bool changed = (int)c->batch_schemes.size() != c->ninst;
+    for (int k = 0; k < c->ninst; ++k) {
+        sph_status s = check_scheme(c, &schemes[k]);
+        if (s != SPH_OK) return fail(c, s, "instance " + std::to_string(k) + ": " + c->err);
+        if (schemes[k].density != schemes[0].density)
+            return fail(c, SPH_ERR_INVALID, "instances must share the density formulation");
+        if (!std::isfinite(dt[k])) return fail(c, SPH_ERR_INVALID, "dt is not finite");
+        if (!changed && (!same_scheme(schemes[k], c->batch_schemes[k]) || c->batch_dt[k] != dt[k]))
+            changed = true;
+    }
+    if (changed) {
+        c->batch_schemes.assign(schemes, schemes + c->ninst);
+        c->batch_dt.assign(dt, dt + c->ninst);
+        sph_status s = upload_table(c, schemes, dt);
+        if (s != SPH_OK) return s;
+        c->have_rates = false;
+    }
+    c->hist_at_call = c->steps_total;
+    if (!c->have_rates) {
+        sph_status s = batch_initial_eval(c);
+        if (s != SPH_OK) return s;
+    }
+    for (int k = 0; k < c->ninst; ++k)
+        if (dt[k] > 0.0)
+            CK(cudaMemcpyAsync(&c->idt[k], &dt[k], sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if (nsteps > 0) {
+        if (!c->graph[0] || c->graph_timed != c->timing) {
+            sph_status s = capture_step_graphs(c);
+            if (s != SPH_OK) return s;
+        }
+        for (int k = 0; k < nsteps; ++k) {
+            CK(cudaGraphLaunch(c->graph[c->cur], c->stream));
+            c->cur ^= 1;
+        }
+        c->skeys = c->keys[c->passes & 1];
+        c->steps_total += (unsigned)nsteps;
+        if (c->timing) c->timed_step_ran = true;
+    }
+    return sync_status(c);
+}
+
+sph_status sph_batch_diagnostics(sph_ctx* c, double* out) {
+    if (!c || !out) return fail(c, SPH_ERR_INVALID, "NULL argument");
+    if (c->ninst == 0) return fail(c, SPH_ERR_STATE, "not a batch context");
+    CK(cudaMemcpyAsync(out, c->irec, (size_t)c->ninst * DIAG_N * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return SPH_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+sph_status sph_create(const sph_domain* domain, const sph_array_desc* arrays, int32_t n_arrays,
+                      void* stream, sph_alloc_fn alloc, sph_free_fn free_fn, void* alloc_user,
+                      sph_ctx** out) {
+    return create_impl(domain, 0, arrays, nullptr, n_arrays, stream, alloc, free_fn, alloc_user, out);
+}
+
+sph_status sph_create_batch(const sph_domain* domains, const sph_array_desc* arrays,
+                            const int32_t* arrays_per_instance, int32_t n_instances, void* stream,
+                            sph_alloc_fn alloc, sph_free_fn free_fn, void* alloc_user,
+                            sph_ctx** out) {
+    if (n_instances < 1) return fail(nullptr, SPH_ERR_INVALID, "n_instances < 1");
+    int32_t na = 0;
+    if (arrays_per_instance)
+        for (int k = 0; k < n_instances; ++k) na += arrays_per_instance[k];
+    return create_impl(domains, n_instances, arrays, arrays_per_instance, na, stream, alloc, free_fn,
+                       alloc_user, out);
 }
 
 void sph_destroy(sph_ctx* c) {
@@ -733,6 +1027,7 @@ sph_status sph_grid(const sph_ctx* ctx, int32_t n_cells[3], double cell_size[3],
 
 sph_status sph_build_neighbors(sph_ctx* c) {
     if (!c) return fail(c, SPH_ERR_INVALID, "ctx is NULL");
+    if (c->ninst) return fail(c, SPH_ERR_STATE, "batch context: use the batch entry points");
     c->nbr_valid = false;
     sph_status s = ensure_neighbors(c);
     if (s != SPH_OK) return s;
@@ -741,6 +1036,7 @@ sph_status sph_build_neighbors(sph_ctx* c) {
 
 sph_status sph_get_cells(sph_ctx* c, uint32_t* cell_of, uint32_t* offsets, int64_t* order) {
     if (!c || !cell_of || !offsets) return fail(c, SPH_ERR_INVALID, "NULL argument");
+    if (c->ninst) return fail(c, SPH_ERR_STATE, "batch context: use the batch entry points");
     sph_status s = ensure_neighbors(c);
     if (s != SPH_OK) return s;
     uint32_t* d_cell = (uint32_t*)c->io;
@@ -756,6 +1052,7 @@ sph_status sph_get_cells(sph_ctx* c, uint32_t* cell_of, uint32_t* offsets, int64
 
 sph_status sph_get_neighbors(sph_ctx* c, int64_t* offsets, int32_t* idx, int64_t* nnz) {
     if (!c || !offsets || !nnz) return fail(c, SPH_ERR_INVALID, "NULL argument");
+    if (c->ninst) return fail(c, SPH_ERR_STATE, "batch context: use the batch entry points");
     sph_status s = ensure_neighbors(c);
     if (s != SPH_OK) return s;
     const PairConst<float> Kf = pair_const<float>(c, nullptr);
@@ -805,6 +1102,7 @@ sph_status sph_get_neighbors(sph_ctx* c, int64_t* offsets, int32_t* idx, int64_t
 
 sph_status sph_eval_rhs(sph_ctx* c, const sph_scheme* scheme) {
     if (!c) return fail(c, SPH_ERR_INVALID, "ctx is NULL");
+    if (c->ninst) return fail(c, SPH_ERR_STATE, "batch context: use the batch entry points");
     sph_status s = check_scheme(c, scheme);
     if (s != SPH_OK) return s;
     s = initial_eval(c, scheme, 0.0);
@@ -814,6 +1112,7 @@ sph_status sph_eval_rhs(sph_ctx* c, const sph_scheme* scheme) {
 
 sph_status sph_step_async(sph_ctx* c, const sph_scheme* scheme, double dt, int32_t nsteps) {
     if (!c) return fail(c, SPH_ERR_INVALID, "ctx is NULL");
+    if (c->ninst) return fail(c, SPH_ERR_STATE, "batch context: use the batch entry points");
     sph_status s = check_scheme(c, scheme);
     if (s != SPH_OK) return s;
     if (nsteps < 0) return fail(c, SPH_ERR_INVALID, "nsteps < 0");
@@ -824,11 +1123,12 @@ sph_status sph_step_async(sph_ctx* c, const sph_scheme* scheme, double dt, int32
         s = initial_eval(c, scheme, dt);
         if (s != SPH_OK) return s;
     }
+    s = upload_single(c, scheme, dt);
+    if (s != SPH_OK) return s;
     if (dt > 0.0) CK(cudaMemcpyAsync(&c->ctl->dt, &dt, sizeof dt, cudaMemcpyHostToDevice, c->stream));
     if (nsteps == 0) return SPH_OK;
-    if (!c->graph[0] || !same_scheme(*scheme, c->graph_scheme) || c->graph_dt != dt ||
-        c->graph_timed != c->timing) {
-        s = capture_step_graphs(c, scheme, dt);
+    if (!c->graph[0] || c->graph_timed != c->timing) {
+        s = capture_step_graphs(c);
         if (s != SPH_OK) return s;
     }
     for (int k = 0; k < nsteps; ++k) {
@@ -875,7 +1175,8 @@ sph_status sph_kernels_per_step(const sph_ctx* ctx, const sph_scheme* scheme, in
     sph_ctx* c = const_cast<sph_ctx*>(ctx);
     if (!c || !scheme || !count) return fail(c, SPH_ERR_INVALID, "NULL argument");
     // drift+keys, 3 per radix pass, reorder, cell table, density pass, momentum pass
-    *count = 1 + 3 * c->passes + 1 + 1 + 1 + 1;
+    // (+ the per-instance reduction of a batch)
+    *count = 1 + 3 * c->passes + 1 + 1 + 1 + 1 + (c->ninst ? 1 : 0);
     return SPH_OK;
 }
 
@@ -890,6 +1191,39 @@ sph_status sph_set_groups(sph_ctx* c, int32_t momentum_lanes) {
 
 sph_status sph_autotune(sph_ctx* c, const sph_scheme* scheme, int32_t* chosen) {
     if (!c) return fail(c, SPH_ERR_INVALID, "ctx is NULL");
+    if (c->ninst) {  // batch: time whole evaluations of all instances per tile shape
+        if ((int)c->batch_schemes.size() != c->ninst)
+            return fail(c, SPH_ERR_STATE, "call sph_step_batch once before tuning a batch");
+        sph_status s = batch_initial_eval(c);
+        if (s != SPH_OK) return s;
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        int best = c->group_m;
+        float best_ms = 1e30f;
+        for (int T = 1; T <= 8; T *= 2) {
+            c->group_m = T;
+            for (int r = 0; r <= 5; ++r) {
+                if (r == 1) CK(cudaEventRecord(e0, c->stream));
+                enqueue_eval(c, 0);
+            }
+            CK(cudaEventRecord(e1, c->stream));
+            CK(cudaEventSynchronize(e1));
+            CK(cudaGetLastError());
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = T;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        c->group_m = best;
+        drop_graphs(c);
+        if (chosen) *chosen = best;
+        return sync_status(c);
+    }
     sph_status s = check_scheme(c, scheme);
     if (s != SPH_OK) return s;
     s = initial_eval(c, scheme, 0.0);  // neighbours, list and a density pass at this state
@@ -899,32 +1233,7 @@ sph_status sph_autotune(sph_ctx* c, const sph_scheme* scheme, int32_t* chosen) {
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    const StepConst C = step_const(c, scheme, 0.0);
-    const PairConst<float> Kf = pair_const<float>(c, scheme);
-    const PairConst<double> Kd = pair_const<double>(c, scheme);
-    PairLaunch L{};
-    L.precision = c->dom.precision;
-    L.dim = c->dom.dim;
-    L.kernel = c->dom.kernel;
-    L.kick = 0;
-    L.n = c->N;
-    L.P = c->P;
-    L.Q = c->Q;
-    L.R = c->R;
-    L.skeys = c->skeys;
-    L.off = c->off;
-    L.G = c->G;
-    L.C = C;
-    L.S = c->set[c->cur];
-    L.ctl = c->ctl;
-    L.nl = c->nl;
-    L.cnt = c->cnt;
-    L.maxn = c->maxn;
-    L.pm = c->pm;
-    L.pd = c->pd;
-    L.history = c->history;
-    L.group_d = 1;
-    L.grid_d = c->grid_d;
+    StepLaunch L = step_launch(c, 0);
     int best = c->group_m;
     float best_ms = 1e30f;
     const int reps = 5;
@@ -933,7 +1242,7 @@ sph_status sph_autotune(sph_ctx* c, const sph_scheme* scheme, int32_t* chosen) {
         L.grid_m = pass_grid(c, 1, T);
         for (int r = 0; r <= reps; ++r) {
             if (r == 1) CK(cudaEventRecord(e0, c->stream));
-            launch_momentum_pass(L, Kf, Kd, c->stream);
+            launch_momentum_pass(L, c->stream);
         }
         CK(cudaEventRecord(e1, c->stream));
         CK(cudaEventSynchronize(e1));
@@ -1058,6 +1367,7 @@ AdjSet adj_take(sph_ctx* c, char*& p) {
 sph_status sph_backward(sph_ctx* c, const sph_scheme* scheme, double dt, int32_t K,
                         int32_t ckpt_every, double* dKE_du0, double* dKE_dnu, double* dKE_dalpha) {
     if (!c) return fail(c, SPH_ERR_INVALID, "ctx is NULL");
+    if (c->ninst) return fail(c, SPH_ERR_STATE, "batch context: use the batch entry points");
     sph_status s = check_scheme(c, scheme);
     if (s != SPH_OK) return s;
     if (scheme->density != SPH_DENSITY_CONTINUITY)
@@ -1116,9 +1426,8 @@ sph_status sph_backward(sph_ctx* c, const sph_scheme* scheme, double dt, int32_t
     if (s != SPH_OK) return s;
     CK(cudaMemcpyAsync(&c->ctl->dt, &dt, sizeof dt, cudaMemcpyHostToDevice, c->stream));
     CK(tape_record(c, tape[C]));
-    if (!c->graph[0] || !same_scheme(*scheme, c->graph_scheme) || c->graph_dt != dt ||
-        c->graph_timed != c->timing) {
-        s = capture_step_graphs(c, scheme, dt);
+    if (!c->graph[0] || c->graph_timed != c->timing) {
+        s = capture_step_graphs(c);
         if (s != SPH_OK) return s;
     }
     for (int step = 0; step < K; ++step) {

@@ -5,6 +5,7 @@
 // (Eq. eos) fused into the write of the pair-loop shadow arrays, and the cell table.
 #include "sph_device.cuh"
 #include "sph_launch.h"
+#include "step_impl.cuh"
 
 namespace sph {
 
@@ -12,33 +13,19 @@ namespace sph {
 // Per particle in the current order: for fluid, u_half = u + dt/2 a and
 // x <- wrap(x + dt (u_half + xsph)) (written back in place); then the linear cell id
 // of the position rounded to the pair-loop precision.
-__global__ void k_drift_keys(ParticleSet S, int n, Grid G, StepConst C, Control* ctl,
-                             int drift, uint32_t* keys) {
+template <class Real>
+__global__ void k_drift_keys(ParticleSet S, int n, const Inst<Real>* __restrict__ tab,
+                             const uint32_t* __restrict__ id_bounds, int ninst,
+                             const double* __restrict__ idt, int drift, uint32_t* keys,
+                             Control* ctl) {
     if (ctl->status) return;
-    const double dt = ctl->dt;
     unsigned outside = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const bool fluid = !(S.tag[i] & WALL_BIT);
-        int c[3] = {0, 0, 0};
+        const int inst = find_instance(id_bounds, ninst, S.tag[i] & ID_MASK);
+        const Inst<Real>& I = tab[inst];
         int clamped = 0;
-        for (int d = 0; d < G.dim; ++d) {
-            double x = S.x[d][i];
-            if (drift && fluid) {
-                double uh = S.u[d][i] + 0.5 * dt * S.a[d][i];
-                x = x + dt * (uh + S.xs[d][i]);
-                if (G.periodic[d] && !(x >= G.lo[d] && x < G.hi[d])) {
-                    double k = floor(__ddiv_rn(__dsub_rn(x, G.lo[d]), G.L[d]));
-                    x = __dsub_rn(x, __dmul_rn(k, G.L[d]));
-                    if (x >= G.hi[d]) x = __dsub_rn(x, G.L[d]);
-                    if (x < G.lo[d]) x = G.lo[d];
-                }
-                S.x[d][i] = x;
-            }
-            double xm = C.precision ? (double)__double2float_rn(x) : x;
-            c[d] = cell_coord(xm, G.lo[d], G.cs[d], G.nc[d], &clamped);
-        }
+        keys[i] = I.cell_base + drift_key_one(S, i, I.G, I.C, idt[inst], drift, clamped);
         outside += clamped;
-        keys[i] = (uint32_t)(c[0] + G.nc[0] * (c[1] + G.nc[1] * c[2]));
     }
     // count clamped particles (warp-aggregated)
     for (int o = 16; o > 0; o >>= 1) outside += __shfl_down_sync(0xffffffffu, outside, o);
@@ -197,43 +184,16 @@ __global__ void k_cell_offsets(const uint32_t* __restrict__ skeys, int n, int nc
 // Q = (u, v, w, rho), R = p / rho^2 with p from the Tait EOS (Eq. eos) in FP64.
 template <class Real>
 __global__ void k_reorder(ParticleSet in, ParticleSet out, const uint32_t* __restrict__ perm,
-                          int n, int dim, StepConst C, Control* ctl, int kick, int carry_rates,
+                          const uint32_t* __restrict__ skeys, int n, int dim,
+                          const Inst<Real>* __restrict__ tab, const uint32_t* __restrict__ cell_bounds,
+                          int ninst, const double* __restrict__ idt, int kick, int carry_rates,
                           typename V4<Real>::T* __restrict__ P, typename V4<Real>::T* __restrict__ Q,
-                          Real* __restrict__ R) {
+                          Real* __restrict__ R, const Control* ctl) {
     if (ctl->status) return;
-    const double dt = ctl->dt;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const int o = (int)perm[k];
-        const uint32_t tag = in.tag[o];
-        const bool fluid = !(tag & WALL_BIT);
-        double x[3] = {0, 0, 0}, u[3] = {0, 0, 0};
-        for (int d = 0; d < dim; ++d) {
-            x[d] = in.x[d][o];
-            u[d] = in.u[d][o];
-            if (kick && fluid) u[d] += 0.5 * dt * in.a[d][o];
-            out.x[d][k] = x[d];
-            out.u[d][k] = u[d];
-        }
-        const double rho = in.rho[o];
-        const double m = in.m[o];
-        out.rho[k] = rho;
-        out.m[k] = m;
-        out.tag[k] = tag;
-        if (carry_rates) {
-            out.arho[k] = in.arho[o];
-            for (int d = 0; d < dim; ++d) {
-                out.a[d][k] = in.a[d][o];
-                out.xs[d][k] = in.xs[d][o];
-            }
-        }
-        const double p = tait_pressure(rho, C);
-        typename V4<Real>::T pv, qv;
-        pv.x = (Real)x[0]; pv.y = (Real)x[1]; pv.z = (Real)x[2];
-        pv.w = (Real)(fluid ? m : -m);
-        qv.x = (Real)u[0]; qv.y = (Real)u[1]; qv.z = (Real)u[2]; qv.w = (Real)rho;
-        P[k] = pv;
-        Q[k] = qv;
-        R[k] = (Real)(p / (rho * rho));
+        const int inst = find_instance(cell_bounds, ninst, skeys[k]);
+        reorder_one<Real>(in, out, k, (int)perm[k], dim, tab[inst].C, idt[inst], kick,
+                          carry_rates, P, Q, R);
     }
 }
 
@@ -364,9 +324,14 @@ static inline int grid_for(long long n, int threads, int cap) {
     return (int)b;
 }
 
-void launch_drift_keys(const ParticleSet& S, int n, const Grid& G, const StepConst& C,
-                       Control* ctl, int drift, uint32_t* keys, cudaStream_t st, int sms) {
-    k_drift_keys<<<grid_for(n, 256, sms * 8), 256, 0, st>>>(S, n, G, C, ctl, drift, keys);
+void launch_drift_keys(const StepLaunch& L, int drift, uint32_t* keys, cudaStream_t st) {
+    const int g = grid_for(L.n, 256, L.sms * 8);
+    if (L.precision)
+        k_drift_keys<float><<<g, 256, 0, st>>>(L.Sin, L.n, (const Inst<float>*)L.tab, L.id_bounds,
+                                               L.ninst, L.idt, drift, keys, L.ctl);
+    else
+        k_drift_keys<double><<<g, 256, 0, st>>>(L.Sin, L.n, (const Inst<double>*)L.tab, L.id_bounds,
+                                                L.ninst, L.idt, drift, keys, L.ctl);
 }
 
 int radix_passes(int ncells) {
@@ -407,16 +372,18 @@ void launch_cell_offsets(const uint32_t* skeys, int n, int ncells, uint32_t* off
                                                                                   off, ctl);
 }
 
-void launch_reorder(int precision, const ParticleSet& in, const ParticleSet& out,
-                    const uint32_t* perm, int n, int dim, const StepConst& C, Control* ctl,
-                    int kick, int carry_rates, void* P, void* Q, void* R, cudaStream_t st, int sms) {
-    int g = grid_for(n, 256, sms * 8);
-    if (precision)
-        k_reorder<float><<<g, 256, 0, st>>>(in, out, perm, n, dim, C, ctl, kick, carry_rates,
-                                            (F4*)P, (F4*)Q, (float*)R);
+void launch_reorder(const StepLaunch& L, const uint32_t* perm, int carry_rates, cudaStream_t st) {
+    const int g = grid_for(L.n, 256, L.sms * 8);
+    if (L.precision)
+        k_reorder<float><<<g, 256, 0, st>>>(L.Sin, L.S, perm, L.skeys, L.n, L.dim,
+                                            (const Inst<float>*)L.tab, L.cell_bounds, L.ninst, L.idt,
+                                            L.kick, carry_rates, (F4*)L.P, (F4*)L.Q, (float*)L.R,
+                                            L.ctl);
     else
-        k_reorder<double><<<g, 256, 0, st>>>(in, out, perm, n, dim, C, ctl, kick, carry_rates,
-                                             (D4*)P, (D4*)Q, (double*)R);
+        k_reorder<double><<<g, 256, 0, st>>>(L.Sin, L.S, perm, L.skeys, L.n, L.dim,
+                                             (const Inst<double>*)L.tab, L.cell_bounds, L.ninst,
+                                             L.idt, L.kick, carry_rates, (D4*)L.P, (D4*)L.Q,
+                                             (double*)L.R, L.ctl);
 }
 
 void launch_gather_by_id(const double* field, const uint32_t* tag, int n, uint32_t first,

@@ -13,16 +13,14 @@ int pairs_bps_f32(int pass, int dim, int kernel, int T) {
     }
 }
 
-void launch_density_f32(const PairLaunch& L, const PairConst<float>& K, cudaStream_t st) {
-    PairDispatch<float>::density_t<1>(L, K, L.grid_d, st);
-}
+void launch_density_f32(const StepLaunch& L, cudaStream_t st) { PairDispatch<float>::density(L, st); }
 
-void launch_momentum_f32(const PairLaunch& L, const PairConst<float>& K, cudaStream_t st) {
+void launch_momentum_f32(const StepLaunch& L, cudaStream_t st) {
     switch (L.group_m) {
-        case 1: PairDispatch<float>::momentum_t<1>(L, K, L.grid_m, L.grid_d, st); break;
-        case 2: PairDispatch<float>::momentum_t<2>(L, K, L.grid_m, L.grid_d, st); break;
-        case 4: PairDispatch<float>::momentum_t<4>(L, K, L.grid_m, L.grid_d, st); break;
-        default: PairDispatch<float>::momentum_t<8>(L, K, L.grid_m, L.grid_d, st); break;
+        case 1: PairDispatch<float>::momentum_t<1>(L, st); break;
+        case 2: PairDispatch<float>::momentum_t<2>(L, st); break;
+        case 4: PairDispatch<float>::momentum_t<4>(L, st); break;
+        default: PairDispatch<float>::momentum_t<8>(L, st); break;
     }
 }
 

@@ -18,6 +18,7 @@
 
 #include "sph_device.cuh"
 #include "sph_launch.h"
+#include "step_impl.cuh"
 
 namespace sph {
 
@@ -140,86 +141,116 @@ __device__ __forceinline__ void block_counts(double c0, double c1, double c2, do
 // Then p from the Tait EOS in FP64 and the shadow rho, p / rho^2. Counts interacting pairs
 // (not both walls), candidates and the interacting pairs with a wall destination. A list
 // overflow raises ST_CAPACITY (the evaluation is then invalid and the step reports it).
+struct DensityCounts {
+    double pairs, cand, wall;
+    int overflow;
+};
+
+// Density pass for destination i (cell key `key`, cell table `off` of its grid).
+template <class Real, int DIM, int KERNEL>
+__device__ __forceinline__ void density_dest(int i, uint32_t key,
+                                             const typename V4<Real>::T* __restrict__ P,
+                                             typename V4<Real>::T* __restrict__ Q,
+                                             Real* __restrict__ R, const uint32_t* __restrict__ off,
+                                             int n, const Grid& G, const PairConst<Real>& K,
+                                             const StepConst& C, const ParticleSet& S, double dt,
+                                             int kick, uint32_t* __restrict__ nl,
+                                             uint32_t* __restrict__ cnt, int maxn,
+                                             DensityCounts& dc, uint32_t* npairs_out,
+                                             uint32_t* ncand_out) {
+    const bool summation = !(K.flags & F_CONTINUITY);
+    const typename V4<Real>::T pi = P[i];
+    const bool fluid_i = pi.w > Real(0);
+    int cx, cy, cz;
+    cell_of_key(G, key, cx, cy, cz);
+    uint32_t k = 0, npairs = 0, ncand = 0;
+    for_each_run<DIM>(G, off, cx, cy, cz, [&](uint32_t jb, uint32_t je) {
+#pragma unroll 2
+        for (uint32_t j = jb; j < je; ++j) {
+            if ((int)j == i) continue;
+            ++ncand;
+            const typename V4<Real>::T pj = P[j];
+            Real dx, dy, dz;
+            const Real r2 = separation<Real, DIM>(pi, pj, G, K, dx, dy, dz);
+            if (r2 < K.kh2) {
+                const bool interacting = fluid_i || pj.w > Real(0);
+                if (interacting || summation) {
+                    if (k < (uint32_t)maxn) nl[(size_t)k * n + i] = j;
+                    ++k;
+                }
+                npairs += interacting ? 1u : 0u;
+            }
+        }
+    });
+    if (k > (uint32_t)maxn) {
+        dc.overflow = 1;
+        k = maxn;
+    }
+    cnt[i] = k;
+    Acc<Real> sum;
+    sum.zero();
+    const typename V4<Real>::T qi = Q[i];
+    for (uint32_t kk = 0; kk < k; ++kk) {
+        const uint32_t j = nl[(size_t)kk * n + i];
+        const typename V4<Real>::T pj = P[j];
+        Real dx, dy, dz;
+        const Real r2 = separation<Real, DIM>(pi, pj, G, K, dx, dy, dz);
+        const Real q = sqrt(r2) * K.inv_h;
+        if (summation) {
+            sum.add(fabs(pj.w) * K.wfac * kernel_w<Real, KERNEL>(q));
+        } else {
+            const typename V4<Real>::T qj = Q[j];
+            const Real Gk = K.gfac * kernel_f<Real, KERNEL>(q);
+            const Real vdotr = (qi.x - qj.x) * dx + (qi.y - qj.y) * dy +
+                               (DIM == 3 ? (qi.z - qj.z) * dz : Real(0));
+            sum.add(fabs(pj.w) * Gk * vdotr);
+        }
+    }
+    double rho;
+    if (summation) {
+        rho = sum.value() + (double)(fabs(pi.w) * K.wfac * kernel_w<Real, KERNEL>(Real(0)));
+        S.arho[i] = 0.0;
+    } else {
+        const double ar = sum.value();
+        S.arho[i] = ar;
+        rho = S.rho[i];
+        if (kick) rho += dt * ar;
+    }
+    S.rho[i] = rho;
+    const double p = tait_pressure(rho, C);
+    reinterpret_cast<Real*>(&Q[i])[3] = (Real)rho;
+    R[i] = (Real)(p / (rho * rho));
+    dc.pairs += (double)npairs;
+    dc.cand += (double)ncand;
+    if (!fluid_i) dc.wall += (double)npairs;
+    if (npairs_out) *npairs_out = npairs;
+    if (ncand_out) *ncand_out = ncand;
+}
+
+// Density pass over all destinations; each finds its instance's constants in the table
+// (one entry for a single problem). Single problems accumulate block counts in pd; batches
+// store per-particle counts in pcount for the per-instance reduction.
 template <class Real, int DIM, int KERNEL>
 __global__ void __launch_bounds__(PAIR_THREADS, 6)
 k_density(const typename V4<Real>::T* __restrict__ P, typename V4<Real>::T* __restrict__ Q,
           Real* __restrict__ R, const uint32_t* __restrict__ skeys, const uint32_t* __restrict__ off,
-          int n, Grid G, PairConst<Real> K, StepConst C, ParticleSet S, Control* ctl,
-          int kick, uint32_t* __restrict__ nl, uint32_t* __restrict__ cnt, int maxn,
-          double* __restrict__ pd) {
+          int n, const Inst<Real>* __restrict__ tab, const uint32_t* __restrict__ cell_bounds,
+          int ninst, const double* __restrict__ idt, ParticleSet S, Control* ctl, int kick,
+          uint32_t* __restrict__ nl, uint32_t* __restrict__ cnt, int maxn,
+          double* __restrict__ pd, uint32_t* __restrict__ pcount) {
     if (ctl->status) return;
-    const double dt = ctl->dt;
-    const bool summation = !(K.flags & F_CONTINUITY);
-    double c_pairs = 0, c_cand = 0, c_wall = 0;
-    int overflow = 0;
+    DensityCounts dc{0, 0, 0, 0};
     for (int i = blockIdx.x * PAIR_THREADS + threadIdx.x; i < n; i += gridDim.x * PAIR_THREADS) {
-        const typename V4<Real>::T pi = P[i];
-        const bool fluid_i = pi.w > Real(0);
-        int cx, cy, cz;
-        cell_of_key(G, skeys[i], cx, cy, cz);
-        uint32_t k = 0, npairs = 0, ncand = 0;
-        for_each_run<DIM>(G, off, cx, cy, cz, [&](uint32_t jb, uint32_t je) {
-#pragma unroll 2
-            for (uint32_t j = jb; j < je; ++j) {
-                if ((int)j == i) continue;
-                ++ncand;
-                const typename V4<Real>::T pj = P[j];
-                Real dx, dy, dz;
-                const Real r2 = separation<Real, DIM>(pi, pj, G, K, dx, dy, dz);
-                if (r2 < K.kh2) {
-                    const bool interacting = fluid_i || pj.w > Real(0);
-                    if (interacting || summation) {
-                        if (k < (uint32_t)maxn) nl[(size_t)k * n + i] = j;
-                        ++k;
-                    }
-                    npairs += interacting ? 1u : 0u;
-                }
-            }
-        });
-        if (k > (uint32_t)maxn) {
-            overflow = 1;
-            k = maxn;
-        }
-        cnt[i] = k;
-        Acc<Real> sum;
-        sum.zero();
-        const typename V4<Real>::T qi = Q[i];
-        for (uint32_t kk = 0; kk < k; ++kk) {
-            const uint32_t j = nl[(size_t)kk * n + i];
-            const typename V4<Real>::T pj = P[j];
-            Real dx, dy, dz;
-            const Real r2 = separation<Real, DIM>(pi, pj, G, K, dx, dy, dz);
-            const Real q = sqrt(r2) * K.inv_h;
-            if (summation) {
-                sum.add(fabs(pj.w) * K.wfac * kernel_w<Real, KERNEL>(q));
-            } else {
-                const typename V4<Real>::T qj = Q[j];
-                const Real Gk = K.gfac * kernel_f<Real, KERNEL>(q);
-                const Real vdotr = (qi.x - qj.x) * dx + (qi.y - qj.y) * dy +
-                                   (DIM == 3 ? (qi.z - qj.z) * dz : Real(0));
-                sum.add(fabs(pj.w) * Gk * vdotr);
-            }
-        }
-        double rho;
-        if (summation) {
-            rho = sum.value() + (double)(fabs(pi.w) * K.wfac * kernel_w<Real, KERNEL>(Real(0)));
-            S.arho[i] = 0.0;
-        } else {
-            const double ar = sum.value();
-            S.arho[i] = ar;
-            rho = S.rho[i];
-            if (kick) rho += dt * ar;
-        }
-        S.rho[i] = rho;
-        const double p = tait_pressure(rho, C);
-        reinterpret_cast<Real*>(&Q[i])[3] = (Real)rho;
-        R[i] = (Real)(p / (rho * rho));
-        c_pairs += (double)npairs;
-        c_cand += (double)ncand;
-        if (!fluid_i) c_wall += (double)npairs;
+        const uint32_t key = skeys[i];
+        const int inst = find_instance(cell_bounds, ninst, key);
+        const Inst<Real>& I = tab[inst];
+        density_dest<Real, DIM, KERNEL>(i, key - I.cell_base, P, Q, R, off + I.cell_base, n, I.G,
+                                        I.K, I.C, S, idt[inst], kick, nl, cnt, maxn, dc,
+                                        pcount ? pcount + 2 * (size_t)i : nullptr,
+                                        pcount ? pcount + 2 * (size_t)i + 1 : nullptr);
     }
-    if (overflow) atomicOr(&ctl->status, ST_CAPACITY);
-    block_counts(c_pairs, c_cand, c_wall, pd);
+    if (dc.overflow) atomicOr(&ctl->status, ST_CAPACITY);
+    if (pd) block_counts(dc.pairs, dc.cand, dc.wall, pd);
 }
 
 // ------------------------------------------------------------- momentum pass
@@ -229,110 +260,139 @@ k_density(const typename V4<Real>::T* __restrict__ P, typename V4<Real>::T* __re
 // corrector half-kick u^{n+1} = u^{n+1/2} + dt/2 a^{n+1} inside a step and the FP64
 // diagnostics. The last block to finish reduces the block partials of both passes in a
 // fixed order (deterministic) and writes the record, history entry, next dt and status.
+struct MomDiag {
+    double px, py, pz, ke, u2, a2;
+    int bad;
+};
+
+// Momentum pass for destination i, shared by the T lanes of group g (lane 0 finishes).
+template <class Real, int DIM, int KERNEL, int T>
+__device__ __forceinline__ void momentum_dest(int i, const Group<T>& g,
+                                              const typename V4<Real>::T* __restrict__ P,
+                                              const typename V4<Real>::T* __restrict__ Q,
+                                              const Real* __restrict__ R, int n,
+                                              const Grid& G, const PairConst<Real>& K,
+                                              const StepConst& C, const ParticleSet& S, double dt,
+                                              int kick, const uint32_t* __restrict__ nl,
+                                              const uint32_t* __restrict__ cnt, MomDiag& md) {
+    const int flags = K.flags;
+    const typename V4<Real>::T pi = P[i];
+    const bool fluid_i = pi.w > Real(0);
+    if (!fluid_i) {  // walls: no momentum equation, static
+        if (g.t == 0) {
+            for (int d = 0; d < DIM; ++d) {
+                S.a[d][i] = 0.0;
+                S.xs[d][i] = 0.0;
+            }
+            if (!isfinite(S.rho[i])) md.bad = 1;
+        }
+        return;
+    }
+    const typename V4<Real>::T qi = Q[i];
+    const Real pri = R[i];
+    Acc<Real> ax, ay, az, sx, sy, sz;
+    ax.zero(); ay.zero(); az.zero(); sx.zero(); sy.zero(); sz.zero();
+    const uint32_t ni = cnt[i];
+    for (uint32_t kk = g.t; kk < ni; kk += T) {
+        const uint32_t j = nl[(size_t)kk * n + i];
+        const typename V4<Real>::T pj = P[j];
+        Real dx, dy, dz;
+        const Real r2 = separation<Real, DIM>(pi, pj, G, K, dx, dy, dz);
+        const typename V4<Real>::T qj = Q[j];
+        const Real mj = fabs(pj.w);
+        const Real q = sqrt(r2) * K.inv_h;
+        const Real Gk = K.gfac * kernel_f<Real, KERNEL>(q);  // grad_i W = Gk (x_i - x_j)
+        const Real vx = qi.x - qj.x, vy = qi.y - qj.y, vz = DIM == 3 ? qi.z - qj.z : Real(0);
+        Real coef = pri + R[j];
+        const Real rhobar = Real(0.5) * (qi.w + qj.w);
+        if (flags & F_AV) {
+            const Real vdotr = vx * dx + vy * dy + (DIM == 3 ? vz * dz : Real(0));
+            if (vdotr < Real(0)) {
+                const Real mu = K.h * vdotr / (r2 + K.av_h2);
+                coef -= K.alpha_c0 * mu / rhobar;
+            }
+        }
+        const Real cg = -mj * coef * Gk;
+        Real cv = Real(0);
+        if (flags & F_LAMINAR) cv = mj * K.nu4 / (qi.w + qj.w) * Gk * r2 / (r2 + K.eta_h2);
+        ax.add(cg * dx + cv * vx);
+        ay.add(cg * dy + cv * vy);
+        if (DIM == 3) az.add(cg * dz + cv * vz);
+        if ((flags & F_XSPH) && pj.w > Real(0)) {
+            const Real fx = K.xsph * mj / rhobar * (K.wfac * kernel_w<Real, KERNEL>(q));
+            sx.add(-fx * vx);
+            sy.add(-fx * vy);
+            if (DIM == 3) sz.add(-fx * vz);
+        }
+    }
+    if (T > 1) {
+        group_reduce<Real, T>(ax, g);
+        group_reduce<Real, T>(ay, g);
+        if (DIM == 3) group_reduce<Real, T>(az, g);
+        if (flags & F_XSPH) {
+            group_reduce<Real, T>(sx, g);
+            group_reduce<Real, T>(sy, g);
+            if (DIM == 3) group_reduce<Real, T>(sz, g);
+        }
+    }
+    if (g.t == 0) {  // epilogue: FP64 rates, corrector half-kick, diagnostics
+        double a[3] = {ax.value(), ay.value(), az.value()};
+        double xs[3] = {sx.value(), sy.value(), sz.value()};
+        double u[3] = {0, 0, 0};
+        double u2 = 0, a2 = 0;
+        for (int d = 0; d < DIM; ++d) {
+            a[d] += C.g[d];
+            S.a[d][i] = a[d];
+            S.xs[d][i] = xs[d];
+            u[d] = S.u[d][i];
+            if (kick) {
+                u[d] += 0.5 * dt * a[d];
+                S.u[d][i] = u[d];
+            }
+            u2 += u[d] * u[d];
+            a2 += a[d] * a[d];
+            if (!isfinite(u[d]) || !isfinite(S.x[d][i])) md.bad = 1;
+        }
+        if (!isfinite(S.rho[i]) || !isfinite(a2)) md.bad = 1;
+        const double m = S.m[i];
+        md.px += m * u[0];
+        md.py += m * u[1];
+        md.pz += m * u[2];
+        md.ke += 0.5 * m * u2;
+        md.u2 = fmax(md.u2, u2);
+        md.a2 = fmax(md.a2, a2);
+    }
+}
+
+// Momentum pass over all destinations (instance constants from the table). With
+// finalize (single problems) the block partials of both passes are reduced by the last
+// block, which writes the record, the history entry, the next dt and the status.
 template <class Real, int DIM, int KERNEL, int T>
 __global__ void __launch_bounds__(PAIR_THREADS, 5)
 k_momentum(const typename V4<Real>::T* __restrict__ P, const typename V4<Real>::T* __restrict__ Q,
-           const Real* __restrict__ R, int n, Grid G, PairConst<Real> K, StepConst C,
-           ParticleSet S, Control* ctl, int kick, const uint32_t* __restrict__ nl,
-           const uint32_t* __restrict__ cnt, double* __restrict__ pm,
-           const double* __restrict__ pd, int density_blocks, double* __restrict__ history) {
+           const Real* __restrict__ R, const uint32_t* __restrict__ skeys, int n,
+           const Inst<Real>* __restrict__ tab, const uint32_t* __restrict__ cell_bounds, int ninst,
+           double* __restrict__ idt, ParticleSet S, Control* ctl, int kick,
+           const uint32_t* __restrict__ nl, const uint32_t* __restrict__ cnt,
+           double* __restrict__ pm, const double* __restrict__ pd, int density_blocks,
+           double* __restrict__ history, int finalize) {
     __shared__ double red[PAIR_THREADS / 32][10];
     __shared__ bool is_last;
     if (ctl->status) return;
     const Group<T> g;
-    const double dt = ctl->dt;
-    const int flags = K.flags;
-    double d_px = 0, d_py = 0, d_pz = 0, d_ke = 0, d_u2 = 0, d_a2 = 0;
-    int bad = 0;
+    const double dt = idt[0];
+    MomDiag md{0, 0, 0, 0, 0, 0, 0};
     const int groups = gridDim.x * (PAIR_THREADS / T);
     for (int i = (blockIdx.x * PAIR_THREADS + threadIdx.x) / T; i < n; i += groups) {
-        const typename V4<Real>::T pi = P[i];
-        const bool fluid_i = pi.w > Real(0);
-        if (!fluid_i) {  // walls: no momentum equation, static
-            if (g.t == 0) {
-                for (int d = 0; d < DIM; ++d) {
-                    S.a[d][i] = 0.0;
-                    S.xs[d][i] = 0.0;
-                }
-                if (!isfinite(S.rho[i])) bad = 1;
-            }
-            continue;
-        }
-        const typename V4<Real>::T qi = Q[i];
-        const Real pri = R[i];
-        Acc<Real> ax, ay, az, sx, sy, sz;
-        ax.zero(); ay.zero(); az.zero(); sx.zero(); sy.zero(); sz.zero();
-        const uint32_t ni = cnt[i];
-        for (uint32_t kk = g.t; kk < ni; kk += T) {
-            const uint32_t j = nl[(size_t)kk * n + i];
-            const typename V4<Real>::T pj = P[j];
-            Real dx, dy, dz;
-            const Real r2 = separation<Real, DIM>(pi, pj, G, K, dx, dy, dz);
-            const typename V4<Real>::T qj = Q[j];
-            const Real mj = fabs(pj.w);
-            const Real q = sqrt(r2) * K.inv_h;
-            const Real Gk = K.gfac * kernel_f<Real, KERNEL>(q);  // grad_i W = Gk (x_i - x_j)
-            const Real vx = qi.x - qj.x, vy = qi.y - qj.y, vz = DIM == 3 ? qi.z - qj.z : Real(0);
-            Real coef = pri + R[j];
-            const Real rhobar = Real(0.5) * (qi.w + qj.w);
-            if (flags & F_AV) {
-                const Real vdotr = vx * dx + vy * dy + (DIM == 3 ? vz * dz : Real(0));
-                if (vdotr < Real(0)) {
-                    const Real mu = K.h * vdotr / (r2 + K.av_h2);
-                    coef -= K.alpha_c0 * mu / rhobar;
-                }
-            }
-            const Real cg = -mj * coef * Gk;
-            Real cv = Real(0);
-            if (flags & F_LAMINAR) cv = mj * K.nu4 / (qi.w + qj.w) * Gk * r2 / (r2 + K.eta_h2);
-            ax.add(cg * dx + cv * vx);
-            ay.add(cg * dy + cv * vy);
-            if (DIM == 3) az.add(cg * dz + cv * vz);
-            if ((flags & F_XSPH) && pj.w > Real(0)) {
-                const Real fx = K.xsph * mj / rhobar * (K.wfac * kernel_w<Real, KERNEL>(q));
-                sx.add(-fx * vx);
-                sy.add(-fx * vy);
-                if (DIM == 3) sz.add(-fx * vz);
-            }
-        }
-        if (T > 1) {
-            group_reduce<Real, T>(ax, g);
-            group_reduce<Real, T>(ay, g);
-            if (DIM == 3) group_reduce<Real, T>(az, g);
-            if (flags & F_XSPH) {
-                group_reduce<Real, T>(sx, g);
-                group_reduce<Real, T>(sy, g);
-                if (DIM == 3) group_reduce<Real, T>(sz, g);
-            }
-        }
-        if (g.t == 0) {  // epilogue: FP64 rates, corrector half-kick, diagnostics
-            double a[3] = {ax.value(), ay.value(), az.value()};
-            double xs[3] = {sx.value(), sy.value(), sz.value()};
-            double u[3] = {0, 0, 0};
-            double u2 = 0, a2 = 0;
-            for (int d = 0; d < DIM; ++d) {
-                a[d] += C.g[d];
-                S.a[d][i] = a[d];
-                S.xs[d][i] = xs[d];
-                u[d] = S.u[d][i];
-                if (kick) {
-                    u[d] += 0.5 * dt * a[d];
-                    S.u[d][i] = u[d];
-                }
-                u2 += u[d] * u[d];
-                a2 += a[d] * a[d];
-                if (!isfinite(u[d]) || !isfinite(S.x[d][i])) bad = 1;
-            }
-            if (!isfinite(S.rho[i]) || !isfinite(a2)) bad = 1;
-            const double m = S.m[i];
-            d_px += m * u[0];
-            d_py += m * u[1];
-            d_pz += m * u[2];
-            d_ke += 0.5 * m * u2;
-            d_u2 = fmax(d_u2, u2);
-            d_a2 = fmax(d_a2, a2);
-        }
+        const int inst = find_instance(cell_bounds, ninst, skeys[i]);
+        const Inst<Real>& I = tab[inst];
+        momentum_dest<Real, DIM, KERNEL, T>(i, g, P, Q, R, n, I.G, I.K, I.C, S, idt[inst], kick,
+                                            nl, cnt, md);
     }
+    if (!finalize) return;
+    const StepConst& C = tab[0].C;
+    double d_px = md.px, d_py = md.py, d_pz = md.pz, d_ke = md.ke, d_u2 = md.u2, d_a2 = md.a2;
+    int bad = md.bad;
 
     // ---- block reduction (fixed tree order: deterministic)
     constexpr int NV = 7;  // px py pz ke u2max a2max bad
@@ -451,20 +511,21 @@ int momentum_bps() {
 }
 
 template <class Real, int DIM, int KERNEL>
-void launch_density_t(const PairLaunch& L, const PairConst<Real>& K, int grid, cudaStream_t st) {
+void launch_density_t(const StepLaunch& L, cudaStream_t st) {
     using V = typename V4<Real>::T;
-    k_density<Real, DIM, KERNEL><<<grid, PAIR_THREADS, 0, st>>>(
-        (const V*)L.P, (V*)L.Q, (Real*)L.R, L.skeys, L.off, L.n, L.G, K, L.C, L.S, L.ctl, L.kick,
-        L.nl, L.cnt, L.maxn, L.pd);
+    k_density<Real, DIM, KERNEL><<<L.grid_d, PAIR_THREADS, 0, st>>>(
+        (const V*)L.P, (V*)L.Q, (Real*)L.R, L.skeys, L.off, L.n, (const Inst<Real>*)L.tab,
+        L.cell_bounds, L.ninst, L.idt, L.S, L.ctl, L.kick, L.nl, L.cnt, L.maxn,
+        L.finalize ? L.pd : nullptr, L.finalize ? nullptr : L.pcount);
 }
 
 template <class Real, int DIM, int KERNEL, int T>
-void launch_momentum_t(const PairLaunch& L, const PairConst<Real>& K, int grid, int density_grid,
-                       cudaStream_t st) {
+void launch_momentum_t(const StepLaunch& L, cudaStream_t st) {
     using V = typename V4<Real>::T;
-    k_momentum<Real, DIM, KERNEL, T><<<grid, PAIR_THREADS, 0, st>>>(
-        (const V*)L.P, (const V*)L.Q, (const Real*)L.R, L.n, L.G, K, L.C, L.S, L.ctl, L.kick, L.nl,
-        L.cnt, L.pm, L.pd, density_grid, L.history);
+    k_momentum<Real, DIM, KERNEL, T><<<L.grid_m, PAIR_THREADS, 0, st>>>(
+        (const V*)L.P, (const V*)L.Q, (const Real*)L.R, L.skeys, L.n, (const Inst<Real>*)L.tab,
+        L.cell_bounds, L.ninst, L.idt, L.S, L.ctl, L.kick, L.nl, L.cnt, L.pm, L.pd, L.grid_d,
+        L.history, L.finalize);
 }
 
 // One precision's dispatch over (dim, kernel, group size).
@@ -480,25 +541,23 @@ struct PairDispatch {
             default: return pass ? momentum_bps<Real, 3, WENDLAND_C2, T>() : density_bps<Real, 3, WENDLAND_C2>();
         }
     }
-    template <int T>
-    static void density_t(const PairLaunch& L, const PairConst<Real>& K, int grid, cudaStream_t st) {
+    static void density(const StepLaunch& L, cudaStream_t st) {
         const int sel = (L.dim == 3 ? 2 : 0) + (L.kernel == WENDLAND_C2 ? 1 : 0);
         switch (sel) {
-            case 0: launch_density_t<Real, 2, QUINTIC>(L, K, grid, st); break;
-            case 1: launch_density_t<Real, 2, WENDLAND_C2>(L, K, grid, st); break;
-            case 2: launch_density_t<Real, 3, QUINTIC>(L, K, grid, st); break;
-            default: launch_density_t<Real, 3, WENDLAND_C2>(L, K, grid, st); break;
+            case 0: launch_density_t<Real, 2, QUINTIC>(L, st); break;
+            case 1: launch_density_t<Real, 2, WENDLAND_C2>(L, st); break;
+            case 2: launch_density_t<Real, 3, QUINTIC>(L, st); break;
+            default: launch_density_t<Real, 3, WENDLAND_C2>(L, st); break;
         }
     }
     template <int T>
-    static void momentum_t(const PairLaunch& L, const PairConst<Real>& K, int grid, int dgrid,
-                           cudaStream_t st) {
+    static void momentum_t(const StepLaunch& L, cudaStream_t st) {
         const int sel = (L.dim == 3 ? 2 : 0) + (L.kernel == WENDLAND_C2 ? 1 : 0);
         switch (sel) {
-            case 0: launch_momentum_t<Real, 2, QUINTIC, T>(L, K, grid, dgrid, st); break;
-            case 1: launch_momentum_t<Real, 2, WENDLAND_C2, T>(L, K, grid, dgrid, st); break;
-            case 2: launch_momentum_t<Real, 3, QUINTIC, T>(L, K, grid, dgrid, st); break;
-            default: launch_momentum_t<Real, 3, WENDLAND_C2, T>(L, K, grid, dgrid, st); break;
+            case 0: launch_momentum_t<Real, 2, QUINTIC, T>(L, st); break;
+            case 1: launch_momentum_t<Real, 2, WENDLAND_C2, T>(L, st); break;
+            case 2: launch_momentum_t<Real, 3, QUINTIC, T>(L, st); break;
+            default: launch_momentum_t<Real, 3, WENDLAND_C2, T>(L, st); break;
         }
     }
 };

@@ -11,18 +11,13 @@
 
 namespace sph {
 
-// nnps.cu
-void launch_drift_keys(const ParticleSet& S, int n, const Grid& G, const StepConst& C,
-                       Control* ctl, int drift, uint32_t* keys, cudaStream_t st, int sms);
+// nnps.cu (the build stages take the instance table of a StepLaunch, declared below)
 int radix_passes(int ncells);
 size_t radix_hist_words(int n);
 int launch_radix_sort(uint32_t* keys[2], uint32_t* vals[2], int n, int passes, uint32_t* hist,
                       Control* ctl, cudaStream_t st);
 void launch_cell_offsets(const uint32_t* skeys, int n, int ncells, uint32_t* off, Control* ctl,
                          cudaStream_t st, int sms);
-void launch_reorder(int precision, const ParticleSet& in, const ParticleSet& out,
-                    const uint32_t* perm, int n, int dim, const StepConst& C, Control* ctl,
-                    int kick, int carry_rates, void* P, void* Q, void* R, cudaStream_t st, int sms);
 void launch_gather_by_id(const double* field, const uint32_t* tag, int n, uint32_t first,
                          uint32_t count, double* out, cudaStream_t st, int sms);
 void launch_scatter_by_id(double* field, const uint32_t* tag, int n, uint32_t first,
@@ -39,34 +34,49 @@ void launch_export_neighbors(int precision, int dim, const void* P, const uint32
 // capi.cu: sets the message sph_last_error(NULL) returns on this thread
 void set_global_error(const std::string& msg);
 
-// pairs.cu: one evaluation = density pass (group size group_d, grid_d blocks) then
-// momentum pass (group_m, grid_m). pm / pd: per-block partials of the two passes.
-struct PairLaunch {
-    int precision, dim, kernel, kick, n;
-    int group_d, group_m, grid_d, grid_m;
-    const void* P;
+// batch.cu: constants of one instance of a batch (device table, one entry per instance).
+template <class Real>
+struct Inst {
+    Grid G;
+    PairConst<Real> K;
+    StepConst C;
+    uint32_t cell_base;      // first global cell id of the instance
+    uint32_t cell_base_end;  // first global cell id of the next instance
+};
+// Everything one step's kernels need. A single problem is a table of one instance whose
+// dt is the control block's; a batch has one entry per instance.
+struct StepLaunch {
+    int precision, dim, kernel, n, sms, ninst, kick, maxn;
+    int group_m, grid_d, grid_m;
+    int finalize;                 // 1: the momentum pass reduces the diagnostics (single)
+    const void* tab;              // Inst<Real>[ninst]
+    const uint32_t* id_bounds;    // ninst + 1 global-id bounds
+    const uint32_t* cell_bounds;  // ninst + 1 global-cell bounds
+    double* idt;                  // dt of the next step, per instance
+    double* it;                   // batch: time per instance
+    double* irec;                 // batch: diagnostics per instance
+    ParticleSet Sin;              // current set (drift, reorder source)
+    ParticleSet S;                // cell-ordered set (reorder target, pair passes)
+    void* P;
     void* Q;
     void* R;
     const uint32_t* skeys;
     const uint32_t* off;
-    Grid G;
-    StepConst C;
-    ParticleSet S;
-    Control* ctl;
-    uint32_t* nl;   // neighbour list, nl[k * n + i], k < maxn
-    uint32_t* cnt;  // list length per particle
-    int maxn;
-    double* pm;  // 8 doubles per momentum block
-    double* pd;  // 4 doubles per density block
+    uint32_t* nl;                 // neighbour list, nl[k * n + i], k < maxn
+    uint32_t* cnt;                // list length per particle
+    uint32_t* pcount;             // batch: interacting pairs and candidates per particle
+    double* pm;                   // single: 8 doubles per momentum block
+    double* pd;                   // single: 4 doubles per density block
     double* history;
+    Control* ctl;
 };
+void launch_drift_keys(const StepLaunch& L, int drift, uint32_t* keys, cudaStream_t st);
+void launch_reorder(const StepLaunch& L, const uint32_t* perm, int carry_rates, cudaStream_t st);
 int pair_threads();
-void launch_pairs(const PairLaunch& L, const PairConst<float>& Kf, const PairConst<double>& Kd,
-                  cudaStream_t st);
-void launch_density_pass(const PairLaunch& L, const PairConst<float>& Kf,
-                         const PairConst<double>& Kd, cudaStream_t st);
-void launch_momentum_pass(const PairLaunch& L, const PairConst<float>& Kf,
-                          const PairConst<double>& Kd, cudaStream_t st);
+void launch_pairs(const StepLaunch& L, cudaStream_t st);
+void launch_density_pass(const StepLaunch& L, cudaStream_t st);
+void launch_momentum_pass(const StepLaunch& L, cudaStream_t st);
+void launch_batch_reduce(const StepLaunch& L, cudaStream_t st);
 // pass 0: density (thread per destination), 1: momentum (T = 1, 2, 4 or 8 lanes per
 // destination)
 int pairs_max_blocks_per_sm(int precision, int pass, int dim, int kernel, int T);

@@ -106,3 +106,22 @@ def test_backward_rejects_summation_density_and_adaptive_dt():
             sim.backward(sch, wl.dt, 2)
         with pytest.raises(G.SphError):
             sim.backward(G.scheme_of(wl), 0.0, 2)
+
+
+def test_autograd_function_gives_the_adjoint_gradients():
+    import torch
+    wl = _tg2(W.PREC_FP64, n=16)
+    s = O.state_of(wl)
+    K = 6
+    with sim_of(wl) as sim:
+        u0 = torch.tensor(np.stack([s["u"], s["v"]]), dtype=torch.float64, requires_grad=True)
+        nu = torch.tensor(wl.nu, dtype=torch.float64, requires_grad=True)
+        ke = G.final_kinetic_energy(sim, G.scheme_of(wl), wl.dt, K, u0, nu)
+        ke.backward()
+    ke_o, dke_nu = O.grad(wl, s, wl.dt, K, dnu=1.0)
+    assert abs(ke.item() - ke_o) <= 1e-12 * ke_o
+    assert abs(nu.grad.item() - dke_nu) <= 1e-8 * abs(dke_nu)
+    d = _direction(s, 2, 9)
+    _, dke_u = O.grad(wl, s, wl.dt, K, du=d[0], dv=d[1])
+    got = float((u0.grad.numpy() * np.stack(d)).sum())
+    assert abs(got - dke_u) <= 1e-8 * abs(dke_u)

@@ -1,0 +1,100 @@
+"""Batched step (sph_create_batch / sph_step_batch): a batch of independent instances of
+uneven size gives, instance by instance, bitwise the state of single runs (same equations,
+same tile shape, same summation order), and matches the oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from gpu_util import rel_l2
+
+import paper_1909_04504_gb300 as G
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("x", "y", "u", "v", "rho")
+
+
+def _tg_instances(precision):
+    out = []
+    for k, (n, re) in enumerate(((20, 100.0), (27, 400.0), (33, 60.0), (24, 900.0))):
+        out.append(W.taylor_green_2d(n=n, re=re, precision=precision, seed=77 + k))
+    return out
+
+
+def _db_instances(precision):
+    return [W.dam_break_2d(dx=dx, precision=precision) for dx in (0.05, 0.04, 0.06)]
+
+
+@pytest.mark.parametrize("maker", [_tg_instances, _db_instances])
+@pytest.mark.parametrize("precision", [W.PREC_FP64, W.PREC_FP32])
+def test_batch_equals_single_runs_bitwise(maker, precision):
+    wls = maker(precision)
+    steps = 15
+    lanes = 4
+    batch = G.BatchSimulation(wls)
+    batch.set_groups(lanes)
+    batch.step_batch([G.scheme_of(w) for w in wls], [w.dt for w in wls], steps)
+    diag = batch.batch_diagnostics()
+    for k, wl in enumerate(wls):
+        with G.Simulation.from_workload(wl) as sim:
+            sim.set_groups(lanes)
+            sim.step(G.scheme_of(wl), wl.dt, steps)
+            st = sim.state()
+            d = sim.diagnostics()
+        bs = batch.instance_state(k)
+        for f in FIELDS:
+            assert np.array_equal(bs[f], st[f]), (k, f)
+        assert diag[k, 8] == d[8] and diag[k, 9] == d[9] and diag[k, 12] == d[12]
+        assert abs(diag[k, 0] - d[0]) <= 1e-15 * abs(d[0]) and diag[k, 10] == steps
+        assert abs(diag[k, 2] - d[2]) <= 1e-12 * abs(d[2])
+    batch.close()
+
+
+def test_batch_instance_matches_oracle():
+    wls = _tg_instances(W.PREC_FP32)
+    batch = G.BatchSimulation(wls)
+    batch.step_batch([G.scheme_of(w) for w in wls], [w.dt for w in wls], 1)
+    for k, wl in enumerate(wls):
+        st, _ = O.run(wl, O.state_of(wl), wl.dt, 1)
+        bs = batch.instance_state(k)
+        for f in FIELDS:
+            assert rel_l2(bs[f], st[f]) <= 1e-4, (k, f)
+    batch.close()
+
+
+def test_batched_configuration_runs_and_matches_a_single_run():
+    """The batching configuration: 64 Taylor-Green instances of 2,500-40,000 particles,
+    Re in [50, 1000], FP32; a few steps, instance 7 against its own single run."""
+    wls = W.batch_tg2d()
+    batch = G.BatchSimulation(wls)
+    batch.step_batch([G.scheme_of(w) for w in wls], [w.dt for w in wls], 3)
+    lanes = batch.autotune(None)
+    assert lanes in (1, 2, 4, 8)
+    batch.step_batch([G.scheme_of(w) for w in wls], [w.dt for w in wls], 2)
+    diag = batch.batch_diagnostics()
+    assert np.all(diag[:, 8] > 0) and np.all(np.isfinite(diag[:, 2]))
+    assert batch.n == sum(w.n_total for w in wls)
+    bs = batch.instance_state(7)
+    batch.close()
+    wl = wls[7]
+    with G.Simulation.from_workload(wl) as sim:
+        sim.step(G.scheme_of(wl), wl.dt, 3)
+        sim.set_groups(lanes)  # the batch switched tile shape after three steps
+        sim.step(G.scheme_of(wl), wl.dt, 2)
+        st = sim.state()
+    # the first three steps used the default tile shape of the batch size class, the
+    # single run's default may differ: compare within FP32 rounding instead of bitwise
+    for f in FIELDS:
+        assert rel_l2(bs[f], st[f]) <= 1e-5, f
+
+
+def test_batch_rejects_mixed_kernels_and_single_calls():
+    a = W.taylor_green_2d(n=20)
+    b = W.dam_break_2d(dx=0.05, precision=W.PREC_FP64)
+    with pytest.raises(G.SphError):
+        G.BatchSimulation([a, b])
+    batch = G.BatchSimulation([a, W.taylor_green_2d(n=22)])
+    with pytest.raises(G.SphError):
+        batch.step(G.scheme_of(a), a.dt, 1)
+    batch.close()
