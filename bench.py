@@ -2,8 +2,9 @@
 """Benchmark of the GB300 WCSPH particle loop.
 
 A step is one pass of the whole per-timestep hot path over the workload: drift + cell
-keys, radix sort, reorder + EOS, cell table, fused pair loop with the corrector kick and
-the FP64 reductions (one captured CUDA graph). Default workload: the 2D dam break of the
+keys, radix sort, reorder + EOS shadow, cell table, density pass (neighbour scan and list,
+continuity or summation density, EOS), momentum pass with the corrector kick and the FP64
+reductions (one captured CUDA graph). Default workload: the 2D dam break of the
 precision configuration (20,000 fluid + 3,618 wall particles, Wendland C2, FP32 pair loops
 with an FP64 integrator). Inputs are resident in HBM; L2 is flushed (a 512 MB write)
 between timed steps because the working set (a few MB) would otherwise stay in L2.
@@ -59,23 +60,34 @@ def describe(wl) -> dict:
 
 
 # --------------------------------------------------------------------- flops
-def pair_flops(wl) -> dict:
-    """Algorithmic FP32 operations per candidate and per interacting pair of the fused loop
-    (add, sub, mul, div, sqrt = 1; a Neumaier compensated add = 4), by destination role."""
+def kernel_flops(wl) -> tuple[int, int]:
+    """Flops of f(q) = w'(q)/q and of w(q) as the kernels evaluate them."""
+    return (5, 6) if wl.kernel == 1 else (12, 14)
+
+
+def pass_flops(wl) -> dict:
+    """Algorithmic FP32 operations (add, sub, mul, div, sqrt = 1; a Neumaier compensated
+    add = 4) per unit of each pair pass, counted from the operations the passes perform:
+    density pass: per candidate (separation + squared distance), per listed pair
+    (continuity rate or summation term); momentum pass: per fluid-destination pair
+    (pressure, viscosity or AV, XSPH on fluid sources), per wall-destination pair 0."""
     d = wl.dim
-    cand = (d) + d + (d - 1)                      # differences, squares, sum
-    base = 2 + (5 if wl.kernel == 1 else 8) + 1   # sqrt, q; kernel f(q); gfac
-    base += d + (2 * d - 1)                       # v_ij, v_ij . r_ij
-    cont = 2 + 4                                  # m_j Gk (v.r), compensated add
-    wall_dest = base + cont
-    fluid = base + cont + 1 + 2 + 2               # Pr_i + Pr_j, rhobar, cg
+    kf, kw = kernel_flops(wl)
+    sep = 3 * d - 1                                   # differences, squares, sum
+    cand = sep                                        # + compare
+    if wl.density == 1:                               # summation: m W, compensated add
+        listed = sep + 2 + kw + 2 + 4
+    else:                                             # continuity: m Gk (v_ij . r_ij)
+        listed = sep + 2 + kf + 1 + (3 * d - 1) + 2 + 4
+    mom = sep + 2 + kf + 1 + d + 1 + 2 + 2            # q, Gk, v_ij, Pr_i+Pr_j, rhobar, cg
     if wl.alpha:
-        fluid += 0.5 * 6                          # Monaghan AV on approaching pairs (~half)
-    lam = 7 if wl.nu else 0
-    fluid += lam + d * ((3 if wl.nu else 1) + 4)  # momentum per axis + compensated add
-    if wl.xsph_eps:
-        fluid += (5 if wl.kernel == 1 else 10) + 1 + 3 + d * (1 + 4)
-    return {"candidate": cand, "fluid_dest_pair": fluid, "wall_dest_pair": wall_dest}
+        mom += 0.5 * ((2 * d - 1) + 3 + 3)            # AV on approaching pairs (about half)
+    if wl.nu:
+        mom += 7 + d * 2                              # laminar coefficient and cv v_ij
+    mom += d * (2 + 4)                                # cg dx (+cv v), compensated add
+    xsph = (kw + 1 + 3 + d * (1 + 4)) if wl.xsph_eps else 0
+    return {"candidate": cand, "listed_pair": listed, "fluid_dest_pair": mom,
+            "xsph_fluid_source_pair": xsph}
 
 
 # --------------------------------------------------------------------- clocks
@@ -135,12 +147,17 @@ def gpu_arm(args, rank, world, dist):
     sch = G.scheme_of(wl)
     sim = G.Simulation.from_workload(wl)
     stream = sim.stream
-    sim.set_timing(True)
     sim.step(sch, wl.dt, args.warmup)
+    if args.step_mode == "auto":
+        sim.autotune(sch)  # tile shape and step form (graph of phases / persistent launch)
+    else:
+        sim.set_step_mode(G.STEP_PERSISTENT if args.step_mode == "persistent" else G.STEP_GRAPH)
+    sim_lanes, sim_mode = sim.tuning()
+    mode = "persistent" if sim_mode == G.STEP_PERSISTENT else "graph"
+    sim.step(sch, wl.dt, 3)
     flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.int32, device=dev)
     e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    pair_ms, phases = [], {k: 0.0 for k in G.Simulation.PHASES}
     counts = [0.0, 0.0, 0.0]  # interacting pairs, candidates, wall-destination pairs
     uuid = None
     try:
@@ -153,17 +170,14 @@ def gpu_arm(args, rank, world, dist):
         dist.barrier()
     torch.cuda.synchronize()
     t_wall0 = time.perf_counter()
+    # ---- timed region: K steps, L2 flushed before each, CUDA events on the step stream
     for k in range(args.steps):
         with torch.cuda.stream(stream):
             flush.zero_()
         e0[k].record(stream)
         sim.step_async(sch, wl.dt, 1)
         e1[k].record(stream)
-        ph = sim.phase_times()  # waits for the step
-        pair_ms.append(ph["pairs"])
-        for key in phases:
-            phases[key] += ph[key]
-        dg = sim.diagnostics()
+        dg = sim.diagnostics()  # waits for the step (outside the events)
         counts[0] += dg[8]
         counts[1] += dg[9]
         counts[2] += dg[12]
@@ -172,6 +186,24 @@ def gpu_arm(args, rank, world, dist):
     if dist:
         dist.barrier()
     t_wall = time.perf_counter() - t_wall0
+    # ---- kernel durations: the same steps with events recorded between the phases inside
+    # the step (graph event nodes / phase-end stamps of the persistent kernel)
+    sim.set_timing(True)
+    phases = {k: 0.0 for k in G.Simulation.PHASES}
+    pcounts = [0.0, 0.0, 0.0]
+    psteps_n = min(args.steps, 200)
+    for k in range(psteps_n):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        sim.step_async(sch, wl.dt, 1)
+        ph = sim.phase_times()  # waits for the step
+        for key in phases:
+            phases[key] += ph[key]
+        dg = sim.diagnostics()
+        pcounts[0] += dg[8]
+        pcounts[1] += dg[9]
+        pcounts[2] += dg[12]
+    sim.set_timing(False)
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in zip(e0, e1)]
     total_ms = sum(step_ms)
@@ -184,22 +216,36 @@ def gpu_arm(args, rank, world, dist):
     value = world * pairs / (total_ms / 1e3)
     psteps = world * n * args.steps / (total_ms / 1e3)
 
-    # ---- roofline of the dominant kernel (pair loop), algorithmic flops / live duration
-    fl = pair_flops(wl)
-    flops = (fl["candidate"] * cand + (pairs - wall_pairs) * fl["fluid_dest_pair"]
-             + wall_pairs * fl["wall_dest_pair"])
-    flops_per_launch = flops / args.steps
-    pair_avg_ms = sum(pair_ms) / len(pair_ms)
-    achieved = flops_per_launch / (pair_avg_ms / 1e3) / 1e12
+    # ---- roofline of the dominant kernel (the longer pair pass), algorithmic flops over
+    # its live duration (CUDA events recorded on the launching stream inside the graph)
+    fl = pass_flops(wl)
+    p_pairs, p_cand, p_wall = pcounts
+    listed = p_pairs  # interacting pairs (summation also lists wall-wall pairs: not counted)
+    fluid_pairs = p_pairs - p_wall
+    fluid_src_frac = wl.n_fluid / wl.n_total        # XSPH sources: fluid share (estimate)
+    flops = {"density": (fl["candidate"] * p_cand + fl["listed_pair"] * listed) / psteps_n,
+             "momentum": (fl["fluid_dest_pair"] * fluid_pairs
+                          + fl["xsph_fluid_source_pair"] * fluid_pairs * fluid_src_frac) / psteps_n}
     peak = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     if wl.precision == 0:
         peak = peak / 64.0  # FP64 CUDA-core rate of this part: 1/64 of FP32
-    roofline = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 3),
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 5), "traffic": None,
-                "kernel": "k_pairs (fused continuity + momentum + AV + XSPH + kick + reductions)",
-                "flops_per_launch": flops_per_launch, "avg_launch_ms": round(pair_avg_ms, 5),
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
-    phase_avg = {k: round(v / args.steps, 5) for k, v in phases.items()}
+    per_pass = {}
+    for k in ("density", "momentum"):
+        ms = phases[k] / psteps_n
+        ach = flops[k] / (ms / 1e3) / 1e12
+        per_pass[k] = {"avg_launch_ms": round(ms, 5), "flops_per_launch": flops[k],
+                       "achieved_tflops": round(ach, 4), "frac": round(ach / peak, 5)}
+    dom = max(per_pass, key=lambda k: per_pass[k]["avg_launch_ms"])
+    names = {"density": "k_density (neighbour scan + list, continuity/summation, EOS)",
+             "momentum": "k_momentum (pressure, AV/viscosity, XSPH, corrector kick, reductions)"}
+    roofline = {"bound": "alu", "achieved": per_pass[dom]["achieved_tflops"],
+                "peak": round(peak, 3), "unit": "TFLOP/s", "frac": per_pass[dom]["frac"],
+                "traffic": None, "kernel": names[dom],
+                "flops_per_launch": flops[dom], "avg_launch_ms": per_pass[dom]["avg_launch_ms"],
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
+                               + (" / 64 (FP64)" if wl.precision == 0 else ""),
+                "passes": per_pass}
+    phase_avg = {k: round(v / psteps_n, 5) for k, v in phases.items()}
 
     # ---- end to end through the C ABI with host buffers
     blob = sim.save_state()
@@ -225,6 +271,10 @@ def gpu_arm(args, rank, world, dist):
     if wl.precision == 1 and args.fp64_steps > 0:
         sim64 = G.Simulation.from_workload(wl.with_precision(0))
         sim64.step(sch, wl.dt, args.warmup)
+        if args.step_mode == "auto":
+            sim64.autotune(sch)
+        else:
+            sim64.set_step_mode(G.STEP_PERSISTENT if args.step_mode == "persistent" else G.STEP_GRAPH)
         f0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.fp64_steps)]
         f1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.fp64_steps)]
         p64 = 0.0
@@ -247,21 +297,19 @@ def gpu_arm(args, rank, world, dist):
     state0 = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         state0 = one_step_states(wl, sch)
+    launches = sim.kernels_per_step(sch) * args.steps
     sim.close()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if wl.precision == 1 else "f64", "data": "synthetic",
-        "config": describe(wl),
+        "config": dict(describe(wl), step_mode=mode, momentum_lanes=sim_lanes),
         "particle_steps_per_s": psteps, "candidates_per_s": world * cand / (total_ms / 1e3),
         "pairs_per_step": pairs / args.steps, "phase_ms": phase_avg,
         "roofline": roofline, "e2e": e2e, "fp64_mode": fp64,
-        "gpu_launches": None, "clocks": clocks, "wall_s": round(t_wall, 3),
+        "gpu_launches": launches, "clocks": clocks, "wall_s": round(t_wall, 3),
     }
-    import paper_1909_04504_gb300 as G2  # noqa: F401
-    with G.Simulation.from_workload(wl) as s2:
-        line["gpu_launches"] = s2.kernels_per_step(sch) * args.steps
     return line, state0, wl
 
 
@@ -357,6 +405,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--step-mode", default="auto", choices=["auto", "graph", "persistent"],
+                    help="auto: the autotuner picks the tile shape and the step form")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 

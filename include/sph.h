@@ -201,23 +201,47 @@ sph_status sph_synchronize(sph_ctx* ctx);
 /* Phase timing. enable != 0: steps captured from now on record CUDA events between their
  * phases (a few microseconds of overhead per step). sph_phase_times then gives the device
  * time in ms of the last completed step's phases: out[0] drift + cell keys, out[1] radix
- * sort, out[2] reorder + EOS, out[3] cell table, out[4] pair loop (summation density
- * included) with the corrector kick and reductions. SPH_ERR_STATE if no timed step ran. */
+ * sort, out[2] reorder + EOS, out[3] cell table, out[4] density pass (neighbour scan and
+ * list, summation density or continuity, EOS), out[5] momentum pass with the corrector
+ * kick and the reductions. SPH_ERR_STATE if no timed step ran. */
 sph_status sph_set_timing(sph_ctx* ctx, int32_t enable);
-sph_status sph_phase_times(sph_ctx* ctx, float out[5]);
+sph_status sph_phase_times(sph_ctx* ctx, float out[6]);
 
-/* Tile shape of the momentum pass: lanes per destination particle (1, 2, 4 or 8) that
- * share its neighbour list (the density pass always gives one thread per destination).
- * More lanes hide latency on small problems. Changing it changes the summation order
- * (results stay within rounding of each other) and forces a new graph capture. */
+/* Tile shape of the pair passes: lanes per destination particle (1, 2, 4 or 8) that
+ * share its stencil scan (density pass) and its neighbour list (both passes). More lanes
+ * hide latency and spread small problems over more SMs. The neighbour list is the same for
+ * every shape; the summation order changes (results stay within rounding of each other).
+ * Forces a new graph capture. */
 sph_status sph_set_groups(sph_ctx* ctx, int32_t momentum_lanes);
 
-/* Autotuner: times the momentum pass for every tile shape on the current state (the
- * evaluations act like sph_eval_rhs), keeps the fastest, caches the choice for this
- * (precision, dim, kernel, log2 n) for contexts created later in the process, and returns
- * it in *chosen (may be NULL). Contexts start from a cached choice, else 4 lanes below
- * 200,000 particles and 1 above. Timing-dependent: call it explicitly, not inside a run
- * whose bitwise reproducibility matters. */
+/* How a step runs. SPH_STEP_GRAPH (default): the phases (drift + keys, radix sort passes,
+ * reorder, cell table, density pass, momentum pass, reductions) as separate kernels in a
+ * captured CUDA graph. SPH_STEP_PERSISTENT: the whole step as ONE cooperative launch whose
+ * blocks stay resident and meet at grid-wide barriers between the phases (no launch gaps;
+ * pays off on small problems and batches of them). Both run the same per-particle code;
+ * the diagnostics are summed in another order. SPH_ERR_INVALID if the mode is unknown or
+ * the device cannot launch cooperatively. */
+enum { SPH_STEP_GRAPH = 0, SPH_STEP_PERSISTENT = 1 };
+sph_status sph_set_step_mode(sph_ctx* ctx, int32_t mode);
+
+/* Current tuning: momentum-pass lanes per destination and step mode (either may be NULL). */
+sph_status sph_get_tuning(const sph_ctx* ctx, int32_t* momentum_lanes, int32_t* mode);
+
+/* Time limit of one device-side wait (a grid barrier of the persistent step), in ns;
+ * default 1 s; 0 lets no block wait (a persistent step of more than one block then fails
+ * at its first barrier). A wait that runs out raises SPH_ERR_TIMEOUT at the next
+ * synchronising call; the step is then incomplete and the state must be set again
+ * (sph_load_state / sph_set) before stepping on. */
+sph_status sph_set_wait_limit(sph_ctx* ctx, uint64_t ns);
+
+/* Autotuner: times whole evaluations (density + momentum pass) for every tile shape on
+ * the current state (they act like sph_eval_rhs) and keeps the fastest; then times a few
+ * steps in each step mode from the same state, keeps the faster mode and puts the state,
+ * time and records back bitwise. Caches the choice for this (precision, dim, kernel,
+ * log2 n) for contexts created later in the process and returns the lanes in *chosen (may
+ * be NULL). Contexts start from a cached choice, else 4 lanes below 200,000 particles and
+ * 1 above, in graph mode. Timing-dependent: call it explicitly, not inside a run whose
+ * bitwise reproducibility matters. A batch needs one sph_step_batch call first. */
 sph_status sph_autotune(sph_ctx* ctx, const sph_scheme* scheme, int32_t* chosen);
 
 /* Kernel launches one step issues (for launch accounting). */

@@ -19,6 +19,7 @@ QUINTIC, WENDLAND_C2 = 0, 1
 PREC_FP64, PREC_FP32 = 0, 1
 FLUID, WALL = 0, 1
 CONTINUITY, SUMMATION = 0, 1
+STEP_GRAPH, STEP_PERSISTENT = 0, 1
 DIAG_COUNT = 13
 DIAG_NAMES = ("t", "dt", "ke", "umax", "px", "py", "pz", "amax", "pairs", "candidates",
               "step", "outside", "wall_pairs")
@@ -58,7 +59,9 @@ _lib = None
 EXPORTS = ("sph_create", "sph_destroy", "sph_last_error", "sph_count", "sph_grid",
            "sph_build_neighbors", "sph_get_cells", "sph_get_neighbors", "sph_eval_rhs",
            "sph_step", "sph_step_async", "sph_synchronize", "sph_set_timing", "sph_phase_times",
-           "sph_kernels_per_step", "sph_set_groups", "sph_autotune", "sph_backward", "sph_get", "sph_set", "sph_diagnostics", "sph_history",
+           "sph_kernels_per_step", "sph_set_groups", "sph_set_step_mode", "sph_set_wait_limit",
+           "sph_get_tuning",
+           "sph_autotune", "sph_backward", "sph_get", "sph_set", "sph_diagnostics", "sph_history",
            "sph_save_state", "sph_load_state", "sph_create_batch", "sph_step_batch",
            "sph_batch_diagnostics")
 
@@ -100,6 +103,9 @@ def load(build_if_missing: bool = True):
     L.sph_phase_times.argtypes = [ctxp, C.POINTER(C.c_float)]
     L.sph_kernels_per_step.argtypes = [ctxp, C.POINTER(Scheme), i32]
     L.sph_set_groups.argtypes = [ctxp, C.c_int32]
+    L.sph_set_step_mode.argtypes = [ctxp, C.c_int32]
+    L.sph_set_wait_limit.argtypes = [ctxp, C.c_uint64]
+    L.sph_get_tuning.argtypes = [ctxp, i32, i32]
     L.sph_backward.argtypes = [ctxp, C.POINTER(Scheme), C.c_double, C.c_int32, C.c_int32, d, d, d]
     L.sph_autotune.argtypes = [ctxp, C.POINTER(Scheme), i32]
     L.sph_create_batch.argtypes = [C.POINTER(Domain), C.POINTER(ArrayDesc), i32, C.c_int32, P,
@@ -315,10 +321,10 @@ class Simulation:
     def set_timing(self, enable: bool = True):
         self._check(self._L.sph_set_timing(self._ctx, int(bool(enable))))
 
-    PHASES = ("keys", "sort", "reorder", "cells", "pairs")
+    PHASES = ("keys", "sort", "reorder", "cells", "density", "momentum")
 
     def phase_times(self) -> dict:
-        out = (C.c_float * 5)()
+        out = (C.c_float * 6)()
         self._check(self._L.sph_phase_times(self._ctx, out))
         return dict(zip(self.PHASES, [float(v) for v in out]))
 
@@ -329,6 +335,23 @@ class Simulation:
 
     def set_groups(self, momentum_lanes: int):
         self._check(self._L.sph_set_groups(self._ctx, int(momentum_lanes)))
+
+    def set_step_mode(self, mode: int):
+        """STEP_GRAPH: per-phase kernels in a CUDA graph; STEP_PERSISTENT: one cooperative
+        launch per step."""
+        self._check(self._L.sph_set_step_mode(self._ctx, int(mode)))
+
+    def tuning(self) -> tuple:
+        """(momentum lanes per destination, step mode)."""
+        lanes, mode = C.c_int32(), C.c_int32()
+        self._check(self._L.sph_get_tuning(self._ctx, C.byref(lanes), C.byref(mode)))
+        return int(lanes.value), int(mode.value)
+
+    def step_mode(self) -> int:
+        return self.tuning()[1]
+
+    def set_wait_limit(self, ns: int):
+        self._check(self._L.sph_set_wait_limit(self._ctx, int(ns)))
 
     def autotune(self, scheme: Optional[Scheme]) -> int:
         out = C.c_int32()

@@ -73,7 +73,7 @@ struct sph_ctx {
     void* io = nullptr;  // scratch for get/set/exports: 4 N + 2 (8 N + 8) bytes, 256-aligned parts
     int grid_cap = 1;                 // largest pair-pass grid (sizes pm, pd)
     int bps[2][4] = {{1, 1, 1, 1}, {1, 1, 1, 1}};  // blocks per SM: [pass][T = 1, 2, 4, 8]
-    int group_d = 1, group_m = 1;     // lanes per destination (density pass: always 1)
+    int group_d = 1, group_m = 1;     // lanes per destination of the pair passes (equal)
     int grid_d = 1, grid_m = 1;
     uint32_t* nl = nullptr;           // neighbour list nl[k * N + i], separately allocated
     uint32_t* cnt = nullptr;          // list length per particle (arena)
@@ -89,7 +89,12 @@ struct sph_ctx {
     // phase timing events (recorded inside captured steps when enabled)
     bool timing = false;
     bool timed_step_ran = false;
-    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    int step_mode = SPH_STEP_GRAPH;   // per-phase kernels in a graph, or one persistent launch
+    int fused_bps[4] = {0, 0, 0, 0};  // persistent kernel: blocks per SM for T = 1, 2, 4, 8
+    double* fpart = nullptr;          // persistent kernel: per-block partials
+    unsigned long long wait_ns = 1000000000ull;  // limit of one device-side wait
+    bool last_fused = false;          // the last step ran as one persistent launch
+    cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 
     // batch of independent instances (ninst > 0)
     int ninst = 0;
@@ -277,7 +282,11 @@ struct TuneKey {
     }
 };
 std::mutex g_tune_lock;
-std::vector<std::pair<TuneKey, std::pair<int, int>>> g_tune_cache;
+struct TuneVal {
+    int lanes;  // momentum-pass lanes per destination
+    int mode;   // SPH_STEP_GRAPH or SPH_STEP_PERSISTENT
+};
+std::vector<std::pair<TuneKey, TuneVal>> g_tune_cache;
 
 TuneKey tune_key(const sph_ctx* c) {
     int b = 0;
@@ -285,20 +294,33 @@ TuneKey tune_key(const sph_ctx* c) {
     return TuneKey{c->dom.precision, c->dom.dim, c->dom.kernel, b};
 }
 
-// Momentum-pass lanes per destination before any tuning: a cached tuning result for
-// this shape, else 4 for small problems (more threads to hide latency) and 1 otherwise.
-void default_groups(const sph_ctx* c, int* td, int* tm) {
-    *td = 1;
+// Tuning before any autotune call: a cached result for this shape, else 4 momentum lanes
+// below 200,000 particles and 1 above, and the per-phase graph.
+void default_tuning(const sph_ctx* c, int* tm, int* mode) {
+    *mode = SPH_STEP_GRAPH;
     {
         std::lock_guard<std::mutex> lock(g_tune_lock);
         const TuneKey k = tune_key(c);
         for (auto& e : g_tune_cache)
             if (e.first == k) {
-                *tm = e.second.second;
+                *tm = e.second.lanes;
+                *mode = e.second.mode;
                 return;
             }
     }
     *tm = c->N < 200000 ? 4 : 1;
+}
+
+void remember_tuning(const sph_ctx* c) {
+    std::lock_guard<std::mutex> lock(g_tune_lock);
+    const TuneKey k = tune_key(c);
+    const TuneVal v{c->group_m, c->step_mode};
+    for (auto& e : g_tune_cache)
+        if (e.first == k) {
+            e.second = v;
+            return;
+        }
+    g_tune_cache.push_back({k, v});
 }
 
 void mark(sph_ctx* c, int k, bool timed) {
@@ -318,6 +340,7 @@ StepLaunch step_launch(sph_ctx* c, int kick) {
     L.ninst = ntab(c);
     L.kick = kick;
     L.maxn = c->maxn;
+    L.group_d = c->group_d;
     L.group_m = c->group_m;
     L.grid_d = c->grid_d;
     L.grid_m = c->grid_m;
@@ -367,7 +390,85 @@ void enqueue_build(sph_ctx* c, int drift, int kick, int carry_rates, bool timed 
     c->cur = nxt;
 }
 
-void enqueue_eval(sph_ctx* c, int kick) { launch_pairs(step_launch(c, kick), c->stream); }
+// Density pass, then momentum pass (+ the per-instance reduction of a batch).
+void enqueue_eval(sph_ctx* c, int kick, bool timed = false) {
+    const StepLaunch L = step_launch(c, kick);
+    launch_density_pass(L, c->stream);
+    mark(c, 5, timed);
+    launch_momentum_pass(L, c->stream);
+    if (!L.finalize) launch_batch_reduce(L, c->stream);
+}
+
+// ------------------------------------------------------------ persistent step
+constexpr int FUSED_MAX_BPS = 8;
+
+// Grid of the persistent kernel: enough blocks for one group of T lanes per particle,
+// capped at the blocks that are co-resident (a cooperative launch needs all of them).
+int fused_grid(const sph_ctx* c) {
+    int bps = c->fused_bps[tindex(c->group_m)];
+    if (bps > FUSED_MAX_BPS) bps = FUSED_MAX_BPS;
+    const long long cap = (long long)c->sms * bps;
+    const long long want = ((long long)c->N * c->group_m + FUSED_THREADS - 1) / FUSED_THREADS;
+    long long g = want < cap ? want : cap;
+    return g < 1 ? 1 : (int)g;
+}
+
+FusedLaunch fused_launch(sph_ctx* c) {
+    FusedLaunch F{};
+    F.L = step_launch(c, 1);
+    F.L.Sin = c->set[c->cur];
+    F.L.S = c->set[c->cur ^ 1];
+    for (int k = 0; k < 2; ++k) {
+        F.keys[k] = c->keys[k];
+        F.vals[k] = c->vals[k];
+    }
+    F.hist = c->hist;
+    F.off = c->off;
+    F.part = c->fpart;
+    F.passes = c->passes;
+    F.ntiles = radix_tiles(c->N);
+    F.ncells = c->G.ncells;
+    F.wait_ns = c->wait_ns;
+    return F;
+}
+
+// nsteps persistent launches (one per step) on the context stream.
+sph_status run_fused(sph_ctx* c, int nsteps) {
+    if (c->fused_bps[tindex(c->group_m)] < 1)
+        return fail(c, SPH_ERR_INVALID, "the persistent step kernel cannot be resident on this device");
+    CK(cudaMemsetAsync(&c->ctl->outside, 0, sizeof(unsigned), c->stream));
+    CK(cudaMemsetAsync(&c->ctl->bar_count, 0, sizeof(unsigned), c->stream));
+    CK(cudaMemsetAsync(&c->ctl->bar_gen, 0, sizeof(unsigned), c->stream));
+    const int grid = fused_grid(c);
+    for (int k = 0; k < nsteps; ++k) {
+        const FusedLaunch F = fused_launch(c);
+        const cudaError_t e = launch_fused(F, c->group_m, grid, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "persistent step launch");
+        c->cur ^= 1;
+    }
+    c->skeys = c->keys[c->passes & 1];
+    c->last_fused = true;
+    return SPH_OK;
+}
+
+sph_status capture_step_graphs(sph_ctx* c);
+
+// nsteps steps in the context's mode (tables already uploaded, rates valid).
+sph_status run_steps(sph_ctx* c, int nsteps) {
+    if (nsteps <= 0) return SPH_OK;
+    if (c->step_mode == SPH_STEP_PERSISTENT) return run_fused(c, nsteps);
+    if (!c->graph[0] || c->graph_timed != c->timing) {
+        sph_status s = capture_step_graphs(c);
+        if (s != SPH_OK) return s;
+    }
+    for (int k = 0; k < nsteps; ++k) {
+        CK(cudaGraphLaunch(c->graph[c->cur], c->stream));
+        c->cur ^= 1;
+    }
+    c->skeys = c->keys[c->passes & 1];
+    c->last_fused = false;
+    return SPH_OK;
+}
 
 // Instance table on the device: one entry (a single problem: its domain, scheme, dt) or
 // one per batch instance. Uploaded outside graph capture when it changes.
@@ -492,8 +593,8 @@ sph_status capture_step_graphs(sph_ctx* c) {
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
         enqueue_build(c, 1, 1, 0, c->timing);
-        enqueue_eval(c, 1);
-        mark(c, 5, c->timing);
+        enqueue_eval(c, 1, c->timing);
+        mark(c, 6, c->timing);
         cudaError_t e = cudaStreamEndCapture(c->stream, &g);
         if (e != cudaSuccess) {
             c->cur = cur0;
@@ -698,10 +799,13 @@ sph_status create_impl(const sph_domain* domains, int ninst, const sph_array_des
                                                       domain->kernel, 1 << k);
             if (c->sms * c->bps[pass][k] > c->grid_cap) c->grid_cap = c->sms * c->bps[pass][k];
         }
+    for (int k = 0; k < 4; ++k)
+        c->fused_bps[k] = fused_max_blocks_per_sm(domain->precision, domain->dim, domain->kernel, 1 << k);
     {
-        int td = 1, tm = 1;
-        default_groups(c, &td, &tm);
-        set_groups(c, td, tm);
+        int tm = 1, mode = SPH_STEP_GRAPH;
+        default_tuning(c, &tm, &mode);
+        set_groups(c, tm, tm);
+        c->step_mode = mode;
     }
 
     // ---- arena
@@ -716,6 +820,7 @@ sph_status create_impl(const sph_domain* domains, int ninst, const sph_array_des
     bytes += al(radix_hist_words(c->N) * 4);                   // radix histograms
     bytes += al((size_t)c->grid_cap * 8 * 8) + al((size_t)c->grid_cap * 4 * 8);  // partials
     bytes += al(N * 4);                                        // neighbour-list lengths
+    bytes += al((size_t)c->sms * FUSED_MAX_BPS * FUSED_PART * 8);  // persistent partials
     bytes += al(sizeof(Control));
     bytes += al((size_t)HIST_CAP * DIAG_N * 8);                // history ring
     const size_t io_bytes = al(N * 4) + 2 * al(N * 8 + 8);     // io scratch
@@ -756,6 +861,7 @@ sph_status create_impl(const sph_domain* domains, int ninst, const sph_array_des
     c->pm = (double*)arena_take(p, (size_t)c->grid_cap * 8 * 8);
     c->pd = (double*)arena_take(p, (size_t)c->grid_cap * 4 * 8);
     c->cnt = (uint32_t*)arena_take(p, N * 4);
+    c->fpart = (double*)arena_take(p, (size_t)c->sms * FUSED_MAX_BPS * FUSED_PART * 8);
     c->ctl = (Control*)arena_take(p, sizeof(Control));
     c->history = (double*)arena_take(p, (size_t)HIST_CAP * DIAG_N * 8);
     c->io = arena_take(p, io_bytes);
@@ -943,15 +1049,8 @@ sph_status sph_step_batch(sph_ctx* c, const sph_scheme* schemes, const double* d
         if (dt[k] > 0.0)
             CK(cudaMemcpyAsync(&c->idt[k], &dt[k], sizeof(double), cudaMemcpyHostToDevice, c->stream));
     if (nsteps > 0) {
-        if (!c->graph[0] || c->graph_timed != c->timing) {
-            sph_status s = capture_step_graphs(c);
-            if (s != SPH_OK) return s;
-        }
-        for (int k = 0; k < nsteps; ++k) {
-            CK(cudaGraphLaunch(c->graph[c->cur], c->stream));
-            c->cur ^= 1;
-        }
-        c->skeys = c->keys[c->passes & 1];
+        sph_status s = run_steps(c, nsteps);
+        if (s != SPH_OK) return s;
         c->steps_total += (unsigned)nsteps;
         if (c->timing) c->timed_step_ran = true;
     }
@@ -1127,17 +1226,9 @@ sph_status sph_step_async(sph_ctx* c, const sph_scheme* scheme, double dt, int32
     if (s != SPH_OK) return s;
     if (dt > 0.0) CK(cudaMemcpyAsync(&c->ctl->dt, &dt, sizeof dt, cudaMemcpyHostToDevice, c->stream));
     if (nsteps == 0) return SPH_OK;
-    if (!c->graph[0] || c->graph_timed != c->timing) {
-        s = capture_step_graphs(c);
-        if (s != SPH_OK) return s;
-    }
-    for (int k = 0; k < nsteps; ++k) {
-        CK(cudaGraphLaunch(c->graph[c->cur], c->stream));
-        c->cur ^= 1;
-    }
+    s = run_steps(c, nsteps);
+    if (s != SPH_OK) return s;
     c->steps_total += (unsigned)nsteps;
-    // the build inside the graph leaves the sorted keys in the parity-fixed buffer
-    c->skeys = c->keys[c->passes & 1];
     c->nbr_valid = true;
     c->have_rates = true;
     if (c->timing) c->timed_step_ran = true;
@@ -1158,16 +1249,27 @@ sph_status sph_step(sph_ctx* c, const sph_scheme* scheme, double dt, int32_t nst
 sph_status sph_set_timing(sph_ctx* c, int32_t enable) {
     if (!c) return fail(c, SPH_ERR_INVALID, "ctx is NULL");
     if (enable && !c->ev[0])
-        for (int k = 0; k < 6; ++k) CK(cudaEventCreate(&c->ev[k]));
+        for (int k = 0; k < 7; ++k) CK(cudaEventCreate(&c->ev[k]));
     c->timing = enable != 0;
     return SPH_OK;
 }
 
-sph_status sph_phase_times(sph_ctx* c, float out[5]) {
+sph_status sph_phase_times(sph_ctx* c, float out[6]) {
     if (!c || !out) return fail(c, SPH_ERR_INVALID, "NULL argument");
-    if (!c->timed_step_ran || !c->ev[0]) return fail(c, SPH_ERR_STATE, "no timed step has run");
+    if (!c->timed_step_ran) return fail(c, SPH_ERR_STATE, "no timed step has run");
+    if (c->last_fused) {  // phase-end stamps of the persistent kernel (block 0)
+        Control h{};
+        CK(cudaMemcpyAsync(&h, c->ctl, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        const unsigned long long* t = h.stamp;
+        const double d[6] = {(double)(t[1] - t[0]), (double)(t[2] - t[1]), (double)(t[3] - t[2]),
+                             0.0, (double)(t[4] - t[3]), (double)(t[6] - t[4])};
+        for (int k = 0; k < 6; ++k) out[k] = (float)(d[k] * 1e-6);
+        return SPH_OK;
+    }
+    if (!c->ev[0]) return fail(c, SPH_ERR_STATE, "no timed step has run");
     CK(cudaStreamSynchronize(c->stream));
-    for (int k = 0; k < 5; ++k) CK(cudaEventElapsedTime(&out[k], c->ev[k], c->ev[k + 1]));
+    for (int k = 0; k < 6; ++k) CK(cudaEventElapsedTime(&out[k], c->ev[k], c->ev[k + 1]));
     return SPH_OK;
 }
 
@@ -1176,7 +1278,7 @@ sph_status sph_kernels_per_step(const sph_ctx* ctx, const sph_scheme* scheme, in
     if (!c || !scheme || !count) return fail(c, SPH_ERR_INVALID, "NULL argument");
     // drift+keys, 3 per radix pass, reorder, cell table, density pass, momentum pass
     // (+ the per-instance reduction of a batch)
-    *count = 1 + 3 * c->passes + 1 + 1 + 1 + 1 + (c->ninst ? 1 : 0);
+    *count = c->step_mode == SPH_STEP_PERSISTENT ? 1 : 1 + 3 * c->passes + 1 + 1 + 1 + 1 + (c->ninst ? 1 : 0);
     return SPH_OK;
 }
 
@@ -1184,8 +1286,135 @@ sph_status sph_set_groups(sph_ctx* c, int32_t momentum_lanes) {
     if (!c) return fail(c, SPH_ERR_INVALID, "ctx is NULL");
     if (momentum_lanes != 1 && momentum_lanes != 2 && momentum_lanes != 4 && momentum_lanes != 8)
         return fail(c, SPH_ERR_INVALID, "lanes per destination must be 1, 2, 4 or 8");
-    set_groups(c, 1, momentum_lanes);
+    set_groups(c, momentum_lanes, momentum_lanes);
     drop_graphs(c);
+    return SPH_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Device copy of everything a few trial steps change (the current set, the control block,
+// the batch's per-instance time, dt and records), to put the state back bitwise.
+struct DevSnap {
+    char* buf = nullptr;
+    size_t bytes = 0;
+};
+
+size_t snap_bytes(const sph_ctx* c) {
+    const size_t N = (size_t)c->N;
+    return 15 * N * 8 + N * 4 + sizeof(Control) + (size_t)c->ninst * (2 + DIAG_N) * 8;
+}
+
+cudaError_t snap_copy(sph_ctx* c, const DevSnap& sn, bool restore) {
+    const size_t N = (size_t)c->N;
+    const ParticleSet& S = c->set[c->cur];
+    double* f[15] = {S.x[0], S.x[1], S.x[2], S.u[0], S.u[1], S.u[2], S.rho, S.m,
+                     S.arho, S.a[0], S.a[1], S.a[2], S.xs[0], S.xs[1], S.xs[2]};
+    char* p = sn.buf;
+    cudaError_t e = cudaSuccess;
+    auto cp = [&](void* dev, size_t b) {
+        if (e == cudaSuccess)
+            e = restore ? cudaMemcpyAsync(dev, p, b, cudaMemcpyDeviceToDevice, c->stream)
+                        : cudaMemcpyAsync(p, dev, b, cudaMemcpyDeviceToDevice, c->stream);
+        p += b;
+    };
+    for (int k = 0; k < 15; ++k) cp(f[k], N * 8);
+    cp(S.tag, N * 4);
+    cp(c->ctl, sizeof(Control));
+    if (c->ninst) {
+        cp(c->idt, (size_t)c->ninst * 8);
+        cp(c->it, (size_t)c->ninst * 8);
+        cp(c->irec, (size_t)c->ninst * DIAG_N * 8);
+    }
+    return e;
+}
+
+// Times a few steps in each mode from the same state and keeps the faster mode; the
+// state, time and records are put back afterwards.
+sph_status choose_mode(sph_ctx* c) {
+    if (c->fused_bps[tindex(c->group_m)] < 1) {
+        c->step_mode = SPH_STEP_GRAPH;
+        return SPH_OK;
+    }
+    int coop = 0;
+    CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device));
+    if (!coop) {
+        c->step_mode = SPH_STEP_GRAPH;
+        return SPH_OK;
+    }
+    DevSnap sn;
+    sn.bytes = snap_bytes(c);
+    void* mem = nullptr;
+    if (c->alloc) mem = c->alloc(sn.bytes, c->user);
+    else if (cudaMalloc(&mem, sn.bytes) != cudaSuccess) mem = nullptr;
+    if (!mem) {
+        cudaGetLastError();
+        return fail(c, SPH_ERR_OOM, "autotune snapshot of " + std::to_string(sn.bytes) + " bytes");
+    }
+    sn.buf = (char*)mem;
+    const int cur0 = c->cur;
+    uint32_t* skeys0 = c->skeys;
+    const bool fused0 = c->last_fused;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    sph_status st = SPH_OK;
+    float ms[2] = {0.f, 0.f};
+    cudaError_t e = snap_copy(c, sn, false);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    for (int mode = 0; mode < 2 && e == cudaSuccess && st == SPH_OK; ++mode) {
+        c->step_mode = mode;
+        st = run_steps(c, 2);  // warm-up (and graph capture)
+        if (st == SPH_OK) e = cudaEventRecord(e0, c->stream);
+        if (st == SPH_OK && e == cudaSuccess) st = run_steps(c, 6);
+        if (st == SPH_OK && e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+        if (st == SPH_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (st == SPH_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms[mode], e0, e1);
+        // back to the starting state
+        c->cur = cur0;
+        c->skeys = skeys0;
+        if (e == cudaSuccess) e = snap_copy(c, sn, true);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    }
+    c->last_fused = fused0;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(c->stream);
+    free_dev(c, mem);
+    if (e != cudaSuccess) return cuda_fail(c, e, "autotune of the step mode");
+    if (st != SPH_OK) return st;
+    c->step_mode = ms[1] < ms[0] ? SPH_STEP_PERSISTENT : SPH_STEP_GRAPH;
+    return SPH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sph_status sph_set_step_mode(sph_ctx* c, int32_t mode) {
+    if (!c) return fail(c, SPH_ERR_INVALID, "ctx is NULL");
+    if (mode != SPH_STEP_GRAPH && mode != SPH_STEP_PERSISTENT)
+        return fail(c, SPH_ERR_INVALID, "unknown step mode");
+    if (mode == SPH_STEP_PERSISTENT) {
+        int coop = 0;
+        CK(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, c->device));
+        if (!coop) return fail(c, SPH_ERR_INVALID, "the device has no cooperative launch");
+    }
+    c->step_mode = mode;
+    return SPH_OK;
+}
+
+sph_status sph_get_tuning(const sph_ctx* c, int32_t* momentum_lanes, int32_t* mode) {
+    if (!c) return fail(nullptr, SPH_ERR_INVALID, "ctx is NULL");
+    if (momentum_lanes) *momentum_lanes = c->group_m;
+    if (mode) *mode = c->step_mode;
+    return SPH_OK;
+}
+
+sph_status sph_set_wait_limit(sph_ctx* c, uint64_t ns) {
+    if (!c) return fail(c, SPH_ERR_INVALID, "ctx is NULL");
+    c->wait_ns = ns;
     return SPH_OK;
 }
 
@@ -1202,7 +1431,7 @@ sph_status sph_autotune(sph_ctx* c, const sph_scheme* scheme, int32_t* chosen) {
         int best = c->group_m;
         float best_ms = 1e30f;
         for (int T = 1; T <= 8; T *= 2) {
-            c->group_m = T;
+            set_groups(c, T, T);
             for (int r = 0; r <= 5; ++r) {
                 if (r == 1) CK(cudaEventRecord(e0, c->stream));
                 enqueue_eval(c, 0);
@@ -1219,7 +1448,12 @@ sph_status sph_autotune(sph_ctx* c, const sph_scheme* scheme, int32_t* chosen) {
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        c->group_m = best;
+        set_groups(c, best, best);
+        drop_graphs(c);
+        s = sync_status(c);
+        if (s != SPH_OK) return s;
+        s = choose_mode(c);
+        if (s != SPH_OK) return s;
         drop_graphs(c);
         if (chosen) *chosen = best;
         return sync_status(c);
@@ -1233,16 +1467,14 @@ sph_status sph_autotune(sph_ctx* c, const sph_scheme* scheme, int32_t* chosen) {
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    StepLaunch L = step_launch(c, 0);
     int best = c->group_m;
     float best_ms = 1e30f;
     const int reps = 5;
-    for (int T = 1; T <= 8; T *= 2) {
-        L.group_m = T;
-        L.grid_m = pass_grid(c, 1, T);
+    for (int T = 1; T <= 8; T *= 2) {  // whole evaluations (density + momentum pass)
+        set_groups(c, T, T);
         for (int r = 0; r <= reps; ++r) {
             if (r == 1) CK(cudaEventRecord(e0, c->stream));
-            launch_momentum_pass(L, c->stream);
+            enqueue_eval(c, 0);
         }
         CK(cudaEventRecord(e1, c->stream));
         CK(cudaEventSynchronize(e1));
@@ -1256,21 +1488,16 @@ sph_status sph_autotune(sph_ctx* c, const sph_scheme* scheme, int32_t* chosen) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    {
-        std::lock_guard<std::mutex> lock(g_tune_lock);
-        const TuneKey k = tune_key(c);
-        bool found = false;
-        for (auto& e : g_tune_cache)
-            if (e.first == k) {
-                e.second = {1, best};
-                found = true;
-            }
-        if (!found) g_tune_cache.push_back({k, {1, best}});
-    }
-    set_groups(c, 1, best);
+    set_groups(c, best, best);
     drop_graphs(c);
-    s = initial_eval(c, scheme, 0.0);  // leave rates and diagnostics of the chosen shape
+    s = initial_eval(c, scheme, 0.0);  // rates and diagnostics of the chosen shape
     if (s != SPH_OK) return s;
+    s = sync_status(c);
+    if (s != SPH_OK) return s;
+    s = choose_mode(c);
+    if (s != SPH_OK) return s;
+    drop_graphs(c);
+    remember_tuning(c);
     if (chosen) *chosen = best;
     return sync_status(c);
 }

@@ -1,0 +1,302 @@
+// Persistent step: the whole time step (Sec. 2.1 predictor-corrector with the Sec. 2.2
+// neighbour build and the Sec. 3.4 pair loops) as ONE cooperative launch. Every block
+// stays resident for the step and walks each phase with a grid-stride loop; the phases
+// are separated by a grid-wide barrier:
+//   drift + cell keys | radix sort (histogram | digit scan | scatter, per 8-bit pass) |
+//   reorder + predictor kick + EOS shadow, and the cell table | density pass |
+//   momentum pass + corrector kick | diagnostics, next dt (per instance for a batch).
+// The per-particle and per-tile bodies are the ones of the per-phase kernels, so both
+// forms compute the same step; a small problem saves the launch gaps between phases.
+//
+// The barrier spins on a generation counter in the control block with a time limit:
+// a block that waits longer raises ST_TIMEOUT and leaves, and the others leave at their
+// next barrier (they also watch the status word), so no wait is unbounded. A limit of 0
+// lets no block wait at all (the first barrier of a multi-block grid then fails).
+#pragma once
+
+#include "pairs_impl.cuh"
+#include "reduce_impl.cuh"
+#include "sort_impl.cuh"
+#include "step_impl.cuh"
+
+namespace sph {
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier (all blocks co-resident: cooperative launch). Returns false, in every
+// thread of the block, if the step must stop: the wait ran out (ST_TIMEOUT raised here)
+// or a status bit is set.
+__device__ __forceinline__ bool grid_sync(Control* ctl, unsigned long long limit_ns) {
+    __syncthreads();
+    int ok = 1;
+    if (threadIdx.x == 0) {
+        volatile unsigned* gen = &ctl->bar_gen;
+        volatile unsigned* status = &ctl->status;
+        const unsigned g = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(&ctl->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&ctl->bar_gen, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (*gen == g) {
+                if (limit_ns == 0 || (*status & ST_TIMEOUT) || global_ns() - t0 > limit_ns) {
+                    atomicOr(&ctl->status, ST_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(40);
+            }
+        }
+        __threadfence();
+        if (*status) ok = 0;
+    }
+    return __syncthreads_and(ok) != 0;
+}
+
+// Block sums (k < NMAX0 or k >= NMAX1) and maxima (NMAX0 <= k < NMAX1) of NV values per
+// thread, fixed tree order; the result is valid in thread 0.
+template <int NV, int NMAX0, int NMAX1>
+__device__ __forceinline__ void block_reduce(double* v, double (*red)[FUSED_PART]) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            const double y = __shfl_down_sync(0xffffffffu, v[k], o);
+            v[k] = (k >= NMAX0 && k < NMAX1) ? fmax(v[k], y) : v[k] + y;
+        }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) red[warp][k] = v[k];
+    __syncthreads();
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double t = red[0][k];
+            for (int w = 1; w < FUSED_THREADS / 32; ++w)
+                t = (k >= NMAX0 && k < NMAX1) ? fmax(t, red[w][k]) : t + red[w][k];
+            v[k] = t;
+        }
+    __syncthreads();
+}
+
+template <class Real, int DIM, int KERNEL, int T>
+__global__ void __launch_bounds__(FUSED_THREADS, 2) k_step_fused(const FusedLaunch F) {
+    using V = typename V4<Real>::T;
+    __shared__ union {
+        uint32_t h[RADIX];
+        uint32_t wsum[32];
+        ScatterSmem sc;
+        double red[FUSED_THREADS / 32][FUSED_PART];
+        double bred[FUSED_THREADS / 32][10];
+    } sm;
+    const StepLaunch& L = F.L;
+    Control* ctl = L.ctl;
+    if (ctl->status) return;
+    const Inst<Real>* __restrict__ tab = (const Inst<Real>*)L.tab;
+    const int nb = gridDim.x;
+    const int tid = blockIdx.x * FUSED_THREADS + threadIdx.x, nthreads = nb * FUSED_THREADS;
+    const bool stamp = blockIdx.x == 0 && threadIdx.x == 0;
+    V* P = (V*)L.P;
+    V* Q = (V*)L.Q;
+    Real* R = (Real*)L.R;
+    if (stamp) ctl->stamp[0] = global_ns();
+
+    // ---- drift of the fluid (predictor half-kick folded in) + cell keys
+    {
+        unsigned outside = 0;
+        for (int i = tid; i < L.n; i += nthreads) {
+            const int inst = find_instance(L.id_bounds, L.ninst, L.Sin.tag[i] & ID_MASK);
+            const Inst<Real>& I = tab[inst];
+            int clamped = 0;
+            F.keys[0][i] = I.cell_base + drift_key_one(L.Sin, i, I.G, I.C, L.idt[inst], 1, clamped);
+            outside += clamped;
+        }
+        for (int o = 16; o > 0; o >>= 1) outside += __shfl_down_sync(0xffffffffu, outside, o);
+        if ((threadIdx.x & 31) == 0 && outside) atomicAdd(&ctl->outside, outside);
+    }
+    if (!grid_sync(ctl, F.wait_ns)) return;
+    if (stamp) ctl->stamp[1] = global_ns();
+
+    // ---- stable LSD radix sort of (key, index)
+    uint32_t* totals = F.hist + (size_t)RADIX * F.ntiles;
+    int cur = 0;
+    for (int p = 0; p < F.passes; ++p) {
+        const int shift = 8 * p;
+        for (int t = blockIdx.x; t < F.ntiles; t += nb) {
+            radix_hist_tile(F.keys[cur], L.n, shift, F.hist, F.ntiles, t, sm.h);
+            __syncthreads();
+        }
+        if (!grid_sync(ctl, F.wait_ns)) return;
+        for (int d = blockIdx.x; d < RADIX; d += nb) {
+            radix_scan_row(F.hist, F.ntiles, totals, d, sm.wsum);
+            __syncthreads();
+        }
+        if (!grid_sync(ctl, F.wait_ns)) return;
+        for (int t = blockIdx.x; t < F.ntiles; t += nb) {
+            radix_scatter_tile(F.keys[cur], p ? F.vals[cur] : nullptr, F.keys[cur ^ 1],
+                               F.vals[cur ^ 1], L.n, shift, F.hist, totals, F.ntiles, t, sm.sc);
+            __syncthreads();
+        }
+        if (!grid_sync(ctl, F.wait_ns)) return;
+        cur ^= 1;
+    }
+    if (stamp) ctl->stamp[2] = global_ns();
+    const uint32_t* __restrict__ skeys = F.keys[cur];
+    const uint32_t* __restrict__ perm = F.vals[cur];
+
+    // ---- gather into cell order (predictor kick, EOS shadow) and the cell table
+    for (int k = tid; k < L.n; k += nthreads) {
+        const int inst = find_instance(L.cell_bounds, L.ninst, skeys[k]);
+        reorder_one<Real>(L.Sin, L.S, k, (int)perm[k], L.dim, tab[inst].C, L.idt[inst], 1, 0, P,
+                          Q, R);
+    }
+    for (int c = tid; c <= F.ncells; c += nthreads) F.off[c] = cell_offset(skeys, L.n, (uint32_t)c);
+    if (!grid_sync(ctl, F.wait_ns)) return;
+    if (stamp) ctl->stamp[3] = global_ns();
+
+    // ---- density pass (T lanes per destination)
+    const Group<T> g;
+    {
+        DensityCounts dc{0, 0, 0, 0};
+        for (int i = tid / T; i < L.n; i += nthreads / T) {
+            const uint32_t key = skeys[i];
+            const int inst = find_instance(L.cell_bounds, L.ninst, key);
+            const Inst<Real>& I = tab[inst];
+            density_dest<Real, DIM, KERNEL, T>(i, g, key - I.cell_base, P, Q, R, F.off + I.cell_base,
+                                            L.n, I.G, I.K, I.C, L.S, L.idt[inst], 1, L.nl, L.cnt,
+                                            L.maxn, dc,
+                                            L.finalize ? nullptr : L.pcount + 2 * (size_t)i,
+                                            L.finalize ? nullptr : L.pcount + 2 * (size_t)i + 1);
+        }
+        if (dc.overflow) atomicOr(&ctl->status, ST_CAPACITY);
+        if (L.finalize) {
+            double v[3] = {dc.pairs, dc.cand, dc.wall};
+            block_reduce<3, 3, 3>(v, sm.red);
+            if (threadIdx.x == 0)
+                for (int k = 0; k < 3; ++k) F.part[(size_t)blockIdx.x * FUSED_PART + 7 + k] = v[k];
+        }
+    }
+    if (!grid_sync(ctl, F.wait_ns)) return;
+    if (stamp) ctl->stamp[4] = global_ns();
+
+    // ---- momentum pass (T lanes per destination) + corrector kick
+    {
+        MomDiag md{0, 0, 0, 0, 0, 0, 0};
+        for (int i = tid / T; i < L.n; i += nthreads / T) {
+            const int inst = find_instance(L.cell_bounds, L.ninst, skeys[i]);
+            const Inst<Real>& I = tab[inst];
+            momentum_dest<Real, DIM, KERNEL, T>(i, g, P, Q, R, L.n, I.G, I.K, I.C, L.S,
+                                                L.idt[inst], 1, L.nl, L.cnt, md);
+        }
+        if (L.finalize) {
+            double v[7] = {md.px, md.py, md.pz, md.ke, md.u2, md.a2, (double)md.bad};
+            block_reduce<7, 4, 7>(v, sm.red);
+            if (threadIdx.x == 0)
+                for (int k = 0; k < 7; ++k) F.part[(size_t)blockIdx.x * FUSED_PART + k] = v[k];
+        }
+    }
+    if (!grid_sync(ctl, F.wait_ns)) return;
+    if (stamp) ctl->stamp[5] = global_ns();
+
+    // ---- diagnostics, time and next dt
+    if (L.finalize) {
+        if (blockIdx.x != 0) return;
+        double w[10];
+#pragma unroll
+        for (int k = 0; k < 10; ++k) w[k] = 0.0;
+        for (int b = threadIdx.x; b < nb; b += FUSED_THREADS) {
+            const double* p = F.part + (size_t)b * FUSED_PART;
+#pragma unroll
+            for (int k = 0; k < 10; ++k) w[k] = (k >= 4 && k < 7) ? fmax(w[k], p[k]) : w[k] + p[k];
+        }
+        block_reduce<10, 4, 7>(w, sm.red);
+        if (threadIdx.x == 0) {
+            finish_single(ctl, L.history, tab[0].C, L.idt[0], 1, w);
+            ctl->outside = 0;
+            ctl->stamp[6] = global_ns();
+        }
+    } else {
+        for (int inst = blockIdx.x; inst < L.ninst; inst += nb)
+            batch_reduce_inst<Real, FUSED_THREADS>(L.S, L.pcount, F.off, tab[inst], inst, L.dim,
+                                                   L.idt, L.it, L.irec, 1, ctl, sm.bred);
+        if (stamp) {
+            ctl->outside = 0;
+            ctl->stamp[6] = global_ns();
+        }
+    }
+}
+
+template <class Real, int DIM, int KERNEL, int T>
+cudaError_t launch_fused_t(const FusedLaunch& F, int grid, cudaStream_t st) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(FUSED_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_step_fused<Real, DIM, KERNEL, T>, F);
+}
+
+template <class Real, int DIM, int KERNEL, int T>
+int fused_bps_t() {
+    int b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_step_fused<Real, DIM, KERNEL, T>,
+                                                  FUSED_THREADS, 0);
+    return b;
+}
+
+// One precision's dispatch over (dim, kernel, lanes per destination).
+template <class Real>
+struct FusedDispatch {
+    template <int DIM, int KERNEL>
+    static cudaError_t launch_dk(const FusedLaunch& F, int T, int grid, cudaStream_t st) {
+        switch (T) {
+            case 1: return launch_fused_t<Real, DIM, KERNEL, 1>(F, grid, st);
+            case 2: return launch_fused_t<Real, DIM, KERNEL, 2>(F, grid, st);
+            case 4: return launch_fused_t<Real, DIM, KERNEL, 4>(F, grid, st);
+            default: return launch_fused_t<Real, DIM, KERNEL, 8>(F, grid, st);
+        }
+    }
+    template <int DIM, int KERNEL>
+    static int bps_dk(int T) {
+        switch (T) {
+            case 1: return fused_bps_t<Real, DIM, KERNEL, 1>();
+            case 2: return fused_bps_t<Real, DIM, KERNEL, 2>();
+            case 4: return fused_bps_t<Real, DIM, KERNEL, 4>();
+            default: return fused_bps_t<Real, DIM, KERNEL, 8>();
+        }
+    }
+    static cudaError_t launch(const FusedLaunch& F, int T, int grid, cudaStream_t st) {
+        const int sel = (F.L.dim == 3 ? 2 : 0) + (F.L.kernel == WENDLAND_C2 ? 1 : 0);
+        switch (sel) {
+            case 0: return launch_dk<2, QUINTIC>(F, T, grid, st);
+            case 1: return launch_dk<2, WENDLAND_C2>(F, T, grid, st);
+            case 2: return launch_dk<3, QUINTIC>(F, T, grid, st);
+            default: return launch_dk<3, WENDLAND_C2>(F, T, grid, st);
+        }
+    }
+    static int bps(int dim, int kernel, int T) {
+        const int sel = (dim == 3 ? 2 : 0) + (kernel == WENDLAND_C2 ? 1 : 0);
+        switch (sel) {
+            case 0: return bps_dk<2, QUINTIC>(T);
+            case 1: return bps_dk<2, WENDLAND_C2>(T);
+            case 2: return bps_dk<3, QUINTIC>(T);
+            default: return bps_dk<3, WENDLAND_C2>(T);
+        }
+    }
+};
+
+}  // namespace sph

@@ -5,6 +5,7 @@
 // (Eq. eos) fused into the write of the pair-loop shadow arrays, and the cell table.
 #include "sph_device.cuh"
 #include "sph_launch.h"
+#include "sort_impl.cuh"
 #include "step_impl.cuh"
 
 namespace sph {
@@ -33,66 +34,20 @@ __global__ void k_drift_keys(ParticleSet S, int n, const Inst<Real>* __restrict_
 }
 
 // -------------------------------------------------------------- radix sort
-// Stable least-significant-digit radix sort, 8-bit digits. A tile of SORT_TILE keys
-// belongs to one block; inside the tile warp w owns the contiguous range
-// [w * 512, (w + 1) * 512) and walks it in order, so block order, warp order,
-// iteration order and lane order reproduce the input order (stability).
-constexpr int RADIX = 256;
-constexpr int SORT_THREADS = 256;
-constexpr int SORT_WARPS = SORT_THREADS / 32;
-constexpr int SORT_ITEMS = 16;
-constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
-
+// Block bodies in sort_impl.cuh (shared with the persistent step kernel).
 __global__ void __launch_bounds__(SORT_THREADS)
 k_radix_hist(const uint32_t* __restrict__ keys, int n, int shift, uint32_t* hist, int nblocks,
              const Control* ctl) {
     __shared__ uint32_t h[RADIX];
     if (ctl->status) return;
-    h[threadIdx.x] = 0;
-    __syncthreads();
-    const int base = blockIdx.x * SORT_TILE;
-#pragma unroll 4
-    for (int k = 0; k < SORT_ITEMS; ++k) {
-        int idx = base + k * SORT_THREADS + threadIdx.x;
-        if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & (RADIX - 1)], 1u);
-    }
-    __syncthreads();
-    hist[threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+    radix_hist_tile(keys, n, shift, hist, nblocks, blockIdx.x, h);
 }
 
-// Exclusive scan of each digit's row of per-block counts; totals[d] = row sum.
 __global__ void __launch_bounds__(1024)
 k_radix_scan(uint32_t* hist, int nblocks, uint32_t* totals, const Control* ctl) {
     __shared__ uint32_t wsum[32];
     if (ctl->status) return;
-    uint32_t* row = hist + (size_t)blockIdx.x * nblocks;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t carry = 0;
-    for (int base = 0; base < nblocks; base += 1024) {
-        int i = base + threadIdx.x;
-        uint32_t v = i < nblocks ? row[i] : 0u;
-        uint32_t x = v;
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) wsum[warp] = x;
-        __syncthreads();
-        if (warp == 0) {
-            uint32_t s = wsum[lane];
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
-                if (lane >= o) s += y;
-            }
-            wsum[lane] = s;
-        }
-        __syncthreads();
-        uint32_t excl = carry + x - v + (warp ? wsum[warp - 1] : 0u);
-        if (i < nblocks) row[i] = excl;
-        carry += wsum[31];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) totals[blockIdx.x] = carry;
+    radix_scan_row(hist, nblocks, totals, blockIdx.x, wsum);
 }
 
 __global__ void __launch_bounds__(SORT_THREADS)
@@ -100,80 +55,18 @@ k_radix_scatter(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict
                 uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int n, int shift,
                 const uint32_t* __restrict__ hist, const uint32_t* __restrict__ totals, int nblocks,
                 const Control* ctl) {
-    __shared__ uint32_t base_d[RADIX];
-    __shared__ uint32_t wcnt[SORT_WARPS][RADIX];
-    __shared__ uint32_t wsum[SORT_WARPS];
+    __shared__ ScatterSmem sm;
     if (ctl->status) return;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // digit bases: exclusive scan of the 256 digit totals, plus this block's offset
-    {
-        uint32_t v = totals[tid];
-        uint32_t x = v;
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) wsum[warp] = x;
-        for (int w = 0; w < SORT_WARPS; ++w) wcnt[w][tid] = 0;
-        __syncthreads();
-        uint32_t pre = 0;
-        for (int w = 0; w < warp; ++w) pre += wsum[w];
-        base_d[tid] = pre + x - v + hist[tid * nblocks + blockIdx.x];
-    }
-    __syncthreads();
-    const int wbase = blockIdx.x * SORT_TILE + warp * (SORT_TILE / SORT_WARPS);
-    uint32_t kr[SORT_ITEMS], vr[SORT_ITEMS], rank[SORT_ITEMS];
-    const unsigned ltmask = lanemask_lt();
-#pragma unroll
-    for (int it = 0; it < SORT_ITEMS; ++it) {
-        int idx = wbase + it * 32 + lane;
-        bool valid = idx < n;
-        uint32_t key = valid ? keys_in[idx] : 0u;
-        uint32_t d = valid ? ((key >> shift) & (RADIX - 1)) : (uint32_t)RADIX;
-        unsigned peers = __match_any_sync(0xffffffffu, d);
-        uint32_t before = valid ? wcnt[warp][d] : 0u;
-        __syncwarp();
-        if (valid && lane == __ffs(peers) - 1) wcnt[warp][d] = before + __popc(peers);
-        __syncwarp();
-        kr[it] = key;
-        vr[it] = valid ? (vals_in ? vals_in[idx] : (uint32_t)idx) : 0u;
-        rank[it] = before + __popc(peers & ltmask);
-    }
-    __syncthreads();
-    {   // exclusive prefix over warps, per digit
-        uint32_t run = 0;
-        for (int w = 0; w < SORT_WARPS; ++w) {
-            uint32_t c = wcnt[w][tid];
-            wcnt[w][tid] = run;
-            run += c;
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int it = 0; it < SORT_ITEMS; ++it) {
-        int idx = wbase + it * 32 + lane;
-        if (idx < n) {
-            uint32_t d = (kr[it] >> shift) & (RADIX - 1);
-            uint32_t pos = base_d[d] + wcnt[warp][d] + rank[it];
-            keys_out[pos] = kr[it];
-            vals_out[pos] = vr[it];
-        }
-    }
+    radix_scatter_tile(keys_in, vals_in, keys_out, vals_out, n, shift, hist, totals, nblocks,
+                       blockIdx.x, sm);
 }
 
 // offsets[c] = number of sorted keys < c, for c in [0, ncells].
 __global__ void k_cell_offsets(const uint32_t* __restrict__ skeys, int n, int ncells,
                                uint32_t* __restrict__ off, const Control* ctl) {
     if (ctl->status) return;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= ncells; c += gridDim.x * blockDim.x) {
-        int lo = 0, hi = n;
-        while (lo < hi) {
-            int mid = (lo + hi) >> 1;
-            if (skeys[mid] < (uint32_t)c) lo = mid + 1;
-            else hi = mid;
-        }
-        off[c] = (uint32_t)lo;
-    }
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= ncells; c += gridDim.x * blockDim.x)
+        off[c] = cell_offset(skeys, n, (uint32_t)c);
 }
 
 // ------------------------------------------------------------------ reorder
@@ -338,6 +231,11 @@ int radix_passes(int ncells) {
     int bits = 0;
     while (bits < 32 && (1ull << bits) < (unsigned long long)ncells) ++bits;
     return (bits + 7) / 8;
+}
+
+int radix_tiles(int n) {
+    const int t = (n + SORT_TILE - 1) / SORT_TILE;
+    return t < 1 ? 1 : t;
 }
 
 size_t radix_hist_words(int n) {

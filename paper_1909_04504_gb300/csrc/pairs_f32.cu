@@ -13,7 +13,14 @@ int pairs_bps_f32(int pass, int dim, int kernel, int T) {
     }
 }
 
-void launch_density_f32(const StepLaunch& L, cudaStream_t st) { PairDispatch<float>::density(L, st); }
+void launch_density_f32(const StepLaunch& L, cudaStream_t st) {
+    switch (L.group_d) {
+        case 1: PairDispatch<float>::density_t<1>(L, st); break;
+        case 2: PairDispatch<float>::density_t<2>(L, st); break;
+        case 4: PairDispatch<float>::density_t<4>(L, st); break;
+        default: PairDispatch<float>::density_t<8>(L, st); break;
+    }
+}
 
 void launch_momentum_f32(const StepLaunch& L, cudaStream_t st) {
     switch (L.group_m) {

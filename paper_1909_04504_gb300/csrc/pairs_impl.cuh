@@ -19,6 +19,7 @@
 #include "sph_device.cuh"
 #include "sph_launch.h"
 #include "step_impl.cuh"
+#include "reduce_impl.cuh"
 
 namespace sph {
 
@@ -130,11 +131,15 @@ __device__ __forceinline__ void block_counts(double c0, double c1, double c2, do
 }
 
 // ---------------------------------------------------------------- density pass
-// One thread per destination. (1) Neighbour scan: the 3^(d-1) contiguous source runs of
-// the destination's stencil, the exact neighbour predicate, and the accepted sources
-// written to the interleaved neighbour list nl[k * n + i] (k < maxn; cnt[i] entries).
-// Continuity mode lists interacting sources only (a wall destination takes fluid
-// sources); summation mode lists every neighbour. (2) The density group over the list:
+// A group of T lanes per destination (T = 1, 2, 4 or 8). (1) Neighbour scan: the 3^(d-1)
+// contiguous source runs of the destination's stencil, T candidates at a time (lane t
+// takes the t-th), the exact neighbour predicate, and the accepted sources appended to
+// the interleaved neighbour list nl[k * n + i] (k < maxn; cnt[i] entries) in candidate
+// order: a ballot over the group gives each accepted lane its slot, so the list is the
+// same for every T. Continuity mode lists interacting sources only (a wall destination
+// takes fluid sources); summation mode lists every neighbour. (2) The density group
+// over the list, lane t taking every T-th entry with compensated partial sums combined
+// by a fixed shuffle tree:
 //  summation (Eq. 2): rho_i = sum_j m_j W_ij, self term included;
 //  continuity (Eq. continuity:sph): arho_i = sum_j m_j v_ij . grad_i W_ij and, inside a
 //    step, rho_i += dt arho_i (density advanced like the positions, Sec. 2.1 reading).
@@ -146,9 +151,17 @@ struct DensityCounts {
     int overflow;
 };
 
-// Density pass for destination i (cell key `key`, cell table `off` of its grid).
-template <class Real, int DIM, int KERNEL>
-__device__ __forceinline__ void density_dest(int i, uint32_t key,
+template <int T>
+__device__ __forceinline__ uint32_t group_sum_u32(uint32_t v, const Group<T>& g) {
+#pragma unroll
+    for (int o = T / 2; o > 0; o >>= 1) v += g.down(v, o);
+    return v;
+}
+
+// Density pass for destination i (cell key `key`, cell table `off` of its grid), shared by
+// the T lanes of group g (lane 0 finishes).
+template <class Real, int DIM, int KERNEL, int T>
+__device__ __forceinline__ void density_dest(int i, const Group<T>& g, uint32_t key,
                                              const typename V4<Real>::T* __restrict__ P,
                                              typename V4<Real>::T* __restrict__ Q,
                                              Real* __restrict__ R, const uint32_t* __restrict__ off,
@@ -164,21 +177,35 @@ __device__ __forceinline__ void density_dest(int i, uint32_t key,
     int cx, cy, cz;
     cell_of_key(G, key, cx, cy, cz);
     uint32_t k = 0, npairs = 0, ncand = 0;
+    const unsigned below = (1u << g.t) - 1u;
     for_each_run<DIM>(G, off, cx, cy, cz, [&](uint32_t jb, uint32_t je) {
 #pragma unroll 2
-        for (uint32_t j = jb; j < je; ++j) {
-            if ((int)j == i) continue;
-            ++ncand;
-            const typename V4<Real>::T pj = P[j];
-            Real dx, dy, dz;
-            const Real r2 = separation<Real, DIM>(pi, pj, G, K, dx, dy, dz);
-            if (r2 < K.kh2) {
-                const bool interacting = fluid_i || pj.w > Real(0);
-                if (interacting || summation) {
+        for (uint32_t c = jb; c < je; c += T) {
+            const uint32_t j = c + g.t;
+            bool listed = false;
+            if (j < je && (int)j != i) {
+                ++ncand;
+                const typename V4<Real>::T pj = P[j];
+                Real dx, dy, dz;
+                const Real r2 = separation<Real, DIM>(pi, pj, G, K, dx, dy, dz);
+                if (r2 < K.kh2) {
+                    const bool interacting = fluid_i || pj.w > Real(0);
+                    listed = interacting || summation;
+                    npairs += interacting ? 1u : 0u;
+                }
+            }
+            if (T == 1) {
+                if (listed) {
                     if (k < (uint32_t)maxn) nl[(size_t)k * n + i] = j;
                     ++k;
                 }
-                npairs += interacting ? 1u : 0u;
+            } else {
+                const unsigned m = g.ballot(listed);
+                if (listed) {
+                    const uint32_t pos = k + __popc(m & below);
+                    if (pos < (uint32_t)maxn) nl[(size_t)pos * n + i] = j;
+                }
+                k += __popc(m);
             }
         }
     });
@@ -186,11 +213,12 @@ __device__ __forceinline__ void density_dest(int i, uint32_t key,
         dc.overflow = 1;
         k = maxn;
     }
-    cnt[i] = k;
+    if (g.t == 0) cnt[i] = k;
+    g.sync();  // the list entries of the other lanes are visible from here on
     Acc<Real> sum;
     sum.zero();
     const typename V4<Real>::T qi = Q[i];
-    for (uint32_t kk = 0; kk < k; ++kk) {
+    for (uint32_t kk = g.t; kk < k; kk += T) {
         const uint32_t j = nl[(size_t)kk * n + i];
         const typename V4<Real>::T pj = P[j];
         Real dx, dy, dz;
@@ -206,6 +234,18 @@ __device__ __forceinline__ void density_dest(int i, uint32_t key,
             sum.add(fabs(pj.w) * Gk * vdotr);
         }
     }
+    if (T > 1) group_reduce<Real, T>(sum, g);
+    dc.pairs += (double)npairs;
+    dc.cand += (double)ncand;
+    if (!fluid_i) dc.wall += (double)npairs;
+    if (npairs_out) {
+        const uint32_t np = group_sum_u32<T>(npairs, g), nc = group_sum_u32<T>(ncand, g);
+        if (g.t == 0) {
+            *npairs_out = np;
+            *ncand_out = nc;
+        }
+    }
+    if (g.t != 0) return;
     double rho;
     if (summation) {
         rho = sum.value() + (double)(fabs(pi.w) * K.wfac * kernel_w<Real, KERNEL>(Real(0)));
@@ -220,17 +260,12 @@ __device__ __forceinline__ void density_dest(int i, uint32_t key,
     const double p = tait_pressure(rho, C);
     reinterpret_cast<Real*>(&Q[i])[3] = (Real)rho;
     R[i] = (Real)(p / (rho * rho));
-    dc.pairs += (double)npairs;
-    dc.cand += (double)ncand;
-    if (!fluid_i) dc.wall += (double)npairs;
-    if (npairs_out) *npairs_out = npairs;
-    if (ncand_out) *ncand_out = ncand;
 }
 
 // Density pass over all destinations; each finds its instance's constants in the table
 // (one entry for a single problem). Single problems accumulate block counts in pd; batches
 // store per-particle counts in pcount for the per-instance reduction.
-template <class Real, int DIM, int KERNEL>
+template <class Real, int DIM, int KERNEL, int T>
 __global__ void __launch_bounds__(PAIR_THREADS, 6)
 k_density(const typename V4<Real>::T* __restrict__ P, typename V4<Real>::T* __restrict__ Q,
           Real* __restrict__ R, const uint32_t* __restrict__ skeys, const uint32_t* __restrict__ off,
@@ -239,15 +274,17 @@ k_density(const typename V4<Real>::T* __restrict__ P, typename V4<Real>::T* __re
           uint32_t* __restrict__ nl, uint32_t* __restrict__ cnt, int maxn,
           double* __restrict__ pd, uint32_t* __restrict__ pcount) {
     if (ctl->status) return;
+    const Group<T> g;
     DensityCounts dc{0, 0, 0, 0};
-    for (int i = blockIdx.x * PAIR_THREADS + threadIdx.x; i < n; i += gridDim.x * PAIR_THREADS) {
+    const int groups = gridDim.x * (PAIR_THREADS / T);
+    for (int i = (blockIdx.x * PAIR_THREADS + threadIdx.x) / T; i < n; i += groups) {
         const uint32_t key = skeys[i];
         const int inst = find_instance(cell_bounds, ninst, key);
         const Inst<Real>& I = tab[inst];
-        density_dest<Real, DIM, KERNEL>(i, key - I.cell_base, P, Q, R, off + I.cell_base, n, I.G,
-                                        I.K, I.C, S, idt[inst], kick, nl, cnt, maxn, dc,
-                                        pcount ? pcount + 2 * (size_t)i : nullptr,
-                                        pcount ? pcount + 2 * (size_t)i + 1 : nullptr);
+        density_dest<Real, DIM, KERNEL, T>(i, g, key - I.cell_base, P, Q, R, off + I.cell_base, n,
+                                           I.G, I.K, I.C, S, idt[inst], kick, nl, cnt, maxn, dc,
+                                           pcount ? pcount + 2 * (size_t)i : nullptr,
+                                           pcount ? pcount + 2 * (size_t)i + 1 : nullptr);
     }
     if (dc.overflow) atomicOr(&ctl->status, ST_CAPACITY);
     if (pd) block_counts(dc.pairs, dc.cand, dc.wall, pd);
@@ -460,46 +497,15 @@ k_momentum(const typename V4<Real>::T* __restrict__ P, const typename V4<Real>::
             out[k] = t;
         }
         ctl->ticket = 0;
-        double* rec = ctl->rec;
-        if (kick) {
-            ctl->t += dt;
-            ctl->step += 1;
-        }
-        rec[0] = ctl->t;
-        rec[1] = kick ? dt : 0.0;
-        rec[2] = out[3];
-        rec[3] = sqrt(out[4]);
-        rec[4] = out[0];
-        rec[5] = out[1];
-        rec[6] = out[2];
-        rec[7] = sqrt(out[5]);
-        rec[8] = out[7];
-        rec[9] = out[8];
-        rec[10] = (double)ctl->step;
-        rec[11] = (double)ctl->outside;
-        rec[12] = out[9];
-        if (out[6] != 0.0) ctl->status |= ST_NONFINITE;
-        double dt_next = C.dt_fixed;
-        if (!(dt_next > 0.0)) {
-            dt_next = 0.25 * C.h / (C.c0 + rec[3]);
-            if (rec[7] > 0.0) dt_next = fmin(dt_next, 0.25 * sqrt(C.h / rec[7]));
-            if (C.nu > 0.0) dt_next = fmin(dt_next, 0.125 * C.h * C.h / C.nu);
-        }
-        ctl->dt = dt_next;
-        if (kick) {
-            double* hrec = history + (size_t)(ctl->hist_count % HIST_CAP) * DIAG_N;
-            for (int k = 0; k < DIAG_N; ++k) hrec[k] = rec[k];
-            ctl->hist_count += 1;
-        }
-        __threadfence();
+        finish_single(ctl, history, C, dt, kick, out);
     }
 }
 
 // ---------------------------------------------------------------- launchers
-template <class Real, int DIM, int KERNEL>
+template <class Real, int DIM, int KERNEL, int T>
 int density_bps() {
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_density<Real, DIM, KERNEL>, PAIR_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_density<Real, DIM, KERNEL, T>, PAIR_THREADS, 0);
     return b > 0 ? b : 1;
 }
 
@@ -510,10 +516,10 @@ int momentum_bps() {
     return b > 0 ? b : 1;
 }
 
-template <class Real, int DIM, int KERNEL>
+template <class Real, int DIM, int KERNEL, int T>
 void launch_density_t(const StepLaunch& L, cudaStream_t st) {
     using V = typename V4<Real>::T;
-    k_density<Real, DIM, KERNEL><<<L.grid_d, PAIR_THREADS, 0, st>>>(
+    k_density<Real, DIM, KERNEL, T><<<L.grid_d, PAIR_THREADS, 0, st>>>(
         (const V*)L.P, (V*)L.Q, (Real*)L.R, L.skeys, L.off, L.n, (const Inst<Real>*)L.tab,
         L.cell_bounds, L.ninst, L.idt, L.S, L.ctl, L.kick, L.nl, L.cnt, L.maxn,
         L.finalize ? L.pd : nullptr, L.finalize ? nullptr : L.pcount);
@@ -535,19 +541,20 @@ struct PairDispatch {
     static int bps_t(int pass, int dim, int kernel) {
         const int sel = (dim == 3 ? 2 : 0) + (kernel == WENDLAND_C2 ? 1 : 0);
         switch (sel) {
-            case 0: return pass ? momentum_bps<Real, 2, QUINTIC, T>() : density_bps<Real, 2, QUINTIC>();
-            case 1: return pass ? momentum_bps<Real, 2, WENDLAND_C2, T>() : density_bps<Real, 2, WENDLAND_C2>();
-            case 2: return pass ? momentum_bps<Real, 3, QUINTIC, T>() : density_bps<Real, 3, QUINTIC>();
-            default: return pass ? momentum_bps<Real, 3, WENDLAND_C2, T>() : density_bps<Real, 3, WENDLAND_C2>();
+            case 0: return pass ? momentum_bps<Real, 2, QUINTIC, T>() : density_bps<Real, 2, QUINTIC, T>();
+            case 1: return pass ? momentum_bps<Real, 2, WENDLAND_C2, T>() : density_bps<Real, 2, WENDLAND_C2, T>();
+            case 2: return pass ? momentum_bps<Real, 3, QUINTIC, T>() : density_bps<Real, 3, QUINTIC, T>();
+            default: return pass ? momentum_bps<Real, 3, WENDLAND_C2, T>() : density_bps<Real, 3, WENDLAND_C2, T>();
         }
     }
-    static void density(const StepLaunch& L, cudaStream_t st) {
+    template <int T>
+    static void density_t(const StepLaunch& L, cudaStream_t st) {
         const int sel = (L.dim == 3 ? 2 : 0) + (L.kernel == WENDLAND_C2 ? 1 : 0);
         switch (sel) {
-            case 0: launch_density_t<Real, 2, QUINTIC>(L, st); break;
-            case 1: launch_density_t<Real, 2, WENDLAND_C2>(L, st); break;
-            case 2: launch_density_t<Real, 3, QUINTIC>(L, st); break;
-            default: launch_density_t<Real, 3, WENDLAND_C2>(L, st); break;
+            case 0: launch_density_t<Real, 2, QUINTIC, T>(L, st); break;
+            case 1: launch_density_t<Real, 2, WENDLAND_C2, T>(L, st); break;
+            case 2: launch_density_t<Real, 3, QUINTIC, T>(L, st); break;
+            default: launch_density_t<Real, 3, WENDLAND_C2, T>(L, st); break;
         }
     }
     template <int T>

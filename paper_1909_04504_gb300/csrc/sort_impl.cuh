@@ -1,0 +1,153 @@
+// Block-level bodies of the stable LSD radix sort (8-bit digits) of the cell keys and of
+// the cell table (Sec. 2.2 cell-sort neighbour search), shared by the per-phase kernels
+// and the persistent step kernel. A tile of SORT_TILE keys belongs to one block; inside
+// the tile warp w owns the contiguous range [w * 512, (w + 1) * 512) and walks it in
+// order, so tile order, warp order, iteration order and lane order reproduce the input
+// order (stability).
+#pragma once
+
+#include "sph_device.cuh"
+
+namespace sph {
+
+constexpr int RADIX = 256;
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_WARPS = SORT_THREADS / 32;
+constexpr int SORT_ITEMS = 16;
+constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
+
+struct ScatterSmem {
+    uint32_t base_d[RADIX];
+    uint32_t wcnt[SORT_WARPS][RADIX];
+    uint32_t wsum[SORT_WARPS];
+};
+
+// Digit histogram of tile `tile` into hist[digit * ntiles + tile] (SORT_THREADS threads).
+__device__ __forceinline__ void radix_hist_tile(const uint32_t* __restrict__ keys, int n, int shift,
+                                                uint32_t* __restrict__ hist, int ntiles, int tile,
+                                                uint32_t* h) {
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int base = tile * SORT_TILE;
+#pragma unroll 4
+    for (int k = 0; k < SORT_ITEMS; ++k) {
+        const int idx = base + k * SORT_THREADS + threadIdx.x;
+        if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & (RADIX - 1)], 1u);
+    }
+    __syncthreads();
+    hist[threadIdx.x * ntiles + tile] = h[threadIdx.x];
+}
+
+// Exclusive scan of digit `digit`'s row of per-tile counts; totals[digit] = row sum.
+// Any block size that is a multiple of 32 (up to 1024).
+__device__ __forceinline__ void radix_scan_row(uint32_t* __restrict__ hist, int ntiles,
+                                               uint32_t* __restrict__ totals, int digit,
+                                               uint32_t* wsum) {
+    uint32_t* row = hist + (size_t)digit * ntiles;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t carry = 0;
+    for (int base = 0; base < ntiles; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const uint32_t v = i < ntiles ? row[i] : 0u;
+        uint32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t s = lane < nw ? wsum[lane] : 0u;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += y;
+            }
+            wsum[lane] = s;
+        }
+        __syncthreads();
+        const uint32_t excl = carry + x - v + (warp ? wsum[warp - 1] : 0u);
+        if (i < ntiles) row[i] = excl;
+        carry += wsum[nw - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) totals[digit] = carry;
+}
+
+// Stable scatter of tile `tile` (SORT_THREADS threads): digit base = exclusive scan of the
+// digit totals + this tile's offset in its digit row; rank inside the tile by per-warp
+// match_any counting in warp order. vals_in == nullptr: the values are the input indices.
+__device__ __forceinline__ void radix_scatter_tile(const uint32_t* __restrict__ keys_in,
+                                                   const uint32_t* __restrict__ vals_in,
+                                                   uint32_t* __restrict__ keys_out,
+                                                   uint32_t* __restrict__ vals_out, int n, int shift,
+                                                   const uint32_t* __restrict__ hist,
+                                                   const uint32_t* __restrict__ totals, int ntiles,
+                                                   int tile, ScatterSmem& sm) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    {
+        const uint32_t v = totals[tid];
+        uint32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) sm.wsum[warp] = x;
+        for (int w = 0; w < SORT_WARPS; ++w) sm.wcnt[w][tid] = 0;
+        __syncthreads();
+        uint32_t pre = 0;
+        for (int w = 0; w < warp; ++w) pre += sm.wsum[w];
+        sm.base_d[tid] = pre + x - v + hist[tid * ntiles + tile];
+    }
+    __syncthreads();
+    const int wbase = tile * SORT_TILE + warp * (SORT_TILE / SORT_WARPS);
+    uint32_t kr[SORT_ITEMS], vr[SORT_ITEMS], rank[SORT_ITEMS];
+    const unsigned ltmask = lanemask_lt();
+#pragma unroll
+    for (int it = 0; it < SORT_ITEMS; ++it) {
+        const int idx = wbase + it * 32 + lane;
+        const bool valid = idx < n;
+        const uint32_t key = valid ? keys_in[idx] : 0u;
+        const uint32_t d = valid ? ((key >> shift) & (RADIX - 1)) : (uint32_t)RADIX;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t before = valid ? sm.wcnt[warp][d] : 0u;
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) sm.wcnt[warp][d] = before + __popc(peers);
+        __syncwarp();
+        kr[it] = key;
+        vr[it] = valid ? (vals_in ? vals_in[idx] : (uint32_t)idx) : 0u;
+        rank[it] = before + __popc(peers & ltmask);
+    }
+    __syncthreads();
+    {   // exclusive prefix over warps, per digit
+        uint32_t run = 0;
+        for (int w = 0; w < SORT_WARPS; ++w) {
+            const uint32_t c = sm.wcnt[w][tid];
+            sm.wcnt[w][tid] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < SORT_ITEMS; ++it) {
+        const int idx = wbase + it * 32 + lane;
+        if (idx < n) {
+            const uint32_t d = (kr[it] >> shift) & (RADIX - 1);
+            const uint32_t pos = sm.base_d[d] + sm.wcnt[warp][d] + rank[it];
+            keys_out[pos] = kr[it];
+            vals_out[pos] = vr[it];
+        }
+    }
+}
+
+// Cell table entry: number of sorted keys < c (lower bound), for c in [0, ncells].
+__device__ __forceinline__ uint32_t cell_offset(const uint32_t* __restrict__ skeys, int n, uint32_t c) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (skeys[mid] < c) lo = mid + 1;
+        else hi = mid;
+    }
+    return (uint32_t)lo;
+}
+
+}  // namespace sph

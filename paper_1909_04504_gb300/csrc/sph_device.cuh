@@ -57,6 +57,11 @@ struct Control {
     unsigned int ticket;  // last-block counter of the reduction
     unsigned int outside; // particles clamped into an edge cell at the last key build
     unsigned int hist_count;
+    unsigned long long stamp[8];  // persistent step: global timer (ns) at each phase end
+    // grid barrier of the persistent step: arrivals and generation, each on its own
+    // 128-byte line so that the pollers of one do not contend with the atomics on the other
+    alignas(128) unsigned int bar_count;
+    alignas(128) unsigned int bar_gen;
 };
 
 // Grid of cells (Sec. 2.2): cells no smaller than the support radius.

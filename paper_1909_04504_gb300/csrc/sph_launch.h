@@ -47,7 +47,7 @@ struct Inst {
 // dt is the control block's; a batch has one entry per instance.
 struct StepLaunch {
     int precision, dim, kernel, n, sms, ninst, kick, maxn;
-    int group_m, grid_d, grid_m;
+    int group_d, group_m, grid_d, grid_m;  // lanes per destination and grid of each pass
     int finalize;                 // 1: the momentum pass reduces the diagnostics (single)
     const void* tab;              // Inst<Real>[ninst]
     const uint32_t* id_bounds;    // ninst + 1 global-id bounds
@@ -77,6 +77,24 @@ void launch_pairs(const StepLaunch& L, cudaStream_t st);
 void launch_density_pass(const StepLaunch& L, cudaStream_t st);
 void launch_momentum_pass(const StepLaunch& L, cudaStream_t st);
 void launch_batch_reduce(const StepLaunch& L, cudaStream_t st);
+// fused_f32.cu / fused_f64.cu: the whole step as one cooperative launch (persistent blocks,
+// grid barriers between the phases).
+constexpr int FUSED_THREADS = 256;  // = the radix: one digit per thread in the sort phases
+constexpr int FUSED_PART = 16;      // doubles of per-block partials
+struct FusedLaunch {
+    StepLaunch L;                // L.Sin: current set; L.S: the other set (reorder target)
+    uint32_t* keys[2];
+    uint32_t* vals[2];
+    uint32_t* hist;              // 256 x ntiles digit counts, then 256 totals
+    uint32_t* off;               // cell table, written by the reorder phase
+    double* part;                // FUSED_PART doubles per block
+    int passes, ntiles, ncells;
+    unsigned long long wait_ns;  // limit of one barrier wait
+};
+cudaError_t launch_fused(const FusedLaunch& F, int T, int grid, cudaStream_t st);
+int fused_max_blocks_per_sm(int precision, int dim, int kernel, int T);
+int radix_tiles(int n);
+
 // pass 0: density (thread per destination), 1: momentum (T = 1, 2, 4 or 8 lanes per
 // destination)
 int pairs_max_blocks_per_sm(int precision, int pass, int dim, int kernel, int T);

@@ -1,0 +1,159 @@
+"""Persistent step (one cooperative launch per step, grid barriers between the phases):
+it meets the oracle bars of the per-phase graph, follows the graph step by step, keeps the
+neighbour sets bit-exact, runs batches, and reports a device wait that runs out as
+SPH_ERR_TIMEOUT with the context still usable."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from gpu_util import csr_equal, normwise, oracle_wl, rel_l2, sim_of
+
+import paper_1909_04504_gb300 as G
+
+pytestmark = pytest.mark.gpu
+
+CONFIGS = {
+    "tg2d": W.taylor_green_2d(n=50),
+    "db2d": W.dam_break_2d(dx=0.02),
+    "tg3d": W.taylor_green_3d(n=16),
+    "db3d": W.dam_break_3d(dx=0.04),
+}
+
+
+def fields_of(wl):
+    return ("x", "y", "z", "u", "v", "w", "rho") if wl.dim == 3 else ("x", "y", "u", "v", "rho")
+
+
+@pytest.mark.parametrize("name", sorted(CONFIGS))
+@pytest.mark.parametrize("prec", [G.PREC_FP64, G.PREC_FP32])
+def test_one_step_matches_oracle(name, prec):
+    wl = oracle_wl(CONFIGS[name], prec)
+    st, hist = O.run(wl, O.state_of(wl), wl.dt, 1)
+    with sim_of(wl) as sim:
+        sim.set_step_mode(G.STEP_PERSISTENT)
+        assert sim.kernels_per_step(G.scheme_of(wl)) == 1
+        sim.step(G.scheme_of(wl), wl.dt, 1)
+        g = sim.state()
+        h = sim.history()
+    for k in fields_of(wl):
+        if prec == G.PREC_FP64:
+            assert normwise(g[k], st[k]) <= 1e-10, k
+        else:
+            assert rel_l2(g[k], st[k]) <= 1e-4, k
+    assert h.shape[0] == 1 and h[0, 8] == hist[1, 8] and h[0, 9] == hist[1, 9]
+    assert abs(h[0, 2] - hist[1, 2]) <= 1e-6 * abs(hist[1, 2]) + 1e-300
+
+
+@pytest.mark.parametrize("name", sorted(CONFIGS))
+@pytest.mark.parametrize("prec", [G.PREC_FP64, G.PREC_FP32])
+def test_persistent_follows_graph(name, prec):
+    """Same per-particle code in both forms: 20 steps agree to rounding, counts exactly."""
+    wl = oracle_wl(CONFIGS[name], prec)
+    out = []
+    for mode in (G.STEP_GRAPH, G.STEP_PERSISTENT):
+        with sim_of(wl) as sim:
+            sim.set_groups(4)
+            sim.set_step_mode(mode)
+            sim.step(G.scheme_of(wl), wl.dt, 20)
+            out.append((sim.state(), sim.history()))
+    (ga, ha), (gb, hb) = out
+    tol = 1e-12 if prec == G.PREC_FP64 else 1e-6
+    for k in fields_of(wl):
+        assert normwise(gb[k], ga[k]) <= tol, k
+    assert np.array_equal(ha[:, 8], hb[:, 8]) and np.array_equal(ha[:, 9], hb[:, 9])
+    assert np.allclose(ha[:, 2], hb[:, 2], rtol=1e-9 if prec == G.PREC_FP64 else 1e-5)
+    assert np.array_equal(ha[:, 0], hb[:, 0])
+
+
+@pytest.mark.parametrize("prec", [G.PREC_FP64, G.PREC_FP32])
+def test_neighbours_after_persistent_steps(prec):
+    wl = W.dam_break_2d(dx=0.02, precision=prec)
+    with sim_of(wl) as sim:
+        sim.set_step_mode(G.STEP_PERSISTENT)
+        sim.step(G.scheme_of(wl), wl.dt, 50)
+        g = sim.state()
+        noff, nidx = sim.neighbors()
+        cell_of, off, _ = sim.cells()
+    ooff, oidx, _ = O.neighbors(wl, g["x"], g["y"])
+    assert csr_equal(noff, nidx, ooff, oidx)
+    ocell, ooffs, _ = O.cells(wl, g["x"], g["y"])
+    assert np.array_equal(cell_of, ocell) and np.array_equal(off, ooffs)
+
+
+def test_taylor_green_decay_fp64_persistent():
+    wl = W.taylor_green_2d(n=50, steps=200)
+    st, hist = O.run(wl, O.state_of(wl), wl.dt, wl.steps)
+    with sim_of(wl) as sim:
+        sim.set_step_mode(G.STEP_PERSISTENT)
+        sim.step(G.scheme_of(wl), wl.dt, wl.steps)
+        h = sim.history()
+        g = sim.state()
+    assert np.max(np.abs(h[:, 3] - hist[1:, 3]) / hist[1:, 3]) <= 1e-9
+    for k in ("x", "y", "u", "v", "rho"):
+        assert normwise(g[k], st[k]) <= 1e-8, k
+
+
+@pytest.mark.parametrize("precision", [W.PREC_FP64, W.PREC_FP32])
+def test_batch_persistent_follows_graph(precision):
+    wls = [W.taylor_green_2d(n=n, re=re, precision=precision, seed=90 + k)
+           for k, (n, re) in enumerate(((20, 100.0), (31, 500.0), (26, 70.0), (17, 900.0)))]
+    res = []
+    for mode in (G.STEP_GRAPH, G.STEP_PERSISTENT):
+        b = G.BatchSimulation(wls)
+        b.set_groups(4)
+        b.set_step_mode(mode)
+        b.step_batch([G.scheme_of(w) for w in wls], [w.dt for w in wls], 12)
+        res.append(([b.instance_state(k) for k in range(len(wls))], b.batch_diagnostics()))
+        b.close()
+    (sa, da), (sb, db) = res
+    tol = 1e-12 if precision == W.PREC_FP64 else 1e-6
+    for k, wl in enumerate(wls):
+        for f in ("x", "y", "u", "v", "rho"):
+            assert normwise(sb[k][f], sa[k][f]) <= tol, (k, f)
+    assert np.array_equal(da[:, 8], db[:, 8]) and np.array_equal(da[:, 9], db[:, 9])
+    assert np.array_equal(da[:, 10], db[:, 10]) and np.all(db[:, 10] == 12)
+
+
+def test_wait_that_runs_out_is_reported_and_context_recovers():
+    """A zero wait limit makes the first grid barrier give up: the step reports
+    SPH_ERR_TIMEOUT (no fault, no hang); after the state is loaded again it steps on."""
+    wl = W.taylor_green_2d(n=40)
+    sch = G.scheme_of(wl)
+    with sim_of(wl) as sim:
+        sim.set_step_mode(G.STEP_PERSISTENT)
+        sim.step(sch, wl.dt, 2)
+        blob = sim.save_state()
+        ref_state = sim.state()
+        sim.set_wait_limit(0)
+        with pytest.raises(G.SphError) as err:
+            sim.step(sch, wl.dt, 1)
+        assert "TIMEOUT" in str(err.value)
+        sim.set_wait_limit(1_000_000_000)
+        sim.load_state(blob)
+        sim.step(sch, wl.dt, 3)
+        after = sim.state()
+    with sim_of(wl) as ref:
+        ref.set_step_mode(G.STEP_PERSISTENT)
+        ref.step(sch, wl.dt, 5)
+        want = ref.state()
+    assert np.all(np.isfinite(after["u"]))
+    for k in ("x", "y", "u", "v", "rho"):
+        assert normwise(after[k], want[k]) <= 1e-14, k
+    assert ref_state["x"].shape == after["x"].shape
+
+
+def test_autotune_picks_a_mode_and_keeps_the_state():
+    wl = W.dam_break_2d(dx=0.02, precision=W.PREC_FP32)
+    sch = G.scheme_of(wl)
+    with sim_of(wl) as sim:
+        sim.step(sch, wl.dt, 3)
+        before = sim.state()
+        lanes = sim.autotune(sch)
+        after = sim.state()
+        assert lanes in (1, 2, 4, 8)
+        assert sim.kernels_per_step(sch) >= 1
+        for k in ("x", "y", "u", "v", "rho"):
+            assert np.array_equal(before[k], after[k]), k
+        sim.step(sch, wl.dt, 3)
+        assert np.all(np.isfinite(sim.state()["u"]))
