@@ -141,7 +141,7 @@ enum {
 /* Create a context: copy the arrays to the device (global ids in array order), wrap
  * periodic coordinates into the box. `stream` is a cudaStream_t (NULL: the context creates
  * and owns a non-blocking stream, needed because steps run as captured CUDA graphs). Returns SPH_ERR_INVALID for a bad domain (dim, kernel, h <= 0, empty box,
- * a periodic axis with fewer than 3 cells, more than 2^31 - 1 particles). */
+ * a periodic axis with fewer than 3 cells, 2^30 particles or more). */
 sph_status sph_create(const sph_domain* domain, const sph_array_desc* arrays, int32_t n_arrays,
                       void* stream, sph_alloc_fn alloc, sph_free_fn free_fn, void* alloc_user,
                       sph_ctx** out);

@@ -92,6 +92,7 @@ struct sph_ctx {
     int step_mode = SPH_STEP_GRAPH;   // per-phase kernels in a graph, or one persistent launch
     int fused_bps[4] = {0, 0, 0, 0};  // persistent kernel: blocks per SM for T = 1, 2, 4, 8
     double* fpart = nullptr;          // persistent kernel: per-block partials
+    uint32_t* sort_work = nullptr;    // one-sweep sort: histograms, counters, look-back words
     unsigned long long wait_ns = 1000000000ull;  // limit of one device-side wait
     bool last_fused = false;          // the last step ran as one persistent launch
     cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -375,17 +376,16 @@ void enqueue_build(sph_ctx* c, int drift, int kick, int carry_rates, bool timed 
     cudaMemsetAsync(&c->ctl->outside, 0, sizeof(unsigned), st);
     StepLaunch L = step_launch(c, kick);
     mark(c, 0, timed);
-    launch_drift_keys(L, drift, c->keys[0], st);
+    launch_keys_hist(L, drift, c->keys[0], c->passes, c->sort_work, st);
     mark(c, 1, timed);
-    const int b = launch_radix_sort(c->keys, c->vals, c->N, c->passes, c->hist, c->ctl, st);
+    const int b = launch_onesweep(c->N, c->keys, c->vals, c->passes, c->sort_work, c->ctl, c->wait_ns, st);
     c->skeys = c->keys[b];
     mark(c, 2, timed);
     const int nxt = c->cur ^ 1;
     L.S = c->set[nxt];
     L.skeys = c->skeys;
-    launch_reorder(L, c->vals[b], carry_rates, st);
-    mark(c, 3, timed);
-    launch_cell_offsets(c->skeys, c->N, c->G.ncells, c->off, c->ctl, st, c->sms);
+    launch_reorder(L, c->vals[b], carry_rates, c->off, c->G.ncells, st);
+    mark(c, 3, timed);  // the cell table is written by the reorder kernel
     mark(c, 4, timed);
     c->cur = nxt;
 }
@@ -422,7 +422,8 @@ FusedLaunch fused_launch(sph_ctx* c) {
         F.keys[k] = c->keys[k];
         F.vals[k] = c->vals[k];
     }
-    F.hist = c->hist;
+    F.work = c->sort_work;
+    F.work_words = (int)sort_work_words(c->N, c->passes);
     F.off = c->off;
     F.part = c->fpart;
     F.passes = c->passes;
@@ -439,6 +440,7 @@ sph_status run_fused(sph_ctx* c, int nsteps) {
     CK(cudaMemsetAsync(&c->ctl->outside, 0, sizeof(unsigned), c->stream));
     CK(cudaMemsetAsync(&c->ctl->bar_count, 0, sizeof(unsigned), c->stream));
     CK(cudaMemsetAsync(&c->ctl->bar_gen, 0, sizeof(unsigned), c->stream));
+    CK(cudaMemsetAsync(c->sort_work, 0, sort_work_words(c->N, c->passes) * 4, c->stream));
     const int grid = fused_grid(c);
     for (int k = 0; k < nsteps; ++k) {
         const FusedLaunch F = fused_launch(c);
@@ -751,8 +753,8 @@ sph_status create_impl(const sph_domain* domains, int ninst, const sph_array_des
         }
         c->arr_off.push_back(c->arr_off.back() + A.n);
     }
-    if (c->arr_off.back() > 0x7ffffff0LL || c->arr_off.back() < 1) {
-        g_create_error = "particle count must be in [1, 2^31)";
+    if (c->arr_off.back() > 0x3ffffff0LL || c->arr_off.back() < 1) {
+        g_create_error = "particle count must be in [1, 2^30)";
         delete c;
         return SPH_ERR_INVALID;
     }
@@ -818,6 +820,7 @@ sph_status create_impl(const sph_domain* domains, int ninst, const sph_array_des
     bytes += 4 * al(N * 4);                                    // keys, vals
     bytes += al(((size_t)c->G.ncells + 1) * 4);                // cell offsets
     bytes += al(radix_hist_words(c->N) * 4);                   // radix histograms
+    bytes += al(sort_work_words(c->N, c->passes) * 4);          // one-sweep workspace
     bytes += al((size_t)c->grid_cap * 8 * 8) + al((size_t)c->grid_cap * 4 * 8);  // partials
     bytes += al(N * 4);                                        // neighbour-list lengths
     bytes += al((size_t)c->sms * FUSED_MAX_BPS * FUSED_PART * 8);  // persistent partials
@@ -858,6 +861,7 @@ sph_status create_impl(const sph_domain* domains, int ninst, const sph_array_des
     for (int k = 0; k < 2; ++k) c->vals[k] = (uint32_t*)arena_take(p, N * 4);
     c->off = (uint32_t*)arena_take(p, ((size_t)c->G.ncells + 1) * 4);
     c->hist = (uint32_t*)arena_take(p, radix_hist_words(c->N) * 4);
+    c->sort_work = (uint32_t*)arena_take(p, sort_work_words(c->N, c->passes) * 4);
     c->pm = (double*)arena_take(p, (size_t)c->grid_cap * 8 * 8);
     c->pd = (double*)arena_take(p, (size_t)c->grid_cap * 4 * 8);
     c->cnt = (uint32_t*)arena_take(p, N * 4);
@@ -1278,7 +1282,9 @@ sph_status sph_kernels_per_step(const sph_ctx* ctx, const sph_scheme* scheme, in
     if (!c || !scheme || !count) return fail(c, SPH_ERR_INVALID, "NULL argument");
     // drift+keys, 3 per radix pass, reorder, cell table, density pass, momentum pass
     // (+ the per-instance reduction of a batch)
-    *count = c->step_mode == SPH_STEP_PERSISTENT ? 1 : 1 + 3 * c->passes + 1 + 1 + 1 + 1 + (c->ninst ? 1 : 0);
+    // graph: keys + histograms, one launch per radix pass, reorder + cell table, density
+    // pass, momentum pass (+ the per-instance reduction of a batch)
+    *count = c->step_mode == SPH_STEP_PERSISTENT ? 1 : 1 + c->passes + 1 + 1 + 1 + (c->ninst ? 1 : 0);
     return SPH_OK;
 }
 

@@ -92,12 +92,12 @@ template <class Real, int DIM, int KERNEL, int T>
 __global__ void __launch_bounds__(FUSED_THREADS, 2) k_step_fused(const FusedLaunch F) {
     using V = typename V4<Real>::T;
     __shared__ union {
-        uint32_t h[RADIX];
-        uint32_t wsum[32];
-        ScatterSmem sc;
+        uint32_t h[4][RADIX];
+        OnesweepSmem os;
         double red[FUSED_THREADS / 32][FUSED_PART];
         double bred[FUSED_THREADS / 32][10];
     } sm;
+    __shared__ int tile_s;
     const StepLaunch& L = F.L;
     Control* ctl = L.ctl;
     if (ctl->status) return;
@@ -108,42 +108,53 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_step_fused(const FusedLaun
     V* P = (V*)L.P;
     V* Q = (V*)L.Q;
     Real* R = (Real*)L.R;
+    uint32_t* ghist = F.work;
+    uint32_t* counters = F.work + 4 * RADIX;
+    uint32_t* status = counters + 32;
     if (stamp) ctl->stamp[0] = global_ns();
 
-    // ---- drift of the fluid (predictor half-kick folded in) + cell keys
+    // ---- drift of the fluid (predictor half-kick folded in) + cell keys + digit histograms
     {
+        for (int p = 0; p < F.passes; ++p) sm.h[p][threadIdx.x] = 0;
+        __syncthreads();
         unsigned outside = 0;
-        for (int i = tid; i < L.n; i += nthreads) {
-            const int inst = find_instance(L.id_bounds, L.ninst, L.Sin.tag[i] & ID_MASK);
-            const Inst<Real>& I = tab[inst];
-            int clamped = 0;
-            F.keys[0][i] = I.cell_base + drift_key_one(L.Sin, i, I.G, I.C, L.idt[inst], 1, clamped);
-            outside += clamped;
+        for (int base = blockIdx.x * FUSED_THREADS; base < L.n; base += nthreads) {
+            const int i = base + threadIdx.x;
+            const bool valid = i < L.n;
+            uint32_t key = 0;
+            if (valid) {
+                const int inst = find_instance(L.id_bounds, L.ninst, L.Sin.tag[i] & ID_MASK);
+                const Inst<Real>& I = tab[inst];
+                int clamped = 0;
+                key = I.cell_base + drift_key_one(L.Sin, i, I.G, I.C, L.idt[inst], 1, clamped);
+                F.keys[0][i] = key;
+                outside += clamped;
+            }
+            digit_hist_add(key, valid, F.passes, sm.h);
         }
         for (int o = 16; o > 0; o >>= 1) outside += __shfl_down_sync(0xffffffffu, outside, o);
         if ((threadIdx.x & 31) == 0 && outside) atomicAdd(&ctl->outside, outside);
+        __syncthreads();
+        for (int p = 0; p < F.passes; ++p) {
+            const uint32_t v = sm.h[p][threadIdx.x];
+            if (v) atomicAdd(&ghist[p * RADIX + threadIdx.x], v);
+        }
     }
     if (!grid_sync(ctl, F.wait_ns)) return;
     if (stamp) ctl->stamp[1] = global_ns();
 
-    // ---- stable LSD radix sort of (key, index)
-    uint32_t* totals = F.hist + (size_t)RADIX * F.ntiles;
+    // ---- stable LSD radix sort of (key, index): one-sweep passes, tiles taken in order
     int cur = 0;
     for (int p = 0; p < F.passes; ++p) {
-        const int shift = 8 * p;
-        for (int t = blockIdx.x; t < F.ntiles; t += nb) {
-            radix_hist_tile(F.keys[cur], L.n, shift, F.hist, F.ntiles, t, sm.h);
+        for (;;) {
+            if (threadIdx.x == 0) tile_s = (int)atomicAdd(&counters[p], 1u);
             __syncthreads();
-        }
-        if (!grid_sync(ctl, F.wait_ns)) return;
-        for (int d = blockIdx.x; d < RADIX; d += nb) {
-            radix_scan_row(F.hist, F.ntiles, totals, d, sm.wsum);
-            __syncthreads();
-        }
-        if (!grid_sync(ctl, F.wait_ns)) return;
-        for (int t = blockIdx.x; t < F.ntiles; t += nb) {
-            radix_scatter_tile(F.keys[cur], p ? F.vals[cur] : nullptr, F.keys[cur ^ 1],
-                               F.vals[cur ^ 1], L.n, shift, F.hist, totals, F.ntiles, t, sm.sc);
+            const int t = tile_s;
+            if (t >= F.ntiles) break;
+            radix_onesweep_tile(F.keys[cur], p ? F.vals[cur] : nullptr, F.keys[cur ^ 1],
+                                F.vals[cur ^ 1], L.n, 8 * p, ghist + p * RADIX,
+                                status + (size_t)p * F.ntiles * RADIX, t, sm.os, &ctl->status,
+                                F.wait_ns);
             __syncthreads();
         }
         if (!grid_sync(ctl, F.wait_ns)) return;
@@ -188,7 +199,9 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_step_fused(const FusedLaun
     if (!grid_sync(ctl, F.wait_ns)) return;
     if (stamp) ctl->stamp[4] = global_ns();
 
-    // ---- momentum pass (T lanes per destination) + corrector kick
+    // ---- momentum pass (T lanes per destination) + corrector kick; the sort workspace is
+    // no longer read in this step and is zeroed for the next one
+    for (int w = tid; w < F.work_words; w += nthreads) F.work[w] = 0u;
     {
         MomDiag md{0, 0, 0, 0, 0, 0, 0};
         for (int i = tid / T; i < L.n; i += nthreads / T) {

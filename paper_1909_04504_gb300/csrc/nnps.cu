@@ -33,6 +33,55 @@ __global__ void k_drift_keys(ParticleSet S, int n, const Inst<Real>* __restrict_
     if ((threadIdx.x & 31) == 0 && outside) atomicAdd(&ctl->outside, outside);
 }
 
+// Drift + cell key as above, and the digit histograms of all radix passes of the keys
+// (block histograms in shared memory, added to ghist[pass * 256 + digit]). 256 threads.
+template <class Real>
+__global__ void __launch_bounds__(256)
+k_keys_hist(ParticleSet S, int n, const Inst<Real>* __restrict__ tab,
+            const uint32_t* __restrict__ id_bounds, int ninst, const double* __restrict__ idt,
+            int drift, uint32_t* keys, uint32_t* __restrict__ ghist, int passes, Control* ctl) {
+    __shared__ uint32_t h[4][RADIX];
+    if (ctl->status) return;
+    for (int p = 0; p < passes; ++p) h[p][threadIdx.x] = 0;
+    __syncthreads();
+    unsigned outside = 0;
+    for (int base = blockIdx.x * 256; base < n; base += gridDim.x * 256) {
+        const int i = base + threadIdx.x;
+        const bool valid = i < n;
+        uint32_t key = 0;
+        if (valid) {
+            const int inst = find_instance(id_bounds, ninst, S.tag[i] & ID_MASK);
+            const Inst<Real>& I = tab[inst];
+            int clamped = 0;
+            key = I.cell_base + drift_key_one(S, i, I.G, I.C, idt[inst], drift, clamped);
+            keys[i] = key;
+            outside += clamped;
+        }
+        digit_hist_add(key, valid, passes, h);
+    }
+    for (int o = 16; o > 0; o >>= 1) outside += __shfl_down_sync(0xffffffffu, outside, o);
+    if ((threadIdx.x & 31) == 0 && outside) atomicAdd(&ctl->outside, outside);
+    __syncthreads();
+    for (int p = 0; p < passes; ++p) {
+        const uint32_t v = h[p][threadIdx.x];
+        if (v) atomicAdd(&ghist[p * RADIX + threadIdx.x], v);
+    }
+}
+
+// One radix pass in one launch (decoupled look-back); one tile per block.
+__global__ void __launch_bounds__(SORT_THREADS)
+k_radix_onesweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+                 uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int n, int shift,
+                 const uint32_t* __restrict__ ghist, uint32_t* status, uint32_t* counter,
+                 Control* ctl, unsigned long long wait_ns) {
+    __shared__ OnesweepSmem sm;
+    if (ctl->status) return;
+    if (threadIdx.x == 0) sm.tile = (int)atomicAdd(counter, 1u);
+    __syncthreads();
+    radix_onesweep_tile(keys_in, vals_in, keys_out, vals_out, n, shift, ghist, status, sm.tile, sm,
+                        &ctl->status, wait_ns);
+}
+
 // -------------------------------------------------------------- radix sort
 // Block bodies in sort_impl.cuh (shared with the persistent step kernel).
 __global__ void __launch_bounds__(SORT_THREADS)
@@ -81,12 +130,17 @@ __global__ void k_reorder(ParticleSet in, ParticleSet out, const uint32_t* __res
                           const Inst<Real>* __restrict__ tab, const uint32_t* __restrict__ cell_bounds,
                           int ninst, const double* __restrict__ idt, int kick, int carry_rates,
                           typename V4<Real>::T* __restrict__ P, typename V4<Real>::T* __restrict__ Q,
-                          Real* __restrict__ R, const Control* ctl) {
+                          Real* __restrict__ R, uint32_t* __restrict__ off, int ncells,
+                          const Control* ctl) {
     if (ctl->status) return;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const int inst = find_instance(cell_bounds, ninst, skeys[k]);
-        reorder_one<Real>(in, out, k, (int)perm[k], dim, tab[inst].C, idt[inst], kick,
-                          carry_rates, P, Q, R);
+    const int m = n > ncells + 1 ? n : ncells + 1;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
+        if (k < n) {
+            const int inst = find_instance(cell_bounds, ninst, skeys[k]);
+            reorder_one<Real>(in, out, k, (int)perm[k], dim, tab[inst].C, idt[inst], kick,
+                              carry_rates, P, Q, R);
+        }
+        if (k <= ncells) off[k] = cell_offset(skeys, n, (uint32_t)k);  // the cell table
     }
 }
 
@@ -270,18 +324,55 @@ void launch_cell_offsets(const uint32_t* skeys, int n, int ncells, uint32_t* off
                                                                                   off, ctl);
 }
 
-void launch_reorder(const StepLaunch& L, const uint32_t* perm, int carry_rates, cudaStream_t st) {
-    const int g = grid_for(L.n, 256, L.sms * 8);
+void launch_reorder(const StepLaunch& L, const uint32_t* perm, int carry_rates, uint32_t* off,
+                    int ncells, cudaStream_t st) {
+    const int m = L.n > ncells + 1 ? L.n : ncells + 1;
+    const int g = grid_for(m, 256, L.sms * 8);
     if (L.precision)
         k_reorder<float><<<g, 256, 0, st>>>(L.Sin, L.S, perm, L.skeys, L.n, L.dim,
                                             (const Inst<float>*)L.tab, L.cell_bounds, L.ninst, L.idt,
                                             L.kick, carry_rates, (F4*)L.P, (F4*)L.Q, (float*)L.R,
-                                            L.ctl);
+                                            off, ncells, L.ctl);
     else
         k_reorder<double><<<g, 256, 0, st>>>(L.Sin, L.S, perm, L.skeys, L.n, L.dim,
                                              (const Inst<double>*)L.tab, L.cell_bounds, L.ninst,
                                              L.idt, L.kick, carry_rates, (D4*)L.P, (D4*)L.Q,
-                                             (double*)L.R, L.ctl);
+                                             (double*)L.R, off, ncells, L.ctl);
+}
+
+size_t sort_work_words(int n, int passes) {
+    return (size_t)4 * RADIX + 32 + (size_t)passes * radix_tiles(n) * RADIX;
+}
+
+// Zeroes the sort workspace, then drift + keys + the digit histograms of all passes.
+void launch_keys_hist(const StepLaunch& L, int drift, uint32_t* keys0, int passes, uint32_t* work,
+                      cudaStream_t st) {
+    cudaMemsetAsync(work, 0, sort_work_words(L.n, passes) * 4, st);
+    const int g = grid_for(L.n, 256, L.sms * 8);
+    if (L.precision)
+        k_keys_hist<float><<<g, 256, 0, st>>>(L.Sin, L.n, (const Inst<float>*)L.tab, L.id_bounds,
+                                              L.ninst, L.idt, drift, keys0, work, passes, L.ctl);
+    else
+        k_keys_hist<double><<<g, 256, 0, st>>>(L.Sin, L.n, (const Inst<double>*)L.tab, L.id_bounds,
+                                               L.ninst, L.idt, drift, keys0, work, passes, L.ctl);
+}
+
+// One one-sweep launch per pass over (keys[0], identity). Returns the buffer index (0 or
+// 1) holding the sorted keys and the permutation.
+int launch_onesweep(int n, uint32_t* keys[2], uint32_t* vals[2], int passes, uint32_t* work,
+                    Control* ctl, unsigned long long wait_ns, cudaStream_t st) {
+    const int ntiles = radix_tiles(n);
+    uint32_t* ghist = work;
+    uint32_t* counters = work + 4 * RADIX;
+    uint32_t* status = counters + 32;
+    int cur = 0;
+    for (int p = 0; p < passes; ++p) {
+        k_radix_onesweep<<<ntiles, SORT_THREADS, 0, st>>>(
+            keys[cur], p == 0 ? nullptr : vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, 8 * p,
+            ghist + p * RADIX, status + (size_t)p * ntiles * RADIX, counters + p, ctl, wait_ns);
+        cur ^= 1;
+    }
+    return cur;
 }
 
 void launch_gather_by_id(const double* field, const uint32_t* tag, int n, uint32_t first,

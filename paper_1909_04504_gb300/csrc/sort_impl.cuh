@@ -139,6 +139,135 @@ __device__ __forceinline__ void radix_scatter_tile(const uint32_t* __restrict__ 
     }
 }
 
+// ------------------------------------------------------------ one-sweep passes
+// A pass in one launch: every tile ranks its keys locally, publishes its per-digit count
+// and looks back over the preceding tiles' published counts for its exclusive prefix
+// (decoupled look-back), while the global digit bases come from a histogram of all passes
+// taken beforehand (with the cell keys). Tiles take their index from a counter in launch
+// order, so every tile a tile waits for has started and waits only on earlier tiles.
+// Status word per (tile, digit): 2 flag bits (aggregate / inclusive prefix) + 30-bit count.
+constexpr uint32_t LB_AGGREGATE = 1u << 30;
+constexpr uint32_t LB_PREFIX = 2u << 30;
+constexpr uint32_t LB_COUNT = (1u << 30) - 1u;
+
+struct OnesweepSmem {
+    uint32_t base_d[RADIX];
+    uint32_t wcnt[SORT_WARPS][RADIX];
+    uint32_t wsum[SORT_WARPS];
+    int tile;
+};
+
+__device__ __forceinline__ unsigned long long sort_clock_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// One tile of a one-sweep pass (SORT_THREADS threads). ghist: the RADIX digit counts of
+// this pass over all keys; status: ntiles x RADIX look-back words, zero before the pass.
+// A look-back wait longer than wait_ns raises ST_TIMEOUT and the tile writes nothing.
+__device__ __forceinline__ void radix_onesweep_tile(const uint32_t* __restrict__ keys_in,
+                                                    const uint32_t* __restrict__ vals_in,
+                                                    uint32_t* __restrict__ keys_out,
+                                                    uint32_t* __restrict__ vals_out, int n,
+                                                    int shift, const uint32_t* __restrict__ ghist,
+                                                    uint32_t* status, int tile,
+                                                    OnesweepSmem& sm, unsigned* ctl_status,
+                                                    unsigned long long wait_ns) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int w = 0; w < SORT_WARPS; ++w) sm.wcnt[w][tid] = 0;
+    __syncthreads();
+    const int wbase = tile * SORT_TILE + warp * (SORT_TILE / SORT_WARPS);
+    uint32_t kr[SORT_ITEMS], vr[SORT_ITEMS], rank[SORT_ITEMS];
+    const unsigned ltmask = lanemask_lt();
+#pragma unroll
+    for (int it = 0; it < SORT_ITEMS; ++it) {
+        const int idx = wbase + it * 32 + lane;
+        const bool valid = idx < n;
+        const uint32_t key = valid ? keys_in[idx] : 0u;
+        const uint32_t d = valid ? ((key >> shift) & (RADIX - 1)) : (uint32_t)RADIX;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t before = valid ? sm.wcnt[warp][d] : 0u;
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) sm.wcnt[warp][d] = before + __popc(peers);
+        __syncwarp();
+        kr[it] = key;
+        vr[it] = valid ? (vals_in ? vals_in[idx] : (uint32_t)idx) : 0u;
+        rank[it] = before + __popc(peers & ltmask);
+    }
+    __syncthreads();
+    // per digit (thread tid): exclusive prefix over warps and the tile's count
+    uint32_t count = 0;
+    for (int w = 0; w < SORT_WARPS; ++w) {
+        const uint32_t c = sm.wcnt[w][tid];
+        sm.wcnt[w][tid] = count;
+        count += c;
+    }
+    uint32_t* mine = status + (size_t)tile * RADIX + tid;
+    atomicExch(mine, (tile == 0 ? LB_PREFIX : LB_AGGREGATE) | count);
+    uint32_t excl = 0;
+    int ok = 1;
+    if (tile > 0) {
+        const unsigned long long t0 = sort_clock_ns();
+        int p = tile - 1;
+        while (p >= 0) {
+            const uint32_t v = *(volatile uint32_t*)(status + (size_t)p * RADIX + tid);
+            if ((v & ~LB_COUNT) == 0u) {  // not published yet
+                if ((*(volatile unsigned*)ctl_status & ST_TIMEOUT) || sort_clock_ns() - t0 > wait_ns) {
+                    atomicOr(ctl_status, ST_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+                continue;
+            }
+            excl += v & LB_COUNT;
+            if (v & LB_PREFIX) break;
+            --p;
+        }
+        if (ok) atomicExch(mine, LB_PREFIX | (excl + count));
+    }
+    // global digit base: exclusive scan of the pass histogram
+    {
+        const uint32_t v = ghist[tid];
+        uint32_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) sm.wsum[warp] = x;
+        __syncthreads();
+        uint32_t pre = 0;
+        for (int w = 0; w < warp; ++w) pre += sm.wsum[w];
+        sm.base_d[tid] = pre + x - v + excl;
+    }
+    if (!__syncthreads_and(ok)) return;
+#pragma unroll
+    for (int it = 0; it < SORT_ITEMS; ++it) {
+        const int idx = wbase + it * 32 + lane;
+        if (idx < n) {
+            const uint32_t d = (kr[it] >> shift) & (RADIX - 1);
+            const uint32_t pos = sm.base_d[d] + sm.wcnt[warp][d] + rank[it];
+            if (pos < (uint32_t)n) {
+                keys_out[pos] = kr[it];
+                vals_out[pos] = vr[it];
+            }
+        }
+    }
+}
+
+// Adds the digits of `key` for every pass to the block's shared histograms h[pass][digit]
+// (warp-aggregated: one shared atomic per distinct digit in the warp).
+__device__ __forceinline__ void digit_hist_add(uint32_t key, bool valid, int passes,
+                                               uint32_t (*h)[RADIX]) {
+    const unsigned lm = lanemask_lt();
+    for (int p = 0; p < passes; ++p) {
+        const uint32_t d = valid ? ((key >> (8 * p)) & (RADIX - 1)) : (uint32_t)RADIX;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (valid && (peers & lm) == 0u) atomicAdd(&h[p][d], (uint32_t)__popc(peers));
+    }
+}
+
 // Cell table entry: number of sorted keys < c (lower bound), for c in [0, ncells].
 __device__ __forceinline__ uint32_t cell_offset(const uint32_t* __restrict__ skeys, int n, uint32_t c) {
     int lo = 0, hi = n;

@@ -71,7 +71,15 @@ struct StepLaunch {
     Control* ctl;
 };
 void launch_drift_keys(const StepLaunch& L, int drift, uint32_t* keys, cudaStream_t st);
-void launch_reorder(const StepLaunch& L, const uint32_t* perm, int carry_rates, cudaStream_t st);
+// Gather into cell order (reorder + EOS shadow) and the cell table off[0..ncells].
+void launch_reorder(const StepLaunch& L, const uint32_t* perm, int carry_rates, uint32_t* off,
+                    int ncells, cudaStream_t st);
+// Sort workspace (digit histograms, tile counters, look-back words) in 32-bit words.
+size_t sort_work_words(int n, int passes);
+void launch_keys_hist(const StepLaunch& L, int drift, uint32_t* keys0, int passes, uint32_t* work,
+                      cudaStream_t st);
+int launch_onesweep(int n, uint32_t* keys[2], uint32_t* vals[2], int passes, uint32_t* work,
+                    Control* ctl, unsigned long long wait_ns, cudaStream_t st);
 int pair_threads();
 void launch_pairs(const StepLaunch& L, cudaStream_t st);
 void launch_density_pass(const StepLaunch& L, cudaStream_t st);
@@ -85,7 +93,8 @@ struct FusedLaunch {
     StepLaunch L;                // L.Sin: current set; L.S: the other set (reorder target)
     uint32_t* keys[2];
     uint32_t* vals[2];
-    uint32_t* hist;              // 256 x ntiles digit counts, then 256 totals
+    uint32_t* work;              // one-sweep sort workspace (zero at launch; zeroed again)
+    int work_words;
     uint32_t* off;               // cell table, written by the reorder phase
     double* part;                // FUSED_PART doubles per block
     int passes, ntiles, ncells;
