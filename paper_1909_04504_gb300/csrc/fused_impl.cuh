@@ -60,42 +60,19 @@ __device__ __forceinline__ bool grid_sync(Control* ctl, unsigned long long limit
     return __syncthreads_and(ok) != 0;
 }
 
-// Block sums (k < NMAX0 or k >= NMAX1) and maxima (NMAX0 <= k < NMAX1) of NV values per
-// thread, fixed tree order; the result is valid in thread 0.
-template <int NV, int NMAX0, int NMAX1>
-__device__ __forceinline__ void block_reduce(double* v, double (*red)[FUSED_PART]) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            const double y = __shfl_down_sync(0xffffffffu, v[k], o);
-            v[k] = (k >= NMAX0 && k < NMAX1) ? fmax(v[k], y) : v[k] + y;
-        }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) red[warp][k] = v[k];
-    __syncthreads();
-    if (threadIdx.x == 0)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            double t = red[0][k];
-            for (int w = 1; w < FUSED_THREADS / 32; ++w)
-                t = (k >= NMAX0 && k < NMAX1) ? fmax(t, red[w][k]) : t + red[w][k];
-            v[k] = t;
-        }
-    __syncthreads();
-}
-
 template <class Real, int DIM, int KERNEL, int T>
 __global__ void __launch_bounds__(FUSED_THREADS, 2) k_step_fused(const FusedLaunch F) {
     using V = typename V4<Real>::T;
     __shared__ union {
         uint32_t h[4][RADIX];
         OnesweepSmem os;
-        double red[FUSED_THREADS / 32][FUSED_PART];
+        DensitySmem<FUSED_THREADS / T> dens;
+        MomSmem<FUSED_THREADS / T> mom;
         double bred[FUSED_THREADS / 32][10];
+        struct {
+            MomDiag mred[FUSED_THREADS / 32];
+            unsigned long long cred[FUSED_THREADS / 32][3];
+        };
     } sm;
     __shared__ int tile_s;
     const StepLaunch& L = F.L;
@@ -164,37 +141,23 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_step_fused(const FusedLaun
     const uint32_t* __restrict__ skeys = F.keys[cur];
     const uint32_t* __restrict__ perm = F.vals[cur];
 
-    // ---- gather into cell order (predictor kick, EOS shadow) and the cell table
+    // ---- gather into cell order (predictor kick, shadow) and the cell table
     for (int k = tid; k < L.n; k += nthreads) {
         const int inst = find_instance(L.cell_bounds, L.ninst, skeys[k]);
-        reorder_one<Real>(L.Sin, L.S, k, (int)perm[k], L.dim, tab[inst].C, L.idt[inst], 1, 0, P,
-                          Q, R);
+        reorder_one<Real>(L.Sin, L.S, k, (int)perm[k], L.dim, L.idt[inst], 1, 0, P, Q);
     }
     for (int c = tid; c <= F.ncells; c += nthreads) F.off[c] = cell_offset(skeys, L.n, (uint32_t)c);
     if (!grid_sync(ctl, F.wait_ns)) return;
     if (stamp) ctl->stamp[3] = global_ns();
 
-    // ---- density pass (T lanes per destination)
-    const Group<T> g;
+    // ---- density pass (T lanes per destination, compact FP64 epilogue)
     {
-        DensityCounts dc{0, 0, 0, 0};
-        for (int i = tid / T; i < L.n; i += nthreads / T) {
-            const uint32_t key = skeys[i];
-            const int inst = find_instance(L.cell_bounds, L.ninst, key);
-            const Inst<Real>& I = tab[inst];
-            density_dest<Real, DIM, KERNEL, T>(i, g, key - I.cell_base, P, Q, R, F.off + I.cell_base,
-                                            L.n, I.G, I.K, I.C, L.S, L.idt[inst], 1, L.nl, L.cnt,
-                                            L.maxn, dc,
-                                            L.finalize ? nullptr : L.pcount + 2 * (size_t)i,
-                                            L.finalize ? nullptr : L.pcount + 2 * (size_t)i + 1);
-        }
+        DensityCounts dc{0ull, 0ull, 0ull, 0};
+        density_tiles<Real, DIM, KERNEL, T, FUSED_THREADS>(
+            blockIdx.x, nb, P, Q, R, skeys, F.off, L.n, tab, L.cell_bounds, L.ninst, L.idt, L.S, 1,
+            L.nl, L.cnt, L.maxn, L.finalize ? nullptr : L.pcount, dc, sm.dens);
         if (dc.overflow) atomicOr(&ctl->status, ST_CAPACITY);
-        if (L.finalize) {
-            double v[3] = {dc.pairs, dc.cand, dc.wall};
-            block_reduce<3, 3, 3>(v, sm.red);
-            if (threadIdx.x == 0)
-                for (int k = 0; k < 3; ++k) F.part[(size_t)blockIdx.x * FUSED_PART + 7 + k] = v[k];
-        }
+        if (L.finalize) block_counts<FUSED_THREADS>(dc, F.part + (size_t)blockIdx.x * FUSED_PART + 8, sm.cred);
     }
     if (!grid_sync(ctl, F.wait_ns)) return;
     if (stamp) ctl->stamp[4] = global_ns();
@@ -203,19 +166,13 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_step_fused(const FusedLaun
     // no longer read in this step and is zeroed for the next one
     for (int w = tid; w < F.work_words; w += nthreads) F.work[w] = 0u;
     {
-        MomDiag md{0, 0, 0, 0, 0, 0, 0};
-        for (int i = tid / T; i < L.n; i += nthreads / T) {
-            const int inst = find_instance(L.cell_bounds, L.ninst, skeys[i]);
-            const Inst<Real>& I = tab[inst];
-            momentum_dest<Real, DIM, KERNEL, T>(i, g, P, Q, R, L.n, I.G, I.K, I.C, L.S,
-                                                L.idt[inst], 1, L.nl, L.cnt, md);
-        }
-        if (L.finalize) {
-            double v[7] = {md.px, md.py, md.pz, md.ke, md.u2, md.a2, (double)md.bad};
-            block_reduce<7, 4, 7>(v, sm.red);
-            if (threadIdx.x == 0)
-                for (int k = 0; k < 7; ++k) F.part[(size_t)blockIdx.x * FUSED_PART + k] = v[k];
-        }
+        MomDiag md{0, 0, 0, 0, 0ull, 0ull, 0u};
+        momentum_tiles<Real, DIM, KERNEL, T, FUSED_THREADS>(blockIdx.x, nb, P, Q, R, skeys, L.n, tab,
+                                                            L.cell_bounds, L.ninst, L.idt, L.S, 1,
+                                                            L.nl, L.cnt, md, sm.mom);
+        if (L.finalize)
+            block_mom_diag<(FUSED_THREADS / T + 31) / 32>(md, F.part + (size_t)blockIdx.x * FUSED_PART,
+                                                         sm.mred);
     }
     if (!grid_sync(ctl, F.wait_ns)) return;
     if (stamp) ctl->stamp[5] = global_ns();
@@ -223,17 +180,11 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_step_fused(const FusedLaun
     // ---- diagnostics, time and next dt
     if (L.finalize) {
         if (blockIdx.x != 0) return;
-        double w[10];
-#pragma unroll
-        for (int k = 0; k < 10; ++k) w[k] = 0.0;
-        for (int b = threadIdx.x; b < nb; b += FUSED_THREADS) {
-            const double* p = F.part + (size_t)b * FUSED_PART;
-#pragma unroll
-            for (int k = 0; k < 10; ++k) w[k] = (k >= 4 && k < 7) ? fmax(w[k], p[k]) : w[k] + p[k];
-        }
-        block_reduce<10, 4, 7>(w, sm.red);
+        double out[10];
+        reduce_partials<FUSED_THREADS>(F.part, FUSED_PART, nb, F.part + 8, FUSED_PART, nb, out,
+                                       sm.mred, sm.cred);
         if (threadIdx.x == 0) {
-            finish_single(ctl, L.history, tab[0].C, L.idt[0], 1, w);
+            finish_single(ctl, L.history, tab[0].C, L.idt[0], 1, out);
             ctl->outside = 0;
             ctl->stamp[6] = global_ns();
         }

@@ -130,15 +130,13 @@ __global__ void k_reorder(ParticleSet in, ParticleSet out, const uint32_t* __res
                           const Inst<Real>* __restrict__ tab, const uint32_t* __restrict__ cell_bounds,
                           int ninst, const double* __restrict__ idt, int kick, int carry_rates,
                           typename V4<Real>::T* __restrict__ P, typename V4<Real>::T* __restrict__ Q,
-                          Real* __restrict__ R, uint32_t* __restrict__ off, int ncells,
-                          const Control* ctl) {
+                          uint32_t* __restrict__ off, int ncells, const Control* ctl) {
     if (ctl->status) return;
     const int m = n > ncells + 1 ? n : ncells + 1;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
         if (k < n) {
             const int inst = find_instance(cell_bounds, ninst, skeys[k]);
-            reorder_one<Real>(in, out, k, (int)perm[k], dim, tab[inst].C, idt[inst], kick,
-                              carry_rates, P, Q, R);
+            reorder_one<Real>(in, out, k, (int)perm[k], dim, idt[inst], kick, carry_rates, P, Q);
         }
         if (k <= ncells) off[k] = cell_offset(skeys, n, (uint32_t)k);  // the cell table
     }
@@ -331,13 +329,13 @@ void launch_reorder(const StepLaunch& L, const uint32_t* perm, int carry_rates, 
     if (L.precision)
         k_reorder<float><<<g, 256, 0, st>>>(L.Sin, L.S, perm, L.skeys, L.n, L.dim,
                                             (const Inst<float>*)L.tab, L.cell_bounds, L.ninst, L.idt,
-                                            L.kick, carry_rates, (F4*)L.P, (F4*)L.Q, (float*)L.R,
-                                            off, ncells, L.ctl);
+                                            L.kick, carry_rates, (F4*)L.P, (F4*)L.Q, off, ncells,
+                                            L.ctl);
     else
         k_reorder<double><<<g, 256, 0, st>>>(L.Sin, L.S, perm, L.skeys, L.n, L.dim,
                                              (const Inst<double>*)L.tab, L.cell_bounds, L.ninst,
-                                             L.idt, L.kick, carry_rates, (D4*)L.P, (D4*)L.Q,
-                                             (double*)L.R, off, ncells, L.ctl);
+                                             L.idt, L.kick, carry_rates, (D4*)L.P, (D4*)L.Q, off,
+                                             ncells, L.ctl);
 }
 
 size_t sort_work_words(int n, int passes) {

@@ -108,10 +108,73 @@ __device__ __forceinline__ Real separation(const typename V4<Real>::T& pi,
     return dist2<Real, DIM>(dx, dy, dz);
 }
 
-// Block sum of 3 counters into pd[blockIdx.x * 4 + k] (fixed tree order).
-__device__ __forceinline__ void block_counts(double c0, double c1, double c2, double* pd) {
-    __shared__ double red[PAIR_THREADS / 32][3];
-    double v[3] = {c0, c1, c2};
+// ------------------------------------------------------------ diagnostics
+// Block partials of one evaluation, 8-byte slots: momentum pass [px, py, pz, ke] (FP64
+// sums), [max |u|^2, max |a|^2] (bit patterns of non-negative doubles, whose integer
+// order is their numeric order), [non-finite flag]; density pass [interacting pairs,
+// candidates, wall-destination pairs] (64-bit integers). Integer maxima, flags and counts
+// are exact in any order and keep the scarce FP64 pipe for the sums.
+struct MomDiag {
+    double px, py, pz, ke;
+    unsigned long long u2b, a2b;
+    unsigned bad;
+};
+
+struct DensityCounts {
+    unsigned long long pairs, cand, wall;
+    int overflow;
+};
+
+__device__ __forceinline__ unsigned long long u64max(unsigned long long a, unsigned long long b) {
+    return a > b ? a : b;
+}
+
+// Block reduction of the momentum diagnostics held by the first NW warps (fixed order);
+// thread 0 writes the 7 slots to out.
+template <int NW>
+__device__ __forceinline__ void block_mom_diag(MomDiag md, double* out, MomDiag* red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp < NW) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            md.px += __shfl_down_sync(0xffffffffu, md.px, o);
+            md.py += __shfl_down_sync(0xffffffffu, md.py, o);
+            md.pz += __shfl_down_sync(0xffffffffu, md.pz, o);
+            md.ke += __shfl_down_sync(0xffffffffu, md.ke, o);
+            md.u2b = u64max(md.u2b, __shfl_down_sync(0xffffffffu, md.u2b, o));
+            md.a2b = u64max(md.a2b, __shfl_down_sync(0xffffffffu, md.a2b, o));
+            md.bad |= __shfl_down_sync(0xffffffffu, md.bad, o);
+        }
+        if (lane == 0) red[warp] = md;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        MomDiag t = red[0];
+        for (int w = 1; w < NW; ++w) {
+            t.px += red[w].px;
+            t.py += red[w].py;
+            t.pz += red[w].pz;
+            t.ke += red[w].ke;
+            t.u2b = u64max(t.u2b, red[w].u2b);
+            t.a2b = u64max(t.a2b, red[w].a2b);
+            t.bad |= red[w].bad;
+        }
+        out[0] = t.px;
+        out[1] = t.py;
+        out[2] = t.pz;
+        out[3] = t.ke;
+        out[4] = __longlong_as_double((long long)t.u2b);
+        out[5] = __longlong_as_double((long long)t.a2b);
+        out[6] = __longlong_as_double((long long)t.bad);
+    }
+    __syncthreads();
+}
+
+// Block sums of the density-pass counters (NTH threads); thread 0 writes 3 slots to out.
+template <int NTH>
+__device__ __forceinline__ void block_counts(const DensityCounts& dc, double* out,
+                                             unsigned long long (*red)[3]) {
+    unsigned long long v[3] = {dc.pairs, dc.cand, dc.wall};
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
@@ -124,10 +187,48 @@ __device__ __forceinline__ void block_counts(double c0, double c1, double c2, do
     if (threadIdx.x == 0)
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            double t = red[0][k];
-            for (int w = 1; w < PAIR_THREADS / 32; ++w) t += red[w][k];
-            pd[(size_t)blockIdx.x * 4 + k] = t;
+            unsigned long long t = red[0][k];
+            for (int w = 1; w < NTH / 32; ++w) t += red[w][k];
+            out[k] = __longlong_as_double((long long)t);
         }
+    __syncthreads();
+}
+
+// Reduction of the block partials of both passes (NTH threads, fixed order) into
+// out[10] = px py pz ke max|u|^2 max|a|^2 bad pairs candidates wall-pairs (thread 0).
+template <int NTH>
+__device__ __forceinline__ void reduce_partials(const double* pm, int pm_stride, int nbm,
+                                                const double* pd, int pd_stride, int nbd,
+                                                double* out, MomDiag* red,
+                                                unsigned long long (*cred)[3]) {
+    MomDiag md{0, 0, 0, 0, 0ull, 0ull, 0u};
+    for (int b = threadIdx.x; b < nbm; b += NTH) {
+        const volatile double* p = pm + (size_t)b * pm_stride;
+        md.px += p[0];
+        md.py += p[1];
+        md.pz += p[2];
+        md.ke += p[3];
+        md.u2b = u64max(md.u2b, (unsigned long long)__double_as_longlong(p[4]));
+        md.a2b = u64max(md.a2b, (unsigned long long)__double_as_longlong(p[5]));
+        md.bad |= (unsigned)__double_as_longlong(p[6]);
+    }
+    DensityCounts dc{0ull, 0ull, 0ull, 0};
+    for (int b = threadIdx.x; b < nbd; b += NTH) {
+        const volatile double* p = pd + (size_t)b * pd_stride;
+        dc.pairs += (unsigned long long)__double_as_longlong(p[0]);
+        dc.cand += (unsigned long long)__double_as_longlong(p[1]);
+        dc.wall += (unsigned long long)__double_as_longlong(p[2]);
+    }
+    double m[7], c[3];
+    block_mom_diag<NTH / 32>(md, m, red);
+    block_counts<NTH>(dc, c, cred);
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 4; ++k) out[k] = m[k];
+        out[4] = __longlong_as_double(__double_as_longlong(m[4]));
+        out[5] = __longlong_as_double(__double_as_longlong(m[5]));
+        out[6] = (double)(unsigned)__double_as_longlong(m[6]);
+        for (int k = 0; k < 3; ++k) out[7 + k] = (double)(unsigned long long)__double_as_longlong(c[k]);
+    }
 }
 
 // ---------------------------------------------------------------- density pass
@@ -143,14 +244,12 @@ __device__ __forceinline__ void block_counts(double c0, double c1, double c2, do
 //  summation (Eq. 2): rho_i = sum_j m_j W_ij, self term included;
 //  continuity (Eq. continuity:sph): arho_i = sum_j m_j v_ij . grad_i W_ij and, inside a
 //    step, rho_i += dt arho_i (density advanced like the positions, Sec. 2.1 reading).
-// Then p from the Tait EOS in FP64 and the shadow rho, p / rho^2. Counts interacting pairs
-// (not both walls), candidates and the interacting pairs with a wall destination. A list
-// overflow raises ST_CAPACITY (the evaluation is then invalid and the step reports it).
-struct DensityCounts {
-    double pairs, cand, wall;
-    int overflow;
-};
-
+// (3) The epilogue (FP64 density update, the Tait EOS of Eq. eos for the shadow
+// p / rho^2, in the pair-loop precision): with T > 1 the destinations of a block tile
+// hand their sums through shared memory to one thread each, so the FP64 work runs on
+// full warps. Counts interacting pairs (not both walls), candidates and the interacting
+// pairs with a wall destination. A list overflow raises ST_CAPACITY (the evaluation is
+// then invalid and the step reports it).
 template <int T>
 __device__ __forceinline__ uint32_t group_sum_u32(uint32_t v, const Group<T>& g) {
 #pragma unroll
@@ -158,19 +257,17 @@ __device__ __forceinline__ uint32_t group_sum_u32(uint32_t v, const Group<T>& g)
     return v;
 }
 
-// Density pass for destination i (cell key `key`, cell table `off` of its grid), shared by
-// the T lanes of group g (lane 0 finishes).
+// Steps (1) and (2) for destination i; the compensated sum is valid in lane 0.
 template <class Real, int DIM, int KERNEL, int T>
-__device__ __forceinline__ void density_dest(int i, const Group<T>& g, uint32_t key,
-                                             const typename V4<Real>::T* __restrict__ P,
-                                             typename V4<Real>::T* __restrict__ Q,
-                                             Real* __restrict__ R, const uint32_t* __restrict__ off,
-                                             int n, const Grid& G, const PairConst<Real>& K,
-                                             const StepConst& C, const ParticleSet& S, double dt,
-                                             int kick, uint32_t* __restrict__ nl,
-                                             uint32_t* __restrict__ cnt, int maxn,
-                                             DensityCounts& dc, uint32_t* npairs_out,
-                                             uint32_t* ncand_out) {
+__device__ __forceinline__ void density_scan_sum(int i, const Group<T>& g, uint32_t key,
+                                                 const typename V4<Real>::T* __restrict__ P,
+                                                 const typename V4<Real>::T* __restrict__ Q,
+                                                 const uint32_t* __restrict__ off, int n,
+                                                 const Grid& G, const PairConst<Real>& K,
+                                                 uint32_t* __restrict__ nl,
+                                                 uint32_t* __restrict__ cnt, int maxn,
+                                                 DensityCounts& dc, uint32_t* pcount_i,
+                                                 Acc<Real>& sum) {
     const bool summation = !(K.flags & F_CONTINUITY);
     const typename V4<Real>::T pi = P[i];
     const bool fluid_i = pi.w > Real(0);
@@ -215,7 +312,6 @@ __device__ __forceinline__ void density_dest(int i, const Group<T>& g, uint32_t 
     }
     if (g.t == 0) cnt[i] = k;
     g.sync();  // the list entries of the other lanes are visible from here on
-    Acc<Real> sum;
     sum.zero();
     const typename V4<Real>::T qi = Q[i];
     for (uint32_t kk = g.t; kk < k; kk += T) {
@@ -235,36 +331,111 @@ __device__ __forceinline__ void density_dest(int i, const Group<T>& g, uint32_t 
         }
     }
     if (T > 1) group_reduce<Real, T>(sum, g);
-    dc.pairs += (double)npairs;
-    dc.cand += (double)ncand;
-    if (!fluid_i) dc.wall += (double)npairs;
-    if (npairs_out) {
+    dc.pairs += npairs;
+    dc.cand += ncand;
+    if (!fluid_i) dc.wall += npairs;
+    if (pcount_i) {
         const uint32_t np = group_sum_u32<T>(npairs, g), nc = group_sum_u32<T>(ncand, g);
         if (g.t == 0) {
-            *npairs_out = np;
-            *ncand_out = nc;
+            pcount_i[0] = np;
+            pcount_i[1] = nc;
         }
     }
-    if (g.t != 0) return;
-    double rho;
-    if (summation) {
-        rho = sum.value() + (double)(fabs(pi.w) * K.wfac * kernel_w<Real, KERNEL>(Real(0)));
-        S.arho[i] = 0.0;
-    } else {
-        const double ar = sum.value();
-        S.arho[i] = ar;
-        rho = S.rho[i];
-        if (kick) rho += dt * ar;
-    }
-    S.rho[i] = rho;
-    const double p = tait_pressure(rho, C);
-    reinterpret_cast<Real*>(&Q[i])[3] = (Real)rho;
-    R[i] = (Real)(p / (rho * rho));
 }
 
-// Density pass over all destinations; each finds its instance's constants in the table
-// (one entry for a single problem). Single problems accumulate block counts in pd; batches
-// store per-particle counts in pcount for the per-instance reduction.
+// Step (3) for destination i with the density-group value `value` (one thread).
+template <class Real, int KERNEL>
+__device__ __forceinline__ void density_finish(int i, double value, Real mi,
+                                               typename V4<Real>::T* __restrict__ Q,
+                                               Real* __restrict__ R, const PairConst<Real>& K,
+                                               const StepConst& C, const ParticleSet& S,
+                                               double dt, int kick) {
+    double rho, arho;
+    if (!(K.flags & F_CONTINUITY)) {
+        rho = value + (double)(fabs(mi) * K.wfac * kernel_w<Real, KERNEL>(Real(0)));
+        arho = 0.0;
+    } else {
+        arho = value;
+        rho = S.rho[i];
+        if (kick) rho += dt * arho;
+    }
+    S.rho[i] = rho;
+    S.arho[i] = arho;
+    reinterpret_cast<Real*>(&Q[i])[3] = (Real)rho;
+    R[i] = pressure_over_rho2<Real>(rho, C);
+}
+
+template <int GD>
+struct DensitySmem {
+    float s[GD], c[GD];  // unused when T = 1
+    double sd[GD], cd[GD];
+};
+
+// Density pass over destinations [tile * GD, (tile + 1) * GD) for tile = block,
+// block + nblocks, ... (GD = NTH / T); each destination finds its instance's constants in
+// the table (one entry for a single problem). pcount (batches): per-particle counts.
+template <class Real, int DIM, int KERNEL, int T, int NTH>
+__device__ __forceinline__ void density_tiles(int block, int nblocks,
+                                              const typename V4<Real>::T* __restrict__ P,
+                                              typename V4<Real>::T* __restrict__ Q,
+                                              Real* __restrict__ R,
+                                              const uint32_t* __restrict__ skeys,
+                                              const uint32_t* __restrict__ off, int n,
+                                              const Inst<Real>* __restrict__ tab,
+                                              const uint32_t* __restrict__ cell_bounds, int ninst,
+                                              const double* __restrict__ idt, const ParticleSet& S,
+                                              int kick, uint32_t* __restrict__ nl,
+                                              uint32_t* __restrict__ cnt, int maxn,
+                                              uint32_t* __restrict__ pcount, DensityCounts& dc,
+                                              DensitySmem<NTH / T>& sm) {
+    constexpr int GD = NTH / T;
+    const Group<T> g;
+    const int grp = threadIdx.x / T;
+    for (int tile = block; (long long)tile * GD < n; tile += nblocks) {
+        const int i = tile * GD + grp;
+        if (i < n) {
+            const uint32_t key = skeys[i];
+            const int inst = find_instance(cell_bounds, ninst, key);
+            const Inst<Real>& I = tab[inst];
+            Acc<Real> sum;
+            density_scan_sum<Real, DIM, KERNEL, T>(i, g, key - I.cell_base, P, Q, off + I.cell_base,
+                                                   n, I.G, I.K, nl, cnt, maxn, dc,
+                                                   pcount ? pcount + 2 * (size_t)i : nullptr, sum);
+            if (T == 1) {
+                density_finish<Real, KERNEL>(i, sum.value(), P[i].w, Q, R, I.K, I.C, S, idt[inst], kick);
+            } else if (g.t == 0) {
+                if (sizeof(Real) == 4) {
+                    sm.s[grp] = (float)sum.s;
+                    sm.c[grp] = (float)sum.c;
+                } else {
+                    sm.sd[grp] = (double)sum.s;
+                    sm.cd[grp] = (double)sum.c;
+                }
+            }
+        }
+        if (T > 1) {
+            __syncthreads();
+            const int e = tile * GD + threadIdx.x;
+            if (threadIdx.x < GD && e < n) {
+                const int inst = find_instance(cell_bounds, ninst, skeys[e]);
+                const Inst<Real>& I = tab[inst];
+                Acc<Real> a;
+                if (sizeof(Real) == 4) {
+                    a.s = (Real)sm.s[threadIdx.x];
+                    a.c = (Real)sm.c[threadIdx.x];
+                } else {
+                    a.s = (Real)sm.sd[threadIdx.x];
+                    a.c = (Real)sm.cd[threadIdx.x];
+                }
+                density_finish<Real, KERNEL>(e, a.value(), P[e].w, Q, R, I.K, I.C, S, idt[inst], kick);
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Density pass kernel. Single problems write block counts to pd; batches per-particle
+// counts to pcount for the per-instance reduction.
 template <class Real, int DIM, int KERNEL, int T>
 __global__ void __launch_bounds__(PAIR_THREADS, 6)
 k_density(const typename V4<Real>::T* __restrict__ P, typename V4<Real>::T* __restrict__ Q,
@@ -273,62 +444,43 @@ k_density(const typename V4<Real>::T* __restrict__ P, typename V4<Real>::T* __re
           int ninst, const double* __restrict__ idt, ParticleSet S, Control* ctl, int kick,
           uint32_t* __restrict__ nl, uint32_t* __restrict__ cnt, int maxn,
           double* __restrict__ pd, uint32_t* __restrict__ pcount) {
+    __shared__ DensitySmem<PAIR_THREADS / T> sm;
+    __shared__ unsigned long long cred[PAIR_THREADS / 32][3];
     if (ctl->status) return;
-    const Group<T> g;
-    DensityCounts dc{0, 0, 0, 0};
-    const int groups = gridDim.x * (PAIR_THREADS / T);
-    for (int i = (blockIdx.x * PAIR_THREADS + threadIdx.x) / T; i < n; i += groups) {
-        const uint32_t key = skeys[i];
-        const int inst = find_instance(cell_bounds, ninst, key);
-        const Inst<Real>& I = tab[inst];
-        density_dest<Real, DIM, KERNEL, T>(i, g, key - I.cell_base, P, Q, R, off + I.cell_base, n,
-                                           I.G, I.K, I.C, S, idt[inst], kick, nl, cnt, maxn, dc,
-                                           pcount ? pcount + 2 * (size_t)i : nullptr,
-                                           pcount ? pcount + 2 * (size_t)i + 1 : nullptr);
-    }
+    DensityCounts dc{0ull, 0ull, 0ull, 0};
+    density_tiles<Real, DIM, KERNEL, T, PAIR_THREADS>(blockIdx.x, gridDim.x, P, Q, R, skeys, off, n,
+                                                      tab, cell_bounds, ninst, idt, S, kick, nl,
+                                                      cnt, maxn, pcount, dc, sm);
     if (dc.overflow) atomicOr(&ctl->status, ST_CAPACITY);
-    if (pd) block_counts(dc.pairs, dc.cand, dc.wall, pd);
+    if (pd) block_counts<PAIR_THREADS>(dc, pd + (size_t)blockIdx.x * 4, cred);
 }
 
 // ------------------------------------------------------------- momentum pass
 // Fluid destinations only (walls are static), over the neighbour list of the density
-// pass: S lanes per destination take every S-th list entry (the tile shape the autotuner
-// picks) and combine their compensated partial sums with a fixed shuffle tree. Then the
-// corrector half-kick u^{n+1} = u^{n+1/2} + dt/2 a^{n+1} inside a step and the FP64
-// diagnostics. The last block to finish reduces the block partials of both passes in a
-// fixed order (deterministic) and writes the record, history entry, next dt and status.
-struct MomDiag {
-    double px, py, pz, ke, u2, a2;
-    int bad;
-};
+// pass: T lanes per destination take every T-th list entry (the tile shape the autotuner
+// picks) and combine their compensated partial sums with a fixed shuffle tree. The
+// epilogue (FP64 rates, the corrector half-kick u^{n+1} = u^{n+1/2} + dt/2 a^{n+1} inside
+// a step, the FP64 diagnostics) runs on one thread per destination: with T > 1 the sums
+// pass through shared memory so the FP64 work runs on full warps. With finalize (single
+// problems) the last block to finish reduces the block partials of both passes in a fixed
+// order (deterministic) and writes the record, history entry, next dt and status.
 
-// Momentum pass for destination i, shared by the T lanes of group g (lane 0 finishes).
+// Pair sums of destination i (fluid) into acc[0..5] = a_x a_y a_z xsph_x xsph_y xsph_z,
+// valid in lane 0.
 template <class Real, int DIM, int KERNEL, int T>
-__device__ __forceinline__ void momentum_dest(int i, const Group<T>& g,
+__device__ __forceinline__ void momentum_sums(int i, const Group<T>& g,
+                                              const typename V4<Real>::T& pi,
                                               const typename V4<Real>::T* __restrict__ P,
                                               const typename V4<Real>::T* __restrict__ Q,
-                                              const Real* __restrict__ R, int n,
-                                              const Grid& G, const PairConst<Real>& K,
-                                              const StepConst& C, const ParticleSet& S, double dt,
-                                              int kick, const uint32_t* __restrict__ nl,
-                                              const uint32_t* __restrict__ cnt, MomDiag& md) {
+                                              const Real* __restrict__ R, int n, const Grid& G,
+                                              const PairConst<Real>& K,
+                                              const uint32_t* __restrict__ nl,
+                                              const uint32_t* __restrict__ cnt, Acc<Real>* acc) {
     const int flags = K.flags;
-    const typename V4<Real>::T pi = P[i];
-    const bool fluid_i = pi.w > Real(0);
-    if (!fluid_i) {  // walls: no momentum equation, static
-        if (g.t == 0) {
-            for (int d = 0; d < DIM; ++d) {
-                S.a[d][i] = 0.0;
-                S.xs[d][i] = 0.0;
-            }
-            if (!isfinite(S.rho[i])) md.bad = 1;
-        }
-        return;
-    }
     const typename V4<Real>::T qi = Q[i];
     const Real pri = R[i];
-    Acc<Real> ax, ay, az, sx, sy, sz;
-    ax.zero(); ay.zero(); az.zero(); sx.zero(); sy.zero(); sz.zero();
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc[k].zero();
     const uint32_t ni = cnt[i];
     for (uint32_t kk = g.t; kk < ni; kk += T) {
         const uint32_t j = nl[(size_t)kk * n + i];
@@ -352,58 +504,159 @@ __device__ __forceinline__ void momentum_dest(int i, const Group<T>& g,
         const Real cg = -mj * coef * Gk;
         Real cv = Real(0);
         if (flags & F_LAMINAR) cv = mj * K.nu4 / (qi.w + qj.w) * Gk * r2 / (r2 + K.eta_h2);
-        ax.add(cg * dx + cv * vx);
-        ay.add(cg * dy + cv * vy);
-        if (DIM == 3) az.add(cg * dz + cv * vz);
+        acc[0].add(cg * dx + cv * vx);
+        acc[1].add(cg * dy + cv * vy);
+        if (DIM == 3) acc[2].add(cg * dz + cv * vz);
         if ((flags & F_XSPH) && pj.w > Real(0)) {
             const Real fx = K.xsph * mj / rhobar * (K.wfac * kernel_w<Real, KERNEL>(q));
-            sx.add(-fx * vx);
-            sy.add(-fx * vy);
-            if (DIM == 3) sz.add(-fx * vz);
+            acc[3].add(-fx * vx);
+            acc[4].add(-fx * vy);
+            if (DIM == 3) acc[5].add(-fx * vz);
         }
     }
     if (T > 1) {
-        group_reduce<Real, T>(ax, g);
-        group_reduce<Real, T>(ay, g);
-        if (DIM == 3) group_reduce<Real, T>(az, g);
+        group_reduce<Real, T>(acc[0], g);
+        group_reduce<Real, T>(acc[1], g);
+        if (DIM == 3) group_reduce<Real, T>(acc[2], g);
         if (flags & F_XSPH) {
-            group_reduce<Real, T>(sx, g);
-            group_reduce<Real, T>(sy, g);
-            if (DIM == 3) group_reduce<Real, T>(sz, g);
+            group_reduce<Real, T>(acc[3], g);
+            group_reduce<Real, T>(acc[4], g);
+            if (DIM == 3) group_reduce<Real, T>(acc[5], g);
         }
-    }
-    if (g.t == 0) {  // epilogue: FP64 rates, corrector half-kick, diagnostics
-        double a[3] = {ax.value(), ay.value(), az.value()};
-        double xs[3] = {sx.value(), sy.value(), sz.value()};
-        double u[3] = {0, 0, 0};
-        double u2 = 0, a2 = 0;
-        for (int d = 0; d < DIM; ++d) {
-            a[d] += C.g[d];
-            S.a[d][i] = a[d];
-            S.xs[d][i] = xs[d];
-            u[d] = S.u[d][i];
-            if (kick) {
-                u[d] += 0.5 * dt * a[d];
-                S.u[d][i] = u[d];
-            }
-            u2 += u[d] * u[d];
-            a2 += a[d] * a[d];
-            if (!isfinite(u[d]) || !isfinite(S.x[d][i])) md.bad = 1;
-        }
-        if (!isfinite(S.rho[i]) || !isfinite(a2)) md.bad = 1;
-        const double m = S.m[i];
-        md.px += m * u[0];
-        md.py += m * u[1];
-        md.pz += m * u[2];
-        md.ke += 0.5 * m * u2;
-        md.u2 = fmax(md.u2, u2);
-        md.a2 = fmax(md.a2, a2);
     }
 }
 
-// Momentum pass over all destinations (instance constants from the table). With
-// finalize (single problems) the block partials of both passes are reduced by the last
-// block, which writes the record, the history entry, the next dt and the status.
+// Epilogue of destination i (one thread): FP64 rates + body force, corrector half-kick,
+// diagnostics. Walls: rates zero, static.
+template <int DIM>
+__device__ __forceinline__ void momentum_finish(int i, bool fluid, const double* a_in,
+                                                const double* xs_in, const StepConst& C,
+                                                const ParticleSet& S, double dt, int kick,
+                                                MomDiag& md) {
+    if (!fluid) {
+        for (int d = 0; d < DIM; ++d) {
+            S.a[d][i] = 0.0;
+            S.xs[d][i] = 0.0;
+        }
+        if (!isfinite(S.rho[i])) md.bad = 1u;
+        return;
+    }
+    double u[3] = {0, 0, 0};
+    double u2 = 0, a2 = 0;
+    bool bad = false;
+    for (int d = 0; d < DIM; ++d) {
+        const double a = a_in[d] + C.g[d];
+        S.a[d][i] = a;
+        S.xs[d][i] = xs_in[d];
+        u[d] = S.u[d][i];
+        if (kick) {
+            u[d] += 0.5 * dt * a;
+            S.u[d][i] = u[d];
+        }
+        u2 += u[d] * u[d];
+        a2 += a * a;
+        bad |= !isfinite(u[d]) || !isfinite(S.x[d][i]);
+    }
+    bad |= !isfinite(S.rho[i]) || !isfinite(a2);
+    const double m = S.m[i];
+    md.px += m * u[0];
+    md.py += m * u[1];
+    md.pz += m * u[2];
+    md.ke += 0.5 * m * u2;
+    if (bad) md.bad = 1u;
+    else {
+        md.u2b = u64max(md.u2b, (unsigned long long)__double_as_longlong(u2));
+        md.a2b = u64max(md.a2b, (unsigned long long)__double_as_longlong(a2));
+    }
+}
+
+template <int GM>
+struct MomSmem {
+    float f[12][GM];   // s, c of the 6 sums (unused when T = 1)
+    double d[12][GM];
+    unsigned char fluid[GM];
+};
+
+// Momentum pass over destinations [tile * GM, (tile + 1) * GM) for tile = block,
+// block + nblocks, ... (GM = NTH / T).
+template <class Real, int DIM, int KERNEL, int T, int NTH>
+__device__ __forceinline__ void momentum_tiles(int block, int nblocks,
+                                               const typename V4<Real>::T* __restrict__ P,
+                                               const typename V4<Real>::T* __restrict__ Q,
+                                               const Real* __restrict__ R,
+                                               const uint32_t* __restrict__ skeys, int n,
+                                               const Inst<Real>* __restrict__ tab,
+                                               const uint32_t* __restrict__ cell_bounds, int ninst,
+                                               const double* __restrict__ idt, const ParticleSet& S,
+                                               int kick, const uint32_t* __restrict__ nl,
+                                               const uint32_t* __restrict__ cnt, MomDiag& md,
+                                               MomSmem<NTH / T>& sm) {
+    constexpr int GM = NTH / T;
+    const Group<T> g;
+    const int grp = threadIdx.x / T;
+    for (int tile = block; (long long)tile * GM < n; tile += nblocks) {
+        const int i = tile * GM + grp;
+        if (i < n) {
+            const int inst = find_instance(cell_bounds, ninst, skeys[i]);
+            const Inst<Real>& I = tab[inst];
+            const typename V4<Real>::T pi = P[i];
+            const bool fluid = pi.w > Real(0);
+            Acc<Real> acc[6];
+            if (fluid) momentum_sums<Real, DIM, KERNEL, T>(i, g, pi, P, Q, R, n, I.G, I.K, nl, cnt, acc);
+            else
+#pragma unroll
+                for (int k = 0; k < 6; ++k) acc[k].zero();
+            if (T == 1) {
+                double a[3], xs[3];
+                for (int d = 0; d < 3; ++d) {
+                    a[d] = acc[d].value();
+                    xs[d] = acc[3 + d].value();
+                }
+                momentum_finish<DIM>(i, fluid, a, xs, I.C, S, idt[inst], kick, md);
+            } else if (g.t == 0) {
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    if (sizeof(Real) == 4) {
+                        sm.f[2 * k][grp] = (float)acc[k].s;
+                        sm.f[2 * k + 1][grp] = (float)acc[k].c;
+                    } else {
+                        sm.d[2 * k][grp] = (double)acc[k].s;
+                        sm.d[2 * k + 1][grp] = (double)acc[k].c;
+                    }
+                }
+                sm.fluid[grp] = fluid ? 1 : 0;
+            }
+        }
+        if (T > 1) {
+            __syncthreads();
+            const int e = tile * GM + threadIdx.x;
+            if (threadIdx.x < GM && e < n) {
+                const int inst = find_instance(cell_bounds, ninst, skeys[e]);
+                double a[3], xs[3];
+                for (int d = 0; d < 3; ++d) {
+                    Acc<Real> x, y;
+                    if (sizeof(Real) == 4) {
+                        x.s = (Real)sm.f[2 * d][threadIdx.x];
+                        x.c = (Real)sm.f[2 * d + 1][threadIdx.x];
+                        y.s = (Real)sm.f[6 + 2 * d][threadIdx.x];
+                        y.c = (Real)sm.f[6 + 2 * d + 1][threadIdx.x];
+                    } else {
+                        x.s = (Real)sm.d[2 * d][threadIdx.x];
+                        x.c = (Real)sm.d[2 * d + 1][threadIdx.x];
+                        y.s = (Real)sm.d[6 + 2 * d][threadIdx.x];
+                        y.c = (Real)sm.d[6 + 2 * d + 1][threadIdx.x];
+                    }
+                    a[d] = x.value();
+                    xs[d] = y.value();
+                }
+                momentum_finish<DIM>(e, sm.fluid[threadIdx.x] != 0, a, xs, tab[inst].C, S, idt[inst],
+                                     kick, md);
+            }
+            __syncthreads();
+        }
+    }
+}
+
 template <class Real, int DIM, int KERNEL, int T>
 __global__ void __launch_bounds__(PAIR_THREADS, 5)
 k_momentum(const typename V4<Real>::T* __restrict__ P, const typename V4<Real>::T* __restrict__ Q,
@@ -413,46 +666,21 @@ k_momentum(const typename V4<Real>::T* __restrict__ P, const typename V4<Real>::
            const uint32_t* __restrict__ nl, const uint32_t* __restrict__ cnt,
            double* __restrict__ pm, const double* __restrict__ pd, int density_blocks,
            double* __restrict__ history, int finalize) {
-    __shared__ double red[PAIR_THREADS / 32][10];
+    constexpr int GM = PAIR_THREADS / T;
+    __shared__ MomSmem<GM> sm;
+    __shared__ MomDiag red[PAIR_THREADS / 32];
+    __shared__ unsigned long long cred[PAIR_THREADS / 32][3];
     __shared__ bool is_last;
     if (ctl->status) return;
-    const Group<T> g;
-    const double dt = idt[0];
-    MomDiag md{0, 0, 0, 0, 0, 0, 0};
-    const int groups = gridDim.x * (PAIR_THREADS / T);
-    for (int i = (blockIdx.x * PAIR_THREADS + threadIdx.x) / T; i < n; i += groups) {
-        const int inst = find_instance(cell_bounds, ninst, skeys[i]);
-        const Inst<Real>& I = tab[inst];
-        momentum_dest<Real, DIM, KERNEL, T>(i, g, P, Q, R, n, I.G, I.K, I.C, S, idt[inst], kick,
-                                            nl, cnt, md);
-    }
+    MomDiag md{0, 0, 0, 0, 0ull, 0ull, 0u};
+    momentum_tiles<Real, DIM, KERNEL, T, PAIR_THREADS>(blockIdx.x, gridDim.x, P, Q, R, skeys, n, tab,
+                                                       cell_bounds, ninst, idt, S, kick, nl, cnt, md,
+                                                       sm);
     if (!finalize) return;
-    const StepConst& C = tab[0].C;
-    double d_px = md.px, d_py = md.py, d_pz = md.pz, d_ke = md.ke, d_u2 = md.u2, d_a2 = md.a2;
-    int bad = md.bad;
-
-    // ---- block reduction (fixed tree order: deterministic)
-    constexpr int NV = 7;  // px py pz ke u2max a2max bad
-    double v[NV] = {d_px, d_py, d_pz, d_ke, d_u2, d_a2, (double)bad};
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            const double y = __shfl_down_sync(0xffffffffu, v[k], o);
-            v[k] = k >= 4 ? fmax(v[k], y) : v[k] + y;
-        }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) red[warp][k] = v[k];
-    __syncthreads();
+    const double dt = idt[0];
+    // ---- block partials (epilogue threads: the first ceil(GM / 32) warps)
+    block_mom_diag<(GM + 31) / 32>(md, pm + (size_t)blockIdx.x * 8, red);
     if (threadIdx.x == 0) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) {
-            double t = red[0][k];
-            for (int w = 1; w < PAIR_THREADS / 32; ++w) t = k >= 4 ? fmax(t, red[w][k]) : t + red[w][k];
-            pm[(size_t)blockIdx.x * 8 + k] = t;
-        }
         __threadfence();
         const unsigned t = atomicAdd(&ctl->ticket, 1u);
         is_last = (t == gridDim.x - 1);
@@ -460,44 +688,12 @@ k_momentum(const typename V4<Real>::T* __restrict__ P, const typename V4<Real>::
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    // ---- last block: momentum partials (7) and density-pass counts (3), fixed order
-    constexpr int NT = 10;
-    double w[NT];
-#pragma unroll
-    for (int k = 0; k < NT; ++k) w[k] = 0.0;
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += PAIR_THREADS) {
-        const volatile double* p = pm + (size_t)b * 8;
-#pragma unroll
-        for (int k = 0; k < NV; ++k) w[k] = k >= 4 ? fmax(w[k], p[k]) : w[k] + p[k];
-    }
-    for (int b = threadIdx.x; b < density_blocks; b += PAIR_THREADS) {
-        const volatile double* p = pd + (size_t)b * 4;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) w[NV + k] += p[k];
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int k = 0; k < NT; ++k) {
-            const double y = __shfl_down_sync(0xffffffffu, w[k], o);
-            w[k] = (k >= 4 && k < NV) ? fmax(w[k], y) : w[k] + y;
-        }
-    __syncthreads();
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < NT; ++k) red[warp][k] = w[k];
-    __syncthreads();
+    // ---- last block: both passes' partials in a fixed order
+    double out[10];
+    reduce_partials<PAIR_THREADS>(pm, 8, gridDim.x, pd, 4, density_blocks, out, red, cred);
     if (threadIdx.x == 0) {
-        double out[NT];
-#pragma unroll
-        for (int k = 0; k < NT; ++k) {
-            double t = red[0][k];
-            for (int ww = 1; ww < PAIR_THREADS / 32; ++ww)
-                t = (k >= 4 && k < NV) ? fmax(t, red[ww][k]) : t + red[ww][k];
-            out[k] = t;
-        }
         ctl->ticket = 0;
-        finish_single(ctl, history, C, dt, kick, out);
+        finish_single(ctl, history, tab[0].C, dt, kick, out);
     }
 }
 

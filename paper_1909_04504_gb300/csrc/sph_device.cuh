@@ -206,6 +206,30 @@ __device__ __forceinline__ double tait_pressure(double rho, const StepConst& C) 
     return C.B * e;
 }
 
+// The pair-loop shadow p / rho^2 in the pair-loop precision: FP64 mode from the FP64 EOS;
+// FP32 mode with delta formed in FP64 (no cancellation) and the polynomial (or
+// expm1(gamma log1p(delta))) and the quotient in FP32, the precision the pair loop reads.
+template <class Real>
+__device__ __forceinline__ Real pressure_over_rho2(double rho, const StepConst& C);
+
+template <>
+__device__ __forceinline__ double pressure_over_rho2<double>(double rho, const StepConst& C) {
+    return tait_pressure(rho, C) / (rho * rho);
+}
+
+template <>
+__device__ __forceinline__ float pressure_over_rho2<float>(double rho, const StepConst& C) {
+    const float d = (float)((rho - C.rho0) * C.inv_rho0);
+    float e;
+    if (C.gamma7) {
+        e = d * (7.f + d * (21.f + d * (35.f + d * (35.f + d * (21.f + d * (7.f + d))))));
+    } else {
+        e = expm1f((float)C.gamma * log1pf(d));
+    }
+    const float r = (float)rho;
+    return (float)C.B * e / (r * r);
+}
+
 // --------------------------------------------------------- compensated sums
 // Neumaier's improved Kahan-Babuska summation for FP32 per-particle sums; a plain sum
 // in FP64 mode. The value is read out in FP64 as s + c.

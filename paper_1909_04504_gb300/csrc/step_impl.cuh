@@ -48,15 +48,13 @@ __device__ __forceinline__ uint32_t drift_key_one(const ParticleSet& S, int i, c
 // Gather of particle o (previous order) into position k of the cell order. kick: the
 // predictor half-kick of the fluid velocity (the density is advanced later, like the
 // positions, by the density pass). Rates are carried along only outside a step
-// (carry_rates). Writes the pair-loop shadow: P = (x, y, z, +-m) with the sign marking
-// walls, Q = (u, v, w, rho), R = p / rho^2 with p from the Tait EOS (Eq. eos) in FP64.
+// (carry_rates). Writes the pair-loop shadow P = (x, y, z, +-m) with the sign marking
+// walls and Q = (u, v, w, rho); the density pass that follows writes Q.w and p / rho^2.
 template <class Real>
 __device__ __forceinline__ void reorder_one(const ParticleSet& in, const ParticleSet& out, int k,
-                                            int o, int dim, const StepConst& C, double dt,
-                                            int kick, int carry_rates,
+                                            int o, int dim, double dt, int kick, int carry_rates,
                                             typename V4<Real>::T* __restrict__ P,
-                                            typename V4<Real>::T* __restrict__ Q,
-                                            Real* __restrict__ R) {
+                                            typename V4<Real>::T* __restrict__ Q) {
     const uint32_t tag = in.tag[o];
     const bool fluid = !(tag & WALL_BIT);
     double x[3] = {0, 0, 0}, u[3] = {0, 0, 0};
@@ -79,14 +77,12 @@ __device__ __forceinline__ void reorder_one(const ParticleSet& in, const Particl
             out.xs[d][k] = in.xs[d][o];
         }
     }
-    const double p = tait_pressure(rho, C);
     typename V4<Real>::T pv, qv;
     pv.x = (Real)x[0]; pv.y = (Real)x[1]; pv.z = (Real)x[2];
     pv.w = (Real)(fluid ? m : -m);
     qv.x = (Real)u[0]; qv.y = (Real)u[1]; qv.z = (Real)u[2]; qv.w = (Real)rho;
     P[k] = pv;
     Q[k] = qv;
-    R[k] = (Real)(p / (rho * rho));
 }
 
 }  // namespace sph
