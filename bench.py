@@ -90,6 +90,35 @@ def pass_flops(wl) -> dict:
             "xsph_fluid_source_pair": xsph}
 
 
+# ------------------------------------------------------------ ncu traffic
+def source_hash() -> str:
+    """Hash of the CUDA sources; ncu figures taken from another tree are not reported."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_1909_04504_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload_name: str, kernel: str, lanes: int):
+    """DRAM bytes (read + write) per launch of `kernel` from the committed ncu summary, or
+    None when the kernels changed since the capture or the capture used another shape."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+    except (OSError, ValueError):
+        return None
+    entry = t.get(workload_name)
+    if t.get("source_hash") != source_hash() or not entry or entry.get("lanes") != lanes:
+        return None
+    return entry.get(kernel)
+
+
 # --------------------------------------------------------------------- clocks
 class ClockSampler:
     def __init__(self, gpu_index: str):
@@ -240,7 +269,8 @@ def gpu_arm(args, rank, world, dist):
              "momentum": "k_momentum (pressure, AV/viscosity, XSPH, corrector kick, reductions)"}
     roofline = {"bound": "alu", "achieved": per_pass[dom]["achieved_tflops"],
                 "peak": round(peak, 3), "unit": "TFLOP/s", "frac": per_pass[dom]["frac"],
-                "traffic": None, "kernel": names[dom],
+                "traffic": measured_traffic(args.workload, "k_" + dom, sim_lanes),
+                "kernel": names[dom],
                 "flops_per_launch": flops[dom], "avg_launch_ms": per_pass[dom]["avg_launch_ms"],
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
                                + (" / 64 (FP64)" if wl.precision == 0 else ""),
