@@ -182,6 +182,13 @@ sph_status make_grid(sph_ctx* c, const sph_domain& D, Grid* G) {
     }
     if (ncells > 2147483000.0) return fail(c, SPH_ERR_INVALID, "too many cells");
     G->ncells = (int)ncells;
+    // With >= 5 cells on every periodic axis a source run of the 3-cell stencil either
+    // lies within 2 cells (|dx| < 0.4 L: the minimum image never applies) or wraps around
+    // the box (|dx| > 0.6 L: it always applies, with the sign of the wrap), so the pair
+    // loops can apply it per run with the same arithmetic.
+    G->run_shift = 1;
+    for (int d = 0; d < D.dim; ++d)
+        if (G->periodic[d] && G->nc[d] < 5) G->run_shift = 0;
     return SPH_OK;
 }
 

@@ -16,6 +16,8 @@
 // are deterministic.
 #pragma once
 
+#include <type_traits>
+
 #include "sph_device.cuh"
 #include "sph_launch.h"
 #include "step_impl.cuh"
@@ -53,6 +55,44 @@ __device__ __forceinline__ void for_each_run(const Grid& G, const uint32_t* __re
                 if (x1 >= G.nc[0]) x1 = G.nc[0] - 1;
             }
             body(off[row + x0], off[row + x1 + 1]);
+        }
+    }
+}
+
+// As for_each_run, with the minimum-image shift of each run: body(jb, je, sx, sy, sz),
+// s = +L where the run wraps below the box (x_i - x_j is near -L), -L where it wraps above.
+template <class Real, int DIM, class Body>
+__device__ __forceinline__ void for_each_run_shift(const Grid& G, const PairConst<Real>& K,
+                                                   const uint32_t* __restrict__ off, int cx, int cy,
+                                                   int cz, Body body) {
+#pragma unroll 1
+    for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz) {
+        int z = cz + dz;
+        Real sz = Real(0);
+        if (DIM == 3 && (z < 0 || z >= G.nc[2])) {
+            if (!G.periodic[2]) continue;
+            sz = z < 0 ? K.L[2] : -K.L[2];
+            z = (z + G.nc[2]) % G.nc[2];
+        }
+#pragma unroll 1
+        for (int dy = -1; dy <= 1; ++dy) {
+            int y = cy + dy;
+            Real sy = Real(0);
+            if (y < 0 || y >= G.nc[1]) {
+                if (!G.periodic[1]) continue;
+                sy = y < 0 ? K.L[1] : -K.L[1];
+                y = (y + G.nc[1]) % G.nc[1];
+            }
+            const int row = G.nc[0] * (y + G.nc[1] * z);
+            int x0 = cx - 1, x1 = cx + 1;
+            if (G.periodic[0]) {
+                if (x0 < 0) { body(off[row + G.nc[0] - 1], off[row + G.nc[0]], K.L[0], sy, sz); x0 = 0; }
+                if (x1 >= G.nc[0]) { body(off[row], off[row + 1], -K.L[0], sy, sz); x1 = G.nc[0] - 1; }
+            } else {
+                if (x0 < 0) x0 = 0;
+                if (x1 >= G.nc[0]) x1 = G.nc[0] - 1;
+            }
+            body(off[row + x0], off[row + x1 + 1], Real(0), sy, sz);
         }
     }
 }
@@ -275,16 +315,32 @@ __device__ __forceinline__ void density_scan_sum(int i, const Group<T>& g, uint3
     cell_of_key(G, key, cx, cy, cz);
     uint32_t k = 0, npairs = 0, ncand = 0;
     const unsigned below = (1u << g.t) - 1u;
-    for_each_run<DIM>(G, off, cx, cy, cz, [&](uint32_t jb, uint32_t je) {
+    // candidates of one run: SHIFT adds the run's minimum-image shift (exact: adding 0
+    // changes nothing but the sign of a zero), MINIMG applies the per-pair minimum image
+    auto scan = [&](uint32_t jb, uint32_t je, Real sx, Real sy, Real sz, auto shift_tag,
+                    auto minimg_tag) {
+        constexpr bool SHIFT = decltype(shift_tag)::value;
+        constexpr bool MINIMG = decltype(minimg_tag)::value;
+        if (g.t == 0) ncand += (je - jb) - ((uint32_t)i - jb < je - jb ? 1u : 0u);
 #pragma unroll 2
         for (uint32_t c = jb; c < je; c += T) {
             const uint32_t j = c + g.t;
             bool listed = false;
             if (j < je && (int)j != i) {
-                ++ncand;
                 const typename V4<Real>::T pj = P[j];
-                Real dx, dy, dz;
-                const Real r2 = separation<Real, DIM>(pi, pj, G, K, dx, dy, dz);
+                Real dx = rn_sub(pi.x, pj.x), dy = rn_sub(pi.y, pj.y);
+                Real dz = DIM == 3 ? rn_sub(pi.z, pj.z) : Real(0);
+                if (MINIMG) {
+                    dx = min_image(dx, G.periodic[0], K.L[0], K.halfL[0]);
+                    dy = min_image(dy, G.periodic[1], K.L[1], K.halfL[1]);
+                    if (DIM == 3) dz = min_image(dz, G.periodic[2], K.L[2], K.halfL[2]);
+                }
+                if (SHIFT) {
+                    dx = rn_add(dx, sx);
+                    dy = rn_add(dy, sy);
+                    if (DIM == 3) dz = rn_add(dz, sz);
+                }
+                const Real r2 = dist2<Real, DIM>(dx, dy, dz);
                 if (r2 < K.kh2) {
                     const bool interacting = fluid_i || pj.w > Real(0);
                     listed = interacting || summation;
@@ -305,7 +361,19 @@ __device__ __forceinline__ void density_scan_sum(int i, const Group<T>& g, uint3
                 k += __popc(m);
             }
         }
-    });
+    };
+    using yes = std::true_type;
+    using no = std::false_type;
+    if (G.run_shift) {
+        for_each_run_shift<Real, DIM>(G, K, off, cx, cy, cz, [&](uint32_t jb, uint32_t je, Real sx, Real sy, Real sz) {
+            if (sx == Real(0) && sy == Real(0) && sz == Real(0)) scan(jb, je, sx, sy, sz, no(), no());
+            else scan(jb, je, sx, sy, sz, yes(), no());
+        });
+    } else {
+        for_each_run<DIM>(G, off, cx, cy, cz, [&](uint32_t jb, uint32_t je) {
+            scan(jb, je, Real(0), Real(0), Real(0), no(), yes());
+        });
+    }
     if (k > (uint32_t)maxn) {
         dc.overflow = 1;
         k = maxn;

@@ -70,6 +70,7 @@ struct Grid {
     int nc[3];
     int periodic[3];
     int ncells;
+    int run_shift;  // every periodic axis has >= 5 cells: the minimum image is a per-run shift
     double lo[3], cs[3], L[3], hi[3];
 };
 

@@ -255,3 +255,17 @@ def test_cell_sort_many_tiles_bit_exact(prec):
     assert np.array_equal(cell_of, ocell)
     assert np.array_equal(off, ooff)
     assert np.array_equal(np.asarray(order, np.int64), np.argsort(ocell, kind="stable"))
+
+
+@pytest.mark.parametrize("dim,n", [(2, 12), (2, 14), (2, 16), (3, 12), (3, 14), (3, 16)])
+@pytest.mark.parametrize("prec", [G.PREC_FP64, G.PREC_FP32])
+def test_neighbours_small_periodic_grids(dim, n, prec):
+    """3, 4 and 5 cells per periodic axis: the per-pair minimum image (fewer than 5 cells)
+    and the per-run shift (5 or more) give the oracle's neighbour sets after 5 steps."""
+    wl = (W.taylor_green_2d if dim == 2 else W.taylor_green_3d)(n=n, precision=prec)
+    with sim_of(wl) as sim:
+        sim.step(G.scheme_of(wl), wl.dt, 5)
+        g = sim.state()
+        noff, nidx = sim.neighbors()
+    ooff, oidx, _ = O.neighbors(wl, g["x"], g["y"], g.get("z"))
+    assert csr_equal(noff, nidx, ooff, oidx)
