@@ -167,6 +167,8 @@ sph_status make_grid(sph_ctx* c, const sph_domain& D, Grid* G) {
             if (G->periodic[d] && G->nc[d] < 3)
                 return fail(c, SPH_ERR_INVALID, "a periodic axis needs at least 3 cells");
             G->cs[d] = ext / (double)G->nc[d];
+            G->lo_f[d] = (float)D.lo[d];
+            G->inv_cs_f[d] = (float)(1.0 / G->cs[d]);
             G->lo[d] = D.lo[d];
             G->hi[d] = D.hi[d];
             G->L[d] = ext;
@@ -174,6 +176,8 @@ sph_status make_grid(sph_ctx* c, const sph_domain& D, Grid* G) {
             G->nc[d] = 1;
             G->periodic[d] = 0;
             G->cs[d] = 1.0;
+            G->lo_f[d] = 0.0f;
+            G->inv_cs_f[d] = 1.0f;
             G->lo[d] = 0.0;
             G->hi[d] = 1.0;
             G->L[d] = 1.0;

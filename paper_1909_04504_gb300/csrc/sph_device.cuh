@@ -71,6 +71,7 @@ struct Grid {
     int periodic[3];
     int ncells;
     int run_shift;  // every periodic axis has >= 5 cells: the minimum image is a per-run shift
+    float lo_f[3], inv_cs_f[3];  // lo and 1 / cs rounded to FP32 (screened cell coordinate)
     double lo[3], cs[3], L[3], hi[3];
 };
 
@@ -131,13 +132,31 @@ __device__ __forceinline__ Real dist2(Real dx, Real dy, Real dz) {
     return r2;
 }
 
-// Cell coordinate of a position on one axis: floor((x_mode - lo) / cs), clamped.
+// Cell coordinate of a position on one axis: floor((x_mode - lo) / cs) in FP64, clamped.
 __device__ __forceinline__ int cell_coord(double xm, double lo, double cs, int n, int* clamped) {
     double v = __ddiv_rn(__dsub_rn(xm, lo), cs);
     double c = floor(v);
     if (!(c >= 0.0)) { *clamped = 1; return 0; }
     if (c > (double)(n - 1)) { *clamped = 1; return n - 1; }
     return (int)c;
+}
+
+// The same cell coordinate, screened in FP32: q = (x_f - lo_f) * inv_cs_f differs from the
+// FP64 quotient by at most 8 u ((|x_f| + |lo_f|) inv_cs_f + |q| + 1), u = 2^-24 (each of the
+// five FP32 roundings contributes at most u times its operand). When no integer lies
+// within that bound of q, floor(q) is the FP64 result; otherwise (about one coordinate in
+// a few thousand) the FP64 quotient decides. The FP64 pipe of this part runs at 1/64 of
+// FP32 and its divide costs many instructions, so the screen keeps it off the common path.
+__device__ __forceinline__ int cell_coord_screened(double xm, float xf, double lo, double cs,
+                                                   float lo_f, float inv_cs_f, int n,
+                                                   int* clamped) {
+    const float q = (xf - lo_f) * inv_cs_f;
+    const float m = 4.7683716e-7f * ((fabsf(xf) + fabsf(lo_f)) * inv_cs_f + fabsf(q) + 1.0f);
+    const float lo_q = floorf(q - m), hi_q = floorf(q + m);
+    if (!(lo_q == hi_q)) return cell_coord(xm, lo, cs, n, clamped);  // near a cell edge, NaN
+    if (!(lo_q >= 0.0f)) { *clamped = 1; return 0; }
+    if (lo_q > (float)(n - 1)) { *clamped = 1; return n - 1; }
+    return (int)lo_q;
 }
 
 // ------------------------------------------------------------------- kernels

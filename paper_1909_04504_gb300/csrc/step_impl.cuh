@@ -39,8 +39,10 @@ __device__ __forceinline__ uint32_t drift_key_one(const ParticleSet& S, int i, c
             }
             S.x[d][i] = x;
         }
-        double xm = C.precision ? (double)__double2float_rn(x) : x;
-        c[d] = cell_coord(xm, G.lo[d], G.cs[d], G.nc[d], &clamped);
+        const float xf = __double2float_rn(x);
+        const double xm = C.precision ? (double)xf : x;
+        c[d] = cell_coord_screened(xm, xf, G.lo[d], G.cs[d], G.lo_f[d], G.inv_cs_f[d], G.nc[d],
+                                   &clamped);
     }
     return (uint32_t)(c[0] + G.nc[0] * (c[1] + G.nc[1] * c[2]));
 }
@@ -49,7 +51,7 @@ __device__ __forceinline__ uint32_t drift_key_one(const ParticleSet& S, int i, c
 // predictor half-kick of the fluid velocity (the density is advanced later, like the
 // positions, by the density pass). Rates are carried along only outside a step
 // (carry_rates). Writes the pair-loop shadow P = (x, y, z, +-m) with the sign marking
-// walls and Q = (u, v, w, rho); the density pass that follows writes Q.w and p / rho^2.
+// walls and Q = (u, v, w, .); the density pass that follows writes Q.w = rho and p / rho^2.
 template <class Real>
 __device__ __forceinline__ void reorder_one(const ParticleSet& in, const ParticleSet& out, int k,
                                             int o, int dim, double dt, int kick, int carry_rates,
@@ -80,7 +82,8 @@ __device__ __forceinline__ void reorder_one(const ParticleSet& in, const Particl
     typename V4<Real>::T pv, qv;
     pv.x = (Real)x[0]; pv.y = (Real)x[1]; pv.z = (Real)x[2];
     pv.w = (Real)(fluid ? m : -m);
-    qv.x = (Real)u[0]; qv.y = (Real)u[1]; qv.z = (Real)u[2]; qv.w = (Real)rho;
+    qv.x = (Real)u[0]; qv.y = (Real)u[1]; qv.z = (Real)u[2];
+    qv.w = Real(0);  // the density pass writes it
     P[k] = pv;
     Q[k] = qv;
 }
