@@ -66,8 +66,8 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_step_fused(const FusedLaun
     __shared__ union {
         uint32_t h[4][RADIX];
         OnesweepSmem os;
-        DensitySmem<FUSED_THREADS / T> dens;
-        MomSmem<FUSED_THREADS / T> mom;
+        DensitySmem<Real, T == 1 ? 1 : FUSED_THREADS / T> dens;
+        MomSmem<Real, T == 1 ? 1 : FUSED_THREADS / T> mom;
         double bred[FUSED_THREADS / 32][10];
         struct {
             MomDiag mred[FUSED_THREADS / 32];

@@ -433,10 +433,11 @@ __device__ __forceinline__ void density_finish(int i, double value, Real mi,
     R[i] = pressure_over_rho2<Real>(rho, C);
 }
 
-template <int GD>
+// Hand-off of the compensated sums of a block tile to the epilogue threads (T > 1; a
+// single placeholder entry when T = 1).
+template <class Real, int GD>
 struct DensitySmem {
-    float s[GD], c[GD];  // unused when T = 1
-    double sd[GD], cd[GD];
+    Real s[GD], c[GD];
 };
 
 // Density pass over destinations [tile * GD, (tile + 1) * GD) for tile = block,
@@ -455,7 +456,7 @@ __device__ __forceinline__ void density_tiles(int block, int nblocks,
                                               int kick, uint32_t* __restrict__ nl,
                                               uint32_t* __restrict__ cnt, int maxn,
                                               uint32_t* __restrict__ pcount, DensityCounts& dc,
-                                              DensitySmem<NTH / T>& sm) {
+                                              DensitySmem<Real, T == 1 ? 1 : NTH / T>& sm) {
     constexpr int GD = NTH / T;
     const Group<T> g;
     const int grp = threadIdx.x / T;
@@ -472,13 +473,8 @@ __device__ __forceinline__ void density_tiles(int block, int nblocks,
             if (T == 1) {
                 density_finish<Real, KERNEL>(i, sum.value(), P[i].w, Q, R, I.K, I.C, S, idt[inst], kick);
             } else if (g.t == 0) {
-                if (sizeof(Real) == 4) {
-                    sm.s[grp] = (float)sum.s;
-                    sm.c[grp] = (float)sum.c;
-                } else {
-                    sm.sd[grp] = (double)sum.s;
-                    sm.cd[grp] = (double)sum.c;
-                }
+                sm.s[grp] = sum.s;
+                sm.c[grp] = sum.c;
             }
         }
         if (T > 1) {
@@ -488,13 +484,8 @@ __device__ __forceinline__ void density_tiles(int block, int nblocks,
                 const int inst = find_instance(cell_bounds, ninst, skeys[e]);
                 const Inst<Real>& I = tab[inst];
                 Acc<Real> a;
-                if (sizeof(Real) == 4) {
-                    a.s = (Real)sm.s[threadIdx.x];
-                    a.c = (Real)sm.c[threadIdx.x];
-                } else {
-                    a.s = (Real)sm.sd[threadIdx.x];
-                    a.c = (Real)sm.cd[threadIdx.x];
-                }
+                a.s = sm.s[threadIdx.x];
+                a.c = sm.c[threadIdx.x];
                 density_finish<Real, KERNEL>(e, a.value(), P[e].w, Q, R, I.K, I.C, S, idt[inst], kick);
             }
             __syncthreads();
@@ -512,7 +503,7 @@ k_density(const typename V4<Real>::T* __restrict__ P, typename V4<Real>::T* __re
           int ninst, const double* __restrict__ idt, ParticleSet S, Control* ctl, int kick,
           uint32_t* __restrict__ nl, uint32_t* __restrict__ cnt, int maxn,
           double* __restrict__ pd, uint32_t* __restrict__ pcount) {
-    __shared__ DensitySmem<PAIR_THREADS / T> sm;
+    __shared__ DensitySmem<Real, T == 1 ? 1 : PAIR_THREADS / T> sm;
     __shared__ unsigned long long cred[PAIR_THREADS / 32][3];
     if (ctl->status) return;
     DensityCounts dc{0ull, 0ull, 0ull, 0};
@@ -638,10 +629,11 @@ __device__ __forceinline__ void momentum_finish(int i, bool fluid, const double*
     }
 }
 
-template <int GM>
+// Hand-off of the 6 compensated sums (s, c) of a block tile to the epilogue threads
+// (T > 1; a single placeholder entry when T = 1).
+template <class Real, int GM>
 struct MomSmem {
-    float f[12][GM];   // s, c of the 6 sums (unused when T = 1)
-    double d[12][GM];
+    Real v[12][GM];
     unsigned char fluid[GM];
 };
 
@@ -658,7 +650,7 @@ __device__ __forceinline__ void momentum_tiles(int block, int nblocks,
                                                const double* __restrict__ idt, const ParticleSet& S,
                                                int kick, const uint32_t* __restrict__ nl,
                                                const uint32_t* __restrict__ cnt, MomDiag& md,
-                                               MomSmem<NTH / T>& sm) {
+                                               MomSmem<Real, T == 1 ? 1 : NTH / T>& sm) {
     constexpr int GM = NTH / T;
     const Group<T> g;
     const int grp = threadIdx.x / T;
@@ -684,13 +676,8 @@ __device__ __forceinline__ void momentum_tiles(int block, int nblocks,
             } else if (g.t == 0) {
 #pragma unroll
                 for (int k = 0; k < 6; ++k) {
-                    if (sizeof(Real) == 4) {
-                        sm.f[2 * k][grp] = (float)acc[k].s;
-                        sm.f[2 * k + 1][grp] = (float)acc[k].c;
-                    } else {
-                        sm.d[2 * k][grp] = (double)acc[k].s;
-                        sm.d[2 * k + 1][grp] = (double)acc[k].c;
-                    }
+                    sm.v[2 * k][grp] = acc[k].s;
+                    sm.v[2 * k + 1][grp] = acc[k].c;
                 }
                 sm.fluid[grp] = fluid ? 1 : 0;
             }
@@ -703,17 +690,10 @@ __device__ __forceinline__ void momentum_tiles(int block, int nblocks,
                 double a[3], xs[3];
                 for (int d = 0; d < 3; ++d) {
                     Acc<Real> x, y;
-                    if (sizeof(Real) == 4) {
-                        x.s = (Real)sm.f[2 * d][threadIdx.x];
-                        x.c = (Real)sm.f[2 * d + 1][threadIdx.x];
-                        y.s = (Real)sm.f[6 + 2 * d][threadIdx.x];
-                        y.c = (Real)sm.f[6 + 2 * d + 1][threadIdx.x];
-                    } else {
-                        x.s = (Real)sm.d[2 * d][threadIdx.x];
-                        x.c = (Real)sm.d[2 * d + 1][threadIdx.x];
-                        y.s = (Real)sm.d[6 + 2 * d][threadIdx.x];
-                        y.c = (Real)sm.d[6 + 2 * d + 1][threadIdx.x];
-                    }
+                    x.s = sm.v[2 * d][threadIdx.x];
+                    x.c = sm.v[2 * d + 1][threadIdx.x];
+                    y.s = sm.v[6 + 2 * d][threadIdx.x];
+                    y.c = sm.v[6 + 2 * d + 1][threadIdx.x];
                     a[d] = x.value();
                     xs[d] = y.value();
                 }
@@ -725,8 +705,10 @@ __device__ __forceinline__ void momentum_tiles(int block, int nblocks,
     }
 }
 
+// FP32: 8 blocks of 128 per SM (64 registers; the gathers of the pair loop are latency-
+// bound and gain more from the extra warps than the few spills cost); FP64: 5.
 template <class Real, int DIM, int KERNEL, int T>
-__global__ void __launch_bounds__(PAIR_THREADS, 5)
+__global__ void __launch_bounds__(PAIR_THREADS, sizeof(Real) == 4 ? 8 : 5)
 k_momentum(const typename V4<Real>::T* __restrict__ P, const typename V4<Real>::T* __restrict__ Q,
            const Real* __restrict__ R, const uint32_t* __restrict__ skeys, int n,
            const Inst<Real>* __restrict__ tab, const uint32_t* __restrict__ cell_bounds, int ninst,
@@ -735,7 +717,7 @@ k_momentum(const typename V4<Real>::T* __restrict__ P, const typename V4<Real>::
            double* __restrict__ pm, const double* __restrict__ pd, int density_blocks,
            double* __restrict__ history, int finalize) {
     constexpr int GM = PAIR_THREADS / T;
-    __shared__ MomSmem<GM> sm;
+    __shared__ MomSmem<Real, T == 1 ? 1 : GM> sm;
     __shared__ MomDiag red[PAIR_THREADS / 32];
     __shared__ unsigned long long cred[PAIR_THREADS / 32][3];
     __shared__ bool is_last;
