@@ -59,12 +59,22 @@ __device__ __forceinline__ void for_each_run(const Grid& G, const uint32_t* __re
     }
 }
 
-// As for_each_run, with the minimum-image shift of each run: body(jb, je, sx, sy, sz),
-// s = +L where the run wraps below the box (x_i - x_j is near -L), -L where it wraps above.
+// The stencil walk clipped to the support: a row (dy, dz) whose distance from the
+// destination in (y, z) reaches the support radius is skipped, and in every other row the
+// x cells out of reach are dropped, so only candidates that can pass the predicate are
+// examined; the order of the remaining runs (and so of the neighbour list) is that of
+// for_each_run. body(jb, je, sx, sy, sz) also gets the run's minimum-image shift
+// (s = +L where the run wraps below the box, -L above; valid when G.run_shift). `e` holds
+// the destination's distances to the lower faces of its own cell and `c` the cell sizes;
+// `reach2` is the squared support radius widened by a margin far above the FP32 rounding of
+// these distances, so no cell that holds a neighbour is dropped. Returns, in ncand, the
+// candidates of the full 3^d stencil (the count the interaction metric reports).
 template <class Real, int DIM, class Body>
-__device__ __forceinline__ void for_each_run_shift(const Grid& G, const PairConst<Real>& K,
-                                                   const uint32_t* __restrict__ off, int cx, int cy,
-                                                   int cz, Body body) {
+__device__ __forceinline__ void for_each_clipped_run(const Grid& G, const PairConst<Real>& K,
+                                                     const uint32_t* __restrict__ off, int cx, int cy,
+                                                     int cz, const float* e, const float* c,
+                                                     float reach2, uint32_t& ncand, Body body) {
+    const float ex_lo = e[0], ex_hi = c[0] - e[0];
 #pragma unroll 1
     for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz) {
         int z = cz + dz;
@@ -74,6 +84,7 @@ __device__ __forceinline__ void for_each_run_shift(const Grid& G, const PairCons
             sz = z < 0 ? K.L[2] : -K.L[2];
             z = (z + G.nc[2]) % G.nc[2];
         }
+        const float bz = DIM == 3 ? (dz < 0 ? e[2] : (dz > 0 ? c[2] - e[2] : 0.0f)) : 0.0f;
 #pragma unroll 1
         for (int dy = -1; dy <= 1; ++dy) {
             int y = cy + dy;
@@ -83,16 +94,35 @@ __device__ __forceinline__ void for_each_run_shift(const Grid& G, const PairCons
                 sy = y < 0 ? K.L[1] : -K.L[1];
                 y = (y + G.nc[1]) % G.nc[1];
             }
-            const int row = G.nc[0] * (y + G.nc[1] * z);
-            int x0 = cx - 1, x1 = cx + 1;
+            const float ay = dy < 0 ? e[1] : (dy > 0 ? c[1] - e[1] : 0.0f);
+            const float w2 = reach2 - (ay * ay + bz * bz);  // <= 0: the row is out of reach
+            const bool row = w2 > 0.0f;
+            const bool need_l = row && ex_lo * ex_lo < w2, need_r = row && ex_hi * ex_hi < w2;
+            const int rowb = G.nc[0] * (y + G.nc[1] * z);
+            int xa = cx - 1, xb = cx + 1;
             if (G.periodic[0]) {
-                if (x0 < 0) { body(off[row + G.nc[0] - 1], off[row + G.nc[0]], K.L[0], sy, sz); x0 = 0; }
-                if (x1 >= G.nc[0]) { body(off[row], off[row + 1], -K.L[0], sy, sz); x1 = G.nc[0] - 1; }
+                if (xa < 0) {
+                    const uint32_t jb = off[rowb + G.nc[0] - 1], je = off[rowb + G.nc[0]];
+                    ncand += je - jb;
+                    if (need_l) body(jb, je, K.L[0], sy, sz);
+                    xa = 0;
+                }
+                if (xb >= G.nc[0]) {
+                    const uint32_t jb = off[rowb], je = off[rowb + 1];
+                    ncand += je - jb;
+                    if (need_r) body(jb, je, -K.L[0], sy, sz);
+                    xb = G.nc[0] - 1;
+                }
             } else {
-                if (x0 < 0) x0 = 0;
-                if (x1 >= G.nc[0]) x1 = G.nc[0] - 1;
+                if (xa < 0) xa = 0;
+                if (xb >= G.nc[0]) xb = G.nc[0] - 1;
             }
-            body(off[row + x0], off[row + x1 + 1], Real(0), sy, sz);
+            const uint32_t fb = off[rowb + xa], fe = off[rowb + xb + 1];
+            ncand += fe - fb;
+            if (!row) continue;
+            const int t0 = max(xa, need_l ? cx - 1 : cx), t1 = min(xb, need_r ? cx + 1 : cx);
+            if (t0 > t1) continue;
+            body(t0 == xa ? fb : off[rowb + t0], t1 == xb ? fe : off[rowb + t1 + 1], Real(0), sy, sz);
         }
     }
 }
@@ -321,12 +351,13 @@ __device__ __forceinline__ void density_scan_sum(int i, const Group<T>& g, uint3
                     auto minimg_tag) {
         constexpr bool SHIFT = decltype(shift_tag)::value;
         constexpr bool MINIMG = decltype(minimg_tag)::value;
-        if (g.t == 0) ncand += (je - jb) - ((uint32_t)i - jb < je - jb ? 1u : 0u);
 #pragma unroll 2
         for (uint32_t c = jb; c < je; c += T) {
             const uint32_t j = c + g.t;
-            bool listed = false;
-            if (j < je && (int)j != i) {
+            // written as predicates: the loop body is a straight line (no per-candidate
+            // branches but the loop's own)
+            bool listed = false, inter = false;
+            if (T == 1 || j < je) {
                 const typename V4<Real>::T pj = P[j];
                 Real dx = rn_sub(pi.x, pj.x), dy = rn_sub(pi.y, pj.y);
                 Real dz = DIM == 3 ? rn_sub(pi.z, pj.z) : Real(0);
@@ -341,39 +372,47 @@ __device__ __forceinline__ void density_scan_sum(int i, const Group<T>& g, uint3
                     if (DIM == 3) dz = rn_add(dz, sz);
                 }
                 const Real r2 = dist2<Real, DIM>(dx, dy, dz);
-                if (r2 < K.kh2) {
-                    const bool interacting = fluid_i || pj.w > Real(0);
-                    listed = interacting || summation;
-                    npairs += interacting ? 1u : 0u;
-                }
+                const bool hit = (r2 < K.kh2) & ((int)j != i);
+                inter = hit & (fluid_i | (pj.w > Real(0)));
+                listed = summation ? hit : inter;
             }
+            npairs += inter ? 1u : 0u;
             if (T == 1) {
-                if (listed) {
-                    if (k < (uint32_t)maxn) nl[(size_t)k * n + i] = j;
-                    ++k;
-                }
+                if (listed & (k < (uint32_t)maxn)) nl[(size_t)k * n + i] = j;
+                k += listed ? 1u : 0u;
             } else {
                 const unsigned m = g.ballot(listed);
-                if (listed) {
-                    const uint32_t pos = k + __popc(m & below);
-                    if (pos < (uint32_t)maxn) nl[(size_t)pos * n + i] = j;
-                }
+                const uint32_t pos = k + __popc(m & below);
+                if (listed & (pos < (uint32_t)maxn)) nl[(size_t)pos * n + i] = j;
                 k += __popc(m);
             }
         }
     };
     using yes = std::true_type;
     using no = std::false_type;
+    uint32_t nfull = 0;  // candidates of the full stencil, self included
     if (G.run_shift) {
-        for_each_run_shift<Real, DIM>(G, K, off, cx, cy, cz, [&](uint32_t jb, uint32_t je, Real sx, Real sy, Real sz) {
+        // distances to the lower faces of the own cell (FP64, then FP32 with a margin)
+        float e[3] = {0.f, 0.f, 0.f}, cs[3] = {1.f, 1.f, 1.f};
+        const int cc[3] = {cx, cy, cz};
+        const double xs[3] = {(double)pi.x, (double)pi.y, (double)pi.z};
+        for (int d = 0; d < DIM; ++d) {
+            e[d] = (float)((xs[d] - G.lo[d]) - (double)cc[d] * G.cs[d]);
+            cs[d] = (float)G.cs[d];
+        }
+        const float reach2 = (float)K.kh2 * 1.002f;
+        for_each_clipped_run<Real, DIM>(G, K, off, cx, cy, cz, e, cs, reach2, nfull,
+                                        [&](uint32_t jb, uint32_t je, Real sx, Real sy, Real sz) {
             if (sx == Real(0) && sy == Real(0) && sz == Real(0)) scan(jb, je, sx, sy, sz, no(), no());
             else scan(jb, je, sx, sy, sz, yes(), no());
         });
     } else {
         for_each_run<DIM>(G, off, cx, cy, cz, [&](uint32_t jb, uint32_t je) {
+            nfull += je - jb;
             scan(jb, je, Real(0), Real(0), Real(0), no(), yes());
         });
     }
+    if (g.t == 0) ncand = nfull - 1u;  // the destination itself is in its own cell
     if (k > (uint32_t)maxn) {
         dc.overflow = 1;
         k = maxn;
