@@ -426,7 +426,7 @@ __device__ __forceinline__ void density_scan_sum(int i, const Group<T>& g, uint3
         const typename V4<Real>::T pj = P[j];
         Real dx, dy, dz;
         const Real r2 = separation<Real, DIM>(pi, pj, G, K, dx, dy, dz);
-        const Real q = sqrt(r2) * K.inv_h;
+        const Real q = PairMath<Real>::sqrt(r2) * K.inv_h;
         if (summation) {
             sum.add(fabs(pj.w) * K.wfac * kernel_w<Real, KERNEL>(q));
         } else {
@@ -587,26 +587,28 @@ __device__ __forceinline__ void momentum_sums(int i, const Group<T>& g,
         const Real r2 = separation<Real, DIM>(pi, pj, G, K, dx, dy, dz);
         const typename V4<Real>::T qj = Q[j];
         const Real mj = fabs(pj.w);
-        const Real q = sqrt(r2) * K.inv_h;
+        const Real q = PairMath<Real>::sqrt(r2) * K.inv_h;
         const Real Gk = K.gfac * kernel_f<Real, KERNEL>(q);  // grad_i W = Gk (x_i - x_j)
         const Real vx = qi.x - qj.x, vy = qi.y - qj.y, vz = DIM == 3 ? qi.z - qj.z : Real(0);
         Real coef = pri + R[j];
-        const Real rhobar = Real(0.5) * (qi.w + qj.w);
+        const Real inv_rhobar = PairMath<Real>::rcp(Real(0.5) * (qi.w + qj.w));
         if (flags & F_AV) {
             const Real vdotr = vx * dx + vy * dy + (DIM == 3 ? vz * dz : Real(0));
             if (vdotr < Real(0)) {
-                const Real mu = K.h * vdotr / (r2 + K.av_h2);
-                coef -= K.alpha_c0 * mu / rhobar;
+                const Real mu = K.h * vdotr * PairMath<Real>::rcp(r2 + K.av_h2);
+                coef -= K.alpha_c0 * mu * inv_rhobar;
             }
         }
         const Real cg = -mj * coef * Gk;
         Real cv = Real(0);
-        if (flags & F_LAMINAR) cv = mj * K.nu4 / (qi.w + qj.w) * Gk * r2 / (r2 + K.eta_h2);
+        // 4 nu m_j / (rho_i + rho_j) = 2 nu m_j / rhobar
+        if (flags & F_LAMINAR)
+            cv = mj * (Real(0.5) * K.nu4) * inv_rhobar * Gk * r2 * PairMath<Real>::rcp(r2 + K.eta_h2);
         acc[0].add(cg * dx + cv * vx);
         acc[1].add(cg * dy + cv * vy);
         if (DIM == 3) acc[2].add(cg * dz + cv * vz);
         if ((flags & F_XSPH) && pj.w > Real(0)) {
-            const Real fx = K.xsph * mj / rhobar * (K.wfac * kernel_w<Real, KERNEL>(q));
+            const Real fx = K.xsph * mj * inv_rhobar * (K.wfac * kernel_w<Real, KERNEL>(q));
             acc[3].add(-fx * vx);
             acc[4].add(-fx * vy);
             if (DIM == 3) acc[5].add(-fx * vz);
