@@ -117,11 +117,10 @@ __device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(
 // is the same IEEE value on any machine.
 template <class Real>
 __device__ __forceinline__ Real min_image(Real d, int periodic, Real L, Real halfL) {
-    if (periodic) {
-        if (d > halfL) d = rn_sub(d, L);
-        else if (d < -halfL) d = rn_add(d, L);
-    }
-    return d;
+    const Real up = rn_sub(d, L), dn = rn_add(d, L);  // selected, not branched on
+    Real r = (periodic && d > halfL) ? up : d;
+    r = (periodic && d < -halfL) ? dn : r;
+    return r;
 }
 
 // r^2 = ((dx dx) + dy dy) + dz dz, each operation rounded separately.
@@ -197,18 +196,26 @@ struct PairMath<double> {
 template <class Real, int KERNEL>
 __device__ __forceinline__ Real kernel_f(Real q) {
     if (KERNEL == QUINTIC) {
-        if (q < Real(1)) {
-            return (Real(-50) * q + Real(120)) * q * q - Real(120);
+        if (sizeof(Real) == 8) {  // FP64: the divide is costly, keep it off the inner branch
+            if (q < Real(1)) return (Real(-50) * q + Real(120)) * q * q - Real(120);
+            Real t3 = Real(3) - q;
+            Real t3s = t3 * t3;
+            Real p = Real(-5) * t3s * t3s;
+            Real t2 = q < Real(2) ? Real(2) - q : Real(0);
+            Real t2s = t2 * t2;
+            p += Real(30) * t2s * t2s;
+            return PairMath<Real>::div(p, q);
         }
+        // FP32: both branches evaluated and one selected (neighbours of a warp spread over q)
+        const Real inner = (Real(-50) * q + Real(120)) * q * q - Real(120);
         Real t3 = Real(3) - q;
         Real t3s = t3 * t3;
         Real p = Real(-5) * t3s * t3s;
-        if (q < Real(2)) {
-            Real t2 = Real(2) - q;
-            Real t2s = t2 * t2;
-            p += Real(30) * t2s * t2s;
-        }
-        return PairMath<Real>::div(p, q);
+        Real t2 = q < Real(2) ? Real(2) - q : Real(0);
+        Real t2s = t2 * t2;
+        p += Real(30) * t2s * t2s;
+        const Real outer = PairMath<Real>::div(p, q);
+        return q < Real(1) ? inner : outer;
     } else {
         Real t = Real(1) - Real(0.5) * q;
         return Real(-5) * t * t * t;
@@ -218,19 +225,17 @@ __device__ __forceinline__ Real kernel_f(Real q) {
 template <class Real, int KERNEL>
 __device__ __forceinline__ Real kernel_w(Real q) {
     if (KERNEL == QUINTIC) {
+        // the terms (2 - q)^5 and (1 - q)^5 vanish outside their intervals: clamped, not
+        // branched on
         Real t3 = Real(3) - q;
         Real t3s = t3 * t3;
         Real w = t3s * t3s * t3;
-        if (q < Real(2)) {
-            Real t2 = Real(2) - q;
-            Real t2s = t2 * t2;
-            w -= Real(6) * t2s * t2s * t2;
-            if (q < Real(1)) {
-                Real t1 = Real(1) - q;
-                Real t1s = t1 * t1;
-                w += Real(15) * t1s * t1s * t1;
-            }
-        }
+        Real t2 = q < Real(2) ? Real(2) - q : Real(0);
+        Real t2s = t2 * t2;
+        w -= Real(6) * t2s * t2s * t2;
+        Real t1 = q < Real(1) ? Real(1) - q : Real(0);
+        Real t1s = t1 * t1;
+        w += Real(15) * t1s * t1s * t1;
         return w;
     } else {
         Real t = Real(1) - Real(0.5) * q;
