@@ -35,17 +35,92 @@ SM_MAX_MHZ = 2070.0
 
 
 def workload(name: str):
+    """The workload, or for the batched configuration the list of its instances."""
     import workloads as W
     table = {
         "dam_break_2d": lambda: W.dam_break_2d(),
         "taylor_green_2d": lambda: W.taylor_green_2d(),
         "taylor_green_3d": lambda: W.taylor_green_3d(),
         "dam_break_3d": lambda: W.dam_break_3d(),
+        "batch_tg2d": lambda: W.batch_tg2d(),
     }
     return table[name]()
 
 
+class BatchView:
+    """The attributes of a batch that the reporting reads from a single workload."""
+
+    def __init__(self, wls):
+        w0 = wls[0]
+        self.instances = wls
+        self.name = f"batch_tg2d_{len(wls)}"
+        self.dim, self.kernel, self.precision = w0.dim, w0.kernel, w0.precision
+        self.density, self.alpha, self.xsph_eps, self.nu = w0.density, w0.alpha, w0.xsph_eps, w0.nu
+        self.h, self.dt = w0.h, w0.dt
+        self.n_total = sum(w.n_total for w in wls)
+        self.n_fluid = sum(w.n_fluid for w in wls)
+
+
+class Runner:
+    """One problem (Simulation) or a batch of them (BatchSimulation) behind the same calls."""
+
+    def __init__(self, G, wl):
+        self.G = G
+        self.batch = isinstance(wl, list)
+        if self.batch:
+            self.sim = G.BatchSimulation(wl)
+            self.sch = [G.scheme_of(w) for w in wl]
+            self.dts = [w.dt for w in wl]
+        else:
+            self.sim = G.Simulation.from_workload(wl)
+            self.sch = G.scheme_of(wl)
+            self.dt = wl.dt
+        self.stream = self.sim.stream
+        self.n = self.sim.n
+
+    def step(self, k):
+        if self.batch:
+            self.sim.step_batch(self.sch, self.dts, k)
+        else:
+            self.sim.step(self.sch, self.dt, k)
+
+    def step_async(self, k):
+        if self.batch:
+            self.sim.step_batch_async(self.sch, self.dts, k)
+        else:
+            self.sim.step_async(self.sch, self.dt, k)
+
+    def counts(self):
+        """Interacting pairs, candidates and wall-destination pairs of the last step."""
+        if self.batch:
+            d = self.sim.batch_diagnostics()
+            return float(d[:, 8].sum()), float(d[:, 9].sum()), float(d[:, 12].sum())
+        d = self.sim.diagnostics()
+        return float(d[8]), float(d[9]), float(d[12])
+
+    def autotune(self):
+        return self.sim.autotune(None if self.batch else self.sch)
+
+    def kernels_per_step(self):
+        return self.sim.kernels_per_step(self.sch[0] if self.batch else self.sch)
+
+    def __getattr__(self, name):  # set_step_mode, tuning, set_timing, phase_times, ...
+        return getattr(self.sim, name)
+
+
 def describe(wl) -> dict:
+    if isinstance(wl, BatchView):
+        ns = [w.n_total for w in wl.instances]
+        return {
+            "workload": f"{wl.name}: {len(ns)} independent 2D Taylor-Green instances of "
+                        f"{min(ns):,}-{max(ns):,} particles ({wl.n_total:,} in all), quintic "
+                        f"h=dx, Re in [50, 1000], FP32 pair loops / FP64 integrator, one "
+                        f"batched step for all instances, neighbour rebuild every step",
+            "particles": wl.n_total,
+            "fluid_particles": wl.n_fluid,
+            "l2": "no flush: the working set (~500 MB) exceeds L2",
+            "parallelism": "replicas (one independent batch per GPU)",
+        }
     kern = "quintic spline" if wl.kernel == 0 else "Wendland C2"
     prec = "FP32 pair loops / FP64 integrator" if wl.precision == 1 else "FP64"
     return {
@@ -91,16 +166,20 @@ def pass_flops(wl) -> dict:
 
 
 # ------------------------------------------------------------ ncu traffic
+PAIR_KERNEL_SOURCES = ("sph_device.cuh", "sph_launch.h", "step_impl.cuh", "reduce_impl.cuh",
+                       "pairs_impl.cuh", "pairs_f32.cu", "pairs_f64.cu")
+
+
 def source_hash() -> str:
-    """Hash of the CUDA sources; ncu figures taken from another tree are not reported."""
+    """Hash of the pair kernels' sources; ncu figures taken from other kernels are not
+    reported."""
     import hashlib
     d = os.path.join(ROOT, "paper_1909_04504_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(f.encode())
-            with open(os.path.join(d, f), "rb") as fh:
-                h.update(fh.read())
+    for f in PAIR_KERNEL_SOURCES:
+        h.update(f.encode())
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -114,7 +193,10 @@ def measured_traffic(workload_name: str, kernel: str, lanes: int):
     except (OSError, ValueError):
         return None
     entry = t.get(workload_name)
-    if t.get("source_hash") != source_hash() or not entry or entry.get("lanes") != lanes:
+    if t.get("source_hash") != source_hash() or not entry:
+        return None
+    key = "density_lanes" if kernel == "k_density" else "lanes"
+    if entry.get(key, entry.get("lanes")) != lanes:
         return None
     return entry.get(kernel)
 
@@ -172,18 +254,20 @@ def gpu_arm(args, rank, world, dist):
     import paper_1909_04504_gb300 as G
 
     dev = torch.cuda.current_device()
-    wl = workload(args.workload)
-    sch = G.scheme_of(wl)
-    sim = G.Simulation.from_workload(wl)
+    raw = workload(args.workload)
+    wl = BatchView(raw) if isinstance(raw, list) else raw
+    sim = Runner(G, raw)
+    sch = sim.sch
     stream = sim.stream
-    sim.step(sch, wl.dt, args.warmup)
+    sim.step(args.warmup)
     if args.step_mode == "auto":
-        sim.autotune(sch)  # tile shape and step form (graph of phases / persistent launch)
+        sim.autotune()  # tile shape and step form (graph of phases / persistent launch)
     else:
         sim.set_step_mode(G.STEP_PERSISTENT if args.step_mode == "persistent" else G.STEP_GRAPH)
-    sim_lanes, sim_mode = sim.tuning()
+    sim_lanes, sim_mode, density_lanes = sim.tuning()
     mode = "persistent" if sim_mode == G.STEP_PERSISTENT else "graph"
-    sim.step(sch, wl.dt, 3)
+    sim.step(3)
+    flush_each = not sim.batch  # a batch's working set exceeds L2
     flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.int32, device=dev)
     e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -201,15 +285,15 @@ def gpu_arm(args, rank, world, dist):
     t_wall0 = time.perf_counter()
     # ---- timed region: K steps, L2 flushed before each, CUDA events on the step stream
     for k in range(args.steps):
-        with torch.cuda.stream(stream):
-            flush.zero_()
+        if flush_each:
+            with torch.cuda.stream(stream):
+                flush.zero_()
         e0[k].record(stream)
-        sim.step_async(sch, wl.dt, 1)
+        sim.step_async(1)
         e1[k].record(stream)
-        dg = sim.diagnostics()  # waits for the step (outside the events)
-        counts[0] += dg[8]
-        counts[1] += dg[9]
-        counts[2] += dg[12]
+        dg = sim.counts()  # waits for the step (outside the events)
+        for q in range(3):
+            counts[q] += dg[q]
     sim.synchronize()
     torch.cuda.synchronize()
     if dist:
@@ -222,16 +306,16 @@ def gpu_arm(args, rank, world, dist):
     pcounts = [0.0, 0.0, 0.0]
     psteps_n = min(args.steps, 200)
     for k in range(psteps_n):
-        with torch.cuda.stream(stream):
-            flush.zero_()
-        sim.step_async(sch, wl.dt, 1)
+        if flush_each:
+            with torch.cuda.stream(stream):
+                flush.zero_()
+        sim.step_async(1)
         ph = sim.phase_times()  # waits for the step
         for key in phases:
             phases[key] += ph[key]
-        dg = sim.diagnostics()
-        pcounts[0] += dg[8]
-        pcounts[1] += dg[9]
-        pcounts[2] += dg[12]
+        dg = sim.counts()
+        for q in range(3):
+            pcounts[q] += dg[q]
     sim.set_timing(False)
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in zip(e0, e1)]
@@ -269,7 +353,8 @@ def gpu_arm(args, rank, world, dist):
              "momentum": "k_momentum (pressure, AV/viscosity, XSPH, corrector kick, reductions)"}
     roofline = {"bound": "alu", "achieved": per_pass[dom]["achieved_tflops"],
                 "peak": round(peak, 3), "unit": "TFLOP/s", "frac": per_pass[dom]["frac"],
-                "traffic": measured_traffic(args.workload, "k_" + dom, sim_lanes),
+                "traffic": measured_traffic(args.workload, "k_" + dom,
+                                            sim_lanes if dom == "momentum" else density_lanes),
                 "kernel": names[dom],
                 "flops_per_launch": flops[dom], "avg_launch_ms": per_pass[dom]["avg_launch_ms"],
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
@@ -284,13 +369,13 @@ def gpu_arm(args, rank, world, dist):
     e2e_steps = min(args.steps, 200)
     sim.set_timing(False)
     sim.load_state(pinned)
-    sim.step(sch, wl.dt, 1)  # re-capture without timing events
+    sim.step(1)  # re-capture without timing events
     tt = time.perf_counter()
     e2e_pairs = 0.0
     for _ in range(e2e_steps):
         sim.load_state(pinned)
-        sim.step(sch, wl.dt, 1)
-        e2e_pairs += sim.diagnostics()[8]
+        sim.step(1)
+        e2e_pairs += sim.counts()[0]
     e2e_s = time.perf_counter() - tt
     e2e = {"value": world * e2e_pairs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": len(blob),
            "d2h_bytes_per_step": 8 * G.DIAG_COUNT,
@@ -298,7 +383,7 @@ def gpu_arm(args, rank, world, dist):
 
     # ---- FP64 mode of the same workload (the metric compares FP32 with FP64)
     fp64 = None
-    if wl.precision == 1 and args.fp64_steps > 0:
+    if wl.precision == 1 and args.fp64_steps > 0 and not sim.batch:
         sim64 = G.Simulation.from_workload(wl.with_precision(0))
         sim64.step(sch, wl.dt, args.warmup)
         if args.step_mode == "auto":
@@ -325,16 +410,17 @@ def gpu_arm(args, rank, world, dist):
         sim64.close()
 
     state0 = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not sim.batch:
         state0 = one_step_states(wl, sch)
-    launches = sim.kernels_per_step(sch) * args.steps
+    launches = sim.kernels_per_step() * args.steps
     sim.close()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if wl.precision == 1 else "f64", "data": "synthetic",
-        "config": dict(describe(wl), step_mode=mode, momentum_lanes=sim_lanes),
+        "config": dict(describe(wl), step_mode=mode, momentum_lanes=sim_lanes,
+                       density_lanes=density_lanes),
         "particle_steps_per_s": psteps, "candidates_per_s": world * cand / (total_ms / 1e3),
         "pairs_per_step": pairs / args.steps, "phase_ms": phase_avg,
         "roofline": roofline, "e2e": e2e, "fp64_mode": fp64,
@@ -355,11 +441,32 @@ def one_step_states(wl, sch):
 
 
 # ---------------------------------------------------------------- oracle legs
+def oracle_batch_sample(wls, target_s: float):
+    """The oracle on the instances of a batch in order, 2 steps each, until target_s."""
+    import oracle as O
+    O.build()
+    pairs, el, used = 0.0, 0.0, 0
+    for w in wls:
+        t0 = time.perf_counter()
+        _, h = O.run(w, O.state_of(w), w.dt, 2)
+        el += time.perf_counter() - t0
+        pairs += float(h[:, 8].sum())
+        used += 1
+        if el > target_s:
+            break
+    sample = (f"2 steps (+1 initial evaluation) of each of the first {used} of {len(wls)} "
+              f"instances, {el:.1f} s")
+    return pairs / el, el, sample, O.threads()
+
+
 def cpu_baseline(wl, target_s: float, states=None) -> dict:
     """The oracle as it stands, timed on the host cores on a bounded sample of the workload."""
     import numpy as np
 
     import oracle as O
+    if isinstance(wl, BatchView):
+        v, _, sample, cores = oracle_batch_sample(wl.instances, target_s)
+        return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
     O.build()
     s = O.state_of(wl)
     t0 = time.perf_counter()
@@ -396,6 +503,18 @@ def reference_arm(args):
     """Times the oracle on the host cores in the base contract's reference slot."""
     import oracle as O
     wl = workload(args.workload)
+    if isinstance(wl, list):
+        v, el, sample, cores = oracle_batch_sample(wl, 150.0)
+        return {
+            "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": describe(BatchView(wl)),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        }
     O.build()
     s = O.state_of(wl)
     t0 = time.perf_counter()
@@ -430,7 +549,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="dam_break_2d",
-                    choices=["dam_break_2d", "taylor_green_2d", "taylor_green_3d", "dam_break_3d"])
+                    choices=["dam_break_2d", "taylor_green_2d", "taylor_green_3d", "dam_break_3d",
+                             "batch_tg2d"])
     ap.add_argument("--flush-mb", type=int, default=512)
     ap.add_argument("--fp64-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -224,8 +224,10 @@ sph_status sph_set_groups(sph_ctx* ctx, int32_t momentum_lanes);
 enum { SPH_STEP_GRAPH = 0, SPH_STEP_PERSISTENT = 1 };
 sph_status sph_set_step_mode(sph_ctx* ctx, int32_t mode);
 
-/* Current tuning: momentum-pass lanes per destination and step mode (either may be NULL). */
-sph_status sph_get_tuning(const sph_ctx* ctx, int32_t* momentum_lanes, int32_t* mode);
+/* Current tuning: momentum-pass lanes per destination, step mode and density-pass lanes per
+ * destination (any may be NULL). */
+sph_status sph_get_tuning(const sph_ctx* ctx, int32_t* momentum_lanes, int32_t* mode,
+                          int32_t* density_lanes);
 
 /* Time limit of one device-side wait (a grid barrier of the persistent step), in ns;
  * default 1 s; 0 lets no block wait (a persistent step of more than one block then fails
@@ -234,14 +236,15 @@ sph_status sph_get_tuning(const sph_ctx* ctx, int32_t* momentum_lanes, int32_t* 
  * (sph_load_state / sph_set) before stepping on. */
 sph_status sph_set_wait_limit(sph_ctx* ctx, uint64_t ns);
 
-/* Autotuner: times whole evaluations (density + momentum pass) for every tile shape on
- * the current state (they act like sph_eval_rhs) and keeps the fastest; then times a few
- * steps in each step mode from the same state, keeps the faster mode and puts the state,
- * time and records back bitwise. Caches the choice for this (precision, dim, kernel,
- * log2 n) for contexts created later in the process and returns the lanes in *chosen (may
- * be NULL). Contexts start from a cached choice, else 4 lanes below 200,000 particles and
- * 1 above, in graph mode. Timing-dependent: call it explicitly, not inside a run whose
- * bitwise reproducibility matters. A batch needs one sph_step_batch call first. */
+/* Autotuner: times each pair pass for every tile shape on the current state (the passes
+ * act like sph_eval_rhs) and keeps the fastest shape per pass; then times a few steps in
+ * each step mode from the same state, keeps the faster mode and puts the state, time and
+ * records back bitwise. Caches the choice for this (precision, dim, kernel, log2 n) for
+ * contexts created later in the process and returns the momentum-pass lanes in *chosen
+ * (may be NULL). Contexts start from a cached choice, else 4 lanes below 200,000 particles
+ * and 1 above, in graph mode. The persistent step uses the momentum-pass shape for both
+ * passes. Timing-dependent: call it explicitly, not inside a run whose bitwise
+ * reproducibility matters. A batch needs one sph_step_batch call first. */
 sph_status sph_autotune(sph_ctx* ctx, const sph_scheme* scheme, int32_t* chosen);
 
 /* Kernel launches one step issues (for launch accounting). */
@@ -288,6 +291,11 @@ sph_status sph_create_batch(const sph_domain* domains, const sph_array_desc* arr
  * return SPH_ERR_STATE on a batch; sph_get, sph_set, sph_set_groups, sph_autotune (scheme
  * ignored, after a first sph_step_batch), sph_set_timing and sph_phase_times work. */
 sph_status sph_step_batch(sph_ctx* ctx, const sph_scheme* schemes, const double* dt, int32_t nsteps);
+
+/* As sph_step_batch without waiting for the steps (errors raised on the device are
+ * reported by the next sph_synchronize). */
+sph_status sph_step_batch_async(sph_ctx* ctx, const sph_scheme* schemes, const double* dt,
+                                int32_t nsteps);
 
 /* Diagnostics record (SPH_DIAG_COUNT doubles) of every instance after its last evaluation,
  * instance-major, into out (n_instances * SPH_DIAG_COUNT doubles, host). */

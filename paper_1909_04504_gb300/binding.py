@@ -63,6 +63,7 @@ EXPORTS = ("sph_create", "sph_destroy", "sph_last_error", "sph_count", "sph_grid
            "sph_get_tuning",
            "sph_autotune", "sph_backward", "sph_get", "sph_set", "sph_diagnostics", "sph_history",
            "sph_save_state", "sph_load_state", "sph_create_batch", "sph_step_batch",
+           "sph_step_batch_async",
            "sph_batch_diagnostics")
 
 
@@ -105,12 +106,13 @@ def load(build_if_missing: bool = True):
     L.sph_set_groups.argtypes = [ctxp, C.c_int32]
     L.sph_set_step_mode.argtypes = [ctxp, C.c_int32]
     L.sph_set_wait_limit.argtypes = [ctxp, C.c_uint64]
-    L.sph_get_tuning.argtypes = [ctxp, i32, i32]
+    L.sph_get_tuning.argtypes = [ctxp, i32, i32, i32]
     L.sph_backward.argtypes = [ctxp, C.POINTER(Scheme), C.c_double, C.c_int32, C.c_int32, d, d, d]
     L.sph_autotune.argtypes = [ctxp, C.POINTER(Scheme), i32]
     L.sph_create_batch.argtypes = [C.POINTER(Domain), C.POINTER(ArrayDesc), i32, C.c_int32, P,
                                    ALLOC_FN, FREE_FN, P, C.POINTER(ctxp)]
     L.sph_step_batch.argtypes = [ctxp, C.POINTER(Scheme), d, C.c_int32]
+    L.sph_step_batch_async.argtypes = [ctxp, C.POINTER(Scheme), d, C.c_int32]
     L.sph_batch_diagnostics.argtypes = [ctxp, d]
     L.sph_get.argtypes = [ctxp, C.c_int32, C.c_char_p, d]
     L.sph_set.argtypes = [ctxp, C.c_int32, C.c_char_p, d]
@@ -342,10 +344,10 @@ class Simulation:
         self._check(self._L.sph_set_step_mode(self._ctx, int(mode)))
 
     def tuning(self) -> tuple:
-        """(momentum lanes per destination, step mode)."""
-        lanes, mode = C.c_int32(), C.c_int32()
-        self._check(self._L.sph_get_tuning(self._ctx, C.byref(lanes), C.byref(mode)))
-        return int(lanes.value), int(mode.value)
+        """(momentum lanes per destination, step mode, density lanes per destination)."""
+        lanes, mode, dl = C.c_int32(), C.c_int32(), C.c_int32()
+        self._check(self._L.sph_get_tuning(self._ctx, C.byref(lanes), C.byref(mode), C.byref(dl)))
+        return int(lanes.value), int(mode.value), int(dl.value)
 
     def step_mode(self) -> int:
         return self.tuning()[1]
@@ -472,6 +474,11 @@ class BatchSimulation(Simulation):
         arr = (Scheme * self.ninst)(*schemes)
         d = np.ascontiguousarray(dts, dtype=np.float64)
         self._check(self._L.sph_step_batch(self._ctx, arr, _dptr(d), int(nsteps)))
+
+    def step_batch_async(self, schemes: Sequence[Scheme], dts: Sequence[float], nsteps: int = 1):
+        arr = (Scheme * self.ninst)(*schemes)
+        d = np.ascontiguousarray(dts, dtype=np.float64)
+        self._check(self._L.sph_step_batch_async(self._ctx, arr, _dptr(d), int(nsteps)))
 
     def batch_diagnostics(self) -> np.ndarray:
         out = np.zeros((self.ninst, DIAG_COUNT))

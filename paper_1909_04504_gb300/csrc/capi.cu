@@ -93,6 +93,7 @@ struct sph_ctx {
     int fused_bps[4] = {0, 0, 0, 0};  // persistent kernel: blocks per SM for T = 1, 2, 4, 8
     double* fpart = nullptr;          // persistent kernel: per-block partials
     uint32_t* sort_work = nullptr;    // one-sweep sort: histograms, counters, look-back words
+    double* bpart = nullptr;          // batch: partial diagnostics per instance
     unsigned long long wait_ns = 1000000000ull;  // limit of one device-side wait
     bool last_fused = false;          // the last step ran as one persistent launch
     cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -295,8 +296,9 @@ struct TuneKey {
 };
 std::mutex g_tune_lock;
 struct TuneVal {
-    int lanes;  // momentum-pass lanes per destination
-    int mode;   // SPH_STEP_GRAPH or SPH_STEP_PERSISTENT
+    int lanes;   // momentum-pass lanes per destination
+    int mode;    // SPH_STEP_GRAPH or SPH_STEP_PERSISTENT
+    int dlanes;  // density-pass lanes per destination
 };
 std::vector<std::pair<TuneKey, TuneVal>> g_tune_cache;
 
@@ -308,7 +310,7 @@ TuneKey tune_key(const sph_ctx* c) {
 
 // Tuning before any autotune call: a cached result for this shape, else 4 momentum lanes
 // below 200,000 particles and 1 above, and the per-phase graph.
-void default_tuning(const sph_ctx* c, int* tm, int* mode) {
+void default_tuning(const sph_ctx* c, int* td, int* tm, int* mode) {
     *mode = SPH_STEP_GRAPH;
     {
         std::lock_guard<std::mutex> lock(g_tune_lock);
@@ -316,17 +318,19 @@ void default_tuning(const sph_ctx* c, int* tm, int* mode) {
         for (auto& e : g_tune_cache)
             if (e.first == k) {
                 *tm = e.second.lanes;
+                *td = e.second.dlanes;
                 *mode = e.second.mode;
                 return;
             }
     }
     *tm = c->N < 200000 ? 4 : 1;
+    *td = *tm;
 }
 
 void remember_tuning(const sph_ctx* c) {
     std::lock_guard<std::mutex> lock(g_tune_lock);
     const TuneKey k = tune_key(c);
-    const TuneVal v{c->group_m, c->step_mode};
+    const TuneVal v{c->group_m, c->step_mode, c->group_d};
     for (auto& e : g_tune_cache)
         if (e.first == k) {
             e.second = v;
@@ -373,6 +377,7 @@ StepLaunch step_launch(sph_ctx* c, int kick) {
     L.nl = c->nl;
     L.cnt = c->cnt;
     L.pcount = c->pcount;
+    L.bpart = c->bpart;
     L.pm = c->pm;
     L.pd = c->pd;
     L.history = c->history;
@@ -815,9 +820,9 @@ sph_status create_impl(const sph_domain* domains, int ninst, const sph_array_des
     for (int k = 0; k < 4; ++k)
         c->fused_bps[k] = fused_max_blocks_per_sm(domain->precision, domain->dim, domain->kernel, 1 << k);
     {
-        int tm = 1, mode = SPH_STEP_GRAPH;
-        default_tuning(c, &tm, &mode);
-        set_groups(c, tm, tm);
+        int td = 1, tm = 1, mode = SPH_STEP_GRAPH;
+        default_tuning(c, &td, &tm, &mode);
+        set_groups(c, td, tm);
         c->step_mode = mode;
     }
 
@@ -842,7 +847,7 @@ sph_status create_impl(const sph_domain* domains, int ninst, const sph_array_des
     const size_t inst_bytes = domain->precision == SPH_PREC_FP32 ? sizeof(Inst<float>) : sizeof(Inst<double>);
     const size_t nt = ninst > 0 ? (size_t)ninst : 1;
     bytes += al(nt * inst_bytes) + 2 * al((nt + 1) * 4);        // instance table, bounds
-    if (ninst > 0) bytes += 2 * al(nt * 8) + al(nt * DIAG_N * 8) + al(N * 8);
+    if (ninst > 0) bytes += 2 * al(nt * 8) + al(nt * DIAG_N * 8) + al(N * 8) + al(nt * BATCH_SPLIT * 10 * 8);
     c->arena_bytes = bytes;
     if (alloc) c->arena = alloc(bytes, alloc_user);
     else if (cudaMalloc(&c->arena, bytes) != cudaSuccess) c->arena = nullptr;
@@ -889,6 +894,7 @@ sph_status create_impl(const sph_domain* domains, int ninst, const sph_array_des
         c->it = (double*)arena_take(p, (size_t)ninst * 8);
         c->irec = (double*)arena_take(p, (size_t)ninst * DIAG_N * 8);
         c->pcount = (uint32_t*)arena_take(p, N * 8);
+        c->bpart = (double*)arena_take(p, nt * BATCH_SPLIT * 10 * 8);
     }
 
     // ---- upload
@@ -1034,7 +1040,12 @@ sph_status batch_initial_eval(sph_ctx* c) {
 
 extern "C" {
 
-sph_status sph_step_batch(sph_ctx* c, const sph_scheme* schemes, const double* dt, int32_t nsteps) {
+}  // extern "C"
+
+namespace {
+
+sph_status step_batch_impl(sph_ctx* c, const sph_scheme* schemes, const double* dt, int32_t nsteps,
+                           bool sync) {
     if (!c) return fail(c, SPH_ERR_INVALID, "ctx is NULL");
     if (c->ninst == 0) return fail(c, SPH_ERR_STATE, "not a batch context");
     if (!schemes || !dt || nsteps < 0) return fail(c, SPH_ERR_INVALID, "bad arguments");
@@ -1057,19 +1068,31 @@ sph_status sph_step_batch(sph_ctx* c, const sph_scheme* schemes, const double* d
     }
     c->hist_at_call = c->steps_total;
     if (!c->have_rates) {
+        // the initial evaluation's reduction sets every instance's next dt (the fixed dt of
+        // the table, or the CFL-type criteria)
         sph_status s = batch_initial_eval(c);
         if (s != SPH_OK) return s;
     }
-    for (int k = 0; k < c->ninst; ++k)
-        if (dt[k] > 0.0)
-            CK(cudaMemcpyAsync(&c->idt[k], &dt[k], sizeof(double), cudaMemcpyHostToDevice, c->stream));
     if (nsteps > 0) {
         sph_status s = run_steps(c, nsteps);
         if (s != SPH_OK) return s;
         c->steps_total += (unsigned)nsteps;
         if (c->timing) c->timed_step_ran = true;
     }
-    return sync_status(c);
+    return sync ? sync_status(c) : SPH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sph_status sph_step_batch(sph_ctx* c, const sph_scheme* schemes, const double* dt, int32_t nsteps) {
+    return step_batch_impl(c, schemes, dt, nsteps, true);
+}
+
+sph_status sph_step_batch_async(sph_ctx* c, const sph_scheme* schemes, const double* dt,
+                                int32_t nsteps) {
+    return step_batch_impl(c, schemes, dt, nsteps, false);
 }
 
 sph_status sph_batch_diagnostics(sph_ctx* c, double* out) {
@@ -1294,8 +1317,8 @@ sph_status sph_kernels_per_step(const sph_ctx* ctx, const sph_scheme* scheme, in
     // drift+keys, 3 per radix pass, reorder, cell table, density pass, momentum pass
     // (+ the per-instance reduction of a batch)
     // graph: keys + histograms, one launch per radix pass, reorder + cell table, density
-    // pass, momentum pass (+ the per-instance reduction of a batch)
-    *count = c->step_mode == SPH_STEP_PERSISTENT ? 1 : 1 + c->passes + 1 + 1 + 1 + (c->ninst ? 1 : 0);
+    // pass, momentum pass (+ the two-stage per-instance reduction of a batch)
+    *count = c->step_mode == SPH_STEP_PERSISTENT ? 1 : 1 + c->passes + 1 + 1 + 1 + (c->ninst ? 2 : 0);
     return SPH_OK;
 }
 
@@ -1346,6 +1369,55 @@ cudaError_t snap_copy(sph_ctx* c, const DevSnap& sn, bool restore) {
         cp(c->irec, (size_t)c->ninst * DIAG_N * 8);
     }
     return e;
+}
+
+// Lanes per destination of each pair pass, timed pass by pass at the current state (the
+// passes run without a kick: they act like an evaluation). The density pass of the chosen
+// shape then leaves the lists the momentum pass is timed on.
+sph_status tune_lanes(sph_ctx* c) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int reps = 5;
+    auto time_it = [&](int pass, float* ms) -> cudaError_t {
+        const StepLaunch L = step_launch(c, 0);
+        for (int r = 0; r <= reps; ++r) {
+            if (r == 1) cudaEventRecord(e0, c->stream);
+            if (pass == 0) launch_density_pass(L, c->stream);
+            else launch_momentum_pass(L, c->stream);
+        }
+        cudaEventRecord(e1, c->stream);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+        return e;
+    };
+    int best[2] = {c->group_d, c->group_m};
+    cudaError_t e = cudaSuccess;
+    for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
+        float best_ms = 1e30f;
+        for (int T = 1; T <= 8 && e == cudaSuccess; T *= 2) {
+            if (pass == 0) set_groups(c, T, c->group_m);
+            else set_groups(c, best[0], T);
+            float ms = 0.f;
+            e = time_it(pass, &ms);
+            if (e == cudaSuccess && ms < best_ms) {
+                best_ms = ms;
+                best[pass] = T;
+            }
+        }
+        set_groups(c, best[0], pass == 0 ? c->group_m : best[1]);
+        if (pass == 0 && e == cudaSuccess) {  // lists of the chosen density shape
+            launch_density_pass(step_launch(c, 0), c->stream);
+            e = cudaGetLastError();
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(c, e, "autotune of the tile shapes");
+    set_groups(c, best[0], best[1]);
+    drop_graphs(c);
+    return SPH_OK;
 }
 
 // Times a few steps in each mode from the same state and keeps the faster mode; the
@@ -1422,10 +1494,12 @@ sph_status sph_set_step_mode(sph_ctx* c, int32_t mode) {
     return SPH_OK;
 }
 
-sph_status sph_get_tuning(const sph_ctx* c, int32_t* momentum_lanes, int32_t* mode) {
+sph_status sph_get_tuning(const sph_ctx* c, int32_t* momentum_lanes, int32_t* mode,
+                          int32_t* density_lanes) {
     if (!c) return fail(nullptr, SPH_ERR_INVALID, "ctx is NULL");
     if (momentum_lanes) *momentum_lanes = c->group_m;
     if (mode) *mode = c->step_mode;
+    if (density_lanes) *density_lanes = c->group_d;
     return SPH_OK;
 }
 
@@ -1437,42 +1511,19 @@ sph_status sph_set_wait_limit(sph_ctx* c, uint64_t ns) {
 
 sph_status sph_autotune(sph_ctx* c, const sph_scheme* scheme, int32_t* chosen) {
     if (!c) return fail(c, SPH_ERR_INVALID, "ctx is NULL");
-    if (c->ninst) {  // batch: time whole evaluations of all instances per tile shape
+    if (c->ninst) {  // batch: the passes over all instances
         if ((int)c->batch_schemes.size() != c->ninst)
             return fail(c, SPH_ERR_STATE, "call sph_step_batch once before tuning a batch");
         sph_status s = batch_initial_eval(c);
         if (s != SPH_OK) return s;
-        cudaEvent_t e0, e1;
-        CK(cudaEventCreate(&e0));
-        CK(cudaEventCreate(&e1));
-        int best = c->group_m;
-        float best_ms = 1e30f;
-        for (int T = 1; T <= 8; T *= 2) {
-            set_groups(c, T, T);
-            for (int r = 0; r <= 5; ++r) {
-                if (r == 1) CK(cudaEventRecord(e0, c->stream));
-                enqueue_eval(c, 0);
-            }
-            CK(cudaEventRecord(e1, c->stream));
-            CK(cudaEventSynchronize(e1));
-            CK(cudaGetLastError());
-            float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, e0, e1));
-            if (ms < best_ms) {
-                best_ms = ms;
-                best = T;
-            }
-        }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        set_groups(c, best, best);
-        drop_graphs(c);
+        s = tune_lanes(c);
+        if (s != SPH_OK) return s;
         s = sync_status(c);
         if (s != SPH_OK) return s;
         s = choose_mode(c);
         if (s != SPH_OK) return s;
         drop_graphs(c);
-        if (chosen) *chosen = best;
+        if (chosen) *chosen = c->group_m;
         return sync_status(c);
     }
     sph_status s = check_scheme(c, scheme);
@@ -1481,32 +1532,8 @@ sph_status sph_autotune(sph_ctx* c, const sph_scheme* scheme, int32_t* chosen) {
     if (s != SPH_OK) return s;
     s = sync_status(c);
     if (s != SPH_OK) return s;
-    cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
-    int best = c->group_m;
-    float best_ms = 1e30f;
-    const int reps = 5;
-    for (int T = 1; T <= 8; T *= 2) {  // whole evaluations (density + momentum pass)
-        set_groups(c, T, T);
-        for (int r = 0; r <= reps; ++r) {
-            if (r == 1) CK(cudaEventRecord(e0, c->stream));
-            enqueue_eval(c, 0);
-        }
-        CK(cudaEventRecord(e1, c->stream));
-        CK(cudaEventSynchronize(e1));
-        CK(cudaGetLastError());
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = T;
-        }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    set_groups(c, best, best);
-    drop_graphs(c);
+    s = tune_lanes(c);
+    if (s != SPH_OK) return s;
     s = initial_eval(c, scheme, 0.0);  // rates and diagnostics of the chosen shape
     if (s != SPH_OK) return s;
     s = sync_status(c);
@@ -1515,7 +1542,7 @@ sph_status sph_autotune(sph_ctx* c, const sph_scheme* scheme, int32_t* chosen) {
     if (s != SPH_OK) return s;
     drop_graphs(c);
     remember_tuning(c);
-    if (chosen) *chosen = best;
+    if (chosen) *chosen = c->group_m;
     return sync_status(c);
 }
 

@@ -54,18 +54,14 @@ __device__ __forceinline__ void finish_single(Control* ctl, double* __restrict__
     __threadfence();
 }
 
-// Batch instance `inst` (one block of NT threads, red: NT/32 x 10 doubles of shared
-// memory): FP64 diagnostics of its segment in a fixed order, its record, time, next dt.
-template <class Real, int NT>
-__device__ __forceinline__ void batch_reduce_inst(const ParticleSet& S,
-                                                  const uint32_t* __restrict__ pcount,
-                                                  const uint32_t* __restrict__ off,
-                                                  const Inst<Real>& I, int inst, int dim,
-                                                  double* __restrict__ idt, double* __restrict__ it,
-                                                  double* __restrict__ irec, int kick, Control* ctl,
-                                                  double (*red)[10]) {
-    const uint32_t b = off[I.cell_base], e = off[I.cell_base_end];
-    double v[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};  // px py pz ke u2 a2 bad pairs cand wall
+// FP64 diagnostics of the particles [b, e) of the cell order (one block of NT threads,
+// red: NT/32 x 10 doubles of shared memory), in a fixed order; valid in thread 0:
+// px py pz ke max|u|^2 max|a|^2 bad pairs candidates wall-pairs.
+template <int NT>
+__device__ __forceinline__ void batch_partial(const ParticleSet& S,
+                                              const uint32_t* __restrict__ pcount, uint32_t b,
+                                              uint32_t e, int dim, double* o, double (*red)[10]) {
+    double v[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (uint32_t k = b + threadIdx.x; k < e; k += NT) {
         const bool fluid = !(S.tag[k] & WALL_BIT);
         const double np = (double)pcount[2 * (size_t)k], nc = (double)pcount[2 * (size_t)k + 1];
@@ -91,41 +87,62 @@ __device__ __forceinline__ void batch_reduce_inst(const ParticleSet& S,
         v[4] = fmax(v[4], u2);
         v[5] = fmax(v[5], a2);
     }
-    for (int o = 16; o > 0; o >>= 1)
+    for (int o2 = 16; o2 > 0; o2 >>= 1)
         for (int q = 0; q < 10; ++q) {
-            const double y = __shfl_down_sync(0xffffffffu, v[q], o);
+            const double y = __shfl_down_sync(0xffffffffu, v[q], o2);
             v[q] = (q >= 4 && q <= 6) ? fmax(v[q], y) : v[q] + y;
         }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0)
         for (int q = 0; q < 10; ++q) red[warp][q] = v[q];
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double o[10];
+    if (threadIdx.x == 0)
         for (int q = 0; q < 10; ++q) {
             double t = red[0][q];
             for (int w = 1; w < NT / 32; ++w) t = (q >= 4 && q <= 6) ? fmax(t, red[w][q]) : t + red[w][q];
             o[q] = t;
         }
-        const double dt = idt[inst];
-        if (kick) it[inst] += dt;
-        double* rec = irec + (size_t)inst * DIAG_N;
-        rec[0] = it[inst];
-        rec[1] = kick ? dt : 0.0;
-        rec[2] = o[3];
-        rec[3] = sqrt(o[4]);
-        rec[4] = o[0];
-        rec[5] = o[1];
-        rec[6] = o[2];
-        rec[7] = sqrt(o[5]);
-        rec[8] = o[7];
-        rec[9] = o[8];
-        rec[10] = rec[10] + (kick ? 1.0 : 0.0);
-        rec[11] = 0.0;
-        rec[12] = o[9];
-        if (o[6] != 0.0) atomicOr(&ctl->status, ST_NONFINITE);
-        idt[inst] = next_dt(I.C, rec[3], rec[7]);
-    }
+    __syncthreads();
+}
+
+// Record, time and next dt of batch instance `inst` from its reduced diagnostics o[10]
+// (one thread).
+template <class Real>
+__device__ __forceinline__ void batch_finish_inst(const Inst<Real>& I, int inst, const double* o,
+                                                  double* __restrict__ idt, double* __restrict__ it,
+                                                  double* __restrict__ irec, int kick, Control* ctl) {
+    const double dt = idt[inst];
+    if (kick) it[inst] += dt;
+    double* rec = irec + (size_t)inst * DIAG_N;
+    rec[0] = it[inst];
+    rec[1] = kick ? dt : 0.0;
+    rec[2] = o[3];
+    rec[3] = sqrt(o[4]);
+    rec[4] = o[0];
+    rec[5] = o[1];
+    rec[6] = o[2];
+    rec[7] = sqrt(o[5]);
+    rec[8] = o[7];
+    rec[9] = o[8];
+    rec[10] = rec[10] + (kick ? 1.0 : 0.0);
+    rec[11] = 0.0;
+    rec[12] = o[9];
+    if (o[6] != 0.0) atomicOr(&ctl->status, ST_NONFINITE);
+    idt[inst] = next_dt(I.C, rec[3], rec[7]);
+}
+
+// Batch instance `inst` in one block (the persistent step): its whole segment.
+template <class Real, int NT>
+__device__ __forceinline__ void batch_reduce_inst(const ParticleSet& S,
+                                                  const uint32_t* __restrict__ pcount,
+                                                  const uint32_t* __restrict__ off,
+                                                  const Inst<Real>& I, int inst, int dim,
+                                                  double* __restrict__ idt, double* __restrict__ it,
+                                                  double* __restrict__ irec, int kick, Control* ctl,
+                                                  double (*red)[10]) {
+    double o[10];
+    batch_partial<NT>(S, pcount, off[I.cell_base], off[I.cell_base_end], dim, o, red);
+    if (threadIdx.x == 0) batch_finish_inst<Real>(I, inst, o, idt, it, irec, kick, ctl);
     __syncthreads();
 }
 

@@ -65,6 +65,7 @@ struct StepLaunch {
     uint32_t* nl;                 // neighbour list, nl[k * n + i], k < maxn
     uint32_t* cnt;                // list length per particle
     uint32_t* pcount;             // batch: interacting pairs and candidates per particle
+    double* bpart;                // batch: BATCH_SPLIT x 10 partial diagnostics per instance
     double* pm;                   // single: 8 doubles per momentum block
     double* pd;                   // single: 4 doubles per density block
     double* history;
@@ -84,6 +85,7 @@ int pair_threads();
 void launch_pairs(const StepLaunch& L, cudaStream_t st);
 void launch_density_pass(const StepLaunch& L, cudaStream_t st);
 void launch_momentum_pass(const StepLaunch& L, cudaStream_t st);
+constexpr int BATCH_SPLIT = 32;  // blocks per instance in the first stage of a batch reduction
 void launch_batch_reduce(const StepLaunch& L, cudaStream_t st);
 // fused_f32.cu / fused_f64.cu: the whole step as one cooperative launch (persistent blocks,
 // grid barriers between the phases).
