@@ -15,6 +15,7 @@
 #include "sph.h"
 #include "sph_device.cuh"
 #include "sph_launch.h"
+#include "sort_impl.cuh"
 
 using namespace sph;
 
@@ -443,7 +444,7 @@ FusedLaunch fused_launch(sph_ctx* c) {
     F.off = c->off;
     F.part = c->fpart;
     F.passes = c->passes;
-    F.ntiles = radix_tiles(c->N);
+    F.ntiles = onesweep_tiles(c->N);
     F.ncells = c->G.ncells;
     F.wait_ns = c->wait_ns;
     return F;

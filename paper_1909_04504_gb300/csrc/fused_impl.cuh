@@ -128,10 +128,16 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_step_fused(const FusedLaun
             __syncthreads();
             const int t = tile_s;
             if (t >= F.ntiles) break;
-            radix_onesweep_tile(F.keys[cur], p ? F.vals[cur] : nullptr, F.keys[cur ^ 1],
-                                F.vals[cur ^ 1], L.n, 8 * p, ghist + p * RADIX,
-                                status + (size_t)p * F.ntiles * RADIX, t, sm.os, &ctl->status,
-                                F.wait_ns);
+            if (onesweep_items(L.n) == 4)
+                radix_onesweep_tile<4>(F.keys[cur], p ? F.vals[cur] : nullptr, F.keys[cur ^ 1],
+                                       F.vals[cur ^ 1], L.n, 8 * p, ghist + p * RADIX,
+                                       status + (size_t)p * F.ntiles * RADIX, t, sm.os,
+                                       &ctl->status, F.wait_ns);
+            else
+                radix_onesweep_tile<16>(F.keys[cur], p ? F.vals[cur] : nullptr, F.keys[cur ^ 1],
+                                        F.vals[cur ^ 1], L.n, 8 * p, ghist + p * RADIX,
+                                        status + (size_t)p * F.ntiles * RADIX, t, sm.os,
+                                        &ctl->status, F.wait_ns);
             __syncthreads();
         }
         if (!grid_sync(ctl, F.wait_ns)) return;
@@ -146,7 +152,8 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_step_fused(const FusedLaun
         const int inst = find_instance(L.cell_bounds, L.ninst, skeys[k]);
         reorder_one<Real>(L.Sin, L.S, k, (int)perm[k], L.dim, L.idt[inst], 1, 0, P, Q);
     }
-    for (int c = tid; c <= F.ncells; c += nthreads) F.off[c] = cell_offset(skeys, L.n, (uint32_t)c);
+    for (int c = tid; c <= F.ncells; c += nthreads)
+        F.off[c] = cell_offset_near(skeys, L.n, (uint32_t)c, F.off[c]);
     if (!grid_sync(ctl, F.wait_ns)) return;
     if (stamp) ctl->stamp[3] = global_ns();
 

@@ -69,6 +69,7 @@ k_keys_hist(ParticleSet S, int n, const Inst<Real>* __restrict__ tab,
 }
 
 // One radix pass in one launch (decoupled look-back); one tile per block.
+template <int ITEMS>
 __global__ void __launch_bounds__(SORT_THREADS)
 k_radix_onesweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                  uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int n, int shift,
@@ -78,8 +79,8 @@ k_radix_onesweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restric
     if (ctl->status) return;
     if (threadIdx.x == 0) sm.tile = (int)atomicAdd(counter, 1u);
     __syncthreads();
-    radix_onesweep_tile(keys_in, vals_in, keys_out, vals_out, n, shift, ghist, status, sm.tile, sm,
-                        &ctl->status, wait_ns);
+    radix_onesweep_tile<ITEMS>(keys_in, vals_in, keys_out, vals_out, n, shift, ghist, status,
+                               sm.tile, sm, &ctl->status, wait_ns);
 }
 
 // -------------------------------------------------------------- radix sort
@@ -138,7 +139,7 @@ __global__ void k_reorder(ParticleSet in, ParticleSet out, const uint32_t* __res
             const int inst = find_instance(cell_bounds, ninst, skeys[k]);
             reorder_one<Real>(in, out, k, (int)perm[k], dim, idt[inst], kick, carry_rates, P, Q);
         }
-        if (k <= ncells) off[k] = cell_offset(skeys, n, (uint32_t)k);  // the cell table
+        if (k <= ncells) off[k] = cell_offset_near(skeys, n, (uint32_t)k, off[k]);  // cell table
     }
 }
 
@@ -339,7 +340,7 @@ void launch_reorder(const StepLaunch& L, const uint32_t* perm, int carry_rates, 
 }
 
 size_t sort_work_words(int n, int passes) {
-    return (size_t)4 * RADIX + 32 + (size_t)passes * radix_tiles(n) * RADIX;
+    return (size_t)4 * RADIX + 32 + (size_t)passes * onesweep_tiles(n) * RADIX;
 }
 
 // Zeroes the sort workspace, then drift + keys + the digit histograms of all passes.
@@ -359,15 +360,20 @@ void launch_keys_hist(const StepLaunch& L, int drift, uint32_t* keys0, int passe
 // 1) holding the sorted keys and the permutation.
 int launch_onesweep(int n, uint32_t* keys[2], uint32_t* vals[2], int passes, uint32_t* work,
                     Control* ctl, unsigned long long wait_ns, cudaStream_t st) {
-    const int ntiles = radix_tiles(n);
+    const int ntiles = onesweep_tiles(n);
     uint32_t* ghist = work;
     uint32_t* counters = work + 4 * RADIX;
     uint32_t* status = counters + 32;
     int cur = 0;
     for (int p = 0; p < passes; ++p) {
-        k_radix_onesweep<<<ntiles, SORT_THREADS, 0, st>>>(
-            keys[cur], p == 0 ? nullptr : vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, 8 * p,
-            ghist + p * RADIX, status + (size_t)p * ntiles * RADIX, counters + p, ctl, wait_ns);
+        if (onesweep_items(n) == 4)
+            k_radix_onesweep<4><<<ntiles, SORT_THREADS, 0, st>>>(
+                keys[cur], p == 0 ? nullptr : vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, 8 * p,
+                ghist + p * RADIX, status + (size_t)p * ntiles * RADIX, counters + p, ctl, wait_ns);
+        else
+            k_radix_onesweep<16><<<ntiles, SORT_THREADS, 0, st>>>(
+                keys[cur], p == 0 ? nullptr : vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, 8 * p,
+                ghist + p * RADIX, status + (size_t)p * ntiles * RADIX, counters + p, ctl, wait_ns);
         cur ^= 1;
     }
     return cur;

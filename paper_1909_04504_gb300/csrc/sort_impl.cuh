@@ -163,9 +163,20 @@ __device__ __forceinline__ unsigned long long sort_clock_ns() {
     return t;
 }
 
-// One tile of a one-sweep pass (SORT_THREADS threads). ghist: the RADIX digit counts of
-// this pass over all keys; status: ntiles x RADIX look-back words, zero before the pass.
-// A look-back wait longer than wait_ns raises ST_TIMEOUT and the tile writes nothing.
+// Keys per thread of a one-sweep tile: small problems take short tiles (more blocks,
+// shorter serial ranking loops), large ones long tiles (fewer look-back steps).
+__host__ __device__ __forceinline__ int onesweep_items(int n) { return n <= 131072 ? 4 : 16; }
+__host__ __device__ __forceinline__ int onesweep_tiles(int n) {
+    const int tile = SORT_THREADS * onesweep_items(n);
+    const int t = (n + tile - 1) / tile;
+    return t < 1 ? 1 : t;
+}
+
+// One tile of a one-sweep pass (SORT_THREADS threads, ITEMS keys each). ghist: the RADIX
+// digit counts of this pass over all keys; status: ntiles x RADIX look-back words, zero
+// before the pass. A look-back wait longer than wait_ns raises ST_TIMEOUT and the tile
+// writes nothing.
+template <int ITEMS>
 __device__ __forceinline__ void radix_onesweep_tile(const uint32_t* __restrict__ keys_in,
                                                     const uint32_t* __restrict__ vals_in,
                                                     uint32_t* __restrict__ keys_out,
@@ -177,11 +188,12 @@ __device__ __forceinline__ void radix_onesweep_tile(const uint32_t* __restrict__
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int w = 0; w < SORT_WARPS; ++w) sm.wcnt[w][tid] = 0;
     __syncthreads();
-    const int wbase = tile * SORT_TILE + warp * (SORT_TILE / SORT_WARPS);
-    uint32_t kr[SORT_ITEMS], vr[SORT_ITEMS], rank[SORT_ITEMS];
+    constexpr int TILE = SORT_THREADS * ITEMS;
+    const int wbase = tile * TILE + warp * (TILE / SORT_WARPS);
+    uint32_t kr[ITEMS], vr[ITEMS], rank[ITEMS];
     const unsigned ltmask = lanemask_lt();
 #pragma unroll
-    for (int it = 0; it < SORT_ITEMS; ++it) {
+    for (int it = 0; it < ITEMS; ++it) {
         const int idx = wbase + it * 32 + lane;
         const bool valid = idx < n;
         const uint32_t key = valid ? keys_in[idx] : 0u;
@@ -243,7 +255,7 @@ __device__ __forceinline__ void radix_onesweep_tile(const uint32_t* __restrict__
     }
     if (!__syncthreads_and(ok)) return;
 #pragma unroll
-    for (int it = 0; it < SORT_ITEMS; ++it) {
+    for (int it = 0; it < ITEMS; ++it) {
         const int idx = wbase + it * 32 + lane;
         if (idx < n) {
             const uint32_t d = (kr[it] >> shift) & (RADIX - 1);
@@ -266,6 +278,40 @@ __device__ __forceinline__ void digit_hist_add(uint32_t key, bool valid, int pas
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         if (valid && (peers & lm) == 0u) atomicAdd(&h[p][d], (uint32_t)__popc(peers));
     }
+}
+
+// The same lower bound found by an exponential search from a guess (the cell's offset
+// at the previous build: particles move less than a cell per step, so it is a few places
+// off): O(log distance) dependent loads instead of O(log n).
+__device__ __forceinline__ uint32_t cell_offset_near(const uint32_t* __restrict__ skeys, int n,
+                                                     uint32_t c, uint32_t guess) {
+    int lo, hi;  // the answer lies in [lo, hi]
+    int g = guess > (uint32_t)n ? n : (int)guess;
+    if (g < n && skeys[g] < c) {  // answer > g: gallop right
+        int step = 1;
+        lo = g + 1;
+        hi = g + 1;
+        while (hi < n && skeys[hi] < c) {
+            lo = hi + 1;
+            step <<= 1;
+            hi = g + step < n ? g + step : n;
+        }
+    } else {  // answer <= g: gallop left
+        int step = 1;
+        hi = g;
+        lo = g;
+        while (lo > 0 && skeys[lo - 1] >= c) {
+            hi = lo - 1;
+            step <<= 1;
+            lo = g - step > 0 ? g - step : 0;
+        }
+    }
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (skeys[mid] < c) lo = mid + 1;
+        else hi = mid;
+    }
+    return (uint32_t)lo;
 }
 
 // Cell table entry: number of sorted keys < c (lower bound), for c in [0, ncells].
