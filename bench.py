@@ -246,6 +246,20 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ------------------------------------------------------------ whole-job totals
+def job_totals(dist, total_ms: float, units: float, device="cpu"):
+    """The whole job's view of one timed region: the slowest rank's time and the units all
+    ranks processed (each rank runs its own replica: weak scaling, no data-path collective)."""
+    if dist is None:
+        return total_ms, units
+    import torch
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 # ------------------------------------------------------------------ GPU arm
 def gpu_arm(args, rank, world, dist):
     import numpy as np
@@ -322,12 +336,11 @@ def gpu_arm(args, rank, world, dist):
     total_ms = sum(step_ms)
     pairs, cand, wall_pairs = counts
     n = sim.n
-    if dist:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * pairs / (total_ms / 1e3)
-    psteps = world * n * args.steps / (total_ms / 1e3)
+    total_ms, job_pairs = job_totals(dist, total_ms, pairs, device=dev)
+    _, job_cand = job_totals(dist, total_ms, cand, device=dev)
+    _, job_psteps = job_totals(dist, total_ms, float(n) * args.steps, device=dev)
+    value = job_pairs / (total_ms / 1e3)
+    psteps = job_psteps / (total_ms / 1e3)
 
     # ---- roofline of the dominant kernel (the longer pair pass), algorithmic flops over
     # its live duration (CUDA events recorded on the launching stream inside the graph)
@@ -377,7 +390,8 @@ def gpu_arm(args, rank, world, dist):
         sim.step(1)
         e2e_pairs += sim.counts()[0]
     e2e_s = time.perf_counter() - tt
-    e2e = {"value": world * e2e_pairs / e2e_s, "unit": UNIT, "h2d_bytes_per_step": len(blob),
+    e2e_ms, e2e_job_pairs = job_totals(dist, e2e_s * 1e3, e2e_pairs, device=dev)
+    e2e = {"value": e2e_job_pairs / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": len(blob),
            "d2h_bytes_per_step": 8 * G.DIAG_COUNT,
            "path": "sph_load_state(pinned host state) + sph_step + sph_diagnostics per step"}
 
@@ -403,10 +417,11 @@ def gpu_arm(args, rank, world, dist):
             p64 += sim64.diagnostics()[8]
         torch.cuda.synchronize()
         ms64 = sum(a.elapsed_time(b) for a, b in zip(f0, f1))
+        ms64, p64 = job_totals(dist, ms64, p64, device=dev)
         v64 = p64 / (ms64 / 1e3)
-        fp64 = {"value": world * v64, "unit": UNIT, "steps": args.fp64_steps,
+        fp64 = {"value": v64, "unit": UNIT, "steps": args.fp64_steps,
                 "ms_per_step": ms64 / args.fp64_steps,
-                "fp32_speedup": round(value / (world * v64), 3)}
+                "fp32_speedup": round(value / v64, 3)}
         sim64.close()
 
     state0 = None
@@ -421,7 +436,7 @@ def gpu_arm(args, rank, world, dist):
         "dtype": "f32" if wl.precision == 1 else "f64", "data": "synthetic",
         "config": dict(describe(wl), step_mode=mode, momentum_lanes=sim_lanes,
                        density_lanes=density_lanes),
-        "particle_steps_per_s": psteps, "candidates_per_s": world * cand / (total_ms / 1e3),
+        "particle_steps_per_s": psteps, "candidates_per_s": job_cand / (total_ms / 1e3),
         "pairs_per_step": pairs / args.steps, "phase_ms": phase_avg,
         "roofline": roofline, "e2e": e2e, "fp64_mode": fp64,
         "gpu_launches": launches, "clocks": clocks, "wall_s": round(t_wall, 3),
@@ -504,7 +519,7 @@ def reference_arm(args):
     import oracle as O
     wl = workload(args.workload)
     if isinstance(wl, list):
-        v, el, sample, cores = oracle_batch_sample(wl, 150.0)
+        v, el, sample, cores = oracle_batch_sample(wl, args.ref_seconds)
         return {
             "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -522,7 +537,7 @@ def reference_arm(args):
     warm_s = time.perf_counter() - t0
     per_step = warm_s / (max(1, args.warmup) + 1)
     steps = args.steps
-    cap = max(1, int(150.0 / max(per_step, 1e-6)))
+    cap = max(1, int(args.ref_seconds / max(per_step, 1e-6)))
     sample_steps = min(steps, cap)
     t0 = time.perf_counter()
     st, h = O.run(wl, st, wl.dt, sample_steps)
@@ -555,6 +570,8 @@ def main():
     ap.add_argument("--fp64-steps", type=int, default=200)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-seconds", type=float, default=150.0,
+                    help="reference arm: seconds of oracle time in the timed sample")
     ap.add_argument("--step-mode", default="auto", choices=["auto", "graph", "persistent"],
                     help="auto: the autotuner picks the tile shape and the step form")
     args = ap.parse_args()
