@@ -24,8 +24,9 @@
  *  - Wendland C2: (1-q/2)^4 (2q+1), support 2h, sigma_2D = 7/(4 pi), sigma_3D = 21/(16 pi);
  *  - neighbour predicate: i != j and r^2 < (k h)^2 with r^2 = ((dx dx) + dy dy) + dz dz,
  *    minimum image dx -= L if dx > L/2, dx += L if dx < -L/2, in the mode's precision;
- *  - cell grid: n_d = floor(ext_d / (k h * 1.00001)), cs_d = ext_d / n_d,
- *    c_d = floor(((double)x_mode - lo_d) / cs_d) clamped to [0, n_d - 1];
+ *  - cell grid: n_d = floor(ext_d / (k h / R * 1.00001)) with R = 1 in 2D and 2 in 3D,
+ *    cs_d = ext_d / n_d, c_d = floor(((double)x_mode - lo_d) / cs_d) clamped to
+ *    [0, n_d - 1], a stencil of (2R + 1)^d cells;
  *  - eta = 0.01 in the laminar viscosity, Monaghan AV with beta = 0 and 0.01 h^2;
  *  - XSPH over fluid sources, entering the drift only;
  *  - predictor-corrector as kick-drift-kick for u and x; the density advanced like the
@@ -144,8 +145,12 @@ void kernel_eval(int kernel, int dim, double h, T r, T* W, T* dWdr) {
 }
 
 /* ------------------------------------------------------------------- grid
- * Sec. 2.2: cells no smaller than the support radius, 3^d stencil.
+ * Sec. 2.2: a uniform cell grid searched with a stencil of (2R + 1)^d cells: R = 1 in 2D
+ * (cells no smaller than the support radius kh, 3 x 3), R = 2 in 3D (cells no smaller than
+ * kh / 2, 5 x 5 x 5). Any pair inside the support lies at most R cells apart per axis.
  */
+int reach_of(int dim) { return dim == 3 ? 2 : 1; }
+
 struct Grid {
     int dim;
     int n[3];
@@ -163,11 +168,12 @@ int make_grid(const ora_params* P, Grid* G) {
         if (d < P->dim) {
             double ext = P->hi[d] - P->lo[d];
             if (!(ext > 0.0) || !(kh > 0.0)) return -1;
-            double nd = std::floor(ext / (kh * 1.00001));
+            const int R = reach_of(P->dim);
+            double nd = std::floor(ext / (kh / R * 1.00001));
             if (nd < 1.0) nd = 1.0;
             if (nd > 1e7) return -1;
             G->n[d] = (int)nd;
-            if (P->periodic[d] && G->n[d] < 3) return -2;
+            if (P->periodic[d] && G->n[d] < 2 * R + 1) return -2;
             G->cs[d] = ext / (double)G->n[d];
             G->lo[d] = P->lo[d];
         } else {
@@ -267,8 +273,9 @@ struct Neighbours {
         }
         const int32_t* ci = &cell3[i * 3];
         int lo3[3], hi3[3];
+        const int R = reach_of(P->dim);
         for (int d = 0; d < 3; ++d) {
-            if (d < P->dim) { lo3[d] = -1; hi3[d] = 1; } else { lo3[d] = 0; hi3[d] = 0; }
+            if (d < P->dim) { lo3[d] = -R; hi3[d] = R; } else { lo3[d] = 0; hi3[d] = 0; }
         }
         for (int oz = lo3[2]; oz <= hi3[2]; ++oz)
             for (int oy = lo3[1]; oy <= hi3[1]; ++oy)
@@ -348,7 +355,7 @@ T tait(const ora_params* P, T rho) {
 
 struct Counts {
     int64_t pairs = 0;       // ordered interacting pairs i != j
-    int64_t candidates = 0;  // ordered (i, j) pairs examined in the 3^d stencil, j != i
+    int64_t candidates = 0;  // ordered (i, j) pairs examined in the (2R + 1)^d stencil, j != i
 };
 
 /* ------------------------------------------------------------- the RHS

@@ -155,19 +155,21 @@ sph_status make_grid(sph_ctx* c, const sph_domain& D, Grid* G) {
         return fail(c, SPH_ERR_INVALID, "unknown precision");
     const double kh = support_factor(D.kernel) * D.h;
     if (!(D.h > 0.0) || !std::isfinite(kh)) return fail(c, SPH_ERR_INVALID, "h must be > 0");
+    // cells of side >= kh / R (R = 1 in 2D, 2 in 3D: the stencil of stencil.cuh)
+    const int R = D.dim == 3 ? 2 : 1;
     G->dim = D.dim;
     double ncells = 1.0;
     for (int d = 0; d < 3; ++d) {
         if (d < D.dim) {
             const double ext = D.hi[d] - D.lo[d];
             if (!(ext > 0.0)) return fail(c, SPH_ERR_INVALID, "empty cell box");
-            double nd = std::floor(ext / (kh * 1.00001));
+            double nd = std::floor(ext / (kh / R * 1.00001));
             if (nd < 1.0) nd = 1.0;
             if (nd > 1e7) return fail(c, SPH_ERR_INVALID, "too many cells");
             G->nc[d] = (int)nd;
             G->periodic[d] = D.periodic[d] ? 1 : 0;
-            if (G->periodic[d] && G->nc[d] < 3)
-                return fail(c, SPH_ERR_INVALID, "a periodic axis needs at least 3 cells");
+            if (G->periodic[d] && G->nc[d] < 2 * R + 1)
+                return fail(c, SPH_ERR_INVALID, "a periodic axis needs at least 2R + 1 cells (3 in 2D, 5 in 3D)");
             G->cs[d] = ext / (double)G->nc[d];
             G->lo_f[d] = (float)D.lo[d];
             G->inv_cs_f[d] = (float)(1.0 / G->cs[d]);
@@ -188,13 +190,14 @@ sph_status make_grid(sph_ctx* c, const sph_domain& D, Grid* G) {
     }
     if (ncells > 2147483000.0) return fail(c, SPH_ERR_INVALID, "too many cells");
     G->ncells = (int)ncells;
-    // With >= 5 cells on every periodic axis a source run of the 3-cell stencil either
-    // lies within 2 cells (|dx| < 0.4 L: the minimum image never applies) or wraps around
-    // the box (|dx| > 0.6 L: it always applies, with the sign of the wrap), so the pair
-    // loops can apply it per run with the same arithmetic.
+    // With >= 2R + 3 cells on every periodic axis a source run of the stencil either lies
+    // within R + 1 cells (|dx| <= (R + 1) L / (2R + 3) < L / 2: the minimum image never
+    // applies) or wraps around the box (|dx| > L - (R + 1) cs > L / 2: it always applies,
+    // with the sign of the wrap), so the pair loops can apply it per run with the same
+    // arithmetic.
     G->run_shift = 1;
     for (int d = 0; d < D.dim; ++d)
-        if (G->periodic[d] && G->nc[d] < 5) G->run_shift = 0;
+        if (G->periodic[d] && G->nc[d] < 2 * R + 3) G->run_shift = 0;
     return SPH_OK;
 }
 

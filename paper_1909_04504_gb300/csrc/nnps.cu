@@ -7,6 +7,7 @@
 #include "sph_launch.h"
 #include "sort_impl.cuh"
 #include "step_impl.cuh"
+#include "stencil.cuh"
 
 namespace sph {
 
@@ -199,61 +200,31 @@ __global__ void k_export_neighbors(const typename V4<Real>::T* __restrict__ P,
                                    const int64_t* __restrict__ row_off, int32_t* __restrict__ idx) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const typename V4<Real>::T pi = P[i];
-        const uint32_t key = skeys[i];
-        const int cx = key % G.nc[0];
-        const int cy = (key / G.nc[0]) % G.nc[1];
-        const int cz = key / (G.nc[0] * G.nc[1]);
+        int cx, cy, cz;
+        cell_of_key(G, skeys[i], cx, cy, cz);
         const uint32_t id = tag[i] & ID_MASK;
         int64_t w = pass ? row_off[id] : 0;
         const int64_t w0 = w;
         uint32_t cnt = 0;
-        for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz) {
-            int z = cz + dz;
-            if (DIM == 3) {
-                if (z < 0 || z >= G.nc[2]) {
-                    if (!G.periodic[2]) continue;
-                    z = (z + G.nc[2]) % G.nc[2];
-                }
+        for_each_run<DIM>(G, off, cx, cy, cz, [&](uint32_t jb, uint32_t je) {
+            for (uint32_t j = jb; j < je; ++j) {
+                if ((int)j == i) continue;
+                const typename V4<Real>::T pj = P[j];
+                const Real dx = min_image(rn_sub(pi.x, pj.x), G.periodic[0], K.L[0], K.halfL[0]);
+                const Real dy = min_image(rn_sub(pi.y, pj.y), G.periodic[1], K.L[1], K.halfL[1]);
+                const Real dzv = DIM == 3 ? min_image(rn_sub(pi.z, pj.z), G.periodic[2], K.L[2], K.halfL[2])
+                                          : Real(0);
+                const Real r2 = dist2<Real, DIM>(dx, dy, dzv);
+                if (!(r2 < K.kh2)) continue;
+                if (pass) idx[w++] = (int32_t)(tag[j] & ID_MASK);
+                ++cnt;
             }
-            for (int dy = -1; dy <= 1; ++dy) {
-                int y = cy + dy;
-                if (y < 0 || y >= G.nc[1]) {
-                    if (!G.periodic[1]) continue;
-                    y = (y + G.nc[1]) % G.nc[1];
-                }
-                const int row = G.nc[0] * (y + G.nc[1] * z);
-                int xr[2][2];
-                int nruns = 0;
-                int x0 = cx - 1, x1 = cx + 1;
-                if (G.periodic[0]) {
-                    if (x0 < 0) { xr[nruns][0] = G.nc[0] - 1; xr[nruns][1] = G.nc[0] - 1; ++nruns; x0 = 0; }
-                    if (x1 >= G.nc[0]) { xr[nruns][0] = 0; xr[nruns][1] = 0; ++nruns; x1 = G.nc[0] - 1; }
-                } else {
-                    if (x0 < 0) x0 = 0;
-                    if (x1 >= G.nc[0]) x1 = G.nc[0] - 1;
-                }
-                xr[nruns][0] = x0; xr[nruns][1] = x1; ++nruns;
-                for (int r = 0; r < nruns; ++r) {
-                    const uint32_t jb = off[row + xr[r][0]], je = off[row + xr[r][1] + 1];
-                    for (uint32_t j = jb; j < je; ++j) {
-                        if ((int)j == i) continue;
-                        const typename V4<Real>::T pj = P[j];
-                        Real dx = min_image(rn_sub(pi.x, pj.x), G.periodic[0], K.L[0], K.halfL[0]);
-                        Real dy = min_image(rn_sub(pi.y, pj.y), G.periodic[1], K.L[1], K.halfL[1]);
-                        Real dzv = DIM == 3 ? min_image(rn_sub(pi.z, pj.z), G.periodic[2], K.L[2], K.halfL[2]) : Real(0);
-                        Real r2 = dist2<Real, DIM>(dx, dy, dzv);
-                        if (!(r2 < K.kh2)) continue;
-                        if (pass) idx[w++] = (int32_t)(tag[j] & ID_MASK);
-                        ++cnt;
-                    }
-                }
-            }
-        }
+        });
         if (!pass) {
             counts[id] = cnt;
         } else {
             for (int64_t a = w0 + 1; a < w; ++a) {  // insertion sort of the row
-                int32_t v = idx[a];
+                const int32_t v = idx[a];
                 int64_t b = a - 1;
                 while (b >= w0 && idx[b] > v) { idx[b + 1] = idx[b]; --b; }
                 idx[b + 1] = v;

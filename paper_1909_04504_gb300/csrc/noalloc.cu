@@ -80,6 +80,7 @@ extern "C" sph_status sph_cell_sort_noalloc(const sph_domain* domain, const doub
     // grid: the rule of sph_create
     const double kh = (D.kernel == SPH_KERNEL_QUINTIC ? 3.0 : 2.0) * D.h;
     if (!(D.h > 0.0) || !std::isfinite(kh)) return fail(SPH_ERR_INVALID, "h must be > 0");
+    const int R = D.dim == 3 ? 2 : 1;
     Grid G{};
     G.dim = D.dim;
     double ncells = 1.0;
@@ -87,13 +88,13 @@ extern "C" sph_status sph_cell_sort_noalloc(const sph_domain* domain, const doub
         if (d < D.dim) {
             const double ext = D.hi[d] - D.lo[d];
             if (!(ext > 0.0)) return fail(SPH_ERR_INVALID, "empty cell box");
-            double nd = std::floor(ext / (kh * 1.00001));
+            double nd = std::floor(ext / (kh / R * 1.00001));
             if (nd < 1.0) nd = 1.0;
             if (nd > 1e7) return fail(SPH_ERR_INVALID, "too many cells");
             G.nc[d] = (int)nd;
             G.periodic[d] = D.periodic[d] ? 1 : 0;
-            if (G.periodic[d] && G.nc[d] < 3)
-                return fail(SPH_ERR_INVALID, "a periodic axis needs at least 3 cells");
+            if (G.periodic[d] && G.nc[d] < 2 * R + 1)
+                return fail(SPH_ERR_INVALID, "a periodic axis needs at least 2R + 1 cells");
             G.cs[d] = ext / (double)G.nc[d];
             G.lo[d] = D.lo[d];
             G.hi[d] = D.hi[d];

@@ -21,43 +21,12 @@
 #include "sph_device.cuh"
 #include "sph_launch.h"
 #include "step_impl.cuh"
+#include "stencil.cuh"
 #include "reduce_impl.cuh"
 
 namespace sph {
 
 constexpr int PAIR_THREADS = 128;
-
-// Walks the stencil of cell (cx, cy, cz): calls body(jb, je) for each contiguous run.
-template <int DIM, class Body>
-__device__ __forceinline__ void for_each_run(const Grid& G, const uint32_t* __restrict__ off,
-                                             int cx, int cy, int cz, Body body) {
-#pragma unroll 1
-    for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz) {
-        int z = cz + dz;
-        if (DIM == 3 && (z < 0 || z >= G.nc[2])) {
-            if (!G.periodic[2]) continue;
-            z = (z + G.nc[2]) % G.nc[2];
-        }
-#pragma unroll 1
-        for (int dy = -1; dy <= 1; ++dy) {
-            int y = cy + dy;
-            if (y < 0 || y >= G.nc[1]) {
-                if (!G.periodic[1]) continue;
-                y = (y + G.nc[1]) % G.nc[1];
-            }
-            const int row = G.nc[0] * (y + G.nc[1] * z);
-            int x0 = cx - 1, x1 = cx + 1;
-            if (G.periodic[0]) {
-                if (x0 < 0) { body(off[row + G.nc[0] - 1], off[row + G.nc[0]]); x0 = 0; }
-                if (x1 >= G.nc[0]) { body(off[row], off[row + 1]); x1 = G.nc[0] - 1; }
-            } else {
-                if (x0 < 0) x0 = 0;
-                if (x1 >= G.nc[0]) x1 = G.nc[0] - 1;
-            }
-            body(off[row + x0], off[row + x1 + 1]);
-        }
-    }
-}
 
 // The stencil walk clipped to the support: a row (dy, dz) whose distance from the
 // destination in (y, z) reaches the support radius is skipped, and in every other row the
@@ -68,70 +37,76 @@ __device__ __forceinline__ void for_each_run(const Grid& G, const uint32_t* __re
 // the destination's distances to the lower faces of its own cell and `c` the cell sizes;
 // `reach2` is the squared support radius widened by a margin far above the FP32 rounding of
 // these distances, so no cell that holds a neighbour is dropped. Returns, in ncand, the
-// candidates of the full 3^d stencil (the count the interaction metric reports).
+// candidates of the full stencil (the count the interaction metric reports).
 template <class Real, int DIM, class Body>
 __device__ __forceinline__ void for_each_clipped_run(const Grid& G, const PairConst<Real>& K,
                                                      const uint32_t* __restrict__ off, int cx, int cy,
                                                      int cz, const float* e, const float* c,
                                                      float reach2, uint32_t& ncand, Body body) {
-    const float ex_lo = e[0], ex_hi = c[0] - e[0];
+    constexpr int R = Stencil<DIM>::R, RZ = Stencil<DIM>::RZ;
+    const int nx = G.nc[0];
 #pragma unroll 1
-    for (int dz = (DIM == 3 ? -1 : 0); dz <= (DIM == 3 ? 1 : 0); ++dz) {
+    for (int dz = -RZ; dz <= RZ; ++dz) {
         int z = cz + dz;
         Real sz = Real(0);
         if (DIM == 3 && (z < 0 || z >= G.nc[2])) {
             if (!G.periodic[2]) continue;
             sz = z < 0 ? K.L[2] : -K.L[2];
-            z = (z + G.nc[2]) % G.nc[2];
+            z = z < 0 ? z + G.nc[2] : z - G.nc[2];
         }
-        const float bz = DIM == 3 ? (dz < 0 ? e[2] : (dz > 0 ? c[2] - e[2] : 0.0f)) : 0.0f;
+        // distance to the nearest face of the layer dz cells away
+        const float bz = DIM == 3 ? (dz < 0 ? e[2] + (float)(-dz - 1) * c[2]
+                                            : (dz > 0 ? (c[2] - e[2]) + (float)(dz - 1) * c[2] : 0.0f))
+                                  : 0.0f;
 #pragma unroll 1
-        for (int dy = -1; dy <= 1; ++dy) {
+        for (int dy = -R; dy <= R; ++dy) {
             int y = cy + dy;
             Real sy = Real(0);
             if (y < 0 || y >= G.nc[1]) {
                 if (!G.periodic[1]) continue;
                 sy = y < 0 ? K.L[1] : -K.L[1];
-                y = (y + G.nc[1]) % G.nc[1];
+                y = y < 0 ? y + G.nc[1] : y - G.nc[1];
             }
-            const float ay = dy < 0 ? e[1] : (dy > 0 ? c[1] - e[1] : 0.0f);
+            const float ay = dy < 0 ? e[1] + (float)(-dy - 1) * c[1]
+                                    : (dy > 0 ? (c[1] - e[1]) + (float)(dy - 1) * c[1] : 0.0f);
             const float w2 = reach2 - (ay * ay + bz * bz);  // <= 0: the row is out of reach
-            const bool row = w2 > 0.0f;
-            const bool need_l = row && ex_lo * ex_lo < w2, need_r = row && ex_hi * ex_hi < w2;
-            const int rowb = G.nc[0] * (y + G.nc[1] * z);
-            int xa = cx - 1, xb = cx + 1;
+            // cells within reach on each side of cx
+            int nl = 0, nr = 0;
+            if (w2 > 0.0f) {
+#pragma unroll
+                for (int k = 1; k <= R; ++k) {
+                    const float dl = e[0] + (float)(k - 1) * c[0], dr = (c[0] - e[0]) + (float)(k - 1) * c[0];
+                    nl += dl * dl < w2 ? 1 : 0;
+                    nr += dr * dr < w2 ? 1 : 0;
+                }
+            }
+            const int rowb = nx * (y + G.nc[1] * z);
+            int xa = cx - R, xb = cx + R;               // full row
+            int t0 = cx - nl, t1 = cx + nr;             // clipped row
             if (G.periodic[0]) {
                 if (xa < 0) {
-                    const uint32_t jb = off[rowb + G.nc[0] - 1], je = off[rowb + G.nc[0]];
-                    ncand += je - jb;
-                    if (need_l) body(jb, je, K.L[0], sy, sz);
+                    ncand += off[rowb + nx] - off[rowb + nx + xa];
+                    if (w2 > 0.0f && t0 < 0) body(off[rowb + nx + t0], off[rowb + nx], K.L[0], sy, sz);
                     xa = 0;
                 }
-                if (xb >= G.nc[0]) {
-                    const uint32_t jb = off[rowb], je = off[rowb + 1];
-                    ncand += je - jb;
-                    if (need_r) body(jb, je, -K.L[0], sy, sz);
-                    xb = G.nc[0] - 1;
+                if (xb >= nx) {
+                    ncand += off[rowb + xb - nx + 1] - off[rowb];
+                    if (w2 > 0.0f && t1 >= nx) body(off[rowb], off[rowb + t1 - nx + 1], -K.L[0], sy, sz);
+                    xb = nx - 1;
                 }
             } else {
                 if (xa < 0) xa = 0;
-                if (xb >= G.nc[0]) xb = G.nc[0] - 1;
+                if (xb >= nx) xb = nx - 1;
             }
             const uint32_t fb = off[rowb + xa], fe = off[rowb + xb + 1];
             ncand += fe - fb;
-            if (!row) continue;
-            const int t0 = max(xa, need_l ? cx - 1 : cx), t1 = min(xb, need_r ? cx + 1 : cx);
+            if (!(w2 > 0.0f)) continue;
+            t0 = max(t0, xa);
+            t1 = min(t1, xb);
             if (t0 > t1) continue;
             body(t0 == xa ? fb : off[rowb + t0], t1 == xb ? fe : off[rowb + t1 + 1], Real(0), sy, sz);
         }
     }
-}
-
-__device__ __forceinline__ void cell_of_key(const Grid& G, uint32_t key, int& cx, int& cy, int& cz) {
-    cx = (int)(key % (uint32_t)G.nc[0]);
-    uint32_t r = key / (uint32_t)G.nc[0];
-    cy = (int)(r % (uint32_t)G.nc[1]);
-    cz = (int)(r / (uint32_t)G.nc[1]);
 }
 
 // The T lanes of one destination inside a warp.
@@ -535,7 +510,7 @@ __device__ __forceinline__ void density_tiles(int block, int nblocks,
 // Density pass kernel. Single problems write block counts to pd; batches per-particle
 // counts to pcount for the per-instance reduction.
 template <class Real, int DIM, int KERNEL, int T>
-__global__ void __launch_bounds__(PAIR_THREADS, 6)
+__global__ void __launch_bounds__(PAIR_THREADS, sizeof(Real) == 4 ? 7 : 6)
 k_density(const typename V4<Real>::T* __restrict__ P, typename V4<Real>::T* __restrict__ Q,
           Real* __restrict__ R, const uint32_t* __restrict__ skeys, const uint32_t* __restrict__ off,
           int n, const Inst<Real>* __restrict__ tab, const uint32_t* __restrict__ cell_bounds,

@@ -257,11 +257,12 @@ def test_cell_sort_many_tiles_bit_exact(prec):
     assert np.array_equal(np.asarray(order, np.int64), np.argsort(ocell, kind="stable"))
 
 
-@pytest.mark.parametrize("dim,n", [(2, 12), (2, 14), (2, 16), (3, 12), (3, 14), (3, 16)])
+@pytest.mark.parametrize("dim,n", [(2, 12), (2, 14), (2, 16), (3, 8), (3, 10), (3, 12), (3, 16)])
 @pytest.mark.parametrize("prec", [G.PREC_FP64, G.PREC_FP32])
 def test_neighbours_small_periodic_grids(dim, n, prec):
-    """3, 4 and 5 cells per periodic axis: the per-pair minimum image (fewer than 5 cells)
-    and the per-run shift (5 or more) give the oracle's neighbour sets after 5 steps."""
+    """Few cells per periodic axis (2D: 3, 4, 5; 3D: 5, 6, 7, 10): the per-pair minimum image
+    (fewer than 2R + 3 cells) and the per-run shift give the oracle's neighbour sets after 5
+    steps."""
     wl = (W.taylor_green_2d if dim == 2 else W.taylor_green_3d)(n=n, precision=prec)
     with sim_of(wl) as sim:
         sim.step(G.scheme_of(wl), wl.dt, 5)
