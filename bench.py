@@ -29,6 +29,8 @@ if ROOT not in sys.path:
 
 METRIC = "neighbour-pair interactions/s and particle-steps/s, FP32 vs FP64 at stated error"
 UNIT = "neighbour-pair interactions/s"
+# steps of the timed adjoint (gradient of the final kinetic energy) per workload
+ADJOINT_STEPS = {"taylor_green_3d": 50, "dam_break_3d": 20}
 FP32_LANES_PER_SM = 128   # FP32 CUDA-core lanes per Blackwell SM (4 sub-partitions x 32)
 SMS = 152
 SM_MAX_MHZ = 2070.0
@@ -184,21 +186,18 @@ def source_hash() -> str:
 
 
 def measured_traffic(workload_name: str, kernel: str, lanes: int):
-    """DRAM bytes (read + write) per launch of `kernel` from the committed ncu summary, or
-    None when the kernels changed since the capture or the capture used another shape."""
+    """DRAM bytes (read + write) per launch of `kernel` at `lanes` lanes per destination
+    from the committed ncu summary, or None when the kernels changed since the capture or
+    no capture used that shape."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             t = json.load(f)
     except (OSError, ValueError):
         return None
-    entry = t.get(workload_name)
-    if t.get("source_hash") != source_hash() or not entry:
+    if t.get("source_hash") != source_hash():
         return None
-    key = "density_lanes" if kernel == "k_density" else "lanes"
-    if entry.get(key, entry.get("lanes")) != lanes:
-        return None
-    return entry.get(kernel)
+    return t.get(workload_name, {}).get(kernel, {}).get(str(lanes))
 
 
 # --------------------------------------------------------------------- clocks
@@ -278,6 +277,8 @@ def gpu_arm(args, rank, world, dist):
         sim.autotune()  # tile shape and step form (graph of phases / persistent launch)
     else:
         sim.set_step_mode(G.STEP_PERSISTENT if args.step_mode == "persistent" else G.STEP_GRAPH)
+    if args.lanes:
+        sim.set_groups(args.lanes)  # both passes (after the autotuner, which it overrides)
     sim_lanes, sim_mode, density_lanes = sim.tuning()
     mode = "persistent" if sim_mode == G.STEP_PERSISTENT else "graph"
     sim.step(3)
@@ -424,6 +425,33 @@ def gpu_arm(args, rank, world, dist):
                 "fp32_speedup": round(value / v64, 3)}
         sim64.close()
 
+    # ---- hand-written adjoint: K steps forward, then the same K steps with the reverse sweep
+    adjoint = None
+    k_adj = args.adjoint_steps if args.adjoint_steps >= 0 else ADJOINT_STEPS.get(args.workload, 0)
+    if k_adj > 0 and not sim.batch and sch.density == G.CONTINUITY:
+        sim.set_timing(False)
+        sim.load_state(pinned)
+        sim.sim.backward(sch, wl.dt, k_adj)  # warm: workspace and graphs
+        sim.load_state(pinned)
+        sim.synchronize()
+        tt = time.perf_counter()
+        sim.step(k_adj)
+        sim.synchronize()
+        fwd_s = time.perf_counter() - tt
+        sim.load_state(pinned)
+        sim.synchronize()
+        tt = time.perf_counter()
+        _, g_nu, _ = sim.sim.backward(sch, wl.dt, k_adj)
+        adj_s = time.perf_counter() - tt
+        fwd_ms, _ = job_totals(dist, fwd_s * 1e3, 0.0, device=dev)
+        adj_ms, _ = job_totals(dist, adj_s * 1e3, 0.0, device=dev)
+        adjoint = {"steps": k_adj, "ckpt_every": math.ceil(math.sqrt(k_adj)),
+                   "forward_ms": round(fwd_ms, 3), "forward_and_adjoint_ms": round(adj_ms, 3),
+                   "ratio": round(adj_ms / fwd_ms, 3), "dKE_dnu": g_nu,
+                   "path": "sph_backward (checkpoint every ckpt_every steps, recompute, taped "
+                           "neighbour lists, reverse sweep) vs sph_step, host clock around the "
+                           "synchronous calls"}
+
     state0 = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not sim.batch:
         state0 = one_step_states(wl, sch)
@@ -438,7 +466,7 @@ def gpu_arm(args, rank, world, dist):
                        density_lanes=density_lanes),
         "particle_steps_per_s": psteps, "candidates_per_s": job_cand / (total_ms / 1e3),
         "pairs_per_step": pairs / args.steps, "phase_ms": phase_avg,
-        "roofline": roofline, "e2e": e2e, "fp64_mode": fp64,
+        "roofline": roofline, "e2e": e2e, "fp64_mode": fp64, "adjoint": adjoint,
         "gpu_launches": launches, "clocks": clocks, "wall_s": round(t_wall, 3),
     }
     return line, state0, wl
@@ -574,6 +602,12 @@ def main():
                     help="reference arm: seconds of oracle time in the timed sample")
     ap.add_argument("--step-mode", default="auto", choices=["auto", "graph", "persistent"],
                     help="auto: the autotuner picks the tile shape and the step form")
+    ap.add_argument("--adjoint-steps", type=int, default=-1,
+                    help="K of the timed adjoint (-1: 50 for taylor_green_3d, 20 for "
+                         "dam_break_3d, none otherwise; 0: off)")
+    ap.add_argument("--lanes", type=int, default=0, choices=[0, 1, 2, 4, 8],
+                    help="lanes per destination of both pair passes (0: the autotuner's or "
+                         "the default shape)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 

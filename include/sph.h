@@ -262,11 +262,13 @@ sph_status sph_kernels_per_step(const sph_ctx* ctx, const sph_scheme* scheme, in
  *             is then switched off).
  * Any output may be NULL. Checkpoint and recompute: the state is saved every ckpt_every
  * steps (<= 0: ceil(sqrt K)); each segment is recomputed once, taping the pair-loop
- * inputs of its steps, and reversed. Pair terms in the pair-loop precision with
- * compensated sums; adjoint state and the scalar gradients in FP64. Continuity
- * formulation only (SPH_ERR_INVALID for summation density), dt > 0 required. Device
- * workspace: about (K / ckpt_every + 1) * 124 + (ckpt_every + 1) * 44 + 300 bytes per
- * particle in FP32 mode, allocated for the call. */
+ * inputs and the neighbour list of its steps, and reversed over the taped lists. Pair
+ * terms in the pair-loop precision with compensated sums; adjoint state and the scalar
+ * gradients in FP64. Continuity formulation only (SPH_ERR_INVALID for summation density),
+ * dt > 0 required. Device workspace: about (K / ckpt_every + 1) * 124 +
+ * (ckpt_every + 1) * (48 + 4 * maxn) + 300 bytes per particle in FP32 mode, maxn being the
+ * neighbour-list capacity (about twice the largest neighbour count), allocated for the
+ * call. */
 sph_status sph_backward(sph_ctx* ctx, const sph_scheme* scheme, double dt, int32_t K,
                         int32_t ckpt_every, double* dKE_du0, double* dKE_dnu, double* dKE_dalpha);
 

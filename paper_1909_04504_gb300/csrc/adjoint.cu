@@ -11,7 +11,8 @@
 //     momentum VJP  -> lambda_x, lambda_uh, lambda_rho' (+ Pr chain), nu-bar, alpha-bar
 //     continuity VJP with cotangent dt (lambda_rho' + momentum part) -> lambda_x, lambda_uh
 //     scatter to O_n and the drift transpose.
-// The pair VJPs are gathers over each particle's neighbour list: a particle collects the
+// The pair VJPs are gathers over each particle's neighbour list (the forward evaluation's,
+// copied to the tape when the step is recomputed): a particle collects the
 // terms where it is the destination (its own cotangents) and where it is the source (the
 // neighbour's cotangents), so no atomics are needed. Pair arithmetic in the pair-loop
 // precision with compensated per-particle sums; adjoint state and scalar gradients in FP64.
@@ -19,54 +20,17 @@
 
 namespace sph {
 
-// ----------------------------------------------------------- list rebuild
-// Cell key of each taped particle from its pair-loop position (the forward's binning).
-template <class Real>
-__global__ void k_adj_keys(const typename V4<Real>::T* __restrict__ P, int n, Grid G,
-                           uint32_t* __restrict__ keys) {
+// ------------------------------------------------------------ taped lists
+// Copy of the forward evaluation's neighbour list (nl[k * n + i], k < cnt[i]) into the
+// tape: the reverse sweep runs over exactly the pairs the forward step summed. Only the
+// filled entries move; for each k the threads of a warp touch consecutive words.
+__global__ void k_tape_list(const uint32_t* __restrict__ nl, const uint32_t* __restrict__ cnt,
+                            int n, uint32_t* __restrict__ tnl, uint32_t* __restrict__ tcnt) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const typename V4<Real>::T p = P[i];
-        const double xs[3] = {(double)p.x, (double)p.y, (double)p.z};
-        int c[3] = {0, 0, 0};
-        int clamped = 0;
-        for (int d = 0; d < G.dim; ++d) c[d] = cell_coord(xs[d], G.lo[d], G.cs[d], G.nc[d], &clamped);
-        keys[i] = (uint32_t)(c[0] + G.nc[0] * (c[1] + G.nc[1] * c[2]));
+        const uint32_t c = cnt[i];
+        tcnt[i] = c;
+        for (uint32_t k = 0; k < c; ++k) tnl[(size_t)k * n + i] = nl[(size_t)k * n + i];
     }
-}
-
-// Neighbour list of the taped configuration with the continuity-mode rule (a fluid
-// destination lists every neighbour, a wall destination its fluid neighbours).
-template <class Real, int DIM>
-__global__ void __launch_bounds__(PAIR_THREADS)
-k_adj_list(const typename V4<Real>::T* __restrict__ P, const uint32_t* __restrict__ skeys,
-           const uint32_t* __restrict__ off, int n, Grid G, PairConst<Real> K,
-           uint32_t* __restrict__ nl, uint32_t* __restrict__ cnt, int maxn, Control* ctl) {
-    int overflow = 0;
-    for (int i = blockIdx.x * PAIR_THREADS + threadIdx.x; i < n; i += gridDim.x * PAIR_THREADS) {
-        const typename V4<Real>::T pi = P[i];
-        const bool fluid_i = pi.w > Real(0);
-        int cx, cy, cz;
-        cell_of_key(G, skeys[i], cx, cy, cz);
-        uint32_t k = 0;
-        for_each_run<DIM>(G, off, cx, cy, cz, [&](uint32_t jb, uint32_t je) {
-            for (uint32_t j = jb; j < je; ++j) {
-                if ((int)j == i) continue;
-                const typename V4<Real>::T pj = P[j];
-                Real dx, dy, dz;
-                const Real r2 = separation<Real, DIM>(pi, pj, G, K, dx, dy, dz);
-                if (r2 < K.kh2 && (fluid_i || pj.w > Real(0))) {
-                    if (k < (uint32_t)maxn) nl[(size_t)k * n + i] = j;
-                    ++k;
-                }
-            }
-        });
-        if (k > (uint32_t)maxn) {
-            overflow = 1;
-            k = maxn;
-        }
-        cnt[i] = k;
-    }
-    if (overflow) atomicOr(&ctl->status, ST_CAPACITY);
 }
 
 // ------------------------------------------------------------- kernel derivative
@@ -463,11 +427,6 @@ static void adj_eval_t(const AdjLaunch& A, const PairConst<Real>& K, cudaStream_
     using V = typename V4<Real>::T;
     const int g256 = grid_of(A.n, 256, A.sms * 8);
     const int gp = grid_of(A.n, PAIR_THREADS, A.sms * 16);
-    // list of the taped configuration
-    k_adj_keys<Real><<<g256, 256, 0, st>>>((const V*)A.P, A.n, A.G, A.keys);
-    launch_cell_offsets(A.keys, A.n, A.G.ncells, A.off, A.ctl, st, A.sms);
-    k_adj_list<Real, DIM><<<gp, PAIR_THREADS, 0, st>>>((const V*)A.P, A.keys, A.off, A.n, A.G, K,
-                                                       A.nl, A.cnt, A.maxn, A.ctl);
     k_adj_cot<Real><<<g256, 256, 0, st>>>(A.L, (const V*)A.P, A.n, A.dt, A.kick, (V*)A.CA,
                                           (V*)A.CS, A.luh[0], A.luh[1], A.luh[2], DIM);
     k_adj_momentum<Real, DIM, KERNEL><<<gp, PAIR_THREADS, 0, st>>>(
@@ -494,6 +453,11 @@ void launch_adjoint_eval(const AdjLaunch& A, const PairConst<float>& Kf, const P
         case 6: adj_eval_t<float, 3, QUINTIC>(A, Kf, st); break;
         default: adj_eval_t<float, 3, WENDLAND_C2>(A, Kf, st); break;
     }
+}
+
+void launch_tape_list(const uint32_t* nl, const uint32_t* cnt, int n, uint32_t* tnl, uint32_t* tcnt,
+                      int sms, cudaStream_t st) {
+    k_tape_list<<<grid_of(n, 256, sms * 8), 256, 0, st>>>(nl, cnt, n, tnl, tcnt);
 }
 
 void launch_adjoint_scatter(const AdjLaunch& A, const AdjSet& out, cudaStream_t st) {

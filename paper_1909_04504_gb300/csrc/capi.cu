@@ -1603,6 +1603,8 @@ struct TapeEntry {
     void* R;
     uint32_t* perm;
     uint32_t* tag;
+    uint32_t* nl;   // neighbour list of the evaluation (maxn x N words, interleaved)
+    uint32_t* cnt;
 };
 
 void tape_take(sph_ctx* c, char*& p, TapeEntry& t) {
@@ -1612,6 +1614,8 @@ void tape_take(sph_ctx* c, char*& p, TapeEntry& t) {
     t.R = arena_take(p, (size_t)c->N * real);
     t.perm = (uint32_t*)arena_take(p, (size_t)c->N * 4);
     t.tag = (uint32_t*)arena_take(p, (size_t)c->N * 4);
+    t.nl = (uint32_t*)arena_take(p, (size_t)c->maxn * c->N * 4);
+    t.cnt = (uint32_t*)arena_take(p, (size_t)c->N * 4);
 }
 
 cudaError_t tape_record(sph_ctx* c, const TapeEntry& t) {
@@ -1624,6 +1628,10 @@ cudaError_t tape_record(sph_ctx* c, const TapeEntry& t) {
         e = cudaMemcpyAsync(t.perm, c->vals[c->passes & 1], N * 4, cudaMemcpyDeviceToDevice, c->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(t.tag, c->set[c->cur].tag, N * 4, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) {
+        launch_tape_list(c->nl, c->cnt, c->N, t.nl, t.cnt, c->sms, c->stream);
+        e = cudaGetLastError();
+    }
     return e;
 }
 
@@ -1654,13 +1662,17 @@ sph_status sph_backward(sph_ctx* c, const sph_scheme* scheme, double dt, int32_t
     if (C > K && K > 0) C = K;
     if (C < 1) C = 1;
     const int nseg = K > 0 ? (K + C - 1) / C : 0;
+    // initial evaluation first: it sizes the neighbour list that the tape copies
+    s = initial_eval(c, scheme, dt);
+    if (s != SPH_OK) return s;
     const size_t N = (size_t)c->N;
     const size_t real = c->dom.precision ? 4 : 8;
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     const int pblocks = adjoint_partial_blocks(c->N, c->sms);
     size_t bytes = 0;
     bytes += (size_t)(nseg + 1) * (15 * al(N * 8) + al(N * 4));                 // checkpoints + final
-    bytes += (size_t)(C + 1) * (2 * al(N * 4 * real) + al(N * real) + 2 * al(N * 4));  // tape
+    bytes += (size_t)(C + 1) * (2 * al(N * 4 * real) + al(N * real) + 3 * al(N * 4) +
+                                al((size_t)c->maxn * N * 4));                      // tape
     bytes += 2 * 13 * al(N * 8) + 5 * al(N * 8) + 2 * al(N * 4 * real);         // adjoint state
     bytes += al(N * 8 * 3) + al((size_t)pblocks * 16) + al(sizeof(AdjCtl));
     void* arena = nullptr;
@@ -1697,8 +1709,6 @@ sph_status sph_backward(sph_ctx* c, const sph_scheme* scheme, double dt, int32_t
     CK(cudaMemsetAsync(d_out, 0, N * 8 * 3, c->stream));
 
     // ---- forward: initial evaluation (taped) and checkpoints every C steps
-    s = initial_eval(c, scheme, dt);
-    if (s != SPH_OK) return s;
     CK(cudaMemcpyAsync(&c->ctl->dt, &dt, sizeof dt, cudaMemcpyHostToDevice, c->stream));
     CK(tape_record(c, tape[C]));
     if (!c->graph[0] || c->graph_timed != c->timing) {
@@ -1726,7 +1736,6 @@ sph_status sph_backward(sph_ctx* c, const sph_scheme* scheme, double dt, int32_t
     A.kernel = c->dom.kernel;
     A.n = c->N;
     A.sms = c->sms;
-    A.maxn = c->maxn;
     A.dt = dt;
     A.G = c->G;
     A.C = Cst;
@@ -1735,13 +1744,8 @@ sph_status sph_backward(sph_ctx* c, const sph_scheme* scheme, double dt, int32_t
     A.lrho_tot = lrho_tot;
     A.CA = CA;
     A.CS = CS;
-    A.keys = c->keys[0];
-    A.off = c->off;
-    A.nl = c->nl;
-    A.cnt = c->cnt;
     A.part = part;
     A.actl = actl;
-    A.ctl = c->ctl;
     int lc = 0;
     launch_adjoint_terminal(L[lc], c->set[c->cur], c->N, c->dom.dim, c->sms, c->stream);
     for (int seg = nseg - 1; seg >= 0; --seg) {
@@ -1761,6 +1765,8 @@ sph_status sph_backward(sph_ctx* c, const sph_scheme* scheme, double dt, int32_t
             A.R = t.R;
             A.perm = t.perm;
             A.tag = t.tag;
+            A.nl = t.nl;
+            A.cnt = t.cnt;
             A.kick = 1;
             A.L = L[lc];
             launch_adjoint_eval(A, Kf, Kd, c->stream);
@@ -1775,6 +1781,8 @@ sph_status sph_backward(sph_ctx* c, const sph_scheme* scheme, double dt, int32_t
     A.R = tape[C].R;
     A.perm = tape[C].perm;
     A.tag = tape[C].tag;
+    A.nl = tape[C].nl;
+    A.cnt = tape[C].cnt;
     A.kick = 0;
     A.L = L[lc];
     launch_adjoint_eval(A, Kf, Kd, c->stream);

@@ -124,7 +124,7 @@ struct AdjCtl {
 };
 // One reversed evaluation on a taped configuration (P, Q, R after its density pass).
 struct AdjLaunch {
-    int precision, dim, kernel, n, sms, kick, maxn;
+    int precision, dim, kernel, n, sms, kick;
     double dt;
     const void* P;
     const void* Q;
@@ -139,17 +139,16 @@ struct AdjLaunch {
     double* lrho_tot;
     void* CA;
     void* CS;
-    uint32_t* keys;
-    uint32_t* off;
-    uint32_t* nl;
-    uint32_t* cnt;
+    const uint32_t* nl;    // taped neighbour list of the evaluation (nl[k * n + i])
+    const uint32_t* cnt;
     double* part;
     AdjCtl* actl;
-    Control* ctl;
 };
 void launch_adjoint_eval(const AdjLaunch& A, const PairConst<float>& Kf, const PairConst<double>& Kd,
                          cudaStream_t st);
 void launch_adjoint_scatter(const AdjLaunch& A, const AdjSet& out, cudaStream_t st);
+void launch_tape_list(const uint32_t* nl, const uint32_t* cnt, int n, uint32_t* tnl, uint32_t* tcnt,
+                      int sms, cudaStream_t st);
 void launch_adjoint_terminal(const AdjSet& L, const ParticleSet& S, int n, int dim, int sms,
                              cudaStream_t st);
 void launch_adjoint_to_original(const AdjLaunch& A, double* out, cudaStream_t st);
