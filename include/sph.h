@@ -261,8 +261,10 @@ sph_status sph_kernels_per_step(const sph_ctx* ctx, const sph_scheme* scheme, in
  *   dKE_dalpha the artificial-viscosity coefficient alpha (0 when alpha is 0: the term
  *             is then switched off).
  * Any output may be NULL. Checkpoint and recompute: the state is saved every ckpt_every
- * steps (<= 0: ceil(sqrt K)); each segment is recomputed once, taping the pair-loop
- * inputs and the neighbour list of its steps, and reversed over the taped lists. Pair
+ * steps (<= 0: ceil(sqrt K)), the segments aligned to the end (the first one holds the
+ * remainder); the last segment is taped as the K steps run, every other segment is
+ * recomputed once from its checkpoint, taping the pair-loop inputs and the neighbour list
+ * of its steps, and each is reversed over the taped lists. Pair
  * terms in the pair-loop precision with compensated sums; adjoint state and the scalar
  * gradients in FP64. Continuity formulation only (SPH_ERR_INVALID for summation density),
  * dt > 0 required. Device workspace: about (K / ckpt_every + 1) * 124 +

@@ -48,11 +48,11 @@ __device__ __forceinline__ Real kernel_fp(Real q) {
             w1 += Real(30) * t2 * t2 * t2 * t2;
             w1p -= Real(120) * t2 * t2 * t2;
         }
-        return (w1p * q - w1) / (q * q * q);
+        return PairMath<Real>::div(w1p * q - w1, q * q * q);
     } else {
         if (q < Real(1e-6)) return Real(0);  // multiplies r_vec -> 0 (coincident particles)
         const Real t = Real(1) - Real(0.5) * q;
-        return Real(7.5) * t * t / q;
+        return PairMath<Real>::div(Real(7.5) * t * t, q);
     }
 }
 
@@ -62,86 +62,108 @@ struct MomCot {
     Real ax, ay, az, sx, sy, sz;
 };
 
-// VJP of the momentum + XSPH terms of the ordered pair (i dest fluid, j source) with the
-// cotangents of i. Inputs: r = x_i - x_j, v = u_i - u_j, densities, Pr = p / rho^2, m_j,
-// whether j is fluid. Outputs (added): g_r, g_v (vectors), g_rho_i, g_rho_j, g_pr (the
-// same for Pr_i and Pr_j), g_nu, g_alpha.
+// Factors of the momentum + XSPH terms of a pair that do not depend on the cotangents and
+// are the same for both orders (i, j) and (j, i): kernel values, AV, laminar and XSPH
+// weights. Inputs: r2, vr = v_ij . r_ij (even in the order), densities, Pr = p / rho^2.
+template <class Real>
+struct PairFactors {
+    Real Gk, Gp, W, rhobar, inv_rb, coef, dPi_dvr, dPi_dr2, dPi_drhobar, c0mu_rb, lam_r, Gkg2, inv_rs;
+    bool av_on;
+};
+
 template <class Real, int DIM, int KERNEL>
-__device__ __forceinline__ void momentum_vjp(Real rx, Real ry, Real rz, Real r2, Real vx, Real vy,
-                                             Real vz, Real rho_i, Real rho_j, Real pr_i, Real pr_j,
-                                             Real mj, bool fluid_j, const MomCot<Real>& c,
-                                             const PairConst<Real>& K, int flags, Real* g_r,
-                                             Real* g_v, Real& g_rho_i, Real& g_rho_j, Real& g_pr,
-                                             Real& g_nu, Real& g_alpha) {
-    const Real q = sqrt(r2) * K.inv_h;
-    const Real Gk = K.gfac * kernel_f<Real, KERNEL>(q);
-    const Real Gp = K.gfac * kernel_fp<Real, KERNEL>(q) * (K.inv_h * K.inv_h);  // dGk/dr = Gp r
-    const Real vr = vx * rx + vy * ry + (DIM == 3 ? vz * rz : Real(0));
-    const Real ar = c.ax * rx + c.ay * ry + (DIM == 3 ? c.az * rz : Real(0));
-    const Real av = c.ax * vx + c.ay * vy + (DIM == 3 ? c.az * vz : Real(0));
-    const Real rhobar = Real(0.5) * (rho_i + rho_j);
-    // pressure + artificial viscosity: a_i += -m_j (Pr_i + Pr_j + Pi) Gk r
-    Real Pi = Real(0), dPi_dvr = Real(0), dPi_dr2 = Real(0), dPi_drhobar = Real(0);
-    const bool av_on = (flags & F_AV) && vr < Real(0);
-    if (av_on) {
-        const Real den = r2 + K.av_h2;
-        const Real mu = K.h * vr / den;
-        Pi = -K.alpha_c0 * mu / rhobar;
-        dPi_dvr = -K.alpha_c0 * K.h / (den * rhobar);
-        dPi_dr2 = K.alpha_c0 * mu / (den * rhobar);  // d(-a c mu/rb)/dr2 with dmu/dr2 = -mu/den
-        dPi_drhobar = -Pi / rhobar;
-        g_alpha += -mj * Gk * ar * (-K.c0 * mu / rhobar);  // dPi/dalpha = -c0 mu / rhobar
+__device__ __forceinline__ PairFactors<Real> pair_factors(Real r2, Real vr, Real rho_i, Real rho_j,
+                                                          Real pr_i, Real pr_j,
+                                                          const PairConst<Real>& K, int flags) {
+    using M = PairMath<Real>;
+    PairFactors<Real> f;
+    const Real q = M::sqrt(r2) * K.inv_h;
+    f.Gk = K.gfac * kernel_f<Real, KERNEL>(q);
+    f.Gp = K.gfac * kernel_fp<Real, KERNEL>(q) * (K.inv_h * K.inv_h);  // dGk/dr = Gp r
+    f.W = (flags & F_XSPH) ? K.wfac * kernel_w<Real, KERNEL>(q) : Real(0);
+    f.rhobar = Real(0.5) * (rho_i + rho_j);
+    f.inv_rb = M::rcp(f.rhobar);
+    // artificial viscosity Pi = -alpha c0 mu / rhobar, mu = h vr / (r2 + 0.01 h^2), vr < 0
+    Real Pi = Real(0);
+    f.dPi_dvr = f.dPi_dr2 = f.dPi_drhobar = f.c0mu_rb = Real(0);
+    f.av_on = (flags & F_AV) && vr < Real(0);
+    if (f.av_on) {
+        const Real inv_den = M::rcp(r2 + K.av_h2);
+        const Real mu = K.h * vr * inv_den;
+        Pi = -K.alpha_c0 * mu * f.inv_rb;
+        f.dPi_dvr = -K.alpha_c0 * K.h * inv_den * f.inv_rb;
+        f.dPi_dr2 = K.alpha_c0 * mu * inv_den * f.inv_rb;  // dmu/dr2 = -mu / den
+        f.dPi_drhobar = -Pi * f.inv_rb;
+        f.c0mu_rb = -K.c0 * mu * f.inv_rb;  // dPi/dalpha
     }
-    const Real coef = pr_i + pr_j + Pi;
+    f.coef = pr_i + pr_j + Pi;
+    // laminar viscosity weight g2 = r2 / (r2 + eta h^2) and d(Gk g2)/dr = lam_r r
+    f.lam_r = f.Gkg2 = Real(0);
+    f.inv_rs = M::rcp(rho_i + rho_j);
+    if (flags & F_LAMINAR) {
+        const Real inv_den = M::rcp(r2 + K.eta_h2);
+        const Real g2 = r2 * inv_den;
+        const Real dg2 = K.eta_h2 * inv_den * inv_den;  // d g2 / d r2
+        f.lam_r = f.Gp * g2 + f.Gk * dg2 * Real(2);
+        f.Gkg2 = f.Gk * g2;
+    }
+    return f;
+}
+
+// VJP of the momentum + XSPH terms of the ordered pair (i dest fluid, j source) with the
+// cotangents c of i, from the pair's factors. Inputs: r = x_i - x_j, v = u_i - u_j, m_j,
+// whether j is fluid. Outputs (added): g_r, g_v (vectors), g_rho (the same for rho_i and
+// rho_j: every density enters through rhobar or rho_i + rho_j), g_pr (the same for Pr_i
+// and Pr_j); with SCALARS also g_nu and g_alpha.
+template <class Real, int DIM, bool SCALARS>
+__device__ __forceinline__ void momentum_vjp(Real rx, Real ry, Real rz, Real vx, Real vy, Real vz,
+                                             const PairFactors<Real>& f, Real mj, bool fluid_j,
+                                             const MomCot<Real>& c, const PairConst<Real>& K,
+                                             int flags, Real* g_r, Real* g_v, Real& g_rho,
+                                             Real& g_pr, Real& g_nu, Real& g_alpha) {
+    const Real ar = c.ax * rx + c.ay * ry + (DIM == 3 ? c.az * rz : Real(0));
+    // pressure + artificial viscosity: a_i += -m_j (Pr_i + Pr_j + Pi) Gk r
     // d(ar Gk coef)/dr: ar -> abar, Gk -> Gp r, coef -> dPi/dr (vr: v, r2: 2 r)
-    const Real s1 = -mj * (coef * Gp * ar + Gk * ar * dPi_dr2 * Real(2));
-    const Real s2 = -mj * coef * Gk;
-    const Real s3 = -mj * Gk * ar * dPi_dvr;
+    const Real mGa = mj * f.Gk * ar;
+    const Real s1 = -mj * (f.coef * f.Gp * ar + f.Gk * ar * f.dPi_dr2 * Real(2));
+    const Real s2 = -mj * f.coef * f.Gk;
+    const Real s3 = -mGa * f.dPi_dvr;
     g_r[0] += s1 * rx + s2 * c.ax + s3 * vx;
     g_r[1] += s1 * ry + s2 * c.ay + s3 * vy;
     if (DIM == 3) g_r[2] += s1 * rz + s2 * c.az + s3 * vz;
     g_v[0] += s3 * rx;
     g_v[1] += s3 * ry;
     if (DIM == 3) g_v[2] += s3 * rz;
-    g_pr += -mj * Gk * ar;
-    const Real gP_rhobar = -mj * Gk * ar * dPi_drhobar * Real(0.5);
-    g_rho_i += gP_rhobar;
-    g_rho_j += gP_rhobar;
-    // laminar viscosity: a_i += m_j 4 nu / (rho_i + rho_j) Gk g2 v, g2 = r2 / (r2 + eta h^2)
+    g_pr += -mGa;
+    g_rho += -mGa * f.dPi_drhobar * Real(0.5);
+    if (SCALARS && f.av_on) g_alpha += -mGa * f.c0mu_rb;
+    // laminar viscosity: a_i += m_j 4 nu / (rho_i + rho_j) Gk g2 v
     if (flags & F_LAMINAR) {
-        const Real den = r2 + K.eta_h2;
-        const Real g2 = r2 / den;
-        const Real dg2 = K.eta_h2 / (den * den);  // d g2 / d r2
-        const Real rs = rho_i + rho_j;
-        const Real cvn = mj * K.nu4 / rs;  // cv / (Gk g2)
-        const Real t1 = cvn * av * (Gp * g2 + Gk * dg2 * Real(2));
+        const Real av = c.ax * vx + c.ay * vy + (DIM == 3 ? c.az * vz : Real(0));
+        const Real cvn = mj * K.nu4 * f.inv_rs;  // cv / (Gk g2)
+        const Real t1 = cvn * av * f.lam_r;
         g_r[0] += t1 * rx;
         g_r[1] += t1 * ry;
         if (DIM == 3) g_r[2] += t1 * rz;
-        const Real cv = cvn * Gk * g2;
+        const Real cv = cvn * f.Gkg2;
         g_v[0] += cv * c.ax;
         g_v[1] += cv * c.ay;
         if (DIM == 3) g_v[2] += cv * c.az;
-        const Real grs = -cv * av / rs;
-        g_rho_i += grs;
-        g_rho_j += grs;
-        g_nu += Real(4) * mj / rs * Gk * g2 * av;  // d/dnu (nu4 = 4 nu)
+        g_rho += -cv * av * f.inv_rs;
+        if (SCALARS) g_nu += Real(4) * mj * f.inv_rs * f.Gkg2 * av;  // d/dnu (nu4 = 4 nu)
     }
     // XSPH over fluid sources: xs_i += -eps m_j W v / rhobar
     if ((flags & F_XSPH) && fluid_j) {
-        const Real W = K.wfac * kernel_w<Real, KERNEL>(q);
         const Real sv = c.sx * vx + c.sy * vy + (DIM == 3 ? c.sz * vz : Real(0));
-        const Real e = K.xsph * mj / rhobar;
-        const Real t1 = -e * sv * Gk;  // dW/dr = Gk r
+        const Real e = K.xsph * mj * f.inv_rb;
+        const Real t1 = -e * sv * f.Gk;  // dW/dr = Gk r
         g_r[0] += t1 * rx;
         g_r[1] += t1 * ry;
         if (DIM == 3) g_r[2] += t1 * rz;
-        g_v[0] += -e * W * c.sx;
-        g_v[1] += -e * W * c.sy;
-        if (DIM == 3) g_v[2] += -e * W * c.sz;
-        const Real grb = e * W * sv / rhobar * Real(0.5);
-        g_rho_i += grb;
-        g_rho_j += grb;
+        g_v[0] += -e * f.W * c.sx;
+        g_v[1] += -e * f.W * c.sy;
+        if (DIM == 3) g_v[2] += -e * f.W * c.sz;
+        g_rho += e * f.W * sv * f.inv_rb * Real(0.5);
     }
 }
 
@@ -222,7 +244,7 @@ __device__ __forceinline__ void adj_scalars(double a, double b, double* part, Ad
 // lambda_x and lambda_uh (fluid k), writes rhom_k = d/drho' of the momentum terms (the
 // Pr = p / rho^2 part through the EOS derivative), and accumulates d/dnu, d/dalpha.
 template <class Real, int DIM, int KERNEL>
-__global__ void __launch_bounds__(PAIR_THREADS)
+__global__ void __launch_bounds__(PAIR_THREADS, sizeof(Real) == 4 ? 8 : 1)
 k_adj_momentum(const typename V4<Real>::T* __restrict__ P, const typename V4<Real>::T* __restrict__ Q,
                const Real* __restrict__ R, const uint32_t* __restrict__ nl,
                const uint32_t* __restrict__ cnt, int n, Grid G, PairConst<Real> K, StepConst C,
@@ -257,35 +279,35 @@ k_adj_momentum(const typename V4<Real>::T* __restrict__ P, const typename V4<Rea
             const Real prj = R[j];
             const bool fluid_j = pj.w > Real(0);
             const Real vx = qk.x - qj.x, vy = qk.y - qj.y, vz = DIM == 3 ? qk.z - qj.z : Real(0);
-            if (fluid_k) {  // k is the destination
-                Real g_r[3] = {0, 0, 0}, g_v[3] = {0, 0, 0}, g_ri = 0, g_rj = 0, g_p = 0, g_n = 0,
-                     g_a = 0;
-                momentum_vjp<Real, DIM, KERNEL>(rx, ry, rz, r2, vx, vy, vz, qk.w, qj.w, prk, prj,
-                                                fabs(pj.w), fluid_j, cot_k, K, flags, g_r, g_v, g_ri,
-                                                g_rj, g_p, g_n, g_a);
-                for (int d = 0; d < DIM; ++d) {
-                    gx[d].add(g_r[d]);
-                    gu[d].add(g_v[d]);
-                }
-                grho.add(g_ri);
-                gpr.add(g_p);
-                gnu.add(g_n);
-                gal.add(g_a);
-            }
-            if (fluid_j) {  // k is the source of destination j
+            const Real vr = vx * rx + vy * ry + (DIM == 3 ? vz * rz : Real(0));
+            // the factors of the pair serve both orders: (k, j) and (j, k)
+            const PairFactors<Real> f =
+                pair_factors<Real, DIM, KERNEL>(r2, vr, qk.w, qj.w, prk, prj, K, flags);
+            // both roles summed before the compensated accumulation
+            Real g_r[3] = {0, 0, 0}, g_v[3] = {0, 0, 0}, g_rho = 0, g_p = 0, g_n = 0, g_a = 0;
+            if (fluid_k)  // k is the destination
+                momentum_vjp<Real, DIM, true>(rx, ry, rz, vx, vy, vz, f, fabs(pj.w), fluid_j,
+                                              cot_k, K, flags, g_r, g_v, g_rho, g_p, g_n, g_a);
+            if (fluid_j) {  // k is the source of destination j: d/dx_k = -d/dr
                 const typename V4<Real>::T caj = CA[j], csj = CS[j];
                 const MomCot<Real> cot_j{caj.x, caj.y, caj.z, csj.x, csj.y, csj.z};
-                Real g_r[3] = {0, 0, 0}, g_v[3] = {0, 0, 0}, g_ri = 0, g_rj = 0, g_p = 0, g_n = 0,
-                     g_a = 0;
-                momentum_vjp<Real, DIM, KERNEL>(-rx, -ry, -rz, r2, -vx, -vy, -vz, qj.w, qk.w, prj,
-                                                prk, mk, fluid_k, cot_j, K, flags, g_r, g_v, g_ri,
-                                                g_rj, g_p, g_n, g_a);
+                Real h_r[3] = {0, 0, 0}, h_v[3] = {0, 0, 0};
+                momentum_vjp<Real, DIM, false>(-rx, -ry, -rz, -vx, -vy, -vz, f, mk, fluid_k, cot_j,
+                                               K, flags, h_r, h_v, g_rho, g_p, g_n, g_a);
                 for (int d = 0; d < DIM; ++d) {
-                    gx[d].add(-g_r[d]);
-                    gu[d].add(-g_v[d]);
+                    g_r[d] -= h_r[d];
+                    g_v[d] -= h_v[d];
                 }
-                grho.add(g_rj);
-                gpr.add(g_p);
+            }
+            for (int d = 0; d < DIM; ++d) {
+                gx[d].add(g_r[d]);
+                gu[d].add(g_v[d]);
+            }
+            grho.add(g_rho);
+            gpr.add(g_p);
+            if (fluid_k) {
+                gnu.add(g_n);
+                gal.add(g_a);
             }
         }
         if (fluid_k)
@@ -345,7 +367,7 @@ k_adj_continuity(const typename V4<Real>::T* __restrict__ P, const typename V4<R
             const Real r2 = separation<Real, DIM>(pk, pj, G, K, rx, ry, rz);
             const typename V4<Real>::T qj = Q[j];
             const Real cj = reinterpret_cast<const Real*>(&CA[j])[3];
-            const Real q = sqrt(r2) * K.inv_h;
+            const Real q = PairMath<Real>::sqrt(r2) * K.inv_h;
             const Real Gk = K.gfac * kernel_f<Real, KERNEL>(q);
             const Real Gp = K.gfac * kernel_fp<Real, KERNEL>(q) * (K.inv_h * K.inv_h);
             const Real vx = qk.x - qj.x, vy = qk.y - qj.y, vz = DIM == 3 ? qk.z - qj.z : Real(0);

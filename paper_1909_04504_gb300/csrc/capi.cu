@@ -1715,10 +1715,16 @@ sph_status sph_backward(sph_ctx* c, const sph_scheme* scheme, double dt, int32_t
         s = capture_step_graphs(c);
         if (s != SPH_OK) return s;
     }
-    for (int step = 0; step < K; ++step) {
-        if (step % C == 0) CK(snap_save(c, ck[step / C]));
+    // segments end-aligned: segment 0 holds the remainder (1..C steps), the others C steps;
+    // the last segment is taped during this sweep (it is reversed first, so it is never
+    // recomputed), the others are recomputed from their checkpoints
+    auto seg_begin = [&](int sg) { return sg == 0 ? 0 : K - (nseg - sg) * C; };
+    const int taped0 = nseg > 0 ? seg_begin(nseg - 1) : K;
+    for (int sg = 0, step = 0; step < K; ++step) {
+        if (sg < nseg - 1 && step == seg_begin(sg)) CK(snap_save(c, ck[sg++]));
         CK(cudaGraphLaunch(c->graph[c->cur], c->stream));
         c->cur ^= 1;
+        if (step >= taped0) CK(tape_record(c, tape[step - taped0]));
     }
     CK(snap_save(c, ck[nseg]));
     Control ctl_final{};
@@ -1749,14 +1755,16 @@ sph_status sph_backward(sph_ctx* c, const sph_scheme* scheme, double dt, int32_t
     int lc = 0;
     launch_adjoint_terminal(L[lc], c->set[c->cur], c->N, c->dom.dim, c->sms, c->stream);
     for (int seg = nseg - 1; seg >= 0; --seg) {
-        const int s0 = seg * C, s1 = std::min(K, s0 + C);
-        CK(snap_load(c, ck[seg]));
-        CK(cudaMemsetAsync(&c->ctl->status, 0, sizeof(unsigned), c->stream));
-        CK(cudaMemcpyAsync(&c->ctl->dt, &dt, sizeof dt, cudaMemcpyHostToDevice, c->stream));
-        for (int step = s0; step < s1; ++step) {
-            CK(cudaGraphLaunch(c->graph[c->cur], c->stream));
-            c->cur ^= 1;
-            CK(tape_record(c, tape[step - s0]));
+        const int s0 = seg_begin(seg), s1 = seg + 1 < nseg ? seg_begin(seg + 1) : K;
+        if (seg < nseg - 1) {  // recompute from the checkpoint, taping each step
+            CK(snap_load(c, ck[seg]));
+            CK(cudaMemsetAsync(&c->ctl->status, 0, sizeof(unsigned), c->stream));
+            CK(cudaMemcpyAsync(&c->ctl->dt, &dt, sizeof dt, cudaMemcpyHostToDevice, c->stream));
+            for (int step = s0; step < s1; ++step) {
+                CK(cudaGraphLaunch(c->graph[c->cur], c->stream));
+                c->cur ^= 1;
+                CK(tape_record(c, tape[step - s0]));
+            }
         }
         for (int step = s1 - 1; step >= s0; --step) {
             const TapeEntry& t = tape[step - s0];

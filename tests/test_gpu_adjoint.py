@@ -82,7 +82,7 @@ def test_checkpoint_interval_does_not_change_the_gradient_and_final_state():
     sch = G.scheme_of(wl)
     K = 9
     outs = []
-    for C in (1, 3, 9):
+    for C in (1, 3, 4, 9):  # 4: a remainder segment of one step
         with sim_of(wl) as sim:
             gu, gnu, gal = sim.backward(sch, wl.dt, K, ckpt_every=C)
             outs.append((gu, gal, sim.state()))
