@@ -318,7 +318,15 @@ k_adj_momentum(const typename V4<Real>::T* __restrict__ P, const typename V4<Rea
         // EOS chain: d(p / rho^2)/drho = c0^2 (rho/rho0)^(gamma-1) / rho^2 - 2 p / rho^3
         const double rho = (double)qk.w;
         const double p = tait_pressure(rho, C);
-        const double dp = C.c0 * C.c0 * pow(rho * C.inv_rho0, C.gamma - 1.0);
+        const double x = rho * C.inv_rho0;
+        double xg1;  // (rho / rho0)^(gamma - 1)
+        if (C.gamma7) {
+            const double x3 = x * x * x;
+            xg1 = x3 * x3;
+        } else {
+            xg1 = pow(x, C.gamma - 1.0);
+        }
+        const double dp = C.c0 * C.c0 * xg1;
         const double dpr = dp / (rho * rho) - 2.0 * p / (rho * rho * rho);
         rhom[k] = grho.value() + dpr * gpr.value();
         s_nu += gnu.value();
