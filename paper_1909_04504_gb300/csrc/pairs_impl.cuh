@@ -396,8 +396,12 @@ __device__ __forceinline__ void density_scan_sum(int i, const Group<T>& g, uint3
     g.sync();  // the list entries of the other lanes are visible from here on
     sum.zero();
     const typename V4<Real>::T qi = Q[i];
+    // the next list entry is fetched one iteration ahead, so its load overlaps this
+    // iteration's source loads and arithmetic
+    uint32_t j_next = g.t < k ? nl[(size_t)g.t * n + i] : 0u;
     for (uint32_t kk = g.t; kk < k; kk += T) {
-        const uint32_t j = nl[(size_t)kk * n + i];
+        const uint32_t j = j_next;
+        if (kk + T < k) j_next = nl[(size_t)(kk + T) * n + i];
         const typename V4<Real>::T pj = P[j];
         Real dx, dy, dz;
         const Real r2 = separation<Real, DIM>(pi, pj, G, K, dx, dy, dz);
@@ -555,8 +559,10 @@ __device__ __forceinline__ void momentum_sums(int i, const Group<T>& g,
 #pragma unroll
     for (int k = 0; k < 6; ++k) acc[k].zero();
     const uint32_t ni = cnt[i];
+    uint32_t j_next = g.t < ni ? nl[(size_t)g.t * n + i] : 0u;  // fetched one entry ahead
     for (uint32_t kk = g.t; kk < ni; kk += T) {
-        const uint32_t j = nl[(size_t)kk * n + i];
+        const uint32_t j = j_next;
+        if (kk + T < ni) j_next = nl[(size_t)(kk + T) * n + i];
         const typename V4<Real>::T pj = P[j];
         Real dx, dy, dz;
         const Real r2 = separation<Real, DIM>(pi, pj, G, K, dx, dy, dz);
