@@ -425,6 +425,49 @@ def gpu_arm(args, rank, world, dist):
                 "fp32_speedup": round(value / v64, 3)}
         sim64.close()
 
+    # ---- the batch against its alternatives: the same instances with FP64 pair loops, and
+    # as separate problems (one context and stream each, every step launched before any wait)
+    batch_vs = None
+    if sim.batch and args.fp64_steps > 0:
+        rounds = max(3, min(args.fp64_steps, 50))
+        insts = wl.instances
+        b64 = G.BatchSimulation(insts, precision=0)
+        b64.step_batch(sim.sch, sim.dts, args.warmup)
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(b64.stream)
+        b64.step_batch_async(sim.sch, sim.dts, rounds)
+        g1.record(b64.stream)
+        b64.synchronize()
+        torch.cuda.synchronize()
+        ms64 = g0.elapsed_time(g1) / rounds
+        p64 = float(b64.batch_diagnostics()[:, 8].sum())
+        b64.close()
+        singles = [G.Simulation.from_workload(w) for w in insts]
+        for one, sc, w in zip(singles, sim.sch, insts):
+            one.step(sc, w.dt, args.warmup)
+        torch.cuda.synchronize()
+        tt = time.perf_counter()
+        for _ in range(rounds):
+            for one, sc, w in zip(singles, sim.sch, insts):
+                one.step_async(sc, w.dt, 1)
+        for one in singles:
+            one.synchronize()
+        ms_sep = (time.perf_counter() - tt) * 1e3 / rounds
+        p_sep = sum(float(one.diagnostics()[8]) for one in singles)
+        for one in singles:
+            one.close()
+        ms64, p64 = job_totals(dist, ms64, p64, device=dev)
+        ms_sep, p_sep = job_totals(dist, ms_sep, p_sep, device=dev)
+        batch_vs = {
+            "fp64_batch": {"value": p64 / (ms64 / 1e3), "unit": UNIT, "steps": rounds,
+                           "ms_per_step": ms64, "fp32_speedup": round(value / (p64 / (ms64 / 1e3)), 3)},
+            "separate_problems": {"value": p_sep / (ms_sep / 1e3), "unit": UNIT, "steps": rounds,
+                                  "ms_per_step": ms_sep,
+                                  "batched_speedup": round(value / (p_sep / (ms_sep / 1e3)), 3),
+                                  "path": "one Simulation per instance (default tile shape, "
+                                          "graph mode), sph_step_async on each, host clock"}}
+
     # ---- hand-written adjoint: K steps forward, then the same K steps with the reverse sweep
     adjoint = None
     k_adj = args.adjoint_steps if args.adjoint_steps >= 0 else ADJOINT_STEPS.get(args.workload, 0)
@@ -467,6 +510,7 @@ def gpu_arm(args, rank, world, dist):
         "particle_steps_per_s": psteps, "candidates_per_s": job_cand / (total_ms / 1e3),
         "pairs_per_step": pairs / args.steps, "phase_ms": phase_avg,
         "roofline": roofline, "e2e": e2e, "fp64_mode": fp64, "adjoint": adjoint,
+        "batch_vs": batch_vs,
         "gpu_launches": launches, "clocks": clocks, "wall_s": round(t_wall, 3),
     }
     return line, state0, wl
