@@ -134,13 +134,29 @@ __global__ void k_reorder(ParticleSet in, ParticleSet out, const uint32_t* __res
                           typename V4<Real>::T* __restrict__ P, typename V4<Real>::T* __restrict__ Q,
                           uint32_t* __restrict__ off, int ncells, const Control* ctl) {
     if (ctl->status) return;
-    const int m = n > ncells + 1 ? n : ncells + 1;
+    // cell table: four consecutive cells per thread, their previous offsets read and the
+    // new ones written as one 16-byte word (grids with many more cells than particles,
+    // as the half-size cells of 3D, would otherwise take several loop trips per thread)
+    const int nq = (ncells + 4) / 4;
+    const int m = n > nq ? n : nq;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
         if (k < n) {
             const int inst = find_instance(cell_bounds, ninst, skeys[k]);
             reorder_one<Real>(in, out, k, (int)perm[k], dim, idt[inst], kick, carry_rates, P, Q);
         }
-        if (k <= ncells) off[k] = cell_offset_near(skeys, n, (uint32_t)k, off[k]);  // cell table
+        if (k < nq) {
+            const uint32_t c0 = 4u * (uint32_t)k;
+            if (c0 + 3 <= (uint32_t)ncells) {
+                uint4 g = reinterpret_cast<const uint4*>(off)[k];
+                g.x = cell_offset_near(skeys, n, c0, g.x);
+                g.y = cell_offset_near(skeys, n, c0 + 1, g.y);
+                g.z = cell_offset_near(skeys, n, c0 + 2, g.z);
+                g.w = cell_offset_near(skeys, n, c0 + 3, g.w);
+                reinterpret_cast<uint4*>(off)[k] = g;
+            } else {
+                for (uint32_t c = c0; c <= (uint32_t)ncells; ++c) off[c] = cell_offset_near(skeys, n, c, off[c]);
+            }
+        }
     }
 }
 
@@ -296,7 +312,8 @@ void launch_cell_offsets(const uint32_t* skeys, int n, int ncells, uint32_t* off
 
 void launch_reorder(const StepLaunch& L, const uint32_t* perm, int carry_rates, uint32_t* off,
                     int ncells, cudaStream_t st) {
-    const int m = L.n > ncells + 1 ? L.n : ncells + 1;
+    const int nq = (ncells + 4) / 4;
+    const int m = L.n > nq ? L.n : nq;
     const int g = grid_for(m, 256, L.sms * 8);
     if (L.precision)
         k_reorder<float><<<g, 256, 0, st>>>(L.Sin, L.S, perm, L.skeys, L.n, L.dim,

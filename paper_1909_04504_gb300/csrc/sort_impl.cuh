@@ -149,6 +149,7 @@ __device__ __forceinline__ void radix_scatter_tile(const uint32_t* __restrict__ 
 constexpr uint32_t LB_AGGREGATE = 1u << 30;
 constexpr uint32_t LB_PREFIX = 2u << 30;
 constexpr uint32_t LB_COUNT = (1u << 30) - 1u;
+constexpr int LB_BATCH = 8;  // predecessors read per look-back round
 
 struct OnesweepSmem {
     uint32_t base_d[RADIX];
@@ -220,22 +221,37 @@ __device__ __forceinline__ void radix_onesweep_tile(const uint32_t* __restrict__
     uint32_t excl = 0;
     int ok = 1;
     if (tile > 0) {
+        // decoupled look-back, LB_BATCH predecessors read at once (independent loads):
+        // counts are added from tile - 1 downwards until a tile that holds its inclusive
+        // prefix; an unpublished tile is waited for (bounded) and read again
         const unsigned long long t0 = sort_clock_ns();
         int p = tile - 1;
-        while (p >= 0) {
-            const uint32_t v = *(volatile uint32_t*)(status + (size_t)p * RADIX + tid);
-            if ((v & ~LB_COUNT) == 0u) {  // not published yet
+        bool done = false;
+        while (!done) {
+            uint32_t v[LB_BATCH];
+#pragma unroll
+            for (int b = 0; b < LB_BATCH; ++b)
+                v[b] = p - b >= 0 ? *(volatile uint32_t*)(status + (size_t)(p - b) * RADIX + tid)
+                                  : (LB_PREFIX | 0u);
+            int b = 0;
+            for (; b < LB_BATCH; ++b) {
+                if ((v[b] & ~LB_COUNT) == 0u) break;  // not published yet
+                excl += v[b] & LB_COUNT;
+                if (v[b] & LB_PREFIX) {
+                    done = true;
+                    break;
+                }
+            }
+            if (done) break;
+            p -= b;
+            if (b < LB_BATCH) {  // tile p is not published: wait, then read again from it
                 if ((*(volatile unsigned*)ctl_status & ST_TIMEOUT) || sort_clock_ns() - t0 > wait_ns) {
                     atomicOr(ctl_status, ST_TIMEOUT);
                     ok = 0;
                     break;
                 }
                 __nanosleep(32);
-                continue;
             }
-            excl += v & LB_COUNT;
-            if (v & LB_PREFIX) break;
-            --p;
         }
         if (ok) atomicExch(mine, LB_PREFIX | (excl + count));
     }
