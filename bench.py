@@ -36,8 +36,9 @@ SMS = 152
 SM_MAX_MHZ = 2070.0
 
 
-def workload(name: str):
-    """The workload, or for the batched configuration the list of its instances."""
+def workload(name: str, wall_bc: str = "density"):
+    """The workload, or for the batched configuration the list of its instances; with
+    wall_bc "adami" the solid-wall pressure condition replaces the continuity walls."""
     import workloads as W
     table = {
         "dam_break_2d": lambda: W.dam_break_2d(),
@@ -46,7 +47,10 @@ def workload(name: str):
         "dam_break_3d": lambda: W.dam_break_3d(),
         "batch_tg2d": lambda: W.batch_tg2d(),
     }
-    return table[name]()
+    wl = table[name]()
+    if wall_bc == "adami":
+        wl = [w.with_wall_bc(1) for w in wl] if isinstance(wl, list) else wl.with_wall_bc(1)
+    return wl
 
 
 class BatchView:
@@ -128,7 +132,8 @@ def describe(wl) -> dict:
     return {
         "workload": f"{wl.name}: {wl.n_fluid:,} fluid + {wl.n_total - wl.n_fluid:,} wall particles, "
                     f"{wl.dim}D, {kern} h={wl.h:g}, {prec}, alpha={wl.alpha:g}, xsph={wl.xsph_eps:g}, "
-                    f"nu={wl.nu:g}, dt={wl.dt:.6g}, neighbour rebuild every step",
+                    f"nu={wl.nu:g}, dt={wl.dt:.6g}, neighbour rebuild every step"
+                    + (", solid-wall pressure of Adami et al." if getattr(wl, "wall_bc", 0) else ""),
         "particles": wl.n_total,
         "fluid_particles": wl.n_fluid,
         "l2": "flushed between timed steps (512 MB write)",
@@ -167,6 +172,25 @@ def pass_flops(wl) -> dict:
             "xsph_fluid_source_pair": xsph}
 
 
+def stream_bytes(wl, ncells: int) -> dict:
+    """Algorithmic DRAM bytes of one step's streaming kernels (in-step form; 8-byte FP64
+    state words, d = dimension). keys (drift + cell key + histograms): a fluid particle
+    reads x, u, a, xsph and the tag and writes x and the key, a wall reads x and the tag
+    and writes the key; each radix pass reads and writes a (key, index) pair; the reorder
+    reads the permutation, the key and the state it gathers (tag, x, u, rho, m, and a for
+    fluid), writes x, u, rho, m, tag and the shadow P, Q (2 x 16 B FP32, 2 x 32 B FP64),
+    and reads and writes one 4-byte offset per cell."""
+    d = wl.dim
+    n, nf = wl.n_total, wl.n_fluid
+    shadow = 32 if wl.precision == 1 else 64
+    bits = max(0, (max(ncells, 1) - 1).bit_length())
+    passes = max(1, (bits + 7) // 8)
+    keys = nf * (4 * d * 8 + 4 + d * 8 + 4) + (n - nf) * (d * 8 + 4 + 4)
+    reorder = (n * (4 + 4 + 4 + 2 * d * 8 + 16) + nf * d * 8
+               + n * (2 * d * 8 + 16 + 4 + shadow) + ncells * 8)
+    return {"keys": keys, "sort": passes * n * 16, "reorder": reorder, "passes": passes}
+
+
 # ------------------------------------------------------------ ncu traffic
 PAIR_KERNEL_SOURCES = ("sph_device.cuh", "sph_launch.h", "step_impl.cuh", "reduce_impl.cuh",
                        "pairs_impl.cuh", "pairs_f32.cu", "pairs_f64.cu")
@@ -183,6 +207,15 @@ def source_hash() -> str:
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def measured_hbm_gbs():
+    """HBM copy bandwidth measured on this machine (MEASURED_PEAKS.json), else None."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError, TypeError):
+        return None
 
 
 def measured_traffic(workload_name: str, kernel: str, lanes: int):
@@ -267,7 +300,7 @@ def gpu_arm(args, rank, world, dist):
     import paper_1909_04504_gb300 as G
 
     dev = torch.cuda.current_device()
-    raw = workload(args.workload)
+    raw = workload(args.workload, args.wall_bc)
     wl = BatchView(raw) if isinstance(raw, list) else raw
     sim = Runner(G, raw)
     sch = sim.sch
@@ -375,6 +408,19 @@ def gpu_arm(args, rank, world, dist):
                                + (" / 64 (FP64)" if wl.precision == 0 else ""),
                 "passes": per_pass}
     phase_avg = {k: round(v / psteps_n, 5) for k, v in phases.items()}
+    # the streaming kernels against the measured HBM copy bandwidth
+    _, _, ncells = sim.grid()
+    sb = stream_bytes(wl, int(ncells))
+    hbm = measured_hbm_gbs()
+    streaming = {}
+    for k in ("keys", "sort", "reorder"):
+        ms = phases[k] / psteps_n
+        gbs = sb[k] / (ms / 1e3) / 1e9
+        streaming[k] = {"bytes_per_step": sb[k], "avg_ms": round(ms, 5), "achieved_gbs": round(gbs, 1),
+                        "frac": round(gbs / hbm, 4) if hbm else None}
+    roofline["streaming"] = {"peak_gbs": hbm, "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+                             "sort_passes": sb["passes"], "kernels": streaming,
+                             "note": "phase times include ~2-3 us of event-node gaps each"}
 
     # ---- end to end through the C ABI with host buffers
     blob = sim.save_state()
@@ -589,7 +635,7 @@ def cpu_baseline(wl, target_s: float, states=None) -> dict:
 def reference_arm(args):
     """Times the oracle on the host cores in the base contract's reference slot."""
     import oracle as O
-    wl = workload(args.workload)
+    wl = workload(args.workload, args.wall_bc)
     if isinstance(wl, list):
         v, el, sample, cores = oracle_batch_sample(wl, args.ref_seconds)
         return {
@@ -646,6 +692,9 @@ def main():
                     help="reference arm: seconds of oracle time in the timed sample")
     ap.add_argument("--step-mode", default="auto", choices=["auto", "graph", "persistent"],
                     help="auto: the autotuner picks the tile shape and the step form")
+    ap.add_argument("--wall-bc", default="density", choices=["density", "adami"],
+                    help="wall condition: continuity walls (the configurations') or the "
+                         "solid-wall pressure of Adami et al.")
     ap.add_argument("--adjoint-steps", type=int, default=-1,
                     help="K of the timed adjoint (-1: 50 for taylor_green_3d, 20 for "
                          "dam_break_3d, none otherwise; 0: off)")

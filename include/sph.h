@@ -49,6 +49,7 @@ typedef enum { SPH_KERNEL_QUINTIC = 0, SPH_KERNEL_WENDLAND_C2 = 1 } sph_kernel;
 typedef enum { SPH_PREC_FP64 = 0, SPH_PREC_FP32 = 1 } sph_precision;
 typedef enum { SPH_ROLE_FLUID = 0, SPH_ROLE_WALL = 1 } sph_role;
 typedef enum { SPH_DENSITY_CONTINUITY = 0, SPH_DENSITY_SUMMATION = 1 } sph_density;
+typedef enum { SPH_WALL_DENSITY = 0, SPH_WALL_ADAMI = 1 } sph_wall_bc;
 
 /* Geometry of a problem (Sec. 2.2, Sec. 3 create_domain).
  *  dim        2 or 3.
@@ -58,11 +59,11 @@ typedef enum { SPH_DENSITY_CONTINUITY = 0, SPH_DENSITY_SUMMATION = 1 } sph_densi
  *             (Neumaier) per-particle sums; the integrator, the state and the
  *             reductions stay FP64. FP64: everything in double.
  *  periodic   per axis; a periodic axis wraps positions into [lo, hi) and uses the
- *             minimum image in the neighbour test. It needs at least 3 cells.
+ *             minimum image in the neighbour test. It needs at least 2 R + 1 cells.
  *  h          smoothing length (constant for all particles).
  *  lo, hi     cell box. On a periodic axis it is the period. Cells per axis:
- *             n = floor((hi - lo) / (k h * 1.00001)), size (hi - lo) / n, with k the
- *             support factor; a particle outside the box on a non-periodic axis is
+ *             n = floor((hi - lo) / (k h / R * 1.00001)), size (hi - lo) / n, with k the
+ *             support factor and R = 1 in 2D, 2 in 3D (a (2R + 1)^dim cell stencil); a particle outside the box on a non-periodic axis is
  *             clamped into the edge cell (the result stays exact, only slower). */
 typedef struct {
     int32_t dim;
@@ -100,10 +101,19 @@ typedef struct {
  *             v_ij . r_ij < 0, mu_ij = h v_ij . r_ij / (r^2 + 0.01 h^2) (off when 0).
  *  xsph_eps   XSPH: dx_i = eps sum_fluid j m_j / rhobar_ij (u_j - u_i) W_ij, added to the
  *             drift velocity (off when 0).
- *  g          body acceleration of fluid particles, Eq. mom:sph. */
+ *  g          body acceleration of fluid particles, Eq. mom:sph.
+ *  wall_bc    sph_wall_bc. SPH_WALL_DENSITY: wall pressure from the wall density of the
+ *             formulation (continuity from fluid sources, or summation). SPH_WALL_ADAMI:
+ *             the solid-wall condition of Adami, Hu and Adams (2012), one of the wall
+ *             boundary conditions listed among the schemes of Sec. 2.3: after the density
+ *             pass each wall particle w takes p_w = (sum_f p_f W_wf + g . sum_f rho_f
+ *             (x_w - x_f) W_wf) / sum_f W_wf over its fluid neighbours f (static walls)
+ *             and rho_w = rho0 (1 + p_w / B)^(1/gamma), B = c0^2 rho0 / gamma; a wall
+ *             with no fluid neighbour takes p_w = 0, rho_w = rho0. One more launch per
+ *             evaluation (graph step form only; sph_backward rejects it). */
 typedef struct {
     int32_t density;
-    int32_t reserved;
+    int32_t wall_bc;
     double rho0;
     double c0;
     double gamma;

@@ -32,7 +32,8 @@
  *  - predictor-corrector as kick-drift-kick for u and x; the density advanced like the
  *    positions with the continuity rate at (x^{n+1}, u^{n+1/2}) before the momentum
  *    evaluation at (x^{n+1}, u^{n+1/2}, rho^{n+1});
- *  - walls static (x and u fixed), wall density from continuity with fluid sources.
+ *  - walls static (x and u fixed), wall density from continuity with fluid sources, or
+ *    (option) the wall pressure of Adami et al. (2012) with the density from the EOS.
  */
 #include <algorithm>
 #include <cmath>
@@ -50,6 +51,7 @@ constexpr int KERNEL_WENDLAND_C2 = 1;
 constexpr int ROLE_FLUID = 0;
 constexpr int PREC_FP32 = 1;
 constexpr int DENSITY_SUMMATION = 1;
+constexpr int WALL_ADAMI = 1;
 constexpr double PI = 3.14159265358979323846;
 
 /* ---------------------------------------------------------------- dual numbers */
@@ -100,6 +102,7 @@ typedef struct {
     int32_t density;      // 0 continuity equation, 1 summation density
     int32_t periodic[3];  // per axis
     int32_t brute;        // 1: neighbour search by all-pairs loop instead of cells
+    int32_t wall_bc;      // 0: wall density from continuity, 1: wall pressure of Adami et al.
     double h;             // smoothing length
     double lo[3], hi[3];  // cell box (periodic box on periodic axes)
     double rho0, c0, gamma;
@@ -453,6 +456,47 @@ void rhs(const ora_params* P, T nu, T alpha, int64_t n, State<T>& S, const doubl
 
     R.p.assign(n, T(0.0));
     for (int64_t i = 0; i < n; ++i) R.p[i] = tait(P, S.rho[i]);
+
+    /* Solid-wall pressure of Adami, Hu and Adams (2012), the wall boundary condition listed
+     * among the schemes of Sec. 2.3 (formula from that reference): a wall particle w takes the kernel-weighted mean of its fluid
+     * neighbours' pressure plus the hydrostatic part of the body force (static walls, no
+     * wall acceleration),
+     *   p_w = (sum_f p_f W_wf + g . sum_f rho_f r_wf W_wf) / sum_f W_wf,  r_wf = x_w - x_f,
+     * and the density the Tait EOS maps to p_w, rho_w = rho0 (1 + p_w / B)^(1 / gamma).
+     * A wall with no fluid neighbour takes p_w = 0 and rho_w = rho0. The fluid values are
+     * those of this evaluation (after the density update above). */
+    if (P->wall_bc == WALL_ADAMI) {
+        const double B = P->c0 * P->c0 * P->rho0 / P->gamma;
+        std::vector<T> pw(n, T(0.0)), rw(n, T(0.0));
+#pragma omp parallel for schedule(dynamic, 256)
+        for (int64_t i = 0; i < n; ++i) {
+            if (role[i] == ROLE_FLUID) continue;
+            T sw = T(0.0), sp = T(0.0), sg = T(0.0);
+            for (int64_t j : nbr[i]) {
+                if (role[j] != ROLE_FLUID) continue;
+                T r[3], W, gW[3];
+                diff(i, j, r);
+                kern(r, &W, gW);
+                T gr = T(0.0);
+                for (int d = 0; d < dim; ++d) gr = gr + P->g[d] * r[d];
+                sw = sw + W;
+                sp = sp + R.p[j] * W;
+                sg = sg + S.rho[j] * gr * W;
+            }
+            if (val(sw) > 0.0) {
+                pw[i] = (sp + sg) / sw;
+                rw[i] = P->rho0 * pow_(1.0 + pw[i] / B, 1.0 / P->gamma);
+            } else {
+                pw[i] = T(0.0);
+                rw[i] = T(P->rho0);
+            }
+        }
+        for (int64_t i = 0; i < n; ++i)
+            if (role[i] != ROLE_FLUID) {
+                R.p[i] = pw[i];
+                S.rho[i] = rw[i];
+            }
+    }
 
     for (int d = 0; d < 3; ++d) {
         R.a[d].assign(n, T(0.0));

@@ -51,6 +51,8 @@ struct sph_ctx {
     sph_domain dom{};
     Grid G{};
     int N = 0;
+    int nwall = 0;                 // wall particles
+    bool wall_pass = false;        // the scheme(s) in use take the solid-wall pressure pass
     std::vector<int64_t> arr_off;  // n_arrays + 1
     int passes = 1;
 
@@ -228,6 +230,7 @@ PairConst<Real> pair_const_dg(const sph_domain& D, const Grid& Gr, const sph_sch
         if (s->nu != 0.0) f |= F_LAMINAR;
         if (s->alpha != 0.0) f |= F_AV;
         if (s->xsph_eps != 0.0) f |= F_XSPH;
+        if (s->wall_bc == SPH_WALL_ADAMI) f |= F_WALLP;
         K.flags = f;
     }
     return K;
@@ -267,6 +270,8 @@ sph_status check_scheme(sph_ctx* c, const sph_scheme* s) {
         return fail(c, SPH_ERR_INVALID, "rho0, c0 and gamma must be > 0");
     if (!(s->nu >= 0.0) || !(s->eta >= 0.0) || !(s->alpha >= 0.0) || !std::isfinite(s->xsph_eps))
         return fail(c, SPH_ERR_INVALID, "nu, eta, alpha must be >= 0");
+    if (s->wall_bc != SPH_WALL_DENSITY && s->wall_bc != SPH_WALL_ADAMI)
+        return fail(c, SPH_ERR_INVALID, "unknown wall condition");
     return SPH_OK;
 }
 
@@ -414,6 +419,7 @@ void enqueue_build(sph_ctx* c, int drift, int kick, int carry_rates, bool timed 
 void enqueue_eval(sph_ctx* c, int kick, bool timed = false) {
     const StepLaunch L = step_launch(c, kick);
     launch_density_pass(L, c->stream);
+    if (c->wall_pass) launch_wall_pressure(L, c->stream);
     mark(c, 5, timed);
     launch_momentum_pass(L, c->stream);
     if (!L.finalize) launch_batch_reduce(L, c->stream);
@@ -478,7 +484,8 @@ sph_status capture_step_graphs(sph_ctx* c);
 // nsteps steps in the context's mode (tables already uploaded, rates valid).
 sph_status run_steps(sph_ctx* c, int nsteps) {
     if (nsteps <= 0) return SPH_OK;
-    if (c->step_mode == SPH_STEP_PERSISTENT) return run_fused(c, nsteps);
+    // the persistent kernel has no solid-wall pressure phase: such steps run as the graph
+    if (c->step_mode == SPH_STEP_PERSISTENT && !c->wall_pass) return run_fused(c, nsteps);
     if (!c->graph[0] || c->graph_timed != c->timing) {
         sph_status s = capture_step_graphs(c);
         if (s != SPH_OK) return s;
@@ -513,7 +520,16 @@ void table_bytes(const sph_ctx* c, const sph_scheme* schemes, const double* dts,
     }
 }
 
+void drop_graphs(sph_ctx* c);
+
 sph_status upload_table(sph_ctx* c, const sph_scheme* schemes, const double* dts) {
+    bool wp = false;
+    for (int k = 0; k < ntab(c); ++k) wp |= schemes[k].wall_bc == SPH_WALL_ADAMI;
+    wp &= c->nwall > 0;
+    if (wp != c->wall_pass) {  // the captured steps hold the pass or not
+        c->wall_pass = wp;
+        drop_graphs(c);
+    }
     std::vector<unsigned char> bytes;
     if (c->dom.precision) table_bytes<float>(c, schemes, dts, bytes);
     else table_bytes<double>(c, schemes, dts, bytes);
@@ -932,10 +948,12 @@ sph_status create_impl(const sph_domain* domains, int ninst, const sph_array_des
             ue = upload(dsts[k], k);
             if (ue == cudaSuccess) ue = cudaStreamSynchronize(c->stream);
         }
-        for (int a = 0; a < n_arrays; ++a)
+        for (int a = 0; a < n_arrays; ++a) {
             for (int64_t i = 0; i < arrays[a].n; ++i)
                 tag[c->arr_off[a] + i] = (uint32_t)(c->arr_off[a] + i) |
                                          (arrays[a].role == SPH_ROLE_WALL ? WALL_BIT : 0u);
+            if (arrays[a].role == SPH_ROLE_WALL) c->nwall += (int)arrays[a].n;
+        }
         if (ue == cudaSuccess)
             ue = cudaMemcpyAsync(S.tag, tag.data(), N * 4, cudaMemcpyHostToDevice, c->stream);
         // zero rates and the unused axes of both sets, the control block and the history
@@ -1322,7 +1340,10 @@ sph_status sph_kernels_per_step(const sph_ctx* ctx, const sph_scheme* scheme, in
     // (+ the per-instance reduction of a batch)
     // graph: keys + histograms, one launch per radix pass, reorder + cell table, density
     // pass, momentum pass (+ the two-stage per-instance reduction of a batch)
-    *count = c->step_mode == SPH_STEP_PERSISTENT ? 1 : 1 + c->passes + 1 + 1 + 1 + (c->ninst ? 2 : 0);
+    const bool wp = scheme->wall_bc == SPH_WALL_ADAMI && c->nwall > 0;
+    *count = c->step_mode == SPH_STEP_PERSISTENT && !wp
+                 ? 1
+                 : 1 + c->passes + 1 + 1 + (wp ? 1 : 0) + 1 + (c->ninst ? 2 : 0);
     return SPH_OK;
 }
 
@@ -1427,7 +1448,7 @@ sph_status tune_lanes(sph_ctx* c) {
 // Times a few steps in each mode from the same state and keeps the faster mode; the
 // state, time and records are put back afterwards.
 sph_status choose_mode(sph_ctx* c) {
-    if (c->fused_bps[tindex(c->group_m)] < 1) {
+    if (c->fused_bps[tindex(c->group_m)] < 1 || c->wall_pass) {  // the wall pass: graph only
         c->step_mode = SPH_STEP_GRAPH;
         return SPH_OK;
     }
@@ -1655,6 +1676,8 @@ sph_status sph_backward(sph_ctx* c, const sph_scheme* scheme, double dt, int32_t
     if (s != SPH_OK) return s;
     if (scheme->density != SPH_DENSITY_CONTINUITY)
         return fail(c, SPH_ERR_INVALID, "the adjoint covers the continuity formulation only");
+    if (scheme->wall_bc != SPH_WALL_DENSITY)
+        return fail(c, SPH_ERR_INVALID, "the adjoint does not cover the solid-wall pressure");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, SPH_ERR_INVALID, "the adjoint needs a fixed dt > 0");
     if (K < 0) return fail(c, SPH_ERR_INVALID, "K < 0");
     int C = ckpt_every;

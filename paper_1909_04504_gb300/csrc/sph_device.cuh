@@ -23,6 +23,7 @@ constexpr int F_CONTINUITY = 1;   // Eq. continuity:sph (else summation density,
 constexpr int F_LAMINAR = 2;      // Eq. mom:sph:visc
 constexpr int F_AV = 4;           // Monaghan artificial viscosity
 constexpr int F_XSPH = 8;         // XSPH correction
+constexpr int F_WALLP = 16;       // solid-wall pressure of Adami et al. (Sec. 2.3 wall condition)
 
 constexpr int DIAG_N = 13;
 constexpr int HIST_CAP = 65536;

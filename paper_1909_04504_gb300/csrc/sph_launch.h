@@ -85,6 +85,8 @@ int pair_threads();
 void launch_pairs(const StepLaunch& L, cudaStream_t st);
 void launch_density_pass(const StepLaunch& L, cudaStream_t st);
 void launch_momentum_pass(const StepLaunch& L, cudaStream_t st);
+// Solid-wall pressure (scheme option) between the density and the momentum pass.
+void launch_wall_pressure(const StepLaunch& L, cudaStream_t st);
 constexpr int BATCH_SPLIT = 32;  // blocks per instance in the first stage of a batch reduction
 void launch_batch_reduce(const StepLaunch& L, cudaStream_t st);
 // fused_f32.cu / fused_f64.cu: the whole step as one cooperative launch (persistent blocks,

@@ -24,26 +24,49 @@ __device__ __forceinline__ int find_instance(const uint32_t* __restrict__ bounds
 __device__ __forceinline__ uint32_t drift_key_one(const ParticleSet& S, int i, const Grid& G,
                                                   const StepConst& C, double dt, int drift,
                                                   int& clamped) {
+    // every load before any store: the compiler cannot tell that the stores to x do not
+    // alias the other arrays, and interleaving them would serialise the round trips
+    const int dim = G.dim;
     const bool fluid = !(S.tag[i] & WALL_BIT);
-    int c[3] = {0, 0, 0};
-    for (int d = 0; d < G.dim; ++d) {
-        double x = S.x[d][i];
-        if (drift && fluid) {
-            double uh = S.u[d][i] + 0.5 * dt * S.a[d][i];
-            x = x + dt * (uh + S.xs[d][i]);
-            if (G.periodic[d] && !(x >= G.lo[d] && x < G.hi[d])) {
-                double k = floor(__ddiv_rn(__dsub_rn(x, G.lo[d]), G.L[d]));
-                x = __dsub_rn(x, __dmul_rn(k, G.L[d]));
-                if (x >= G.hi[d]) x = __dsub_rn(x, G.L[d]);
-                if (x < G.lo[d]) x = G.lo[d];
+    double x[3] = {0, 0, 0};
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        if (d < dim) x[d] = S.x[d][i];
+    if (drift && fluid) {
+        double u[3] = {0, 0, 0}, a[3] = {0, 0, 0}, xs[3] = {0, 0, 0};
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            if (d < dim) {
+                u[d] = S.u[d][i];
+                a[d] = S.a[d][i];
+                xs[d] = S.xs[d][i];
             }
-            S.x[d][i] = x;
-        }
-        const float xf = __double2float_rn(x);
-        const double xm = C.precision ? (double)xf : x;
-        c[d] = cell_coord_screened(xm, xf, G.lo[d], G.cs[d], G.lo_f[d], G.inv_cs_f[d], G.nc[d],
-                                   &clamped);
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            if (d < dim) {
+                const double uh = u[d] + 0.5 * dt * a[d];
+                double xn = x[d] + dt * (uh + xs[d]);
+                if (G.periodic[d] && !(xn >= G.lo[d] && xn < G.hi[d])) {
+                    const double k = floor(__ddiv_rn(__dsub_rn(xn, G.lo[d]), G.L[d]));
+                    xn = __dsub_rn(xn, __dmul_rn(k, G.L[d]));
+                    if (xn >= G.hi[d]) xn = __dsub_rn(xn, G.L[d]);
+                    if (xn < G.lo[d]) xn = G.lo[d];
+                }
+                x[d] = xn;
+            }
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            if (d < dim) S.x[d][i] = x[d];
     }
+    int c[3] = {0, 0, 0};
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        if (d < dim) {
+            const float xf = __double2float_rn(x[d]);
+            const double xm = C.precision ? (double)xf : x[d];
+            c[d] = cell_coord_screened(xm, xf, G.lo[d], G.cs[d], G.lo_f[d], G.inv_cs_f[d],
+                                       G.nc[d], &clamped);
+        }
     return (uint32_t)(c[0] + G.nc[0] * (c[1] + G.nc[1] * c[2]));
 }
 
@@ -57,32 +80,50 @@ __device__ __forceinline__ void reorder_one(const ParticleSet& in, const Particl
                                             int o, int dim, double dt, int kick, int carry_rates,
                                             typename V4<Real>::T* __restrict__ P,
                                             typename V4<Real>::T* __restrict__ Q) {
+    // every load of particle o before any store (the output arrays could alias the inputs
+    // as far as the compiler knows); the acceleration is read for walls too (it is zero
+    // there) so that no load waits for the tag
     const uint32_t tag = in.tag[o];
-    const bool fluid = !(tag & WALL_BIT);
-    double x[3] = {0, 0, 0}, u[3] = {0, 0, 0};
-    for (int d = 0; d < dim; ++d) {
-        x[d] = in.x[d][o];
-        u[d] = in.u[d][o];
-        if (kick && fluid) u[d] += 0.5 * dt * in.a[d][o];
-        out.x[d][k] = x[d];
-        out.u[d][k] = u[d];
-    }
+    double x[3] = {0, 0, 0}, u[3] = {0, 0, 0}, a[3] = {0, 0, 0}, xs[3] = {0, 0, 0};
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        if (d < dim) {
+            x[d] = in.x[d][o];
+            u[d] = in.u[d][o];
+            if (kick || carry_rates) a[d] = in.a[d][o];
+            if (carry_rates) xs[d] = in.xs[d][o];
+        }
     const double rho = in.rho[o];
     const double m = in.m[o];
+    const double arho = carry_rates ? in.arho[o] : 0.0;
+    const bool fluid = !(tag & WALL_BIT);
+    double uk[3] = {u[0], u[1], u[2]};
+    if (kick && fluid)
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            if (d < dim) uk[d] += 0.5 * dt * a[d];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        if (d < dim) {
+            out.x[d][k] = x[d];
+            out.u[d][k] = uk[d];
+        }
     out.rho[k] = rho;
     out.m[k] = m;
     out.tag[k] = tag;
     if (carry_rates) {
-        out.arho[k] = in.arho[o];
-        for (int d = 0; d < dim; ++d) {
-            out.a[d][k] = in.a[d][o];
-            out.xs[d][k] = in.xs[d][o];
-        }
+        out.arho[k] = arho;
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            if (d < dim) {
+                out.a[d][k] = a[d];
+                out.xs[d][k] = xs[d];
+            }
     }
     typename V4<Real>::T pv, qv;
     pv.x = (Real)x[0]; pv.y = (Real)x[1]; pv.z = (Real)x[2];
     pv.w = (Real)(fluid ? m : -m);
-    qv.x = (Real)u[0]; qv.y = (Real)u[1]; qv.z = (Real)u[2];
+    qv.x = (Real)uk[0]; qv.y = (Real)uk[1]; qv.z = (Real)uk[2];
     qv.w = Real(0);  // the density pass writes it
     P[k] = pv;
     Q[k] = qv;

@@ -1,0 +1,96 @@
+// Solid-wall pressure of Adami, Hu and Adams (2012), the wall boundary condition listed
+// among the schemes of Sec. 2.3 (scheme option SPH_WALL_ADAMI). Runs between the density
+// pass and the momentum pass of an evaluation: each wall particle w takes
+//   p_w = (sum_f p_f W_wf + g . sum_f rho_f (x_w - x_f) W_wf) / sum_f W_wf
+// over its fluid neighbours f (static walls: no wall acceleration) and the density the
+// Tait EOS (Eq. eos) maps to it, rho_w = rho0 (1 + p_w / B)^(1/gamma); a wall with no
+// fluid neighbour takes p_w = 0 and rho_w = rho0. The neighbours are those of the
+// density pass's list (in continuity mode a wall lists its fluid neighbours only; in
+// summation mode every neighbour, the walls among them skipped here). Fluid pressures
+// come from the pair-loop shadow, p_f = (p/rho^2)_f rho_f^2; the sums are compensated in
+// the pair-loop precision (8 lanes per wall particle, combined by a fixed shuffle tree),
+// the quotient and the EOS inversion run in FP64.
+#include "pairs_impl.cuh"
+
+namespace sph {
+
+constexpr int WALL_LANES = 8;  // lanes per particle: a wall's list is split among them
+
+template <class Real, int DIM, int KERNEL>
+__global__ void __launch_bounds__(PAIR_THREADS)
+k_wall_pressure(const typename V4<Real>::T* __restrict__ P, typename V4<Real>::T* __restrict__ Q,
+                Real* __restrict__ R, const uint32_t* __restrict__ skeys, int n,
+                const Inst<Real>* __restrict__ tab, const uint32_t* __restrict__ cell_bounds,
+                int ninst, ParticleSet S, const uint32_t* __restrict__ nl,
+                const uint32_t* __restrict__ cnt, const Control* ctl) {
+    if (ctl->status) return;
+    constexpr int T = WALL_LANES;
+    const Group<T> g;
+    const int groups = gridDim.x * (PAIR_THREADS / T);
+    for (int i = blockIdx.x * (PAIR_THREADS / T) + (int)threadIdx.x / T; i < n; i += groups) {
+        const typename V4<Real>::T pi = P[i];
+        if (pi.w > Real(0)) continue;  // fluid (uniform over the group)
+        const Inst<Real>& I = tab[find_instance(cell_bounds, ninst, skeys[i])];
+        if (!(I.K.flags & F_WALLP)) continue;
+        const Real gx = (Real)I.C.g[0], gy = (Real)I.C.g[1], gz = (Real)I.C.g[2];
+        Acc<Real> sw, sp, sg;
+        sw.zero();
+        sp.zero();
+        sg.zero();
+        const uint32_t k = cnt[i];
+        for (uint32_t kk = g.t; kk < k; kk += T) {
+            const uint32_t j = nl[(size_t)kk * n + i];
+            const typename V4<Real>::T pj = P[j];
+            if (!(pj.w > Real(0))) continue;  // wall source
+            Real dx, dy, dz;
+            const Real r2 = separation<Real, DIM>(pi, pj, I.G, I.K, dx, dy, dz);
+            const Real W = I.K.wfac * kernel_w<Real, KERNEL>(PairMath<Real>::sqrt(r2) * I.K.inv_h);
+            const Real rho_j = Q[j].w;
+            const Real gr = gx * dx + gy * dy + (DIM == 3 ? gz * dz : Real(0));
+            sw.add(W);
+            sp.add(R[j] * rho_j * rho_j * W);
+            sg.add(rho_j * gr * W);
+        }
+        group_reduce<Real, T>(sw, g);
+        group_reduce<Real, T>(sp, g);
+        group_reduce<Real, T>(sg, g);
+        if (g.t == 0) {
+            const double w = sw.value();
+            double pw = 0.0, rw = I.C.rho0;
+            if (w > 0.0) {
+                pw = (sp.value() + sg.value()) / w;
+                rw = I.C.rho0 * pow(1.0 + pw / I.C.B, 1.0 / I.C.gamma);
+            }
+            S.rho[i] = rw;
+            reinterpret_cast<Real*>(&Q[i])[3] = (Real)rw;
+            R[i] = (Real)(pw / (rw * rw));
+        }
+    }
+}
+
+template <class Real, int DIM, int KERNEL>
+static void wall_pressure_t(const StepLaunch& L, cudaStream_t st) {
+    using V = typename V4<Real>::T;
+    long long want = ((long long)L.n * WALL_LANES + PAIR_THREADS - 1) / PAIR_THREADS;
+    const long long cap = (long long)L.sms * 16;
+    const int g = (int)(want < 1 ? 1 : (want > cap ? cap : want));
+    k_wall_pressure<Real, DIM, KERNEL><<<g, PAIR_THREADS, 0, st>>>(
+        (const V*)L.P, (V*)L.Q, (Real*)L.R, L.skeys, L.n, (const Inst<Real>*)L.tab, L.cell_bounds,
+        L.ninst, L.S, L.nl, L.cnt, L.ctl);
+}
+
+void launch_wall_pressure(const StepLaunch& L, cudaStream_t st) {
+    const int sel = (L.precision ? 4 : 0) + (L.dim == 3 ? 2 : 0) + (L.kernel == WENDLAND_C2 ? 1 : 0);
+    switch (sel) {
+        case 0: wall_pressure_t<double, 2, QUINTIC>(L, st); break;
+        case 1: wall_pressure_t<double, 2, WENDLAND_C2>(L, st); break;
+        case 2: wall_pressure_t<double, 3, QUINTIC>(L, st); break;
+        case 3: wall_pressure_t<double, 3, WENDLAND_C2>(L, st); break;
+        case 4: wall_pressure_t<float, 2, QUINTIC>(L, st); break;
+        case 5: wall_pressure_t<float, 2, WENDLAND_C2>(L, st); break;
+        case 6: wall_pressure_t<float, 3, QUINTIC>(L, st); break;
+        default: wall_pressure_t<float, 3, WENDLAND_C2>(L, st); break;
+    }
+}
+
+}  // namespace sph

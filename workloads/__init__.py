@@ -80,6 +80,7 @@ class Workload:
     xsph_eps: float = 0.0
     g: List[float] = field(default_factory=lambda: [0.0, 0.0, 0.0])
     density: int = 0          # 0 continuity equation, 1 summation density
+    wall_bc: int = 0          # 0 wall density from continuity, 1 wall pressure of Adami et al.
     dt: float = 0.0
     steps: int = 1
 
@@ -102,6 +103,13 @@ class Workload:
         import copy
         w = copy.deepcopy(self)
         w.precision = precision
+        return w
+
+    def with_wall_bc(self, wall_bc: int) -> "Workload":
+        import copy
+        w = copy.deepcopy(self)
+        w.wall_bc = wall_bc
+        w.name = self.name + ("_adami" if wall_bc == 1 else "")
         return w
 
 
