@@ -614,32 +614,40 @@ __device__ __forceinline__ void momentum_finish(int i, bool fluid, const double*
                                                 const double* xs_in, const StepConst& C,
                                                 const ParticleSet& S, double dt, int kick,
                                                 MomDiag& md) {
+    // every load before any store: the state arrays could alias as far as the compiler
+    // knows, and interleaving would serialise the round trips of the epilogue
+    const double rho = S.rho[i];
     if (!fluid) {
         for (int d = 0; d < DIM; ++d) {
             S.a[d][i] = 0.0;
             S.xs[d][i] = 0.0;
         }
-        if (!isfinite(S.rho[i])) md.bad = 1u;
+        if (!isfinite(rho)) md.bad = 1u;
         return;
     }
-    double u[3] = {0, 0, 0};
+    double u[3] = {0, 0, 0}, x[3] = {0, 0, 0};
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        u[d] = S.u[d][i];
+        x[d] = S.x[d][i];
+    }
+    const double m = S.m[i];
     double u2 = 0, a2 = 0;
     bool bad = false;
+#pragma unroll
     for (int d = 0; d < DIM; ++d) {
         const double a = a_in[d] + C.g[d];
         S.a[d][i] = a;
         S.xs[d][i] = xs_in[d];
-        u[d] = S.u[d][i];
         if (kick) {
             u[d] += 0.5 * dt * a;
             S.u[d][i] = u[d];
         }
         u2 += u[d] * u[d];
         a2 += a * a;
-        bad |= !isfinite(u[d]) || !isfinite(S.x[d][i]);
+        bad |= !isfinite(u[d]) || !isfinite(x[d]);
     }
-    bad |= !isfinite(S.rho[i]) || !isfinite(a2);
-    const double m = S.m[i];
+    bad |= !isfinite(rho) || !isfinite(a2);
     md.px += m * u[0];
     md.py += m * u[1];
     md.pz += m * u[2];
