@@ -179,18 +179,27 @@ __global__ void k_adj_cot(AdjSet L, const typename V4<Real>::T* __restrict__ P, 
                           double* __restrict__ luh1, double* __restrict__ luh2, int dim) {
     double* luh[3] = {luh0, luh1, luh2};
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        // loads first (the arrays could alias as far as the compiler knows), walls zeroed
         const bool fluid = P[k].w > Real(0);
+        double la[3] = {0, 0, 0}, lu[3] = {0, 0, 0}, ls[3] = {0, 0, 0};
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            if (d < dim) {
+                la[d] = L.a[d][k];
+                lu[d] = L.u[d][k];
+                ls[d] = L.xs[d][k];
+            }
         typename V4<Real>::T ca, cs;
         double ab[3] = {0, 0, 0}, sb[3] = {0, 0, 0};
-        for (int d = 0; d < dim; ++d) {
-            if (fluid) {
-                ab[d] = L.a[d][k] + (kick ? 0.5 * dt * L.u[d][k] : 0.0);
-                sb[d] = L.xs[d][k];
-                luh[d][k] = L.u[d][k];
-            } else {
-                luh[d][k] = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            if (d < dim) {
+                if (fluid) {
+                    ab[d] = la[d] + (kick ? 0.5 * dt * lu[d] : 0.0);
+                    sb[d] = ls[d];
+                }
+                luh[d][k] = fluid ? lu[d] : 0.0;
             }
-        }
         ca.x = (Real)ab[0]; ca.y = (Real)ab[1]; ca.z = (Real)ab[2]; ca.w = Real(0);
         cs.x = (Real)sb[0]; cs.y = (Real)sb[1]; cs.z = (Real)sb[2]; cs.w = Real(0);
         CA[k] = ca;
@@ -310,11 +319,19 @@ k_adj_momentum(const typename V4<Real>::T* __restrict__ P, const typename V4<Rea
                 gal.add(g_a);
             }
         }
-        if (fluid_k)
+        if (fluid_k) {  // read-modify-write: every read before the first write
+            double lx[DIM], lu[DIM];
+#pragma unroll
             for (int d = 0; d < DIM; ++d) {
-                L.x[d][k] += gx[d].value();
-                luh[d][k] += gu[d].value();
+                lx[d] = L.x[d][k];
+                lu[d] = luh[d][k];
             }
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+                L.x[d][k] = lx[d] + gx[d].value();
+                luh[d][k] = lu[d] + gu[d].value();
+            }
+        }
         // EOS chain: d(p / rho^2)/drho = c0^2 (rho/rho0)^(gamma-1) / rho^2 - 2 p / rho^3
         const double rho = (double)qk.w;
         const double p = tait_pressure(rho, C);
@@ -389,9 +406,16 @@ k_adj_continuity(const typename V4<Real>::T* __restrict__ P, const typename V4<R
             gu[1].add(b * ry);
             if (DIM == 3) gu[2].add(b * rz);
         }
+        double lx[DIM], lu[DIM];  // read-modify-write: every read before the first write
+#pragma unroll
         for (int d = 0; d < DIM; ++d) {
-            L.x[d][k] += gx[d].value();
-            luh[d][k] += gu[d].value();
+            lx[d] = L.x[d][k];
+            lu[d] = luh[d][k];
+        }
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            L.x[d][k] = lx[d] + gx[d].value();
+            luh[d][k] = lu[d] + gu[d].value();
         }
     }
 }
@@ -404,17 +428,27 @@ __global__ void k_adj_scatter(AdjSet in, AdjSet out, const double* __restrict__ 
                               const uint32_t* __restrict__ tag, int n, int dim, double dt) {
     const double* luh[3] = {luh0, luh1, luh2};
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        // loads first (the arrays could alias as far as the compiler knows), walls zeroed
         const int o = (int)perm[k];
         const bool fluid = !(tag[k] & WALL_BIT);
-        for (int d = 0; d < dim; ++d) {
-            const double lx = fluid ? in.x[d][k] : 0.0;
-            const double lu = fluid ? luh[d][k] : 0.0;
-            out.x[d][o] = lx;
-            out.u[d][o] = lu + dt * lx;
-            out.a[d][o] = 0.5 * dt * lu + 0.5 * dt * dt * lx;
-            out.xs[d][o] = dt * lx;
-        }
-        out.rho[o] = lrho_tot[k];
+        double lx[3] = {0, 0, 0}, lu[3] = {0, 0, 0};
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            if (d < dim) {
+                lx[d] = in.x[d][k];
+                lu[d] = luh[d][k];
+            }
+        const double lr = lrho_tot[k];
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            if (d < dim) {
+                const double x = fluid ? lx[d] : 0.0, u = fluid ? lu[d] : 0.0;
+                out.x[d][o] = x;
+                out.u[d][o] = u + dt * x;
+                out.a[d][o] = 0.5 * dt * u + 0.5 * dt * dt * x;
+                out.xs[d][o] = dt * x;
+            }
+        out.rho[o] = lr;
     }
 }
 
