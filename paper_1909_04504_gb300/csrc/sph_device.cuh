@@ -147,13 +147,16 @@ __device__ __forceinline__ int cell_coord(double xm, double lo, double cs, int n
 // within that bound of q, floor(q) is the FP64 result; otherwise (about one coordinate in
 // a few thousand) the FP64 quotient decides. The FP64 pipe of this part runs at 1/64 of
 // FP32 and its divide costs many instructions, so the screen keeps it off the common path.
-__device__ __forceinline__ int cell_coord_screened(double xm, float xf, double lo, double cs,
-                                                   float lo_f, float inv_cs_f, int n,
+// x is the FP64 position and xf = x rounded to float; the binned position is xf widened
+// (to_float: FP32 pair loops) or x itself, formed only on the rare FP64 path.
+__device__ __forceinline__ int cell_coord_screened(double x, float xf, int to_float, double lo,
+                                                   double cs, float lo_f, float inv_cs_f, int n,
                                                    int* clamped) {
     const float q = (xf - lo_f) * inv_cs_f;
     const float m = 4.7683716e-7f * ((fabsf(xf) + fabsf(lo_f)) * inv_cs_f + fabsf(q) + 1.0f);
     const float lo_q = floorf(q - m), hi_q = floorf(q + m);
-    if (!(lo_q == hi_q)) return cell_coord(xm, lo, cs, n, clamped);  // near a cell edge, NaN
+    if (!(lo_q == hi_q))  // near a cell edge, NaN
+        return cell_coord(to_float ? (double)xf : x, lo, cs, n, clamped);
     if (!(lo_q >= 0.0f)) { *clamped = 1; return 0; }
     if (lo_q > (float)(n - 1)) { *clamped = 1; return n - 1; }
     return (int)lo_q;

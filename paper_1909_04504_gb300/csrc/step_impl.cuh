@@ -62,10 +62,8 @@ __device__ __forceinline__ uint32_t drift_key_one(const ParticleSet& S, int i, c
 #pragma unroll
     for (int d = 0; d < 3; ++d)
         if (d < dim) {
-            const float xf = __double2float_rn(x[d]);
-            const double xm = C.precision ? (double)xf : x[d];
-            c[d] = cell_coord_screened(xm, xf, G.lo[d], G.cs[d], G.lo_f[d], G.inv_cs_f[d],
-                                       G.nc[d], &clamped);
+            c[d] = cell_coord_screened(x[d], __double2float_rn(x[d]), C.precision, G.lo[d],
+                                       G.cs[d], G.lo_f[d], G.inv_cs_f[d], G.nc[d], &clamped);
         }
     return (uint32_t)(c[0] + G.nc[0] * (c[1] + G.nc[1] * c[2]));
 }

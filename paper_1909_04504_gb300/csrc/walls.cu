@@ -16,6 +16,25 @@ namespace sph {
 
 constexpr int WALL_LANES = 8;  // lanes per particle: a wall's list is split among them
 
+// The FP64 pipe of this part runs at 1/64 of FP32, and a warp pays for every FP64
+// instruction whatever its active lanes: the reciprocal and the EOS root start from the
+// FP32 hardware value and take one Newton step in FP64 (the FP32 start is good to a few
+// 2^-23, so one step leaves an error of order 2^-46, far below the sums' rounding).
+__device__ __forceinline__ double rcp_fp64(double x) {
+    const double r = (double)PairMath<float>::rcp((float)x);
+    return r * fma(-x, r, 2.0);
+}
+
+// x^(1/gamma): for gamma = 7 Newton's step on y^7 = x from the FP32 root; else pow.
+__device__ __forceinline__ double eos_root(double x, const StepConst& C) {
+    if (!C.gamma7) return pow(x, 1.0 / C.gamma);
+    double y = (double)powf((float)x, 1.0f / 7.0f);
+    const double y3 = y * y * y;
+    const double y6 = y3 * y3;
+    y -= fma(y6, y, -x) * (1.0 / 7.0) * rcp_fp64(y6);
+    return y;
+}
+
 template <class Real, int DIM, int KERNEL>
 __global__ void __launch_bounds__(PAIR_THREADS)
 k_wall_pressure(const typename V4<Real>::T* __restrict__ P, typename V4<Real>::T* __restrict__ Q,
@@ -58,12 +77,12 @@ k_wall_pressure(const typename V4<Real>::T* __restrict__ P, typename V4<Real>::T
             const double w = sw.value();
             double pw = 0.0, rw = I.C.rho0;
             if (w > 0.0) {
-                pw = (sp.value() + sg.value()) / w;
-                rw = I.C.rho0 * pow(1.0 + pw / I.C.B, 1.0 / I.C.gamma);
+                pw = (sp.value() + sg.value()) * rcp_fp64(w);
+                rw = I.C.rho0 * eos_root(1.0 + pw * (1.0 / I.C.B), I.C);
             }
             S.rho[i] = rw;
             reinterpret_cast<Real*>(&Q[i])[3] = (Real)rw;
-            R[i] = (Real)(pw / (rw * rw));
+            R[i] = (Real)(pw * rcp_fp64(rw * rw));
         }
     }
 }
