@@ -128,16 +128,20 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_step_fused(const FusedLaun
             __syncthreads();
             const int t = tile_s;
             if (t >= F.ntiles) break;
-            if (onesweep_items(L.n) == 4)
-                radix_onesweep_tile<4>(F.keys[cur], p ? F.vals[cur] : nullptr, F.keys[cur ^ 1],
-                                       F.vals[cur ^ 1], L.n, 8 * p, ghist + p * RADIX,
-                                       status + (size_t)p * F.ntiles * RADIX, t, sm.os,
-                                       &ctl->status, F.wait_ns);
-            else
-                radix_onesweep_tile<16>(F.keys[cur], p ? F.vals[cur] : nullptr, F.keys[cur ^ 1],
-                                        F.vals[cur ^ 1], L.n, 8 * p, ghist + p * RADIX,
-                                        status + (size_t)p * F.ntiles * RADIX, t, sm.os,
-                                        &ctl->status, F.wait_ns);
+            const uint32_t* vin = p ? F.vals[cur] : nullptr;
+            uint32_t* st_p = status + (size_t)p * F.ntiles * RADIX;
+            switch (onesweep_items(L.n)) {
+                case 4:
+                    radix_onesweep_tile<4>(F.keys[cur], vin, F.keys[cur ^ 1], F.vals[cur ^ 1], L.n,
+                                           8 * p, ghist + p * RADIX, st_p, t, sm.os, &ctl->status,
+                                           F.wait_ns);
+                    break;
+                default:
+                    radix_onesweep_tile<8>(F.keys[cur], vin, F.keys[cur ^ 1], F.vals[cur ^ 1], L.n,
+                                           8 * p, ghist + p * RADIX, st_p, t, sm.os, &ctl->status,
+                                           F.wait_ns);
+                    break;
+            }
             __syncthreads();
         }
         if (!grid_sync(ctl, F.wait_ns)) return;

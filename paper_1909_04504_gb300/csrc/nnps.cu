@@ -354,14 +354,20 @@ int launch_onesweep(int n, uint32_t* keys[2], uint32_t* vals[2], int passes, uin
     uint32_t* status = counters + 32;
     int cur = 0;
     for (int p = 0; p < passes; ++p) {
-        if (onesweep_items(n) == 4)
-            k_radix_onesweep<4><<<ntiles, SORT_THREADS, 0, st>>>(
-                keys[cur], p == 0 ? nullptr : vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, 8 * p,
-                ghist + p * RADIX, status + (size_t)p * ntiles * RADIX, counters + p, ctl, wait_ns);
-        else
-            k_radix_onesweep<16><<<ntiles, SORT_THREADS, 0, st>>>(
-                keys[cur], p == 0 ? nullptr : vals[cur], keys[cur ^ 1], vals[cur ^ 1], n, 8 * p,
-                ghist + p * RADIX, status + (size_t)p * ntiles * RADIX, counters + p, ctl, wait_ns);
+        const uint32_t* vin = p == 0 ? nullptr : vals[cur];
+        uint32_t* st_p = status + (size_t)p * ntiles * RADIX;
+        switch (onesweep_items(n)) {
+            case 4:
+                k_radix_onesweep<4><<<ntiles, SORT_THREADS, 0, st>>>(
+                    keys[cur], vin, keys[cur ^ 1], vals[cur ^ 1], n, 8 * p, ghist + p * RADIX,
+                    st_p, counters + p, ctl, wait_ns);
+                break;
+            default:
+                k_radix_onesweep<8><<<ntiles, SORT_THREADS, 0, st>>>(
+                    keys[cur], vin, keys[cur ^ 1], vals[cur ^ 1], n, 8 * p, ghist + p * RADIX,
+                    st_p, counters + p, ctl, wait_ns);
+                break;
+        }
         cur ^= 1;
     }
     return cur;

@@ -165,8 +165,9 @@ __device__ __forceinline__ unsigned long long sort_clock_ns() {
 }
 
 // Keys per thread of a one-sweep tile: small problems take short tiles (more blocks,
-// shorter serial ranking loops), large ones long tiles (fewer look-back steps).
-__host__ __device__ __forceinline__ int onesweep_items(int n) { return n <= 131072 ? 4 : 16; }
+// shorter serial ranking loops), large ones tiles of 2,048 keys (8 per thread: 79
+// registers, three blocks per SM; 16 per thread needed 128 and ran slower).
+__host__ __device__ __forceinline__ int onesweep_items(int n) { return n <= 131072 ? 4 : 8; }
 __host__ __device__ __forceinline__ int onesweep_tiles(int n) {
     const int tile = SORT_THREADS * onesweep_items(n);
     const int t = (n + tile - 1) / tile;
