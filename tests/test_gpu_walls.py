@@ -146,3 +146,23 @@ def test_persistent_form_runs_the_graph_and_adjoint_refuses():
         assert b.kernels_per_step(sch) == b.kernels_per_step(sch0) + 1
         with pytest.raises(G.SphError):
             b.backward(sch, wl.dt, 3)
+
+
+@pytest.mark.parametrize("wall_bc", [0, 1])
+@pytest.mark.parametrize("prec", [G.PREC_FP64, G.PREC_FP32])
+def test_summation_density_with_walls(wall_bc, prec):
+    """Summation density (Eq. 2) on the dam break: walls sum every neighbour (continuity
+    walls) or take the solid-wall pressure after the summation."""
+    wl = copy.deepcopy(oracle_wl(W.dam_break_2d(dx=0.02), prec)).with_wall_bc(wall_bc)
+    wl.density = G.SUMMATION
+    s = O.state_of(wl)
+    ref = O.rhs(wl, s)
+    st, _ = O.run(wl, s, wl.dt, 3)
+    with sim_of(wl) as sim:
+        sim.eval_rhs(G.scheme_of(wl))
+        assert _close(prec, sim.get("rho"), ref["rho"])
+        for k in RATES_2D[1:]:
+            assert _close(prec, sim.get(k), ref[k]), k
+        sim.step(G.scheme_of(wl), wl.dt, 3)
+        for k in FIELDS_2D:
+            assert _close(prec, sim.get(k), st[k]), k
