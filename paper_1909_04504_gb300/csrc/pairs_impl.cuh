@@ -735,10 +735,11 @@ __device__ __forceinline__ void momentum_tiles(int block, int nblocks,
     }
 }
 
-// FP32: 8 blocks of 128 per SM (64 registers; the gathers of the pair loop are latency-
-// bound and gain more from the extra warps than the few spills cost); FP64: 5.
+// FP32: 8 blocks of 128 per SM in 2D (64 registers; the gathers of the pair loop are
+// latency-bound and gain more from the extra warps than the few spills cost), 7 in 3D
+// (72 registers: fewer spills of the longer 3D body measured faster); FP64: 5.
 template <class Real, int DIM, int KERNEL, int T>
-__global__ void __launch_bounds__(PAIR_THREADS, sizeof(Real) == 4 ? 8 : 5)
+__global__ void __launch_bounds__(PAIR_THREADS, sizeof(Real) == 4 ? (DIM == 3 ? 7 : 8) : 5)
 k_momentum(const typename V4<Real>::T* __restrict__ P, const typename V4<Real>::T* __restrict__ Q,
            const Real* __restrict__ R, const uint32_t* __restrict__ skeys, int n,
            const Inst<Real>* __restrict__ tab, const uint32_t* __restrict__ cell_bounds, int ninst,
