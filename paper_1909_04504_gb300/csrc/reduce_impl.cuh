@@ -56,45 +56,87 @@ __device__ __forceinline__ void finish_single(Control* ctl, double* __restrict__
 
 // FP64 diagnostics of the particles [b, e) of the cell order (one block of NT threads,
 // red: NT/32 x 10 doubles of shared memory), in a fixed order; valid in thread 0:
-// px py pz ke max|u|^2 max|a|^2 bad pairs candidates wall-pairs.
+// px py pz ke max|u|^2 max|a|^2 bad pairs candidates wall-pairs. Only the momentum and
+// kinetic-energy sums use the FP64 pipe (1/64 of the FP32 rate on this part): counts,
+// flags and maxima (the bit pattern of a non-negative double orders like the double)
+// reduce as integers, as in the single-problem reduction.
 template <int NT>
 __device__ __forceinline__ void batch_partial(const ParticleSet& S,
                                               const uint32_t* __restrict__ pcount, uint32_t b,
                                               uint32_t e, int dim, double* o, double (*red)[10]) {
-    double v[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    double px = 0, py = 0, pz = 0, ke = 0;
+    unsigned long long u2b = 0, a2b = 0, np = 0, nc = 0, nw = 0;
+    unsigned bad = 0;
     for (uint32_t k = b + threadIdx.x; k < e; k += NT) {
         const bool fluid = !(S.tag[k] & WALL_BIT);
-        const double np = (double)pcount[2 * (size_t)k], nc = (double)pcount[2 * (size_t)k + 1];
-        v[7] += np;
-        v[8] += nc;
+        const uint32_t pk = pcount[2 * (size_t)k], ck = pcount[2 * (size_t)k + 1];
+        const double rho = S.rho[k];
+        np += pk;
+        nc += ck;
         if (!fluid) {
-            v[9] += np;
-            if (!isfinite(S.rho[k])) v[6] = 1.0;
+            nw += pk;
+            bad |= !isfinite(rho);
             continue;
         }
+        double u[3] = {0, 0, 0}, a[3] = {0, 0, 0}, x[3] = {0, 0, 0};
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            if (d < dim) {
+                u[d] = S.u[d][k];
+                a[d] = S.a[d][k];
+                x[d] = S.x[d][k];
+            }
+        const double m = S.m[k];
         double u2 = 0, a2 = 0;
-        for (int d = 0; d < dim; ++d) {
-            const double u = S.u[d][k], a = S.a[d][k];
-            u2 += u * u;
-            a2 += a * a;
-            if (d == 0) v[0] += S.m[k] * u;
-            if (d == 1) v[1] += S.m[k] * u;
-            if (d == 2) v[2] += S.m[k] * u;
-            if (!isfinite(u) || !isfinite(S.x[d][k])) v[6] = 1.0;
+        bool bk = !isfinite(rho);
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            if (d < dim) {
+                u2 += u[d] * u[d];
+                a2 += a[d] * a[d];
+                bk |= !isfinite(u[d]) || !isfinite(x[d]);
+            }
+        bk |= !isfinite(a2);
+        px += m * u[0];
+        py += m * u[1];
+        pz += m * u[2];
+        ke += 0.5 * m * u2;
+        if (bk) bad = 1u;
+        else {
+            u2b = u2b > (unsigned long long)__double_as_longlong(u2) ? u2b
+                                                                    : (unsigned long long)__double_as_longlong(u2);
+            a2b = a2b > (unsigned long long)__double_as_longlong(a2) ? a2b
+                                                                    : (unsigned long long)__double_as_longlong(a2);
         }
-        if (!isfinite(S.rho[k]) || !isfinite(a2)) v[6] = 1.0;
-        v[3] += 0.5 * S.m[k] * u2;
-        v[4] = fmax(v[4], u2);
-        v[5] = fmax(v[5], a2);
     }
-    for (int o2 = 16; o2 > 0; o2 >>= 1)
-        for (int q = 0; q < 10; ++q) {
-            const double y = __shfl_down_sync(0xffffffffu, v[q], o2);
-            v[q] = (q >= 4 && q <= 6) ? fmax(v[q], y) : v[q] + y;
-        }
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1) {
+        px += __shfl_down_sync(0xffffffffu, px, o2);
+        py += __shfl_down_sync(0xffffffffu, py, o2);
+        pz += __shfl_down_sync(0xffffffffu, pz, o2);
+        ke += __shfl_down_sync(0xffffffffu, ke, o2);
+        const unsigned long long ou = __shfl_down_sync(0xffffffffu, u2b, o2);
+        const unsigned long long oa = __shfl_down_sync(0xffffffffu, a2b, o2);
+        u2b = u2b > ou ? u2b : ou;
+        a2b = a2b > oa ? a2b : oa;
+        np += __shfl_down_sync(0xffffffffu, np, o2);
+        nc += __shfl_down_sync(0xffffffffu, nc, o2);
+        nw += __shfl_down_sync(0xffffffffu, nw, o2);
+        bad |= __shfl_down_sync(0xffffffffu, bad, o2);
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0)
-        for (int q = 0; q < 10; ++q) red[warp][q] = v[q];
+    if (lane == 0) {
+        red[warp][0] = px;
+        red[warp][1] = py;
+        red[warp][2] = pz;
+        red[warp][3] = ke;
+        red[warp][4] = __longlong_as_double((long long)u2b);
+        red[warp][5] = __longlong_as_double((long long)a2b);
+        red[warp][6] = bad ? 1.0 : 0.0;
+        red[warp][7] = (double)np;
+        red[warp][8] = (double)nc;
+        red[warp][9] = (double)nw;
+    }
     __syncthreads();
     if (threadIdx.x == 0)
         for (int q = 0; q < 10; ++q) {
