@@ -6,7 +6,7 @@
 // an instance of a batch computes bitwise what its single run computes.
 #include "sph_device.cuh"
 #include "sph_launch.h"
-#include "reduce_impl.cuh"
+#include "batch_impl.cuh"
 
 namespace sph {
 

@@ -15,7 +15,7 @@
 #pragma once
 
 #include "pairs_impl.cuh"
-#include "reduce_impl.cuh"
+#include "batch_impl.cuh"
 #include "sort_impl.cuh"
 #include "step_impl.cuh"
 
