@@ -96,6 +96,7 @@ struct sph_ctx {
     int fused_bps[4] = {0, 0, 0, 0};  // persistent kernel: blocks per SM for T = 1, 2, 4, 8
     double* fpart = nullptr;          // persistent kernel: per-block partials
     uint32_t* sort_work = nullptr;    // one-sweep sort: histograms, counters, look-back words
+    bool work_dirty = true;           // a build may have stopped before clearing sort_work
     double* bpart = nullptr;          // batch: partial diagnostics per instance
     unsigned long long wait_ns = 1000000000ull;  // limit of one device-side wait
     bool last_fused = false;          // the last step ran as one persistent launch
@@ -396,8 +397,18 @@ StepLaunch step_launch(sph_ctx* c, int kick) {
 
 // Neighbour build: [drift] + keys, radix sort, gather into the other set (+EOS shadow),
 // cell table. Enqueued on the context stream (capturable); constants from the table.
+// The sort workspace is zero after every completed build (the reorder kernel clears it);
+// it is cleared on the stream only when a build may have stopped part-way. Called before
+// graph capture and before graph launches, so captured steps hold no memset of it.
+cudaError_t clear_work_if_dirty(sph_ctx* c) {
+    if (!c->work_dirty) return cudaSuccess;
+    c->work_dirty = false;
+    return cudaMemsetAsync(c->sort_work, 0, sort_work_words(c->N, c->passes) * 4, c->stream);
+}
+
 void enqueue_build(sph_ctx* c, int drift, int kick, int carry_rates, bool timed = false) {
     cudaStream_t st = c->stream;
+    clear_work_if_dirty(c);
     cudaMemsetAsync(&c->ctl->outside, 0, sizeof(unsigned), st);
     StepLaunch L = step_launch(c, kick);
     mark(c, 0, timed);
@@ -409,7 +420,8 @@ void enqueue_build(sph_ctx* c, int drift, int kick, int carry_rates, bool timed 
     const int nxt = c->cur ^ 1;
     L.S = c->set[nxt];
     L.skeys = c->skeys;
-    launch_reorder(L, c->vals[b], carry_rates, c->off, c->G.ncells, st);
+    launch_reorder(L, c->vals[b], carry_rates, c->off, c->G.ncells, c->sort_work,
+                   (int)sort_work_words(c->N, c->passes), st);
     mark(c, 3, timed);  // the cell table is written by the reorder kernel
     mark(c, 4, timed);
     c->cur = nxt;
@@ -490,6 +502,7 @@ sph_status run_steps(sph_ctx* c, int nsteps) {
         sph_status s = capture_step_graphs(c);
         if (s != SPH_OK) return s;
     }
+    CK(clear_work_if_dirty(c));
     for (int k = 0; k < nsteps; ++k) {
         CK(cudaGraphLaunch(c->graph[c->cur], c->stream));
         c->cur ^= 1;
@@ -549,6 +562,7 @@ sph_status sync_status(sph_ctx* c) {
     CK(cudaMemcpyAsync(&status, &c->ctl->status, sizeof status, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     CK(cudaGetLastError());
+    if (status) c->work_dirty = true;
     if (status & ST_NONFINITE) return fail(c, SPH_ERR_NONFINITE, "non-finite state detected");
     if (status & ST_TIMEOUT) return fail(c, SPH_ERR_TIMEOUT, "device wait timed out");
     if (status & ST_CAPACITY)
@@ -625,6 +639,7 @@ sph_status initial_eval(sph_ctx* c, const sph_scheme* s, double dt_fixed) {
 // the buffers, the tile shape or the timing mode change (drop_graphs).
 sph_status capture_step_graphs(sph_ctx* c) {
     drop_graphs(c);
+    CK(clear_work_if_dirty(c));  // outside the capture
     const int cur0 = c->cur;
     for (int k = 0; k < 2; ++k) {
         c->cur = cur0 ^ k;
@@ -1041,6 +1056,7 @@ sph_status batch_initial_eval(sph_ctx* c) {
         CK(cudaStreamSynchronize(c->stream));
         if (!(status & ST_CAPACITY)) break;
         CK(cudaMemsetAsync(&c->ctl->status, 0, sizeof(unsigned), c->stream));
+        c->work_dirty = true;
         sph_status s = grow_list(c, c->maxn * 2);
         if (s != SPH_OK) return s;
     }
@@ -1743,6 +1759,7 @@ sph_status sph_backward(sph_ctx* c, const sph_scheme* scheme, double dt, int32_t
     // recomputed), the others are recomputed from their checkpoints
     auto seg_begin = [&](int sg) { return sg == 0 ? 0 : K - (nseg - sg) * C; };
     const int taped0 = nseg > 0 ? seg_begin(nseg - 1) : K;
+    CK(clear_work_if_dirty(c));
     for (int sg = 0, step = 0; step < K; ++step) {
         if (sg < nseg - 1 && step == seg_begin(sg)) CK(snap_save(c, ck[sg++]));
         CK(cudaGraphLaunch(c->graph[c->cur], c->stream));
@@ -1782,6 +1799,8 @@ sph_status sph_backward(sph_ctx* c, const sph_scheme* scheme, double dt, int32_t
         if (seg < nseg - 1) {  // recompute from the checkpoint, taping each step
             CK(snap_load(c, ck[seg]));
             CK(cudaMemsetAsync(&c->ctl->status, 0, sizeof(unsigned), c->stream));
+            c->work_dirty = true;
+            CK(clear_work_if_dirty(c));
             CK(cudaMemcpyAsync(&c->ctl->dt, &dt, sizeof dt, cudaMemcpyHostToDevice, c->stream));
             for (int step = s0; step < s1; ++step) {
                 CK(cudaGraphLaunch(c->graph[c->cur], c->stream));
@@ -1871,6 +1890,7 @@ sph_status sph_set(sph_ctx* c, int32_t array, const char* prop, const double* in
         launch_wrap_all(c->set[c->cur], c->N, c->G, c->stream, c->sms);
     CK(cudaGetLastError());
     CK(cudaMemsetAsync(&c->ctl->status, 0, sizeof(unsigned), c->stream));
+        c->work_dirty = true;
     CK(cudaStreamSynchronize(c->stream));
     c->have_rates = false;
     c->nbr_valid = false;
@@ -1965,6 +1985,7 @@ sph_status sph_load_state(sph_ctx* c, const void* buf, size_t bytes) {
     for (int k = 0; k < 15; ++k)
         CK(cudaMemcpyAsync(fields[k], p + (size_t)k * N * 8, N * 8, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(S.tag, p + 15 * N * 8, N * 4, cudaMemcpyHostToDevice, c->stream));
+    c->work_dirty = true;
     Control ctl{};
     ctl.t = H.t;
     ctl.dt = H.dt;

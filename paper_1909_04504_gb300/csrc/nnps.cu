@@ -132,14 +132,19 @@ __global__ void k_reorder(ParticleSet in, ParticleSet out, const uint32_t* __res
                           const Inst<Real>* __restrict__ tab, const uint32_t* __restrict__ cell_bounds,
                           int ninst, const double* __restrict__ idt, int kick, int carry_rates,
                           typename V4<Real>::T* __restrict__ P, typename V4<Real>::T* __restrict__ Q,
-                          uint32_t* __restrict__ off, int ncells, const Control* ctl) {
+                          uint32_t* __restrict__ off, int ncells, uint32_t* __restrict__ work,
+                          int work_words, const Control* ctl) {
     if (ctl->status) return;
     // cell table: four consecutive cells per thread, their previous offsets read and the
     // new ones written as one 16-byte word (grids with many more cells than particles,
-    // as the half-size cells of 3D, would otherwise take several loop trips per thread)
+    // as the half-size cells of 3D, would otherwise take several loop trips per thread);
+    // the sort passes are done, so their workspace (histograms, tile counters, look-back
+    // words) is cleared here for the next build instead of by a separate memset
     const int nq = (ncells + 4) / 4;
-    const int m = n > nq ? n : nq;
+    int m = n > nq ? n : nq;
+    m = m > work_words ? m : work_words;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
+        if (k < work_words) work[k] = 0u;
         if (k < n) {
             const int inst = find_instance(cell_bounds, ninst, skeys[k]);
             reorder_one<Real>(in, out, k, (int)perm[k], dim, idt[inst], kick, carry_rates, P, Q);
@@ -311,20 +316,21 @@ void launch_cell_offsets(const uint32_t* skeys, int n, int ncells, uint32_t* off
 }
 
 void launch_reorder(const StepLaunch& L, const uint32_t* perm, int carry_rates, uint32_t* off,
-                    int ncells, cudaStream_t st) {
+                    int ncells, uint32_t* work, int work_words, cudaStream_t st) {
     const int nq = (ncells + 4) / 4;
-    const int m = L.n > nq ? L.n : nq;
+    int m = L.n > nq ? L.n : nq;
+    m = m > work_words ? m : work_words;
     const int g = grid_for(m, 256, L.sms * 8);
     if (L.precision)
         k_reorder<float><<<g, 256, 0, st>>>(L.Sin, L.S, perm, L.skeys, L.n, L.dim,
                                             (const Inst<float>*)L.tab, L.cell_bounds, L.ninst, L.idt,
                                             L.kick, carry_rates, (F4*)L.P, (F4*)L.Q, off, ncells,
-                                            L.ctl);
+                                            work, work_words, L.ctl);
     else
         k_reorder<double><<<g, 256, 0, st>>>(L.Sin, L.S, perm, L.skeys, L.n, L.dim,
                                              (const Inst<double>*)L.tab, L.cell_bounds, L.ninst,
                                              L.idt, L.kick, carry_rates, (D4*)L.P, (D4*)L.Q, off,
-                                             ncells, L.ctl);
+                                             ncells, work, work_words, L.ctl);
 }
 
 size_t sort_work_words(int n, int passes) {
@@ -334,7 +340,6 @@ size_t sort_work_words(int n, int passes) {
 // Zeroes the sort workspace, then drift + keys + the digit histograms of all passes.
 void launch_keys_hist(const StepLaunch& L, int drift, uint32_t* keys0, int passes, uint32_t* work,
                       cudaStream_t st) {
-    cudaMemsetAsync(work, 0, sort_work_words(L.n, passes) * 4, st);
     const int g = grid_for(L.n, 256, L.sms * 8);
     if (L.precision)
         k_keys_hist<float><<<g, 256, 0, st>>>(L.Sin, L.n, (const Inst<float>*)L.tab, L.id_bounds,

@@ -74,7 +74,7 @@ struct StepLaunch {
 void launch_drift_keys(const StepLaunch& L, int drift, uint32_t* keys, cudaStream_t st);
 // Gather into cell order (reorder + EOS shadow) and the cell table off[0..ncells].
 void launch_reorder(const StepLaunch& L, const uint32_t* perm, int carry_rates, uint32_t* off,
-                    int ncells, cudaStream_t st);
+                    int ncells, uint32_t* work, int work_words, cudaStream_t st);
 // Sort workspace (digit histograms, tile counters, look-back words) in 32-bit words.
 size_t sort_work_words(int n, int passes);
 void launch_keys_hist(const StepLaunch& L, int drift, uint32_t* keys0, int passes, uint32_t* work,
