@@ -150,6 +150,39 @@ def test_artificial_viscosity_only_acts_on_approaching_pairs():
     assert np.max(np.abs(r["ax"][inner])) > 0.0
 
 
+@pytest.mark.parametrize("kind,tol", [(W.QUINTIC, 2e-3), (W.WENDLAND_C2, 5e-3)])
+def test_artificial_viscosity_magnitude(kind, tol):
+    """Magnitude of the Monaghan AV term at rho0, in 2D. With u = (g x^2, 0) on x < 0
+    every pair approaches (v_ij . r_ij = g s_x^2 (2 x_i + s_x) < 0 for s = x_j - x_i
+    within the support), so the term is linear in the velocity field and its lattice sum
+    tends to the integral over the support. The part odd in s_x cancels, which leaves
+      a_x = -alpha c0 h g int s_x^4 F(s) / (s^2 + eps h^2) dV
+          = -(3/8) alpha c0 h g int r^4 F(r) / (r^2 + eps h^2) 2 pi r dr,
+    F = (dW/dr) / r, eps = 0.01. The lattice error falls with h/dx (2e-2 at 1.3,
+    7e-4 at 3.0 for the quintic); at h/dx = 3 the tolerance is tight enough to tell the
+    eps term (a 1 % effect), a factor on h or c0, or a wrong sign."""
+    wl, s, _ = block(kind, hdx=3.0, n=60)
+    s = dict(s)
+    s["x"] = s["x"] - 1.5
+    wl.lo = [-2.0, -1.0, 0.0]
+    h = wl.h
+    kh = (3.0 if kind == W.QUINTIC else 2.0) * h
+    inner = ((s["x"] > -1.5 + kh) & (s["x"] < -0.5 - kh)
+             & (s["y"] > kh) & (s["y"] < 1.0 - kh))
+    g, alpha, eps = 0.5, 0.1, 0.01
+    r = O.rhs(wl, with_(s, u=g * s["x"] ** 2), alpha=alpha)
+
+    def F(q):
+        return O.kernel(kind, 2, h, q)[1] / q
+
+    I = integrate.quad(lambda q: q ** 5 * F(q) / (q * q + eps * h * h) * 2 * math.pi,
+                       0.0, kh, limit=400)[0]
+    expect = -0.375 * alpha * wl.c0 * h * g * I
+    assert expect > 0.0 and inner.sum() > 1000
+    assert np.max(np.abs(r["ax"][inner] / expect - 1.0)) < tol
+    assert np.max(np.abs(r["ay"][inner])) < 1e-12 * expect
+
+
 def test_dam_break_first_step_closed_form():
     """At t = 0 (rho = rho0 so p = 0, u = 0) every fluid particle has a = g, arho = 0.
     After the first kick-drift-kick step, particles with no wall neighbour have
