@@ -47,7 +47,7 @@ def build(force: bool = False) -> str:
 class Params(C.Structure):
     _fields_ = [("dim", C.c_int32), ("kernel", C.c_int32), ("precision", C.c_int32),
                 ("density", C.c_int32), ("periodic", C.c_int32 * 3), ("brute", C.c_int32),
-                ("wall_bc", C.c_int32), ("h", C.c_double), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+                ("wall_bc", C.c_int32), ("integrator", C.c_int32), ("h", C.c_double), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
                 ("rho0", C.c_double), ("c0", C.c_double), ("gamma", C.c_double),
                 ("nu", C.c_double), ("eta", C.c_double), ("alpha", C.c_double),
                 ("xsph_eps", C.c_double), ("g", C.c_double * 3)]
@@ -93,6 +93,7 @@ def params(wl, brute: bool = False, **over) -> Params:
         p.g[d] = float(wl.g[d])
     p.brute = int(brute)
     p.wall_bc = int(getattr(wl, "wall_bc", 0))
+    p.integrator = int(getattr(wl, "integrator", 0))
     p.h = wl.h
     p.rho0, p.c0, p.gamma = wl.rho0, wl.c0, wl.gamma
     p.nu, p.eta, p.alpha, p.xsph_eps = wl.nu, wl.eta, wl.alpha, wl.xsph_eps

@@ -32,6 +32,9 @@
  *  - predictor-corrector as kick-drift-kick for u and x; the density advanced like the
  *    positions with the continuity rate at (x^{n+1}, u^{n+1/2}) before the momentum
  *    evaluation at (x^{n+1}, u^{n+1/2}, rho^{n+1});
+ *  - (option) the two-evaluation midpoint predict-evaluate-correct form of the same
+ *    integrator (Monaghan 2005): a half step with the rates at t^n, the rates at the
+ *    midpoint, a full step from t^n with those, then the rates at t^{n+1};
  *  - walls static (x and u fixed), wall density from continuity with fluid sources, or
  *    (option) the wall pressure of Adami et al. (2012) with the density from the EOS.
  */
@@ -52,6 +55,7 @@ constexpr int ROLE_FLUID = 0;
 constexpr int PREC_FP32 = 1;
 constexpr int DENSITY_SUMMATION = 1;
 constexpr int WALL_ADAMI = 1;
+constexpr int INTEGRATOR_PEC = 1;
 constexpr double PI = 3.14159265358979323846;
 
 /* ---------------------------------------------------------------- dual numbers */
@@ -103,6 +107,7 @@ typedef struct {
     int32_t periodic[3];  // per axis
     int32_t brute;        // 1: neighbour search by all-pairs loop instead of cells
     int32_t wall_bc;      // 0: wall density from continuity, 1: wall pressure of Adami et al.
+    int32_t integrator;   // 0: kick-drift-kick, 1: midpoint predict-evaluate-correct
     double h;             // smoothing length
     double lo[3], hi[3];  // cell box (periodic box on periodic axes)
     double rho0, c0, gamma;
@@ -606,6 +611,45 @@ double cfl_dt(const ora_params* P, double umax, double amax) {
  * forward-Euler map of the acoustic pair (u, rho) and diverges.) Walls keep x and
  * u; their density is advanced. With summation density the RHS replaces rho.
  */
+/* The midpoint predict-evaluate-correct form (Monaghan 2005), two evaluations per step.
+ * R holds the rates at t^n on entry and at t^{n+1} on return:
+ *   u* = u^n + dt/2 a^n,  x* = wrap(x^n + dt/2 (u^n + xsph^n)),  rho* = rho^n + dt/2 arho^n,
+ *   (arho, a, xsph)* = RHS(x*, u*, rho*),
+ *   u^{n+1} = u^n + dt a*,  x^{n+1} = wrap(x^n + dt (u^n + dt/2 a* + xsph*)),
+ *   rho^{n+1} = rho^n + dt arho*,
+ *   (arho, a, xsph)^{n+1} = RHS(x^{n+1}, u^{n+1}, rho^{n+1}).
+ * x^n + dt (u^n + dt/2 a*) is the corrected midpoint velocity carried over the full
+ * step. Walls keep x and u and have their density advanced like the fluid's; with
+ * summation density every RHS replaces rho and the density is not integrated. */
+template <class T>
+void pec_step(const ora_params* P, T nu, T alpha, int64_t n, State<T>& S, const double* m,
+              const uint8_t* role, Rates<T>& R, Counts& c, double dt) {
+    const int dim = P->dim;
+    const bool cont = P->density != DENSITY_SUMMATION;
+    State<T> S0 = S;
+    for (int64_t i = 0; i < n; ++i) {
+        if (role[i] == ROLE_FLUID)
+            for (int d = 0; d < dim; ++d) {
+                S.u[d][i] = S0.u[d][i] + 0.5 * dt * R.a[d][i];
+                T xh = S0.x[d][i] + 0.5 * dt * (S0.u[d][i] + R.xs[d][i]);
+                S.x[d][i] = P->periodic[d] ? wrap_t(xh, P->lo[d], P->hi[d]) : xh;
+            }
+        if (cont) S.rho[i] = S0.rho[i] + 0.5 * dt * R.arho[i];
+    }
+    rhs(P, nu, alpha, n, S, m, role, R, &c, 0.0);
+    for (int64_t i = 0; i < n; ++i) {
+        if (role[i] == ROLE_FLUID)
+            for (int d = 0; d < dim; ++d) {
+                T ubar = S0.u[d][i] + 0.5 * dt * R.a[d][i];
+                T xn = S0.x[d][i] + dt * (ubar + R.xs[d][i]);
+                S.x[d][i] = P->periodic[d] ? wrap_t(xn, P->lo[d], P->hi[d]) : xn;
+                S.u[d][i] = S0.u[d][i] + dt * R.a[d][i];
+            }
+        if (cont) S.rho[i] = S0.rho[i] + dt * R.arho[i];
+    }
+    rhs(P, nu, alpha, n, S, m, role, R, &c, 0.0);
+}
+
 template <class T>
 double run(const ora_params* P, T nu, T alpha, int64_t n, State<T>& S, const double* m,
            const uint8_t* role, double dt_fixed, int nsteps, double* hist, Rates<T>* R_out) {
@@ -622,6 +666,13 @@ double run(const ora_params* P, T nu, T alpha, int64_t n, State<T>& S, const dou
     if (hist) std::memcpy(hist, rec.data(), sizeof(double) * HIST);
     for (int step = 0; step < nsteps; ++step) {
         double dt = dt_fixed > 0.0 ? dt_fixed : cfl_dt(P, rec[3], rec[7]);
+        if (P->integrator == INTEGRATOR_PEC) {
+            pec_step(P, nu, alpha, n, S, m, role, R, c, dt);
+            t += dt;
+            diagnostics(P, n, S, R, m, role, t, dt, c, rec.data());
+            if (hist) std::memcpy(hist + (size_t)(step + 1) * HIST, rec.data(), sizeof(double) * HIST);
+            continue;
+        }
         for (int64_t i = 0; i < n; ++i) {
             if (role[i] == ROLE_FLUID) {
                 for (int d = 0; d < dim; ++d) {
@@ -796,6 +847,7 @@ int ora_grad(const ora_params* P, int64_t n, const double* x, const double* y, c
     int rc = make_grid(P, &G);
     if (rc) return rc;
     if (!(dt > 0.0)) return -3;
+    if (P->integrator != 0) return -4;  // derivative of the kick-drift-kick map only
     const double* cx[3] = {x, y, z};
     const double* cu[3] = {u, v, w};
     const double* dirs[3] = {du, dv, dw};

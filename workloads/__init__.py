@@ -81,6 +81,7 @@ class Workload:
     g: List[float] = field(default_factory=lambda: [0.0, 0.0, 0.0])
     density: int = 0          # 0 continuity equation, 1 summation density
     wall_bc: int = 0          # 0 wall density from continuity, 1 wall pressure of Adami et al.
+    integrator: int = 0       # 0 kick-drift-kick, 1 midpoint predict-evaluate-correct
     dt: float = 0.0
     steps: int = 1
 
@@ -110,6 +111,13 @@ class Workload:
         w = copy.deepcopy(self)
         w.wall_bc = wall_bc
         w.name = self.name + ("_adami" if wall_bc == 1 else "")
+        return w
+
+    def with_integrator(self, integrator: int) -> "Workload":
+        import copy
+        w = copy.deepcopy(self)
+        w.integrator = integrator
+        w.name = self.name + ("_pec" if integrator == 1 else "")
         return w
 
 
