@@ -36,9 +36,11 @@ SMS = 152
 SM_MAX_MHZ = 2070.0
 
 
-def workload(name: str, wall_bc: str = "density"):
+def workload(name: str, wall_bc: str = "density", integrator: str = "kdk"):
     """The workload, or for the batched configuration the list of its instances; with
-    wall_bc "adami" the solid-wall pressure condition replaces the continuity walls."""
+    wall_bc "adami" the solid-wall pressure condition replaces the continuity walls, with
+    integrator "pec" the midpoint predict-evaluate-correct form (single problems only)
+    replaces kick-drift-kick."""
     import workloads as W
     table = {
         "dam_break_2d": lambda: W.dam_break_2d(),
@@ -50,6 +52,10 @@ def workload(name: str, wall_bc: str = "density"):
     wl = table[name]()
     if wall_bc == "adami":
         wl = [w.with_wall_bc(1) for w in wl] if isinstance(wl, list) else wl.with_wall_bc(1)
+    if integrator == "pec":
+        if isinstance(wl, list):
+            raise SystemExit("the midpoint integrator runs single problems, not batches")
+        wl = wl.with_integrator(1)
     return wl
 
 
@@ -133,11 +139,15 @@ def describe(wl) -> dict:
         "workload": f"{wl.name}: {wl.n_fluid:,} fluid + {wl.n_total - wl.n_fluid:,} wall particles, "
                     f"{wl.dim}D, {kern} h={wl.h:g}, {prec}, alpha={wl.alpha:g}, xsph={wl.xsph_eps:g}, "
                     f"nu={wl.nu:g}, dt={wl.dt:.6g}, neighbour rebuild every step"
-                    + (", solid-wall pressure of Adami et al." if getattr(wl, "wall_bc", 0) else ""),
+                    + (", solid-wall pressure of Adami et al." if getattr(wl, "wall_bc", 0) else "")
+                    + (", midpoint predict-evaluate-correct integrator (two neighbour builds "
+                       "and evaluations per step)" if getattr(wl, "integrator", 0) else ""),
         "particles": wl.n_total,
         "fluid_particles": wl.n_fluid,
         "l2": "flushed between timed steps (512 MB write)",
         "parallelism": "replicas (one independent problem per GPU)",
+        **({"pairs_counted": "end-of-step evaluation only (the midpoint evaluation of each "
+                             "step is not counted)"} if getattr(wl, "integrator", 0) else {}),
     }
 
 
@@ -300,7 +310,7 @@ def gpu_arm(args, rank, world, dist):
     import paper_1909_04504_gb300 as G
 
     dev = torch.cuda.current_device()
-    raw = workload(args.workload, args.wall_bc)
+    raw = workload(args.workload, args.wall_bc, args.integrator)
     wl = BatchView(raw) if isinstance(raw, list) else raw
     sim = Runner(G, raw)
     sch = sim.sch
@@ -517,6 +527,8 @@ def gpu_arm(args, rank, world, dist):
     # ---- hand-written adjoint: K steps forward, then the same K steps with the reverse sweep
     adjoint = None
     k_adj = args.adjoint_steps if args.adjoint_steps >= 0 else ADJOINT_STEPS.get(args.workload, 0)
+    if args.integrator != "kdk":
+        k_adj = 0  # the adjoint covers the kick-drift-kick integrator
     if k_adj > 0 and not sim.batch and sch.density == G.CONTINUITY:
         sim.set_timing(False)
         sim.load_state(pinned)
@@ -635,7 +647,7 @@ def cpu_baseline(wl, target_s: float, states=None) -> dict:
 def reference_arm(args):
     """Times the oracle on the host cores in the base contract's reference slot."""
     import oracle as O
-    wl = workload(args.workload, args.wall_bc)
+    wl = workload(args.workload, args.wall_bc, args.integrator)
     if isinstance(wl, list):
         v, el, sample, cores = oracle_batch_sample(wl, args.ref_seconds)
         return {
@@ -695,6 +707,9 @@ def main():
     ap.add_argument("--wall-bc", default="density", choices=["density", "adami"],
                     help="wall condition: continuity walls (the configurations') or the "
                          "solid-wall pressure of Adami et al.")
+    ap.add_argument("--integrator", default="kdk", choices=["kdk", "pec"],
+                    help="kick-drift-kick (the paper's form) or the two-evaluation midpoint "
+                         "predict-evaluate-correct form")
     ap.add_argument("--adjoint-steps", type=int, default=-1,
                     help="K of the timed adjoint (-1: 50 for taylor_green_3d, 20 for "
                          "dam_break_3d, none otherwise; 0: off)")

@@ -50,6 +50,7 @@ typedef enum { SPH_PREC_FP64 = 0, SPH_PREC_FP32 = 1 } sph_precision;
 typedef enum { SPH_ROLE_FLUID = 0, SPH_ROLE_WALL = 1 } sph_role;
 typedef enum { SPH_DENSITY_CONTINUITY = 0, SPH_DENSITY_SUMMATION = 1 } sph_density;
 typedef enum { SPH_WALL_DENSITY = 0, SPH_WALL_ADAMI = 1 } sph_wall_bc;
+typedef enum { SPH_INTEGRATOR_KDK = 0, SPH_INTEGRATOR_PEC = 1 } sph_integrator;
 
 /* Geometry of a problem (Sec. 2.2, Sec. 3 create_domain).
  *  dim        2 or 3.
@@ -110,10 +111,26 @@ typedef struct {
  *             (x_w - x_f) W_wf) / sum_f W_wf over its fluid neighbours f (static walls)
  *             and rho_w = rho0 (1 + p_w / B)^(1/gamma), B = c0^2 rho0 / gamma; a wall
  *             with no fluid neighbour takes p_w = 0, rho_w = rho0. One more launch per
- *             evaluation (graph step form only; sph_backward rejects it). */
+ *             evaluation (graph step form only; sph_backward rejects it).
+ *  integrator sph_integrator. SPH_INTEGRATOR_KDK: the predictor-corrector of Sec. 2.1 as
+ *             kick-drift-kick (u^{n+1/2} = u^n + dt/2 a^n, x^{n+1} = x^n + dt (u^{n+1/2}
+ *             + xsph^n), rho^{n+1} = rho^n + dt arho(x^{n+1}, u^{n+1/2}), u^{n+1} =
+ *             u^{n+1/2} + dt/2 a^{n+1}), one evaluation per step; second order in u and
+ *             x, first order in the continuity density. SPH_INTEGRATOR_PEC: the
+ *             two-evaluation midpoint predict-evaluate-correct form (Monaghan 2005),
+ *             second order: a half step with the rates at t^n (u* = u^n + dt/2 a^n,
+ *             x* = x^n + dt/2 (u^n + xsph^n), rho* = rho^n + dt/2 arho^n), an evaluation
+ *             at the midpoint, the full step from t^n with the midpoint rates (u^{n+1} =
+ *             u^n + dt a*, x^{n+1} = x^n + dt (u^n + dt/2 a* + xsph*), rho^{n+1} = rho^n +
+ *             dt arho*), and an evaluation at t^{n+1}: two neighbour builds and two
+ *             evaluations per step. Single problems in the graph step form only
+ *             (sph_step_batch and sph_backward reject it).
+ *  reserved   must be 0. */
 typedef struct {
     int32_t density;
     int32_t wall_bc;
+    int32_t integrator;
+    int32_t reserved;
     double rho0;
     double c0;
     double gamma;
@@ -213,7 +230,8 @@ sph_status sph_synchronize(sph_ctx* ctx);
  * time in ms of the last completed step's phases: out[0] drift + cell keys, out[1] radix
  * sort, out[2] reorder + EOS, out[3] cell table, out[4] density pass (neighbour scan and
  * list, summation density or continuity, EOS), out[5] momentum pass with the corrector
- * kick and the reductions. SPH_ERR_STATE if no timed step ran. */
+ * kick and the reductions; with SPH_INTEGRATOR_PEC those of the end-of-step build and
+ * evaluation. SPH_ERR_STATE if no timed step ran. */
 sph_status sph_set_timing(sph_ctx* ctx, int32_t enable);
 sph_status sph_phase_times(sph_ctx* ctx, float out[6]);
 

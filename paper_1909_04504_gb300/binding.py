@@ -20,6 +20,7 @@ PREC_FP64, PREC_FP32 = 0, 1
 FLUID, WALL = 0, 1
 CONTINUITY, SUMMATION = 0, 1
 WALL_DENSITY, WALL_ADAMI = 0, 1  # sph_wall_bc
+INTEGRATOR_KDK, INTEGRATOR_PEC = 0, 1  # sph_integrator
 STEP_GRAPH, STEP_PERSISTENT = 0, 1
 DIAG_COUNT = 13
 DIAG_NAMES = ("t", "dt", "ke", "umax", "px", "py", "pz", "amax", "pairs", "candidates",
@@ -47,7 +48,8 @@ class ArrayDesc(C.Structure):
 
 
 class Scheme(C.Structure):
-    _fields_ = [("density", C.c_int32), ("wall_bc", C.c_int32), ("rho0", C.c_double),
+    _fields_ = [("density", C.c_int32), ("wall_bc", C.c_int32), ("integrator", C.c_int32),
+                ("reserved", C.c_int32), ("rho0", C.c_double),
                 ("c0", C.c_double), ("gamma", C.c_double), ("nu", C.c_double),
                 ("eta", C.c_double), ("alpha", C.c_double), ("xsph_eps", C.c_double),
                 ("g", C.c_double * 3)]
@@ -139,10 +141,12 @@ def _f64(a) -> np.ndarray:
 
 
 def make_scheme(density=CONTINUITY, rho0=1.0, c0=10.0, gamma=7.0, nu=0.0, eta=0.01, alpha=0.0,
-                xsph_eps=0.0, g=(0.0, 0.0, 0.0), wall_bc=WALL_DENSITY) -> Scheme:
+                xsph_eps=0.0, g=(0.0, 0.0, 0.0), wall_bc=WALL_DENSITY,
+                integrator=INTEGRATOR_KDK) -> Scheme:
     s = Scheme()
     s.density, s.rho0, s.c0, s.gamma = int(density), rho0, c0, gamma
     s.wall_bc = int(wall_bc)
+    s.integrator = int(integrator)
     s.nu, s.eta, s.alpha, s.xsph_eps = nu, eta, alpha, xsph_eps
     for k in range(3):
         s.g[k] = float(g[k])
@@ -153,7 +157,8 @@ def scheme_of(wl, **over) -> Scheme:
     """Scheme from an object with the workload attributes (rho0, c0, gamma, nu, ...)."""
     kw = dict(density=wl.density, rho0=wl.rho0, c0=wl.c0, gamma=wl.gamma, nu=wl.nu, eta=wl.eta,
               alpha=wl.alpha, xsph_eps=wl.xsph_eps, g=wl.g,
-              wall_bc=getattr(wl, "wall_bc", WALL_DENSITY))
+              wall_bc=getattr(wl, "wall_bc", WALL_DENSITY),
+              integrator=getattr(wl, "integrator", INTEGRATOR_KDK))
     kw.update(over)
     return make_scheme(**kw)
 

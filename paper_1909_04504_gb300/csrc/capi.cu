@@ -15,6 +15,7 @@
 #include "sph.h"
 #include "sph_device.cuh"
 #include "sph_launch.h"
+#include "pec.h"
 #include "sort_impl.cuh"
 
 using namespace sph;
@@ -25,7 +26,7 @@ thread_local std::string g_create_error;
 
 constexpr double PI = 3.14159265358979323846;
 constexpr uint32_t STATE_MAGIC = 0x53504853u;  // "SPHS"
-constexpr uint32_t STATE_VERSION = 1;
+constexpr uint32_t STATE_VERSION = 2;
 
 struct StateHeader {
     uint32_t magic, version;
@@ -53,6 +54,10 @@ struct sph_ctx {
     int N = 0;
     int nwall = 0;                 // wall particles
     bool wall_pass = false;        // the scheme(s) in use take the solid-wall pressure pass
+    bool pec = false;              // the scheme in use takes the midpoint integrator
+    int pec_cont = 1;              // ... with the continuity density (else summation)
+    double* pec_save = nullptr;    // midpoint integrator: saved (x, u, rho) + the step size
+    uint32_t* perm = nullptr;      // sorted values of the last build: previous position
     std::vector<int64_t> arr_off;  // n_arrays + 1
     int passes = 1;
 
@@ -273,6 +278,9 @@ sph_status check_scheme(sph_ctx* c, const sph_scheme* s) {
         return fail(c, SPH_ERR_INVALID, "nu, eta, alpha must be >= 0");
     if (s->wall_bc != SPH_WALL_DENSITY && s->wall_bc != SPH_WALL_ADAMI)
         return fail(c, SPH_ERR_INVALID, "unknown wall condition");
+    if (s->integrator != SPH_INTEGRATOR_KDK && s->integrator != SPH_INTEGRATOR_PEC)
+        return fail(c, SPH_ERR_INVALID, "unknown integrator");
+    if (s->reserved != 0) return fail(c, SPH_ERR_INVALID, "scheme.reserved must be 0");
     return SPH_OK;
 }
 
@@ -416,6 +424,7 @@ void enqueue_build(sph_ctx* c, int drift, int kick, int carry_rates, bool timed 
     mark(c, 1, timed);
     const int b = launch_onesweep(c->N, c->keys, c->vals, c->passes, c->sort_work, c->ctl, c->wait_ns, st);
     c->skeys = c->keys[b];
+    c->perm = c->vals[b];
     mark(c, 2, timed);
     const int nxt = c->cur ^ 1;
     L.S = c->set[nxt];
@@ -493,11 +502,31 @@ sph_status run_fused(sph_ctx* c, int nsteps) {
 
 sph_status capture_step_graphs(sph_ctx* c);
 
+// One step of the midpoint integrator (rates at the current state valid): predictor in
+// place, build + evaluation at the midpoint, corrector on the midpoint order, build +
+// evaluation at the end of the step (the timed phases), record. Two builds: the set in
+// use is the same at the end.
+void enqueue_pec_step(sph_ctx* c) {
+    const int cont = c->pec_cont;
+    const int dim = c->dom.dim;
+    double* dt_step = c->pec_save + (size_t)(2 * dim + 1) * c->N;
+    launch_pec_predict(c->set[c->cur], c->pec_save, c->N, dim, c->G, &c->ctl->dt, dt_step, cont,
+                       c->ctl, c->sms, c->stream);
+    enqueue_build(c, 0, 0, 0);
+    enqueue_eval(c, 0);
+    launch_pec_correct(c->set[c->cur], c->pec_save, c->perm, c->N, dim, c->G, dt_step, cont,
+                       c->ctl, c->sms, c->stream);
+    enqueue_build(c, 0, 0, 0, c->timing);
+    enqueue_eval(c, 0, c->timing);
+    launch_pec_record(c->ctl, c->history, dt_step, c->stream);
+}
+
 // nsteps steps in the context's mode (tables already uploaded, rates valid).
 sph_status run_steps(sph_ctx* c, int nsteps) {
     if (nsteps <= 0) return SPH_OK;
-    // the persistent kernel has no solid-wall pressure phase: such steps run as the graph
-    if (c->step_mode == SPH_STEP_PERSISTENT && !c->wall_pass) return run_fused(c, nsteps);
+    // the persistent kernel has neither the solid-wall pressure phase nor the midpoint
+    // integrator: such steps run as the graph
+    if (c->step_mode == SPH_STEP_PERSISTENT && !c->wall_pass && !c->pec) return run_fused(c, nsteps);
     if (!c->graph[0] || c->graph_timed != c->timing) {
         sph_status s = capture_step_graphs(c);
         if (s != SPH_OK) return s;
@@ -505,7 +534,7 @@ sph_status run_steps(sph_ctx* c, int nsteps) {
     CK(clear_work_if_dirty(c));
     for (int k = 0; k < nsteps; ++k) {
         CK(cudaGraphLaunch(c->graph[c->cur], c->stream));
-        c->cur ^= 1;
+        if (!c->pec) c->cur ^= 1;  // one build per step, or two
     }
     c->skeys = c->keys[c->passes & 1];
     c->last_fused = false;
@@ -541,6 +570,24 @@ sph_status upload_table(sph_ctx* c, const sph_scheme* schemes, const double* dts
     wp &= c->nwall > 0;
     if (wp != c->wall_pass) {  // the captured steps hold the pass or not
         c->wall_pass = wp;
+        drop_graphs(c);
+    }
+    const bool pec = c->ninst == 0 && schemes[0].integrator == SPH_INTEGRATOR_PEC;
+    if (pec && !c->pec_save) {  // outside any capture: the first use of the integrator
+        const size_t bytes = ((size_t)(2 * c->dom.dim + 1) * c->N + 1) * sizeof(double);
+        void* p = nullptr;
+        if (c->alloc) p = c->alloc(bytes, c->user);
+        else if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+        if (!p) {
+            cudaGetLastError();
+            return fail(c, SPH_ERR_OOM, "midpoint integrator state of " + std::to_string(bytes) + " bytes");
+        }
+        c->pec_save = (double*)p;
+    }
+    const int cont = schemes[0].density != SPH_DENSITY_SUMMATION;
+    if (pec != c->pec || (pec && cont != c->pec_cont)) {  // captured steps: one integrator
+        c->pec = pec;
+        c->pec_cont = cont;
         drop_graphs(c);
     }
     std::vector<unsigned char> bytes;
@@ -645,8 +692,11 @@ sph_status capture_step_graphs(sph_ctx* c) {
         c->cur = cur0 ^ k;
         cudaGraph_t g = nullptr;
         CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-        enqueue_build(c, 1, 1, 0, c->timing);
-        enqueue_eval(c, 1, c->timing);
+        if (c->pec) enqueue_pec_step(c);
+        else {
+            enqueue_build(c, 1, 1, 0, c->timing);
+            enqueue_eval(c, 1, c->timing);
+        }
         mark(c, 6, c->timing);
         cudaError_t e = cudaStreamEndCapture(c->stream, &g);
         if (e != cudaSuccess) {
@@ -1093,6 +1143,8 @@ sph_status step_batch_impl(sph_ctx* c, const sph_scheme* schemes, const double* 
         if (s != SPH_OK) return fail(c, s, "instance " + std::to_string(k) + ": " + c->err);
         if (schemes[k].density != schemes[0].density)
             return fail(c, SPH_ERR_INVALID, "instances must share the density formulation");
+        if (schemes[k].integrator != SPH_INTEGRATOR_KDK)
+            return fail(c, SPH_ERR_INVALID, "batches run the kick-drift-kick integrator");
         if (!std::isfinite(dt[k])) return fail(c, SPH_ERR_INVALID, "dt is not finite");
         if (!changed && (!same_scheme(schemes[k], c->batch_schemes[k]) || c->batch_dt[k] != dt[k]))
             changed = true;
@@ -1167,9 +1219,10 @@ void sph_destroy(sph_ctx* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     drop_graphs(c);
-    for (int k = 0; k < 6; ++k)
+    for (int k = 0; k < 7; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     free_dev(c, c->nl);
+    free_dev(c, c->pec_save);
     free_dev(c, c->arena);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -1352,14 +1405,14 @@ sph_status sph_phase_times(sph_ctx* c, float out[6]) {
 sph_status sph_kernels_per_step(const sph_ctx* ctx, const sph_scheme* scheme, int32_t* count) {
     sph_ctx* c = const_cast<sph_ctx*>(ctx);
     if (!c || !scheme || !count) return fail(c, SPH_ERR_INVALID, "NULL argument");
-    // drift+keys, 3 per radix pass, reorder, cell table, density pass, momentum pass
-    // (+ the per-instance reduction of a batch)
     // graph: keys + histograms, one launch per radix pass, reorder + cell table, density
-    // pass, momentum pass (+ the two-stage per-instance reduction of a batch)
+    // pass, [solid-wall pressure], momentum pass (+ the two-stage per-instance reduction of
+    // a batch); the midpoint integrator runs two of these and three stage kernels
     const bool wp = scheme->wall_bc == SPH_WALL_ADAMI && c->nwall > 0;
-    *count = c->step_mode == SPH_STEP_PERSISTENT && !wp
-                 ? 1
-                 : 1 + c->passes + 1 + 1 + (wp ? 1 : 0) + 1 + (c->ninst ? 2 : 0);
+    const bool pec = scheme->integrator == SPH_INTEGRATOR_PEC && c->ninst == 0;
+    const int build_eval = 1 + c->passes + 1 + 1 + (wp ? 1 : 0) + 1;
+    if (pec) *count = 2 * build_eval + 3;  // + predictor, corrector, record
+    else *count = c->step_mode == SPH_STEP_PERSISTENT && !wp ? 1 : build_eval + (c->ninst ? 2 : 0);
     return SPH_OK;
 }
 
@@ -1464,7 +1517,7 @@ sph_status tune_lanes(sph_ctx* c) {
 // Times a few steps in each mode from the same state and keeps the faster mode; the
 // state, time and records are put back afterwards.
 sph_status choose_mode(sph_ctx* c) {
-    if (c->fused_bps[tindex(c->group_m)] < 1 || c->wall_pass) {  // the wall pass: graph only
+    if (c->fused_bps[tindex(c->group_m)] < 1 || c->wall_pass || c->pec) {  // graph only
         c->step_mode = SPH_STEP_GRAPH;
         return SPH_OK;
     }
@@ -1694,6 +1747,8 @@ sph_status sph_backward(sph_ctx* c, const sph_scheme* scheme, double dt, int32_t
         return fail(c, SPH_ERR_INVALID, "the adjoint covers the continuity formulation only");
     if (scheme->wall_bc != SPH_WALL_DENSITY)
         return fail(c, SPH_ERR_INVALID, "the adjoint does not cover the solid-wall pressure");
+    if (scheme->integrator != SPH_INTEGRATOR_KDK)
+        return fail(c, SPH_ERR_INVALID, "the adjoint covers the kick-drift-kick integrator only");
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(c, SPH_ERR_INVALID, "the adjoint needs a fixed dt > 0");
     if (K < 0) return fail(c, SPH_ERR_INVALID, "K < 0");
     int C = ckpt_every;

@@ -56,3 +56,15 @@ def test_workload_wall_option():
     assert bench.workload("dam_break_2d").wall_bc == 0
     batch = bench.workload("batch_tg2d", "adami")
     assert all(w.wall_bc == 1 for w in batch)
+
+
+def test_workload_integrator_option():
+    wl = bench.workload("dam_break_2d", "density", "pec")
+    assert wl.integrator == 1 and wl.name.endswith("_pec")
+    d = bench.describe(wl)
+    assert "predict-evaluate-correct" in d["workload"] and "pairs_counted" in d
+    assert bench.workload("dam_break_2d").integrator == 0
+    assert "pairs_counted" not in bench.describe(bench.workload("dam_break_2d"))
+    import pytest
+    with pytest.raises(SystemExit):
+        bench.workload("batch_tg2d", "density", "pec")

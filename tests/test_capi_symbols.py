@@ -1,5 +1,6 @@
 """The C ABI library builds for sm_103a, loads, and exports every entry point that
 include/*.h declares (no compute call: runs without a GPU)."""
+import ctypes as C
 import glob
 import os
 import re
@@ -44,3 +45,28 @@ def test_no_host_fallback_in_product_path():
     for f in glob.glob(os.path.join(pkg, "*.py")):
         src = open(f).read()
         assert "import oracle" not in src and "from oracle" not in src
+
+
+def test_ctypes_structures_match_the_header(tmp_path):
+    """Offsets and sizes of sph_domain, sph_array_desc and sph_scheme as the C compiler
+    lays them out from include/sph.h, against the binding's ctypes mirrors."""
+    from paper_1909_04504_gb300 import binding
+    mirrors = {"sph_domain": binding.Domain, "sph_array_desc": binding.ArrayDesc,
+               "sph_scheme": binding.Scheme}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "sph.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f in py._fields_:
+            lines.append(f'printf("{cname} {f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out.splitlines()}
+    for cname, py in mirrors.items():
+        assert got[(cname, "size")] == C.sizeof(py), cname
+        for f in py._fields_:
+            assert got[(cname, f[0])] == getattr(py, f[0]).offset, (cname, f[0])
