@@ -45,7 +45,7 @@ typedef enum {
     SPH_ERR_STATE = 8       /* the call is not valid in the context's current state */
 } sph_status;
 
-typedef enum { SPH_KERNEL_QUINTIC = 0, SPH_KERNEL_WENDLAND_C2 = 1 } sph_kernel;
+typedef enum { SPH_KERNEL_QUINTIC = 0, SPH_KERNEL_WENDLAND_C2 = 1, SPH_KERNEL_CUBIC_SPLINE = 2 } sph_kernel;
 typedef enum { SPH_PREC_FP64 = 0, SPH_PREC_FP32 = 1 } sph_precision;
 typedef enum { SPH_ROLE_FLUID = 0, SPH_ROLE_WALL = 1 } sph_role;
 typedef enum { SPH_DENSITY_CONTINUITY = 0, SPH_DENSITY_SUMMATION = 1 } sph_density;
@@ -54,7 +54,8 @@ typedef enum { SPH_INTEGRATOR_KDK = 0, SPH_INTEGRATOR_PEC = 1 } sph_integrator;
 
 /* Geometry of a problem (Sec. 2.2, Sec. 3 create_domain).
  *  dim        2 or 3.
- *  kernel     sph_kernel: quintic spline (support 3h) or Wendland C2 (support 2h).
+ *  kernel     sph_kernel: quintic spline (support 3h), Wendland C2 (support 2h) or the
+ *             cubic (M4) B-spline (support 2h). sph_cell_sort_noalloc takes the first two.
  *  precision  sph_precision of the pair loops. FP32: positions are rounded once to
  *             float and the neighbour test and pair sums run in float with compensated
  *             (Neumaier) per-particle sums; the integrator, the state and the

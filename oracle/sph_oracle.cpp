@@ -22,6 +22,8 @@
  * Readings of points the paper leaves open (each one is listed in the design notes):
  *  - quintic spline: Morris form, support 3h, sigma_2D = 7/(478 pi), sigma_3D = 1/(120 pi);
  *  - Wendland C2: (1-q/2)^4 (2q+1), support 2h, sigma_2D = 7/(4 pi), sigma_3D = 21/(16 pi);
+ *  - cubic spline: 1 - 3q^2/2 + 3q^3/4 on [0,1), (2-q)^3/4 on [1,2), sigma_2D = 10/(7 pi),
+ *    sigma_3D = 1/pi;
  *  - neighbour predicate: i != j and r^2 < (k h)^2 with r^2 = ((dx dx) + dy dy) + dz dz,
  *    minimum image dx -= L if dx > L/2, dx += L if dx < -L/2, in the mode's precision;
  *  - cell grid: n_d = floor(ext_d / (k h / R * 1.00001)) with R = 1 in 2D and 2 in 3D,
@@ -51,6 +53,7 @@ namespace {
 
 constexpr int KERNEL_QUINTIC = 0;
 constexpr int KERNEL_WENDLAND_C2 = 1;
+constexpr int KERNEL_CUBIC_SPLINE = 2;
 constexpr int ROLE_FLUID = 0;
 constexpr int PREC_FP32 = 1;
 constexpr int DENSITY_SUMMATION = 1;
@@ -139,6 +142,18 @@ void kernel_eval(int kernel, int dim, double h, T r, T* W, T* dWdr) {
         if (qv < 3.0) { T t = 3.0 - q; w += ipow(t, 5); dw -= 5.0 * ipow(t, 4); }
         if (qv < 2.0) { T t = 2.0 - q; w -= 6.0 * ipow(t, 5); dw += 30.0 * ipow(t, 4); }
         if (qv < 1.0) { T t = 1.0 - q; w += 15.0 * ipow(t, 5); dw -= 75.0 * ipow(t, 4); }
+    } else if (kernel == KERNEL_CUBIC_SPLINE) {
+        /* M4 cubic B-spline (Monaghan and Lattanzio 1985), support 2h, piecewise form */
+        sigma = dim == 2 ? 10.0 / (7.0 * PI) : 1.0 / PI;
+        double qv = val(q);
+        if (qv < 1.0) {
+            w = 1.0 - 1.5 * q * q + 0.75 * q * q * q;
+            dw = -3.0 * q + 2.25 * q * q;
+        } else if (qv < 2.0) {
+            T t = 2.0 - q;
+            w = 0.25 * ipow(t, 3);
+            dw = -0.75 * t * t;
+        }
     } else {
         sigma = dim == 2 ? 7.0 / (4.0 * PI) : 21.0 / (16.0 * PI);
         if (val(q) < 2.0) {
@@ -717,7 +732,8 @@ extern "C" {
 
 /* Kernel value and radial derivative at distance r (pins and plots). */
 int ora_kernel(int32_t kernel, int32_t dim, double h, double r, double* W, double* dWdr) {
-    if ((kernel != KERNEL_QUINTIC && kernel != KERNEL_WENDLAND_C2) || (dim != 2 && dim != 3))
+    if ((kernel != KERNEL_QUINTIC && kernel != KERNEL_WENDLAND_C2 && kernel != KERNEL_CUBIC_SPLINE) ||
+        (dim != 2 && dim != 3))
         return -1;
     kernel_eval<double>(kernel, dim, h, r, W, dWdr);
     return 0;

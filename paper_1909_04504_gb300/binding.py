@@ -15,7 +15,7 @@ import numpy as np
 
 from . import build as _build
 
-QUINTIC, WENDLAND_C2 = 0, 1
+QUINTIC, WENDLAND_C2, CUBIC_SPLINE = 0, 1, 2
 PREC_FP64, PREC_FP32 = 0, 1
 FLUID, WALL = 0, 1
 CONTINUITY, SUMMATION = 0, 1

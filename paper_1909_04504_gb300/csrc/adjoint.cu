@@ -49,6 +49,11 @@ __device__ __forceinline__ Real kernel_fp(Real q) {
             w1p -= Real(120) * t2 * t2 * t2;
         }
         return PairMath<Real>::div(w1p * q - w1, q * q * q);
+    } else if (KERNEL == CUBIC_SPLINE) {
+        // f = 9 q - 12 on [0,1): f' = 9; f = -3 (2-q)^2 / q on [1,2): f' = 3 (4 - q^2) / q^2
+        if (q < Real(1e-6)) return Real(0);  // multiplies r_vec -> 0 (coincident particles)
+        if (q < Real(1)) return PairMath<Real>::div(Real(9), q);
+        return PairMath<Real>::div(Real(3) * (Real(4) - q * q), q * q * q);
     } else {
         if (q < Real(1e-6)) return Real(0);  // multiplies r_vec -> 0 (coincident particles)
         const Real t = Real(1) - Real(0.5) * q;
@@ -506,16 +511,20 @@ static void adj_eval_t(const AdjLaunch& A, const PairConst<Real>& K, cudaStream_
 
 void launch_adjoint_eval(const AdjLaunch& A, const PairConst<float>& Kf, const PairConst<double>& Kd,
                          cudaStream_t st) {
-    const int sel = (A.precision ? 4 : 0) + (A.dim == 3 ? 2 : 0) + (A.kernel == WENDLAND_C2 ? 1 : 0);
+    const int sel = (A.precision ? 6 : 0) + (A.dim == 3 ? 3 : 0) + A.kernel;
     switch (sel) {
         case 0: adj_eval_t<double, 2, QUINTIC>(A, Kd, st); break;
         case 1: adj_eval_t<double, 2, WENDLAND_C2>(A, Kd, st); break;
-        case 2: adj_eval_t<double, 3, QUINTIC>(A, Kd, st); break;
-        case 3: adj_eval_t<double, 3, WENDLAND_C2>(A, Kd, st); break;
-        case 4: adj_eval_t<float, 2, QUINTIC>(A, Kf, st); break;
-        case 5: adj_eval_t<float, 2, WENDLAND_C2>(A, Kf, st); break;
-        case 6: adj_eval_t<float, 3, QUINTIC>(A, Kf, st); break;
-        default: adj_eval_t<float, 3, WENDLAND_C2>(A, Kf, st); break;
+        case 2: adj_eval_t<double, 2, CUBIC_SPLINE>(A, Kd, st); break;
+        case 3: adj_eval_t<double, 3, QUINTIC>(A, Kd, st); break;
+        case 4: adj_eval_t<double, 3, WENDLAND_C2>(A, Kd, st); break;
+        case 5: adj_eval_t<double, 3, CUBIC_SPLINE>(A, Kd, st); break;
+        case 6: adj_eval_t<float, 2, QUINTIC>(A, Kf, st); break;
+        case 7: adj_eval_t<float, 2, WENDLAND_C2>(A, Kf, st); break;
+        case 8: adj_eval_t<float, 2, CUBIC_SPLINE>(A, Kf, st); break;
+        case 9: adj_eval_t<float, 3, QUINTIC>(A, Kf, st); break;
+        case 10: adj_eval_t<float, 3, WENDLAND_C2>(A, Kf, st); break;
+        default: adj_eval_t<float, 3, CUBIC_SPLINE>(A, Kf, st); break;
     }
 }
 

@@ -148,8 +148,11 @@ sph_status cuda_fail(sph_ctx* c, cudaError_t e, const char* what) {
 
 double support_factor(int kernel) { return kernel == SPH_KERNEL_QUINTIC ? 3.0 : 2.0; }
 
+// Normalisation of the unscaled smoothing functions of sph_device.cuh (the cubic spline
+// there is four times the M4 B-spline, whose factors are 10 / (7 pi) and 1 / pi).
 double sigma(int kernel, int dim) {
     if (kernel == SPH_KERNEL_QUINTIC) return dim == 2 ? 7.0 / (478.0 * PI) : 1.0 / (120.0 * PI);
+    if (kernel == SPH_KERNEL_CUBIC_SPLINE) return dim == 2 ? 5.0 / (14.0 * PI) : 1.0 / (4.0 * PI);
     return dim == 2 ? 7.0 / (4.0 * PI) : 21.0 / (16.0 * PI);
 }
 
@@ -157,7 +160,8 @@ double sigma(int kernel, int dim) {
 // mode-precision neighbour test never accepts a pair two cells apart).
 sph_status make_grid(sph_ctx* c, const sph_domain& D, Grid* G) {
     if (D.dim != 2 && D.dim != 3) return fail(c, SPH_ERR_INVALID, "dim must be 2 or 3");
-    if (D.kernel != SPH_KERNEL_QUINTIC && D.kernel != SPH_KERNEL_WENDLAND_C2)
+    if (D.kernel != SPH_KERNEL_QUINTIC && D.kernel != SPH_KERNEL_WENDLAND_C2 &&
+        D.kernel != SPH_KERNEL_CUBIC_SPLINE)
         return fail(c, SPH_ERR_INVALID, "unknown kernel");
     if (D.precision != SPH_PREC_FP64 && D.precision != SPH_PREC_FP32)
         return fail(c, SPH_ERR_INVALID, "unknown precision");

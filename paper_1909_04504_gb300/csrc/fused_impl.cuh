@@ -255,21 +255,25 @@ struct FusedDispatch {
         }
     }
     static cudaError_t launch(const FusedLaunch& F, int T, int grid, cudaStream_t st) {
-        const int sel = (F.L.dim == 3 ? 2 : 0) + (F.L.kernel == WENDLAND_C2 ? 1 : 0);
+        const int sel = (F.L.dim == 3 ? 3 : 0) + F.L.kernel;
         switch (sel) {
             case 0: return launch_dk<2, QUINTIC>(F, T, grid, st);
             case 1: return launch_dk<2, WENDLAND_C2>(F, T, grid, st);
-            case 2: return launch_dk<3, QUINTIC>(F, T, grid, st);
-            default: return launch_dk<3, WENDLAND_C2>(F, T, grid, st);
+            case 2: return launch_dk<2, CUBIC_SPLINE>(F, T, grid, st);
+            case 3: return launch_dk<3, QUINTIC>(F, T, grid, st);
+            case 4: return launch_dk<3, WENDLAND_C2>(F, T, grid, st);
+            default: return launch_dk<3, CUBIC_SPLINE>(F, T, grid, st);
         }
     }
     static int bps(int dim, int kernel, int T) {
-        const int sel = (dim == 3 ? 2 : 0) + (kernel == WENDLAND_C2 ? 1 : 0);
+        const int sel = (dim == 3 ? 3 : 0) + kernel;
         switch (sel) {
             case 0: return bps_dk<2, QUINTIC>(T);
             case 1: return bps_dk<2, WENDLAND_C2>(T);
-            case 2: return bps_dk<3, QUINTIC>(T);
-            default: return bps_dk<3, WENDLAND_C2>(T);
+            case 2: return bps_dk<2, CUBIC_SPLINE>(T);
+            case 3: return bps_dk<3, QUINTIC>(T);
+            case 4: return bps_dk<3, WENDLAND_C2>(T);
+            default: return bps_dk<3, CUBIC_SPLINE>(T);
         }
     }
 };

@@ -816,32 +816,38 @@ template <class Real>
 struct PairDispatch {
     template <int T>
     static int bps_t(int pass, int dim, int kernel) {
-        const int sel = (dim == 3 ? 2 : 0) + (kernel == WENDLAND_C2 ? 1 : 0);
+        const int sel = (dim == 3 ? 3 : 0) + kernel;
         switch (sel) {
             case 0: return pass ? momentum_bps<Real, 2, QUINTIC, T>() : density_bps<Real, 2, QUINTIC, T>();
             case 1: return pass ? momentum_bps<Real, 2, WENDLAND_C2, T>() : density_bps<Real, 2, WENDLAND_C2, T>();
-            case 2: return pass ? momentum_bps<Real, 3, QUINTIC, T>() : density_bps<Real, 3, QUINTIC, T>();
-            default: return pass ? momentum_bps<Real, 3, WENDLAND_C2, T>() : density_bps<Real, 3, WENDLAND_C2, T>();
+            case 2: return pass ? momentum_bps<Real, 2, CUBIC_SPLINE, T>() : density_bps<Real, 2, CUBIC_SPLINE, T>();
+            case 3: return pass ? momentum_bps<Real, 3, QUINTIC, T>() : density_bps<Real, 3, QUINTIC, T>();
+            case 4: return pass ? momentum_bps<Real, 3, WENDLAND_C2, T>() : density_bps<Real, 3, WENDLAND_C2, T>();
+            default: return pass ? momentum_bps<Real, 3, CUBIC_SPLINE, T>() : density_bps<Real, 3, CUBIC_SPLINE, T>();
         }
     }
     template <int T>
     static void density_t(const StepLaunch& L, cudaStream_t st) {
-        const int sel = (L.dim == 3 ? 2 : 0) + (L.kernel == WENDLAND_C2 ? 1 : 0);
+        const int sel = (L.dim == 3 ? 3 : 0) + L.kernel;
         switch (sel) {
             case 0: launch_density_t<Real, 2, QUINTIC, T>(L, st); break;
             case 1: launch_density_t<Real, 2, WENDLAND_C2, T>(L, st); break;
-            case 2: launch_density_t<Real, 3, QUINTIC, T>(L, st); break;
-            default: launch_density_t<Real, 3, WENDLAND_C2, T>(L, st); break;
+            case 2: launch_density_t<Real, 2, CUBIC_SPLINE, T>(L, st); break;
+            case 3: launch_density_t<Real, 3, QUINTIC, T>(L, st); break;
+            case 4: launch_density_t<Real, 3, WENDLAND_C2, T>(L, st); break;
+            default: launch_density_t<Real, 3, CUBIC_SPLINE, T>(L, st); break;
         }
     }
     template <int T>
     static void momentum_t(const StepLaunch& L, cudaStream_t st) {
-        const int sel = (L.dim == 3 ? 2 : 0) + (L.kernel == WENDLAND_C2 ? 1 : 0);
+        const int sel = (L.dim == 3 ? 3 : 0) + L.kernel;
         switch (sel) {
             case 0: launch_momentum_t<Real, 2, QUINTIC, T>(L, st); break;
             case 1: launch_momentum_t<Real, 2, WENDLAND_C2, T>(L, st); break;
-            case 2: launch_momentum_t<Real, 3, QUINTIC, T>(L, st); break;
-            default: launch_momentum_t<Real, 3, WENDLAND_C2, T>(L, st); break;
+            case 2: launch_momentum_t<Real, 2, CUBIC_SPLINE, T>(L, st); break;
+            case 3: launch_momentum_t<Real, 3, QUINTIC, T>(L, st); break;
+            case 4: launch_momentum_t<Real, 3, WENDLAND_C2, T>(L, st); break;
+            default: launch_momentum_t<Real, 3, CUBIC_SPLINE, T>(L, st); break;
         }
     }
 };

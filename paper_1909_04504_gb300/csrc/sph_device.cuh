@@ -10,6 +10,7 @@ namespace sph {
 
 constexpr int QUINTIC = 0;
 constexpr int WENDLAND_C2 = 1;
+constexpr int CUBIC_SPLINE = 2;
 constexpr uint32_t WALL_BIT = 0x80000000u;  // tag = global id | WALL_BIT for wall particles
 constexpr uint32_t ID_MASK = 0x7fffffffu;
 
@@ -197,6 +198,8 @@ struct PairMath<double> {
 //    f = -50 q^3 + 120 q^2 - 120 on [0,1), (-5 (3-q)^4 + 30 (2-q)^4) / q on [1,2),
 //    -5 (3-q)^4 / q on [2,3).
 //  Wendland C2 (support 2): w = (1 - q/2)^4 (2q + 1), f = -5 (1 - q/2)^3.
+//  cubic spline (support 2, four times the M4 B-spline): w = (2-q)^3 - 4 (1-q)^3 with
+//    terms where positive; f = 9 q - 12 on [0,1), -3 (2-q)^2 / q on [1,2).
 template <class Real, int KERNEL>
 __device__ __forceinline__ Real kernel_f(Real q) {
     if (KERNEL == QUINTIC) {
@@ -220,6 +223,12 @@ __device__ __forceinline__ Real kernel_f(Real q) {
         p += Real(30) * t2s * t2s;
         const Real outer = PairMath<Real>::div(p, q);
         return q < Real(1) ? inner : outer;
+    } else if (KERNEL == CUBIC_SPLINE) {
+        const Real inner = Real(9) * q - Real(12);
+        if (sizeof(Real) == 8 && q < Real(1)) return inner;
+        const Real t2 = q < Real(2) ? Real(2) - q : Real(0);
+        const Real outer = PairMath<Real>::div(Real(-3) * t2 * t2, q);
+        return q < Real(1) ? inner : outer;
     } else {
         Real t = Real(1) - Real(0.5) * q;
         return Real(-5) * t * t * t;
@@ -241,6 +250,10 @@ __device__ __forceinline__ Real kernel_w(Real q) {
         Real t1s = t1 * t1;
         w += Real(15) * t1s * t1s * t1;
         return w;
+    } else if (KERNEL == CUBIC_SPLINE) {
+        const Real t2 = q < Real(2) ? Real(2) - q : Real(0);
+        const Real t1 = q < Real(1) ? Real(1) - q : Real(0);
+        return t2 * t2 * t2 - Real(4) * (t1 * t1 * t1);
     } else {
         Real t = Real(1) - Real(0.5) * q;
         Real t2 = t * t;

@@ -99,16 +99,20 @@ static void wall_pressure_t(const StepLaunch& L, cudaStream_t st) {
 }
 
 void launch_wall_pressure(const StepLaunch& L, cudaStream_t st) {
-    const int sel = (L.precision ? 4 : 0) + (L.dim == 3 ? 2 : 0) + (L.kernel == WENDLAND_C2 ? 1 : 0);
+    const int sel = (L.precision ? 6 : 0) + (L.dim == 3 ? 3 : 0) + L.kernel;
     switch (sel) {
         case 0: wall_pressure_t<double, 2, QUINTIC>(L, st); break;
         case 1: wall_pressure_t<double, 2, WENDLAND_C2>(L, st); break;
-        case 2: wall_pressure_t<double, 3, QUINTIC>(L, st); break;
-        case 3: wall_pressure_t<double, 3, WENDLAND_C2>(L, st); break;
-        case 4: wall_pressure_t<float, 2, QUINTIC>(L, st); break;
-        case 5: wall_pressure_t<float, 2, WENDLAND_C2>(L, st); break;
-        case 6: wall_pressure_t<float, 3, QUINTIC>(L, st); break;
-        default: wall_pressure_t<float, 3, WENDLAND_C2>(L, st); break;
+        case 2: wall_pressure_t<double, 2, CUBIC_SPLINE>(L, st); break;
+        case 3: wall_pressure_t<double, 3, QUINTIC>(L, st); break;
+        case 4: wall_pressure_t<double, 3, WENDLAND_C2>(L, st); break;
+        case 5: wall_pressure_t<double, 3, CUBIC_SPLINE>(L, st); break;
+        case 6: wall_pressure_t<float, 2, QUINTIC>(L, st); break;
+        case 7: wall_pressure_t<float, 2, WENDLAND_C2>(L, st); break;
+        case 8: wall_pressure_t<float, 2, CUBIC_SPLINE>(L, st); break;
+        case 9: wall_pressure_t<float, 3, QUINTIC>(L, st); break;
+        case 10: wall_pressure_t<float, 3, WENDLAND_C2>(L, st); break;
+        default: wall_pressure_t<float, 3, CUBIC_SPLINE>(L, st); break;
     }
 }
 

@@ -68,3 +68,11 @@ def test_workload_integrator_option():
     import pytest
     with pytest.raises(SystemExit):
         bench.workload("batch_tg2d", "density", "pec")
+
+
+def test_falling_cube_workload():
+    wl = bench.workload("falling_cube_3d")
+    assert wl.kernel == W.CUBIC_SPLINE and wl.n_total == 1_000_000 and wl.n_fluid == wl.n_total
+    d = bench.describe(wl)
+    assert "cubic spline" in d["workload"] and "paper_context" in d
+    assert bench.kernel_flops(wl) == (6, 8)

@@ -12,11 +12,12 @@ import scipy.special as special
 import oracle as O
 import workloads as W
 
-KINDS = [(W.QUINTIC, 3.0, [1.0, 2.0]), (W.WENDLAND_C2, 2.0, [])]
+KINDS = [(W.QUINTIC, 3.0, [1.0, 2.0]), (W.WENDLAND_C2, 2.0, []), (W.CUBIC_SPLINE, 2.0, [1.0])]
+KNOTS = {k: kn for k, _, kn in KINDS}
 
 
 def _quad(f, kind, h, support):
-    knots = [0.0] + [k * h for k in ([1.0, 2.0] if kind == W.QUINTIC else [])] + [support * h]
+    knots = [0.0] + [k * h for k in KNOTS[kind]] + [support * h]
     return sum(integrate.quad(f, a, b, limit=200, epsabs=1e-14, epsrel=1e-12)[0]
                for a, b in zip(knots[:-1], knots[1:]))
 
@@ -62,7 +63,9 @@ def test_compact_support_and_knots(kind, support, knots, dim):
         W0, dW = O.kernel(kind, dim, h, r)
         assert W0 == 0.0 and dW == 0.0
     W_in, dW_in = O.kernel(kind, dim, h, support * h * (1 - 1e-7))
-    assert abs(W_in) < 1e-20 and abs(dW_in) < 1e-18
+    # dW vanishes at the support like (support - r)^4 (quintic), ^3 (Wendland C2) or ^2
+    # (cubic spline): (2e-7)^2 = 4e-14
+    assert abs(W_in) < 1e-20 and abs(dW_in) < (1e-13 if kind == W.CUBIC_SPLINE else 1e-18)
     for q in knots:  # value, slope continuous across the spline knots
         a = O.kernel(kind, dim, h, q * h - 1e-9)
         b = O.kernel(kind, dim, h, q * h + 1e-9)
@@ -100,8 +103,10 @@ def poisson_lattice_sum(kind, dim, hdx, support, K):
 @pytest.mark.parametrize("kind,dim,hdx,K,tol", [
     (W.QUINTIC, 2, 1.0, 12, 2e-8),
     (W.WENDLAND_C2, 2, 1.3, 12, 2e-5),
+    (W.CUBIC_SPLINE, 2, 1.2, 12, 1e-5),
     (W.QUINTIC, 3, 1.0, 8, 2e-8),
     (W.WENDLAND_C2, 3, 1.3, 8, 2e-5),
+    (W.CUBIC_SPLINE, 3, 1.2, 8, 1e-5),
 ])
 def test_summation_density_equals_poisson_lattice_sum(kind, dim, hdx, K, tol):
     """Eq. (2) on a uniform periodic lattice (m = rho0 dx^d) gives rho0 times the lattice

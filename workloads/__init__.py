@@ -34,6 +34,7 @@ SEED_BASE = 1909_04504
 
 QUINTIC = 0
 WENDLAND_C2 = 1
+CUBIC_SPLINE = 2
 FLUID = 0
 WALL = 1
 PREC_FP64 = 0
@@ -280,6 +281,36 @@ def dam_break_3d(dx: float = 0.005, block=(1.0, 0.5, 0.5), tank=(3.2, 1.0, 1.0),
     return Workload(name=f"dam_break_3d_{nf}+{nw}", dim=3, kernel=WENDLAND_C2, h=h,
                     lo=[-pad, -pad, -pad], hi=[tank[0] + pad, tank[1] + pad, tank[2]],
                     periodic=[0, 0, 0], precision=precision, arrays=[fluid, wall],
+                    rho0=rho0, c0=c0, alpha=alpha, xsph_eps=xsph_eps,
+                    g=[0.0, 0.0, -gravity], dt=0.25 * h / c0, steps=steps)
+
+
+def falling_cube_3d(n: int = 100, side: float = 1.0, hdx: float = 1.2, rho0: float = 1000.0,
+                    gravity: float = 9.81, alpha: float = 0.1, xsph_eps: float = 0.0,
+                    fall: float = 0.5, steps: int = 1000,
+                    precision: int = PREC_FP32) -> Workload:
+    """A cube of water falling freely under gravity, no walls (the problem of the
+    performance measurements of Sec. 4.4), z vertical.
+
+    n^3 fluid particles at the centres of a lattice of spacing dx = side / n filling
+    [0, side]^3, at rest, rho = rho0; cubic spline kernel with h = hdx dx. The cell box
+    leaves one support around the cube and ``fall`` below it (particles that leave it are
+    clamped into the edge cells). c0 = 10 sqrt(2 g side), dt = 0.25 h / c0.
+    """
+    dx = side / n
+    i, j, k = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    xf = (i.ravel() + 0.5) * dx
+    yf = (j.ravel() + 0.5) * dx
+    zf = (k.ravel() + 0.5) * dx
+    nf = xf.shape[0]
+    fluid = ParticleSet("fluid", FLUID, xf, yf, zf, _zeros(nf), _zeros(nf), _zeros(nf),
+                        np.full(nf, rho0), np.full(nf, rho0 * dx ** 3))
+    h = hdx * dx
+    kh = 2.0 * h
+    c0 = 10.0 * math.sqrt(2.0 * gravity * side)
+    return Workload(name=f"falling_cube_3d_{n}^3", dim=3, kernel=CUBIC_SPLINE, h=h,
+                    lo=[-kh, -kh, -fall], hi=[side + kh, side + kh, side + kh],
+                    periodic=[0, 0, 0], precision=precision, arrays=[fluid],
                     rho0=rho0, c0=c0, alpha=alpha, xsph_eps=xsph_eps,
                     g=[0.0, 0.0, -gravity], dt=0.25 * h / c0, steps=steps)
 
