@@ -248,8 +248,9 @@ sph_status sph_set_groups(sph_ctx* ctx, int32_t momentum_lanes);
  * captured CUDA graph. SPH_STEP_PERSISTENT: the whole step as ONE cooperative launch whose
  * blocks stay resident and meet at grid-wide barriers between the phases (no launch gaps;
  * pays off on small problems and batches of them). Both run the same per-particle code;
- * the diagnostics are summed in another order. SPH_ERR_INVALID if the mode is unknown or
- * the device cannot launch cooperatively. */
+ * the diagnostics are summed in another order. Steps with the solid-wall pressure or the
+ * midpoint integrator run as the graph in either mode. SPH_ERR_INVALID if the mode is
+ * unknown or the device cannot launch cooperatively. */
 enum { SPH_STEP_GRAPH = 0, SPH_STEP_PERSISTENT = 1 };
 sph_status sph_set_step_mode(sph_ctx* ctx, int32_t mode);
 
