@@ -89,6 +89,7 @@ CASES = {
     "dam_break_2d": lambda: (W.dam_break_2d(dx=0.05), None),
     "dam_break_2d_adami": lambda: (W.dam_break_2d(dx=0.05).with_wall_bc(1), None),
     "taylor_green_2d_summation": lambda: _tg_moving(),
+    "dam_break_3d": lambda: (W.dam_break_3d(dx=0.1, tank=(1.6, 0.6, 1.0)), None),
 }
 
 
@@ -106,7 +107,8 @@ def test_one_step_is_predict_evaluate_correct(name):
     dt = wl.dt
     ref, R1 = _by_hand(wl, s, dt)
     st, hist = O.run(wl, s, dt, 1)
-    for k in ("x", "y", "u", "v", "rho"):
+    fields = ("x", "y", "z", "u", "v", "w", "rho") if wl.dim == 3 else ("x", "y", "u", "v", "rho")
+    for k in fields:
         scale = np.max(np.abs(ref[k])) + 1e-300
         assert np.max(np.abs(st[k] - ref[k])) <= 1e-13 * scale, k
     assert hist[1, 0] == dt and hist[1, 1] == dt
