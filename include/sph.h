@@ -124,8 +124,8 @@ typedef struct {
  *             at the midpoint, the full step from t^n with the midpoint rates (u^{n+1} =
  *             u^n + dt a*, x^{n+1} = x^n + dt (u^n + dt/2 a* + xsph*), rho^{n+1} = rho^n +
  *             dt arho*), and an evaluation at t^{n+1}: two neighbour builds and two
- *             evaluations per step. Single problems in the graph step form only
- *             (sph_step_batch and sph_backward reject it).
+ *             evaluations per step. Graph step form only; the instances of a batch
+ *             share it; sph_backward rejects it.
  *  reserved   must be 0. */
 typedef struct {
     int32_t density;

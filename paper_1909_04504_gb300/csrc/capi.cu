@@ -513,16 +513,28 @@ sph_status capture_step_graphs(sph_ctx* c);
 void enqueue_pec_step(sph_ctx* c) {
     const int cont = c->pec_cont;
     const int dim = c->dom.dim;
+    const int prec = c->dom.precision;
     double* dt_step = c->pec_save + (size_t)(2 * dim + 1) * c->N;
-    launch_pec_predict(c->set[c->cur], c->pec_save, c->N, dim, c->G, &c->ctl->dt, dt_step, cont,
-                       c->ctl, c->sms, c->stream);
+    if (c->ninst)
+        launch_pec_predict_batch(c->set[c->cur], c->pec_save, c->N, dim, prec, c->d_tab,
+                                 c->d_cell_bounds, c->ninst, c->skeys, c->idt, dt_step, cont,
+                                 c->ctl, c->sms, c->stream);
+    else
+        launch_pec_predict(c->set[c->cur], c->pec_save, c->N, dim, c->G, &c->ctl->dt, dt_step,
+                           cont, c->ctl, c->sms, c->stream);
     enqueue_build(c, 0, 0, 0);
     enqueue_eval(c, 0);
-    launch_pec_correct(c->set[c->cur], c->pec_save, c->perm, c->N, dim, c->G, dt_step, cont,
-                       c->ctl, c->sms, c->stream);
+    if (c->ninst)
+        launch_pec_correct_batch(c->set[c->cur], c->pec_save, c->perm, c->N, dim, prec, c->d_tab,
+                                 c->d_cell_bounds, c->ninst, c->skeys, dt_step, cont, c->ctl,
+                                 c->sms, c->stream);
+    else
+        launch_pec_correct(c->set[c->cur], c->pec_save, c->perm, c->N, dim, c->G, dt_step, cont,
+                           c->ctl, c->sms, c->stream);
     enqueue_build(c, 0, 0, 0, c->timing);
     enqueue_eval(c, 0, c->timing);
-    launch_pec_record(c->ctl, c->history, dt_step, c->stream);
+    if (c->ninst) launch_pec_record_batch(c->it, c->irec, dt_step, c->ninst, c->ctl, c->stream);
+    else launch_pec_record(c->ctl, c->history, dt_step, c->stream);
 }
 
 // nsteps steps in the context's mode (tables already uploaded, rates valid).
@@ -576,9 +588,9 @@ sph_status upload_table(sph_ctx* c, const sph_scheme* schemes, const double* dts
         c->wall_pass = wp;
         drop_graphs(c);
     }
-    const bool pec = c->ninst == 0 && schemes[0].integrator == SPH_INTEGRATOR_PEC;
+    const bool pec = schemes[0].integrator == SPH_INTEGRATOR_PEC;  // shared by a batch
     if (pec && !c->pec_save) {  // outside any capture: the first use of the integrator
-        const size_t bytes = ((size_t)(2 * c->dom.dim + 1) * c->N + 1) * sizeof(double);
+        const size_t bytes = ((size_t)(2 * c->dom.dim + 1) * c->N + ntab(c)) * sizeof(double);
         void* p = nullptr;
         if (c->alloc) p = c->alloc(bytes, c->user);
         else if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
@@ -1147,8 +1159,8 @@ sph_status step_batch_impl(sph_ctx* c, const sph_scheme* schemes, const double* 
         if (s != SPH_OK) return fail(c, s, "instance " + std::to_string(k) + ": " + c->err);
         if (schemes[k].density != schemes[0].density)
             return fail(c, SPH_ERR_INVALID, "instances must share the density formulation");
-        if (schemes[k].integrator != SPH_INTEGRATOR_KDK)
-            return fail(c, SPH_ERR_INVALID, "batches run the kick-drift-kick integrator");
+        if (schemes[k].integrator != schemes[0].integrator)
+            return fail(c, SPH_ERR_INVALID, "instances must share the integrator");
         if (!std::isfinite(dt[k])) return fail(c, SPH_ERR_INVALID, "dt is not finite");
         if (!changed && (!same_scheme(schemes[k], c->batch_schemes[k]) || c->batch_dt[k] != dt[k]))
             changed = true;
@@ -1413,10 +1425,10 @@ sph_status sph_kernels_per_step(const sph_ctx* ctx, const sph_scheme* scheme, in
     // pass, [solid-wall pressure], momentum pass (+ the two-stage per-instance reduction of
     // a batch); the midpoint integrator runs two of these and three stage kernels
     const bool wp = scheme->wall_bc == SPH_WALL_ADAMI && c->nwall > 0;
-    const bool pec = scheme->integrator == SPH_INTEGRATOR_PEC && c->ninst == 0;
-    const int build_eval = 1 + c->passes + 1 + 1 + (wp ? 1 : 0) + 1;
+    const bool pec = scheme->integrator == SPH_INTEGRATOR_PEC;
+    const int build_eval = 1 + c->passes + 1 + 1 + (wp ? 1 : 0) + 1 + (c->ninst ? 2 : 0);
     if (pec) *count = 2 * build_eval + 3;  // + predictor, corrector, record
-    else *count = c->step_mode == SPH_STEP_PERSISTENT && !wp ? 1 : build_eval + (c->ninst ? 2 : 0);
+    else *count = c->step_mode == SPH_STEP_PERSISTENT && !wp ? 1 : build_eval;
     return SPH_OK;
 }
 

@@ -4,7 +4,7 @@ the C ABI against the oracle: one step on the four workload structures (FP64 mod
 <= 1e-10 normwise per field, FP32 pair loops <= 1e-4 relative L2), ten steps, the
 CFL-type step size, summation density and the solid-wall pressure, a switch of
 integrator mid-run, save and resume, the persistent step form falling back to the
-graph, and the batch and adjoint entry points refusing the option."""
+graph, a batch bitwise equal to single runs, and the adjoint refusing the option."""
 import copy
 
 import numpy as np
@@ -155,7 +155,36 @@ def test_launch_count_and_refusals():
             sim.step(bad, wl.dt, 1)
     batch = G.BatchSimulation([W.dam_break_2d(dx=0.05), W.dam_break_2d(dx=0.06)])
     try:
-        with pytest.raises(G.SphError):
-            batch.step_batch([sch, sch], [wl.dt, wl.dt], 1)
+        mixed = [sch, G.scheme_of(wl, integrator=G.INTEGRATOR_KDK)]
+        with pytest.raises(G.SphError):  # the instances share the integrator
+            batch.step_batch(mixed, [wl.dt, wl.dt], 1)
+    finally:
+        batch.close()
+
+
+@pytest.mark.parametrize("precision", [W.PREC_FP64, W.PREC_FP32])
+def test_batch_equals_single_runs(precision):
+    """Instances of uneven size (one with the solid-wall pressure), each with its own fixed
+    dt: every instance bitwise equal to its single run."""
+    wls = [W.dam_break_2d(dx=dx, precision=precision).with_integrator(PEC)
+           for dx in (0.05, 0.04, 0.06)]
+    wls[1] = wls[1].with_wall_bc(1)
+    dts = [w.dt for w in wls]
+    steps = 8
+    batch = G.BatchSimulation(wls)
+    batch.set_groups(2)
+    batch.step_batch([G.scheme_of(w) for w in wls], dts, steps)
+    diag = batch.batch_diagnostics()
+    try:
+        for k, wl in enumerate(wls):
+            with G.Simulation.from_workload(wl) as sim:
+                sim.set_groups(2)
+                sim.step(G.scheme_of(wl), dts[k], steps)
+                st = sim.state()
+                d = sim.diagnostics()
+            bs = batch.instance_state(k)
+            for f in FIELDS_2D:
+                assert np.array_equal(bs[f], st[f]), (k, f)
+            assert diag[k, 0] == d[0] and diag[k, 1] == d[1] and diag[k, 10] == steps, k
     finally:
         batch.close()
