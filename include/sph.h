@@ -318,7 +318,8 @@ sph_status sph_create_batch(const sph_domain* domains, const sph_array_desc* arr
                             sph_ctx** out);
 
 /* Advance every instance nsteps steps; schemes[k] and dt[k] (dt <= 0: CFL-type step of
- * that instance) per instance; all instances share the density formulation. The first
+ * that instance) per instance; all instances share the density formulation and the
+ * integrator (SPH_ERR_INVALID otherwise). The first
  * call (or a change of schemes or dts) evaluates every instance at its current state.
  * Same integrator and equations as sph_step. Single-problem calls (sph_step,
  * sph_eval_rhs, sph_backward, sph_get_cells, sph_get_neighbors, sph_build_neighbors)
