@@ -65,9 +65,9 @@ def test_workload_integrator_option():
     assert "predict-evaluate-correct" in d["workload"] and "pairs_counted" in d
     assert bench.workload("dam_break_2d").integrator == 0
     assert "pairs_counted" not in bench.describe(bench.workload("dam_break_2d"))
-    import pytest
-    with pytest.raises(SystemExit):
-        bench.workload("batch_tg2d", "density", "pec")
+    batch = bench.workload("batch_tg2d", "density", "pec")
+    assert all(w.integrator == 1 for w in batch)
+    assert "predict-evaluate-correct" in bench.describe(bench.BatchView(batch))["workload"]
 
 
 def test_falling_cube_workload():
