@@ -3,6 +3,7 @@ mathematics fix: continuum limits of each discrete term (Eqs. continuity:sph,
 mom:sph:press, mom:sph:visc, XSPH), conservation and dissipation invariants, the
 equation of state, closed forms of the first dam-break step and of free fall under
 the predictor-corrector of Sec. 2.1, and the Taylor-Green decay of Sec. 4.1."""
+import copy
 import math
 
 import numpy as np
@@ -150,7 +151,8 @@ def test_artificial_viscosity_only_acts_on_approaching_pairs():
     assert np.max(np.abs(r["ax"][inner])) > 0.0
 
 
-@pytest.mark.parametrize("kind,tol", [(W.QUINTIC, 2e-3), (W.WENDLAND_C2, 5e-3)])
+@pytest.mark.parametrize("kind,tol", [(W.QUINTIC, 2e-3), (W.WENDLAND_C2, 5e-3),
+                                      (W.CUBIC_SPLINE, 5e-3)])
 def test_artificial_viscosity_magnitude(kind, tol):
     """Magnitude of the Monaghan AV term at rho0, in 2D. With u = (g x^2, 0) on x < 0
     every pair approaches (v_ij . r_ij = g s_x^2 (2 x_i + s_x) < 0 for s = x_j - x_i
@@ -178,6 +180,33 @@ def test_artificial_viscosity_magnitude(kind, tol):
     I = integrate.quad(lambda q: q ** 5 * F(q) / (q * q + eps * h * h) * 2 * math.pi,
                        0.0, kh, limit=400)[0]
     expect = -0.375 * alpha * wl.c0 * h * g * I
+    assert expect > 0.0 and inner.sum() > 1000
+    assert np.max(np.abs(r["ax"][inner] / expect - 1.0)) < tol
+    assert np.max(np.abs(r["ay"][inner])) < 1e-12 * expect
+
+
+@pytest.mark.parametrize("kind,hdx,tol", [(W.QUINTIC, 2.0, 5e-3), (W.WENDLAND_C2, 3.0, 4e-3),
+                                          (W.CUBIC_SPLINE, 3.0, 2e-3)])
+def test_artificial_viscosity_magnitude_3d(kind, hdx, tol):
+    """The same flow on a 24^3 lattice: the angular mean of s_x^4 / s^4 over the sphere
+    is 1/5, so a_x = -(1/5) alpha c0 h g int r^4 F(r) / (r^2 + eps h^2) 4 pi r^2 dr."""
+    n = 24
+    wl = copy.deepcopy(W.taylor_green_3d(n=n, jitter=0.0))
+    wl.kernel, wl.h, wl.nu = kind, hdx / n, 0.0
+    wl.periodic, wl.lo, wl.hi = [0, 0, 0], [-2.0, -1.0, -1.0], [2.0, 2.0, 2.0]
+    s = O.state_of(wl)
+    for k in "vw":
+        s[k][:] = 0.0
+    s["x"] = s["x"] - 1.5
+    h = wl.h
+    kh = (3.0 if kind == W.QUINTIC else 2.0) * h
+    inner = ((s["x"] > -1.5 + kh) & (s["x"] < -0.5 - kh) & (s["y"] > kh) & (s["y"] < 1.0 - kh)
+             & (s["z"] > kh) & (s["z"] < 1.0 - kh))
+    g, alpha, eps = 0.5, 0.1, 0.01
+    r = O.rhs(wl, with_(s, u=g * s["x"] ** 2), alpha=alpha)
+    I = integrate.quad(lambda q: q ** 6 * (O.kernel(kind, 3, h, q)[1] / q) / (q * q + eps * h * h)
+                       * 4 * math.pi, 0.0, kh, limit=400)[0]
+    expect = -0.2 * alpha * wl.c0 * h * g * I
     assert expect > 0.0 and inner.sum() > 1000
     assert np.max(np.abs(r["ax"][inner] / expect - 1.0)) < tol
     assert np.max(np.abs(r["ay"][inner])) < 1e-12 * expect
