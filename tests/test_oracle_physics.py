@@ -35,7 +35,8 @@ def with_(s, **kw):
     return out
 
 
-@pytest.mark.parametrize("kind,hdx,tol", [(W.QUINTIC, 1.0, 2e-3), (W.WENDLAND_C2, 1.3, 3e-2)])
+@pytest.mark.parametrize("kind,hdx,tol", [(W.QUINTIC, 1.0, 2e-3), (W.WENDLAND_C2, 1.3, 3e-2),
+                                          (W.CUBIC_SPLINE, 1.2, 2e-2)])
 def test_continuity_limit(kind, hdx, tol):
     """Eq. (continuity:sph) approximates -rho div u: u = beta x gives -rho0 beta."""
     wl, s, inner = block(kind, hdx)
@@ -44,7 +45,8 @@ def test_continuity_limit(kind, hdx, tol):
     assert np.max(np.abs(r["arho"][inner] / (-wl.rho0 * beta) - 1.0)) < tol
 
 
-@pytest.mark.parametrize("kind,hdx,tol", [(W.QUINTIC, 1.0, 2e-3), (W.WENDLAND_C2, 1.3, 3e-2)])
+@pytest.mark.parametrize("kind,hdx,tol", [(W.QUINTIC, 1.0, 2e-3), (W.WENDLAND_C2, 1.3, 3e-2),
+                                          (W.CUBIC_SPLINE, 1.2, 2e-2)])
 def test_pressure_gradient_limit(kind, hdx, tol):
     """Eq. (mom:sph:press) approximates -grad p / rho for a linear density field, with
     p from Eq. (eos): dp/dx = c0^2 (rho/rho0)^(gamma-1) drho/dx."""
