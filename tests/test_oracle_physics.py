@@ -59,26 +59,31 @@ def test_pressure_gradient_limit(kind, hdx, tol):
     assert np.max(np.abs(r["ay"][inner])) < 1e-12 * np.max(np.abs(r["ax"]))
 
 
-@pytest.mark.parametrize("eta,tol", [(0.0, 2e-3), (0.01, 1e-2)])
-def test_laminar_viscosity_limit(eta, tol):
+@pytest.mark.parametrize("kind,hdx,eta,tol", [(W.QUINTIC, 1.0, 0.0, 2e-3),
+                                              (W.QUINTIC, 1.0, 0.01, 1e-2),
+                                              (W.WENDLAND_C2, 2.0, 0.0, 2e-3),
+                                              (W.CUBIC_SPLINE, 2.0, 0.0, 2e-3)])
+def test_laminar_viscosity_limit(kind, hdx, eta, tol):
     """Eq. (mom:sph:visc) approximates nu lap u: u = (y^2, 0) gives (2 nu, 0)."""
-    wl, s, inner = block()
+    wl, s, inner = block(kind, hdx)
     nu = 0.01
     r = O.rhs(wl, with_(s, u=s["y"] ** 2), nu=nu, eta=eta)
     assert np.max(np.abs(r["ax"][inner] / (2 * nu) - 1.0)) < tol
     assert np.max(np.abs(r["ay"][inner])) < 1e-12
 
 
-def test_xsph_limit():
+@pytest.mark.parametrize("kind,hdx,tol", [(W.QUINTIC, 1.0, 1e-3), (W.WENDLAND_C2, 2.0, 1e-3),
+                                          (W.CUBIC_SPLINE, 2.0, 1e-3)])
+def test_xsph_limit(kind, hdx, tol):
     """XSPH = eps sum_j m_j / rho_bar (u_j - u_i) W_ij; for u = (x^2, 0) at rho0 the
     lattice sum tends to eps times the second moment of W, M2 = (1/d) int r^2 W dV."""
-    wl, s, inner = block()
+    wl, s, inner = block(kind, hdx)
     eps = 0.5
     r = O.rhs(wl, with_(s, u=s["x"] ** 2), xsph_eps=eps)
-    kh = 3.0 * wl.h
-    M2 = integrate.quad(lambda q: O.kernel(W.QUINTIC, 2, wl.h, q)[0] * q ** 3 * 2 * math.pi,
+    kh = (3.0 if kind == W.QUINTIC else 2.0) * wl.h
+    M2 = integrate.quad(lambda q: O.kernel(kind, 2, wl.h, q)[0] * q ** 3 * 2 * math.pi,
                         0.0, kh, limit=200)[0] / 2.0
-    assert np.max(np.abs(r["xsx"][inner] / (eps * M2) - 1.0)) < 1e-3
+    assert np.max(np.abs(r["xsx"][inner] / (eps * M2) - 1.0)) < tol
     # uniform velocity: no correction at all
     r = O.rhs(wl, with_(s, u=np.full_like(s["x"], 0.7)), xsph_eps=eps)
     assert np.max(np.abs(r["xsx"])) == 0.0
