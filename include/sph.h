@@ -116,8 +116,10 @@ typedef struct {
  *  integrator sph_integrator. SPH_INTEGRATOR_KDK: the predictor-corrector of Sec. 2.1 as
  *             kick-drift-kick (u^{n+1/2} = u^n + dt/2 a^n, x^{n+1} = x^n + dt (u^{n+1/2}
  *             + xsph^n), rho^{n+1} = rho^n + dt arho(x^{n+1}, u^{n+1/2}), u^{n+1} =
- *             u^{n+1/2} + dt/2 a^{n+1}), one evaluation per step; second order in u and
- *             x, first order in the continuity density. SPH_INTEGRATOR_PEC: the
+ *             u^{n+1/2} + dt/2 a^{n+1}), one evaluation per step; second order for
+ *             forces of the positions alone, first order where the rates depend on
+ *             the velocity (viscosity, artificial viscosity, XSPH, the continuity
+ *             rate), which it evaluates with u^{n+1/2}. SPH_INTEGRATOR_PEC: the
  *             two-evaluation midpoint predict-evaluate-correct form (Monaghan 2005),
  *             second order: a half step with the rates at t^n (u* = u^n + dt/2 a^n,
  *             x* = x^n + dt/2 (u^n + xsph^n), rho* = rho^n + dt/2 arho^n), an evaluation

@@ -129,9 +129,10 @@ def test_convergence_orders():
     """Taylor-Green vortex (Sec. 4.1), 20 x 20, over a fixed time T, velocity error
     against a midpoint run with 32 times smaller steps. The midpoint form is second order
     (the error falls by ~4 per halving of dt). The kick-drift-kick form converges to the
-    same trajectory at first order (~2 per halving): it is second order in u and x, but
-    its density takes the continuity rate at (x^{n+1}, u^{n+1/2}) instead of the
-    midpoint, and the density error reaches the velocity through the pressure."""
+    same trajectory at first order (~2 per halving): it evaluates the velocity-dependent
+    rates (here the laminar viscosity and the continuity rate) with the half-step velocity
+    u^{n+1/2}, which leaves an O(dt) error in them; with summation density the ratio
+    stays between first and second order (about 2.5)."""
     wl, s = _tg_moving()
     T = 16 * wl.dt
     ref, _ = O.run(copy.deepcopy(wl).with_integrator(PEC), s, T / 512, 512)
@@ -142,6 +143,13 @@ def test_convergence_orders():
     for a, b in zip(e0, e0[1:]):
         assert 1.8 < a / b < 2.3, e0
     assert e[-1] < 0.05 * e0[-1]
+    # summation density: no integrated density, the viscous term alone keeps it below order 2
+    ws = copy.deepcopy(wl)
+    ws.density = 1
+    refs, _ = O.run(copy.deepcopy(ws).with_integrator(0), s, T / 512, 512)
+    es = [_tg_error(ws, s, T, k, 0, refs)[0] for k in (16, 32, 64)]
+    for a, b in zip(es, es[1:]):
+        assert 2.2 < a / b < 2.8, es
 
 
 def test_adjoint_of_the_midpoint_form_is_refused():
