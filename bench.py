@@ -4,10 +4,12 @@
 A step is one pass of the whole per-timestep hot path over the workload: drift + cell
 keys, radix sort, reorder + EOS shadow, cell table, density pass (neighbour scan and list,
 continuity or summation density, EOS), momentum pass with the corrector kick and the FP64
-reductions (one captured CUDA graph). Default workload: the 2D dam break of the
-precision configuration (20,000 fluid + 3,618 wall particles, Wendland C2, FP32 pair loops
-with an FP64 integrator). Inputs are resident in HBM; L2 is flushed (a 512 MB write)
-between timed steps because the working set (a few MB) would otherwise stay in L2.
+reductions (one captured CUDA graph). Default workload: the 3D dam break of the scale
+configuration (2,000,000 fluid + 906,828 wall particles, Wendland C2, FP32 pair loops with
+an FP64 integrator, neighbour rebuild every step), the largest configuration that runs on
+one GPU. Inputs are resident in HBM; L2 is flushed (a 512 MB write) between timed steps
+when the state fits in L2 (the small workloads), and not when the state alone is larger
+than L2 (the 3D dam break, the batch).
 
 Prints one JSON line. ``--impl reference`` times the CPU oracle on the same workload.
 """
@@ -32,8 +34,19 @@ UNIT = "neighbour-pair interactions/s"
 # steps of the timed adjoint (gradient of the final kinetic energy) per workload
 ADJOINT_STEPS = {"taylor_green_3d": 50, "dam_break_3d": 20}
 FP32_LANES_PER_SM = 128   # FP32 CUDA-core lanes per Blackwell SM (4 sub-partitions x 32)
-SMS = 152
-SM_MAX_MHZ = 2070.0
+STATE_BYTES_PER_PARTICLE = 124  # one copy of the FP64 state (x, u, rho, m, rates, tag)
+
+
+def sm_max_mhz(clocks: dict):
+    """The SM clock ceiling: nvidia-smi's clocks.max.sm sampled during the run, else the
+    figure MEASURED_PEAKS.json records for this pool; (MHz, source)."""
+    if clocks.get("sm_max_mhz"):
+        return float(clocks["sm_max_mhz"]), "clocks.max.sm sampled during the run"
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["sm_max_mhz"]), "MEASURED_PEAKS.json sm_max_mhz"
+    except (OSError, ValueError, KeyError, TypeError):
+        return None, "unknown"
 
 
 def workload(name: str, wall_bc: str = "density", integrator: str = "kdk"):
@@ -145,7 +158,10 @@ def describe(wl) -> dict:
                        "and evaluations per step)" if getattr(wl, "integrator", 0) else ""),
         "particles": wl.n_total,
         "fluid_particles": wl.n_fluid,
-        "l2": "flushed between timed steps (512 MB write)",
+        "l2": ("flushed between timed steps (512 MB write)"
+               if STATE_BYTES_PER_PARTICLE * wl.n_total <= (129 << 20) else
+               f"no flush: the FP64 state alone ({STATE_BYTES_PER_PARTICLE * wl.n_total / 1e6:.0f} "
+               f"MB) exceeds L2"),
         "parallelism": "replicas (one independent problem per GPU)",
         **({"pairs_counted": "end-of-step evaluation only (the midpoint evaluation of each "
                              "step is not counted)"} if getattr(wl, "integrator", 0) else {}),
@@ -331,7 +347,11 @@ def gpu_arm(args, rank, world, dist):
     sim_lanes, sim_mode, density_lanes = sim.tuning()
     mode = "persistent" if sim_mode == G.STEP_PERSISTENT else "graph"
     sim.step(3)
-    flush_each = not sim.batch  # a batch's working set exceeds L2
+    props = torch.cuda.get_device_properties(dev)
+    sms = int(props.multi_processor_count)
+    l2_bytes = int(getattr(props, "L2_cache_size", 0) or 0) or (129 << 20)
+    # inputs larger than L2 need no flush between steps: the state alone exceeds it
+    flush_each = (not sim.batch) and STATE_BYTES_PER_PARTICLE * sim.n <= l2_bytes
     flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.int32, device=dev)
     e0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     e1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -402,7 +422,8 @@ def gpu_arm(args, rank, world, dist):
     flops = {"density": (fl["candidate"] * p_cand + fl["listed_pair"] * listed) / psteps_n,
              "momentum": (fl["fluid_dest_pair"] * fluid_pairs
                           + fl["xsph_fluid_source_pair"] * fluid_pairs * fluid_src_frac) / psteps_n}
-    peak = SMS * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    mhz, mhz_source = sm_max_mhz(clocks)
+    peak = sms * FP32_LANES_PER_SM * 2 * (mhz or 0.0) * 1e6 / 1e12
     if wl.precision == 0:
         peak = peak / 64.0  # FP64 CUDA-core rate of this part: 1/64 of FP32
     per_pass = {}
@@ -410,7 +431,8 @@ def gpu_arm(args, rank, world, dist):
         ms = phases[k] / psteps_n
         ach = flops[k] / (ms / 1e3) / 1e12
         per_pass[k] = {"avg_launch_ms": round(ms, 5), "flops_per_launch": flops[k],
-                       "achieved_tflops": round(ach, 4), "frac": round(ach / peak, 5)}
+                       "achieved_tflops": round(ach, 4),
+                       "frac": round(ach / peak, 5) if peak > 0 else None}
     dom = max(per_pass, key=lambda k: per_pass[k]["avg_launch_ms"])
     names = {"density": "k_density (neighbour scan + list, continuity/summation, EOS)",
              "momentum": "k_momentum (pressure, AV/viscosity, XSPH, corrector kick, reductions)"}
@@ -420,7 +442,8 @@ def gpu_arm(args, rank, world, dist):
                                             sim_lanes if dom == "momentum" else density_lanes),
                 "kernel": names[dom],
                 "flops_per_launch": flops[dom], "avg_launch_ms": per_pass[dom]["avg_launch_ms"],
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"
+                "peak_source": f"derived: {sms} SMs (device) x 128 FP32 lanes x 2 flop x "
+                               f"{mhz} MHz ({mhz_source})"
                                + (" / 64 (FP64)" if wl.precision == 0 else ""),
                 "passes": per_pass}
     phase_avg = {k: round(v / psteps_n, 5) for k, v in phases.items()}
@@ -438,11 +461,13 @@ def gpu_arm(args, rank, world, dist):
                              "sort_passes": sb["passes"], "kernels": streaming,
                              "note": "phase times include ~2-3 us of event-node gaps each"}
 
-    # ---- end to end through the C ABI with host buffers
-    blob = sim.save_state()
-    pinned = torch.empty(len(blob), dtype=torch.uint8, pin_memory=True).numpy()
-    pinned[:] = np.frombuffer(blob, dtype=np.uint8)
-    e2e_steps = min(args.steps, 200)
+    # ---- end to end through the C ABI with host buffers: every step loads the state from
+    # pinned host memory, steps, and reads the stepped state and the diagnostics back
+    nbytes = sim.state_bytes()
+    pinned = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True).numpy()
+    result = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True).numpy()
+    sim.save_state_into(pinned)
+    e2e_steps = min(args.steps, 100)
     sim.set_timing(False)
     sim.load_state(pinned)
     sim.step(1)  # re-capture without timing events
@@ -451,12 +476,15 @@ def gpu_arm(args, rank, world, dist):
     for _ in range(e2e_steps):
         sim.load_state(pinned)
         sim.step(1)
+        sim.save_state_into(result)
         e2e_pairs += sim.counts()[0]
     e2e_s = time.perf_counter() - tt
     e2e_ms, e2e_job_pairs = job_totals(dist, e2e_s * 1e3, e2e_pairs, device=dev)
-    e2e = {"value": e2e_job_pairs / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": len(blob),
-           "d2h_bytes_per_step": 8 * G.DIAG_COUNT,
-           "path": "sph_load_state(pinned host state) + sph_step + sph_diagnostics per step"}
+    e2e = {"value": e2e_job_pairs / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes + 8 * G.DIAG_COUNT,
+           "steps": e2e_steps,
+           "path": "sph_load_state(pinned host state) + sph_step + sph_save_state(pinned host "
+                   "buffer: the stepped state) + sph_diagnostics per step, host clock"}
 
     # ---- FP64 mode of the same workload (the metric compares FP32 with FP64)
     fp64 = None
@@ -570,7 +598,9 @@ def gpu_arm(args, rank, world, dist):
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32" if wl.precision == 1 else "f64", "data": "synthetic",
         "config": dict(describe(wl), step_mode=mode, momentum_lanes=sim_lanes,
-                       density_lanes=density_lanes),
+                       density_lanes=density_lanes,
+                       l2=("flushed between timed steps (512 MB write)" if flush_each else
+                           f"no flush: inputs larger than L2 ({l2_bytes >> 20} MiB)")),
         "particle_steps_per_s": psteps, "candidates_per_s": job_cand / (total_ms / 1e3),
         "pairs_per_step": pairs / args.steps, "phase_ms": phase_avg,
         "roofline": roofline, "e2e": e2e, "fp64_mode": fp64, "adjoint": adjoint,
@@ -610,6 +640,18 @@ def oracle_batch_sample(wls, target_s: float):
     return pairs / el, el, sample, O.threads()
 
 
+def one_step_increment(wl, prop, new, old):
+    """new - old; on a periodic position axis the minimum image (a wrapped particle moved
+    the short way)."""
+    import numpy as np
+    d = np.asarray(new, np.float64) - np.asarray(old, np.float64)
+    ax = {"x": 0, "y": 1, "z": 2}.get(prop)
+    if ax is not None and wl.periodic[ax]:
+        L = wl.hi[ax] - wl.lo[ax]
+        d = d - L * np.round(d / L)
+    return d
+
+
 def cpu_baseline(wl, target_s: float, states=None) -> dict:
     """The oracle as it stands, timed on the host cores on a bounded sample of the workload."""
     import numpy as np
@@ -634,18 +676,20 @@ def cpu_baseline(wl, target_s: float, states=None) -> dict:
     if states is not None:
         ref, _ = O.run(wl, s, wl.dt, 1)
         err = {}
+        props = ("x", "y", "z", "u", "v", "w", "rho") if wl.dim == 3 else ("x", "y", "u", "v", "rho")
         for prec, g in states.items():
-            key = "fp32_rel_l2" if prec == 1 else "fp64_normwise"
-            vals = []
-            for k in ("x", "y", "z", "u", "v", "w", "rho")[: (7 if wl.dim == 3 else 5)]:
-                if wl.dim == 2 and k in ("z", "w"):
-                    continue
-                a, b = g[k], ref[k]
-                if prec == 1:
-                    vals.append(float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)))
-                else:
-                    vals.append(float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)))
-            err[key] = max(vals)
+            per = {}
+            for k in props:
+                if prec == 1:  # relative L2 of the one-step increment (minimum image)
+                    a = one_step_increment(wl, k, g[k], s[k])
+                    b = one_step_increment(wl, k, ref[k], s[k])
+                    per[k] = float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+                else:  # normwise on the field
+                    a, b = g[k], ref[k]
+                    per[k] = float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+            key = "fp32_increment_rel_l2" if prec == 1 else "fp64_normwise"
+            err[key] = max(per.values())
+            err[key + "_per_field"] = per
         out["one_step_error_vs_oracle"] = err
     return out
 
@@ -696,17 +740,17 @@ def reference_arm(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="dam_break_2d",
+    ap.add_argument("--workload", default="dam_break_3d",
                     choices=["dam_break_2d", "taylor_green_2d", "taylor_green_3d", "dam_break_3d",
                              "batch_tg2d", "falling_cube_3d"])
     ap.add_argument("--flush-mb", type=int, default=512)
-    ap.add_argument("--fp64-steps", type=int, default=200)
+    ap.add_argument("--fp64-steps", type=int, default=50)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-seconds", type=float, default=150.0,
+    ap.add_argument("--ref-seconds", type=float, default=60.0,
                     help="reference arm: seconds of oracle time in the timed sample")
     ap.add_argument("--step-mode", default="auto", choices=["auto", "graph", "persistent"],
                     help="auto: the autotuner picks the tile shape and the step form")

@@ -55,7 +55,7 @@ typedef enum { SPH_INTEGRATOR_KDK = 0, SPH_INTEGRATOR_PEC = 1 } sph_integrator;
 /* Geometry of a problem (Sec. 2.2, Sec. 3 create_domain).
  *  dim        2 or 3.
  *  kernel     sph_kernel: quintic spline (support 3h), Wendland C2 (support 2h) or the
- *             cubic (M4) B-spline (support 2h). sph_cell_sort_noalloc takes the first two.
+ *             cubic (M4) B-spline (support 2h).
  *  precision  sph_precision of the pair loops. FP32: positions are rounded once to
  *             float and the neighbour test and pair sums run in float with compensated
  *             (Neumaier) per-particle sums; the integrator, the state and the
@@ -377,8 +377,10 @@ sph_status sph_load_state(sph_ctx* ctx, const void* buf, size_t bytes);
  * from two threads) race on it and must be serialised by the caller.
  *
  * Set-up: the first call on each device looks up that device's address of the array
- * (cudaGetSymbolAddress, with the device current); make that first call before any
- * stream capture on the device.
+ * (cudaGetSymbolAddress, with the device current) and keeps it for later calls; make that
+ * first call before any stream capture on the device. Each later call checks the kept
+ * address (cudaPointerGetAttributes) and looks it up again when a device reset has
+ * unloaded the array.
  *
  *  domain        grid and binning as in sph_create (dim, kernel, precision, periodic, h,
  *                lo, hi); the cell count follows the same rule.

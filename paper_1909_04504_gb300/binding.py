@@ -412,6 +412,19 @@ class Simulation:
         self._check(self._L.sph_save_state(self._ctx, buf, C.byref(size)))
         return buf.raw
 
+    def state_bytes(self) -> int:
+        size = C.c_size_t(0)
+        self._check(self._L.sph_save_state(self._ctx, None, C.byref(size)))
+        return int(size.value)
+
+    def save_state_into(self, buf: np.ndarray) -> int:
+        """Write the state into a contiguous uint8 array in place (a pinned host array is
+        filled by the device copies without staging); returns the bytes written."""
+        assert buf.dtype == np.uint8 and buf.flags.c_contiguous
+        size = C.c_size_t(buf.nbytes)
+        self._check(self._L.sph_save_state(self._ctx, C.c_void_p(buf.ctypes.data), C.byref(size)))
+        return int(size.value)
+
     def load_state(self, blob):
         """Restore a state from bytes or from a contiguous uint8 numpy array (read in place,
         so a pinned host array is copied to the device without staging)."""

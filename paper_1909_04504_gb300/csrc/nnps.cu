@@ -283,11 +283,7 @@ int radix_tiles(int n) {
     return t < 1 ? 1 : t;
 }
 
-size_t radix_hist_words(int n) {
-    int nblocks = (n + SORT_TILE - 1) / SORT_TILE;
-    if (nblocks < 1) nblocks = 1;
-    return (size_t)RADIX * nblocks + RADIX;
-}
+size_t radix_hist_words(int n) { return radix_hist_words_for(n); }
 
 // Sorts (keys[0], iota) by the low `passes * 8` bits; returns the buffer index (0 or 1)
 // holding the sorted keys and the permutation (sorted position -> previous position).

@@ -11,6 +11,7 @@
 #include "sph.h"
 #include "sph_device.cuh"
 #include "sph_launch.h"
+#include "sort_impl.cuh"
 
 namespace {
 
@@ -18,8 +19,11 @@ using namespace sph;
 
 constexpr int64_t MAX_N = SPH_NOALLOC_MAX_PARTICLES;
 constexpr size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
-// radix histogram words for MAX_N keys: 256 digits x ceil(MAX_N / 4096) tiles + 256 totals
-constexpr size_t HIST_WORDS = 256 * ((MAX_N + 4095) / 4096) + 256;
+// radix histogram words for MAX_N keys, by the sizing rule launch_radix_sort indexes with
+// (one count per digit and tile of SORT_TILE keys, then the digit totals)
+constexpr size_t HIST_WORDS = radix_hist_words_for(MAX_N);
+static_assert(HIST_WORDS == (size_t)RADIX * ((MAX_N + SORT_TILE - 1) / SORT_TILE) + RADIX,
+              "scratch histograms sized for the sort's tile");
 constexpr size_t OFF_KEYS0 = 0;
 constexpr size_t OFF_KEYS1 = OFF_KEYS0 + align256(MAX_N * 4);
 constexpr size_t OFF_VALS = OFF_KEYS1 + align256(MAX_N * 4);
@@ -69,7 +73,8 @@ extern "C" sph_status sph_cell_sort_noalloc(const sph_domain* domain, const doub
     if (!domain || !ncells_out) return fail(SPH_ERR_INVALID, "domain and ncells_out are required");
     const sph_domain& D = *domain;
     if (D.dim != 2 && D.dim != 3) return fail(SPH_ERR_INVALID, "dim must be 2 or 3");
-    if (D.kernel != SPH_KERNEL_QUINTIC && D.kernel != SPH_KERNEL_WENDLAND_C2)
+    if (D.kernel != SPH_KERNEL_QUINTIC && D.kernel != SPH_KERNEL_WENDLAND_C2 &&
+        D.kernel != SPH_KERNEL_CUBIC_SPLINE)
         return fail(SPH_ERR_INVALID, "unknown kernel");
     if (D.precision != SPH_PREC_FP64 && D.precision != SPH_PREC_FP32)
         return fail(SPH_ERR_INVALID, "unknown precision");
@@ -126,6 +131,16 @@ extern "C" sph_status sph_cell_sort_noalloc(const sph_domain* domain, const doub
     int sms = 0;
     {
         std::lock_guard<std::mutex> lock(g_setup_lock);
+        if (g_scratch_ptr[dev]) {
+            // a device reset unloads the module and its array: a cached address that the
+            // runtime no longer knows as this device's memory is looked up again
+            cudaPointerAttributes a{};
+            const cudaError_t pe = cudaPointerGetAttributes(&a, g_scratch_ptr[dev]);
+            if (pe != cudaSuccess || a.type != cudaMemoryTypeDevice || a.device != dev) {
+                cudaGetLastError();  // clear the error the query may have recorded
+                g_scratch_ptr[dev] = nullptr;
+            }
+        }
         if (!g_scratch_ptr[dev]) {
             void* ptr = nullptr;
             e = cudaGetSymbolAddress(&ptr, g_cell_sort_scratch);

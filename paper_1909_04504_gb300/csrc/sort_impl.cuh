@@ -16,6 +16,12 @@ constexpr int SORT_WARPS = SORT_THREADS / 32;
 constexpr int SORT_ITEMS = 16;
 constexpr int SORT_TILE = SORT_THREADS * SORT_ITEMS;
 
+// Words of the digit histograms of launch_radix_sort for n keys: RADIX counts per tile of
+// SORT_TILE keys, then the RADIX digit totals.
+constexpr size_t radix_hist_words_for(long long n) {
+    return (size_t)RADIX * (size_t)(n > 0 ? (n + SORT_TILE - 1) / SORT_TILE : 1) + RADIX;
+}
+
 struct ScatterSmem {
     uint32_t base_d[RADIX];
     uint32_t wcnt[SORT_WARPS][RADIX];

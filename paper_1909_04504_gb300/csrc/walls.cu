@@ -20,14 +20,21 @@ constexpr int WALL_LANES = 8;  // lanes per particle: a wall's list is split amo
 // instruction whatever its active lanes: the reciprocal and the EOS root start from the
 // FP32 hardware value and take one Newton step in FP64 (the FP32 start is good to a few
 // 2^-23, so one step leaves an error of order 2^-46, far below the sums' rounding).
+// The FP32 start needs x and 1/x inside FP32's normal range (the approximation flushes
+// subnormals to zero): outside it, and for 0, infinities and NaN, the FP64 divide. A wall
+// whose only fluid neighbour sits at the edge of the support has a kernel-weight sum far
+// below FP32's range in FP64 mode (1 - q/2 ~ 1e-12 gives ~1e-45).
 __device__ __forceinline__ double rcp_fp64(double x) {
+    const double ax = fabs(x);
+    if (!(ax >= 0x1p-125 && ax <= 0x1p125)) return 1.0 / x;
     const double r = (double)PairMath<float>::rcp((float)x);
     return r * fma(-x, r, 2.0);
 }
 
-// x^(1/gamma): for gamma = 7 Newton's step on y^7 = x from the FP32 root; else pow.
+// x^(1/gamma): for gamma = 7 Newton's step on y^7 = x from the FP32 root; else, or where
+// the FP32 root would leave FP32's normal range, pow.
 __device__ __forceinline__ double eos_root(double x, const StepConst& C) {
-    if (!C.gamma7) return pow(x, 1.0 / C.gamma);
+    if (!C.gamma7 || !(x >= 0x1p-120 && x <= 0x1p120)) return pow(x, 1.0 / C.gamma);
     double y = (double)powf((float)x, 1.0f / 7.0f);
     const double y3 = y * y * y;
     const double y6 = y3 * y3;

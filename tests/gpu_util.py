@@ -35,3 +35,32 @@ def rel_l2(a, b):
 def csr_equal(off_a, idx_a, off_b, idx_b):
     return np.array_equal(np.asarray(off_a, np.int64), np.asarray(off_b, np.int64)) and \
         np.array_equal(np.asarray(idx_a, np.int64), np.asarray(idx_b, np.int64))
+
+
+_AXIS = {"x": 0, "y": 1, "z": 2}
+
+
+def increment(wl, prop, new, old):
+    """new - old, taken across the periodic boundary by the minimum image on periodic
+    position axes (a particle that wrapped moved by the short way)."""
+    d = np.asarray(new, np.float64) - np.asarray(old, np.float64)
+    ax = _AXIS.get(prop)
+    if ax is not None and wl.periodic[ax]:
+        L = wl.hi[ax] - wl.lo[ax]
+        d = d - L * np.round(d / L)
+    return d
+
+
+def field_error(wl, prop, gpu, ora, start):
+    """Error measure of a field after steps from a common start: FP64 mode normwise on the
+    field itself; FP32 mode relative L2 of the change from the start (a step moves x by
+    ~1e-8 of its value and rho by ~1e-6, so an absolute-field L2 would not see a wrong
+    drift or density update)."""
+    if wl.precision == 0:
+        return normwise(gpu, ora)
+    return rel_l2(increment(wl, prop, gpu, start), increment(wl, prop, ora, start))
+
+
+def field_ok(wl, prop, gpu, ora, start, fp64_tol=1e-10, fp32_tol=1e-4):
+    tol = fp64_tol if wl.precision == 0 else fp32_tol
+    return field_error(wl, prop, gpu, ora, start) <= tol

@@ -125,3 +125,24 @@ def test_autograd_function_gives_the_adjoint_gradients():
     _, dke_u = O.grad(wl, s, wl.dt, K, du=d[0], dv=d[1])
     got = float((u0.grad.numpy() * np.stack(d)).sum())
     assert abs(got - dke_u) <= 1e-8 * abs(dke_u)
+
+
+def _dam_break_moving(wl, seed=3):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    for name in ("u", "v", "w")[:wl.dim]:
+        setattr(wl.arrays[0], name, 0.3 * rng.normal(size=wl.arrays[0].n))
+    return wl
+
+
+def test_dam_break_2d_fp32_dalpha():
+    """d/d alpha (Monaghan artificial viscosity) with FP32 pair loops, walls and XSPH."""
+    _check(_dam_break_moving(W.dam_break_2d(dx=0.08, precision=W.PREC_FP32)), K=6, tol=1e-3,
+           check_alpha=True)
+
+
+@pytest.mark.parametrize("prec,tol", [(W.PREC_FP64, 1e-8), (W.PREC_FP32, 1e-3)])
+def test_dam_break_3d_dalpha(prec, tol):
+    """d/d alpha and a velocity direction in 3D: walls, artificial viscosity, XSPH, gravity
+    along z."""
+    wl = _dam_break_moving(W.dam_break_3d(dx=0.1, precision=prec))
+    _check(wl, K=4, tol=tol, check_alpha=True)

@@ -11,7 +11,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from gpu_util import csr_equal, normwise, oracle_wl, rel_l2, sim_of
+from gpu_util import csr_equal, field_ok, normwise, oracle_wl, rel_l2, sim_of
 
 import paper_1909_04504_gb300 as G
 
@@ -90,8 +90,8 @@ def test_rhs_and_step_on_a_perturbed_state(name, prec):
             assert _close(prec, r[k], ref[k]), k
         sim.step(G.scheme_of(wl), wl.dt, 3)
         g = sim.state()
-    for k in FIELDS_3D if wl.dim == 3 else FIELDS_2D:
-        assert _close(prec, g[k], st[k]), k
+    for k in FIELDS_3D if wl.dim == 3 else FIELDS_2D:  # FP32: three-step increments
+        assert field_ok(wl, k, g[k], st[k], s[k]), k
 
 
 @pytest.mark.parametrize("prec", [G.PREC_FP64, G.PREC_FP32])
@@ -136,8 +136,8 @@ def test_persistent_form(prec):
         sim.set_step_mode(G.STEP_PERSISTENT)
         sim.step(G.scheme_of(wl), wl.dt, 5)
         g = sim.state()
-    for k in FIELDS_2D:
-        assert _close(prec, g[k], st[k]), k
+    for k in FIELDS_2D:  # FP32: five-step increments
+        assert field_ok(wl, k, g[k], st[k], s[k]), k
 
 
 @pytest.mark.parametrize("prec,tol", [(G.PREC_FP64, 1e-8), (G.PREC_FP32, 1e-3)])

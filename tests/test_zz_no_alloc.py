@@ -1,15 +1,18 @@
 """The allocation-free cell sort (sph_cell_sort_noalloc), for callers that cannot allocate
 device memory, gives the same permutation and cell table as the allocating path
-(sph_create + sph_get_cells) on the same positions.
+(sph_create + sph_get_cells) and as the oracle's cell search on the same positions.
 
-Called through the C ABI with device buffers owned by the test. Two calls in a row on
+Called through the C ABI with device buffers owned by the test. Calls in a row on
 different problems check that the shared scratch carries nothing from one call into the
-next; a third call repeats the first. Integer outputs: compared bit for bit."""
+next; the last call repeats the first. One problem holds exactly the largest accepted
+count (2^20 particles, 256 sort tiles, three radix passes), so the whole scratch extent is
+used. Integer outputs: compared bit for bit."""
 import ctypes as C
 
 import numpy as np
 import pytest
 
+import oracle as O
 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -69,12 +72,28 @@ def _allocating_sort(wl):
 
 def test_noalloc_cell_sort_matches_allocating_path_twice():
     problems = [W.dam_break_2d(dx=0.02, precision=W.PREC_FP32),
-                W.taylor_green_3d(n=24, precision=W.PREC_FP64)]
+                W.taylor_green_3d(n=24, precision=W.PREC_FP64),
+                W.falling_cube_3d(n=20, precision=W.PREC_FP32)]  # cubic spline kernel
+    assert problems[2].kernel == W.CUBIC_SPLINE
     for wl in problems + problems[:1]:
         order_n, off_n = _noalloc_sort(wl)
         order_a, off_a = _allocating_sort(wl)
         assert np.array_equal(off_n, off_a)
         assert np.array_equal(order_n, order_a)
+        _, off_o, order_o = O.cells(wl, wl.concat("x"), wl.concat("y"), wl.concat("z"))
+        assert np.array_equal(off_n, off_o)
+        assert np.array_equal(order_n, order_o)
+
+
+def test_noalloc_cell_sort_at_the_largest_accepted_count():
+    wl = W.taylor_green_2d(n=1024, precision=W.PREC_FP32)
+    assert wl.n_total == 1 << 20  # SPH_NOALLOC_MAX_PARTICLES
+    small = W.dam_break_2d(dx=0.04, precision=W.PREC_FP64)
+    for w in (wl, small, wl):
+        order_n, off_n = _noalloc_sort(w)
+        _, off_o, order_o = O.cells(w, w.concat("x"), w.concat("y"), w.concat("z"))
+        assert np.array_equal(off_n, off_o)
+        assert np.array_equal(order_n, order_o)
 
 
 def test_noalloc_cell_sort_rejects_oversize_input():
