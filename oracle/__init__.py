@@ -10,7 +10,8 @@ Functions (each follows the paper's passage named in the C source):
   grid(wl)                          cells per axis / cell sizes (Sec. 2.2)
   cells(wl, x, y, z)                linear cell per particle + cell offsets (Sec. 2.2)
   neighbors(wl, x, y, z, brute)     CSR neighbour sets, ascending ids (Sec. 2.2)
-  rhs(wl, state)                    one RHS evaluation (Sec. 2 equations, Sec. 3.2 groups)
+  rhs(wl, state)                    one RHS evaluation (Sec. 2 equations, Sec. 3.2 groups; the
+                                    EDAC pressure equation of Sec. 2.3's scheme list)
   run(wl, state, dt, steps)         predictor-corrector steps (Sec. 2.1)
   grad(wl, state, dt, K, du, dnu)   forward-mode derivative of the final kinetic energy
 """
@@ -50,7 +51,7 @@ class Params(C.Structure):
                 ("wall_bc", C.c_int32), ("integrator", C.c_int32), ("h", C.c_double), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
                 ("rho0", C.c_double), ("c0", C.c_double), ("gamma", C.c_double),
                 ("nu", C.c_double), ("eta", C.c_double), ("alpha", C.c_double),
-                ("xsph_eps", C.c_double), ("g", C.c_double * 3)]
+                ("xsph_eps", C.c_double), ("g", C.c_double * 3), ("edac_alpha", C.c_double)]
 
 
 _lib = None
@@ -67,8 +68,8 @@ def lib():
         _lib.ora_cells.argtypes = [P, C.c_int64, d, d, d, u32, u32, i64]
         _lib.ora_neighbors.argtypes = [P, C.c_int64, d, d, d, i64, i32, i64]
         _lib.ora_neighbors.restype = C.c_int64
-        _lib.ora_rhs.argtypes = [P, C.c_int64] + [d] * 8 + [u8] + [d] * 9 + [i64, i64]
-        _lib.ora_run.argtypes = [P, C.c_int64] + [d] * 7 + [d, u8, C.c_double, C.c_int32, d]
+        _lib.ora_rhs.argtypes = [P, C.c_int64] + [d] * 8 + [u8] + [d] * 9 + [i64, i64, d]
+        _lib.ora_run.argtypes = [P, C.c_int64] + [d] * 7 + [d, u8, C.c_double, C.c_int32, d, d]
         _lib.ora_grad.argtypes = ([P, C.c_int64] + [d] * 8 + [u8, C.c_double, C.c_int32]
                                   + [d] * 3 + [C.c_double, C.c_double, d, d])
         _lib.ora_threads.restype = C.c_int
@@ -97,6 +98,7 @@ def params(wl, brute: bool = False, **over) -> Params:
     p.h = wl.h
     p.rho0, p.c0, p.gamma = wl.rho0, wl.c0, wl.gamma
     p.nu, p.eta, p.alpha, p.xsph_eps = wl.nu, wl.eta, wl.alpha, wl.xsph_eps
+    p.edac_alpha = getattr(wl, "edac_alpha", 0.5)
     for k, v in over.items():
         setattr(p, k, v)
     return p
@@ -115,7 +117,7 @@ def _f64(a) -> np.ndarray:
 
 def state_of(wl) -> Dict[str, np.ndarray]:
     """Concatenated state of a workload (global ids in array order)."""
-    s = {k: _f64(wl.concat(k)) for k in ("x", "y", "z", "u", "v", "w", "rho", "m")}
+    s = {k: _f64(wl.concat(k)) for k in ("x", "y", "z", "u", "v", "w", "rho", "m", "p")}
     s["role"] = np.ascontiguousarray(wl.roles(), dtype=np.uint8)
     return s
 
@@ -188,7 +190,8 @@ def rhs(wl, s: Dict[str, np.ndarray], **over) -> Dict[str, np.ndarray]:
                        s["role"].ctypes.data_as(C.POINTER(C.c_uint8)),
                        *(_d(out[k]) for k in ("arho", "ax", "ay", "az", "xsx", "xsy", "xsz",
                                               "rho", "p")),
-                       C.byref(pairs), C.byref(cand))
+                       C.byref(pairs), C.byref(cand),
+                       _d(_f64(s["p"])) if "p" in s else None)
     if rc:
         raise ValueError(f"rhs failed ({rc})")
     out["pairs"] = pairs.value
@@ -203,10 +206,11 @@ def run(wl, s: Dict[str, np.ndarray], dt: float, steps: int, **over):
     for k in ("x", "y", "z", "u", "v", "w", "rho", "m"):
         st[k] = _f64(st[k]).copy()
     n = st["x"].shape[0]
+    st["p"] = _f64(st["p"]).copy() if "p" in st else np.zeros(n)
     hist = np.zeros((steps + 1, HIST))
     rc = lib().ora_run(C.byref(p), n, *(_d(st[k]) for k in ("x", "y", "z", "u", "v", "w", "rho")),
                        _d(st["m"]), st["role"].ctypes.data_as(C.POINTER(C.c_uint8)), float(dt),
-                       int(steps), _d(hist))
+                       int(steps), _d(hist), _d(st["p"]))
     if rc:
         raise ValueError(f"run failed ({rc})")
     return st, hist

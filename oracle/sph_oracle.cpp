@@ -56,7 +56,9 @@ constexpr int KERNEL_WENDLAND_C2 = 1;
 constexpr int KERNEL_CUBIC_SPLINE = 2;
 constexpr int ROLE_FLUID = 0;
 constexpr int PREC_FP32 = 1;
+constexpr int DENSITY_CONTINUITY = 0;
 constexpr int DENSITY_SUMMATION = 1;
+constexpr int DENSITY_EDAC = 2;
 constexpr int WALL_ADAMI = 1;
 constexpr int INTEGRATOR_PEC = 1;
 constexpr double PI = 3.14159265358979323846;
@@ -106,7 +108,7 @@ typedef struct {
     int32_t dim;          // 2 or 3
     int32_t kernel;       // 0 quintic spline, 1 Wendland C2
     int32_t precision;    // precision of the neighbour predicate: 0 FP64, 1 FP32
-    int32_t density;      // 0 continuity equation, 1 summation density
+    int32_t density;      // 0 continuity equation, 1 summation density, 2 EDAC pressure equation
     int32_t periodic[3];  // per axis
     int32_t brute;        // 1: neighbour search by all-pairs loop instead of cells
     int32_t wall_bc;      // 0: wall density from continuity, 1: wall pressure of Adami et al.
@@ -119,6 +121,7 @@ typedef struct {
     double alpha;         // Monaghan artificial viscosity coefficient
     double xsph_eps;      // XSPH coefficient
     double g[3];          // body acceleration
+    double edac_alpha;    // EDAC: pressure diffusivity nu_e = edac_alpha h c0 / 8
 } ora_params;
 
 }  // extern "C"
@@ -332,6 +335,7 @@ struct Neighbours {
 template <class T>
 struct State {
     std::vector<T> x[3], u[3], rho;
+    std::vector<T> p;  // EDAC: the pressure, a state variable (else unused)
 };
 
 template <class T>
@@ -454,7 +458,7 @@ void rhs(const ora_params* P, T nu, T alpha, int64_t n, State<T>& S, const doubl
     /* Eq. (continuity:sph); wall destinations take fluid sources only. The density
      * is then advanced with the rate, like the positions (Sec. 2.1 reading). */
     R.arho.assign(n, T(0.0));
-    if (P->density != DENSITY_SUMMATION) {
+    if (P->density == DENSITY_CONTINUITY) {
 #pragma omp parallel for schedule(dynamic, 256)
         for (int64_t i = 0; i < n; ++i) {
             const bool fluid_i = role[i] == ROLE_FLUID;
@@ -474,8 +478,43 @@ void rhs(const ora_params* P, T nu, T alpha, int64_t n, State<T>& S, const doubl
             for (int64_t i = 0; i < n; ++i) S.rho[i] = S.rho[i] + dt_rho * R.arho[i];
     }
 
+    /* The EDAC scheme (Sec. 2.3 lists it; Sec. 4.1 solves the Taylor-Green vortex with it):
+     * the pressure is a particle variable evolved by
+     *   dp/dt = -rho0 c0^2 div u + nu_e lap p,   nu_e = edac_alpha h c0 / 8,
+     * with the density held at rho0 (particle volumes m / rho0). The SPH forms: the
+     * divergence as in the continuity equation, the Laplacian in the form of the laminar
+     * viscosity term (Eq. mom:sph:visc) with the 0.01 h^2 regulariser,
+     *   dp_i/dt = c0^2 sum_j m_j u_ij . grad_i W_ij
+     *           + (2 nu_e / rho0) sum_j m_j (p_i - p_j) (r_ij . grad_i W_ij) / (r_ij^2 + 0.01 h^2).
+     * The rate sits in the density-rate slot (arho); the pressure is advanced with it like
+     * the density of the continuity form, before the momentum equation reads it. */
+    if (P->density == DENSITY_EDAC) {
+        const double nu_e = P->edac_alpha * P->h * P->c0 / 8.0;
+        const double c2 = P->c0 * P->c0;
+#pragma omp parallel for schedule(dynamic, 256)
+        for (int64_t i = 0; i < n; ++i) {
+            T ap = T(0.0);
+            for (int64_t j : nbr[i]) {
+                T r[3], W, gW[3];
+                diff(i, j, r);
+                T r2 = kern(r, &W, gW);
+                T vdotg = T(0.0), rdotg = T(0.0);
+                for (int d = 0; d < dim; ++d) {
+                    vdotg = vdotg + (S.u[d][i] - S.u[d][j]) * gW[d];
+                    rdotg = rdotg + r[d] * gW[d];
+                }
+                ap = ap + c2 * m[j] * vdotg;
+                ap = ap + 2.0 * nu_e / P->rho0 * m[j] * (S.p[i] - S.p[j]) * rdotg /
+                              (r2 + 0.01 * P->h * P->h);
+            }
+            R.arho[i] = ap;
+        }
+        if (dt_rho != 0.0)
+            for (int64_t i = 0; i < n; ++i) S.p[i] = S.p[i] + dt_rho * R.arho[i];
+    }
+
     R.p.assign(n, T(0.0));
-    for (int64_t i = 0; i < n; ++i) R.p[i] = tait(P, S.rho[i]);
+    for (int64_t i = 0; i < n; ++i) R.p[i] = P->density == DENSITY_EDAC ? S.p[i] : tait(P, S.rho[i]);
 
     /* Solid-wall pressure of Adami, Hu and Adams (2012), the wall boundary condition listed
      * among the schemes of Sec. 2.3 (formula from that reference): a wall particle w takes the kernel-weighted mean of its fluid
@@ -640,7 +679,7 @@ template <class T>
 void pec_step(const ora_params* P, T nu, T alpha, int64_t n, State<T>& S, const double* m,
               const uint8_t* role, Rates<T>& R, Counts& c, double dt) {
     const int dim = P->dim;
-    const bool cont = P->density != DENSITY_SUMMATION;
+    const bool cont = P->density == DENSITY_CONTINUITY;
     State<T> S0 = S;
     for (int64_t i = 0; i < n; ++i) {
         if (role[i] == ROLE_FLUID)
@@ -711,19 +750,31 @@ double run(const ora_params* P, T nu, T alpha, int64_t n, State<T>& S, const dou
 
 template <class T>
 void load_state(const ora_params* P, int64_t n, const double* const* x, const double* const* u,
-                const double* rho, State<T>& S) {
+                const double* rho, State<T>& S, const double* p = nullptr) {
     for (int d = 0; d < 3; ++d) {
         S.x[d].assign(n, T(0.0));
         S.u[d].assign(n, T(0.0));
     }
     S.rho.assign(n, T(0.0));
+    S.p.assign(n, T(0.0));
     for (int64_t i = 0; i < n; ++i) {
         for (int d = 0; d < P->dim; ++d) {
             S.x[d][i] = T(x[d][i]);
             S.u[d][i] = T(u[d][i]);
         }
         S.rho[i] = T(rho[i]);
+        if (p) S.p[i] = T(p[i]);
     }
+}
+
+/* The EDAC form is built for fluid-only problems with the kick-drift-kick integrator:
+ * -5 for walls or the midpoint integrator with it, else 0. */
+int check_edac(const ora_params* P, int64_t n, const uint8_t* role) {
+    if (P->density != DENSITY_EDAC) return 0;
+    if (P->integrator != 0) return -5;
+    for (int64_t i = 0; i < n; ++i)
+        if (role[i] != ROLE_FLUID) return -5;
+    return 0;
 }
 
 }  // namespace
@@ -792,19 +843,21 @@ int64_t ora_neighbors(const ora_params* P, int64_t n, const double* x, const dou
 }
 
 /* One RHS evaluation (the SPHEvaluator use of Sec. 3.4). Outputs per particle:
- * arho, a (3 arrays), xsph (3 arrays), the density used (summation or input) and p. */
+ * arho (the pressure rate with EDAC), a (3 arrays), xsph (3 arrays), the density used
+ * (summation or input) and p. p_in: the pressure of the EDAC form (NULL otherwise). */
 int ora_rhs(const ora_params* P, int64_t n, const double* x, const double* y, const double* z,
             const double* u, const double* v, const double* w, const double* rho,
             const double* m, const uint8_t* role, double* arho, double* ax, double* ay,
             double* az, double* xsx, double* xsy, double* xsz, double* rho_out, double* p_out,
-            int64_t* pairs, int64_t* candidates) {
+            int64_t* pairs, int64_t* candidates, const double* p_in) {
     Grid G;
     int rc = make_grid(P, &G);
     if (rc) return rc;
+    if ((rc = check_edac(P, n, role))) return rc;
     const double* xs[3] = {x, y, z};
     const double* us[3] = {u, v, w};
     State<double> S;
-    load_state(P, n, xs, us, rho, S);
+    load_state(P, n, xs, us, rho, S, p_in);
     Rates<double> R;
     Counts c;
     rhs<double>(P, P->nu, P->alpha, n, S, m, role, R, &c, 0.0);
@@ -824,21 +877,22 @@ int ora_rhs(const ora_params* P, int64_t n, const double* x, const double* y, co
     return 0;
 }
 
-/* nsteps predictor-corrector steps in place on x, y, z, u, v, w, rho.
- * hist (optional) receives (nsteps + 1) records of 10 doubles. dt <= 0 selects the
- * CFL-type time step. Returns 0 or a negative error. */
+/* nsteps predictor-corrector steps in place on x, y, z, u, v, w, rho (and p, the EDAC
+ * pressure; NULL otherwise). hist (optional) receives (nsteps + 1) records of 10 doubles.
+ * dt <= 0 selects the CFL-type time step. Returns 0 or a negative error. */
 int ora_run(const ora_params* P, int64_t n, double* x, double* y, double* z, double* u,
             double* v, double* w, double* rho, const double* m, const uint8_t* role, double dt,
-            int32_t nsteps, double* hist) {
+            int32_t nsteps, double* hist, double* p) {
     Grid G;
     int rc = make_grid(P, &G);
     if (rc) return rc;
+    if ((rc = check_edac(P, n, role))) return rc;
     double* xs[3] = {x, y, z};
     double* us[3] = {u, v, w};
     const double* cx[3] = {x, y, z};
     const double* cu[3] = {u, v, w};
     State<double> S;
-    load_state(P, n, cx, cu, rho, S);
+    load_state(P, n, cx, cu, rho, S, p);
     run<double>(P, P->nu, P->alpha, n, S, m, role, dt, nsteps, hist, nullptr);
     for (int64_t i = 0; i < n; ++i) {
         for (int d = 0; d < P->dim; ++d) {
@@ -846,6 +900,7 @@ int ora_run(const ora_params* P, int64_t n, double* x, double* y, double* z, dou
             us[d][i] = S.u[d][i];
         }
         rho[i] = S.rho[i];
+        if (p) p[i] = S.p[i];
     }
     return 0;
 }
@@ -864,6 +919,7 @@ int ora_grad(const ora_params* P, int64_t n, const double* x, const double* y, c
     if (rc) return rc;
     if (!(dt > 0.0)) return -3;
     if (P->integrator != 0) return -4;  // derivative of the kick-drift-kick map only
+    if (P->density == DENSITY_EDAC) return -5;  // the adjoint covers the density forms
     const double* cx[3] = {x, y, z};
     const double* cu[3] = {u, v, w};
     const double* dirs[3] = {du, dv, dw};

@@ -54,6 +54,7 @@ class ParticleSet:
     w: np.ndarray
     rho: np.ndarray
     m: np.ndarray
+    p: Optional[np.ndarray] = None  # pressure of the EDAC form (a state variable there)
 
     @property
     def n(self) -> int:
@@ -80,7 +81,8 @@ class Workload:
     alpha: float = 0.0
     xsph_eps: float = 0.0
     g: List[float] = field(default_factory=lambda: [0.0, 0.0, 0.0])
-    density: int = 0          # 0 continuity equation, 1 summation density
+    density: int = 0          # 0 continuity, 1 summation density, 2 EDAC pressure equation
+    edac_alpha: float = 0.5   # EDAC pressure diffusivity nu_e = edac_alpha h c0 / 8
     wall_bc: int = 0          # 0 wall density from continuity, 1 wall pressure of Adami et al.
     integrator: int = 0       # 0 kick-drift-kick, 1 midpoint predict-evaluate-correct
     dt: float = 0.0
@@ -95,8 +97,11 @@ class Workload:
         return sum(a.n for a in self.arrays if a.role == FLUID)
 
     def concat(self, prop: str) -> np.ndarray:
-        """Property concatenated over arrays in the given order (global particle ids)."""
-        return np.concatenate([getattr(a, prop) for a in self.arrays])
+        """Property concatenated over arrays in the given order (global particle ids); an
+        array without a pressure contributes zeros to ``p``."""
+        return np.concatenate([
+            np.zeros(a.n) if prop == "p" and a.p is None else getattr(a, prop)
+            for a in self.arrays])
 
     def roles(self) -> np.ndarray:
         return np.concatenate([np.full(a.n, a.role, dtype=np.uint8) for a in self.arrays])
@@ -157,6 +162,25 @@ def taylor_green_2d(n: int = 50, jitter: float = 0.05, re: float = 100.0, U: flo
                     lo=[0.0, 0.0, 0.0], hi=[1.0, 1.0, 0.0], periodic=[1, 1, 0],
                     precision=precision, arrays=[fluid], rho0=rho0, c0=c0,
                     nu=U * 1.0 / re, dt=0.25 * h / c0, steps=steps)
+
+
+def taylor_green_2d_edac(n: int = 100, hdx: float = 1.2, re: float = 100.0, U: float = 1.0,
+                         rho0: float = 1.0, c0: float = 10.0, steps: int = 0,
+                         jitter: float = 0.0, precision: int = PREC_FP64,
+                         seed: Optional[int] = None, t_end: float = 2.0) -> Workload:
+    """The Taylor-Green vortex as Sec. 4.1 runs it with the EDAC scheme: periodic unit
+    square, n x n lattice (100 x 100 in the paper), quintic kernel with h = 1.2 dx, U = 1,
+    Re = 100, up to t = 2 s. Velocity and pressure at t = 0 from the printed exact solution,
+    p = -U^2 (cos(4 pi x) + cos(4 pi y)) / 4 (times rho0); the density stays rho0.
+    ``steps`` = 0 takes t_end / dt steps."""
+    wl = taylor_green_2d(n=n, jitter=jitter, re=re, U=U, rho0=rho0, c0=c0, precision=precision,
+                         seed=seed, hdx=hdx)
+    a = wl.arrays[0]
+    a.p = -rho0 * U * U * (np.cos(4 * np.pi * a.x) + np.cos(4 * np.pi * a.y)) / 4.0
+    wl.density = 2
+    wl.name = f"taylor_green_2d_edac_{n}x{n}"
+    wl.steps = steps if steps > 0 else int(round(t_end / wl.dt))
+    return wl
 
 
 def taylor_green_3d(n: int = 64, jitter: float = 0.05, re: float = 100.0, U: float = 1.0,
