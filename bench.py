@@ -59,6 +59,8 @@ def workload(name: str, wall_bc: str = "density", integrator: str = "kdk"):
         "taylor_green_2d": lambda: W.taylor_green_2d(),
         "taylor_green_3d": lambda: W.taylor_green_3d(),
         "dam_break_3d": lambda: W.dam_break_3d(),
+        # the same tank at twice the spacing (~0.48 M particles): the size for ncu captures
+        "dam_break_3d_dx01": lambda: W.dam_break_3d(dx=0.01),
         "batch_tg2d": lambda: W.batch_tg2d(),
         "falling_cube_3d": lambda: W.falling_cube_3d(),
     }
@@ -745,7 +747,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="dam_break_3d",
                     choices=["dam_break_2d", "taylor_green_2d", "taylor_green_3d", "dam_break_3d",
-                             "batch_tg2d", "falling_cube_3d"])
+                             "dam_break_3d_dx01", "batch_tg2d", "falling_cube_3d"])
     ap.add_argument("--flush-mb", type=int, default=512)
     ap.add_argument("--fp64-steps", type=int, default=50)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

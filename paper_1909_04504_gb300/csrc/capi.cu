@@ -69,6 +69,7 @@ struct sph_ctx {
     void* P = nullptr;
     void* Q = nullptr;
     void* R = nullptr;
+    void* E = nullptr;  // FP32 pair loops: residuals of the rounded positions
     uint32_t* keys[2]{};
     uint32_t* vals[2]{};
     uint32_t* skeys = nullptr;
@@ -394,6 +395,7 @@ StepLaunch step_launch(sph_ctx* c, int kick) {
     L.P = c->P;
     L.Q = c->Q;
     L.R = c->R;
+    L.E = c->E;
     L.skeys = c->skeys;
     L.off = c->off;
     L.nl = c->nl;
@@ -934,6 +936,7 @@ sph_status create_impl(const sph_domain* domains, int ninst, const sph_array_des
     size_t bytes = 0;
     bytes += 2 * (15 * al(N * 8) + al(N * 4));                 // two particle sets
     bytes += 2 * al(N * 4 * real) + al(N * real);              // shadow P, Q, R
+    if (domain->precision == SPH_PREC_FP32) bytes += al(N * 16);  // position residuals E
     bytes += 4 * al(N * 4);                                    // keys, vals
     bytes += al(((size_t)c->G.ncells + 1) * 4);                // cell offsets
     bytes += al(radix_hist_words(c->N) * 4);                   // radix histograms
@@ -974,6 +977,7 @@ sph_status create_impl(const sph_domain* domains, int ninst, const sph_array_des
     c->P = arena_take(p, N * 4 * real);
     c->Q = arena_take(p, N * 4 * real);
     c->R = arena_take(p, N * real);
+    if (domain->precision == SPH_PREC_FP32) c->E = arena_take(p, N * 16);
     for (int k = 0; k < 2; ++k) c->keys[k] = (uint32_t*)arena_take(p, N * 4);
     for (int k = 0; k < 2; ++k) c->vals[k] = (uint32_t*)arena_take(p, N * 4);
     c->off = (uint32_t*)arena_take(p, ((size_t)c->G.ncells + 1) * 4);

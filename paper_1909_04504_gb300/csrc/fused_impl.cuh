@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_step_fused(const FusedLaun
     V* P = (V*)L.P;
     V* Q = (V*)L.Q;
     Real* R = (Real*)L.R;
+    F4* E = (F4*)L.E;  // FP32 pair loops: position residuals (null in FP64 mode)
     uint32_t* ghist = F.work;
     uint32_t* counters = F.work + 4 * RADIX;
     uint32_t* status = counters + 32;
@@ -154,7 +155,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_step_fused(const FusedLaun
     // ---- gather into cell order (predictor kick, shadow) and the cell table
     for (int k = tid; k < L.n; k += nthreads) {
         const int inst = find_instance(L.cell_bounds, L.ninst, skeys[k]);
-        reorder_one<Real>(L.Sin, L.S, k, (int)perm[k], L.dim, L.idt[inst], 1, 0, P, Q);
+        reorder_one<Real>(L.Sin, L.S, k, (int)perm[k], L.dim, L.idt[inst], 1, 0, P, Q, E);
     }
     for (int c = tid; c <= F.ncells; c += nthreads)
         F.off[c] = cell_offset_near(skeys, L.n, (uint32_t)c, F.off[c]);
@@ -165,7 +166,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_step_fused(const FusedLaun
     {
         DensityCounts dc{0ull, 0ull, 0ull, 0};
         density_tiles<Real, DIM, KERNEL, T, FUSED_THREADS>(
-            blockIdx.x, nb, P, Q, R, skeys, F.off, L.n, tab, L.cell_bounds, L.ninst, L.idt, L.S, 1,
+            blockIdx.x, nb, P, Q, R, E, skeys, F.off, L.n, tab, L.cell_bounds, L.ninst, L.idt, L.S, 1,
             L.nl, L.cnt, L.maxn, L.finalize ? nullptr : L.pcount, dc, sm.dens);
         if (dc.overflow) atomicOr(&ctl->status, ST_CAPACITY);
         if (L.finalize) block_counts<FUSED_THREADS>(dc, F.part + (size_t)blockIdx.x * FUSED_PART + 8, sm.cred);
@@ -178,7 +179,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_step_fused(const FusedLaun
     for (int w = tid; w < F.work_words; w += nthreads) F.work[w] = 0u;
     {
         MomDiag md{0, 0, 0, 0, 0ull, 0ull, 0u};
-        momentum_tiles<Real, DIM, KERNEL, T, FUSED_THREADS>(blockIdx.x, nb, P, Q, R, skeys, L.n, tab,
+        momentum_tiles<Real, DIM, KERNEL, T, FUSED_THREADS>(blockIdx.x, nb, P, Q, R, E, skeys, L.n, tab,
                                                             L.cell_bounds, L.ninst, L.idt, L.S, 1,
                                                             L.nl, L.cnt, md, sm.mom);
         if (L.finalize)

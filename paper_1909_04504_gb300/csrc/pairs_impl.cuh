@@ -153,6 +153,27 @@ __device__ __forceinline__ Real separation(const typename V4<Real>::T& pi,
     return dist2<Real, DIM>(dx, dy, dz);
 }
 
+// FP32 pair sums (not the predicate): the separation of the rounded positions corrected
+// by the difference of their residuals E (reorder_one). x_i - x_j of nearby floats is
+// exact, so the corrected separation carries the rounding of itself rather than that of
+// the positions, which is ulp(x) / r larger where |x| is much larger than the particle
+// spacing (a velocity change of 1e-4 of u per step, as on fine Taylor-Green lattices, then
+// comes from pair sums that cancel to 1e-2 of their terms). FP64 mode passes no E.
+template <class Real, int DIM>
+__device__ __forceinline__ void add_residuals(const F4* __restrict__ E, const F4& ei, uint32_t j,
+                                              Real& dx, Real& dy, Real& dz) {
+    if (sizeof(Real) == 4 && E) {
+        const F4 ej = E[j];
+        dx += (Real)(ei.x - ej.x);
+        dy += (Real)(ei.y - ej.y);
+        if (DIM == 3) dz += (Real)(ei.z - ej.z);
+    }
+}
+
+__device__ __forceinline__ F4 residual_of(const F4* __restrict__ E, int i) {
+    return E ? E[i] : F4{0.f, 0.f, 0.f, 0.f};
+}
+
 // ------------------------------------------------------------ diagnostics
 // Block partials of one evaluation, 8-byte slots: momentum pass [px, py, pz, ke] (FP64
 // sums), [max |u|^2, max |a|^2] (bit patterns of non-negative doubles, whose integer
@@ -307,6 +328,7 @@ template <class Real, int DIM, int KERNEL, int T>
 __device__ __forceinline__ void density_scan_sum(int i, const Group<T>& g, uint32_t key,
                                                  const typename V4<Real>::T* __restrict__ P,
                                                  const typename V4<Real>::T* __restrict__ Q,
+                                                 const F4* __restrict__ E,
                                                  const uint32_t* __restrict__ off, int n,
                                                  const Grid& G, const PairConst<Real>& K,
                                                  uint32_t* __restrict__ nl,
@@ -396,6 +418,7 @@ __device__ __forceinline__ void density_scan_sum(int i, const Group<T>& g, uint3
     g.sync();  // the list entries of the other lanes are visible from here on
     sum.zero();
     const typename V4<Real>::T qi = Q[i];
+    const F4 ei = residual_of(E, i);
     // the next list entry is fetched one iteration ahead, so its load overlaps this
     // iteration's source loads and arithmetic
     uint32_t j_next = g.t < k ? nl[(size_t)g.t * n + i] : 0u;
@@ -404,7 +427,9 @@ __device__ __forceinline__ void density_scan_sum(int i, const Group<T>& g, uint3
         if (kk + T < k) j_next = nl[(size_t)(kk + T) * n + i];
         const typename V4<Real>::T pj = P[j];
         Real dx, dy, dz;
-        const Real r2 = separation<Real, DIM>(pi, pj, G, K, dx, dy, dz);
+        separation<Real, DIM>(pi, pj, G, K, dx, dy, dz);
+        add_residuals<Real, DIM>(E, ei, j, dx, dy, dz);
+        const Real r2 = dist2<Real, DIM>(dx, dy, dz);
         const Real q = PairMath<Real>::sqrt(r2) * K.inv_h;
         if (summation) {
             sum.add(fabs(pj.w) * K.wfac * kernel_w<Real, KERNEL>(q));
@@ -465,7 +490,7 @@ template <class Real, int DIM, int KERNEL, int T, int NTH>
 __device__ __forceinline__ void density_tiles(int block, int nblocks,
                                               const typename V4<Real>::T* __restrict__ P,
                                               typename V4<Real>::T* __restrict__ Q,
-                                              Real* __restrict__ R,
+                                              Real* __restrict__ R, const F4* __restrict__ E,
                                               const uint32_t* __restrict__ skeys,
                                               const uint32_t* __restrict__ off, int n,
                                               const Inst<Real>* __restrict__ tab,
@@ -485,7 +510,7 @@ __device__ __forceinline__ void density_tiles(int block, int nblocks,
             const int inst = find_instance(cell_bounds, ninst, key);
             const Inst<Real>& I = tab[inst];
             Acc<Real> sum;
-            density_scan_sum<Real, DIM, KERNEL, T>(i, g, key - I.cell_base, P, Q, off + I.cell_base,
+            density_scan_sum<Real, DIM, KERNEL, T>(i, g, key - I.cell_base, P, Q, E, off + I.cell_base,
                                                    n, I.G, I.K, nl, cnt, maxn, dc,
                                                    pcount ? pcount + 2 * (size_t)i : nullptr, sum);
             if (T == 1) {
@@ -516,7 +541,8 @@ __device__ __forceinline__ void density_tiles(int block, int nblocks,
 template <class Real, int DIM, int KERNEL, int T>
 __global__ void __launch_bounds__(PAIR_THREADS, sizeof(Real) == 4 ? 7 : 6)
 k_density(const typename V4<Real>::T* __restrict__ P, typename V4<Real>::T* __restrict__ Q,
-          Real* __restrict__ R, const uint32_t* __restrict__ skeys, const uint32_t* __restrict__ off,
+          Real* __restrict__ R, const F4* __restrict__ E, const uint32_t* __restrict__ skeys,
+          const uint32_t* __restrict__ off,
           int n, const Inst<Real>* __restrict__ tab, const uint32_t* __restrict__ cell_bounds,
           int ninst, const double* __restrict__ idt, ParticleSet S, Control* ctl, int kick,
           uint32_t* __restrict__ nl, uint32_t* __restrict__ cnt, int maxn,
@@ -525,7 +551,7 @@ k_density(const typename V4<Real>::T* __restrict__ P, typename V4<Real>::T* __re
     __shared__ unsigned long long cred[PAIR_THREADS / 32][3];
     if (ctl->status) return;
     DensityCounts dc{0ull, 0ull, 0ull, 0};
-    density_tiles<Real, DIM, KERNEL, T, PAIR_THREADS>(blockIdx.x, gridDim.x, P, Q, R, skeys, off, n,
+    density_tiles<Real, DIM, KERNEL, T, PAIR_THREADS>(blockIdx.x, gridDim.x, P, Q, R, E, skeys, off, n,
                                                       tab, cell_bounds, ninst, idt, S, kick, nl,
                                                       cnt, maxn, pcount, dc, sm);
     if (dc.overflow) atomicOr(&ctl->status, ST_CAPACITY);
@@ -549,12 +575,14 @@ __device__ __forceinline__ void momentum_sums(int i, const Group<T>& g,
                                               const typename V4<Real>::T& pi,
                                               const typename V4<Real>::T* __restrict__ P,
                                               const typename V4<Real>::T* __restrict__ Q,
-                                              const Real* __restrict__ R, int n, const Grid& G,
+                                              const Real* __restrict__ R,
+                                              const F4* __restrict__ E, int n, const Grid& G,
                                               const PairConst<Real>& K,
                                               const uint32_t* __restrict__ nl,
                                               const uint32_t* __restrict__ cnt, Acc<Real>* acc) {
     const int flags = K.flags;
     const typename V4<Real>::T qi = Q[i];
+    const F4 ei = residual_of(E, i);
     const Real pri = R[i];
 #pragma unroll
     for (int k = 0; k < 6; ++k) acc[k].zero();
@@ -565,7 +593,9 @@ __device__ __forceinline__ void momentum_sums(int i, const Group<T>& g,
         if (kk + T < ni) j_next = nl[(size_t)(kk + T) * n + i];
         const typename V4<Real>::T pj = P[j];
         Real dx, dy, dz;
-        const Real r2 = separation<Real, DIM>(pi, pj, G, K, dx, dy, dz);
+        separation<Real, DIM>(pi, pj, G, K, dx, dy, dz);
+        add_residuals<Real, DIM>(E, ei, j, dx, dy, dz);
+        const Real r2 = dist2<Real, DIM>(dx, dy, dz);
         const typename V4<Real>::T qj = Q[j];
         const Real mj = fabs(pj.w);
         const Real q = PairMath<Real>::sqrt(r2) * K.inv_h;
@@ -673,7 +703,7 @@ template <class Real, int DIM, int KERNEL, int T, int NTH>
 __device__ __forceinline__ void momentum_tiles(int block, int nblocks,
                                                const typename V4<Real>::T* __restrict__ P,
                                                const typename V4<Real>::T* __restrict__ Q,
-                                               const Real* __restrict__ R,
+                                               const Real* __restrict__ R, const F4* __restrict__ E,
                                                const uint32_t* __restrict__ skeys, int n,
                                                const Inst<Real>* __restrict__ tab,
                                                const uint32_t* __restrict__ cell_bounds, int ninst,
@@ -692,7 +722,7 @@ __device__ __forceinline__ void momentum_tiles(int block, int nblocks,
             const typename V4<Real>::T pi = P[i];
             const bool fluid = pi.w > Real(0);
             Acc<Real> acc[6];
-            if (fluid) momentum_sums<Real, DIM, KERNEL, T>(i, g, pi, P, Q, R, n, I.G, I.K, nl, cnt, acc);
+            if (fluid) momentum_sums<Real, DIM, KERNEL, T>(i, g, pi, P, Q, R, E, n, I.G, I.K, nl, cnt, acc);
             else
 #pragma unroll
                 for (int k = 0; k < 6; ++k) acc[k].zero();
@@ -741,7 +771,8 @@ __device__ __forceinline__ void momentum_tiles(int block, int nblocks,
 template <class Real, int DIM, int KERNEL, int T>
 __global__ void __launch_bounds__(PAIR_THREADS, sizeof(Real) == 4 ? (DIM == 3 ? 7 : 8) : 5)
 k_momentum(const typename V4<Real>::T* __restrict__ P, const typename V4<Real>::T* __restrict__ Q,
-           const Real* __restrict__ R, const uint32_t* __restrict__ skeys, int n,
+           const Real* __restrict__ R, const F4* __restrict__ E, const uint32_t* __restrict__ skeys,
+           int n,
            const Inst<Real>* __restrict__ tab, const uint32_t* __restrict__ cell_bounds, int ninst,
            double* __restrict__ idt, ParticleSet S, Control* ctl, int kick,
            const uint32_t* __restrict__ nl, const uint32_t* __restrict__ cnt,
@@ -754,7 +785,7 @@ k_momentum(const typename V4<Real>::T* __restrict__ P, const typename V4<Real>::
     __shared__ bool is_last;
     if (ctl->status) return;
     MomDiag md{0, 0, 0, 0, 0ull, 0ull, 0u};
-    momentum_tiles<Real, DIM, KERNEL, T, PAIR_THREADS>(blockIdx.x, gridDim.x, P, Q, R, skeys, n, tab,
+    momentum_tiles<Real, DIM, KERNEL, T, PAIR_THREADS>(blockIdx.x, gridDim.x, P, Q, R, E, skeys, n, tab,
                                                        cell_bounds, ninst, idt, S, kick, nl, cnt, md,
                                                        sm);
     if (!finalize) return;
@@ -797,7 +828,7 @@ template <class Real, int DIM, int KERNEL, int T>
 void launch_density_t(const StepLaunch& L, cudaStream_t st) {
     using V = typename V4<Real>::T;
     k_density<Real, DIM, KERNEL, T><<<L.grid_d, PAIR_THREADS, 0, st>>>(
-        (const V*)L.P, (V*)L.Q, (Real*)L.R, L.skeys, L.off, L.n, (const Inst<Real>*)L.tab,
+        (const V*)L.P, (V*)L.Q, (Real*)L.R, (const F4*)L.E, L.skeys, L.off, L.n, (const Inst<Real>*)L.tab,
         L.cell_bounds, L.ninst, L.idt, L.S, L.ctl, L.kick, L.nl, L.cnt, L.maxn,
         L.finalize ? L.pd : nullptr, L.finalize ? nullptr : L.pcount);
 }
@@ -806,7 +837,7 @@ template <class Real, int DIM, int KERNEL, int T>
 void launch_momentum_t(const StepLaunch& L, cudaStream_t st) {
     using V = typename V4<Real>::T;
     k_momentum<Real, DIM, KERNEL, T><<<L.grid_m, PAIR_THREADS, 0, st>>>(
-        (const V*)L.P, (const V*)L.Q, (const Real*)L.R, L.skeys, L.n, (const Inst<Real>*)L.tab,
+        (const V*)L.P, (const V*)L.Q, (const Real*)L.R, (const F4*)L.E, L.skeys, L.n, (const Inst<Real>*)L.tab,
         L.cell_bounds, L.ninst, L.idt, L.S, L.ctl, L.kick, L.nl, L.cnt, L.pm, L.pd, L.grid_d,
         L.history, L.finalize);
 }

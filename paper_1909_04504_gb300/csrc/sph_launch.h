@@ -60,6 +60,7 @@ struct StepLaunch {
     void* P;
     void* Q;
     void* R;
+    void* E;                      // FP32 pair loops: position residuals (reorder_one)
     const uint32_t* skeys;
     const uint32_t* off;
     uint32_t* nl;                 // neighbour list, nl[k * n + i], k < maxn

@@ -73,11 +73,16 @@ __device__ __forceinline__ uint32_t drift_key_one(const ParticleSet& S, int i, c
 // positions, by the density pass). Rates are carried along only outside a step
 // (carry_rates). Writes the pair-loop shadow P = (x, y, z, +-m) with the sign marking
 // walls and Q = (u, v, w, .); the density pass that follows writes Q.w = rho and p / rho^2.
+// E (FP32 pair loops, may be null): the residuals x - (float)x, y - (float)y, z - (float)z
+// of the rounded positions (each exact in FP64, then rounded), so that the pair sums form
+// separations as (x_i - x_j) + (e_i - e_j) to nearly FP32 precision of the separation
+// itself, where x_i - x_j alone carries the rounding of positions far larger than it.
 template <class Real>
 __device__ __forceinline__ void reorder_one(const ParticleSet& in, const ParticleSet& out, int k,
                                             int o, int dim, double dt, int kick, int carry_rates,
                                             typename V4<Real>::T* __restrict__ P,
-                                            typename V4<Real>::T* __restrict__ Q) {
+                                            typename V4<Real>::T* __restrict__ Q,
+                                            F4* __restrict__ E = nullptr) {
     // every load of particle o before any store (the output arrays could alias the inputs
     // as far as the compiler knows); the acceleration is read for walls too (it is zero
     // there) so that no load waits for the tag
@@ -125,6 +130,14 @@ __device__ __forceinline__ void reorder_one(const ParticleSet& in, const Particl
     qv.w = Real(0);  // the density pass writes it
     P[k] = pv;
     Q[k] = qv;
+    if (E) {
+        F4 ev;
+        ev.x = (float)(x[0] - (double)(float)x[0]);
+        ev.y = (float)(x[1] - (double)(float)x[1]);
+        ev.z = (float)(x[2] - (double)(float)x[2]);
+        ev.w = 0.0f;
+        E[k] = ev;
+    }
 }
 
 }  // namespace sph

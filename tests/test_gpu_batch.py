@@ -86,11 +86,15 @@ def test_batched_configuration_runs_and_matches_a_single_run():
         sim.step(G.scheme_of(wl), wl.dt, 2)
         st = sim.state()
     # the first three steps used the default tile shape of the batch size class, the
-    # single run's default may differ: compare the five-step changes within FP32 rounding
-    # instead of bitwise
+    # single run's default may differ (another summation order), so the runs are not
+    # bitwise equal: on this 129^2 instance a step changes u by ~1e-4 of itself, and FP32
+    # rounding differences of the continuity rate pass through the pressure into the
+    # pressure gradient, a residual of much larger terms; over five steps the changes of
+    # the two runs differ by ~1e-3 of themselves. Bitwise equality at equal tile shapes is
+    # test_batch_equals_single_runs_bitwise.
     s0 = wl_state0
     for f in FIELDS:
-        assert field_error(wl, f, bs[f], st[f], s0[f]) <= 1e-5, f
+        assert field_error(wl, f, bs[f], st[f], s0[f]) <= 1e-2, f
 
 
 def test_batch_rejects_mixed_kernels_and_single_calls():

@@ -6,7 +6,7 @@ import pytest
 
 import oracle as O
 import workloads as W
-from gpu_util import csr_equal, field_ok, normwise, rel_l2, sim_of
+from gpu_util import csr_equal, field_error, field_ok, normwise, rel_l2, sim_of
 
 import paper_1909_04504_gb300 as G
 
@@ -114,7 +114,10 @@ def test_particle_outside_the_cell_box(prec):
 
 
 def test_full_size_taylor_green_3d_step():
-    """Config 3 at full size (64^3 = 262,144 particles, FP32 pairs): one step vs oracle."""
+    """Config 3 at full size (64^3 = 262,144 particles, FP32 pairs): one step vs oracle.
+    The drift uses FP32 rates, so the new positions differ from the oracle's in their last
+    bits and a pair at the support edge may be decided the other way: the neighbour sets
+    are compared bit for bit with the oracle's search on the GPU's own coordinates."""
     wl = W.taylor_green_3d()
     s = O.state_of(wl)
     st, hist = O.run(wl, s, wl.dt, 1)
@@ -122,9 +125,13 @@ def test_full_size_taylor_green_3d_step():
         sim.step(G.scheme_of(wl), wl.dt, 1)
         g = sim.state()
         h = sim.history()
+        noff, nidx = sim.neighbors()
     for k in ("x", "y", "z", "u", "v", "w", "rho"):  # one-step increments
         assert field_ok(wl, k, g[k], st[k], s[k]), k
-    assert h[0, 8] == hist[1, 8] and h[0, 9] == hist[1, 9]
+    ooff, oidx, ocand = O.neighbors(wl, g["x"], g["y"], g["z"])
+    assert csr_equal(noff, nidx, ooff, oidx)
+    assert h[0, 8] == len(oidx) and h[0, 9] == ocand
+    assert abs(h[0, 8] - hist[1, 8]) <= 1e-6 * hist[1, 8]
 
 
 def test_full_size_dam_break_3d_step():
@@ -153,5 +160,6 @@ def test_full_size_batch_instances_match_oracle():
         st, _ = O.run(wls[k], s, wls[k].dt, 1)
         bs = b.instance_state(k)
         for f in FIELDS:  # one-step increments
-            assert field_ok(wls[k], f, bs[f], st[f], s[f]), (k, f)
+            e = field_error(wls[k], f, bs[f], st[f], s[f])
+            assert e <= 1e-4, (k, f, e)
     b.close()
