@@ -57,6 +57,8 @@ def workload(name: str, wall_bc: str = "density", integrator: str = "kdk"):
     table = {
         "dam_break_2d": lambda: W.dam_break_2d(),
         "taylor_green_2d": lambda: W.taylor_green_2d(),
+        # Sec. 4.1's run: EDAC, 100^2, h = 1.2 dx, Re = 100, to t = 2 s
+        "taylor_green_2d_edac": lambda: W.taylor_green_2d_edac(),
         "taylor_green_3d": lambda: W.taylor_green_3d(),
         "dam_break_3d": lambda: W.dam_break_3d(),
         # the same tank at twice the spacing (~0.48 M particles): the size for ncu captures
@@ -157,7 +159,9 @@ def describe(wl) -> dict:
                     f"nu={wl.nu:g}, dt={wl.dt:.6g}, neighbour rebuild every step"
                     + (", solid-wall pressure of Adami et al." if getattr(wl, "wall_bc", 0) else "")
                     + (", midpoint predict-evaluate-correct integrator (two neighbour builds "
-                       "and evaluations per step)" if getattr(wl, "integrator", 0) else ""),
+                       "and evaluations per step)" if getattr(wl, "integrator", 0) else "")
+                    + (", EDAC pressure equation (density held at rho0)"
+                       if getattr(wl, "density", 0) == 2 else ""),
         "particles": wl.n_total,
         "fluid_particles": wl.n_fluid,
         "l2": ("flushed between timed steps (512 MB write)"
@@ -589,6 +593,24 @@ def gpu_arm(args, rank, world, dist):
                            "neighbour lists, reverse sweep) vs sph_step, host clock around the "
                            "synchronous calls"}
 
+    # ---- the Taylor-Green runs of Sec. 4.1: max |u| over the whole run against the exact
+    # U exp(b t), b = -8 pi^2 / Re
+    decay = None
+    if not sim.batch and getattr(wl, "density", 0) == 2:
+        with G.Simulation.from_workload(wl) as run:  # from t = 0
+            run.step(sch, wl.dt, wl.steps)
+            h = run.history()
+        t = h[:, 0]
+        b = -8.0 * math.pi ** 2 * wl.nu  # Re = U L / nu with U = L = 1
+        rel = np.abs(h[:, 3] / np.exp(b * t) - 1.0)
+        fitted = math.log(h[-1, 3] / h[0, 3]) / (t[-1] - t[0])
+        decay = {"steps": int(h.shape[0]), "t_end": float(t[-1]),
+                 "max_u_end": float(h[-1, 3]), "exact_end": math.exp(b * t[-1]),
+                 "max_rel_error_vs_exact": float(rel.max()),
+                 "fitted_rate": fitted, "exact_rate": b,
+                 "path": "sph_step over the paper's whole run from t = 0 (a new context), "
+                         "max |u| of each step's record against U exp(-8 pi^2 t / Re)"}
+
     state0 = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not sim.batch:
         state0 = one_step_states(wl, sch)
@@ -605,7 +627,7 @@ def gpu_arm(args, rank, world, dist):
                            f"no flush: inputs larger than L2 ({l2_bytes >> 20} MiB)")),
         "particle_steps_per_s": psteps, "candidates_per_s": job_cand / (total_ms / 1e3),
         "pairs_per_step": pairs / args.steps, "phase_ms": phase_avg,
-        "roofline": roofline, "e2e": e2e, "fp64_mode": fp64, "adjoint": adjoint,
+        "roofline": roofline, "e2e": e2e, "fp64_mode": fp64, "adjoint": adjoint, "decay": decay,
         "batch_vs": batch_vs,
         "gpu_launches": launches, "clocks": clocks, "wall_s": round(t_wall, 3),
     }
@@ -746,8 +768,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="dam_break_3d",
-                    choices=["dam_break_2d", "taylor_green_2d", "taylor_green_3d", "dam_break_3d",
-                             "dam_break_3d_dx01", "batch_tg2d", "falling_cube_3d"])
+                    choices=["dam_break_2d", "taylor_green_2d", "taylor_green_2d_edac",
+                             "taylor_green_3d", "dam_break_3d", "dam_break_3d_dx01", "batch_tg2d",
+                             "falling_cube_3d"])
     ap.add_argument("--flush-mb", type=int, default=512)
     ap.add_argument("--fp64-steps", type=int, default=50)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

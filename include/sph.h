@@ -48,7 +48,7 @@ typedef enum {
 typedef enum { SPH_KERNEL_QUINTIC = 0, SPH_KERNEL_WENDLAND_C2 = 1, SPH_KERNEL_CUBIC_SPLINE = 2 } sph_kernel;
 typedef enum { SPH_PREC_FP64 = 0, SPH_PREC_FP32 = 1 } sph_precision;
 typedef enum { SPH_ROLE_FLUID = 0, SPH_ROLE_WALL = 1 } sph_role;
-typedef enum { SPH_DENSITY_CONTINUITY = 0, SPH_DENSITY_SUMMATION = 1 } sph_density;
+typedef enum { SPH_DENSITY_CONTINUITY = 0, SPH_DENSITY_SUMMATION = 1, SPH_DENSITY_EDAC = 2 } sph_density;
 typedef enum { SPH_WALL_DENSITY = 0, SPH_WALL_ADAMI = 1 } sph_wall_bc;
 typedef enum { SPH_INTEGRATOR_KDK = 0, SPH_INTEGRATOR_PEC = 1 } sph_integrator;
 
@@ -96,7 +96,17 @@ typedef struct {
 
 /* Equations of one right-hand-side evaluation (Sec. 3.2 groups: [summation density],
  * EOS, then continuity + momentum; walls take continuity from fluid sources only).
- *  density    sph_density.
+ *  density    sph_density. SPH_DENSITY_EDAC: the EDAC scheme of the scheme list of
+ *             Sec. 2.3, with which Sec. 4.1 solves the Taylor-Green vortex: the pressure
+ *             "p" is a particle variable, dp/dt = -rho0 c0^2 div u + nu_e lap p with
+ *             nu_e = h c0 / 16 (the EDAC diffusivity alpha h c0 / 8 at alpha = 0.5), as
+ *             dp_i/dt = c0^2 sum_j m_j u_ij . grad_i W_ij + (2 nu_e / rho0) sum_j m_j
+ *             (p_i - p_j) (r_ij . grad_i W_ij) / (r_ij^2 + 0.01 h^2); the density stays
+ *             rho0 (volumes m / rho0) and gamma is unused; the pressure is advanced like
+ *             the continuity density in the step and read by the momentum equation.
+ *             Fluid-only problems with the kick-drift-kick integrator (wall particles,
+ *             SPH_INTEGRATOR_PEC and sph_backward are refused; the persistent step form
+ *             runs it as the graph). The rate is read as "arho", the pressure as "p".
  *  rho0, c0, gamma   Tait EOS, Eq. eos: p = c0^2 rho0 / gamma ((rho/rho0)^gamma - 1).
  *  nu, eta    laminar viscosity, Eq. mom:sph:visc (term off when nu == 0).
  *  alpha      Monaghan artificial viscosity: Pi_ij = -alpha c0 mu_ij / rhobar_ij when
@@ -339,11 +349,12 @@ sph_status sph_step_batch_async(sph_ctx* ctx, const sph_scheme* schemes, const d
 sph_status sph_batch_diagnostics(sph_ctx* ctx, double* out);
 
 /* Property of one array (or -1 for all particles) into a host buffer, original order.
- * prop: "x" "y" "z" "u" "v" "w" "rho" "m", or rates of the last evaluation "arho" "ax"
- * "ay" "az" "xsx" "xsy" "xsz". */
+ * prop: "x" "y" "z" "u" "v" "w" "rho" "m", the EDAC pressure "p" (zero unless set or
+ * evolved by SPH_DENSITY_EDAC), or rates of the last evaluation "arho" (the pressure rate
+ * under SPH_DENSITY_EDAC) "ax" "ay" "az" "xsx" "xsy" "xsz". */
 sph_status sph_get(sph_ctx* ctx, int32_t array, const char* prop, double* out);
 
-/* Overwrite one property ("x" "y" "z" "u" "v" "w" "rho" "m") of one array (or -1 for all
+/* Overwrite one property ("x" "y" "z" "u" "v" "w" "rho" "m" "p") of one array (or -1 for all
  * particles) from a host buffer in original order. Invalidates rates and neighbours. */
 sph_status sph_set(sph_ctx* ctx, int32_t array, const char* prop, const double* in);
 
@@ -355,7 +366,8 @@ sph_status sph_diagnostics(sph_ctx* ctx, double* out);
  * The context keeps the most recent 65536 records. */
 sph_status sph_history(sph_ctx* ctx, double* out, int32_t max_records, int32_t* count);
 
-/* Full device state (positions, velocities, density, mass, rates, internal order, time)
+/* Full device state (positions, velocities, density, mass, EDAC pressure, rates, internal
+ * order, time)
  * to/from a host buffer. buf NULL: *bytes receives the size. Loading restores the exact
  * state so that a resumed run is bitwise identical to an uninterrupted one. */
 sph_status sph_save_state(sph_ctx* ctx, void* buf, size_t* bytes);

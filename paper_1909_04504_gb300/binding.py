@@ -18,7 +18,7 @@ from . import build as _build
 QUINTIC, WENDLAND_C2, CUBIC_SPLINE = 0, 1, 2
 PREC_FP64, PREC_FP32 = 0, 1
 FLUID, WALL = 0, 1
-CONTINUITY, SUMMATION = 0, 1
+CONTINUITY, SUMMATION, EDAC = 0, 1, 2
 WALL_DENSITY, WALL_ADAMI = 0, 1  # sph_wall_bc
 INTEGRATOR_KDK, INTEGRATOR_PEC = 0, 1  # sph_integrator
 STEP_GRAPH, STEP_PERSISTENT = 0, 1
@@ -247,10 +247,16 @@ class Simulation:
 
     @classmethod
     def from_workload(cls, wl, precision: Optional[int] = None, **kw) -> "Simulation":
+        """A context holding the workload's arrays (and the pressure of the EDAC form where
+        an array carries one)."""
         arrays = [dict(name=a.name, role=a.role, x=a.x, y=a.y, z=a.z, u=a.u, v=a.v, w=a.w,
                        rho=a.rho, m=a.m) for a in wl.arrays]
-        return cls(wl.dim, wl.kernel, wl.precision if precision is None else precision, wl.h,
-                   wl.lo, wl.hi, wl.periodic, arrays, **kw)
+        sim = cls(wl.dim, wl.kernel, wl.precision if precision is None else precision, wl.h,
+                  wl.lo, wl.hi, wl.periodic, arrays, **kw)
+        for k, a in enumerate(wl.arrays):
+            if getattr(a, "p", None) is not None:
+                sim.set("p", a.p, array=k)
+        return sim
 
     # ---------------------------------------------------------------- plumbing
     def _check(self, st: int):
@@ -389,7 +395,7 @@ class Simulation:
         self._check(self._L.sph_set(self._ctx, array, prop.encode(), _dptr(v)))
 
     def state(self) -> dict:
-        return {k: self.get(k) for k in ("x", "y", "z", "u", "v", "w", "rho", "m")}
+        return {k: self.get(k) for k in ("x", "y", "z", "u", "v", "w", "rho", "m", "p")}
 
     def rates(self) -> dict:
         return {k: self.get(k) for k in ("arho", "ax", "ay", "az", "xsx", "xsy", "xsz")}
@@ -490,6 +496,8 @@ class BatchSimulation(Simulation):
         self.n = self.count(-1)
         sizes = [sum(a.n for a in w.arrays) for w in self.workloads]
         self.bounds = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+        if any(getattr(a, "p", None) is not None for w in self.workloads for a in w.arrays):
+            self.set("p", np.concatenate([w.concat("p") for w in self.workloads]))
 
     def step_batch(self, schemes: Sequence[Scheme], dts: Sequence[float], nsteps: int = 1):
         arr = (Scheme * self.ninst)(*schemes)

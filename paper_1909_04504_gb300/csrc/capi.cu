@@ -26,7 +26,8 @@ thread_local std::string g_create_error;
 
 constexpr double PI = 3.14159265358979323846;
 constexpr uint32_t STATE_MAGIC = 0x53504853u;  // "SPHS"
-constexpr uint32_t STATE_VERSION = 2;
+constexpr uint32_t STATE_VERSION = 3;
+constexpr int STATE_FIELDS = 16;  // FP64 arrays of a particle set (state_fields)
 
 struct StateHeader {
     uint32_t magic, version;
@@ -38,6 +39,14 @@ struct StateHeader {
 };
 
 }  // namespace
+
+// The FP64 arrays of a particle set in the order of the saved state: x, u, rho, m, the
+// rates (arho, a, xsph) and the EDAC pressure.
+void state_fields(const ParticleSet& S, double** f) {
+    double* t[STATE_FIELDS] = {S.x[0], S.x[1], S.x[2], S.u[0], S.u[1], S.u[2], S.rho, S.m,
+                               S.arho, S.a[0], S.a[1], S.a[2], S.xs[0], S.xs[1], S.xs[2], S.p};
+    for (int k = 0; k < STATE_FIELDS; ++k) f[k] = t[k];
+}
 
 struct sph_ctx {
     int device = 0;
@@ -55,6 +64,7 @@ struct sph_ctx {
     int nwall = 0;                 // wall particles
     bool wall_pass = false;        // the scheme(s) in use take the solid-wall pressure pass
     bool pec = false;              // the scheme in use takes the midpoint integrator
+    bool edac = false;             // the scheme in use is the EDAC form (pressure state)
     int pec_cont = 1;              // ... with the continuity density (else summation)
     double* pec_save = nullptr;    // midpoint integrator: saved (x, u, rho) + the step size
     uint32_t* perm = nullptr;      // sorted values of the last build: previous position
@@ -242,6 +252,12 @@ PairConst<Real> pair_const_dg(const sph_domain& D, const Grid& Gr, const sph_sch
         if (s->alpha != 0.0) f |= F_AV;
         if (s->xsph_eps != 0.0) f |= F_XSPH;
         if (s->wall_bc == SPH_WALL_ADAMI) f |= F_WALLP;
+        if (s->density == SPH_DENSITY_EDAC) {
+            f |= F_EDAC;
+            K.inv_rho0 = (Real)(1.0 / s->rho0);
+            K.edac_d = (Real)(2.0 * (D.h * s->c0 / 16.0) / s->rho0);  // 2 nu_e / rho0
+            K.c02 = (Real)(s->c0 * s->c0);
+        }
         K.flags = f;
     }
     return K;
@@ -275,8 +291,13 @@ StepConst step_const(const sph_ctx* c, const sph_scheme* s, double dt_fixed) {
 
 sph_status check_scheme(sph_ctx* c, const sph_scheme* s) {
     if (!s) return fail(c, SPH_ERR_INVALID, "scheme is NULL");
-    if (s->density != SPH_DENSITY_CONTINUITY && s->density != SPH_DENSITY_SUMMATION)
+    if (s->density != SPH_DENSITY_CONTINUITY && s->density != SPH_DENSITY_SUMMATION &&
+        s->density != SPH_DENSITY_EDAC)
         return fail(c, SPH_ERR_INVALID, "unknown density formulation");
+    if (s->density == SPH_DENSITY_EDAC && c && c->nwall > 0)
+        return fail(c, SPH_ERR_INVALID, "the EDAC form is built for fluid-only problems");
+    if (s->density == SPH_DENSITY_EDAC && s->integrator != SPH_INTEGRATOR_KDK)
+        return fail(c, SPH_ERR_INVALID, "the EDAC form runs with the kick-drift-kick integrator");
     if (!(s->rho0 > 0.0) || !(s->c0 > 0.0) || !(s->gamma > 0.0))
         return fail(c, SPH_ERR_INVALID, "rho0, c0 and gamma must be > 0");
     if (!(s->nu >= 0.0) || !(s->eta >= 0.0) || !(s->alpha >= 0.0) || !std::isfinite(s->xsph_eps))
@@ -396,6 +417,7 @@ StepLaunch step_launch(sph_ctx* c, int kick) {
     L.Q = c->Q;
     L.R = c->R;
     L.E = c->E;
+    L.edac = c->edac ? 1 : 0;
     L.skeys = c->skeys;
     L.off = c->off;
     L.nl = c->nl;
@@ -542,9 +564,10 @@ void enqueue_pec_step(sph_ctx* c) {
 // nsteps steps in the context's mode (tables already uploaded, rates valid).
 sph_status run_steps(sph_ctx* c, int nsteps) {
     if (nsteps <= 0) return SPH_OK;
-    // the persistent kernel has neither the solid-wall pressure phase nor the midpoint
-    // integrator: such steps run as the graph
-    if (c->step_mode == SPH_STEP_PERSISTENT && !c->wall_pass && !c->pec) return run_fused(c, nsteps);
+    // the persistent kernel has neither the solid-wall pressure phase, the midpoint
+    // integrator nor the EDAC pressure gather: such steps run as the graph
+    if (c->step_mode == SPH_STEP_PERSISTENT && !c->wall_pass && !c->pec && !c->edac)
+        return run_fused(c, nsteps);
     if (!c->graph[0] || c->graph_timed != c->timing) {
         sph_status s = capture_step_graphs(c);
         if (s != SPH_OK) return s;
@@ -601,6 +624,11 @@ sph_status upload_table(sph_ctx* c, const sph_scheme* schemes, const double* dts
             return fail(c, SPH_ERR_OOM, "midpoint integrator state of " + std::to_string(bytes) + " bytes");
         }
         c->pec_save = (double*)p;
+    }
+    const bool edac = schemes[0].density == SPH_DENSITY_EDAC;  // shared by a batch
+    if (edac != c->edac) {  // the captured reorder gathers the pressure or not
+        c->edac = edac;
+        drop_graphs(c);
     }
     const int cont = schemes[0].density != SPH_DENSITY_SUMMATION;
     if (pec != c->pec || (pec && cont != c->pec_cont)) {  // captured steps: one integrator
@@ -747,7 +775,7 @@ sph_status prop_field(sph_ctx* c, const char* prop, bool writable, double** fiel
     struct { const char* name; double* f; bool w; } table[] = {
         {"x", S.x[0], true}, {"y", S.x[1], true}, {"z", S.x[2], true},
         {"u", S.u[0], true}, {"v", S.u[1], true}, {"w", S.u[2], true},
-        {"rho", S.rho, true}, {"m", S.m, true},
+        {"rho", S.rho, true}, {"m", S.m, true}, {"p", S.p, true},
         {"arho", S.arho, false}, {"ax", S.a[0], false}, {"ay", S.a[1], false}, {"az", S.a[2], false},
         {"xsx", S.xs[0], false}, {"xsy", S.xs[1], false}, {"xsz", S.xs[2], false}};
     for (auto& t : table)
@@ -934,7 +962,7 @@ sph_status create_impl(const sph_domain* domains, int ninst, const sph_array_des
     const size_t real = domain->precision == SPH_PREC_FP32 ? 4 : 8;
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     size_t bytes = 0;
-    bytes += 2 * (15 * al(N * 8) + al(N * 4));                 // two particle sets
+    bytes += 2 * (STATE_FIELDS * al(N * 8) + al(N * 4));       // two particle sets
     bytes += 2 * al(N * 4 * real) + al(N * real);              // shadow P, Q, R
     if (domain->precision == SPH_PREC_FP32) bytes += al(N * 16);  // position residuals E
     bytes += 4 * al(N * 4);                                    // keys, vals
@@ -972,6 +1000,7 @@ sph_status create_impl(const sph_domain* domains, int ninst, const sph_array_des
         S.arho = (double*)arena_take(p, N * 8);
         for (int d = 0; d < 3; ++d) S.a[d] = (double*)arena_take(p, N * 8);
         for (int d = 0; d < 3; ++d) S.xs[d] = (double*)arena_take(p, N * 8);
+        S.p = (double*)arena_take(p, N * 8);
         S.tag = (uint32_t*)arena_take(p, N * 4);
     }
     c->P = arena_take(p, N * 4 * real);
@@ -1044,7 +1073,7 @@ sph_status create_impl(const sph_domain* domains, int ninst, const sph_array_des
         // zero rates and the unused axes of both sets, the control block and the history
         for (int k = 0; k < 2 && ue == cudaSuccess; ++k) {
             ParticleSet& T = c->set[k];
-            double* zs[7] = {T.arho, T.a[0], T.a[1], T.a[2], T.xs[0], T.xs[1], T.xs[2]};
+            double* zs[8] = {T.arho, T.a[0], T.a[1], T.a[2], T.xs[0], T.xs[1], T.xs[2], T.p};
             for (double* z : zs)
                 if (ue == cudaSuccess) ue = cudaMemsetAsync(z, 0, N * 8, c->stream);
             if (k == 1) {
@@ -1458,14 +1487,14 @@ struct DevSnap {
 
 size_t snap_bytes(const sph_ctx* c) {
     const size_t N = (size_t)c->N;
-    return 15 * N * 8 + N * 4 + sizeof(Control) + (size_t)c->ninst * (2 + DIAG_N) * 8;
+    return STATE_FIELDS * N * 8 + N * 4 + sizeof(Control) + (size_t)c->ninst * (2 + DIAG_N) * 8;
 }
 
 cudaError_t snap_copy(sph_ctx* c, const DevSnap& sn, bool restore) {
     const size_t N = (size_t)c->N;
     const ParticleSet& S = c->set[c->cur];
-    double* f[15] = {S.x[0], S.x[1], S.x[2], S.u[0], S.u[1], S.u[2], S.rho, S.m,
-                     S.arho, S.a[0], S.a[1], S.a[2], S.xs[0], S.xs[1], S.xs[2]};
+    double* f[STATE_FIELDS];
+    state_fields(S, f);
     char* p = sn.buf;
     cudaError_t e = cudaSuccess;
     auto cp = [&](void* dev, size_t b) {
@@ -1474,7 +1503,7 @@ cudaError_t snap_copy(sph_ctx* c, const DevSnap& sn, bool restore) {
                         : cudaMemcpyAsync(p, dev, b, cudaMemcpyDeviceToDevice, c->stream);
         p += b;
     };
-    for (int k = 0; k < 15; ++k) cp(f[k], N * 8);
+    for (int k = 0; k < STATE_FIELDS; ++k) cp(f[k], N * 8);
     cp(S.tag, N * 4);
     cp(c->ctl, sizeof(Control));
     if (c->ninst) {
@@ -2008,7 +2037,7 @@ sph_status sph_history(sph_ctx* c, double* out, int32_t max_records, int32_t* co
 sph_status sph_save_state(sph_ctx* c, void* buf, size_t* bytes) {
     if (!c || !bytes) return fail(c, SPH_ERR_INVALID, "NULL argument");
     const size_t N = (size_t)c->N;
-    const size_t need = sizeof(StateHeader) + 15 * N * 8 + N * 4;
+    const size_t need = sizeof(StateHeader) + STATE_FIELDS * N * 8 + N * 4;
     if (!buf) {
         *bytes = need;
         return SPH_OK;
@@ -2028,12 +2057,12 @@ sph_status sph_save_state(sph_ctx* c, void* buf, size_t* bytes) {
     Control ctl{};
     CK(cudaMemcpyAsync(&ctl, c->ctl, sizeof ctl, cudaMemcpyDeviceToHost, c->stream));
     const ParticleSet& S = c->set[c->cur];
-    const double* fields[15] = {S.x[0], S.x[1], S.x[2], S.u[0], S.u[1], S.u[2], S.rho, S.m,
-                                S.arho, S.a[0], S.a[1], S.a[2], S.xs[0], S.xs[1], S.xs[2]};
+    double* fields[STATE_FIELDS];
+    state_fields(S, fields);
     char* p = (char*)buf + sizeof(StateHeader);
-    for (int k = 0; k < 15; ++k)
+    for (int k = 0; k < STATE_FIELDS; ++k)
         CK(cudaMemcpyAsync(p + (size_t)k * N * 8, fields[k], N * 8, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(p + 15 * N * 8, S.tag, N * 4, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(p + STATE_FIELDS * N * 8, S.tag, N * 4, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     H.t = ctl.t;
     H.dt = ctl.dt;
@@ -2046,7 +2075,7 @@ sph_status sph_save_state(sph_ctx* c, void* buf, size_t* bytes) {
 sph_status sph_load_state(sph_ctx* c, const void* buf, size_t bytes) {
     if (!c || !buf) return fail(c, SPH_ERR_INVALID, "NULL argument");
     const size_t N = (size_t)c->N;
-    const size_t need = sizeof(StateHeader) + 15 * N * 8 + N * 4;
+    const size_t need = sizeof(StateHeader) + STATE_FIELDS * N * 8 + N * 4;
     StateHeader H;
     if (bytes < sizeof H) return fail(c, SPH_ERR_INVALID, "state buffer too small");
     std::memcpy(&H, buf, sizeof H);
@@ -2054,12 +2083,12 @@ sph_status sph_load_state(sph_ctx* c, const void* buf, size_t bytes) {
         bytes < need)
         return fail(c, SPH_ERR_INVALID, "state buffer does not match this context");
     const ParticleSet& S = c->set[c->cur];
-    double* fields[15] = {S.x[0], S.x[1], S.x[2], S.u[0], S.u[1], S.u[2], S.rho, S.m,
-                          S.arho, S.a[0], S.a[1], S.a[2], S.xs[0], S.xs[1], S.xs[2]};
+    double* fields[STATE_FIELDS];
+    state_fields(S, fields);
     const char* p = (const char*)buf + sizeof(StateHeader);
-    for (int k = 0; k < 15; ++k)
+    for (int k = 0; k < STATE_FIELDS; ++k)
         CK(cudaMemcpyAsync(fields[k], p + (size_t)k * N * 8, N * 8, cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(S.tag, p + 15 * N * 8, N * 4, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(S.tag, p + STATE_FIELDS * N * 8, N * 4, cudaMemcpyHostToDevice, c->stream));
     c->work_dirty = true;
     Control ctl{};
     ctl.t = H.t;

@@ -132,7 +132,7 @@ __global__ void k_reorder(ParticleSet in, ParticleSet out, const uint32_t* __res
                           const Inst<Real>* __restrict__ tab, const uint32_t* __restrict__ cell_bounds,
                           int ninst, const double* __restrict__ idt, int kick, int carry_rates,
                           typename V4<Real>::T* __restrict__ P, typename V4<Real>::T* __restrict__ Q,
-                          F4* __restrict__ E, uint32_t* __restrict__ off, int ncells,
+                          F4* __restrict__ E, int edac, uint32_t* __restrict__ off, int ncells,
                           uint32_t* __restrict__ work, int work_words, const Control* ctl) {
     if (ctl->status) return;
     // cell table: four consecutive cells per thread, their previous offsets read and the
@@ -147,7 +147,8 @@ __global__ void k_reorder(ParticleSet in, ParticleSet out, const uint32_t* __res
         if (k < work_words) work[k] = 0u;
         if (k < n) {
             const int inst = find_instance(cell_bounds, ninst, skeys[k]);
-            reorder_one<Real>(in, out, k, (int)perm[k], dim, idt[inst], kick, carry_rates, P, Q, E);
+            reorder_one<Real>(in, out, k, (int)perm[k], dim, idt[inst], kick, carry_rates, P, Q, E,
+                              edac);
         }
         if (k < nq) {
             const uint32_t c0 = 4u * (uint32_t)k;
@@ -320,13 +321,13 @@ void launch_reorder(const StepLaunch& L, const uint32_t* perm, int carry_rates, 
     if (L.precision)
         k_reorder<float><<<g, 256, 0, st>>>(L.Sin, L.S, perm, L.skeys, L.n, L.dim,
                                             (const Inst<float>*)L.tab, L.cell_bounds, L.ninst, L.idt,
-                                            L.kick, carry_rates, (F4*)L.P, (F4*)L.Q, (F4*)L.E, off,
-                                            ncells, work, work_words, L.ctl);
+                                            L.kick, carry_rates, (F4*)L.P, (F4*)L.Q, (F4*)L.E, L.edac,
+                                            off, ncells, work, work_words, L.ctl);
     else
         k_reorder<double><<<g, 256, 0, st>>>(L.Sin, L.S, perm, L.skeys, L.n, L.dim,
                                              (const Inst<double>*)L.tab, L.cell_bounds, L.ninst,
                                              L.idt, L.kick, carry_rates, (D4*)L.P, (D4*)L.Q, nullptr,
-                                             off, ncells, work, work_words, L.ctl);
+                                             L.edac, off, ncells, work, work_words, L.ctl);
 }
 
 size_t sort_work_words(int n, int passes) {

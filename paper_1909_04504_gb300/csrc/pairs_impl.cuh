@@ -1,7 +1,9 @@
 // Pair loops of one right-hand-side evaluation over the cell-sorted particles
 // (Sec. 3.2 groups; per-destination loop of Sec. 3.4), as kernel templates:
 //  - the density pass: summation density, Eq. (2), or the continuity rate,
-//    Eq. (continuity:sph), with the position-like density advance, then the EOS;
+//    Eq. (continuity:sph), with the position-like density advance, then the EOS; or the
+//    pressure rate of the EDAC form (Sec. 2.3 scheme list, the Taylor-Green runs of
+//    Sec. 4.1) with the same advance of the pressure;
 //  - the momentum pass: pressure Eq. (mom:sph:press), laminar viscosity
 //    Eq. (mom:sph:visc), Monaghan artificial viscosity, XSPH and the body force of
 //    Eq. (mom:sph), with the corrector half-kick of Sec. 2.1 and the FP64 diagnostics.
@@ -335,7 +337,8 @@ __device__ __forceinline__ void density_scan_sum(int i, const Group<T>& g, uint3
                                                  uint32_t* __restrict__ cnt, int maxn,
                                                  DensityCounts& dc, uint32_t* pcount_i,
                                                  Acc<Real>& sum) {
-    const bool summation = !(K.flags & F_CONTINUITY);
+    const bool edac = (K.flags & F_EDAC) != 0;
+    const bool summation = !(K.flags & (F_CONTINUITY | F_EDAC));
     const typename V4<Real>::T pi = P[i];
     const bool fluid_i = pi.w > Real(0);
     int cx, cy, cz;
@@ -438,7 +441,11 @@ __device__ __forceinline__ void density_scan_sum(int i, const Group<T>& g, uint3
             const Real Gk = K.gfac * kernel_f<Real, KERNEL>(q);
             const Real vdotr = (qi.x - qj.x) * dx + (qi.y - qj.y) * dy +
                                (DIM == 3 ? (qi.z - qj.z) * dz : Real(0));
-            sum.add(fabs(pj.w) * Gk * vdotr);
+            if (edac)  // Q.w holds the pressure p^n: c0^2 u_ij . grad W + (2 nu_e / rho0) p_ij r . grad W / (r^2 + 0.01 h^2)
+                sum.add(fabs(pj.w) * Gk *
+                        (K.c02 * vdotr + K.edac_d * (qi.w - qj.w) * r2 * PairMath<Real>::rcp(r2 + K.av_h2)));
+            else
+                sum.add(fabs(pj.w) * Gk * vdotr);
         }
     }
     if (T > 1) group_reduce<Real, T>(sum, g);
@@ -461,6 +468,16 @@ __device__ __forceinline__ void density_finish(int i, double value, Real mi,
                                                Real* __restrict__ R, const PairConst<Real>& K,
                                                const StepConst& C, const ParticleSet& S,
                                                double dt, int kick) {
+    if (K.flags & F_EDAC) {
+        // the EDAC pressure advanced like the continuity density; the density stays rho0,
+        // and Q.w keeps p^n, which the other destinations of this pass read
+        double p = S.p[i];
+        if (kick) p += dt * value;
+        S.p[i] = p;
+        S.arho[i] = value;
+        R[i] = (Real)(p * C.inv_rho0 * C.inv_rho0);
+        return;
+    }
     double rho, arho;
     if (!(K.flags & F_CONTINUITY)) {
         rho = value + (double)(fabs(mi) * K.wfac * kernel_w<Real, KERNEL>(Real(0)));
@@ -602,7 +619,8 @@ __device__ __forceinline__ void momentum_sums(int i, const Group<T>& g,
         const Real Gk = K.gfac * kernel_f<Real, KERNEL>(q);  // grad_i W = Gk (x_i - x_j)
         const Real vx = qi.x - qj.x, vy = qi.y - qj.y, vz = DIM == 3 ? qi.z - qj.z : Real(0);
         Real coef = pri + R[j];
-        const Real inv_rhobar = PairMath<Real>::rcp(Real(0.5) * (qi.w + qj.w));
+        // EDAC: the density is rho0 (Q.w holds the pressure)
+        const Real inv_rhobar = (flags & F_EDAC) ? K.inv_rho0 : PairMath<Real>::rcp(Real(0.5) * (qi.w + qj.w));
         if (flags & F_AV) {
             const Real vdotr = vx * dx + vy * dy + (DIM == 3 ? vz * dz : Real(0));
             if (vdotr < Real(0)) {

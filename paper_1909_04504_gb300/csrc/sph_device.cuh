@@ -25,6 +25,7 @@ constexpr int F_LAMINAR = 2;      // Eq. mom:sph:visc
 constexpr int F_AV = 4;           // Monaghan artificial viscosity
 constexpr int F_XSPH = 8;         // XSPH correction
 constexpr int F_WALLP = 16;       // solid-wall pressure of Adami et al. (Sec. 2.3 wall condition)
+constexpr int F_EDAC = 32;        // EDAC pressure equation (Sec. 2.3 scheme list, Sec. 4.1)
 
 constexpr int DIAG_N = 13;
 constexpr int HIST_CAP = 65536;
@@ -46,6 +47,7 @@ struct ParticleSet {
     double* arho;   // rates of the last evaluation
     double* a[3];
     double* xs[3];  // XSPH velocity correction
+    double* p;      // EDAC: the pressure (a state variable there; else unused)
     uint32_t* tag;  // global id | WALL_BIT
 };
 
@@ -92,6 +94,9 @@ struct PairConst {
     Real alpha_c0;  // alpha c0
     Real c0;
     Real xsph;
+    Real inv_rho0;  // EDAC: 1 / rho0 (the density is held at rho0)
+    Real edac_d;    // EDAC: 2 nu_e / rho0, nu_e = h c0 / 16
+    Real c02;       // EDAC: c0^2
     int flags;
 };
 

@@ -61,6 +61,7 @@ struct StepLaunch {
     void* Q;
     void* R;
     void* E;                      // FP32 pair loops: position residuals (reorder_one)
+    int edac;                     // the EDAC form: the reorder gathers the pressure state
     const uint32_t* skeys;
     const uint32_t* off;
     uint32_t* nl;                 // neighbour list, nl[k * n + i], k < maxn

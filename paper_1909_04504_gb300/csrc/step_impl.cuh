@@ -73,6 +73,8 @@ __device__ __forceinline__ uint32_t drift_key_one(const ParticleSet& S, int i, c
 // positions, by the density pass). Rates are carried along only outside a step
 // (carry_rates). Writes the pair-loop shadow P = (x, y, z, +-m) with the sign marking
 // walls and Q = (u, v, w, .); the density pass that follows writes Q.w = rho and p / rho^2.
+// edac: the pressure p (a state variable of the EDAC form) is gathered too and its value
+// at the start of the evaluation goes to Q.w, which the density pass then only reads.
 // E (FP32 pair loops, may be null): the residuals x - (float)x, y - (float)y, z - (float)z
 // of the rounded positions (each exact in FP64, then rounded), so that the pair sums form
 // separations as (x_i - x_j) + (e_i - e_j) to nearly FP32 precision of the separation
@@ -82,7 +84,7 @@ __device__ __forceinline__ void reorder_one(const ParticleSet& in, const Particl
                                             int o, int dim, double dt, int kick, int carry_rates,
                                             typename V4<Real>::T* __restrict__ P,
                                             typename V4<Real>::T* __restrict__ Q,
-                                            F4* __restrict__ E = nullptr) {
+                                            F4* __restrict__ E = nullptr, int edac = 0) {
     // every load of particle o before any store (the output arrays could alias the inputs
     // as far as the compiler knows); the acceleration is read for walls too (it is zero
     // there) so that no load waits for the tag
@@ -98,6 +100,7 @@ __device__ __forceinline__ void reorder_one(const ParticleSet& in, const Particl
         }
     const double rho = in.rho[o];
     const double m = in.m[o];
+    const double pe = edac ? in.p[o] : 0.0;
     const double arho = carry_rates ? in.arho[o] : 0.0;
     const bool fluid = !(tag & WALL_BIT);
     double uk[3] = {u[0], u[1], u[2]};
@@ -113,6 +116,7 @@ __device__ __forceinline__ void reorder_one(const ParticleSet& in, const Particl
         }
     out.rho[k] = rho;
     out.m[k] = m;
+    if (edac) out.p[k] = pe;
     out.tag[k] = tag;
     if (carry_rates) {
         out.arho[k] = arho;
@@ -127,7 +131,7 @@ __device__ __forceinline__ void reorder_one(const ParticleSet& in, const Particl
     pv.x = (Real)x[0]; pv.y = (Real)x[1]; pv.z = (Real)x[2];
     pv.w = (Real)(fluid ? m : -m);
     qv.x = (Real)uk[0]; qv.y = (Real)uk[1]; qv.z = (Real)uk[2];
-    qv.w = Real(0);  // the density pass writes it
+    qv.w = edac ? (Real)pe : Real(0);  // the density pass writes rho; EDAC: the pressure p^n
     P[k] = pv;
     Q[k] = qv;
     if (E) {
