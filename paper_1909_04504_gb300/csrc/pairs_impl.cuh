@@ -176,6 +176,40 @@ __device__ __forceinline__ F4 residual_of(const F4* __restrict__ E, int i) {
     return E ? E[i] : F4{0.f, 0.f, 0.f, 0.f};
 }
 
+// Separation for the pair sums over a neighbour list: with MI the minimum image on the
+// periodic axes (separation above), else the plain difference, which equals it wherever
+// no neighbour lies across a periodic boundary.
+template <class Real, int DIM, bool MI>
+__device__ __forceinline__ void pair_separation(const typename V4<Real>::T& pi,
+                                                const typename V4<Real>::T& pj, const Grid& G,
+                                                const PairConst<Real>& K, Real& dx, Real& dy,
+                                                Real& dz) {
+    if (MI) {
+        separation<Real, DIM>(pi, pj, G, K, dx, dy, dz);
+    } else {
+        dx = rn_sub(pi.x, pj.x);
+        dy = rn_sub(pi.y, pj.y);
+        dz = DIM == 3 ? rn_sub(pi.z, pj.z) : Real(0);
+    }
+}
+
+// Whether a neighbour of destination pi, or of another destination of the warp, can lie
+// across a periodic boundary: within the support (with a margin far above the rounding of
+// the test) of the box faces of some periodic axis. Elsewhere every neighbour's raw
+// difference is shorter than the support, so below half the period, and the minimum image
+// leaves it unchanged. Decided for the whole warp, so that its lanes take one loop.
+template <class Real, int DIM>
+__device__ __forceinline__ bool near_periodic_face(const typename V4<Real>::T& pi, const Grid& G,
+                                                   const PairConst<Real>& K) {
+    const double reach = 1.01 * sqrt((double)K.kh2);
+    const double xs[3] = {(double)pi.x, (double)pi.y, (double)pi.z};
+    bool near = false;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d)
+        near |= G.periodic[d] && (xs[d] - G.lo[d] < reach || G.hi[d] - xs[d] < reach);
+    return __any_sync(__activemask(), near) != 0;
+}
+
 // ------------------------------------------------------------ diagnostics
 // Block partials of one evaluation, 8-byte slots: momentum pass [px, py, pz, ke] (FP64
 // sums), [max |u|^2, max |a|^2] (bit patterns of non-negative doubles, whose integer
@@ -325,6 +359,60 @@ __device__ __forceinline__ uint32_t group_sum_u32(uint32_t v, const Group<T>& g)
     return v;
 }
 
+// Step (2) for destination i over its k list entries (lane t of the group takes every
+// T-th entry); the compensated sum is valid in lane t after the loop, before the group
+// reduction.
+template <class Real, int DIM, int KERNEL, int T>
+__device__ __forceinline__ void density_list_sum(int i, const Group<T>& g,
+                                                 const typename V4<Real>::T& pi,
+                                                 const typename V4<Real>::T* __restrict__ P,
+                                                 const typename V4<Real>::T* __restrict__ Q,
+                                                 const F4* __restrict__ E, int n, const Grid& G,
+                                                 const PairConst<Real>& K,
+                                                 const uint32_t* __restrict__ nl, uint32_t k,
+                                                 Acc<Real>& sum) {
+    using yes = std::true_type;
+    using no = std::false_type;
+    const bool edac = (K.flags & F_EDAC) != 0;
+    const bool summation = !(K.flags & (F_CONTINUITY | F_EDAC));
+    sum.zero();
+    const typename V4<Real>::T qi = Q[i];
+    const F4 ei = residual_of(E, i);
+    // the next list entry is fetched one iteration ahead, so its load overlaps this
+    // iteration's source loads and arithmetic
+    // the loop without the minimum image unless a neighbour can lie across a periodic
+    // boundary (the same values: the image is the identity there)
+    auto sum_loop = [&](auto mi_tag) {
+    constexpr bool MI = decltype(mi_tag)::value;
+    uint32_t j_next = g.t < k ? nl[(size_t)g.t * n + i] : 0u;
+    for (uint32_t kk = g.t; kk < k; kk += T) {
+        const uint32_t j = j_next;
+        if (kk + T < k) j_next = nl[(size_t)(kk + T) * n + i];
+        const typename V4<Real>::T pj = P[j];
+        Real dx, dy, dz;
+        pair_separation<Real, DIM, MI>(pi, pj, G, K, dx, dy, dz);
+        add_residuals<Real, DIM>(E, ei, j, dx, dy, dz);
+        const Real r2 = dist2<Real, DIM>(dx, dy, dz);
+        const Real q = PairMath<Real>::sqrt(r2) * K.inv_h;
+        if (summation) {
+            sum.add(fabs(pj.w) * K.wfac * kernel_w<Real, KERNEL>(q));
+        } else {
+            const typename V4<Real>::T qj = Q[j];
+            const Real Gk = K.gfac * kernel_f<Real, KERNEL>(q);
+            const Real vdotr = (qi.x - qj.x) * dx + (qi.y - qj.y) * dy +
+                               (DIM == 3 ? (qi.z - qj.z) * dz : Real(0));
+            if (edac)  // Q.w holds the pressure p^n: c0^2 u_ij . grad W + (2 nu_e / rho0) p_ij r . grad W / (r^2 + 0.01 h^2)
+                sum.add(fabs(pj.w) * Gk *
+                        (K.c02 * vdotr + K.edac_d * (qi.w - qj.w) * r2 * PairMath<Real>::rcp(r2 + K.av_h2)));
+            else
+                sum.add(fabs(pj.w) * Gk * vdotr);
+        }
+    }
+    };
+    if (near_periodic_face<Real, DIM>(pi, G, K)) sum_loop(yes());
+    else sum_loop(no());
+}
+
 // Steps (1) and (2) for destination i; the compensated sum is valid in lane 0.
 template <class Real, int DIM, int KERNEL, int T>
 __device__ __forceinline__ void density_scan_sum(int i, const Group<T>& g, uint32_t key,
@@ -419,35 +507,7 @@ __device__ __forceinline__ void density_scan_sum(int i, const Group<T>& g, uint3
     }
     if (g.t == 0) cnt[i] = k;
     g.sync();  // the list entries of the other lanes are visible from here on
-    sum.zero();
-    const typename V4<Real>::T qi = Q[i];
-    const F4 ei = residual_of(E, i);
-    // the next list entry is fetched one iteration ahead, so its load overlaps this
-    // iteration's source loads and arithmetic
-    uint32_t j_next = g.t < k ? nl[(size_t)g.t * n + i] : 0u;
-    for (uint32_t kk = g.t; kk < k; kk += T) {
-        const uint32_t j = j_next;
-        if (kk + T < k) j_next = nl[(size_t)(kk + T) * n + i];
-        const typename V4<Real>::T pj = P[j];
-        Real dx, dy, dz;
-        separation<Real, DIM>(pi, pj, G, K, dx, dy, dz);
-        add_residuals<Real, DIM>(E, ei, j, dx, dy, dz);
-        const Real r2 = dist2<Real, DIM>(dx, dy, dz);
-        const Real q = PairMath<Real>::sqrt(r2) * K.inv_h;
-        if (summation) {
-            sum.add(fabs(pj.w) * K.wfac * kernel_w<Real, KERNEL>(q));
-        } else {
-            const typename V4<Real>::T qj = Q[j];
-            const Real Gk = K.gfac * kernel_f<Real, KERNEL>(q);
-            const Real vdotr = (qi.x - qj.x) * dx + (qi.y - qj.y) * dy +
-                               (DIM == 3 ? (qi.z - qj.z) * dz : Real(0));
-            if (edac)  // Q.w holds the pressure p^n: c0^2 u_ij . grad W + (2 nu_e / rho0) p_ij r . grad W / (r^2 + 0.01 h^2)
-                sum.add(fabs(pj.w) * Gk *
-                        (K.c02 * vdotr + K.edac_d * (qi.w - qj.w) * r2 * PairMath<Real>::rcp(r2 + K.av_h2)));
-            else
-                sum.add(fabs(pj.w) * Gk * vdotr);
-        }
-    }
+    density_list_sum<Real, DIM, KERNEL, T>(i, g, pi, P, Q, E, n, G, K, nl, k, sum);
     if (T > 1) group_reduce<Real, T>(sum, g);
     dc.pairs += npairs;
     dc.cand += ncand;
@@ -604,13 +664,16 @@ __device__ __forceinline__ void momentum_sums(int i, const Group<T>& g,
 #pragma unroll
     for (int k = 0; k < 6; ++k) acc[k].zero();
     const uint32_t ni = cnt[i];
+    // without the minimum image unless a neighbour can lie across a periodic boundary
+    auto pair_loop = [&](auto mi_tag) {
+    constexpr bool MI = decltype(mi_tag)::value;
     uint32_t j_next = g.t < ni ? nl[(size_t)g.t * n + i] : 0u;  // fetched one entry ahead
     for (uint32_t kk = g.t; kk < ni; kk += T) {
         const uint32_t j = j_next;
         if (kk + T < ni) j_next = nl[(size_t)(kk + T) * n + i];
         const typename V4<Real>::T pj = P[j];
         Real dx, dy, dz;
-        separation<Real, DIM>(pi, pj, G, K, dx, dy, dz);
+        pair_separation<Real, DIM, MI>(pi, pj, G, K, dx, dy, dz);
         add_residuals<Real, DIM>(E, ei, j, dx, dy, dz);
         const Real r2 = dist2<Real, DIM>(dx, dy, dz);
         const typename V4<Real>::T qj = Q[j];
@@ -643,6 +706,9 @@ __device__ __forceinline__ void momentum_sums(int i, const Group<T>& g,
             if (DIM == 3) acc[5].add(-fx * vz);
         }
     }
+    };
+    if (near_periodic_face<Real, DIM>(pi, G, K)) pair_loop(std::true_type());
+    else pair_loop(std::false_type());
     if (T > 1) {
         group_reduce<Real, T>(acc[0], g);
         group_reduce<Real, T>(acc[1], g);
