@@ -136,6 +136,11 @@ struct sph_ctx {
     // captured step graphs, one per parity of `cur`
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     bool graph_timed = false;
+    // persistent step form: the one cooperative launch of a step captured per parity of
+    // `cur` (null: not captured yet; fused_direct: the runtime refused the capture, the
+    // launches go straight to the stream)
+    cudaGraphExec_t fgraph[2] = {nullptr, nullptr};
+    bool fused_direct = false;
     std::vector<unsigned char> tab_host;  // copy of the device instance table
 };
 
@@ -508,7 +513,44 @@ FusedLaunch fused_launch(sph_ctx* c) {
     return F;
 }
 
-// nsteps persistent launches (one per step) on the context stream.
+// Captures the persistent step (its one cooperative launch) once per parity of the set in
+// use. The kernel leaves the barrier words, the sort workspace and the clamp counter as it
+// found them, so a graph holds the launch alone; the limits of its waits and its grid are
+// baked in (set_groups and sph_set_wait_limit drop the graphs). Returns false, with no
+// graph kept, where the runtime does not capture a cooperative launch.
+bool capture_fused_graphs(sph_ctx* c, int grid) {
+    const int cur0 = c->cur;
+    bool ok = true;
+    for (int k = 0; k < 2 && ok; ++k) {
+        c->cur = cur0 ^ k;
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            ok = false;
+            break;
+        }
+        const FusedLaunch F = fused_launch(c);
+        const cudaError_t le = launch_fused(F, c->group_m, grid, c->stream);
+        const cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
+        cudaGraphExec_t ex = nullptr;
+        if (le != cudaSuccess || ee != cudaSuccess || !g || cudaGraphInstantiate(&ex, g, 0) != cudaSuccess)
+            ok = false;
+        if (g) cudaGraphDestroy(g);
+        if (ok) c->fgraph[cur0 ^ k] = ex;
+    }
+    c->cur = cur0;
+    if (!ok) {
+        cudaGetLastError();
+        for (int k = 0; k < 2; ++k)
+            if (c->fgraph[k]) {
+                cudaGraphExecDestroy(c->fgraph[k]);
+                c->fgraph[k] = nullptr;
+            }
+    }
+    return ok;
+}
+
+// nsteps persistent steps (one cooperative launch each, replayed from the captured step
+// graph of the current parity) on the context stream.
 sph_status run_fused(sph_ctx* c, int nsteps) {
     if (c->fused_bps[tindex(c->group_m)] < 1)
         return fail(c, SPH_ERR_INVALID, "the persistent step kernel cannot be resident on this device");
@@ -517,10 +559,15 @@ sph_status run_fused(sph_ctx* c, int nsteps) {
     CK(cudaMemsetAsync(&c->ctl->bar_gen, 0, sizeof(unsigned), c->stream));
     CK(cudaMemsetAsync(c->sort_work, 0, sort_work_words(c->N, c->passes) * 4, c->stream));
     const int grid = fused_grid(c);
+    if (!c->fgraph[0] && !c->fused_direct) c->fused_direct = !capture_fused_graphs(c, grid);
     for (int k = 0; k < nsteps; ++k) {
-        const FusedLaunch F = fused_launch(c);
-        const cudaError_t e = launch_fused(F, c->group_m, grid, c->stream);
-        if (e != cudaSuccess) return cuda_fail(c, e, "persistent step launch");
+        if (c->fgraph[c->cur]) {
+            CK(cudaGraphLaunch(c->fgraph[c->cur], c->stream));
+        } else {
+            const FusedLaunch F = fused_launch(c);
+            const cudaError_t e = launch_fused(F, c->group_m, grid, c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "persistent step launch");
+        }
         c->cur ^= 1;
     }
     c->skeys = c->keys[c->passes & 1];
@@ -666,11 +713,16 @@ sph_status sync_status(sph_ctx* c) {
 }
 
 void drop_graphs(sph_ctx* c) {
-    for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < 2; ++k) {
         if (c->graph[k]) {
             cudaGraphExecDestroy(c->graph[k]);
             c->graph[k] = nullptr;
         }
+        if (c->fgraph[k]) {
+            cudaGraphExecDestroy(c->fgraph[k]);
+            c->fgraph[k] = nullptr;
+        }
+    }
 }
 
 void free_dev(sph_ctx* c, void* p) {
@@ -1460,8 +1512,9 @@ sph_status sph_kernels_per_step(const sph_ctx* ctx, const sph_scheme* scheme, in
     const bool wp = scheme->wall_bc == SPH_WALL_ADAMI && c->nwall > 0;
     const bool pec = scheme->integrator == SPH_INTEGRATOR_PEC;
     const int build_eval = 1 + c->passes + 1 + 1 + (wp ? 1 : 0) + 1 + (c->ninst ? 2 : 0);
+    const bool edac = scheme->density == SPH_DENSITY_EDAC;  // the persistent form runs it as the graph
     if (pec) *count = 2 * build_eval + 3;  // + predictor, corrector, record
-    else *count = c->step_mode == SPH_STEP_PERSISTENT && !wp ? 1 : build_eval;
+    else *count = c->step_mode == SPH_STEP_PERSISTENT && !wp && !edac ? 1 : build_eval;
     return SPH_OK;
 }
 
@@ -1649,6 +1702,7 @@ sph_status sph_get_tuning(const sph_ctx* c, int32_t* momentum_lanes, int32_t* mo
 sph_status sph_set_wait_limit(sph_ctx* c, uint64_t ns) {
     if (!c) return fail(c, SPH_ERR_INVALID, "ctx is NULL");
     c->wait_ns = ns;
+    drop_graphs(c);  // the captured steps hold the limit
     return SPH_OK;
 }
 
