@@ -105,8 +105,8 @@ typedef struct {
  *             rho0 (volumes m / rho0) and gamma is unused; the pressure is advanced like
  *             the continuity density in the step and read by the momentum equation.
  *             Fluid-only problems with the kick-drift-kick integrator (wall particles,
- *             SPH_INTEGRATOR_PEC and sph_backward are refused; the persistent step form
- *             runs it as the graph). The rate is read as "arho", the pressure as "p".
+ *             SPH_INTEGRATOR_PEC and sph_backward are refused). The rate is read as
+ *             "arho", the pressure as "p".
  *  rho0, c0, gamma   Tait EOS, Eq. eos: p = c0^2 rho0 / gamma ((rho/rho0)^gamma - 1).
  *  nu, eta    laminar viscosity, Eq. mom:sph:visc (term off when nu == 0).
  *  alpha      Monaghan artificial viscosity: Pi_ij = -alpha c0 mu_ij / rhobar_ij when
@@ -257,10 +257,11 @@ sph_status sph_set_groups(sph_ctx* ctx, int32_t momentum_lanes);
 
 /* How a step runs. SPH_STEP_GRAPH (default): the phases (drift + keys, radix sort passes,
  * reorder, cell table, density pass, momentum pass, reductions) as separate kernels in a
- * captured CUDA graph. SPH_STEP_PERSISTENT: the whole step as ONE cooperative launch whose
- * blocks stay resident and meet at grid-wide barriers between the phases (no launch gaps;
- * pays off on small problems and batches of them). Both run the same per-particle code;
- * the diagnostics are summed in another order. Steps with the solid-wall pressure or the
+ * captured CUDA graph. SPH_STEP_PERSISTENT: the whole step (with the solid-wall pressure
+ * phase where the scheme asks for it) as ONE cooperative launch whose blocks stay resident
+ * and meet at grid-wide barriers between the phases, captured in a CUDA graph per parity
+ * of the state buffers (no launch gaps). Both run the same per-particle code, so the
+ * states are equal bitwise; the diagnostics are summed in another order. Steps of the
  * midpoint integrator run as the graph in either mode. SPH_ERR_INVALID if the mode is
  * unknown or the device cannot launch cooperatively. */
 enum { SPH_STEP_GRAPH = 0, SPH_STEP_PERSISTENT = 1 };

@@ -20,15 +20,8 @@ k_batch_partials(ParticleSet S, const uint32_t* __restrict__ pcount, const uint3
                  const Control* ctl) {
     __shared__ double red[8][10];
     if (ctl->status) return;
-    const int inst = blockIdx.y, chunk_id = blockIdx.x;
-    const uint32_t b0 = off[tab[inst].cell_base], e0 = off[tab[inst].cell_base_end];
-    const uint32_t chunk = (e0 - b0 + BATCH_SPLIT - 1) / BATCH_SPLIT;
-    const uint32_t b = b0 + chunk_id * chunk;
-    const uint32_t e = b + chunk < e0 ? b + chunk : e0;
-    double o[10];
-    batch_partial<256>(S, pcount, b < e0 ? b : e0, b < e0 ? e : e0, dim, o, red);
-    if (threadIdx.x == 0)
-        for (int q = 0; q < 10; ++q) part[((size_t)inst * BATCH_SPLIT + chunk_id) * 10 + q] = o[q];
+    batch_chunk_partials<Real, 256>(S, pcount, off, tab[blockIdx.y], blockIdx.y, blockIdx.x, dim, part,
+                                    red);
 }
 
 template <class Real>
@@ -37,17 +30,9 @@ k_batch_finish(const Inst<Real>* __restrict__ tab, int ninst, const double* __re
                double* __restrict__ idt, double* __restrict__ it, double* __restrict__ irec, int kick,
                Control* ctl) {
     if (ctl->status) return;
-    const int inst = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    const int inst = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (inst >= ninst) return;
-    double v[10];
-    for (int q = 0; q < 10; ++q)
-        v[q] = lane < BATCH_SPLIT ? part[((size_t)inst * BATCH_SPLIT + lane) * 10 + q] : 0.0;
-    for (int o2 = 16; o2 > 0; o2 >>= 1)
-        for (int q = 0; q < 10; ++q) {
-            const double y = __shfl_down_sync(0xffffffffu, v[q], o2);
-            v[q] = (q >= 4 && q <= 6) ? fmax(v[q], y) : v[q] + y;
-        }
-    if (lane == 0) batch_finish_inst<Real>(tab[inst], inst, v, idt, it, irec, kick, ctl);
+    batch_finish_warp<Real>(tab[inst], inst, part, idt, it, irec, kick, ctl);
 }
 
 // ---------------------------------------------------------------- launchers

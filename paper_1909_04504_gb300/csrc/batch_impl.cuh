@@ -134,19 +134,43 @@ __device__ __forceinline__ void batch_finish_inst(const Inst<Real>& I, int inst,
     idt[inst] = next_dt(I.C, rec[3], rec[7]);
 }
 
-// Batch instance `inst` in one block (the persistent step): its whole segment.
+// First stage of the two-stage reduction (one block of NT threads): chunk `chunk_id` of
+// BATCH_SPLIT consecutive chunks of instance `inst`'s cell-order segment, its partials to
+// part[(inst * BATCH_SPLIT + chunk_id) * 10 ...].
 template <class Real, int NT>
-__device__ __forceinline__ void batch_reduce_inst(const ParticleSet& S,
-                                                  const uint32_t* __restrict__ pcount,
-                                                  const uint32_t* __restrict__ off,
-                                                  const Inst<Real>& I, int inst, int dim,
-                                                  double* __restrict__ idt, double* __restrict__ it,
-                                                  double* __restrict__ irec, int kick, Control* ctl,
-                                                  double (*red)[10]) {
+__device__ __forceinline__ void batch_chunk_partials(const ParticleSet& S,
+                                                     const uint32_t* __restrict__ pcount,
+                                                     const uint32_t* __restrict__ off,
+                                                     const Inst<Real>& I, int inst, int chunk_id,
+                                                     int dim, double* __restrict__ part,
+                                                     double (*red)[10]) {
+    const uint32_t b0 = off[I.cell_base], e0 = off[I.cell_base_end];
+    const uint32_t chunk = (e0 - b0 + BATCH_SPLIT - 1) / BATCH_SPLIT;
+    const uint32_t b = b0 + chunk_id * chunk;
+    const uint32_t e = b + chunk < e0 ? b + chunk : e0;
     double o[10];
-    batch_partial<NT>(S, pcount, off[I.cell_base], off[I.cell_base_end], dim, o, red);
-    if (threadIdx.x == 0) batch_finish_inst<Real>(I, inst, o, idt, it, irec, kick, ctl);
-    __syncthreads();
+    batch_partial<NT>(S, pcount, b < e0 ? b : e0, b < e0 ? e : e0, dim, o, red);
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 10; ++q) part[((size_t)inst * BATCH_SPLIT + chunk_id) * 10 + q] = o[q];
+}
+
+// Second stage (one warp, every lane calls it): instance `inst`'s BATCH_SPLIT partials
+// combined by a fixed shuffle tree, then its record, time and next dt.
+template <class Real>
+__device__ __forceinline__ void batch_finish_warp(const Inst<Real>& I, int inst,
+                                                  const double* __restrict__ part,
+                                                  double* __restrict__ idt, double* __restrict__ it,
+                                                  double* __restrict__ irec, int kick, Control* ctl) {
+    const int lane = threadIdx.x & 31;
+    double v[10];
+    for (int q = 0; q < 10; ++q)
+        v[q] = lane < BATCH_SPLIT ? part[((size_t)inst * BATCH_SPLIT + lane) * 10 + q] : 0.0;
+    for (int o2 = 16; o2 > 0; o2 >>= 1)
+        for (int q = 0; q < 10; ++q) {
+            const double y = __shfl_down_sync(0xffffffffu, v[q], o2);
+            v[q] = (q >= 4 && q <= 6) ? fmax(v[q], y) : v[q] + y;
+        }
+    if (lane == 0) batch_finish_inst<Real>(I, inst, v, idt, it, irec, kick, ctl);
 }
 
 }  // namespace sph

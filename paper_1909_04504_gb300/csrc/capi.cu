@@ -509,6 +509,7 @@ FusedLaunch fused_launch(sph_ctx* c) {
     F.passes = c->passes;
     F.ntiles = onesweep_tiles(c->N);
     F.ncells = c->G.ncells;
+    F.wall_pass = c->wall_pass ? 1 : 0;
     F.wait_ns = c->wait_ns;
     return F;
 }
@@ -611,10 +612,8 @@ void enqueue_pec_step(sph_ctx* c) {
 // nsteps steps in the context's mode (tables already uploaded, rates valid).
 sph_status run_steps(sph_ctx* c, int nsteps) {
     if (nsteps <= 0) return SPH_OK;
-    // the persistent kernel has neither the solid-wall pressure phase, the midpoint
-    // integrator nor the EDAC pressure gather: such steps run as the graph
-    if (c->step_mode == SPH_STEP_PERSISTENT && !c->wall_pass && !c->pec && !c->edac)
-        return run_fused(c, nsteps);
+    // the persistent kernel runs one evaluation per step: midpoint steps run as the graph
+    if (c->step_mode == SPH_STEP_PERSISTENT && !c->pec) return run_fused(c, nsteps);
     if (!c->graph[0] || c->graph_timed != c->timing) {
         sph_status s = capture_step_graphs(c);
         if (s != SPH_OK) return s;
@@ -1512,9 +1511,8 @@ sph_status sph_kernels_per_step(const sph_ctx* ctx, const sph_scheme* scheme, in
     const bool wp = scheme->wall_bc == SPH_WALL_ADAMI && c->nwall > 0;
     const bool pec = scheme->integrator == SPH_INTEGRATOR_PEC;
     const int build_eval = 1 + c->passes + 1 + 1 + (wp ? 1 : 0) + 1 + (c->ninst ? 2 : 0);
-    const bool edac = scheme->density == SPH_DENSITY_EDAC;  // the persistent form runs it as the graph
     if (pec) *count = 2 * build_eval + 3;  // + predictor, corrector, record
-    else *count = c->step_mode == SPH_STEP_PERSISTENT && !wp && !edac ? 1 : build_eval;
+    else *count = c->step_mode == SPH_STEP_PERSISTENT ? 1 : build_eval;
     return SPH_OK;
 }
 
@@ -1619,7 +1617,7 @@ sph_status tune_lanes(sph_ctx* c) {
 // Times a few steps in each mode from the same state and keeps the faster mode; the
 // state, time and records are put back afterwards.
 sph_status choose_mode(sph_ctx* c) {
-    if (c->fused_bps[tindex(c->group_m)] < 1 || c->wall_pass || c->pec) {  // graph only
+    if (c->fused_bps[tindex(c->group_m)] < 1 || c->pec) {  // graph only
         c->step_mode = SPH_STEP_GRAPH;
         return SPH_OK;
     }

@@ -4,7 +4,8 @@
 // are separated by a grid-wide barrier:
 //   drift + cell keys | radix sort (histogram | digit scan | scatter, per 8-bit pass) |
 //   reorder + predictor kick + EOS shadow, and the cell table | density pass |
-//   momentum pass + corrector kick | diagnostics, next dt (per instance for a batch).
+//   [solid-wall pressure] | momentum pass + corrector kick | diagnostics, next dt (for a
+//   batch per instance, in the two stages of the batch kernels with a barrier between).
 // The per-particle and per-tile bodies are the ones of the per-phase kernels, so both
 // forms compute the same step; a small problem saves the launch gaps between phases.
 //
@@ -18,6 +19,7 @@
 #include "batch_impl.cuh"
 #include "sort_impl.cuh"
 #include "step_impl.cuh"
+#include "walls_impl.cuh"
 
 namespace sph {
 
@@ -60,8 +62,10 @@ __device__ __forceinline__ bool grid_sync(Control* ctl, unsigned long long limit
     return __syncthreads_and(ok) != 0;
 }
 
+// FP32: 3 blocks of 256 per SM (80 registers; the pair phases are latency-bound and gain
+// from the extra warps), FP64: 2.
 template <class Real, int DIM, int KERNEL, int T>
-__global__ void __launch_bounds__(FUSED_THREADS, 2) k_step_fused(const FusedLaunch F) {
+__global__ void __launch_bounds__(FUSED_THREADS, sizeof(Real) == 4 ? 3 : 2) k_step_fused(const FusedLaunch F) {
     using V = typename V4<Real>::T;
     __shared__ union {
         uint32_t h[4][RADIX];
@@ -155,7 +159,7 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_step_fused(const FusedLaun
     // ---- gather into cell order (predictor kick, shadow) and the cell table
     for (int k = tid; k < L.n; k += nthreads) {
         const int inst = find_instance(L.cell_bounds, L.ninst, skeys[k]);
-        reorder_one<Real>(L.Sin, L.S, k, (int)perm[k], L.dim, L.idt[inst], 1, 0, P, Q, E);
+        reorder_one<Real>(L.Sin, L.S, k, (int)perm[k], L.dim, L.idt[inst], 1, 0, P, Q, E, L.edac);
     }
     for (int c = tid; c <= F.ncells; c += nthreads)
         F.off[c] = cell_offset_near(skeys, L.n, (uint32_t)c, F.off[c]);
@@ -172,6 +176,13 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_step_fused(const FusedLaun
         if (L.finalize) block_counts<FUSED_THREADS>(dc, F.part + (size_t)blockIdx.x * FUSED_PART + 8, sm.cred);
     }
     if (!grid_sync(ctl, F.wait_ns)) return;
+
+    // ---- solid-wall pressure of the wall particles from their fluid neighbours
+    if (F.wall_pass) {
+        wall_pressure_range<Real, DIM, KERNEL, FUSED_THREADS>(blockIdx.x, nb, P, Q, R, skeys, L.n, tab,
+                                                              L.cell_bounds, L.ninst, L.S, L.nl, L.cnt);
+        if (!grid_sync(ctl, F.wait_ns)) return;
+    }
     if (stamp) ctl->stamp[4] = global_ns();
 
     // ---- momentum pass (T lanes per destination) + corrector kick; the sort workspace is
@@ -201,9 +212,16 @@ __global__ void __launch_bounds__(FUSED_THREADS, 2) k_step_fused(const FusedLaun
             ctl->stamp[6] = global_ns();
         }
     } else {
-        for (int inst = blockIdx.x; inst < L.ninst; inst += nb)
-            batch_reduce_inst<Real, FUSED_THREADS>(L.S, L.pcount, F.off, tab[inst], inst, L.dim,
-                                                   L.idt, L.it, L.irec, 1, ctl, sm.bred);
+        // the two stages of the batch kernels (same chunks, same fixed-order combination)
+        // with a barrier between them, so every block takes part in the first
+        for (int w = blockIdx.x; w < L.ninst * BATCH_SPLIT; w += nb)
+            batch_chunk_partials<Real, FUSED_THREADS>(L.S, L.pcount, F.off, tab[w / BATCH_SPLIT],
+                                                      w / BATCH_SPLIT, w % BATCH_SPLIT, L.dim, L.bpart,
+                                                      sm.bred);
+        if (!grid_sync(ctl, F.wait_ns)) return;
+        for (int inst = (blockIdx.x * FUSED_THREADS + threadIdx.x) >> 5; inst < L.ninst;
+             inst += nb * (FUSED_THREADS / 32))
+            batch_finish_warp<Real>(tab[inst], inst, L.bpart, L.idt, L.it, L.irec, 1, ctl);
         if (stamp) {
             ctl->outside = 0;
             ctl->stamp[6] = global_ns();

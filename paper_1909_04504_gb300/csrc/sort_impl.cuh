@@ -152,15 +152,23 @@ __device__ __forceinline__ void radix_scatter_tile(const uint32_t* __restrict__ 
 // taken beforehand (with the cell keys). Tiles take their index from a counter in launch
 // order, so every tile a tile waits for has started and waits only on earlier tiles.
 // Status word per (tile, digit): 2 flag bits (aggregate / inclusive prefix) + 30-bit count.
+// The tile is put in digit order in shared memory before the look-back, and written out
+// from there in that order: a warp's 32 stores then cover a few runs of consecutive
+// positions instead of up to 32 scattered words.
 constexpr uint32_t LB_AGGREGATE = 1u << 30;
 constexpr uint32_t LB_PREFIX = 2u << 30;
 constexpr uint32_t LB_COUNT = (1u << 30) - 1u;
-constexpr int LB_BATCH = 8;  // predecessors read per look-back round
+// Predecessors read per look-back round (32 measured slower than 8 on 2.9 M keys: the
+// rounds are not what bounds a pass).
+constexpr int LB_BATCH = 8;
+constexpr int ONESWEEP_MAX_ITEMS = 8;
 
 struct OnesweepSmem {
     uint32_t base_d[RADIX];
     uint32_t wcnt[SORT_WARPS][RADIX];
     uint32_t wsum[SORT_WARPS];
+    uint32_t sk[SORT_THREADS * ONESWEEP_MAX_ITEMS];  // the tile in digit order
+    uint32_t sv[SORT_THREADS * ONESWEEP_MAX_ITEMS];
     int tile;
 };
 
@@ -171,13 +179,28 @@ __device__ __forceinline__ unsigned long long sort_clock_ns() {
 }
 
 // Keys per thread of a one-sweep tile: small problems take short tiles (more blocks,
-// shorter serial ranking loops), large ones tiles of 2,048 keys (8 per thread: 79
-// registers, three blocks per SM; 16 per thread needed 128 and ran slower).
+// shorter serial ranking loops), large ones tiles of 2,048 keys.
 __host__ __device__ __forceinline__ int onesweep_items(int n) { return n <= 131072 ? 4 : 8; }
 __host__ __device__ __forceinline__ int onesweep_tiles(int n) {
     const int tile = SORT_THREADS * onesweep_items(n);
     const int t = (n + tile - 1) / tile;
     return t < 1 ? 1 : t;
+}
+
+// Exclusive scan of v over the block's SORT_THREADS threads (thread tid holds digit tid).
+// Uses wsum: the caller separates two calls by a barrier.
+__device__ __forceinline__ uint32_t digit_scan_excl(uint32_t v, uint32_t* wsum) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    uint32_t pre = 0;
+    for (int w = 0; w < warp; ++w) pre += wsum[w];
+    return pre + x - v;
 }
 
 // One tile of a one-sweep pass (SORT_THREADS threads, ITEMS keys each). ghist: the RADIX
@@ -193,6 +216,7 @@ __device__ __forceinline__ void radix_onesweep_tile(const uint32_t* __restrict__
                                                     uint32_t* status, int tile,
                                                     OnesweepSmem& sm, unsigned* ctl_status,
                                                     unsigned long long wait_ns) {
+    static_assert(ITEMS <= ONESWEEP_MAX_ITEMS, "tile larger than its shared staging");
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int w = 0; w < SORT_WARPS; ++w) sm.wcnt[w][tid] = 0;
     __syncthreads();
@@ -200,6 +224,7 @@ __device__ __forceinline__ void radix_onesweep_tile(const uint32_t* __restrict__
     const int wbase = tile * TILE + warp * (TILE / SORT_WARPS);
     uint32_t kr[ITEMS], vr[ITEMS], rank[ITEMS];
     const unsigned ltmask = lanemask_lt();
+    // ranks inside the warp's contiguous range, in input order (stability)
 #pragma unroll
     for (int it = 0; it < ITEMS; ++it) {
         const int idx = wbase + it * 32 + lane;
@@ -216,7 +241,7 @@ __device__ __forceinline__ void radix_onesweep_tile(const uint32_t* __restrict__
         rank[it] = before + __popc(peers & ltmask);
     }
     __syncthreads();
-    // per digit (thread tid): exclusive prefix over warps and the tile's count
+    // per digit (thread tid): exclusive prefix over warps and the tile's count, published
     uint32_t count = 0;
     for (int w = 0; w < SORT_WARPS; ++w) {
         const uint32_t c = sm.wcnt[w][tid];
@@ -225,6 +250,19 @@ __device__ __forceinline__ void radix_onesweep_tile(const uint32_t* __restrict__
     }
     uint32_t* mine = status + (size_t)tile * RADIX + tid;
     atomicExch(mine, (tile == 0 ? LB_PREFIX : LB_AGGREGATE) | count);
+    // the tile in digit order in shared memory: digit d starts at lstart(d)
+    const uint32_t lstart = digit_scan_excl(count, sm.wsum);
+    sm.base_d[tid] = lstart;
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < ITEMS; ++it) {
+        if (wbase + it * 32 + lane < n) {
+            const uint32_t d = (kr[it] >> shift) & (RADIX - 1);
+            const uint32_t e = sm.base_d[d] + sm.wcnt[warp][d] + rank[it];
+            sm.sk[e] = kr[it];
+            sm.sv[e] = vr[it];
+        }
+    }
     uint32_t excl = 0;
     int ok = 1;
     if (tile > 0) {
@@ -262,31 +300,19 @@ __device__ __forceinline__ void radix_onesweep_tile(const uint32_t* __restrict__
         }
         if (ok) atomicExch(mine, LB_PREFIX | (excl + count));
     }
-    // global digit base: exclusive scan of the pass histogram
-    {
-        const uint32_t v = ghist[tid];
-        uint32_t x = v;
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) sm.wsum[warp] = x;
-        __syncthreads();
-        uint32_t pre = 0;
-        for (int w = 0; w < warp; ++w) pre += sm.wsum[w];
-        sm.base_d[tid] = pre + x - v + excl;
-    }
+    // global position of the tile's element e of digit d: gbase(d) + excl(d) + e - lstart(d)
+    // with gbase the exclusive scan of the pass histogram (the barrier inside the scan
+    // also ends every thread's reads of base_d above)
+    const uint32_t gstart = digit_scan_excl(ghist[tid], sm.wsum) + excl;
+    sm.base_d[tid] = gstart - lstart;  // modulo 2^32: e >= lstart(d) for every element
     if (!__syncthreads_and(ok)) return;
-#pragma unroll
-    for (int it = 0; it < ITEMS; ++it) {
-        const int idx = wbase + it * 32 + lane;
-        if (idx < n) {
-            const uint32_t d = (kr[it] >> shift) & (RADIX - 1);
-            const uint32_t pos = sm.base_d[d] + sm.wcnt[warp][d] + rank[it];
-            if (pos < (uint32_t)n) {
-                keys_out[pos] = kr[it];
-                vals_out[pos] = vr[it];
-            }
+    const int valid_n = min(TILE, n - tile * TILE);
+    for (int e = tid; e < valid_n; e += SORT_THREADS) {
+        const uint32_t key = sm.sk[e];
+        const uint32_t pos = sm.base_d[(key >> shift) & (RADIX - 1)] + (uint32_t)e;
+        if (pos < (uint32_t)n) {
+            keys_out[pos] = key;
+            vals_out[pos] = sm.sv[e];
         }
     }
 }

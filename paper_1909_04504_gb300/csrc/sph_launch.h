@@ -104,6 +104,7 @@ struct FusedLaunch {
     uint32_t* off;               // cell table, written by the reorder phase
     double* part;                // FUSED_PART doubles per block
     int passes, ntiles, ncells;
+    int wall_pass;               // the solid-wall pressure phase runs between the pair passes
     unsigned long long wait_ns;  // limit of one barrier wait
 };
 cudaError_t launch_fused(const FusedLaunch& F, int T, int grid, cudaStream_t st);

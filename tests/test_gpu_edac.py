@@ -131,18 +131,36 @@ def test_batch_equals_single_runs_bitwise():
     batch.close()
 
 
-def test_persistent_mode_runs_the_graph():
-    wl = _wl(G.PREC_FP32, n=24)
+@pytest.mark.parametrize("prec", [G.PREC_FP64, G.PREC_FP32])
+def test_persistent_form_equals_the_graph(prec):
+    """One cooperative launch per step (the reorder gathers the pressure there too),
+    bitwise equal to the per-phase graph; a batch likewise."""
+    wl = _wl(prec, n=24)
     sch = G.scheme_of(wl)
     out = []
     for mode in (G.STEP_GRAPH, G.STEP_PERSISTENT):
         with sim_of(wl) as sim:
             sim.set_groups(4)
             sim.set_step_mode(mode)
+            if mode == G.STEP_PERSISTENT:
+                assert sim.kernels_per_step(sch) == 1
             sim.step(sch, wl.dt, 3)
             out.append(sim.state())
     for k in FIELDS:
         assert np.array_equal(out[0][k], out[1][k]), k
+    wls = [_wl(prec, n=20), _wl(prec, n=26), _wl(prec, n=14)]
+    schemes = [G.scheme_of(w) for w in wls]
+    res = []
+    for mode in (G.STEP_GRAPH, G.STEP_PERSISTENT):
+        batch = G.BatchSimulation(wls)
+        batch.set_groups(2)
+        batch.set_step_mode(mode)
+        batch.step_batch(schemes, [w.dt for w in wls], 3)
+        res.append([batch.instance_state(k) for k in range(len(wls))])
+        batch.close()
+    for k in range(len(wls)):
+        for f in FIELDS:
+            assert np.array_equal(res[0][k][f], res[1][k][f]), (k, f)
 
 
 def test_refusals():

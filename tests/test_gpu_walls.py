@@ -2,8 +2,8 @@
 Adams listed among the schemes of Sec. 2.3) through the C ABI against the oracle: one
 evaluation and one step (FP64 mode <= 1e-10 normwise per field, FP32 pair loops
 <= 1e-4 relative L2), the hydrostatic closed form at the walls, a batch of instances
-bitwise equal to single runs, the persistent step form falling back to the graph, and
-the adjoint refusing the option."""
+bitwise equal to single runs, the persistent step form (its own wall phase) equal to
+the graph bitwise, and the adjoint refusing the option."""
 import copy
 
 import numpy as np
@@ -132,16 +132,37 @@ def test_batch_with_wall_pressure_equals_single_runs(precision):
     batch.close()
 
 
-def test_persistent_form_runs_the_graph_and_adjoint_refuses():
-    wl = oracle_wl(CONFIGS["db2d"], G.PREC_FP32)
+@pytest.mark.parametrize("name", sorted(CONFIGS))
+@pytest.mark.parametrize("prec", [G.PREC_FP64, G.PREC_FP32])
+def test_persistent_form_with_wall_pressure(name, prec):
+    """The persistent step runs the wall phase between its pair passes (one launch per
+    step) and follows the graph bitwise; one step meets the oracle bar."""
+    wl = oracle_wl(CONFIGS[name], prec)
     sch = G.scheme_of(wl)
+    fields = FIELDS_3D if wl.dim == 3 else FIELDS_2D
+    s = O.state_of(wl)
+    st, hist = O.run(wl, s, wl.dt, 1)
     with sim_of(wl) as a, sim_of(wl) as b:
+        for sim in (a, b):
+            sim.set_groups(4)
         a.set_step_mode(G.STEP_PERSISTENT)
-        a.step(sch, wl.dt, 5)
+        assert a.kernels_per_step(sch) == 1
+        a.step(sch, wl.dt, 1)
+        g = a.state()
+        for f in fields:
+            assert field_ok(wl, f, g[f], st[f], s[f]), f
+        assert a.history()[0, 8] == hist[1, 8]
+        a.step(sch, wl.dt, 4)
         b.step(sch, wl.dt, 5)
         sa, sb = a.state(), b.state()
-        for f in ("x", "y", "u", "v", "rho"):
+        for f in fields:
             assert np.array_equal(sa[f], sb[f]), f
+
+
+def test_adjoint_refuses_the_wall_pressure():
+    wl = oracle_wl(CONFIGS["db2d"], G.PREC_FP32)
+    sch = G.scheme_of(wl)
+    with sim_of(wl) as b:
         sch0 = G.scheme_of(wl, wall_bc=G.WALL_DENSITY)
         assert b.kernels_per_step(sch) == b.kernels_per_step(sch0) + 1
         with pytest.raises(G.SphError):
