@@ -14,6 +14,11 @@ Functions (each follows the paper's passage named in the C source):
                                     EDAC pressure equation of Sec. 2.3's scheme list)
   run(wl, state, dt, steps)         predictor-corrector steps (Sec. 2.1)
   grad(wl, state, dt, K, du, dnu)   forward-mode derivative of the final kinetic energy
+  vh_neighbors(dim, kernel, prec, x, y, z, h)
+                                    CSR neighbour sets with a per-particle smoothing length,
+                                    every pair examined (Sec. 2.2, the octree's use case)
+  vh_density(dim, kernel, prec, x, y, z, h, m)
+                                    summation density with h_ij = (h_i + h_j) / 2 (Eq. 2)
 """
 from __future__ import annotations
 
@@ -73,6 +78,9 @@ def lib():
         _lib.ora_grad.argtypes = ([P, C.c_int64] + [d] * 8 + [u8, C.c_double, C.c_int32]
                                   + [d] * 3 + [C.c_double, C.c_double, d, d])
         _lib.ora_threads.restype = C.c_int
+        _lib.ora_vh_neighbors.argtypes = [C.c_int32] * 3 + [C.c_int64] + [d] * 4 + [i64, i32]
+        _lib.ora_vh_neighbors.restype = C.c_int64
+        _lib.ora_vh_density.argtypes = [C.c_int32] * 3 + [C.c_int64] + [d] * 6
     return _lib
 
 
@@ -231,3 +239,42 @@ def grad(wl, s: Dict[str, np.ndarray], dt: float, K: int, du=None, dv=None, dw=N
     if rc:
         raise ValueError(f"grad failed ({rc})")
     return ke.value, dke.value
+
+
+def _vh_args(dim, x, y, z, h):
+    x, y, h = _f64(x), _f64(y), _f64(h)
+    z = _f64(z) if z is not None else np.zeros_like(x)
+    if dim == 2:
+        z = np.zeros_like(x)
+    return x, y, z, h
+
+
+def vh_neighbors(dim: int, kernel: int, precision: int, x, y, z, h):
+    """CSR (offsets int64[n+1], idx int32[nnz]) of the variable-h neighbour relation
+    |x_i - x_j| < k max(h_i, h_j), j != i, ascending ids."""
+    x, y, z, h = _vh_args(dim, x, y, z, h)
+    n = x.shape[0]
+    off = np.zeros(n + 1, np.int64)
+    L = lib()
+    i64 = C.POINTER(C.c_int64)
+    nnz = L.ora_vh_neighbors(dim, kernel, precision, n, _d(x), _d(y), _d(z), _d(h),
+                             off.ctypes.data_as(i64), None)
+    if nnz < 0:
+        raise ValueError(f"vh_neighbors failed ({nnz})")
+    idx = np.zeros(max(nnz, 1), np.int32)
+    L.ora_vh_neighbors(dim, kernel, precision, n, _d(x), _d(y), _d(z), _d(h),
+                       off.ctypes.data_as(i64), idx.ctypes.data_as(C.POINTER(C.c_int32)))
+    return off, idx[:nnz]
+
+
+def vh_density(dim: int, kernel: int, precision: int, x, y, z, h, m):
+    """rho_i = m_i W(0, h_i) + sum_j m_j W(r_ij, (h_i + h_j) / 2) over the variable-h
+    neighbour set of the precision mode."""
+    x, y, z, h = _vh_args(dim, x, y, z, h)
+    m = _f64(m)
+    rho = np.zeros(x.shape[0])
+    rc = lib().ora_vh_density(dim, kernel, precision, x.shape[0], _d(x), _d(y), _d(z), _d(h),
+                              _d(m), _d(rho))
+    if rc:
+        raise ValueError(f"vh_density failed ({rc})")
+    return rho

@@ -941,6 +941,116 @@ int ora_grad(const ora_params* P, int64_t n, const double* x, const double* y, c
     return 0;
 }
 
+/* ------------------------------------------------ variable smoothing length
+ * Sec. 2.2: with a support radius that varies from particle to particle a uniform grid
+ * needs cells of the largest radius, so the paper searches such particle sets with an
+ * octree. What the search computes has a plain definition (reading C-VH): particle i
+ * carries its own h_i, and j != i is a neighbour of i when
+ *   |x_i - x_j|^2 < (k max(h_i, h_j))^2,
+ * a symmetric relation (each pair seen from both ends), with k the kernel's support
+ * factor, r^2 = ((dx dx) + dy dy) + dz dz and R = k max(h_i, h_j) formed in the precision
+ * of the mode from the positions and h rounded to it; no periodic axes. The oracle
+ * examines every pair (the octree only decides which pairs need examining). */
+}  // extern "C"
+
+namespace {
+
+template <class P_>
+bool vh_within(int dim, double k, const double* xi, const double* xj, double hi, double hj) {
+    P_ r2 = (P_)0;
+    for (int d = 0; d < dim; ++d) {
+        P_ dx = (P_)xi[d] - (P_)xj[d];
+        r2 = r2 + dx * dx;
+    }
+    const P_ hm = (P_)hi > (P_)hj ? (P_)hi : (P_)hj;
+    const P_ R = (P_)k * hm;
+    return r2 < R * R;
+}
+
+}  // namespace
+
+extern "C" {
+
+/* Neighbour lists in CSR form (ascending ids); idx == NULL: offsets only. Returns nnz or
+ * a negative error. */
+int64_t ora_vh_neighbors(int32_t dim, int32_t kernel, int32_t precision, int64_t n,
+                         const double* x, const double* y, const double* z, const double* h,
+                         int64_t* offsets, int32_t* idx) {
+    if ((dim != 2 && dim != 3) || n < 0 || (kernel < 0 || kernel > 2)) return -1;
+    const double k = support_factor(kernel);
+    const double* xs[3] = {x, y, z};
+    std::vector<double> pos((size_t)n * 3, 0.0);
+    for (int64_t i = 0; i < n; ++i)
+        for (int d = 0; d < dim; ++d) pos[(size_t)i * 3 + d] = xs[d][i];
+    std::vector<int64_t> cnt((size_t)n, 0);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t c = 0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            const bool in = precision == PREC_FP32
+                                ? vh_within<float>(dim, k, &pos[(size_t)i * 3], &pos[(size_t)j * 3], h[i], h[j])
+                                : vh_within<double>(dim, k, &pos[(size_t)i * 3], &pos[(size_t)j * 3], h[i], h[j]);
+            c += in ? 1 : 0;
+        }
+        cnt[(size_t)i] = c;
+    }
+    offsets[0] = 0;
+    for (int64_t i = 0; i < n; ++i) offsets[i + 1] = offsets[i] + cnt[(size_t)i];
+    if (idx) {
+#pragma omp parallel for schedule(dynamic, 64)
+        for (int64_t i = 0; i < n; ++i) {
+            int64_t w = offsets[i];
+            for (int64_t j = 0; j < n; ++j) {
+                if (j == i) continue;
+                const bool in = precision == PREC_FP32
+                                    ? vh_within<float>(dim, k, &pos[(size_t)i * 3], &pos[(size_t)j * 3], h[i], h[j])
+                                    : vh_within<double>(dim, k, &pos[(size_t)i * 3], &pos[(size_t)j * 3], h[i], h[j]);
+                if (in) idx[w++] = (int32_t)j;
+            }
+        }
+    }
+    return offsets[n];
+}
+
+/* Summation density with variable smoothing length (Eq. 2 with the pair smoothing length
+ * h_ij = (h_i + h_j) / 2, the symmetrised kernel of variable-h SPH, reading C-VH):
+ *   rho_i = m_i W(0, h_i) + sum_{j in N(i)} m_j W(|x_i - x_j|, h_ij)
+ * over the neighbour set of the mode, in FP64 (k h_ij <= k max(h_i, h_j), so every pair
+ * the kernel reaches is in the set). */
+int ora_vh_density(int32_t dim, int32_t kernel, int32_t precision, int64_t n, const double* x,
+                   const double* y, const double* z, const double* h, const double* m,
+                   double* rho) {
+    if ((dim != 2 && dim != 3) || n < 0 || (kernel < 0 || kernel > 2)) return -1;
+    const double k = support_factor(kernel);
+    const double* xs[3] = {x, y, z};
+    std::vector<double> pos((size_t)n * 3, 0.0);
+    for (int64_t i = 0; i < n; ++i)
+        for (int d = 0; d < dim; ++d) pos[(size_t)i * 3 + d] = xs[d][i];
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; ++i) {
+        double W, dW;
+        kernel_eval<double>(kernel, dim, h[i], 0.0, &W, &dW);
+        double s = m[i] * W;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            const bool in = precision == PREC_FP32
+                                ? vh_within<float>(dim, k, &pos[(size_t)i * 3], &pos[(size_t)j * 3], h[i], h[j])
+                                : vh_within<double>(dim, k, &pos[(size_t)i * 3], &pos[(size_t)j * 3], h[i], h[j]);
+            if (!in) continue;
+            double r2 = 0.0;
+            for (int d = 0; d < dim; ++d) {
+                const double dx = pos[(size_t)i * 3 + d] - pos[(size_t)j * 3 + d];
+                r2 = r2 + dx * dx;
+            }
+            kernel_eval<double>(kernel, dim, 0.5 * (h[i] + h[j]), std::sqrt(r2), &W, &dW);
+            s += m[j] * W;
+        }
+        rho[i] = s;
+    }
+    return 0;
+}
+
 /* Threads the oracle's parallel loops use (1 without OpenMP). */
 int ora_threads(void) {
 #ifdef _OPENMP

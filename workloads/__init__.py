@@ -17,6 +17,8 @@ Workloads (sizes follow the five benchmark configurations of the WCSPH hot path)
 * ``batch_tg2d``       many independent Taylor-Green instances of uneven size.
 * ``dam_break_3d``     1 x 0.5 x 0.5 m block at dx = 0.005 in a 3.2 x 1.0 m tank with
   three wall layers 0.5 m high (906,828 wall particles).
+* ``gaussian_blob``    particles with their own smoothing lengths (normally distributed
+  positions, h from the local number density) for the variable-support search.
 
 Seeds: numpy PCG64 with seed = 1909_04504 + workload index unless given.
 Jitter: independent U[-j dx, +j dx] per coordinate.
@@ -358,6 +360,54 @@ def batch_tg2d(instances: int = 64, n_min: int = 2500, n_max: int = 40000,
         w.name = f"tg2d_instance{k}_{n}x{n}"
         out.append(w)
     return out
+
+
+@dataclass
+class VHSet:
+    """Particles with their own smoothing lengths (the variable-support case of Sec. 2.2
+    that the paper searches with an octree): positions, h and masses, all FP64."""
+    name: str
+    dim: int
+    kernel: int
+    precision: int
+    x: np.ndarray
+    y: np.ndarray
+    z: np.ndarray
+    h: np.ndarray
+    m: np.ndarray
+
+    @property
+    def n(self) -> int:
+        return int(self.x.shape[0])
+
+
+def gaussian_blob(n: int = 1_000_000, dim: int = 3, eta: float = 1.2, cut: float = 3.0,
+                  kernel: int = WENDLAND_C2, precision: int = PREC_FP32,
+                  seed: Optional[int] = None) -> VHSet:
+    """A self-gravitating-cloud-like particle set: n positions drawn from an isotropic
+    normal distribution of unit variance, truncated at radius ``cut`` (draws beyond it are
+    redrawn), equal masses 1 / n, and h_i = eta (m / rho(r_i))^(1/dim) from the number
+    density of that distribution, rho(r) = exp(-r^2 / 2) / ((2 pi)^(dim/2) P(r < cut)).
+    The support radius grows by exp(cut^2 / (2 dim)) from the centre to the edge (4.5x in
+    3D, 9.5x in 2D) while the density falls by exp(cut^2 / 2) = 90x.
+    """
+    rng = _rng(seed, 7 if dim == 3 else 6)
+    pts = np.zeros((0, dim))
+    while pts.shape[0] < n:
+        draw = rng.normal(size=(2 * (n - pts.shape[0]) + 16, dim))
+        draw = draw[np.sum(draw * draw, axis=1) < cut * cut]
+        pts = np.vstack([pts, draw[:n - pts.shape[0]]])
+    r2 = np.sum(pts * pts, axis=1)
+    if dim == 3:
+        inside = math.erf(cut / math.sqrt(2.0)) - math.sqrt(2.0 / math.pi) * cut * math.exp(-cut * cut / 2)
+    else:
+        inside = 1.0 - math.exp(-cut * cut / 2)
+    rho = np.exp(-0.5 * r2) / ((2.0 * math.pi) ** (dim / 2.0) * inside)
+    m = np.full(n, 1.0 / n)
+    h = eta * (m / rho) ** (1.0 / dim)
+    z = pts[:, 2].copy() if dim == 3 else _zeros(n)
+    return VHSet(name=f"gaussian_blob_{dim}d_{n}", dim=dim, kernel=kernel, precision=precision,
+                 x=pts[:, 0].copy(), y=pts[:, 1].copy(), z=z, h=h, m=m)
 
 
 def config(index: int, small: bool = False):
