@@ -784,6 +784,175 @@ def reference_arm(args):
     }
 
 
+# ------------------------------------------------- variable smoothing length search
+VH_WORKLOADS = ("gaussian_blob_3d", "gaussian_blob_2d")
+VH_METRIC = "neighbour pairs/s of the variable-h octree search (build + query)"
+VH_UNIT = "neighbour pairs/s"
+VH_N = 1_000_000
+VH_LEAF = 16
+
+
+def vh_set(name: str):
+    import workloads as W
+    return W.gaussian_blob(VH_N, dim=3 if name.endswith("3d") else 2, precision=W.PREC_FP32)
+
+
+def vh_flops(dim: int, cand: float, pairs: float) -> float:
+    """Algorithmic FP32 flops of the query: per pair examined the squared distance (d
+    subtractions, d products, d - 1 sums) and the radius (k max(h_i, h_j), squared); per
+    neighbour the density term (h_ij: 2, reciprocal, square root, q, 1 / h_ij^d: d - 1,
+    the Wendland polynomial: 7, sigma w m: 3, the compensated add: 4). Node tests are not
+    counted (a lower bound)."""
+    test = 3 * dim + 1
+    dens = 2 + 1 + 1 + 1 + (dim - 1) + 7 + 3 + 4
+    return test * cand + dens * pairs
+
+
+def vh_describe(s) -> dict:
+    import numpy as np
+    return {"workload": f"{s.name}: {s.n:,} particles, {s.dim}D, normal positions truncated at "
+                        f"r = 3, h = 1.2 (m / rho)^(1/{s.dim}) from the number density "
+                        f"({float(np.min(s.h)):.4g} .. {float(np.max(s.h)):.4g}), Wendland C2, "
+                        f"FP32 predicate and density, octree leaves of <= {VH_LEAF}",
+            "particles": s.n, "parallelism": "replicas (one independent problem per GPU)"}
+
+
+def vh_arm(args, rank, world, dist):
+    import numpy as np
+    import torch
+
+    import paper_1909_04504_gb300 as G
+
+    dev = torch.cuda.current_device()
+    s = vh_set(args.workload)
+    v = G.VariableHSearch(s.dim, s.kernel, s.precision, s.n, leaf_size=VH_LEAF)
+    z = s.z if s.dim == 3 else None
+    v.set(s.x, s.y, z, s.h, s.m)
+    for _ in range(args.warmup):
+        v.search()
+    st = v.stats()
+    stream = torch.cuda.ExternalStream(v.stream_handle)
+    flush = torch.empty(args.flush_mb * (1 << 20) // 4, dtype=torch.int32, device=dev)
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:  # noqa: BLE001
+        uuid = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]
+    sms = int(torch.cuda.get_device_properties(dev).multi_processor_count)
+    v.set_timing(True)
+    v.search()
+    sampler = ClockSampler(uuid)
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    # ---- timed region: K searches, L2 flushed before each (the inputs fit in L2); the
+    # device time of each search from the events recorded around its two phases
+    build, query = [], []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        v.search()
+        ph = v.phase_times()
+        build.append(ph["build"])
+        query.append(ph["query"])
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t_wall = time.perf_counter() - t_wall0
+    clocks = sampler.stop()
+    v.set_timing(False)
+    total_ms = sum(build) + sum(query)
+    pairs = float(st["pairs"]) * args.steps
+    total_ms, job_pairs = job_totals(dist, total_ms, pairs, device=dev)
+    value = job_pairs / (total_ms / 1e3)
+    # ---- end to end through the public API: the inputs from host memory, the search, the
+    # density back to the host, per step (host clock)
+    e2e_steps = max(3, min(args.steps, 20))
+    rho = None
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        v.set(s.x, s.y, z, s.h, s.m)
+        v.search()
+        rho = v.density()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": st["pairs"] * e2e_steps / e2e_s, "unit": VH_UNIT,
+           "h2d_bytes_per_step": 8 * s.n * (5 if s.dim == 3 else 4),
+           "d2h_bytes_per_step": 8 * s.n, "steps": e2e_steps,
+           "path": "sph_vh_set (host arrays) + sph_vh_search + sph_vh_density per step, host clock"}
+    mhz, mhz_src = sm_max_mhz(clocks)
+    q_ms = statistics.mean(query)
+    flops = vh_flops(s.dim, st["candidates"], st["pairs"])
+    peak = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12 if mhz else None
+    achieved = flops / (q_ms / 1e3) / 1e12
+    B = 10 if s.dim == 3 else 15
+    launches = 2 + 1 + 4 + 1 + B + (B + 1) + 1
+    line = {
+        "metric": VH_METRIC, "value": value, "unit": VH_UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": dict(vh_describe(s), l2="flushed between timed searches (512 MB write)"),
+        "phase_ms": {"build": statistics.mean(build), "query": q_ms},
+        "search": {k: st[k] for k in ("nodes", "leaves", "depth", "candidates", "pairs", "max_count")},
+        "pairs_per_particle": st["pairs"] / s.n,
+        "candidates_per_pair": st["candidates"] / max(st["pairs"], 1),
+        "roofline": {"bound": "alu", "achieved": round(achieved, 4),
+                     "peak": round(peak, 3) if peak else None, "unit": "TFLOP/s",
+                     "frac": round(achieved / peak, 5) if peak else None, "traffic": None,
+                     "kernel": "k_vh_query (octree walk, predicate, list, density)",
+                     "flops_per_launch": flops, "avg_launch_ms": round(q_ms, 5),
+                     "peak_source": f"derived: {sms} SMs (device) x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {mhz} MHz ({mhz_src})"},
+        "e2e": e2e, "gpu_launches": launches * args.steps, "clocks": clocks,
+        "wall_s": round(t_wall, 3),
+        "density_range": [float(np.min(rho)), float(np.max(rho))] if rho is not None else None,
+    }
+    v.close()
+    return line, s
+
+
+def vh_cpu_sample(s, target_s: float, seed: int = 5):
+    """The oracle's selected-rows form on a bounded sample of the particles (every pair of
+    a sampled particle examined): (pairs/s, seconds, rows, cores)."""
+    import numpy as np
+
+    import oracle as O
+    O.build()
+    rng = np.random.Generator(np.random.PCG64(seed))
+    rows = rng.choice(s.n, 64, replace=False)
+    t0 = time.perf_counter()
+    O.vh_rows(s.dim, s.kernel, s.precision, s.x, s.y, s.z, s.h, s.m, rows)
+    probe = max(time.perf_counter() - t0, 1e-3)
+    k = int(min(s.n, max(64, 64 * target_s / probe)))
+    rows = rng.choice(s.n, k, replace=False)
+    t0 = time.perf_counter()
+    off, _, _ = O.vh_rows(s.dim, s.kernel, s.precision, s.x, s.y, s.z, s.h, s.m, rows)
+    el = time.perf_counter() - t0
+    return float(off[-1]) / el, el, k, O.threads()
+
+
+def vh_cpu_baseline(s, target_s: float) -> dict:
+    v, el, k, cores = vh_cpu_sample(s, target_s)
+    return {"value": v, "unit": VH_UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{k} sampled particles of {s.name}, each tested against all {s.n:,} "
+                      f"(the oracle's all-pairs relation and density), {el:.1f} s"}
+
+
+def vh_reference_arm(args):
+    s = vh_set(args.workload)
+    v, el, k, cores = vh_cpu_sample(s, args.ref_seconds)
+    return {
+        "impl": "reference", "metric": VH_METRIC, "value": v, "unit": VH_UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": None,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": vh_describe(s),
+        "cpu_baseline": {"value": v, "unit": VH_UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{k} sampled particles, each against all {s.n:,}, {el:.1f} s"},
+        "e2e": {"value": v, "unit": VH_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -793,7 +962,7 @@ def main():
     ap.add_argument("--workload", default="dam_break_3d",
                     choices=["dam_break_2d", "taylor_green_2d", "taylor_green_2d_edac",
                              "taylor_green_3d", "dam_break_3d", "dam_break_3d_dx01", "batch_tg2d",
-                             "falling_cube_3d"])
+                             "falling_cube_3d"] + list(VH_WORKLOADS))
     ap.add_argument("--flush-mb", type=int, default=512)
     ap.add_argument("--fp64-steps", type=int, default=50)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -822,7 +991,8 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        print(json.dumps(reference_arm(args)), flush=True)
+        arm = vh_reference_arm if args.workload in VH_WORKLOADS else reference_arm
+        print(json.dumps(arm(args)), flush=True)
         return
 
     import torch
@@ -835,10 +1005,15 @@ def main():
         dist = tdist
     else:
         torch.cuda.set_device(0)
-    line, states, wl = gpu_arm(args, rank, world, dist)
+    if args.workload in VH_WORKLOADS:
+        line, vs = vh_arm(args, rank, world, dist)
+        cpu = (lambda: vh_cpu_baseline(vs, args.cpu_seconds))
+    else:
+        line, states, wl = gpu_arm(args, rank, world, dist)
+        cpu = (lambda: cpu_baseline(wl, args.cpu_seconds, states))
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds, states)
+            line["cpu_baseline"] = cpu()
         else:
             line["cpu_baseline"] = None
         print(json.dumps(line), flush=True)

@@ -19,6 +19,8 @@ Functions (each follows the paper's passage named in the C source):
                                     every pair examined (Sec. 2.2, the octree's use case)
   vh_density(dim, kernel, prec, x, y, z, h, m)
                                     summation density with h_ij = (h_i + h_j) / 2 (Eq. 2)
+  vh_rows(dim, kernel, prec, x, y, z, h, m, rows)
+                                    both for selected particles only (large sets)
 """
 from __future__ import annotations
 
@@ -81,6 +83,9 @@ def lib():
         _lib.ora_vh_neighbors.argtypes = [C.c_int32] * 3 + [C.c_int64] + [d] * 4 + [i64, i32]
         _lib.ora_vh_neighbors.restype = C.c_int64
         _lib.ora_vh_density.argtypes = [C.c_int32] * 3 + [C.c_int64] + [d] * 6
+        _lib.ora_vh_rows.argtypes = ([C.c_int32] * 3 + [C.c_int64] + [d] * 5
+                                     + [i64, C.c_int64, i64, i32, d])
+        _lib.ora_vh_rows.restype = C.c_int64
     return _lib
 
 
@@ -278,3 +283,24 @@ def vh_density(dim: int, kernel: int, precision: int, x, y, z, h, m):
     if rc:
         raise ValueError(f"vh_density failed ({rc})")
     return rho
+
+
+def vh_rows(dim: int, kernel: int, precision: int, x, y, z, h, m, rows):
+    """(offsets, idx, rho) of the selected particles: CSR over the selection, ascending ids."""
+    x, y, z, h = _vh_args(dim, x, y, z, h)
+    m = _f64(m)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    nr = rows.shape[0]
+    off = np.zeros(nr + 1, np.int64)
+    rho = np.zeros(nr)
+    L = lib()
+    i64 = C.POINTER(C.c_int64)
+    nnz = L.ora_vh_rows(dim, kernel, precision, x.shape[0], _d(x), _d(y), _d(z), _d(h), _d(m),
+                        rows.ctypes.data_as(i64), nr, off.ctypes.data_as(i64), None, _d(rho))
+    if nnz < 0:
+        raise ValueError(f"vh_rows failed ({nnz})")
+    idx = np.zeros(max(nnz, 1), np.int32)
+    L.ora_vh_rows(dim, kernel, precision, x.shape[0], _d(x), _d(y), _d(z), _d(h), _d(m),
+                  rows.ctypes.data_as(i64), nr, off.ctypes.data_as(i64),
+                  idx.ctypes.data_as(C.POINTER(C.c_int32)), _d(rho))
+    return off, idx[:nnz], rho

@@ -1013,6 +1013,52 @@ int64_t ora_vh_neighbors(int32_t dim, int32_t kernel, int32_t precision, int64_t
     return offsets[n];
 }
 
+/* The same relation and density for selected particles only (rows[0..nrows)): their
+ * neighbour counts, their neighbours (ascending ids, CSR over the selection) and their
+ * densities, every pair of a selected particle examined. For particle sets too large for
+ * the all-pairs lists. */
+int64_t ora_vh_rows(int32_t dim, int32_t kernel, int32_t precision, int64_t n, const double* x,
+                    const double* y, const double* z, const double* h, const double* m,
+                    const int64_t* rows, int64_t nrows, int64_t* offsets, int32_t* idx,
+                    double* rho) {
+    if ((dim != 2 && dim != 3) || n < 0 || nrows < 0 || (kernel < 0 || kernel > 2)) return -1;
+    const double k = support_factor(kernel);
+    const double* xs[3] = {x, y, z};
+    std::vector<std::vector<int32_t>> lists((size_t)nrows);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t r = 0; r < nrows; ++r) {
+        const int64_t i = rows[r];
+        double xi[3] = {0, 0, 0};
+        for (int d = 0; d < dim; ++d) xi[d] = xs[d][i];
+        double W, dW;
+        kernel_eval<double>(kernel, dim, h[i], 0.0, &W, &dW);
+        double s = m[i] * W;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double xj[3] = {0, 0, 0};
+            for (int d = 0; d < dim; ++d) xj[d] = xs[d][j];
+            const bool in = precision == PREC_FP32 ? vh_within<float>(dim, k, xi, xj, h[i], h[j])
+                                                   : vh_within<double>(dim, k, xi, xj, h[i], h[j]);
+            if (!in) continue;
+            lists[(size_t)r].push_back((int32_t)j);
+            double r2 = 0.0;
+            for (int d = 0; d < dim; ++d) {
+                const double dx = xi[d] - xj[d];
+                r2 = r2 + dx * dx;
+            }
+            kernel_eval<double>(kernel, dim, 0.5 * (h[i] + h[j]), std::sqrt(r2), &W, &dW);
+            s += m[j] * W;
+        }
+        if (rho) rho[r] = s;
+    }
+    offsets[0] = 0;
+    for (int64_t r = 0; r < nrows; ++r) offsets[r + 1] = offsets[r] + (int64_t)lists[(size_t)r].size();
+    if (idx)
+        for (int64_t r = 0; r < nrows; ++r)
+            std::copy(lists[(size_t)r].begin(), lists[(size_t)r].end(), idx + offsets[r]);
+    return offsets[nrows];
+}
+
 /* Summation density with variable smoothing length (Eq. 2 with the pair smoothing length
  * h_ij = (h_i + h_j) / 2, the symmetrised kernel of variable-h SPH, reading C-VH):
  *   rho_i = m_i W(0, h_i) + sum_{j in N(i)} m_j W(|x_i - x_j|, h_ij)

@@ -68,6 +68,14 @@ EXPORTS = ("sph_create", "sph_destroy", "sph_last_error", "sph_count", "sph_grid
            "sph_save_state", "sph_load_state", "sph_create_batch", "sph_step_batch",
            "sph_step_batch_async",
            "sph_batch_diagnostics")
+VH_EXPORTS = ("sph_vh_create", "sph_vh_set", "sph_vh_search", "sph_vh_neighbors",
+              "sph_vh_density", "sph_vh_stats", "sph_vh_tree", "sph_vh_set_timing",
+              "sph_vh_phase_times", "sph_vh_last_error", "sph_vh_destroy")
+
+
+class VhParams(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("kernel", C.c_int32), ("precision", C.c_int32),
+                ("leaf_size", C.c_int32)]
 
 
 def library_path() -> str:
@@ -125,6 +133,23 @@ def load(build_if_missing: bool = True):
     L.sph_load_state.argtypes = [ctxp, P, C.c_size_t]
     for name in EXPORTS:
         if name not in ("sph_destroy", "sph_last_error"):
+            getattr(L, name).restype = C.c_int
+    L.sph_vh_create.argtypes = [C.POINTER(VhParams), C.c_int64, P, ALLOC_FN, FREE_FN, P,
+                                C.POINTER(ctxp)]
+    L.sph_vh_set.argtypes = [ctxp, C.c_int64, d, d, d, d, d]
+    L.sph_vh_search.argtypes = [ctxp]
+    L.sph_vh_neighbors.argtypes = [ctxp, i64, i32, C.c_int64, i64]
+    L.sph_vh_density.argtypes = [ctxp, d]
+    L.sph_vh_stats.argtypes = [ctxp, i64]
+    L.sph_vh_tree.argtypes = [ctxp, C.c_int64, i32, i32, i32, i32, d, d, d, i32]
+    L.sph_vh_set_timing.argtypes = [ctxp, C.c_int32]
+    L.sph_vh_phase_times.argtypes = [ctxp, C.POINTER(C.c_float)]
+    L.sph_vh_last_error.argtypes = [ctxp]
+    L.sph_vh_last_error.restype = C.c_char_p
+    L.sph_vh_destroy.argtypes = [ctxp]
+    L.sph_vh_destroy.restype = None
+    for name in VH_EXPORTS:
+        if name not in ("sph_vh_destroy", "sph_vh_last_error"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -553,3 +578,117 @@ def final_kinetic_energy(sim: "Simulation", scheme: Scheme, dt: float, K: int, u
         import torch as _t
         alpha = _t.tensor(float(scheme.alpha), dtype=_t.float64)
     return _FinalKE.apply(u0, nu, alpha)
+
+
+class VariableHSearch:
+    """Neighbour search and density with a per-particle smoothing length through an octree
+    (a ``sph_vh`` context of ``include/sph_vh.h``)."""
+
+    STATS = ("nodes", "leaves", "depth", "candidates", "pairs", "max_count", "slots",
+             "query_runs")
+
+    def __init__(self, dim: int, kernel: int, precision: int, capacity: int,
+                 leaf_size: int = 16, stream=None, torch_alloc: bool = True):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the search runs on the GPU only")
+        self._L = load()
+        prm = VhParams()
+        prm.dim, prm.kernel, prm.precision, prm.leaf_size = dim, kernel, precision, leaf_size
+        self.dim = dim
+        self._stream_obj = None
+        if stream is None:
+            self._stream_obj = torch.cuda.Stream()
+            handle = self._stream_obj.cuda_stream
+        else:
+            handle = int(getattr(stream, "cuda_stream", stream))
+        self.stream_handle = handle
+        self._alloc = None
+        alloc_fn, free_fn = ALLOC_FN(), FREE_FN()
+        if torch_alloc:
+            self._alloc = _TorchAllocator(torch.cuda.current_device(), handle)
+            alloc_fn, free_fn = self._alloc.alloc, self._alloc.free
+        ctx = C.c_void_p()
+        st = self._L.sph_vh_create(C.byref(prm), int(capacity), C.c_void_p(handle), alloc_fn,
+                                   free_fn, None, C.byref(ctx))
+        if st != 0:
+            raise SphError(st, self._L.sph_vh_last_error(None).decode())
+        self._ctx = ctx
+        self.n = 0
+
+    def _check(self, st: int):
+        if st != 0:
+            raise SphError(st, self._L.sph_vh_last_error(self._ctx).decode())
+
+    def set(self, x, y, z, h, m):
+        x, y, h, m = _f64(x), _f64(y), _f64(h), _f64(m)
+        z = _f64(z) if z is not None else None
+        self._check(self._L.sph_vh_set(self._ctx, x.shape[0], _dptr(x), _dptr(y), _dptr(z),
+                                       _dptr(h), _dptr(m)))
+        self.n = x.shape[0]
+
+    def search(self):
+        self._check(self._L.sph_vh_search(self._ctx))
+
+    def neighbors(self):
+        """CSR (offsets int64[n+1], idx int32[nnz]) in the caller's order, rows unsorted."""
+        off = np.zeros(self.n + 1, np.int64)
+        nnz = C.c_int64()
+        i64 = C.POINTER(C.c_int64)
+        self._check(self._L.sph_vh_neighbors(self._ctx, off.ctypes.data_as(i64), None, 0,
+                                             C.byref(nnz)))
+        idx = np.zeros(max(nnz.value, 1), np.int32)
+        self._check(self._L.sph_vh_neighbors(self._ctx, off.ctypes.data_as(i64),
+                                             idx.ctypes.data_as(C.POINTER(C.c_int32)),
+                                             idx.shape[0], C.byref(nnz)))
+        return off, idx[:nnz.value]
+
+    def density(self) -> np.ndarray:
+        rho = np.zeros(self.n)
+        self._check(self._L.sph_vh_density(self._ctx, _dptr(rho)))
+        return rho
+
+    def stats(self) -> dict:
+        out = np.zeros(8, np.int64)
+        self._check(self._L.sph_vh_stats(self._ctx, out.ctypes.data_as(C.POINTER(C.c_int64))))
+        return dict(zip(self.STATS, (int(v) for v in out)))
+
+    def tree(self) -> dict:
+        nn = self.stats()["nodes"]
+        i32p = C.POINTER(C.c_int32)
+        t = {k: np.zeros(max(nn, 1), np.int32) for k in ("start", "end", "child", "nchild")}
+        lo, hi = np.zeros((max(nn, 1), 3)), np.zeros((max(nn, 1), 3))
+        hmax = np.zeros(max(nn, 1))
+        perm = np.zeros(max(self.n, 1), np.int32)
+        self._check(self._L.sph_vh_tree(self._ctx, nn, *(t[k].ctypes.data_as(i32p)
+                                                          for k in ("start", "end", "child", "nchild")),
+                                        _dptr(lo), _dptr(hi), _dptr(hmax), perm.ctypes.data_as(i32p)))
+        out = {k: v[:nn] for k, v in t.items()}
+        out.update(lo=lo[:nn], hi=hi[:nn], hmax=hmax[:nn], perm=perm[:self.n])
+        return out
+
+    def set_timing(self, on: bool):
+        self._check(self._L.sph_vh_set_timing(self._ctx, 1 if on else 0))
+
+    def phase_times(self) -> dict:
+        """ms of the last timed search: build (root box to node boxes) and query."""
+        out = (C.c_float * 2)()
+        self._check(self._L.sph_vh_phase_times(self._ctx, out))
+        return {"build": float(out[0]), "query": float(out[1])}
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            self._L.sph_vh_destroy(self._ctx)
+            self._ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass

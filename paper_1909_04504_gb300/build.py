@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsph_gb300.so")
-SOURCES = ["capi.cu", "nnps.cu", "pairs.cu", "pairs_f32.cu", "pairs_f64.cu", "fused_f32.cu",
+SOURCES = ["capi.cu", "nnps.cu", "pairs.cu", "pairs_f32.cu", "pairs_f64.cu", "fused_f32.cu", "octree.cu",
            "fused_f64.cu", "adjoint.cu", "batch.cu", "noalloc.cu", "walls.cu", "pec.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -37,6 +37,7 @@ def test_library_exports_every_declared_symbol():
 def test_binding_names_match_header():
     from paper_1909_04504_gb300 import binding
     assert set(binding.EXPORTS) <= declared_symbols()
+    assert set(binding.VH_EXPORTS) <= declared_symbols()
 
 
 def test_no_host_fallback_in_product_path():

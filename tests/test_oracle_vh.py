@@ -168,3 +168,17 @@ def test_density_is_order_independent():
     rp = O.vh_density(3, W.QUINTIC, W.PREC_FP64, pts[p, 0], pts[p, 1], pts[p, 2], h[p], m[p])
     assert np.allclose(rp, rho[p], rtol=1e-13, atol=0)
     assert math.isfinite(float(np.sum(rho)))
+
+
+def test_selected_rows_agree_with_the_full_lists():
+    """The selected-rows form (for sets too large for all-pairs lists) returns the rows and
+    densities of the full form, bit for bit."""
+    s = W.gaussian_blob(2000, dim=3, seed=5)
+    rows = np.array([0, 17, 999, 1998])
+    for prec in (W.PREC_FP64, W.PREC_FP32):
+        off, idx = O.vh_neighbors(3, s.kernel, prec, s.x, s.y, s.z, s.h)
+        rho = O.vh_density(3, s.kernel, prec, s.x, s.y, s.z, s.h, s.m)
+        ro, ri, rr = O.vh_rows(3, s.kernel, prec, s.x, s.y, s.z, s.h, s.m, rows)
+        for q, i in enumerate(rows):
+            assert np.array_equal(ri[ro[q]:ro[q + 1]], idx[off[i]:off[i + 1]])
+        assert np.array_equal(rr, rho[rows])
