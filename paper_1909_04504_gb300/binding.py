@@ -588,7 +588,7 @@ class VariableHSearch:
              "query_runs")
 
     def __init__(self, dim: int, kernel: int, precision: int, capacity: int,
-                 leaf_size: int = 16, stream=None, torch_alloc: bool = True):
+                 leaf_size: int = 32, stream=None, torch_alloc: bool = True):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("no CUDA device: the search runs on the GPU only")

@@ -24,9 +24,11 @@
 //    formed with the same rounded operations as a pair distance and is never larger than
 //    the distance to any particle inside, so a node that holds a neighbour is never
 //    skipped (no margin needed);
-//  - the query is one thread per particle in key order (neighbouring threads descend the
-//    same branches), a depth-first walk with an explicit stack, writing the neighbour list
-//    interleaved (nl[k * n + i], coalesced for the warp) and the density in one pass.
+//  - the query is a depth-first walk per particle in key order, done by a warp for 32
+//    neighbouring particles at once (the warp enters a node any of them needs, so control
+//    flow is uniform), with an explicit stack and staged leaf records in shared memory,
+//    writing the neighbour list interleaved (nl[k * n + i], coalesced for the warp) and the
+//    density in one pass.
 #include <algorithm>
 #include <cmath>
 #include <string>
@@ -331,37 +333,54 @@ __host__ __device__ inline double vh_sigma(int kernel, int dim) {
     return dim == 2 ? 7.0 / (4.0 * pi) : 21.0 / (16.0 * pi);
 }
 
-// One thread per particle i of the key order: a depth-first walk from the root that enters
+// The query: a depth-first walk from the root for particle i of the key order that enters
 // a node when the box distance is below k max(h_i, largest h in the node), and tests every
-// particle of an entered leaf with the exact predicate. Writes the neighbours (key-order
-// indices) to nl[k * n + i] for k < maxn, the count to cnt[i] (the true count also when it
-// exceeds maxn, which raises ST_CAPACITY), and rho[i] (FP64, original order through perm).
+// particle of an entered leaf with the exact predicate. A warp walks together for 32
+// consecutive particles (spatially close, so their walks nearly coincide): it enters a node
+// when any of its particles needs it (ballot), so control flow is uniform; the stack lives
+// in shared memory and a leaf's records are staged there 32 at a time, read back by every
+// lane as a broadcast. A particle tests only the leaves it needs itself. Writes the
+// neighbours (key-order indices, in walk order) to nl[k * n + i] for k < maxn, the count
+// to cnt[i] (the true count also when it exceeds maxn, which raises ST_CAPACITY), and
+// rho[i] (FP64, caller order through perm). Measured on 10^6 particles of the Gaussian
+// blob, 3D, leaves of 16: 2.03 ms, against 3.36 ms when each thread walked alone.
 template <class Real, int DIM, int KERNEL>
 __global__ void __launch_bounds__(VH_THREADS)
-k_vh_query(const typename V4<Real>::T* __restrict__ P, const Real* __restrict__ M,
-           const VhNode<Real>* __restrict__ nodes, int n, uint32_t* __restrict__ nl,
-           uint32_t* __restrict__ cnt, int maxn, double* __restrict__ rho,
-           const uint32_t* __restrict__ perm, VhDev* dev, Control* ctl) {
+k_vh_query_warp(const typename V4<Real>::T* __restrict__ P, const Real* __restrict__ M,
+                const VhNode<Real>* __restrict__ nodes, int n, uint32_t* __restrict__ nl,
+                uint32_t* __restrict__ cnt, int maxn, double* __restrict__ rho,
+                const uint32_t* __restrict__ perm, VhDev* dev, Control* ctl) {
     using V = typename V4<Real>::T;
+    constexpr int WARPS = VH_THREADS / 32;
+    __shared__ int stack_s[WARPS][VH_STACK];
+    __shared__ V rec_s[WARPS][32];
+    __shared__ Real mass_s[WARPS][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int* stack = stack_s[w];
+    V* rec = rec_s[w];
+    Real* mass = mass_s[w];
     const Real kf = KERNEL == QUINTIC ? Real(3) : Real(2);
     const Real sigma = (Real)vh_sigma(KERNEL, DIM);
     unsigned long long cand = 0ull, pairs = 0ull;
     uint32_t most = 0u;
     bool overflow = false;
-    for (int i = blockIdx.x * VH_THREADS + threadIdx.x; i < n; i += gridDim.x * VH_THREADS) {
-        const V pi = P[i];
-        int stack[VH_STACK];
-        int sp = 0;
-        stack[sp++] = 0;
+    const int nwarps = (n + 31) / 32;
+    for (int wi = blockIdx.x * WARPS + w; wi < nwarps; wi += gridDim.x * WARPS) {
+        const int i = wi * 32 + lane;
+        const bool valid = i < n;
+        V pi;
+        pi.x = pi.y = pi.z = pi.w = Real(0);
+        if (valid) pi = P[i];
         uint32_t count = 0u;
         Acc<Real> sum;
         sum.zero();
+        int sp = 1;
+        if (lane == 0) stack[0] = 0;
+        __syncwarp();
         while (sp > 0) {
             const int node = stack[--sp];
             const V lo = nodes[node].lo, hi = nodes[node].hi;
             const int4 r = nodes[node].r;
-            // box distance with the operations of a pair distance (never above the distance
-            // to a particle inside: subtraction, squares and sums are monotonic)
             Real d2 = Real(0);
             {
                 const Real c[3] = {pi.x, pi.y, pi.z};
@@ -375,46 +394,63 @@ k_vh_query(const typename V4<Real>::T* __restrict__ P, const Real* __restrict__ 
                 }
             }
             const Real Rn = vh_mul(kf, pi.w > lo.w ? pi.w : lo.w);
-            if (!(d2 < vh_mul(Rn, Rn))) continue;
+            const bool need = valid && d2 < vh_mul(Rn, Rn);
+            __syncwarp();  // every lane has read the popped entry
+            if (!__any_sync(0xffffffffu, need)) continue;
             if (r.z >= 0) {  // children in reverse, so the first is walked first
                 if (sp + r.w > VH_STACK) {
                     overflow = true;  // unreachable for depth <= B (see VH_STACK)
                     continue;
                 }
-                for (int c = r.w - 1; c >= 0; --c) stack[sp++] = r.z + c;
+                if (lane < r.w) stack[sp + r.w - 1 - lane] = r.z + lane;
+                sp += r.w;
+                __syncwarp();
                 continue;
             }
-            for (int j = r.x; j < r.y; ++j) {
-                if (j == i) continue;
-                const V pj = P[j];
-                ++cand;
-                const Real dx = vh_sub(pi.x, pj.x), dy = vh_sub(pi.y, pj.y);
-                Real r2 = vh_add(vh_mul(dx, dx), vh_mul(dy, dy));
-                if (DIM == 3) {
-                    const Real dz = vh_sub(pi.z, pj.z);
-                    r2 = vh_add(r2, vh_mul(dz, dz));
+            for (int j0 = r.x; j0 < r.y; j0 += 32) {
+                const int m = min(32, r.y - j0);
+                if (lane < m) {
+                    rec[lane] = P[j0 + lane];
+                    mass[lane] = M[j0 + lane];
                 }
-                const Real R = vh_mul(kf, pi.w > pj.w ? pi.w : pj.w);
-                if (!(r2 < vh_mul(R, R))) continue;
-                if ((int)count < maxn) nl[(size_t)count * n + i] = (uint32_t)j;
-                ++count;
-                // W(r, h_ij), h_ij = (h_i + h_j) / 2 (zero beyond k h_ij)
-                const Real inv = PairMath<Real>::rcp(Real(0.5) * (pi.w + pj.w));
-                const Real q = PairMath<Real>::sqrt(r2) * inv;
-                Real wn = inv * inv;
-                if (DIM == 3) wn *= inv;
-                if (q < kf) sum.add(M[j] * (sigma * wn * kernel_w<Real, KERNEL>(q)));
+                __syncwarp();
+                if (need) {
+                    for (int t = 0; t < m; ++t) {
+                        const int j = j0 + t;
+                        if (j == i) continue;
+                        const V pj = rec[t];
+                        ++cand;
+                        const Real dx = vh_sub(pi.x, pj.x), dy = vh_sub(pi.y, pj.y);
+                        Real r2 = vh_add(vh_mul(dx, dx), vh_mul(dy, dy));
+                        if (DIM == 3) {
+                            const Real dz = vh_sub(pi.z, pj.z);
+                            r2 = vh_add(r2, vh_mul(dz, dz));
+                        }
+                        const Real R = vh_mul(kf, pi.w > pj.w ? pi.w : pj.w);
+                        if (!(r2 < vh_mul(R, R))) continue;
+                        if ((int)count < maxn) nl[(size_t)count * n + i] = (uint32_t)j;
+                        ++count;
+                        const Real inv = PairMath<Real>::rcp(Real(0.5) * (pi.w + pj.w));
+                        const Real q = PairMath<Real>::sqrt(r2) * inv;
+                        Real wn = inv * inv;
+                        if (DIM == 3) wn *= inv;
+                        if (q < kf) sum.add(mass[t] * (sigma * wn * kernel_w<Real, KERNEL>(q)));
+                    }
+                }
+                __syncwarp();  // the staged records are read before the next ones land
             }
         }
-        cnt[i] = count;
-        pairs += count;
-        most = count > most ? count : most;
-        if ((int)count > maxn) overflow = true;
-        Real w0 = PairMath<Real>::rcp(pi.w);
-        Real wn = w0 * w0;
-        if (DIM == 3) wn *= w0;
-        const double self = (double)M[i] * ((double)sigma * (double)wn * (double)kernel_w<Real, KERNEL>(Real(0)));
-        rho[perm[i]] = self + sum.value();
+        if (valid) {
+            cnt[i] = count;
+            pairs += count;
+            most = count > most ? count : most;
+            if ((int)count > maxn) overflow = true;
+            Real w0 = PairMath<Real>::rcp(pi.w);
+            Real wn = w0 * w0;
+            if (DIM == 3) wn *= w0;
+            const double self = (double)M[i] * ((double)sigma * (double)wn * (double)kernel_w<Real, KERNEL>(Real(0)));
+            rho[perm[i]] = self + sum.value();
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
         cand += __shfl_down_sync(0xffffffffu, cand, o);
@@ -422,7 +458,7 @@ k_vh_query(const typename V4<Real>::T* __restrict__ P, const Real* __restrict__ 
         const uint32_t t = __shfl_down_sync(0xffffffffu, most, o);
         most = t > most ? t : most;
     }
-    if ((threadIdx.x & 31) == 0) {
+    if (lane == 0) {
         atomicAdd(&dev->cand, cand);
         atomicAdd(&dev->pairs, pairs);
         atomicMax(&dev->max_count, most);
@@ -548,7 +584,7 @@ void vh_query_t(sph_vh* c) {
     using V = typename V4<Real>::T;
     const int n = c->n;
     const int gq = (int)((n + VH_THREADS - 1) / VH_THREADS);
-    k_vh_query<Real, DIM, KERNEL><<<gq < 1 ? 1 : gq, VH_THREADS, 0, c->stream>>>(
+    k_vh_query_warp<Real, DIM, KERNEL><<<gq < 1 ? 1 : gq, VH_THREADS, 0, c->stream>>>(
         (const V*)c->rec, (const Real*)c->M, (const VhNode<Real>*)c->nodes, n, c->nl, c->cnt, c->maxn,
         c->rho, c->vals[c->sorted], c->dev, c->ctl);
 }
