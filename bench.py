@@ -231,7 +231,8 @@ def stream_bytes(wl, ncells: int) -> dict:
 
 # ------------------------------------------------------------ ncu traffic
 PAIR_KERNEL_SOURCES = ("sph_device.cuh", "sph_launch.h", "step_impl.cuh", "reduce_impl.cuh",
-                       "pairs_impl.cuh", "pairs_f32.cu", "pairs_f64.cu")
+                       "pairs_impl.cuh", "pair_units.h", "pairs.cu") + tuple(
+                           f"pairs_{p}_t{t}.cu" for p in ("f32", "f64") for t in (1, 2, 4, 8))
 
 
 def source_hash() -> str:

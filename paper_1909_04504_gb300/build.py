@@ -17,8 +17,13 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsph_gb300.so")
-SOURCES = ["capi.cu", "nnps.cu", "pairs.cu", "pairs_f32.cu", "pairs_f64.cu", "fused_f32.cu", "octree.cu",
-           "fused_f64.cu", "adjoint.cu", "batch.cu", "noalloc.cu", "walls.cu", "pec.cu"]
+# the pair passes and the persistent step: one translation unit per pair-loop precision and
+# tile shape, the longest compiles first
+UNITS = [f"{k}_{p}_t{t}.cu" for k in ("fused", "pairs") for p in ("f32", "f64") for t in (1, 2, 4, 8)]
+# the per-phase kernels whose bodies the persistent step shares
+SAME_ROUNDING = ["nnps.cu", "batch.cu", "walls.cu"]
+SOURCES = UNITS + ["capi.cu", "nnps.cu", "pairs.cu", "fused.cu", "octree.cu", "adjoint.cu", "batch.cu",
+                   "noalloc.cu", "walls.cu", "pec.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -55,7 +60,12 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
 
     def compile_one(src: str) -> str:
         obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
-        cmd = [cc] + flags + ["-c", os.path.join(CSRC, src), "-o", obj]
+        # the pair passes come in a single-problem and a batch instantiation, and the
+        # persistent step repeats the bodies of the per-phase kernels: all of them must round
+        # alike, so no multiply-add is fused unless the source asks for it (fma_rn) and no
+        # two instantiations can differ in which products they fuse
+        extra = ["-fmad=false"] if src in UNITS + SAME_ROUNDING else []
+        cmd = [cc] + flags + extra + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if verbose or ptxas_verbose or r.returncode:
             sys.stderr.write(r.stdout + r.stderr)
@@ -72,6 +82,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
         sys.stderr.write(r.stdout + r.stderr)
         raise RuntimeError("nvcc link failed")
     os.replace(tmp, LIB)
+    for o in objs:  # the library holds everything; the objects only take space
+        os.remove(o)
     return LIB
 
 

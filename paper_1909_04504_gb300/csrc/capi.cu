@@ -411,6 +411,7 @@ StepLaunch step_launch(sph_ctx* c, int kick) {
     L.grid_m = c->grid_m;
     L.finalize = c->ninst == 0;
     L.tab = c->d_tab;
+    L.tab_host = (c->ninst == 0 && !c->tab_host.empty()) ? (const void*)c->tab_host.data() : nullptr;
     L.id_bounds = c->d_id_bounds;
     L.cell_bounds = c->d_cell_bounds;
     L.idt = c->ninst ? c->idt : &c->ctl->dt;
@@ -689,6 +690,8 @@ sph_status upload_table(sph_ctx* c, const sph_scheme* schemes, const double* dts
     CK(cudaMemcpyAsync(c->d_tab, bytes.data(), bytes.size(), cudaMemcpyHostToDevice, c->stream));
     CK(cudaStreamSynchronize(c->stream));
     c->tab_host.swap(bytes);
+    // the pair passes of a single problem take the entry by value: captured steps hold it
+    if (c->ninst == 0) drop_graphs(c);
     return SPH_OK;
 }
 

@@ -16,6 +16,7 @@
 #pragma once
 
 #include "pairs_impl.cuh"
+#include "fused_units.h"
 #include "batch_impl.cuh"
 #include "sort_impl.cuh"
 #include "step_impl.cuh"
@@ -252,49 +253,32 @@ int fused_bps_t() {
     return b;
 }
 
-// One precision's dispatch over (dim, kernel, lanes per destination).
-template <class Real>
-struct FusedDispatch {
-    template <int DIM, int KERNEL>
-    static cudaError_t launch_dk(const FusedLaunch& F, int T, int grid, cudaStream_t st) {
-        switch (T) {
-            case 1: return launch_fused_t<Real, DIM, KERNEL, 1>(F, grid, st);
-            case 2: return launch_fused_t<Real, DIM, KERNEL, 2>(F, grid, st);
-            case 4: return launch_fused_t<Real, DIM, KERNEL, 4>(F, grid, st);
-            default: return launch_fused_t<Real, DIM, KERNEL, 8>(F, grid, st);
-        }
+// Launch and blocks per SM of the persistent kernel for one precision and tile shape,
+// dispatched on (dim, kernel); each (precision, shape) is its own translation unit.
+template <class Real, int T>
+cudaError_t fused_launch(const FusedLaunch& F, int grid, cudaStream_t st) {
+    const int sel = (F.L.dim == 3 ? 3 : 0) + F.L.kernel;
+    switch (sel) {
+        case 0: return launch_fused_t<Real, 2, QUINTIC, T>(F, grid, st);
+        case 1: return launch_fused_t<Real, 2, WENDLAND_C2, T>(F, grid, st);
+        case 2: return launch_fused_t<Real, 2, CUBIC_SPLINE, T>(F, grid, st);
+        case 3: return launch_fused_t<Real, 3, QUINTIC, T>(F, grid, st);
+        case 4: return launch_fused_t<Real, 3, WENDLAND_C2, T>(F, grid, st);
+        default: return launch_fused_t<Real, 3, CUBIC_SPLINE, T>(F, grid, st);
     }
-    template <int DIM, int KERNEL>
-    static int bps_dk(int T) {
-        switch (T) {
-            case 1: return fused_bps_t<Real, DIM, KERNEL, 1>();
-            case 2: return fused_bps_t<Real, DIM, KERNEL, 2>();
-            case 4: return fused_bps_t<Real, DIM, KERNEL, 4>();
-            default: return fused_bps_t<Real, DIM, KERNEL, 8>();
-        }
+}
+
+template <class Real, int T>
+int fused_bps(int dim, int kernel) {
+    const int sel = (dim == 3 ? 3 : 0) + kernel;
+    switch (sel) {
+        case 0: return fused_bps_t<Real, 2, QUINTIC, T>();
+        case 1: return fused_bps_t<Real, 2, WENDLAND_C2, T>();
+        case 2: return fused_bps_t<Real, 2, CUBIC_SPLINE, T>();
+        case 3: return fused_bps_t<Real, 3, QUINTIC, T>();
+        case 4: return fused_bps_t<Real, 3, WENDLAND_C2, T>();
+        default: return fused_bps_t<Real, 3, CUBIC_SPLINE, T>();
     }
-    static cudaError_t launch(const FusedLaunch& F, int T, int grid, cudaStream_t st) {
-        const int sel = (F.L.dim == 3 ? 3 : 0) + F.L.kernel;
-        switch (sel) {
-            case 0: return launch_dk<2, QUINTIC>(F, T, grid, st);
-            case 1: return launch_dk<2, WENDLAND_C2>(F, T, grid, st);
-            case 2: return launch_dk<2, CUBIC_SPLINE>(F, T, grid, st);
-            case 3: return launch_dk<3, QUINTIC>(F, T, grid, st);
-            case 4: return launch_dk<3, WENDLAND_C2>(F, T, grid, st);
-            default: return launch_dk<3, CUBIC_SPLINE>(F, T, grid, st);
-        }
-    }
-    static int bps(int dim, int kernel, int T) {
-        const int sel = (dim == 3 ? 3 : 0) + kernel;
-        switch (sel) {
-            case 0: return bps_dk<2, QUINTIC>(T);
-            case 1: return bps_dk<2, WENDLAND_C2>(T);
-            case 2: return bps_dk<2, CUBIC_SPLINE>(T);
-            case 3: return bps_dk<3, QUINTIC>(T);
-            case 4: return bps_dk<3, WENDLAND_C2>(T);
-            default: return bps_dk<3, CUBIC_SPLINE>(T);
-        }
-    }
-};
+}
 
 }  // namespace sph

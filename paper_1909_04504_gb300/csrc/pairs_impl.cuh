@@ -25,6 +25,7 @@
 #include "step_impl.cuh"
 #include "stencil.cuh"
 #include "reduce_impl.cuh"
+#include "pair_units.h"
 
 namespace sph {
 
@@ -38,13 +39,16 @@ constexpr int PAIR_THREADS = 128;
 // (s = +L where the run wraps below the box, -L above; valid when G.run_shift). `e` holds
 // the destination's distances to the lower faces of its own cell and `c` the cell sizes;
 // `reach2` is the squared support radius widened by a margin far above the FP32 rounding of
-// these distances, so no cell that holds a neighbour is dropped. Returns, in ncand, the
-// candidates of the full stencil (the count the interaction metric reports).
+// these distances, so no cell that holds a neighbour is dropped. The run of the
+// destination's own row is passed as the two runs around the destination's own index
+// `self`, so no candidate test has to exclude it. Returns, in ncand, the candidates of the
+// full stencil (the count the interaction metric reports).
 template <class Real, int DIM, class Body>
 __device__ __forceinline__ void for_each_clipped_run(const Grid& G, const PairConst<Real>& K,
                                                      const uint32_t* __restrict__ off, int cx, int cy,
                                                      int cz, const float* e, const float* c,
-                                                     float reach2, uint32_t& ncand, Body body) {
+                                                     float reach2, uint32_t& ncand, uint32_t self,
+                                                     Body body) {
     constexpr int R = Stencil<DIM>::R, RZ = Stencil<DIM>::RZ;
     const int nx = G.nc[0];
 #pragma unroll 1
@@ -106,7 +110,14 @@ __device__ __forceinline__ void for_each_clipped_run(const Grid& G, const PairCo
             t0 = max(t0, xa);
             t1 = min(t1, xb);
             if (t0 > t1) continue;
-            body(t0 == xa ? fb : off[rowb + t0], t1 == xb ? fe : off[rowb + t1 + 1], Real(0), sy, sz);
+            const uint32_t jb = t0 == xa ? fb : off[rowb + t0], je = t1 == xb ? fe : off[rowb + t1 + 1];
+            if (dz == 0 && dy == 0) {
+                // the destination's own cell: its run without the destination itself
+                body(jb, self, Real(0), sy, sz);
+                body(self + 1, je, Real(0), sy, sz);
+            } else {
+                body(jb, je, Real(0), sy, sz);
+            }
         }
     }
 }
@@ -399,11 +410,10 @@ __device__ __forceinline__ void density_list_sum(int i, const Group<T>& g,
         } else {
             const typename V4<Real>::T qj = Q[j];
             const Real Gk = K.gfac * kernel_f<Real, KERNEL>(q);
-            const Real vdotr = (qi.x - qj.x) * dx + (qi.y - qj.y) * dy +
-                               (DIM == 3 ? (qi.z - qj.z) * dz : Real(0));
+            const Real vdotr = dot_rn<Real, DIM>(qi.x - qj.x, qi.y - qj.y, qi.z - qj.z, dx, dy, dz);
             if (edac)  // Q.w holds the pressure p^n: c0^2 u_ij . grad W + (2 nu_e / rho0) p_ij r . grad W / (r^2 + 0.01 h^2)
                 sum.add(fabs(pj.w) * Gk *
-                        (K.c02 * vdotr + K.edac_d * (qi.w - qj.w) * r2 * PairMath<Real>::rcp(r2 + K.av_h2)));
+                        fma_rn(K.c02, vdotr, K.edac_d * (qi.w - qj.w) * r2 * PairMath<Real>::rcp(r2 + K.av_h2)));
             else
                 sum.add(fabs(pj.w) * Gk * vdotr);
         }
@@ -434,11 +444,18 @@ __device__ __forceinline__ void density_scan_sum(int i, const Group<T>& g, uint3
     uint32_t k = 0, npairs = 0, ncand = 0;
     const unsigned below = (1u << g.t) - 1u;
     // candidates of one run: SHIFT adds the run's minimum-image shift (exact: adding 0
-    // changes nothing but the sign of a zero), MINIMG applies the per-pair minimum image
+    // changes nothing but the sign of a zero), MINIMG applies the per-pair minimum image,
+    // SELF tests j != i (the clipped walk leaves i out of its runs instead); MODE 0 lists
+    // every neighbour and counts the interacting ones (summation density), 1 lists
+    // neighbours of a warp of fluid destinations (all interact), 2 lists the interacting
+    // neighbours (a wall destination takes fluid sources only). In modes 1 and 2 every
+    // listed pair interacts, so the interaction count is the list count.
     auto scan = [&](uint32_t jb, uint32_t je, Real sx, Real sy, Real sz, auto shift_tag,
-                    auto minimg_tag) {
+                    auto minimg_tag, auto self_tag, auto mode_tag) {
         constexpr bool SHIFT = decltype(shift_tag)::value;
         constexpr bool MINIMG = decltype(minimg_tag)::value;
+        constexpr bool SELF = decltype(self_tag)::value;
+        constexpr int MODE = decltype(mode_tag)::value;
 #pragma unroll 2
         for (uint32_t c = jb; c < je; c += T) {
             const uint32_t j = c + g.t;
@@ -460,11 +477,17 @@ __device__ __forceinline__ void density_scan_sum(int i, const Group<T>& g, uint3
                     if (DIM == 3) dz = rn_add(dz, sz);
                 }
                 const Real r2 = dist2<Real, DIM>(dx, dy, dz);
-                const bool hit = (r2 < K.kh2) & ((int)j != i);
-                inter = hit & (fluid_i | (pj.w > Real(0)));
-                listed = summation ? hit : inter;
+                const bool hit = SELF ? ((r2 < K.kh2) & ((int)j != i)) : (r2 < K.kh2);
+                if (MODE == 0) {
+                    listed = hit;
+                    inter = hit & (fluid_i | (pj.w > Real(0)));
+                } else if (MODE == 1) {
+                    listed = hit;
+                } else {
+                    listed = hit & (fluid_i | (pj.w > Real(0)));
+                }
             }
-            npairs += inter ? 1u : 0u;
+            if (MODE == 0) npairs += inter ? 1u : 0u;
             if (T == 1) {
                 if (listed & (k < (uint32_t)maxn)) nl[(size_t)k * n + i] = j;
                 k += listed ? 1u : 0u;
@@ -478,6 +501,20 @@ __device__ __forceinline__ void density_scan_sum(int i, const Group<T>& g, uint3
     };
     using yes = std::true_type;
     using no = std::false_type;
+    using M0 = std::integral_constant<int, 0>;
+    using M1 = std::integral_constant<int, 1>;
+    using M2 = std::integral_constant<int, 2>;
+    const bool all_fluid = __all_sync(__activemask(), fluid_i) != 0;
+    const int mode = summation ? 0 : (all_fluid ? 1 : 2);
+    // mode 1 only on the common path (unshifted runs of the clipped walk): elsewhere mode 2
+    // lists the same pairs
+    auto scan_mode = [&](uint32_t jb, uint32_t je, Real sx, Real sy, Real sz, auto shift_tag,
+                         auto minimg_tag, auto self_tag) {
+        constexpr bool COMMON = !decltype(shift_tag)::value && !decltype(minimg_tag)::value;
+        if (mode == 0) scan(jb, je, sx, sy, sz, shift_tag, minimg_tag, self_tag, M0());
+        else if (COMMON && mode == 1) scan(jb, je, sx, sy, sz, shift_tag, minimg_tag, self_tag, M1());
+        else scan(jb, je, sx, sy, sz, shift_tag, minimg_tag, self_tag, M2());
+    };
     uint32_t nfull = 0;  // candidates of the full stencil, self included
     if (G.run_shift) {
         // distances to the lower faces of the own cell (FP64, then FP32 with a margin)
@@ -489,17 +526,18 @@ __device__ __forceinline__ void density_scan_sum(int i, const Group<T>& g, uint3
             cs[d] = (float)G.cs[d];
         }
         const float reach2 = (float)K.kh2 * 1.002f;
-        for_each_clipped_run<Real, DIM>(G, K, off, cx, cy, cz, e, cs, reach2, nfull,
+        for_each_clipped_run<Real, DIM>(G, K, off, cx, cy, cz, e, cs, reach2, nfull, (uint32_t)i,
                                         [&](uint32_t jb, uint32_t je, Real sx, Real sy, Real sz) {
-            if (sx == Real(0) && sy == Real(0) && sz == Real(0)) scan(jb, je, sx, sy, sz, no(), no());
-            else scan(jb, je, sx, sy, sz, yes(), no());
+            if (sx == Real(0) && sy == Real(0) && sz == Real(0)) scan_mode(jb, je, sx, sy, sz, no(), no(), no());
+            else scan_mode(jb, je, sx, sy, sz, yes(), no(), no());
         });
     } else {
         for_each_run<DIM>(G, off, cx, cy, cz, [&](uint32_t jb, uint32_t je) {
             nfull += je - jb;
-            scan(jb, je, Real(0), Real(0), Real(0), no(), yes());
+            scan_mode(jb, je, Real(0), Real(0), Real(0), no(), yes(), yes());
         });
     }
+    if (mode != 0) npairs = g.t == 0 ? k : 0u;  // every listed pair interacts
     if (g.t == 0) ncand = nfull - 1u;  // the destination itself is in its own cell
     if (k > (uint32_t)maxn) {
         dc.overflow = 1;
@@ -532,7 +570,7 @@ __device__ __forceinline__ void density_finish(int i, double value, Real mi,
         // the EDAC pressure advanced like the continuity density; the density stays rho0,
         // and Q.w keeps p^n, which the other destinations of this pass read
         double p = S.p[i];
-        if (kick) p += dt * value;
+        if (kick) p = fma_rn(dt, value, p);
         S.p[i] = p;
         S.arho[i] = value;
         R[i] = (Real)(p * C.inv_rho0 * C.inv_rho0);
@@ -545,7 +583,7 @@ __device__ __forceinline__ void density_finish(int i, double value, Real mi,
     } else {
         arho = value;
         rho = S.rho[i];
-        if (kick) rho += dt * arho;
+        if (kick) rho = fma_rn(dt, arho, rho);
     }
     S.rho[i] = rho;
     S.arho[i] = arho;
@@ -563,7 +601,7 @@ struct DensitySmem {
 // Density pass over destinations [tile * GD, (tile + 1) * GD) for tile = block,
 // block + nblocks, ... (GD = NTH / T); each destination finds its instance's constants in
 // the table (one entry for a single problem). pcount (batches): per-particle counts.
-template <class Real, int DIM, int KERNEL, int T, int NTH>
+template <class Real, int DIM, int KERNEL, int T, int NTH, bool SINGLE = false>
 __device__ __forceinline__ void density_tiles(int block, int nblocks,
                                               const typename V4<Real>::T* __restrict__ P,
                                               typename V4<Real>::T* __restrict__ Q,
@@ -576,7 +614,8 @@ __device__ __forceinline__ void density_tiles(int block, int nblocks,
                                               int kick, uint32_t* __restrict__ nl,
                                               uint32_t* __restrict__ cnt, int maxn,
                                               uint32_t* __restrict__ pcount, DensityCounts& dc,
-                                              DensitySmem<Real, T == 1 ? 1 : NTH / T>& sm) {
+                                              DensitySmem<Real, T == 1 ? 1 : NTH / T>& sm,
+                                              const Inst<Real>* I0 = nullptr) {
     constexpr int GD = NTH / T;
     const Group<T> g;
     const int grp = threadIdx.x / T;
@@ -584,8 +623,8 @@ __device__ __forceinline__ void density_tiles(int block, int nblocks,
         const int i = tile * GD + grp;
         if (i < n) {
             const uint32_t key = skeys[i];
-            const int inst = find_instance(cell_bounds, ninst, key);
-            const Inst<Real>& I = tab[inst];
+            const int inst = SINGLE ? 0 : find_instance(cell_bounds, ninst, key);
+            const Inst<Real>& I = SINGLE ? *I0 : tab[inst];
             Acc<Real> sum;
             density_scan_sum<Real, DIM, KERNEL, T>(i, g, key - I.cell_base, P, Q, E, off + I.cell_base,
                                                    n, I.G, I.K, nl, cnt, maxn, dc,
@@ -601,8 +640,8 @@ __device__ __forceinline__ void density_tiles(int block, int nblocks,
             __syncthreads();
             const int e = tile * GD + threadIdx.x;
             if (threadIdx.x < GD && e < n) {
-                const int inst = find_instance(cell_bounds, ninst, skeys[e]);
-                const Inst<Real>& I = tab[inst];
+                const int inst = SINGLE ? 0 : find_instance(cell_bounds, ninst, skeys[e]);
+                const Inst<Real>& I = SINGLE ? *I0 : tab[inst];
                 Acc<Real> a;
                 a.s = sm.s[threadIdx.x];
                 a.c = sm.c[threadIdx.x];
@@ -615,9 +654,13 @@ __device__ __forceinline__ void density_tiles(int block, int nblocks,
 
 // Density pass kernel. Single problems write block counts to pd; batches per-particle
 // counts to pcount for the per-instance reduction.
-template <class Real, int DIM, int KERNEL, int T>
+// SINGLE: a single problem, whose constants come by value in the parameter bank (I0), so
+// that the pair arithmetic reads them as constant operands instead of holding them in
+// registers; batches read their instance's entry of the table.
+template <class Real, int DIM, int KERNEL, int T, bool SINGLE>
 __global__ void __launch_bounds__(PAIR_THREADS, sizeof(Real) == 4 ? 7 : 6)
-k_density(const typename V4<Real>::T* __restrict__ P, typename V4<Real>::T* __restrict__ Q,
+k_density(const __grid_constant__ Inst<Real> I0,
+          const typename V4<Real>::T* __restrict__ P, typename V4<Real>::T* __restrict__ Q,
           Real* __restrict__ R, const F4* __restrict__ E, const uint32_t* __restrict__ skeys,
           const uint32_t* __restrict__ off,
           int n, const Inst<Real>* __restrict__ tab, const uint32_t* __restrict__ cell_bounds,
@@ -628,9 +671,9 @@ k_density(const typename V4<Real>::T* __restrict__ P, typename V4<Real>::T* __re
     __shared__ unsigned long long cred[PAIR_THREADS / 32][3];
     if (ctl->status) return;
     DensityCounts dc{0ull, 0ull, 0ull, 0};
-    density_tiles<Real, DIM, KERNEL, T, PAIR_THREADS>(blockIdx.x, gridDim.x, P, Q, R, E, skeys, off, n,
-                                                      tab, cell_bounds, ninst, idt, S, kick, nl,
-                                                      cnt, maxn, pcount, dc, sm);
+    density_tiles<Real, DIM, KERNEL, T, PAIR_THREADS, SINGLE>(blockIdx.x, gridDim.x, P, Q, R, E, skeys, off,
+                                                              n, tab, cell_bounds, ninst, idt, S, kick, nl,
+                                                              cnt, maxn, pcount, dc, sm, &I0);
     if (dc.overflow) atomicOr(&ctl->status, ST_CAPACITY);
     if (pd) block_counts<PAIR_THREADS>(dc, pd + (size_t)blockIdx.x * 4, cred);
 }
@@ -685,7 +728,7 @@ __device__ __forceinline__ void momentum_sums(int i, const Group<T>& g,
         // EDAC: the density is rho0 (Q.w holds the pressure)
         const Real inv_rhobar = (flags & F_EDAC) ? K.inv_rho0 : PairMath<Real>::rcp(Real(0.5) * (qi.w + qj.w));
         if (flags & F_AV) {
-            const Real vdotr = vx * dx + vy * dy + (DIM == 3 ? vz * dz : Real(0));
+            const Real vdotr = dot_rn<Real, DIM>(vx, vy, vz, dx, dy, dz);
             if (vdotr < Real(0)) {
                 const Real mu = K.h * vdotr * PairMath<Real>::rcp(r2 + K.av_h2);
                 coef -= K.alpha_c0 * mu * inv_rhobar;
@@ -696,9 +739,9 @@ __device__ __forceinline__ void momentum_sums(int i, const Group<T>& g,
         // 4 nu m_j / (rho_i + rho_j) = 2 nu m_j / rhobar
         if (flags & F_LAMINAR)
             cv = mj * (Real(0.5) * K.nu4) * inv_rhobar * Gk * r2 * PairMath<Real>::rcp(r2 + K.eta_h2);
-        acc[0].add(cg * dx + cv * vx);
-        acc[1].add(cg * dy + cv * vy);
-        if (DIM == 3) acc[2].add(cg * dz + cv * vz);
+        acc[0].add(fma_rn(cg, dx, cv * vx));
+        acc[1].add(fma_rn(cg, dy, cv * vy));
+        if (DIM == 3) acc[2].add(fma_rn(cg, dz, cv * vz));
         if ((flags & F_XSPH) && pj.w > Real(0)) {
             const Real fx = K.xsph * mj * inv_rhobar * (K.wfac * kernel_w<Real, KERNEL>(q));
             acc[3].add(-fx * vx);
@@ -754,18 +797,18 @@ __device__ __forceinline__ void momentum_finish(int i, bool fluid, const double*
         S.a[d][i] = a;
         S.xs[d][i] = xs_in[d];
         if (kick) {
-            u[d] += 0.5 * dt * a;
+            u[d] = fma_rn(0.5 * dt, a, u[d]);
             S.u[d][i] = u[d];
         }
-        u2 += u[d] * u[d];
-        a2 += a * a;
+        u2 = fma_rn(u[d], u[d], u2);
+        a2 = fma_rn(a, a, a2);
         bad |= !isfinite(u[d]) || !isfinite(x[d]);
     }
     bad |= !isfinite(rho) || !isfinite(a2);
-    md.px += m * u[0];
-    md.py += m * u[1];
-    md.pz += m * u[2];
-    md.ke += 0.5 * m * u2;
+    md.px = fma_rn(m, u[0], md.px);
+    md.py = fma_rn(m, u[1], md.py);
+    md.pz = fma_rn(m, u[2], md.pz);
+    md.ke = fma_rn(0.5 * m, u2, md.ke);
     if (bad) md.bad = 1u;
     else {
         md.u2b = u64max(md.u2b, (unsigned long long)__double_as_longlong(u2));
@@ -783,7 +826,7 @@ struct MomSmem {
 
 // Momentum pass over destinations [tile * GM, (tile + 1) * GM) for tile = block,
 // block + nblocks, ... (GM = NTH / T).
-template <class Real, int DIM, int KERNEL, int T, int NTH>
+template <class Real, int DIM, int KERNEL, int T, int NTH, bool SINGLE = false>
 __device__ __forceinline__ void momentum_tiles(int block, int nblocks,
                                                const typename V4<Real>::T* __restrict__ P,
                                                const typename V4<Real>::T* __restrict__ Q,
@@ -794,15 +837,16 @@ __device__ __forceinline__ void momentum_tiles(int block, int nblocks,
                                                const double* __restrict__ idt, const ParticleSet& S,
                                                int kick, const uint32_t* __restrict__ nl,
                                                const uint32_t* __restrict__ cnt, MomDiag& md,
-                                               MomSmem<Real, T == 1 ? 1 : NTH / T>& sm) {
+                                               MomSmem<Real, T == 1 ? 1 : NTH / T>& sm,
+                                               const Inst<Real>* I0 = nullptr) {
     constexpr int GM = NTH / T;
     const Group<T> g;
     const int grp = threadIdx.x / T;
     for (int tile = block; (long long)tile * GM < n; tile += nblocks) {
         const int i = tile * GM + grp;
         if (i < n) {
-            const int inst = find_instance(cell_bounds, ninst, skeys[i]);
-            const Inst<Real>& I = tab[inst];
+            const int inst = SINGLE ? 0 : find_instance(cell_bounds, ninst, skeys[i]);
+            const Inst<Real>& I = SINGLE ? *I0 : tab[inst];
             const typename V4<Real>::T pi = P[i];
             const bool fluid = pi.w > Real(0);
             Acc<Real> acc[6];
@@ -830,7 +874,7 @@ __device__ __forceinline__ void momentum_tiles(int block, int nblocks,
             __syncthreads();
             const int e = tile * GM + threadIdx.x;
             if (threadIdx.x < GM && e < n) {
-                const int inst = find_instance(cell_bounds, ninst, skeys[e]);
+                const int inst = SINGLE ? 0 : find_instance(cell_bounds, ninst, skeys[e]);
                 double a[3], xs[3];
                 for (int d = 0; d < 3; ++d) {
                     Acc<Real> x, y;
@@ -841,8 +885,8 @@ __device__ __forceinline__ void momentum_tiles(int block, int nblocks,
                     a[d] = x.value();
                     xs[d] = y.value();
                 }
-                momentum_finish<DIM>(e, sm.fluid[threadIdx.x] != 0, a, xs, tab[inst].C, S, idt[inst],
-                                     kick, md);
+                momentum_finish<DIM>(e, sm.fluid[threadIdx.x] != 0, a, xs, SINGLE ? I0->C : tab[inst].C, S,
+                                     idt[inst], kick, md);
             }
             __syncthreads();
         }
@@ -852,9 +896,10 @@ __device__ __forceinline__ void momentum_tiles(int block, int nblocks,
 // FP32: 8 blocks of 128 per SM in 2D (64 registers; the gathers of the pair loop are
 // latency-bound and gain more from the extra warps than the few spills cost), 7 in 3D
 // (72 registers: fewer spills of the longer 3D body measured faster); FP64: 5.
-template <class Real, int DIM, int KERNEL, int T>
+template <class Real, int DIM, int KERNEL, int T, bool SINGLE>
 __global__ void __launch_bounds__(PAIR_THREADS, sizeof(Real) == 4 ? (DIM == 3 ? 7 : 8) : 5)
-k_momentum(const typename V4<Real>::T* __restrict__ P, const typename V4<Real>::T* __restrict__ Q,
+k_momentum(const __grid_constant__ Inst<Real> I0,
+           const typename V4<Real>::T* __restrict__ P, const typename V4<Real>::T* __restrict__ Q,
            const Real* __restrict__ R, const F4* __restrict__ E, const uint32_t* __restrict__ skeys,
            int n,
            const Inst<Real>* __restrict__ tab, const uint32_t* __restrict__ cell_bounds, int ninst,
@@ -869,9 +914,9 @@ k_momentum(const typename V4<Real>::T* __restrict__ P, const typename V4<Real>::
     __shared__ bool is_last;
     if (ctl->status) return;
     MomDiag md{0, 0, 0, 0, 0ull, 0ull, 0u};
-    momentum_tiles<Real, DIM, KERNEL, T, PAIR_THREADS>(blockIdx.x, gridDim.x, P, Q, R, E, skeys, n, tab,
-                                                       cell_bounds, ninst, idt, S, kick, nl, cnt, md,
-                                                       sm);
+    momentum_tiles<Real, DIM, KERNEL, T, PAIR_THREADS, SINGLE>(blockIdx.x, gridDim.x, P, Q, R, E, skeys, n,
+                                                               tab, cell_bounds, ninst, idt, S, kick, nl, cnt,
+                                                               md, sm, &I0);
     if (!finalize) return;
     const double dt = idt[0];
     // ---- block partials (epilogue threads: the first ceil(GM / 32) warps)
@@ -889,30 +934,41 @@ k_momentum(const typename V4<Real>::T* __restrict__ P, const typename V4<Real>::
     reduce_partials<PAIR_THREADS>(pm, 8, gridDim.x, pd, 4, density_blocks, out, red, cred);
     if (threadIdx.x == 0) {
         ctl->ticket = 0;
-        finish_single(ctl, history, tab[0].C, dt, kick, out);
+        finish_single(ctl, history, SINGLE ? I0.C : tab[0].C, dt, kick, out);
     }
 }
 
 // ---------------------------------------------------------------- launchers
+// Blocks per SM of each pass (the single-problem form; the batch form has the same bounds).
 template <class Real, int DIM, int KERNEL, int T>
 int density_bps() {
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_density<Real, DIM, KERNEL, T>, PAIR_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_density<Real, DIM, KERNEL, T, true>, PAIR_THREADS, 0);
+    int b2 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_density<Real, DIM, KERNEL, T, false>, PAIR_THREADS, 0);
+    b = b < b2 ? b : b2;
     return b > 0 ? b : 1;
 }
 
 template <class Real, int DIM, int KERNEL, int T>
 int momentum_bps() {
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_momentum<Real, DIM, KERNEL, T>, PAIR_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_momentum<Real, DIM, KERNEL, T, true>, PAIR_THREADS, 0);
+    int b2 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_momentum<Real, DIM, KERNEL, T, false>, PAIR_THREADS, 0);
+    b = b < b2 ? b : b2;
     return b > 0 ? b : 1;
 }
 
+// A single problem (L.tab_host set) passes its constants by value; a batch its table.
 template <class Real, int DIM, int KERNEL, int T>
 void launch_density_t(const StepLaunch& L, cudaStream_t st) {
     using V = typename V4<Real>::T;
-    k_density<Real, DIM, KERNEL, T><<<L.grid_d, PAIR_THREADS, 0, st>>>(
-        (const V*)L.P, (V*)L.Q, (Real*)L.R, (const F4*)L.E, L.skeys, L.off, L.n, (const Inst<Real>*)L.tab,
+    const bool single = L.tab_host != nullptr;
+    const Inst<Real> I0 = single ? *(const Inst<Real>*)L.tab_host : Inst<Real>{};
+    auto k = single ? k_density<Real, DIM, KERNEL, T, true> : k_density<Real, DIM, KERNEL, T, false>;
+    k<<<L.grid_d, PAIR_THREADS, 0, st>>>(
+        I0, (const V*)L.P, (V*)L.Q, (Real*)L.R, (const F4*)L.E, L.skeys, L.off, L.n, (const Inst<Real>*)L.tab,
         L.cell_bounds, L.ninst, L.idt, L.S, L.ctl, L.kick, L.nl, L.cnt, L.maxn,
         L.finalize ? L.pd : nullptr, L.finalize ? nullptr : L.pcount);
 }
@@ -920,10 +976,13 @@ void launch_density_t(const StepLaunch& L, cudaStream_t st) {
 template <class Real, int DIM, int KERNEL, int T>
 void launch_momentum_t(const StepLaunch& L, cudaStream_t st) {
     using V = typename V4<Real>::T;
-    k_momentum<Real, DIM, KERNEL, T><<<L.grid_m, PAIR_THREADS, 0, st>>>(
-        (const V*)L.P, (const V*)L.Q, (const Real*)L.R, (const F4*)L.E, L.skeys, L.n, (const Inst<Real>*)L.tab,
-        L.cell_bounds, L.ninst, L.idt, L.S, L.ctl, L.kick, L.nl, L.cnt, L.pm, L.pd, L.grid_d,
-        L.history, L.finalize);
+    const bool single = L.tab_host != nullptr;
+    const Inst<Real> I0 = single ? *(const Inst<Real>*)L.tab_host : Inst<Real>{};
+    auto k = single ? k_momentum<Real, DIM, KERNEL, T, true> : k_momentum<Real, DIM, KERNEL, T, false>;
+    k<<<L.grid_m, PAIR_THREADS, 0, st>>>(
+        I0, (const V*)L.P, (const V*)L.Q, (const Real*)L.R, (const F4*)L.E, L.skeys, L.n,
+        (const Inst<Real>*)L.tab, L.cell_bounds, L.ninst, L.idt, L.S, L.ctl, L.kick, L.nl, L.cnt, L.pm, L.pd,
+        L.grid_d, L.history, L.finalize);
 }
 
 // One precision's dispatch over (dim, kernel, group size).
@@ -966,5 +1025,18 @@ struct PairDispatch {
         }
     }
 };
+
+template <class Real, int T>
+int pair_bps(int pass, int dim, int kernel) {
+    return PairDispatch<Real>::template bps_t<T>(pass, dim, kernel);
+}
+template <class Real, int T>
+void pair_density(const StepLaunch& L, cudaStream_t st) {
+    PairDispatch<Real>::template density_t<T>(L, st);
+}
+template <class Real, int T>
+void pair_momentum(const StepLaunch& L, cudaStream_t st) {
+    PairDispatch<Real>::template momentum_t<T>(L, st);
+}
 
 }  // namespace sph

@@ -168,6 +168,19 @@ __device__ __forceinline__ int cell_coord_screened(double x, float xf, int to_fl
     return (int)lo_q;
 }
 
+// Fused multiply-add with one rounding, written out where an expression adds two
+// products: left to the compiler, which product is fused could differ between two
+// instantiations of the same arithmetic (the single-problem and the batch kernels), and
+// their results would then differ in the last bit.
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// a . b in DIM dimensions as a chain of fused multiply-adds.
+template <class Real, int DIM>
+__device__ __forceinline__ Real dot_rn(Real ax, Real ay, Real az, Real bx, Real by, Real bz) {
+    return DIM == 3 ? fma_rn(ax, bx, fma_rn(ay, by, az * bz)) : fma_rn(ax, bx, ay * by);
+}
+
 // Square root, reciprocal and quotient of the pair arithmetic: in FP32 the hardware
 // approximations (relative error of a few 2^-23, far inside the FP32 mode's tolerance and
 // with no slow path), in FP64 the correctly rounded operations.
@@ -209,33 +222,33 @@ template <class Real, int KERNEL>
 __device__ __forceinline__ Real kernel_f(Real q) {
     if (KERNEL == QUINTIC) {
         if (sizeof(Real) == 8) {  // FP64: the divide is costly, keep it off the inner branch
-            if (q < Real(1)) return (Real(-50) * q + Real(120)) * q * q - Real(120);
+            if (q < Real(1)) return fma_rn(fma_rn(Real(-50), q, Real(120)) * q, q, Real(-120));
             Real t3 = Real(3) - q;
             Real t3s = t3 * t3;
             Real p = Real(-5) * t3s * t3s;
             Real t2 = q < Real(2) ? Real(2) - q : Real(0);
             Real t2s = t2 * t2;
-            p += Real(30) * t2s * t2s;
+            p = fma_rn(Real(30) * t2s, t2s, p);
             return PairMath<Real>::div(p, q);
         }
         // FP32: both branches evaluated and one selected (neighbours of a warp spread over q)
-        const Real inner = (Real(-50) * q + Real(120)) * q * q - Real(120);
+        const Real inner = fma_rn(fma_rn(Real(-50), q, Real(120)) * q, q, Real(-120));
         Real t3 = Real(3) - q;
         Real t3s = t3 * t3;
         Real p = Real(-5) * t3s * t3s;
         Real t2 = q < Real(2) ? Real(2) - q : Real(0);
         Real t2s = t2 * t2;
-        p += Real(30) * t2s * t2s;
+        p = fma_rn(Real(30) * t2s, t2s, p);
         const Real outer = PairMath<Real>::div(p, q);
         return q < Real(1) ? inner : outer;
     } else if (KERNEL == CUBIC_SPLINE) {
-        const Real inner = Real(9) * q - Real(12);
+        const Real inner = fma_rn(Real(9), q, Real(-12));
         if (sizeof(Real) == 8 && q < Real(1)) return inner;
         const Real t2 = q < Real(2) ? Real(2) - q : Real(0);
         const Real outer = PairMath<Real>::div(Real(-3) * t2 * t2, q);
         return q < Real(1) ? inner : outer;
     } else {
-        Real t = Real(1) - Real(0.5) * q;
+        Real t = fma_rn(Real(-0.5), q, Real(1));
         return Real(-5) * t * t * t;
     }
 }
@@ -250,19 +263,19 @@ __device__ __forceinline__ Real kernel_w(Real q) {
         Real w = t3s * t3s * t3;
         Real t2 = q < Real(2) ? Real(2) - q : Real(0);
         Real t2s = t2 * t2;
-        w -= Real(6) * t2s * t2s * t2;
+        w = fma_rn(-(Real(6) * t2s * t2s), t2, w);
         Real t1 = q < Real(1) ? Real(1) - q : Real(0);
         Real t1s = t1 * t1;
-        w += Real(15) * t1s * t1s * t1;
+        w = fma_rn(Real(15) * t1s * t1s, t1, w);
         return w;
     } else if (KERNEL == CUBIC_SPLINE) {
         const Real t2 = q < Real(2) ? Real(2) - q : Real(0);
         const Real t1 = q < Real(1) ? Real(1) - q : Real(0);
-        return t2 * t2 * t2 - Real(4) * (t1 * t1 * t1);
+        return fma_rn(Real(-4), t1 * t1 * t1, t2 * t2 * t2);
     } else {
-        Real t = Real(1) - Real(0.5) * q;
+        Real t = fma_rn(Real(-0.5), q, Real(1));
         Real t2 = t * t;
-        return t2 * t2 * (Real(2) * q + Real(1));
+        return t2 * t2 * fma_rn(Real(2), q, Real(1));
     }
 }
 
@@ -274,7 +287,7 @@ __device__ __forceinline__ double tait_pressure(double rho, const StepConst& C) 
     const double d = (rho - C.rho0) * C.inv_rho0;
     double e;
     if (C.gamma7) {
-        e = d * (7.0 + d * (21.0 + d * (35.0 + d * (35.0 + d * (21.0 + d * (7.0 + d))))));
+        e = d * fma_rn(d, fma_rn(d, fma_rn(d, fma_rn(d, fma_rn(d, 7.0 + d, 21.0), 35.0), 35.0), 21.0), 7.0);
     } else {
         e = expm1(C.gamma * log1p(d));
     }
@@ -297,7 +310,7 @@ __device__ __forceinline__ float pressure_over_rho2<float>(double rho, const Ste
     const float d = (float)((rho - C.rho0) * C.inv_rho0);
     float e;
     if (C.gamma7) {
-        e = d * (7.f + d * (21.f + d * (35.f + d * (35.f + d * (21.f + d * (7.f + d))))));
+        e = d * fma_rn(d, fma_rn(d, fma_rn(d, fma_rn(d, fma_rn(d, 7.f + d, 21.f), 35.f), 35.f), 21.f), 7.f);
     } else {
         e = expm1f((float)C.gamma * log1pf(d));
     }
@@ -314,9 +327,10 @@ struct Acc {
     __device__ __forceinline__ void zero() { s = Real(0); c = Real(0); }
     __device__ __forceinline__ void add(Real v) {
         if (sizeof(Real) == 4) {
-            Real t = s + v;
-            Real e = (fabs(s) >= fabs(v)) ? ((s - t) + v) : ((v - t) + s);
-            c += e;
+            // each operation rounded on its own (no product of the caller fused into them)
+            const Real t = rn_add(s, v);
+            const Real e = (fabs(s) >= fabs(v)) ? rn_add(rn_sub(s, t), v) : rn_add(rn_sub(v, t), s);
+            c = rn_add(c, e);
             s = t;
         } else {
             s += v;

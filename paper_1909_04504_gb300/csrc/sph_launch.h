@@ -50,6 +50,7 @@ struct StepLaunch {
     int group_d, group_m, grid_d, grid_m;  // lanes per destination and grid of each pass
     int finalize;                 // 1: the momentum pass reduces the diagnostics (single)
     const void* tab;              // Inst<Real>[ninst]
+    const void* tab_host;         // single problem: host copy of its entry (passed by value), else null
     const uint32_t* id_bounds;    // ninst + 1 global-id bounds
     const uint32_t* cell_bounds;  // ninst + 1 global-cell bounds
     double* idt;                  // dt of the next step, per instance

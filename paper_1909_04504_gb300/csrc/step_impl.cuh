@@ -44,8 +44,8 @@ __device__ __forceinline__ uint32_t drift_key_one(const ParticleSet& S, int i, c
 #pragma unroll
         for (int d = 0; d < 3; ++d)
             if (d < dim) {
-                const double uh = u[d] + 0.5 * dt * a[d];
-                double xn = x[d] + dt * (uh + xs[d]);
+                const double uh = fma_rn(0.5 * dt, a[d], u[d]);
+                double xn = fma_rn(dt, uh + xs[d], x[d]);
                 if (G.periodic[d] && !(xn >= G.lo[d] && xn < G.hi[d])) {
                     const double k = floor(__ddiv_rn(__dsub_rn(xn, G.lo[d]), G.L[d]));
                     xn = __dsub_rn(xn, __dmul_rn(k, G.L[d]));
@@ -107,7 +107,7 @@ __device__ __forceinline__ void reorder_one(const ParticleSet& in, const Particl
     if (kick && fluid)
 #pragma unroll
         for (int d = 0; d < 3; ++d)
-            if (d < dim) uk[d] += 0.5 * dt * a[d];
+            if (d < dim) uk[d] = fma_rn(0.5 * dt, a[d], uk[d]);
 #pragma unroll
     for (int d = 0; d < 3; ++d)
         if (d < dim) {
