@@ -396,6 +396,7 @@ __device__ __forceinline__ void density_list_sum(int i, const Group<T>& g,
     auto sum_loop = [&](auto mi_tag) {
     constexpr bool MI = decltype(mi_tag)::value;
     uint32_t j_next = g.t < k ? nl[(size_t)g.t * n + i] : 0u;
+#pragma unroll 2
     for (uint32_t kk = g.t; kk < k; kk += T) {
         const uint32_t j = j_next;
         if (kk + T < k) j_next = nl[(size_t)(kk + T) * n + i];
