@@ -999,7 +999,7 @@ sph_status create_impl(const sph_domain* domains, int ninst, const sph_array_des
     for (int pass = 0; pass < 2; ++pass)
         for (int k = 0; k < 4; ++k) {
             c->bps[pass][k] = pairs_max_blocks_per_sm(domain->precision, pass, domain->dim,
-                                                      domain->kernel, 1 << k);
+                                                      domain->kernel, 1 << k, c->ninst == 0);
             if (c->sms * c->bps[pass][k] > c->grid_cap) c->grid_cap = c->sms * c->bps[pass][k];
         }
     for (int k = 0; k < 4; ++k)

@@ -8,7 +8,7 @@
 namespace sph {
 
 template <class Real, int T>
-int pair_bps(int pass, int dim, int kernel);
+int pair_bps(int pass, int dim, int kernel, int single);
 template <class Real, int T>
 void pair_density(const StepLaunch& L, cudaStream_t st);
 template <class Real, int T>

@@ -9,12 +9,12 @@
 namespace sph {
 
 template <class Real>
-static int pairs_bps_p(int pass, int dim, int kernel, int T) {
+static int pairs_bps_p(int pass, int dim, int kernel, int T, int single) {
     switch (T) {
-        case 1: return pair_bps<Real, 1>(pass, dim, kernel);
-        case 2: return pair_bps<Real, 2>(pass, dim, kernel);
-        case 4: return pair_bps<Real, 4>(pass, dim, kernel);
-        default: return pair_bps<Real, 8>(pass, dim, kernel);
+        case 1: return pair_bps<Real, 1>(pass, dim, kernel, single);
+        case 2: return pair_bps<Real, 2>(pass, dim, kernel, single);
+        case 4: return pair_bps<Real, 4>(pass, dim, kernel, single);
+        default: return pair_bps<Real, 8>(pass, dim, kernel, single);
     }
 }
 
@@ -56,8 +56,9 @@ void launch_pairs(const StepLaunch& L, cudaStream_t st) {
     if (!L.finalize) launch_batch_reduce(L, st);
 }
 
-int pairs_max_blocks_per_sm(int precision, int pass, int dim, int kernel, int T) {
-    return precision ? pairs_bps_p<float>(pass, dim, kernel, T) : pairs_bps_p<double>(pass, dim, kernel, T);
+int pairs_max_blocks_per_sm(int precision, int pass, int dim, int kernel, int T, int single) {
+    return precision ? pairs_bps_p<float>(pass, dim, kernel, T, single)
+                     : pairs_bps_p<double>(pass, dim, kernel, T, single);
 }
 
 }  // namespace sph

@@ -3,7 +3,7 @@
 
 namespace sph {
 
-template int pair_bps<float, 4>(int, int, int);
+template int pair_bps<float, 4>(int, int, int, int);
 template void pair_density<float, 4>(const StepLaunch&, cudaStream_t);
 template void pair_momentum<float, 4>(const StepLaunch&, cudaStream_t);
 

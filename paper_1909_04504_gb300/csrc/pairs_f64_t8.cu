@@ -3,7 +3,7 @@
 
 namespace sph {
 
-template int pair_bps<double, 8>(int, int, int);
+template int pair_bps<double, 8>(int, int, int, int);
 template void pair_density<double, 8>(const StepLaunch&, cudaStream_t);
 template void pair_momentum<double, 8>(const StepLaunch&, cudaStream_t);
 

@@ -940,24 +940,20 @@ k_momentum(const __grid_constant__ Inst<Real> I0,
 }
 
 // ---------------------------------------------------------------- launchers
-// Blocks per SM of each pass (the single-problem form; the batch form has the same bounds).
+// Blocks per SM of each pass, in the single-problem or the batch form.
 template <class Real, int DIM, int KERNEL, int T>
-int density_bps() {
+int density_bps(int single) {
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_density<Real, DIM, KERNEL, T, true>, PAIR_THREADS, 0);
-    int b2 = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_density<Real, DIM, KERNEL, T, false>, PAIR_THREADS, 0);
-    b = b < b2 ? b : b2;
+    if (single) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_density<Real, DIM, KERNEL, T, true>, PAIR_THREADS, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_density<Real, DIM, KERNEL, T, false>, PAIR_THREADS, 0);
     return b > 0 ? b : 1;
 }
 
 template <class Real, int DIM, int KERNEL, int T>
-int momentum_bps() {
+int momentum_bps(int single) {
     int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_momentum<Real, DIM, KERNEL, T, true>, PAIR_THREADS, 0);
-    int b2 = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_momentum<Real, DIM, KERNEL, T, false>, PAIR_THREADS, 0);
-    b = b < b2 ? b : b2;
+    if (single) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_momentum<Real, DIM, KERNEL, T, true>, PAIR_THREADS, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_momentum<Real, DIM, KERNEL, T, false>, PAIR_THREADS, 0);
     return b > 0 ? b : 1;
 }
 
@@ -990,15 +986,15 @@ void launch_momentum_t(const StepLaunch& L, cudaStream_t st) {
 template <class Real>
 struct PairDispatch {
     template <int T>
-    static int bps_t(int pass, int dim, int kernel) {
+    static int bps_t(int pass, int dim, int kernel, int single) {
         const int sel = (dim == 3 ? 3 : 0) + kernel;
         switch (sel) {
-            case 0: return pass ? momentum_bps<Real, 2, QUINTIC, T>() : density_bps<Real, 2, QUINTIC, T>();
-            case 1: return pass ? momentum_bps<Real, 2, WENDLAND_C2, T>() : density_bps<Real, 2, WENDLAND_C2, T>();
-            case 2: return pass ? momentum_bps<Real, 2, CUBIC_SPLINE, T>() : density_bps<Real, 2, CUBIC_SPLINE, T>();
-            case 3: return pass ? momentum_bps<Real, 3, QUINTIC, T>() : density_bps<Real, 3, QUINTIC, T>();
-            case 4: return pass ? momentum_bps<Real, 3, WENDLAND_C2, T>() : density_bps<Real, 3, WENDLAND_C2, T>();
-            default: return pass ? momentum_bps<Real, 3, CUBIC_SPLINE, T>() : density_bps<Real, 3, CUBIC_SPLINE, T>();
+            case 0: return pass ? momentum_bps<Real, 2, QUINTIC, T>(single) : density_bps<Real, 2, QUINTIC, T>(single);
+            case 1: return pass ? momentum_bps<Real, 2, WENDLAND_C2, T>(single) : density_bps<Real, 2, WENDLAND_C2, T>(single);
+            case 2: return pass ? momentum_bps<Real, 2, CUBIC_SPLINE, T>(single) : density_bps<Real, 2, CUBIC_SPLINE, T>(single);
+            case 3: return pass ? momentum_bps<Real, 3, QUINTIC, T>(single) : density_bps<Real, 3, QUINTIC, T>(single);
+            case 4: return pass ? momentum_bps<Real, 3, WENDLAND_C2, T>(single) : density_bps<Real, 3, WENDLAND_C2, T>(single);
+            default: return pass ? momentum_bps<Real, 3, CUBIC_SPLINE, T>(single) : density_bps<Real, 3, CUBIC_SPLINE, T>(single);
         }
     }
     template <int T>
@@ -1028,8 +1024,8 @@ struct PairDispatch {
 };
 
 template <class Real, int T>
-int pair_bps(int pass, int dim, int kernel) {
-    return PairDispatch<Real>::template bps_t<T>(pass, dim, kernel);
+int pair_bps(int pass, int dim, int kernel, int single) {
+    return PairDispatch<Real>::template bps_t<T>(pass, dim, kernel, single);
 }
 template <class Real, int T>
 void pair_density(const StepLaunch& L, cudaStream_t st) {

@@ -114,7 +114,8 @@ int radix_tiles(int n);
 
 // pass 0: density (thread per destination), 1: momentum (T = 1, 2, 4 or 8 lanes per
 // destination)
-int pairs_max_blocks_per_sm(int precision, int pass, int dim, int kernel, int T);
+// single: the single-problem form of the kernels (constants by value), else the batch form
+int pairs_max_blocks_per_sm(int precision, int pass, int dim, int kernel, int T, int single);
 
 // adjoint.cu: adjoint state (FP64, cell order of the current evaluation)
 struct AdjSet {
