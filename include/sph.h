@@ -374,6 +374,16 @@ sph_status sph_history(sph_ctx* ctx, double* out, int32_t max_records, int32_t* 
 sph_status sph_save_state(sph_ctx* ctx, void* buf, size_t* bytes);
 sph_status sph_load_state(sph_ctx* ctx, const void* buf, size_t bytes);
 
+/* As sph_save_state / sph_load_state (the output and restart of Sec. 3.3), but the copies
+ * are only enqueued on the context stream, behind the work already there: the call returns
+ * at once, and the buffer must stay valid (for a load: unchanged; for a save: unread) until
+ * sph_synchronize returns. In a pinned host buffer the copies run on the copy engines while
+ * other contexts compute, so a run that streams states through several contexts overlaps
+ * its transfers with its steps. Errors of the enqueued copies are reported by
+ * sph_synchronize; argument errors as by the synchronous calls. */
+sph_status sph_save_state_async(sph_ctx* ctx, void* buf, size_t* bytes);
+sph_status sph_load_state_async(sph_ctx* ctx, const void* buf, size_t bytes);
+
 /* ---------------------------------------------------------------------------------
  * Allocation-free cell sort. The paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory -- for example code that runs inside a

@@ -65,7 +65,8 @@ EXPORTS = ("sph_create", "sph_destroy", "sph_last_error", "sph_count", "sph_grid
            "sph_kernels_per_step", "sph_set_groups", "sph_set_step_mode", "sph_set_wait_limit",
            "sph_get_tuning",
            "sph_autotune", "sph_backward", "sph_get", "sph_set", "sph_diagnostics", "sph_history",
-           "sph_save_state", "sph_load_state", "sph_create_batch", "sph_step_batch",
+           "sph_save_state", "sph_load_state", "sph_save_state_async", "sph_load_state_async",
+           "sph_create_batch", "sph_step_batch",
            "sph_step_batch_async",
            "sph_batch_diagnostics")
 VH_EXPORTS = ("sph_vh_create", "sph_vh_set", "sph_vh_search", "sph_vh_neighbors",
@@ -131,6 +132,8 @@ def load(build_if_missing: bool = True):
     L.sph_history.argtypes = [ctxp, d, C.c_int32, i32]
     L.sph_save_state.argtypes = [ctxp, P, C.POINTER(C.c_size_t)]
     L.sph_load_state.argtypes = [ctxp, P, C.c_size_t]
+    L.sph_save_state_async.argtypes = [ctxp, P, C.POINTER(C.c_size_t)]
+    L.sph_load_state_async.argtypes = [ctxp, P, C.c_size_t]
     for name in EXPORTS:
         if name not in ("sph_destroy", "sph_last_error"):
             getattr(L, name).restype = C.c_int
@@ -455,6 +458,21 @@ class Simulation:
         size = C.c_size_t(buf.nbytes)
         self._check(self._L.sph_save_state(self._ctx, C.c_void_p(buf.ctypes.data), C.byref(size)))
         return int(size.value)
+
+    def save_state_into_async(self, buf: np.ndarray) -> int:
+        """As save_state_into, but only enqueued on the context stream: buf (pinned, for the
+        copies to overlap other work) holds the state once synchronize() returns."""
+        assert buf.dtype == np.uint8 and buf.flags.c_contiguous
+        size = C.c_size_t(buf.nbytes)
+        self._check(self._L.sph_save_state_async(self._ctx, C.c_void_p(buf.ctypes.data),
+                                                 C.byref(size)))
+        return int(size.value)
+
+    def load_state_async(self, buf: np.ndarray):
+        """As load_state from a contiguous uint8 array, but only enqueued on the context
+        stream: buf must stay unchanged until synchronize() returns."""
+        assert buf.dtype == np.uint8 and buf.flags.c_contiguous
+        self._check(self._L.sph_load_state_async(self._ctx, C.c_void_p(buf.ctypes.data), buf.nbytes))
 
     def load_state(self, blob):
         """Restore a state from bytes or from a contiguous uint8 numpy array (read in place,

@@ -1227,6 +1227,97 @@ sph_status batch_initial_eval(sph_ctx* c) {
     return SPH_OK;
 }
 
+// The control block after a load: zeroed (status, counters, barrier words, stamps), then
+// the saved time, step size and step count.
+__global__ void k_load_control(Control* ctl, double t, double dt, unsigned long long step) {
+    unsigned long long* w = reinterpret_cast<unsigned long long*>(ctl);
+    for (size_t k = threadIdx.x; k < sizeof(Control) / 8; k += blockDim.x) w[k] = 0ull;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ctl->t = t;
+        ctl->dt = dt;
+        ctl->step = step;
+    }
+}
+
+void launch_load_control(Control* ctl, double t, double dt, unsigned long long step, cudaStream_t st) {
+    k_load_control<<<1, 64, 0, st>>>(ctl, t, dt, step);
+}
+
+// The step size of the next steps, set on the stream by value (a copy from host memory that
+// is not pinned could make the host wait for the stream).
+__global__ void k_set_dt(Control* ctl, double dt) { ctl->dt = dt; }
+
+// State to / from a host buffer: the header's fixed part is written on the host, the time,
+// step size and step count come from the control block by three small copies into the
+// header, the fields by one copy each; `async` returns after enqueuing them.
+sph_status save_state_impl(sph_ctx* c, void* buf, size_t* bytes, bool async) {
+    if (!c || !bytes) return fail(c, SPH_ERR_INVALID, "NULL argument");
+    const size_t N = (size_t)c->N;
+    const size_t need = sizeof(StateHeader) + STATE_FIELDS * N * 8 + N * 4;
+    if (!buf) {
+        *bytes = need;
+        return SPH_OK;
+    }
+    if (*bytes < need) {
+        *bytes = need;
+        return fail(c, SPH_ERR_CAPACITY, "state buffer too small");
+    }
+    StateHeader H{};
+    H.magic = STATE_MAGIC;
+    H.version = STATE_VERSION;
+    H.n = c->N;
+    H.dim = c->dom.dim;
+    H.precision = c->dom.precision;
+    H.have_rates = c->have_rates;
+    H.scheme = c->rates_scheme;
+    std::memcpy(buf, &H, sizeof H);
+    StateHeader* hd = (StateHeader*)buf;
+    CK(cudaMemcpyAsync(&hd->t, &c->ctl->t, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&hd->dt, &c->ctl->dt, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(&hd->step, &c->ctl->step, sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                       c->stream));
+    const ParticleSet& S = c->set[c->cur];
+    double* fields[STATE_FIELDS];
+    state_fields(S, fields);
+    char* p = (char*)buf + sizeof(StateHeader);
+    for (int k = 0; k < STATE_FIELDS; ++k)
+        CK(cudaMemcpyAsync(p + (size_t)k * N * 8, fields[k], N * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(p + STATE_FIELDS * N * 8, S.tag, N * 4, cudaMemcpyDeviceToHost, c->stream));
+    if (!async) CK(cudaStreamSynchronize(c->stream));
+    *bytes = need;
+    return SPH_OK;
+}
+
+sph_status load_state_impl(sph_ctx* c, const void* buf, size_t bytes, bool async) {
+    if (!c || !buf) return fail(c, SPH_ERR_INVALID, "NULL argument");
+    const size_t N = (size_t)c->N;
+    const size_t need = sizeof(StateHeader) + STATE_FIELDS * N * 8 + N * 4;
+    StateHeader H;
+    if (bytes < sizeof H) return fail(c, SPH_ERR_INVALID, "state buffer too small");
+    std::memcpy(&H, buf, sizeof H);
+    if (H.magic != STATE_MAGIC || H.version != STATE_VERSION || H.n != c->N || H.dim != c->dom.dim ||
+        bytes < need)
+        return fail(c, SPH_ERR_INVALID, "state buffer does not match this context");
+    const ParticleSet& S = c->set[c->cur];
+    double* fields[STATE_FIELDS];
+    state_fields(S, fields);
+    const char* p = (const char*)buf + sizeof(StateHeader);
+    for (int k = 0; k < STATE_FIELDS; ++k)
+        CK(cudaMemcpyAsync(fields[k], p + (size_t)k * N * 8, N * 8, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(S.tag, p + STATE_FIELDS * N * 8, N * 4, cudaMemcpyHostToDevice, c->stream));
+    c->work_dirty = true;
+    launch_load_control(c->ctl, H.t, H.dt, H.step, c->stream);  // the rest of the block zeroed
+    CK(cudaGetLastError());
+    if (!async) CK(cudaStreamSynchronize(c->stream));
+    c->have_rates = H.have_rates != 0;
+    c->rates_scheme = H.scheme;
+    c->nbr_valid = false;
+    c->hist_at_call = 0;
+    c->steps_total = 0;
+    return SPH_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1454,9 +1545,20 @@ sph_status sph_step_async(sph_ctx* c, const sph_scheme* scheme, double dt, int32
         s = initial_eval(c, scheme, dt);
         if (s != SPH_OK) return s;
     }
+    if (!c->nl) {
+        // a state loaded with its rates into a context that never evaluated: the neighbour
+        // list is sized at the loaded positions (rates carried along, the order unchanged)
+        s = ensure_neighbors(c);
+        if (s != SPH_OK) return s;
+        s = ensure_list_capacity(c);
+        if (s != SPH_OK) return s;
+    }
     s = upload_single(c, scheme, dt);
     if (s != SPH_OK) return s;
-    if (dt > 0.0) CK(cudaMemcpyAsync(&c->ctl->dt, &dt, sizeof dt, cudaMemcpyHostToDevice, c->stream));
+    if (dt > 0.0) {
+        k_set_dt<<<1, 1, 0, c->stream>>>(c->ctl, dt);
+        CK(cudaGetLastError());
+    }
     if (nsteps == 0) return SPH_OK;
     s = run_steps(c, nsteps);
     if (s != SPH_OK) return s;
@@ -2090,73 +2192,19 @@ sph_status sph_history(sph_ctx* c, double* out, int32_t max_records, int32_t* co
 }
 
 sph_status sph_save_state(sph_ctx* c, void* buf, size_t* bytes) {
-    if (!c || !bytes) return fail(c, SPH_ERR_INVALID, "NULL argument");
-    const size_t N = (size_t)c->N;
-    const size_t need = sizeof(StateHeader) + STATE_FIELDS * N * 8 + N * 4;
-    if (!buf) {
-        *bytes = need;
-        return SPH_OK;
-    }
-    if (*bytes < need) {
-        *bytes = need;
-        return fail(c, SPH_ERR_CAPACITY, "state buffer too small");
-    }
-    StateHeader H{};
-    H.magic = STATE_MAGIC;
-    H.version = STATE_VERSION;
-    H.n = c->N;
-    H.dim = c->dom.dim;
-    H.precision = c->dom.precision;
-    H.have_rates = c->have_rates;
-    H.scheme = c->rates_scheme;
-    Control ctl{};
-    CK(cudaMemcpyAsync(&ctl, c->ctl, sizeof ctl, cudaMemcpyDeviceToHost, c->stream));
-    const ParticleSet& S = c->set[c->cur];
-    double* fields[STATE_FIELDS];
-    state_fields(S, fields);
-    char* p = (char*)buf + sizeof(StateHeader);
-    for (int k = 0; k < STATE_FIELDS; ++k)
-        CK(cudaMemcpyAsync(p + (size_t)k * N * 8, fields[k], N * 8, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(p + STATE_FIELDS * N * 8, S.tag, N * 4, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    H.t = ctl.t;
-    H.dt = ctl.dt;
-    H.step = ctl.step;
-    std::memcpy(buf, &H, sizeof H);
-    *bytes = need;
-    return SPH_OK;
+    return save_state_impl(c, buf, bytes, false);
+}
+
+sph_status sph_save_state_async(sph_ctx* c, void* buf, size_t* bytes) {
+    return save_state_impl(c, buf, bytes, true);
 }
 
 sph_status sph_load_state(sph_ctx* c, const void* buf, size_t bytes) {
-    if (!c || !buf) return fail(c, SPH_ERR_INVALID, "NULL argument");
-    const size_t N = (size_t)c->N;
-    const size_t need = sizeof(StateHeader) + STATE_FIELDS * N * 8 + N * 4;
-    StateHeader H;
-    if (bytes < sizeof H) return fail(c, SPH_ERR_INVALID, "state buffer too small");
-    std::memcpy(&H, buf, sizeof H);
-    if (H.magic != STATE_MAGIC || H.version != STATE_VERSION || H.n != c->N || H.dim != c->dom.dim ||
-        bytes < need)
-        return fail(c, SPH_ERR_INVALID, "state buffer does not match this context");
-    const ParticleSet& S = c->set[c->cur];
-    double* fields[STATE_FIELDS];
-    state_fields(S, fields);
-    const char* p = (const char*)buf + sizeof(StateHeader);
-    for (int k = 0; k < STATE_FIELDS; ++k)
-        CK(cudaMemcpyAsync(fields[k], p + (size_t)k * N * 8, N * 8, cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(S.tag, p + STATE_FIELDS * N * 8, N * 4, cudaMemcpyHostToDevice, c->stream));
-    c->work_dirty = true;
-    Control ctl{};
-    ctl.t = H.t;
-    ctl.dt = H.dt;
-    ctl.step = H.step;
-    CK(cudaMemcpyAsync(c->ctl, &ctl, sizeof ctl, cudaMemcpyHostToDevice, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
-    c->have_rates = H.have_rates != 0;
-    c->rates_scheme = H.scheme;
-    c->nbr_valid = false;
-    c->hist_at_call = 0;
-    c->steps_total = 0;
-    return SPH_OK;
+    return load_state_impl(c, buf, bytes, false);
+}
+
+sph_status sph_load_state_async(sph_ctx* c, const void* buf, size_t bytes) {
+    return load_state_impl(c, buf, bytes, true);
 }
 
 }  // extern "C"

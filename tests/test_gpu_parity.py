@@ -189,6 +189,38 @@ def test_deterministic_and_resumable():
         assert np.array_equal(a.diagnostics(), b.diagnostics())
 
 
+def test_asynchronous_save_and_load_equal_the_synchronous_ones():
+    """sph_save_state_async / sph_load_state_async give the bytes and the continued run of
+    the synchronous calls, also with two contexts streaming states in turn."""
+    import torch
+    wl = W.dam_break_2d(dx=0.02, precision=W.PREC_FP32)
+    sch = G.scheme_of(wl)
+    with sim_of(wl) as a, sim_of(wl) as b:
+        a.step(sch, wl.dt, 12)
+        n = a.state_bytes()
+        sync = np.empty(n, np.uint8)
+        a.save_state_into(sync)
+        pin = torch.empty(n, dtype=torch.uint8, pin_memory=True).numpy()
+        pin[:] = 0
+        a.save_state_into_async(pin)
+        a.synchronize()
+        assert np.array_equal(pin, sync)
+        # a state streamed through both contexts in turn: each continued run equals a.
+        a.step(sch, wl.dt, 7)
+        ref = {k: a.get(k) for k in FIELDS_2D}
+        outs = [torch.empty(n, dtype=torch.uint8, pin_memory=True).numpy() for _ in range(2)]
+        for k, s in enumerate((b, a)):
+            s.load_state_async(pin)
+            s.step_async(sch, wl.dt, 7)
+            s.save_state_into_async(outs[k])
+        for s in (b, a):
+            s.synchronize()
+        for s in (b, a):
+            for k in FIELDS_2D:
+                assert np.array_equal(s.get(k), ref[k]), k
+        assert np.array_equal(outs[0], outs[1])
+
+
 def test_set_get_roundtrip_and_errors():
     wl = W.dam_break_2d(dx=0.05)
     with sim_of(wl) as sim:
