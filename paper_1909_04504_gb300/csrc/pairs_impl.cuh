@@ -212,12 +212,15 @@ __device__ __forceinline__ void pair_separation(const typename V4<Real>::T& pi,
 template <class Real, int DIM>
 __device__ __forceinline__ bool near_periodic_face(const typename V4<Real>::T& pi, const Grid& G,
                                                    const PairConst<Real>& K) {
-    const double reach = 1.01 * sqrt((double)K.kh2);
-    const double xs[3] = {(double)pi.x, (double)pi.y, (double)pi.z};
     bool near = false;
+    if (G.periodic[0] || G.periodic[1] || (DIM == 3 && G.periodic[2])) {
+        // the support radius with a 1 % margin, far above the FP32 rounding of its root
+        const double reach = (double)(1.01f * sqrtf((float)K.kh2));
+        const double xs[3] = {(double)pi.x, (double)pi.y, (double)pi.z};
 #pragma unroll
-    for (int d = 0; d < DIM; ++d)
-        near |= G.periodic[d] && (xs[d] - G.lo[d] < reach || G.hi[d] - xs[d] < reach);
+        for (int d = 0; d < DIM; ++d)
+            near |= G.periodic[d] && (xs[d] - G.lo[d] < reach || G.hi[d] - xs[d] < reach);
+    }
     return __any_sync(__activemask(), near) != 0;
 }
 
