@@ -661,7 +661,10 @@ def gpu_arm(args, rank, world, dist):
     state0 = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not sim.batch:
         state0 = one_step_states(wl, sch)
-    launches = sim.kernels_per_step() * args.steps
+    # the captured step's kernels, plus, for a single problem with a fixed step size, the
+    # one-thread kernel of each sph_step_async call that sets the step size on the stream
+    per_call = 0 if isinstance(raw, list) or wl.dt <= 0 else 1
+    launches = (sim.kernels_per_step() + per_call) * args.steps
     sim.close()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
