@@ -714,10 +714,12 @@ __device__ __forceinline__ void momentum_sums(int i, const Group<T>& g,
     // without the minimum image unless a neighbour can lie across a periodic boundary
     auto pair_loop = [&](auto mi_tag) {
     constexpr bool MI = decltype(mi_tag)::value;
-    uint32_t j_next = g.t < ni ? nl[(size_t)g.t * n + i] : 0u;  // fetched one entry ahead
+    // the list's last reader: its entries are fetched one entry ahead and marked for early
+    // eviction (streaming loads), leaving the caches to the source records
+    uint32_t j_next = g.t < ni ? __ldcs(&nl[(size_t)g.t * n + i]) : 0u;
     for (uint32_t kk = g.t; kk < ni; kk += T) {
         const uint32_t j = j_next;
-        if (kk + T < ni) j_next = nl[(size_t)(kk + T) * n + i];
+        if (kk + T < ni) j_next = __ldcs(&nl[(size_t)(kk + T) * n + i]);
         const typename V4<Real>::T pj = P[j];
         Real dx, dy, dz;
         pair_separation<Real, DIM, MI>(pi, pj, G, K, dx, dy, dz);
