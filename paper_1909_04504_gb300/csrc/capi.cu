@@ -86,7 +86,8 @@ struct sph_ctx {
     uint32_t* off = nullptr;
     uint32_t* hist = nullptr;
     double* pm = nullptr;  // momentum-pass block partials (8 doubles per block)
-    double* pd = nullptr;  // density-pass block partials (4 doubles per block)
+    double* pd = nullptr;     // density-pass block partials (4 doubles per block)
+    double* cpart = nullptr;  // momentum chunk partials (single problem, one lane)
     Control* ctl = nullptr;
     double* history = nullptr;
     void* io = nullptr;  // scratch for get/set/exports: 4 N + 2 (8 N + 8) bytes, 256-aligned parts
@@ -426,6 +427,8 @@ StepLaunch step_launch(sph_ctx* c, int kick) {
     L.edac = c->edac ? 1 : 0;
     L.skeys = c->skeys;
     L.off = c->off;
+    L.cpart = c->ninst == 0 ? c->cpart : nullptr;
+    L.mom_dyn = c->nwall > 0 ? 1 : 0;
     L.nl = c->nl;
     L.cnt = c->cnt;
     L.pcount = c->pcount;
@@ -1024,6 +1027,7 @@ sph_status create_impl(const sph_domain* domains, int ninst, const sph_array_des
     bytes += al(radix_hist_words(c->N) * 4);                   // radix histograms
     bytes += al(sort_work_words(c->N, c->passes) * 4);          // one-sweep workspace
     bytes += al((size_t)c->grid_cap * 8 * 8) + al((size_t)c->grid_cap * 4 * 8);  // partials
+    bytes += al(((size_t)c->N + 31) / 32 * 8 * 8);  // momentum chunk partials
     bytes += al(N * 4);                                        // neighbour-list lengths
     bytes += al((size_t)c->sms * FUSED_MAX_BPS * FUSED_PART * 8);  // persistent partials
     bytes += al(sizeof(Control));
@@ -1068,6 +1072,7 @@ sph_status create_impl(const sph_domain* domains, int ninst, const sph_array_des
     c->sort_work = (uint32_t*)arena_take(p, sort_work_words(c->N, c->passes) * 4);
     c->pm = (double*)arena_take(p, (size_t)c->grid_cap * 8 * 8);
     c->pd = (double*)arena_take(p, (size_t)c->grid_cap * 4 * 8);
+    c->cpart = (double*)arena_take(p, ((size_t)c->N + 31) / 32 * 8 * 8);
     c->cnt = (uint32_t*)arena_take(p, N * 4);
     c->fpart = (double*)arena_take(p, (size_t)c->sms * FUSED_MAX_BPS * FUSED_PART * 8);
     c->ctl = (Control*)arena_take(p, sizeof(Control));
@@ -1615,7 +1620,9 @@ sph_status sph_kernels_per_step(const sph_ctx* ctx, const sph_scheme* scheme, in
     // a batch); the midpoint integrator runs two of these and three stage kernels
     const bool wp = scheme->wall_bc == SPH_WALL_ADAMI && c->nwall > 0;
     const bool pec = scheme->integrator == SPH_INTEGRATOR_PEC;
-    const int build_eval = 1 + c->passes + 1 + 1 + (wp ? 1 : 0) + 1 + (c->ninst ? 2 : 0);
+    // (+ the chunk-partial finalize of a single problem's one-lane momentum pass with walls)
+    const int build_eval = 1 + c->passes + 1 + 1 + (wp ? 1 : 0) + 1 + (c->ninst ? 2 : 0) +
+                           (c->ninst == 0 && c->group_m == 1 && c->nwall > 0 ? 1 : 0);
     if (pec) *count = 2 * build_eval + 3;  // + predictor, corrector, record
     else *count = c->step_mode == SPH_STEP_PERSISTENT ? 1 : build_eval;
     return SPH_OK;

@@ -30,6 +30,7 @@
 namespace sph {
 
 constexpr int PAIR_THREADS = 128;
+constexpr int MOM_CHUNK = 32;  // destinations a warp takes at a time (one-lane momentum pass)
 
 // The stencil walk clipped to the support: a row (dy, dz) whose distance from the
 // destination in (y, z) reaches the support radius is skipped, and in every other row the
@@ -243,6 +244,20 @@ struct DensityCounts {
 
 __device__ __forceinline__ unsigned long long u64max(unsigned long long a, unsigned long long b) {
     return a > b ? a : b;
+}
+
+// Reduction of a warp's momentum diagnostics into lane 0 (fixed order).
+__device__ __forceinline__ void warp_mom_diag(MomDiag& md) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        md.px += __shfl_down_sync(0xffffffffu, md.px, o);
+        md.py += __shfl_down_sync(0xffffffffu, md.py, o);
+        md.pz += __shfl_down_sync(0xffffffffu, md.pz, o);
+        md.ke += __shfl_down_sync(0xffffffffu, md.ke, o);
+        md.u2b = u64max(md.u2b, __shfl_down_sync(0xffffffffu, md.u2b, o));
+        md.a2b = u64max(md.a2b, __shfl_down_sync(0xffffffffu, md.a2b, o));
+        md.bad |= __shfl_down_sync(0xffffffffu, md.bad, o);
+    }
 }
 
 // Block reduction of the momentum diagnostics held by the first NW warps (fixed order);
@@ -844,10 +859,62 @@ __device__ __forceinline__ void momentum_tiles(int block, int nblocks,
                                                int kick, const uint32_t* __restrict__ nl,
                                                const uint32_t* __restrict__ cnt, MomDiag& md,
                                                MomSmem<Real, T == 1 ? 1 : NTH / T>& sm,
-                                               const Inst<Real>* I0 = nullptr) {
+                                               const Inst<Real>* I0 = nullptr,
+                                               unsigned int* next = nullptr,
+                                               double* __restrict__ cpart = nullptr) {
     constexpr int GM = NTH / T;
     const Group<T> g;
     const int grp = threadIdx.x / T;
+    if (T == 1 && next) {
+        // each warp takes the next chunk of MOM_CHUNK destinations (MOM_CHUNK / 32 rows of the
+        // warp) from a counter: chunks of wall destinations (no pair sums) and of fluid ones
+        // differ widely in cost. The diagnostics of a chunk are reduced over its lanes in a
+        // fixed order and written to the chunk's slot of cpart (when given), so that their sum
+        // does not depend on which warp took which chunk.
+        const int lane = threadIdx.x & 31;
+        for (;;) {
+            unsigned int c = 0u;
+            if (lane == 0) c = atomicAdd(next, 1u);
+            c = __shfl_sync(0xffffffffu, c, 0);
+            if ((long long)c * MOM_CHUNK >= n) break;
+            MomDiag mc{0, 0, 0, 0, 0ull, 0ull, 0u};
+#pragma unroll 1
+            for (int r = 0; r < MOM_CHUNK / 32; ++r) {
+                const long long il = (long long)c * MOM_CHUNK + r * 32 + lane;
+                if (il >= n) break;
+                const int i = (int)il;
+                const int inst = SINGLE ? 0 : find_instance(cell_bounds, ninst, skeys[i]);
+                const Inst<Real>& I = SINGLE ? *I0 : tab[inst];
+                const typename V4<Real>::T pi = P[i];
+                const bool fluid = pi.w > Real(0);
+                Acc<Real> acc[6];
+                if (fluid) momentum_sums<Real, DIM, KERNEL, T>(i, g, pi, P, Q, R, E, n, I.G, I.K, nl, cnt, acc);
+                else
+#pragma unroll
+                    for (int k = 0; k < 6; ++k) acc[k].zero();
+                double a[3], xs[3];
+                for (int d = 0; d < 3; ++d) {
+                    a[d] = acc[d].value();
+                    xs[d] = acc[3 + d].value();
+                }
+                momentum_finish<DIM>(i, fluid, a, xs, I.C, S, idt[inst], kick, mc);
+            }
+            if (cpart) {
+                warp_mom_diag(mc);
+                if (lane == 0) {
+                    double* o = cpart + (size_t)c * 8;
+                    o[0] = mc.px;
+                    o[1] = mc.py;
+                    o[2] = mc.pz;
+                    o[3] = mc.ke;
+                    o[4] = __longlong_as_double((long long)mc.u2b);
+                    o[5] = __longlong_as_double((long long)mc.a2b);
+                    o[6] = __longlong_as_double((long long)mc.bad);
+                }
+            }
+        }
+        return;
+    }
     for (int tile = block; (long long)tile * GM < n; tile += nblocks) {
         const int i = tile * GM + grp;
         if (i < n) {
@@ -912,7 +979,7 @@ k_momentum(const __grid_constant__ Inst<Real> I0,
            double* __restrict__ idt, ParticleSet S, Control* ctl, int kick,
            const uint32_t* __restrict__ nl, const uint32_t* __restrict__ cnt,
            double* __restrict__ pm, const double* __restrict__ pd, int density_blocks,
-           double* __restrict__ history, int finalize) {
+           double* __restrict__ history, int finalize, double* __restrict__ cpart, int dyn) {
     constexpr int GM = PAIR_THREADS / T;
     __shared__ MomSmem<Real, T == 1 ? 1 : GM> sm;
     __shared__ MomDiag red[PAIR_THREADS / 32];
@@ -920,10 +987,23 @@ k_momentum(const __grid_constant__ Inst<Real> I0,
     __shared__ bool is_last;
     if (ctl->status) return;
     MomDiag md{0, 0, 0, 0, 0ull, 0ull, 0u};
+    // one lane per destination with dyn: chunks from a counter, for a batch (whose
+    // diagnostics come from the state) or with chunk partials (cpart) for a single problem
+    unsigned int* next = (T == 1 && dyn && (cpart != nullptr || !finalize)) ? &ctl->mom_next : nullptr;
     momentum_tiles<Real, DIM, KERNEL, T, PAIR_THREADS, SINGLE>(blockIdx.x, gridDim.x, P, Q, R, E, skeys, n,
                                                                tab, cell_bounds, ninst, idt, S, kick, nl, cnt,
-                                                               md, sm, &I0);
-    if (!finalize) return;
+                                                               md, sm, &I0, next, cpart);
+    if (next) {  // the last block done resets the chunk counter for the next launch
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned int d = atomicAdd(&ctl->mom_done, 1u);
+            if (d == gridDim.x - 1) {
+                ctl->mom_next = 0u;
+                ctl->mom_done = 0u;
+            }
+        }
+    }
+    if (!finalize || cpart) return;  // chunk partials: k_mom_finalize reduces them
     const double dt = idt[0];
     // ---- block partials (epilogue threads: the first ceil(GM / 32) warps)
     block_mom_diag<(GM + 31) / 32>(md, pm + (size_t)blockIdx.x * 8, red);
@@ -941,6 +1021,52 @@ k_momentum(const __grid_constant__ Inst<Real> I0,
     if (threadIdx.x == 0) {
         ctl->ticket = 0;
         finish_single(ctl, history, SINGLE ? I0.C : tab[0].C, dt, kick, out);
+    }
+}
+
+// Diagnostics of a single problem's evaluation whose momentum pass ran one lane per
+// destination: block b sums the chunk partials of a fixed range of chunks (fixed order), the
+// last block both passes' block partials, then writes the record, history entry, next dt and
+// status. FIN_THREADS threads.
+constexpr int FIN_THREADS = 256;
+
+template <int NTH>
+__global__ void __launch_bounds__(NTH)
+k_mom_finalize(const double* __restrict__ cpart, int nchunks, double* __restrict__ pm,
+               const double* __restrict__ pd, int density_blocks, Control* ctl,
+               double* __restrict__ history, const StepConst C, const double* __restrict__ idt,
+               int kick) {
+    __shared__ MomDiag red[NTH / 32];
+    __shared__ unsigned long long cred[NTH / 32][3];
+    __shared__ bool is_last;
+    if (ctl->status) return;
+    const int per = (nchunks + gridDim.x - 1) / gridDim.x;
+    const int lo = blockIdx.x * per, hi = min(nchunks, lo + per);
+    MomDiag md{0, 0, 0, 0, 0ull, 0ull, 0u};
+    for (int c = lo + threadIdx.x; c < hi; c += NTH) {
+        const double* p = cpart + (size_t)c * 8;
+        md.px += p[0];
+        md.py += p[1];
+        md.pz += p[2];
+        md.ke += p[3];
+        md.u2b = u64max(md.u2b, (unsigned long long)__double_as_longlong(p[4]));
+        md.a2b = u64max(md.a2b, (unsigned long long)__double_as_longlong(p[5]));
+        md.bad |= (unsigned)__double_as_longlong(p[6]);
+    }
+    block_mom_diag<NTH / 32>(md, pm + (size_t)blockIdx.x * 8, red);
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned t = atomicAdd(&ctl->ticket, 1u);
+        is_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    double out[10];
+    reduce_partials<NTH>(pm, 8, gridDim.x, pd, 4, density_blocks, out, red, cred);
+    if (threadIdx.x == 0) {
+        ctl->ticket = 0;
+        finish_single(ctl, history, C, idt[0], kick, out);
     }
 }
 
@@ -981,10 +1107,22 @@ void launch_momentum_t(const StepLaunch& L, cudaStream_t st) {
     const bool single = L.tab_host != nullptr;
     const Inst<Real> I0 = single ? *(const Inst<Real>*)L.tab_host : Inst<Real>{};
     auto k = single ? k_momentum<Real, DIM, KERNEL, T, true> : k_momentum<Real, DIM, KERNEL, T, false>;
+    // chunks taken from a counter where costs differ widely (wall destinations have no pair
+    // sums); a single problem's diagnostics then go through chunk partials and k_mom_finalize
+    const bool dyn = T == 1 && L.mom_dyn;
+    const bool chunked = dyn && L.finalize && single && L.cpart;
     k<<<L.grid_m, PAIR_THREADS, 0, st>>>(
         I0, (const V*)L.P, (const V*)L.Q, (const Real*)L.R, (const F4*)L.E, L.skeys, L.n,
         (const Inst<Real>*)L.tab, L.cell_bounds, L.ninst, L.idt, L.S, L.ctl, L.kick, L.nl, L.cnt, L.pm, L.pd,
-        L.grid_d, L.history, L.finalize);
+        L.grid_d, L.history, L.finalize, chunked ? L.cpart : nullptr, dyn ? 1 : 0);
+    if (chunked) {
+        const int nchunks = (L.n + MOM_CHUNK - 1) / MOM_CHUNK;
+        int nb = (nchunks + FIN_THREADS - 1) / FIN_THREADS;
+        nb = nb < 1 ? 1 : (nb > L.sms ? L.sms : nb);
+        const StepConst C = single ? I0.C : StepConst{};
+        k_mom_finalize<FIN_THREADS><<<nb, FIN_THREADS, 0, st>>>(L.cpart, nchunks, L.pm, L.pd, L.grid_d, L.ctl, L.history, C,
+                                                  L.idt, L.kick);
+    }
 }
 
 // One precision's dispatch over (dim, kernel, group size).

@@ -66,6 +66,10 @@ struct Control {
     // 128-byte line so that the pollers of one do not contend with the atomics on the other
     alignas(128) unsigned int bar_count;
     alignas(128) unsigned int bar_gen;
+    // momentum pass, one lane per destination: the next chunk of 32 destinations a warp
+    // takes, and the blocks done (the last block resets both for the next launch)
+    alignas(128) unsigned int mom_next;
+    unsigned int mom_done;
 };
 
 // Grid of cells (Sec. 2.2): cells no smaller than the support radius.

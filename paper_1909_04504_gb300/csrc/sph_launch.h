@@ -71,6 +71,8 @@ struct StepLaunch {
     double* bpart;                // batch: BATCH_SPLIT x 10 partial diagnostics per instance
     double* pm;                   // single: 8 doubles per momentum block
     double* pd;                   // single: 4 doubles per density block
+    double* cpart;                // single: 8 doubles per chunk of destinations (momentum, one lane)
+    int mom_dyn;                  // one-lane momentum pass: chunks from a counter (problems with walls)
     double* history;
     Control* ctl;
 };
