@@ -634,10 +634,34 @@ __device__ __forceinline__ void density_tiles(int block, int nblocks,
                                               uint32_t* __restrict__ cnt, int maxn,
                                               uint32_t* __restrict__ pcount, DensityCounts& dc,
                                               DensitySmem<Real, T == 1 ? 1 : NTH / T>& sm,
-                                              const Inst<Real>* I0 = nullptr) {
+                                              const Inst<Real>* I0 = nullptr,
+                                              unsigned int* next = nullptr) {
     constexpr int GD = NTH / T;
     const Group<T> g;
     const int grp = threadIdx.x / T;
+    if (T == 1 && next) {
+        // each warp takes the next chunk of 32 destinations from a counter (the counts this
+        // pass accumulates are integers: their sum does not depend on the assignment)
+        const int lane = threadIdx.x & 31;
+        for (;;) {
+            unsigned int c = 0u;
+            if (lane == 0) c = atomicAdd(next, 1u);
+            c = __shfl_sync(0xffffffffu, c, 0);
+            if ((long long)c * 32 >= n) break;
+            const int i = (int)c * 32 + lane;
+            if (i < n) {
+                const uint32_t key = skeys[i];
+                const int inst = SINGLE ? 0 : find_instance(cell_bounds, ninst, key);
+                const Inst<Real>& I = SINGLE ? *I0 : tab[inst];
+                Acc<Real> sum;
+                density_scan_sum<Real, DIM, KERNEL, T>(i, g, key - I.cell_base, P, Q, E, off + I.cell_base,
+                                                       n, I.G, I.K, nl, cnt, maxn, dc,
+                                                       pcount ? pcount + 2 * (size_t)i : nullptr, sum);
+                density_finish<Real, KERNEL>(i, sum.value(), P[i].w, Q, R, I.K, I.C, S, idt[inst], kick);
+            }
+        }
+        return;
+    }
     for (int tile = block; (long long)tile * GD < n; tile += nblocks) {
         const int i = tile * GD + grp;
         if (i < n) {
@@ -692,7 +716,18 @@ k_density(const __grid_constant__ Inst<Real> I0,
     DensityCounts dc{0ull, 0ull, 0ull, 0};
     density_tiles<Real, DIM, KERNEL, T, PAIR_THREADS, SINGLE>(blockIdx.x, gridDim.x, P, Q, R, E, skeys, off,
                                                               n, tab, cell_bounds, ninst, idt, S, kick, nl,
-                                                              cnt, maxn, pcount, dc, sm, &I0);
+                                                              cnt, maxn, pcount, dc, sm, &I0,
+                                                              T == 1 ? &ctl->dens_next : nullptr);
+    if (T == 1) {  // the last block done resets the chunk counter for the next launch
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const unsigned int d = atomicAdd(&ctl->dens_done, 1u);
+            if (d == gridDim.x - 1) {
+                ctl->dens_next = 0u;
+                ctl->dens_done = 0u;
+            }
+        }
+    }
     if (dc.overflow) atomicOr(&ctl->status, ST_CAPACITY);
     if (pd) block_counts<PAIR_THREADS>(dc, pd + (size_t)blockIdx.x * 4, cred);
 }

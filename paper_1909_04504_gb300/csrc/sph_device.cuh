@@ -70,6 +70,9 @@ struct Control {
     // takes, and the blocks done (the last block resets both for the next launch)
     alignas(128) unsigned int mom_next;
     unsigned int mom_done;
+    // density pass, one lane per destination: the same for its chunks
+    alignas(128) unsigned int dens_next;
+    unsigned int dens_done;
 };
 
 // Grid of cells (Sec. 2.2): cells no smaller than the support radius.
