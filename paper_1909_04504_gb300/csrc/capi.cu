@@ -428,7 +428,7 @@ StepLaunch step_launch(sph_ctx* c, int kick) {
     L.skeys = c->skeys;
     L.off = c->off;
     L.cpart = c->ninst == 0 ? c->cpart : nullptr;
-    L.mom_dyn = c->nwall > 0 ? 1 : 0;
+    L.dyn = (c->ninst == 0 ? 1 : 0) | (c->nwall > 0 ? 2 : 0);
     L.nl = c->nl;
     L.cnt = c->cnt;
     L.pcount = c->pcount;

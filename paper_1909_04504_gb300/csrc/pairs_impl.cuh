@@ -640,8 +640,10 @@ __device__ __forceinline__ void density_tiles(int block, int nblocks,
     const Group<T> g;
     const int grp = threadIdx.x / T;
     if (T == 1 && next) {
-        // each warp takes the next chunk of 32 destinations from a counter (the counts this
-        // pass accumulates are integers: their sum does not depend on the assignment)
+        // each warp takes the next chunk of 32 destinations from a counter (single problems:
+        // chunks differ in cost, most of all where wall destinations list fluid sources only;
+        // the counts this pass accumulates are integers, so their sum does not depend on the
+        // assignment)
         const int lane = threadIdx.x & 31;
         for (;;) {
             unsigned int c = 0u;
@@ -699,9 +701,10 @@ __device__ __forceinline__ void density_tiles(int block, int nblocks,
 // counts to pcount for the per-instance reduction.
 // SINGLE: a single problem, whose constants come by value in the parameter bank (I0), so
 // that the pair arithmetic reads them as constant operands instead of holding them in
-// registers; batches read their instance's entry of the table.
+// registers; batches read their instance's entry of the table. The single-problem FP32 form
+// is bounded to 64 registers (8 blocks of 128 per SM), which it fits without spills.
 template <class Real, int DIM, int KERNEL, int T, bool SINGLE>
-__global__ void __launch_bounds__(PAIR_THREADS, sizeof(Real) == 4 ? 7 : 6)
+__global__ void __launch_bounds__(PAIR_THREADS, sizeof(Real) == 4 ? (SINGLE ? 8 : 7) : 6)
 k_density(const __grid_constant__ Inst<Real> I0,
           const typename V4<Real>::T* __restrict__ P, typename V4<Real>::T* __restrict__ Q,
           Real* __restrict__ R, const F4* __restrict__ E, const uint32_t* __restrict__ skeys,
@@ -709,7 +712,7 @@ k_density(const __grid_constant__ Inst<Real> I0,
           int n, const Inst<Real>* __restrict__ tab, const uint32_t* __restrict__ cell_bounds,
           int ninst, const double* __restrict__ idt, ParticleSet S, Control* ctl, int kick,
           uint32_t* __restrict__ nl, uint32_t* __restrict__ cnt, int maxn,
-          double* __restrict__ pd, uint32_t* __restrict__ pcount) {
+          double* __restrict__ pd, uint32_t* __restrict__ pcount, int dyn) {
     __shared__ DensitySmem<Real, T == 1 ? 1 : PAIR_THREADS / T> sm;
     __shared__ unsigned long long cred[PAIR_THREADS / 32][3];
     if (ctl->status) return;
@@ -717,8 +720,8 @@ k_density(const __grid_constant__ Inst<Real> I0,
     density_tiles<Real, DIM, KERNEL, T, PAIR_THREADS, SINGLE>(blockIdx.x, gridDim.x, P, Q, R, E, skeys, off,
                                                               n, tab, cell_bounds, ninst, idt, S, kick, nl,
                                                               cnt, maxn, pcount, dc, sm, &I0,
-                                                              T == 1 ? &ctl->dens_next : nullptr);
-    if (T == 1) {  // the last block done resets the chunk counter for the next launch
+                                                              T == 1 && (dyn & 1) ? &ctl->dens_next : nullptr);
+    if (T == 1 && (dyn & 1)) {  // the last block done resets the chunk counter for the next launch
         __syncthreads();
         if (threadIdx.x == 0) {
             const unsigned int d = atomicAdd(&ctl->dens_done, 1u);
@@ -1133,7 +1136,7 @@ void launch_density_t(const StepLaunch& L, cudaStream_t st) {
     k<<<L.grid_d, PAIR_THREADS, 0, st>>>(
         I0, (const V*)L.P, (V*)L.Q, (Real*)L.R, (const F4*)L.E, L.skeys, L.off, L.n, (const Inst<Real>*)L.tab,
         L.cell_bounds, L.ninst, L.idt, L.S, L.ctl, L.kick, L.nl, L.cnt, L.maxn,
-        L.finalize ? L.pd : nullptr, L.finalize ? nullptr : L.pcount);
+        L.finalize ? L.pd : nullptr, L.finalize ? nullptr : L.pcount, L.dyn);
 }
 
 template <class Real, int DIM, int KERNEL, int T>
@@ -1144,7 +1147,7 @@ void launch_momentum_t(const StepLaunch& L, cudaStream_t st) {
     auto k = single ? k_momentum<Real, DIM, KERNEL, T, true> : k_momentum<Real, DIM, KERNEL, T, false>;
     // chunks taken from a counter where costs differ widely (wall destinations have no pair
     // sums); a single problem's diagnostics then go through chunk partials and k_mom_finalize
-    const bool dyn = T == 1 && L.mom_dyn;
+    const bool dyn = T == 1 && (L.dyn & 2);
     const bool chunked = dyn && L.finalize && single && L.cpart;
     k<<<L.grid_m, PAIR_THREADS, 0, st>>>(
         I0, (const V*)L.P, (const V*)L.Q, (const Real*)L.R, (const F4*)L.E, L.skeys, L.n,

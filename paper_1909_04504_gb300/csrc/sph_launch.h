@@ -72,7 +72,8 @@ struct StepLaunch {
     double* pm;                   // single: 8 doubles per momentum block
     double* pd;                   // single: 4 doubles per density block
     double* cpart;                // single: 8 doubles per chunk of destinations (momentum, one lane)
-    int mom_dyn;                  // one-lane momentum pass: chunks from a counter (problems with walls)
+    int dyn;                      // one-lane passes taking chunks from a counter: 1 density (single
+                                  // problems), 2 momentum (problems with walls)
     double* history;
     Control* ctl;
 };
