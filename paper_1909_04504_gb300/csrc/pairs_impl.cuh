@@ -715,12 +715,16 @@ k_density(const __grid_constant__ Inst<Real> I0,
           double* __restrict__ pd, uint32_t* __restrict__ pcount, int dyn) {
     __shared__ DensitySmem<Real, T == 1 ? 1 : PAIR_THREADS / T> sm;
     __shared__ unsigned long long cred[PAIR_THREADS / 32][3];
-    if (ctl->status) return;
+    // a block that starts after an earlier one raised a status (a list overflow) does no
+    // work, but still counts itself done below, so the chunk counter is reset all the same
+    const bool skip = ctl->status != 0u;
     DensityCounts dc{0ull, 0ull, 0ull, 0};
-    density_tiles<Real, DIM, KERNEL, T, PAIR_THREADS, SINGLE>(blockIdx.x, gridDim.x, P, Q, R, E, skeys, off,
-                                                              n, tab, cell_bounds, ninst, idt, S, kick, nl,
-                                                              cnt, maxn, pcount, dc, sm, &I0,
-                                                              T == 1 && (dyn & 1) ? &ctl->dens_next : nullptr);
+    if (!skip)
+        density_tiles<Real, DIM, KERNEL, T, PAIR_THREADS, SINGLE>(blockIdx.x, gridDim.x, P, Q, R, E, skeys,
+                                                                  off, n, tab, cell_bounds, ninst, idt, S, kick,
+                                                                  nl, cnt, maxn, pcount, dc, sm, &I0,
+                                                                  T == 1 && (dyn & 1) ? &ctl->dens_next
+                                                                                      : nullptr);
     if (T == 1 && (dyn & 1)) {  // the last block done resets the chunk counter for the next launch
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -731,6 +735,7 @@ k_density(const __grid_constant__ Inst<Real> I0,
             }
         }
     }
+    if (skip) return;
     if (dc.overflow) atomicOr(&ctl->status, ST_CAPACITY);
     if (pd) block_counts<PAIR_THREADS>(dc, pd + (size_t)blockIdx.x * 4, cred);
 }

@@ -191,3 +191,50 @@ def test_one_lane_runs_repeat_bitwise(name):
     for k in ("x", "y", "z", "u", "v", "w", "rho"):
         assert np.array_equal(sa[k], sb[k]), k
     assert np.array_equal(ha, hb)
+
+
+def _collapsing_ball(n=4000, seed=9):
+    """A ball of fluid whose particles all move towards its centre (a sound speed so low that
+    the pressure does not stop them): within a few steps the neighbour counts grow far beyond
+    the list capacity sized at the start."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    h, r0 = 0.01, 0.1
+    d = rng.normal(size=(n, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    pts = 0.5 + d * (r0 * rng.uniform(size=n) ** (1.0 / 3.0))[:, None]
+    dt = 0.25 * h / 20.0
+    vel = -(pts - 0.5) * (0.5 / (8 * dt))  # the radius halves in about 8 steps
+    fl = W.ParticleSet(name="fluid", role=W.FLUID, x=pts[:, 0].copy(), y=pts[:, 1].copy(),
+                       z=pts[:, 2].copy(), u=vel[:, 0].copy(), v=vel[:, 1].copy(),
+                       w=vel[:, 2].copy(), rho=np.full(n, 1000.0),
+                       m=np.full(n, 1000.0 * (4.19 * r0 ** 3 / n)))
+    return W.Workload(name="ball", dim=3, kernel=W.WENDLAND_C2, h=h, lo=[0.0, 0.0, 0.0],
+                      hi=[1.0, 1.0, 1.0], periodic=[0, 0, 0], precision=W.PREC_FP32,
+                      arrays=[fl], rho0=1000.0, c0=0.5, alpha=0.1, xsph_eps=0.5,
+                      g=[0.0, 0.0, 0.0], dt=dt, steps=1)
+
+
+def test_list_overflow_then_the_state_set_again():
+    """A list overflow stops the run with an error; set again, the context continues as a
+    fresh one: the same pair and candidate counts, fields equal up to the summation order
+    (the used context's particles keep their own order within a cell). A chunk counter left
+    behind by the blocks that skipped their work after the overflow would drop chunks of
+    destinations and change the counts."""
+    wl = _collapsing_ball()
+    sch = G.scheme_of(wl)
+    s0 = O.state_of(wl)
+    keys = ("x", "y", "z", "u", "v", "w", "rho")
+    with sim_of(wl) as a, sim_of(wl) as b:
+        for sim in (a, b):
+            sim.set_groups(1)
+        with pytest.raises(G.SphError, match="CAPACITY"):
+            a.step(sch, wl.dt, 14)
+        for k in keys:
+            a.set(k, s0[k])
+        a.step(sch, wl.dt, 2)
+        b.step(sch, wl.dt, 2)
+        sa, sb = a.state(), b.state()
+        da, db = a.diagnostics(), b.diagnostics()
+        assert da[8] == db[8] and da[9] == db[9]
+        for k in keys:  # the change over the two steps
+            assert rel_l2(sa[k] - s0[k], sb[k] - s0[k]) <= 1e-5, k
