@@ -69,9 +69,11 @@ k_keys_hist(ParticleSet S, int n, const Inst<Real>* __restrict__ tab,
     }
 }
 
-// One radix pass in one launch (decoupled look-back); one tile per block.
+// One radix pass in one launch (decoupled look-back); one tile per block. Tiles of 8 keys
+// per thread are held to 48 registers (5 blocks per SM instead of 4 at 60: 2 % faster on
+// 2.9 M keys; tiles of 16 keys were slower at either occupancy), tiles of 4 to 40.
 template <int ITEMS>
-__global__ void __launch_bounds__(SORT_THREADS)
+__global__ void __launch_bounds__(SORT_THREADS, ITEMS == 8 ? 5 : 6)
 k_radix_onesweep(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
                  uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int n, int shift,
                  const uint32_t* __restrict__ ghist, uint32_t* status, uint32_t* counter,

@@ -221,6 +221,41 @@ def test_asynchronous_save_and_load_equal_the_synchronous_ones():
         assert np.array_equal(outs[0], outs[1])
 
 
+def test_asynchronous_save_holds_the_state_of_its_place_on_the_stream():
+    """An asynchronous save gives the state at its place on the context stream, whatever
+    loads and steps are enqueued after it; two saves into one buffer land in the order they
+    were enqueued; the diagnostics in between read the record without disturbing them."""
+    import torch
+    wl = W.dam_break_2d(dx=0.02, precision=W.PREC_FP32)
+    sch = G.scheme_of(wl)
+    with sim_of(wl) as a:
+        a.step(sch, wl.dt, 5)
+        n = a.state_bytes()
+        s0 = np.empty(n, np.uint8)
+        a.save_state_into(s0)
+        a.step(sch, wl.dt, 4)
+        s1 = np.empty(n, np.uint8)
+        a.save_state_into(s1)
+        p0 = torch.empty(n, dtype=torch.uint8, pin_memory=True).numpy()
+        p0[:] = s0
+        o = [torch.empty(n, dtype=torch.uint8, pin_memory=True).numpy() for _ in range(3)]
+        for b in o:
+            b[:] = 0
+        a.load_state_async(p0)
+        a.save_state_into_async(o[0])
+        a.step_async(sch, wl.dt, 4)
+        a.save_state_into_async(o[1])
+        a.load_state_async(p0)
+        a.save_state_into_async(o[2])
+        a.diagnostics()
+        a.step_async(sch, wl.dt, 4)
+        a.save_state_into_async(o[2])
+        a.synchronize()
+        assert np.array_equal(o[0], s0)
+        assert np.array_equal(o[1], s1)
+        assert np.array_equal(o[2], s1)
+
+
 def test_set_get_roundtrip_and_errors():
     wl = W.dam_break_2d(dx=0.05)
     with sim_of(wl) as sim:
