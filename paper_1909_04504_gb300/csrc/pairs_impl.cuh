@@ -702,9 +702,21 @@ __device__ __forceinline__ void density_tiles(int block, int nblocks,
 // SINGLE: a single problem, whose constants come by value in the parameter bank (I0), so
 // that the pair arithmetic reads them as constant operands instead of holding them in
 // registers; batches read their instance's entry of the table. The single-problem FP32 form
-// is bounded to 64 registers (8 blocks of 128 per SM), which it fits without spills.
+// is bounded to 8 or 9 blocks of 128 per SM (density_single_blocks), which it fits without
+// spills.
+template <int DIM, int KERNEL, int T>
+constexpr int density_single_blocks() {
+    // 9 blocks (56 registers) for the one-lane 3D passes of the Wendland C2 and cubic spline
+    // kernels: 3 % faster than 8 on the 3D dam break and the falling cube, although at 56
+    // registers the compiler recomputes FP64 values of the scan loop that 60 let it hold.
+    // 8 blocks (60 registers) elsewhere: at 9 the quintic's 3D pass (Taylor-Green 3D) ran
+    // 3.4 % slower and a 2D pass (the dam break at 4 lanes) 1 % slower.
+    return DIM == 3 && T == 1 && KERNEL != QUINTIC ? 9 : 8;
+}
+
 template <class Real, int DIM, int KERNEL, int T, bool SINGLE>
-__global__ void __launch_bounds__(PAIR_THREADS, sizeof(Real) == 4 ? (SINGLE ? 8 : 7) : 6)
+__global__ void __launch_bounds__(PAIR_THREADS,
+                                  sizeof(Real) == 4 ? (SINGLE ? density_single_blocks<DIM, KERNEL, T>() : 7) : 6)
 k_density(const __grid_constant__ Inst<Real> I0,
           const typename V4<Real>::T* __restrict__ P, typename V4<Real>::T* __restrict__ Q,
           Real* __restrict__ R, const F4* __restrict__ E, const uint32_t* __restrict__ skeys,
